@@ -1,0 +1,96 @@
+/*
+ * nh_oracle.h -- plain FP64 CPU oracle for the depth-integrated non-hydrostatic
+ * (Yamazaki) system of Escalante, Morales de Luna & Castro, arXiv:1706.04551.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This header and nh_oracle.c are the reference that the
+ * CUDA library is checked against.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / --impl reference legs of bench.py may load it.  It shares no code,
+ * header, table or constant with the CUDA library, and the library never loads it.
+ *
+ * Layout: cell arrays are row-major [ny][nx] (x fastest), node arrays (p, w) are
+ * row-major [ny+1][nx+1]; node (I, J) sits at x = I*dx, y = J*dy, i.e. between cells
+ * I-1 and I in x and J-1 and J in y.  1D problems use the or1d_* entry points with
+ * cells [nx] and nodes [nx+1].  All arrays are double and owned by the caller.
+ *
+ * Parity status per function (pins live in tests/test_oracle_*.py, marked "not gpu"):
+ *   hyperbolic step 1D/2D ................. pinned (exact dam-break solutions, lake at rest,
+ *                                           mass, mirror / transpose symmetry)
+ *   or1d_nh_matrix (Eq. 43) ................ pinned (operator of Eqs. 24-28, App. B A.2)
+ *   or2d_apply_M / or2d_rhs / or2d_solve ... pinned (dense LU, y-invariant reduction to Eq. 43)
+ *   full step 1D/2D ........................ pinned (dispersion relation, solitary wave,
+ *                                           Table 1 orders, 2D == 1D on y-invariant data)
+ *   breaking terms (Sec. 3, Eq. 12) ........ parity unpinned beyond invariants (lake at rest
+ *                                           with breaking on, switch-off limit, dissipation)
+ */
+#ifndef NH_ORACLE_H
+#define NH_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { OR_WALL = 0, OR_OUTFLOW = 1, OR_PERIODIC = 2 };
+
+typedef struct {
+    int nx, ny;          /* cells; 1D entry points ignore ny                          */
+    double dx, dy;
+    int bc[4];           /* west, east, south, north (OR_WALL / OR_OUTFLOW / OR_PERIODIC;
+                            periodic only in 1D)                                      */
+    double g, cfl;
+    double delta;        /* desingularisation depth of Sec. 4.5 (1e-5)                 */
+    double hdry;         /* a cell is dry when h <= hdry                              */
+    double manning;      /* Gauckler-Manning n                                         */
+    double B1, B2;       /* breaking calibration, Eq. (9)                              */
+    int breaking;        /* 1: breaking terms of Eq. (12)                              */
+    int nonhydro;        /* 1: full scheme; 0: hydrostatic SWE only (p = 0)            */
+    double tol;          /* 2D Krylov relative-residual tolerance                       */
+    int max_iter;
+} or_cfg;
+
+typedef struct {
+    int iters[2];        /* solver iterations of the two RK stages                      */
+    double resid[2];     /* final relative residual ||b - M p|| / ||b||                 */
+    int clamped;         /* cells whose depth went negative and was clamped             */
+} or_stats;
+
+/* ---- 1D (Sec. 4) ---- */
+double or1d_cfl_dt(const or_cfg *c, const double *H, const double *h, const double *q);
+int or1d_step(const or_cfg *c, const double *H, double *h, double *q, double *w, double *p,
+              double dt, or_stats *st);
+int or1d_hyperbolic(const or_cfg *c, const double *H, const double *h, const double *q,
+                    double dt, double *ho, double *qo);
+int or1d_nh_matrix(const or_cfg *c, const double *H, const double *h, const double *q,
+                   const double *w, double dt, double *a, double *b, double *cc, double *rhs);
+int or1d_affine_apply(const or_cfg *c, const double *H, const double *h, const double *p,
+                      double dt, double *out);
+int or1d_nh_solve(const or_cfg *c, const double *H, const double *h, const double *q,
+                  const double *w, double dt, double *p);
+int or1d_thomas(int n, const double *a, const double *b, const double *c, const double *d,
+                double *x);
+long long or1d_run(const or_cfg *c, const double *H, double *h, double *q, double *w,
+                   double *p, double t_end, long long max_steps, double fixed_dt, double *t_out);
+
+/* ---- 2D (Sec. 5, App. A) ---- */
+double or2d_cfl_dt(const or_cfg *c, const double *H, const double *h, const double *q1,
+                   const double *q2);
+int or2d_step(const or_cfg *c, const double *H, double *h, double *q1, double *q2, double *w,
+              double *p, double dt, or_stats *st);
+int or2d_stage(const or_cfg *c, const double *H, const double *h, const double *q1,
+               const double *q2, const double *w, double *p, double dt, double *ho,
+               double *q1o, double *q2o, double *wo, int *iters, double *resid);
+int or2d_hyperbolic(const or_cfg *c, const double *H, const double *h, const double *q1,
+                    const double *q2, double dt, double *ho, double *q1o, double *q2o);
+int or2d_rhs(const or_cfg *c, const double *H, const double *h, const double *q1,
+             const double *q2, const double *w, double dt, double *rhs);
+int or2d_apply_M(const or_cfg *c, const double *H, const double *h, const double *p,
+                 double dt, double *out);
+int or2d_solve(const or_cfg *c, const double *H, const double *h, const double *rhs,
+               double dt, double *p, int *iters, double *resid);
+long long or2d_run(const or_cfg *c, const double *H, double *h, double *q1, double *q2,
+                   double *w, double *p, double t_end, long long max_steps, double fixed_dt,
+                   double *t_out, long long *iters_total);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
