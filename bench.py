@@ -1,0 +1,298 @@
+#!/usr/bin/env python
+"""Throughput of the full non-hydrostatic time step on one B300 (or N independent replicas).
+
+Default workload: the 4096^2 conical-island run-up (FP32 state, wet/dry, breaking, Manning
+friction, outflow boundaries; 16.8 M cells, dx = 0.05 m).  A "step" is one full TVD-RK2
+step: two hyperbolic updates, two pressure assemblies and solves, two corrections.
+
+Prints one JSON line (rank 0).  value = cells * steps (all ranks) / device time of the
+timed region; e2e = the same metric through the C-ABI with the state copied from pinned
+host memory and back every step; roofline = the kernel class with the largest share of
+device time, its algorithmic bytes per launch over its CUDA-event duration, against the
+measured HBM copy bandwidth.  --impl reference times the FP64 CPU oracle instead.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mcell-steps/s full NH step"
+UNIT = "Mcell-steps/s"
+
+# Algorithmic words moved per node / cell by one launch of each kernel class (stage-averaged,
+# breaking on): reads of every input field once plus writes of every output field once.
+WORDS = {
+    "hyperbolic": 8.5,    # eta q1 q2 H (+ base eta q1 q2 in stage 2) -> eta* q1* q2*
+    "breaking": 6.0,      # eta* q1* q2* H -> q1** q2**
+    "assembly": 14.5,     # eta* H q1** q2** q1* q2* w (+ w_base) -> w* 5 coefs rhs
+    "solve_init": 11.0,   # b x 5 coefs -> r rhat p^ v
+    "bicg_A": 11.0,       # r rhat p^ v 5 coefs -> p^ v
+    "bicg_B": 8.0,        # r v 5 coefs -> t
+    "bicg_C": 9.0,        # r rhat p^ v t x diag -> x r
+    "tridiag": 5.0,
+    "correction": 10.0,   # eta* H q1** q2** w* p -> eta q1 q2 w
+}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload(name):
+    from paper_1706_04551_b300 import inputs
+    if name == "island_4096":
+        wl = inputs.island_2d(n=4096)
+        prm = dict(manning_n=0.015, breaking=1, B1=0.15, B2=0.5, cfl=0.9, tol=1e-6)
+        desc = ("island_2d 4096x4096 dx=0.05 m FP32: conical island with dry top, solitary "
+                "wave A=0.064 m, wet/dry + breaking + Manning n=0.015, outflow BCs")
+        return wl, prm, "fp32", desc
+    if name == "shoals_1024":
+        wl = inputs.shoals_2d(n=1024)
+        prm = dict(cfl=0.9, tol=1e-6)
+        return wl, prm, "fp32", "shoals_2d 1024x1024 dx=0.1 m FP32, walls"
+    if name == "shoals_1024_fp64":
+        wl = inputs.shoals_2d(n=1024)
+        prm = dict(cfl=0.9, tol=1e-12)
+        return wl, prm, "fp64", "shoals_2d 1024x1024 dx=0.1 m FP64, walls"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def cpu_baseline(steps=2):
+    """The FP64 oracle as it stands on a bounded sample of the island workload: a 512^2
+    window (25.6 m, same dx = 0.05 m) holding the island and the wave, `steps` steps."""
+    import oracle as O
+    from paper_1706_04551_b300 import inputs
+    wl = inputs.island_2d(n=512, L=25.6, center=(12.8, None), x0=4.0)
+    c = O.cfg(wl.nx, wl.ny, dx=wl.dx, bc=wl.bc, manning=0.015, breaking=True, tol=1e-13)
+    zn = np.zeros((wl.ny + 1, wl.nx + 1))
+    O.lib()
+    t0 = time.perf_counter()
+    r = O.run_2d(c, wl.H, wl.h, wl.q1, wl.q2, zn, zn, max_steps=steps)
+    el = time.perf_counter() - t0
+    return {"value": wl.nx * wl.ny * r[6] / el / 1e6, "unit": UNIT, "cores": 1,
+            "kind": "oracle",
+            "sample": f"{r[6]} steps of a 512x512 window (dx 0.05 m) of the island workload, "
+                      f"single-threaded C oracle, FP64, solver tol 1e-13 ({el:.1f} s)"}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    # each timed step is a bounded oracle sample (one step of the 512^2 window)
+    rates = [cpu_baseline(steps=1) for _ in range(max(args.steps, 1))]
+    v = float(np.mean([r["value"] for r in rates]))
+    _, _, _, desc = workload(args.workload)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc + " (oracle sample, see cpu_baseline)"},
+            "cpu_baseline": {**rates[0], "value": v},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="island_4096")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1706_04551_b300 import build as nhbuild
+    from paper_1706_04551_b300 import nh
+    nhbuild.build()
+
+    wl, prm, prec, desc = workload(args.workload)
+    stream = torch.cuda.current_stream()
+    sim = nh.Sim(wl.H, wl.dx, wl.dy, bc=wl.bc, precision=prec, stream=stream, **prm)
+    dt_np = np.float32 if prec == "fp32" else np.float64
+    sim.set_state(wl.eta.astype(dt_np), wl.q1.astype(dt_np), wl.q2.astype(dt_np))
+    cells = wl.nx * wl.ny
+
+    for _ in range(args.warmup):
+        sim.step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sim.profile(True)
+    it0 = sim.stats()["solver_iters"]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            sim.step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    prof = sim.profile_read()
+    sim.profile(False)
+    st = sim.stats()
+    iters = st["solver_iters"] - it0
+    t_max = torch.tensor([ms], device="cuda")
+    if dist:
+        dist.barrier()
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms_max = float(t_max.item())
+    value = cells * args.steps * ws / (ms_max / 1e3) / 1e6
+
+    # end to end through the C-ABI: pinned host state in, one step, state out, every step
+    tdt = torch.float32 if prec == "fp32" else torch.float64
+    nn = (wl.nx + 1) * (wl.ny + 1)
+    host = {k: torch.empty(cells, dtype=tdt, pin_memory=True) for k in ("eta", "q1", "q2")}
+    host.update({k: torch.empty(nn, dtype=tdt, pin_memory=True) for k in ("w", "p")})
+    sim.get_state_into(**host)
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sim.set_state(host["eta"], host["q1"], host["q2"], host["w"], host["p"])
+        sim.step()
+        sim.get_state_into(**host)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    bytes_io = sum(v.numel() * v.element_size() for v in host.values())
+    e2e_t = torch.tensor([e2e_s], device="cuda")
+    if dist:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_val = cells * e2e_steps * ws / float(e2e_t.item()) / 1e6
+
+    # roofline of the kernel class with the largest device-time share
+    total_ms = sum(v[1] for v in prof.values())
+    top = max(prof, key=lambda k: prof[k][1])
+    nl, tms = prof[top]
+    esize = 4 if prec == "fp32" else 8
+    units = cells if top in ("hyperbolic", "breaking") else nn
+    algo_bytes = WORDS[top] * esize * units
+    achieved = algo_bytes / (tms / nl / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        tj = json.load(open(tfile))
+        ent = tj.get(args.workload, {}).get(top)
+        if ent:
+            traffic = ent.get("bytes_per_launch")
+    gpu_launches = int(sum(v[0] for v in prof.values()))
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": desc, "cells": cells, "replicas": ws,
+                       "parallelism": "replicas only (one independent domain per GPU)",
+                       "l2": "inputs larger than L2 (state 268 MB FP32 at 4096^2)",
+                       "solver": f"BiCGStab+Jacobi tol {prm['tol']}",
+                       "solver_iters_per_stage": iters / (2.0 * args.steps)},
+            "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": peak_kind, "algo_bytes_per_launch": algo_bytes,
+                         "ms_per_launch": tms / nl, "share": tms / total_ms},
+            "kernels": {k: {"launches": v[0], "ms": v[1], "share": v[1] / total_ms}
+                        for k, v in prof.items() if v[0]},
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bytes_io,
+                    "d2h_bytes_per_step": bytes_io, "steps": e2e_steps},
+            "gpu_launches": gpu_launches,
+            "clocks": clk.summary(),
+        }
+        if not args.no_cpu_baseline and ws == 1:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

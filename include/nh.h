@@ -1,0 +1,174 @@
+/*
+ * nh.h -- C-ABI of libnh, a B300 (sm_103a) implementation of one time step of the
+ * depth-integrated non-hydrostatic (Yamazaki) shallow-water system by the two-step
+ * projection-correction scheme of Escalante, Morales de Luna & Castro (arXiv:1706.04551).
+ *
+ * The step (Sec. 4.3 in 1D, Sec. 5 / App. A in 2D, Sec. 6 "steps 1-4 twice"):
+ *   for each stage of a second-order TVD Runge-Kutta method (Shu-Osher form),
+ *     hyperbolic PVM-HLL finite-volume update with MUSCL-minmod reconstruction,
+ *       emerging-bottom treatment and velocity desingularisation (Eqs. 18-23, 30;
+ *       Sec. 4.5), semi-implicit Manning friction, optional breaking terms (Eq. 12);
+ *     assembly of the compact finite-difference pressure system (App. B Eq. 43 in 1D,
+ *       the five-point system of Eqs. 36-41 in 2D);
+ *     pressure solve (1D: batched tridiagonal, parallel cyclic reduction; 2D:
+ *       Jacobi-preconditioned BiCGStab with FP64 dot products);
+ *     correction of the discharges and of w (Eqs. 26-28, 36, 41).
+ *
+ * Conventions.
+ *   - Cells: row-major [ny][nx], x fastest; cell (i, j) is centred at ((i+1/2)dx, (j+1/2)dy).
+ *   - Nodes (p, w): row-major [ny+1][nx+1]; node (I, J) sits at (I dx, J dy).
+ *     In 1D (dim = 1) each of the ny rows is an independent channel of nx cells with
+ *     nx + 1 nodes (a batch of 1D problems).
+ *   - State: eta = h - H (free surface), q1, q2 (discharges), w, p.  H is the still-water
+ *     depth, positive below the datum; a dry cell has eta = -H.
+ *   - Arrays passed to nh_set_state / nh_get_state have the handle's precision: double
+ *     for NH_FP64, float for NH_FP32.  H is always double.
+ *   - where = NH_HOST: pointers are host memory (pinned or pageable); NH_DEVICE: device
+ *     memory of the current device, laid out densely as above.
+ * Ownership: the library allocates and owns every device buffer of a handle (freed by
+ *   nh_destroy).  Input pointers are only read during the call.  All work is enqueued on
+ *   the stream given to nh_create (0 = legacy default stream); calls that return results
+ *   to the host synchronise that stream.
+ * Errors: every function returns NH_OK (0) or a negative NH_E* code; the message of the
+ *   last error of a handle is returned by nh_last_error.  Device-side failures (solver
+ *   not converged, non-finite values) are reported as status codes, never by trapping.
+ */
+#ifndef NH_H
+#define NH_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NH_OK 0
+#define NH_EINVAL (-1)      /* invalid argument                                      */
+#define NH_ENOMEM (-2)      /* device allocation failed                              */
+#define NH_ECUDA (-3)       /* CUDA runtime error                                    */
+#define NH_ENOCONV (-4)     /* pressure solve did not reach tol within max_iter      */
+#define NH_ENONFINITE (-5)  /* a non-finite value appeared in the state              */
+
+enum { NH_BC_WALL = 0, NH_BC_OUTFLOW = 1 };
+enum { NH_SOLVER_BICGSTAB = 0 };
+enum { NH_FP64 = 0, NH_FP32 = 1 };
+enum { NH_HOST = 0, NH_DEVICE = 1 };
+
+typedef struct {
+    int dim;            /* 1 or 2                                                        */
+    int nx, ny;         /* cells (2D: nx, ny >= 2; 1D: ny = number of independent rows)  */
+    double dx, dy;      /* cell sizes (dy unused in 1D)                                  */
+    int bc[4];          /* west, east, south, north: NH_BC_WALL / NH_BC_OUTFLOW          */
+} nh_grid;
+
+typedef struct {
+    double g;           /* gravity                                                       */
+    double cfl;         /* Courant number for the Eq. (23) time step                     */
+    double delta;       /* desingularisation depth of Sec. 4.5 (1e-5)                    */
+    double hdry;        /* dry threshold: a cell is dry when h <= hdry                   */
+    double manning_n;   /* Gauckler-Manning coefficient (0: no friction)                 */
+    double B1, B2;      /* breaking calibration coefficients, Eq. (9)                    */
+    int breaking;       /* 1: breaking terms of Eq. (12)                                 */
+    int nonhydrostatic; /* 1: full scheme; 0: hydrostatic shallow water only (p = 0)     */
+    int solver;         /* NH_SOLVER_BICGSTAB (2D)                                       */
+    double tol;         /* 2D solver: stop when ||b - M p||_2 <= tol ||b||_2              */
+    int max_iter;       /* 2D solver iteration cap                                       */
+    int precision;      /* NH_FP64 or NH_FP32 (state and fluxes; dots are FP64 always)   */
+    double fixed_dt;    /* > 0: nh_run uses this step instead of Eq. (23)                */
+} nh_params;
+
+typedef struct {
+    double t;              /* simulated time                                             */
+    double dt;             /* last step taken                                            */
+    double dt_next;        /* Eq. (23) step of the current state                         */
+    long long steps;       /* steps taken since creation / nh_set_state                  */
+    long long solver_iters;/* total pressure-solver iterations                           */
+    int last_iters[2];     /* iterations of the two stages of the last step              */
+    double last_resid[2];  /* relative residuals of those solves                         */
+    double mass;           /* sum of h dx dy over all cells (FP64)                        */
+    int nonfinite;         /* 1 if a non-finite value was detected                       */
+} nh_stats_t;
+
+typedef struct nh_handle nh_handle;
+
+/* Fill p with the paper's defaults: g = 9.81, CFL 0.9, delta = 1e-5, hdry = delta,
+ * n = 0, B1 = 0.15, B2 = 0.5 (Sec. 7.4), breaking off, non-hydrostatic on, BiCGStab,
+ * tol 1e-12, max_iter 500, FP64, fixed_dt 0. */
+int nh_default_params(nh_params *p);
+
+/* Create a simulation on the current CUDA device.  H: host array [ny][nx] (double) of
+ * still-water depths.  stream: a cudaStream_t (or 0).  The state is lake at rest
+ * (eta = max(0, H) - H, q = w = p = 0) until nh_set_state.  Returns NH_EINVAL for bad
+ * sizes / parameters, NH_ENOMEM when allocation fails. */
+int nh_create(const nh_grid *grid, const double *H, const nh_params *params, void *stream,
+              nh_handle **out);
+
+/* Set the state.  eta, q1, q2: [ny][nx]; w, p: [ny+1][nx+1] (may be NULL: set to 0);
+ * q2 may be NULL in 1D.  t: simulation time of the state.  Recomputes the Eq. (23)
+ * step of the new state. */
+int nh_set_state(nh_handle *h, const void *eta, const void *q1, const void *q2,
+                 const void *w, const void *p, double t, int where);
+
+/* Copy the state out (any pointer may be NULL to skip it); t may be NULL. */
+int nh_get_state(nh_handle *h, void *eta, void *q1, void *q2, void *w, void *p, double *t,
+                 int where);
+
+/* Advance one time step.  dt > 0: use it; dt <= 0: the Eq. (23) step of the current
+ * state (or params.fixed_dt when that is > 0).  *dt_taken (may be NULL) receives it. */
+int nh_step(nh_handle *h, double dt, double *dt_taken);
+
+/* Advance until t >= t_end (last step shortened to land on t_end; t_end <= 0: no time
+ * limit) or max_steps steps.  *steps_taken may be NULL. */
+int nh_run(nh_handle *h, double t_end, long long max_steps, long long *steps_taken);
+
+/* Counters and the FP64 mass of the current state (synchronises the stream). */
+int nh_stats(nh_handle *h, nh_stats_t *out);
+
+/* Message of the last error on this handle ("" if none); valid until the next call. */
+const char *nh_last_error(const nh_handle *h);
+
+void nh_destroy(nh_handle *h);
+
+/* ---- per-kernel timing (CUDA events around every launch, on the handle's stream) ---- */
+
+enum {
+    NH_K_HYPERBOLIC = 0,  /* PVM-HLL update + friction + clamp + RK combination        */
+    NH_K_BREAKING,        /* breaking terms at cells                                    */
+    NH_K_ASSEMBLY,        /* w*, pressure-system rows and right-hand side               */
+    NH_K_SOLVE_INIT,      /* BiCGStab initial residual                                  */
+    NH_K_BICG_A,          /* BiCGStab: p^ update and v = M D^-1 p^                       */
+    NH_K_BICG_B,          /* BiCGStab: t = M D^-1 s                                      */
+    NH_K_BICG_C,          /* BiCGStab: x, r updates and convergence test                */
+    NH_K_TRIDIAG,         /* 1D batched tridiagonal solve                               */
+    NH_K_CORRECTION,      /* correction of q and w, Eq. (23) rate                        */
+    NH_K_COUNT
+};
+
+typedef struct {
+    long long launches[NH_K_COUNT];
+    double ms[NH_K_COUNT];          /* summed device time per kernel class              */
+} nh_profile_t;
+
+/* on != 0: start recording an event pair around every kernel launch (counters reset);
+ * on == 0: stop.  Recording adds host work per launch; device times are unaffected. */
+int nh_profile_enable(nh_handle *h, int on);
+
+/* Accumulated times since nh_profile_enable (synchronises the stream). */
+int nh_profile_read(nh_handle *h, nh_profile_t *out);
+
+/* ---- kernel-level entry points used to check the stages one by one ---- */
+
+/* Hyperbolic update of the current state alone (Eqs. 18-22 / 30, friction, clamp):
+ * writes U + dt L(U) into eta_out, q1_out, q2_out ([ny][nx], handle precision). */
+int nh_debug_hyperbolic(nh_handle *h, double dt, void *eta_out, void *q1_out, void *q2_out,
+                        int where);
+
+/* Pressure system of the current state taken as the post-hyperbolic state U* with
+ * w* = w (App. B Eq. 43 / Eqs. 36-41, effective step dt): writes the right-hand side
+ * -(8 dx dy / dt) B(q*, w*) into rhs_out and M x into mx_out (both node arrays; 1D uses
+ * dy = dx).  x is a node array in the handle's precision. */
+int nh_debug_system(nh_handle *h, double dt, const void *x, void *rhs_out, void *mx_out,
+                    int where);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

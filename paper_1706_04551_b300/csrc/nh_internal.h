@@ -1,0 +1,129 @@
+// nh_internal.h -- declarations shared by the kernels (nh_kernels.cu) and the host
+// runtime (nh_api.cu) of libnh.  Not part of the public C-ABI (include/nh.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+
+namespace nh {
+
+// Grid and physical parameters as the kernels see them (T = float or double).
+template <typename T>
+struct Prm {
+    int nx, ny;                 // cells
+    int bcw, bce, bcs, bcn;     // 0 wall (mirror), 1 outflow (copy)
+    T dx, dy;
+    T g, delta, hdry, manning, B1;
+    int breaking;
+};
+
+// Device-side control block of one pressure solve (BiCGStab, FP64 scalars).
+struct SolveCtl {
+    double rho1;      // rhat . r of the current residual
+    double rho;       // rho1 of the previous iteration
+    double alpha, omega;
+    double bb;        // ||b||^2
+    double rr;        // ||r||^2
+    double rv, ts, tt;
+    int iter;         // iterations done in this solve
+    int done;         // 1: stop (converged, cap reached or breakdown)
+    int status;       // 0 running, 1 converged, 2 iteration cap, 3 breakdown
+    int max_iter;
+    double tol2;      // tol^2
+    unsigned counter; // last-block-done ticket
+    unsigned pad;
+};
+
+// Device-side per-step scalars.
+struct StepCtl {
+    double lam;        // max over cells of the Eq. (23) rate, last final stage
+    double mass;       // sum of h (cells), when requested
+    int nonfinite;     // set when a non-finite value was written
+    int clamped;       // depth clamps in the last step
+    unsigned counter;  // last-block-done ticket
+    unsigned pad;
+};
+
+// Device buffers of a 2D (or batched 1D) problem.
+template <typename T>
+struct Bufs {
+    T *H;
+    T *eta, *q1, *q2;            // state U^n
+    T *eta1, *q11, *q21;         // stage-1 result
+    T *etas, *q1s, *q2s;         // U* after the hyperbolic step (+ combination)
+    T *q1k, *q2k;                // U* after the breaking terms (aliases q1s/q2s if off)
+    T *w, *p, *w1, *ws;          // node fields
+    T *cC, *cW, *cE, *cS, *cN;   // 2D five-point coefficients (1D: a = cW, b = cC, c = cE)
+    T *rhs;
+    T *r, *rh, *ph[2], *v[2], *t;  // BiCGStab vectors
+    double *partials;             // per-block partial sums (>= 4 * nblk)
+    SolveCtl *sctl;
+    StepCtl *stctl;
+};
+
+struct Launch {
+    int nblk;          // persistent-style grid size (multiple of the SM count)
+    int nthr;          // threads per block
+    cudaStream_t s;
+};
+
+// ---- 2D ----
+template <typename T>
+void launch_hyp2d(const Prm<T>& P, const Launch& L, const T* eta, const T* q1, const T* q2,
+                  const T* etab, const T* q1b, const T* q2b, const T* H, T a, T b, T dt,
+                  T* eo, T* q1o, T* q2o, StepCtl* st);
+template <typename T>
+void launch_break2d(const Prm<T>& P, const Launch& L, const T* eta, const T* q1, const T* q2,
+                    const T* H, T de, T* q1o, T* q2o);
+template <typename T>
+void launch_asm2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* w_in,
+                  const T* w_base, T a, T b, T de, int with_coef, double tol2, int max_iter,
+                  double* partials, SolveCtl* ctl);
+template <typename T>
+void launch_matvec2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* x, T* y);
+template <typename T>
+void launch_bicg_init(const Prm<T>& P, const Launch& L, const Bufs<T>& B, double* partials);
+// one BiCGStab phase: 0 = A (p^, v), 1 = B (t), 2 = C (x, r); parity selects p^ / v buffers
+template <typename T>
+void launch_bicg_phase(const Prm<T>& P, const Launch& L, const Bufs<T>& B, int parity, int phase,
+                       double* partials);
+template <typename T>
+void launch_corr2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* q1k,
+                   const T* q2k, T de, int with_p, T* eo, T* q1o, T* q2o, T* wo, int final_stage,
+                   double* partials, StepCtl* st);
+
+// ---- batched 1D ----
+template <typename T>
+void launch_hyp1d(const Prm<T>& P, const Launch& L, const T* eta, const T* q, const T* etab,
+                  const T* qb, const T* H, T a, T b, T dt, T* eo, T* qo, StepCtl* st);
+template <typename T>
+void launch_break1d(const Prm<T>& P, const Launch& L, const T* eta, const T* q, const T* H,
+                    T de, T* qo);
+template <typename T>
+void launch_asm1d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* q_pre,
+                  const T* qk, const T* w_in, const T* w_base, T a, T b, T de);
+template <typename T>
+int launch_tridiag1d(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, T* x);
+template <typename T>
+void launch_tridiag_apply1d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* x,
+                            T* y);
+template <typename T>
+void launch_corr1d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* qk, T de,
+                   int with_p, T* eo, T* qo, T* wo, int final_stage, double* partials,
+                   StepCtl* st);
+
+// ---- shared ----
+template <typename T>
+void launch_mass(const Prm<T>& P, const Launch& L, const T* eta, const T* H, double* partials,
+                 StepCtl* st);
+template <typename T>
+void launch_lambda(const Prm<T>& P, const Launch& L, const T* eta, const T* q1, const T* q2,
+                   const T* H, int dim, double* partials, StepCtl* st);
+template <typename T>
+void launch_fill(const Launch& L, T* x, size_t n, T v);
+template <typename T>
+void launch_convert_from_double(const Launch& L, const double* src, T* dst, size_t n);
+
+int pcr_max_n(int elem_bytes);
+
+}  // namespace nh

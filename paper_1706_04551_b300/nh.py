@@ -1,0 +1,240 @@
+"""Thin ctypes binding of libnh (C-ABI in include/nh.h): argument marshalling only.
+
+Every step of the time integration runs in the CUDA kernels of ``libnh.so``; this module
+only converts arguments.  ``load()`` raises if the library is missing, so no code path
+falls back to anything else.  Arrays may be numpy (host) or torch CUDA tensors (device);
+torch is used for device memory and streams only.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnh.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ENONFINITE = 0, -1, -2, -3, -4, -5
+WALL, OUTFLOW = 0, 1
+FP64, FP32 = 0, 1
+HOST, DEVICE = 0, 1
+
+
+class Grid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("dx", C.c_double),
+                ("dy", C.c_double), ("bc", C.c_int * 4)]
+
+
+class Params(C.Structure):
+    _fields_ = [("g", C.c_double), ("cfl", C.c_double), ("delta", C.c_double),
+                ("hdry", C.c_double), ("manning_n", C.c_double), ("B1", C.c_double),
+                ("B2", C.c_double), ("breaking", C.c_int), ("nonhydrostatic", C.c_int),
+                ("solver", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int),
+                ("precision", C.c_int), ("fixed_dt", C.c_double)]
+
+
+class StatsT(C.Structure):
+    _fields_ = [("t", C.c_double), ("dt", C.c_double), ("dt_next", C.c_double),
+                ("steps", C.c_longlong), ("solver_iters", C.c_longlong),
+                ("last_iters", C.c_int * 2), ("last_resid", C.c_double * 2),
+                ("mass", C.c_double), ("nonfinite", C.c_int)]
+
+
+class NHError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libnh error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+EXPORTS = ("nh_default_params", "nh_create", "nh_set_state", "nh_get_state", "nh_step",
+           "nh_run", "nh_stats", "nh_last_error", "nh_destroy", "nh_profile_enable",
+           "nh_profile_read", "nh_debug_hyperbolic", "nh_debug_system")
+
+# kernel classes of nh_profile_t, in enum order
+KERNELS = ("hyperbolic", "breaking", "assembly", "solve_init", "bicg_A", "bicg_B", "bicg_C",
+           "tridiag", "correction")
+
+
+class ProfileT(C.Structure):
+    _fields_ = [("launches", C.c_longlong * len(KERNELS)), ("ms", C.c_double * len(KERNELS))]
+
+
+def load():
+    """Load libnh.so (built in-tree by build.py / __graft_entry__.build()); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libnh.so not found at {LIB_PATH}; run __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, H = C.c_void_p, C.c_void_p
+    L.nh_default_params.argtypes = [C.POINTER(Params)]
+    L.nh_create.argtypes = [C.POINTER(Grid), C.POINTER(C.c_double), C.POINTER(Params), vp,
+                            C.POINTER(H)]
+    L.nh_set_state.argtypes = [H, vp, vp, vp, vp, vp, C.c_double, C.c_int]
+    L.nh_get_state.argtypes = [H, vp, vp, vp, vp, vp, C.POINTER(C.c_double), C.c_int]
+    L.nh_step.argtypes = [H, C.c_double, C.POINTER(C.c_double)]
+    L.nh_run.argtypes = [H, C.c_double, C.c_longlong, C.POINTER(C.c_longlong)]
+    L.nh_stats.argtypes = [H, C.POINTER(StatsT)]
+    L.nh_last_error.argtypes = [H]
+    L.nh_last_error.restype = C.c_char_p
+    L.nh_destroy.argtypes = [H]
+    L.nh_destroy.restype = None
+    L.nh_profile_enable.argtypes = [H, C.c_int]
+    L.nh_profile_read.argtypes = [H, C.POINTER(ProfileT)]
+    L.nh_debug_hyperbolic.argtypes = [H, C.c_double, vp, vp, vp, C.c_int]
+    L.nh_debug_system.argtypes = [H, C.c_double, vp, vp, vp, C.c_int]
+    _lib = L
+    return L
+
+
+def default_params() -> Params:
+    p = Params()
+    load().nh_default_params(C.byref(p))
+    return p
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+class Sim:
+    """One simulation handle (2D grid, or ny independent 1D channels when dim = 1)."""
+
+    def __init__(self, H, dx, dy=None, dim=2, bc=(WALL,) * 4, precision="fp64", stream=None,
+                 **params):
+        L = load()
+        H = np.ascontiguousarray(np.asarray(H, dtype=np.float64))
+        if dim == 1 and H.ndim == 1:
+            H = H[None, :]
+        ny, nx = H.shape
+        self.dim, self.nx, self.ny = dim, nx, ny
+        self.dtype = np.float32 if precision == "fp32" else np.float64
+        self.nnode = (nx + 1) * (ny + 1) if dim == 2 else (nx + 1) * ny
+        g = Grid()
+        g.dim, g.nx, g.ny, g.dx = dim, nx, ny, float(dx)
+        g.dy = float(dx if dy is None else dy)
+        for k in range(4):
+            g.bc[k] = int(bc[k])
+        p = default_params()
+        p.precision = FP32 if precision == "fp32" else FP64
+        for k, v in params.items():
+            if not hasattr(p, k):
+                raise TypeError(f"unknown parameter {k}")
+            setattr(p, k, v)
+        self.params = p
+        self._h = C.c_void_p()
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+        rc = L.nh_create(C.byref(g), H.ctypes.data_as(C.POINTER(C.c_double)), C.byref(p),
+                         C.c_void_p(s), C.byref(self._h))
+        if rc != OK:
+            raise NHError(rc, "nh_create failed")
+        self._keep = []
+
+    # -------------------------------------------------------------- helpers
+    def _check(self, rc):
+        if rc != OK:
+            raise NHError(rc, load().nh_last_error(self._h).decode())
+
+    def _arr(self, a, n):
+        """Pointer + where for a numpy host array or a torch CUDA tensor of n elements."""
+        if a is None:
+            return None, HOST
+        if _is_torch(a):
+            assert a.is_contiguous() and a.numel() == n
+            assert a.element_size() == np.dtype(self.dtype).itemsize
+            return C.c_void_p(a.data_ptr()), (DEVICE if a.is_cuda else HOST)
+        a = np.ascontiguousarray(np.asarray(a, dtype=self.dtype)).reshape(-1)
+        assert a.size == n, (a.size, n)
+        self._keep.append(a)
+        return C.c_void_p(a.ctypes.data), HOST
+
+    @property
+    def node_shape(self):
+        return (self.ny + 1, self.nx + 1) if self.dim == 2 else (self.ny, self.nx + 1)
+
+    # -------------------------------------------------------------- API
+    def set_state(self, eta, q1, q2=None, w=None, p=None, t=0.0):
+        nc = self.nx * self.ny
+        args = [self._arr(eta, nc), self._arr(q1, nc), self._arr(q2, nc),
+                self._arr(w, self.nnode), self._arr(p, self.nnode)]
+        wheres = {wh for ptr, wh in args if ptr is not None}
+        assert len(wheres) == 1, "mixing host and device arrays"
+        self._check(load().nh_set_state(self._h, *[a[0] for a in args], float(t), wheres.pop()))
+        self._keep.clear()
+
+    def get_state(self):
+        out = {k: np.empty((self.ny, self.nx), self.dtype) for k in ("eta", "q1", "q2")}
+        out["w"] = np.empty(self.node_shape, self.dtype)
+        out["p"] = np.empty(self.node_shape, self.dtype)
+        t = C.c_double()
+        self._check(load().nh_get_state(self._h, *[C.c_void_p(out[k].ctypes.data) for k in
+                                                   ("eta", "q1", "q2", "w", "p")],
+                                        C.byref(t), HOST))
+        out["t"] = t.value
+        return out
+
+    def get_state_into(self, eta=None, q1=None, q2=None, w=None, p=None):
+        """Copy the state into caller buffers (numpy host or torch CUDA tensors)."""
+        nc = self.nx * self.ny
+        args = [self._arr(eta, nc), self._arr(q1, nc), self._arr(q2, nc),
+                self._arr(w, self.nnode), self._arr(p, self.nnode)]
+        wheres = {wh for ptr, wh in args if ptr is not None}
+        where = wheres.pop() if wheres else HOST
+        self._check(load().nh_get_state(self._h, *[a[0] for a in args], None, where))
+        self._keep.clear()
+
+    def step(self, dt=0.0):
+        d = C.c_double()
+        self._check(load().nh_step(self._h, float(dt), C.byref(d)))
+        return d.value
+
+    def run(self, t_end=0.0, max_steps=1 << 40):
+        s = C.c_longlong()
+        self._check(load().nh_run(self._h, float(t_end), int(max_steps), C.byref(s)))
+        return s.value
+
+    def stats(self):
+        st = StatsT()
+        self._check(load().nh_stats(self._h, C.byref(st)))
+        return dict(t=st.t, dt=st.dt, dt_next=st.dt_next, steps=st.steps,
+                    solver_iters=st.solver_iters, last_iters=tuple(st.last_iters),
+                    last_resid=tuple(st.last_resid), mass=st.mass, nonfinite=st.nonfinite)
+
+    def profile(self, on=True):
+        """Record CUDA events around every kernel launch (resets the counters)."""
+        self._check(load().nh_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self):
+        pr = ProfileT()
+        self._check(load().nh_profile_read(self._h, C.byref(pr)))
+        return {k: (pr.launches[i], pr.ms[i]) for i, k in enumerate(KERNELS)}
+
+    def debug_hyperbolic(self, dt):
+        out = [np.empty((self.ny, self.nx), self.dtype) for _ in range(3)]
+        self._check(load().nh_debug_hyperbolic(self._h, float(dt),
+                                               *[C.c_void_p(o.ctypes.data) for o in out], HOST))
+        return out
+
+    def debug_system(self, dt, x):
+        x = np.ascontiguousarray(np.asarray(x, dtype=self.dtype)).reshape(self.node_shape)
+        rhs = np.empty(self.node_shape, self.dtype)
+        mx = np.empty(self.node_shape, self.dtype)
+        self._check(load().nh_debug_system(self._h, float(dt), C.c_void_p(x.ctypes.data),
+                                           C.c_void_p(rhs.ctypes.data),
+                                           C.c_void_p(mx.ctypes.data), HOST))
+        return rhs, mx
+
+    def close(self):
+        if self._h:
+            load().nh_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,225 @@
+"""CUDA path (through the C-ABI) against the FP64 oracle, element by element.
+
+Bars: FP64 within 1e-10 relative L-infinity on h, q1, q2, p; FP32 within 1e-4 relative
+L-infinity on eta; lake at rest exact in both precisions.  Relative L-infinity of x against
+x_ref is max|x - x_ref| / max|x_ref|.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1706_04551_b300 import inputs, nh
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(x, ref):
+    s = np.abs(ref).max()
+    return np.abs(np.asarray(x, np.float64) - ref).max() / (s if s > 0 else 1.0)
+
+
+def make(wl, precision="fp64", **kw):
+    dim = 1 if wl.H.ndim == 1 else 2
+    prm = dict(wl.params)
+    for k in ("t_end",):
+        prm.pop(k, None)
+    if "manning" in prm:
+        prm["manning_n"] = prm.pop("manning")
+    prm.update(kw)
+    prm.setdefault("tol", 1e-13 if precision == "fp64" else 1e-6)
+    sim = nh.Sim(wl.H, wl.dx, wl.dy, dim=dim, bc=wl.bc, precision=precision, **prm)
+    ocfg = O.cfg(wl.nx, 1 if dim == 1 else wl.ny, dx=wl.dx, dy=wl.dy, bc=wl.bc,
+                 g=prm.get("g", 9.81), cfl=prm.get("cfl", 0.9),
+                 manning=prm.get("manning_n", 0.0), breaking=bool(prm.get("breaking", 0)),
+                 B1=prm.get("B1", 0.15), nonhydro=bool(prm.get("nonhydrostatic", 1)),
+                 tol=1e-14)
+    return sim, ocfg
+
+
+def developed(wl, seed=0, amp=0.02):
+    """A smooth moving state on the workload's bathymetry (wet cells only)."""
+    rng = np.random.default_rng(seed)
+    ny, nx = wl.H.shape
+    y, x = np.mgrid[0:ny, 0:nx] / max(nx, ny)
+    ph = rng.uniform(0, 2 * np.pi, 4)
+    wet = wl.h > 0
+    eta = np.where(wet, wl.eta + amp * np.sin(6 * x + ph[0]) * np.cos(5 * y + ph[1]), wl.eta)
+    h = np.maximum(eta + wl.H, 0)
+    eta = np.where(h > 0, eta, -wl.H)
+    q1 = np.where(h > 0, wl.q1 + amp * h * np.cos(4 * x + ph[2]), 0)
+    q2 = np.where(h > 0, wl.q2 + amp * h * np.sin(3 * y + ph[3]), 0)
+    return eta, q1, q2
+
+
+def shoals(n=64):
+    return inputs.shoals_2d(n=n)
+
+
+def island(n=64):
+    return inputs.island_2d(n=n, L=25.6, center=(12.8, None), x0=4.0)
+
+
+@pytest.mark.parametrize("which", ["shoals", "island"])
+def test_hyperbolic_kernel_fp64(which):
+    wl = shoals() if which == "shoals" else island()
+    sim, c = make(wl)
+    eta, q1, q2 = developed(wl)
+    sim.set_state(eta, q1, q2)
+    dt = 0.5 * O.cfl_dt_2d(c, wl.H, eta + wl.H, q1, q2)
+    e, a, b = sim.debug_hyperbolic(dt)
+    ho, ao, bo = O.hyperbolic_2d(c, wl.H, np.maximum(eta + wl.H, 0), q1, q2, dt)
+    assert rel(e + wl.H, ho) < 1e-13
+    assert rel(a, ao) < 1e-12 and rel(b, bo) < 1e-12
+
+
+@pytest.mark.parametrize("which", ["shoals", "island"])
+def test_pressure_system_fp64(which):
+    wl = shoals() if which == "shoals" else island()
+    sim, c = make(wl)
+    eta, q1, q2 = developed(wl, seed=3)
+    rng = np.random.default_rng(1)
+    w = 0.01 * rng.standard_normal((wl.ny + 1, wl.nx + 1))
+    sim.set_state(eta, q1, q2, w=w)
+    dt = 0.01
+    x = rng.standard_normal((wl.ny + 1, wl.nx + 1))
+    rhs, mx = sim.debug_system(dt, x)
+    h = np.maximum(eta + wl.H, 0)
+    assert rel(rhs, O.rhs_2d(c, wl.H, h, q1, q2, w, dt)) < 1e-12
+    assert rel(mx, O.apply_M_2d(c, wl.H, h, x, dt)) < 1e-12
+
+
+def _run_both(wl, steps, precision="fp64", state=None, **kw):
+    sim, c = make(wl, precision, **kw)
+    eta, q1, q2 = state if state is not None else (wl.eta, wl.q1, wl.q2)
+    sim.set_state(eta.astype(sim.dtype), q1.astype(sim.dtype), q2.astype(sim.dtype))
+    for _ in range(steps):
+        sim.step()
+    g = sim.get_state()
+    zn = np.zeros((wl.ny + 1, wl.nx + 1))
+    h = np.maximum(eta + wl.H, 0)
+    ro = O.run_2d(c, wl.H, h, q1, q2, zn, zn, max_steps=steps)
+    return sim, g, ro
+
+
+def test_full_step_shoals_fp64():
+    wl = shoals(64)
+    sim, g, (h, q1, q2, w, p, t, s, it) = _run_both(wl, 20)
+    assert rel(g["eta"] + wl.H, h) < 1e-10
+    assert rel(g["q1"], q1) < 1e-10 and rel(g["q2"], q2) < 1e-10
+    assert rel(g["p"], p) < 1e-10
+    assert abs(g["t"] - t) < 1e-12 * t
+
+
+def test_full_step_island_wetdry_breaking_fp64():
+    wl = island(64)
+    sim, g, (h, q1, q2, w, p, t, s, it) = _run_both(wl, 30)
+    assert rel(g["eta"] + wl.H, h) < 1e-10
+    assert rel(g["q1"], q1) < 1e-10 and rel(g["q2"], q2) < 1e-10
+    assert rel(g["p"], p) < 1e-10
+    assert (g["eta"] + wl.H >= 0).all()
+
+
+def test_lake_at_rest_exact_both_precisions():
+    wl = island(64)
+    for prec in ("fp64", "fp32"):
+        sim, _ = make(wl, prec)
+        eta0 = np.where(wl.H > 0, 0.0, -wl.H).astype(sim.dtype)
+        z = np.zeros_like(eta0)
+        sim.set_state(eta0, z, z)
+        for _ in range(20):
+            sim.step()
+        g = sim.get_state()
+        assert np.array_equal(g["eta"], eta0), prec
+        assert not g["q1"].any() and not g["q2"].any() and not g["p"].any()
+
+
+def test_fp32_shoals_within_1e4_of_fp64_oracle():
+    wl = shoals(128)
+    sim, g, (h, q1, q2, w, p, t, s, it) = _run_both(wl, 60, "fp32")
+    assert rel(g["eta"], h - wl.H) < 1e-4
+
+
+def test_fp32_island_within_1e4_of_fp64_oracle():
+    wl = island(128)
+    sim, g, (h, q1, q2, w, p, t, s, it) = _run_both(wl, 40, "fp32")
+    assert rel(g["eta"], h - wl.H) < 1e-4
+
+
+def test_mass_conserved_fp64():
+    wl = shoals(64)
+    sim, _ = make(wl)
+    sim.set_state(wl.eta, wl.q1, wl.q2)
+    m0 = sim.stats()["mass"]
+    sim.run(max_steps=50)
+    assert abs(sim.stats()["mass"] - m0) <= 1e-13 * m0
+
+
+# ------------------------------------------------------------------------------ 1D
+
+
+def test_solitary_1d_workload_fp64():
+    """The 1D channel workload in full: 1000 cells, t = 20 s, CFL 0.9."""
+    wl = inputs.solitary_1d()
+    sim, c = make(wl)
+    sim.set_state(wl.eta, wl.q1)
+    steps = sim.run(t_end=20.0)
+    g = sim.get_state()
+    h, q, w, p, t, s = O.run_1d(c, wl.H, wl.h, wl.q1, np.zeros(wl.nx + 1), np.zeros(wl.nx + 1),
+                                t_end=20.0)
+    assert steps == s and abs(g["t"] - t) < 1e-12
+    assert rel(g["eta"][0] + wl.H, h) < 1e-10
+    assert rel(g["q1"][0], q) < 1e-10
+    assert rel(g["p"][0], p) < 1e-10
+
+
+def test_1d_system_and_batch_rows_fp64():
+    """Eq. (43) rows and Thomas/PCR solves for a batch of different channels."""
+    n, rows = 300, 5
+    rng = np.random.default_rng(7)
+    x = (np.arange(n) + 0.5) * 0.2
+    Hs = np.stack([1.0 - 0.3 * np.exp(-((x - 20 - 5 * r) / 3) ** 2) for r in range(rows)])
+    etas = np.stack([0.1 / np.cosh(0.3 * (x - 15 - 3 * r)) ** 2 for r in range(rows)])
+    qs = np.stack([0.2 * etas[r] for r in range(rows)])
+    sim = nh.Sim(Hs, 0.2, dim=1, bc=(nh.WALL, nh.OUTFLOW, 0, 0))
+    sim.set_state(etas, qs)
+    dt = 0.02
+    xv = rng.standard_normal((rows, n + 1))
+    rhs, mx = sim.debug_system(dt, xv)
+    for r in range(rows):
+        c = O.cfg(n, dx=0.2, bc=(O.WALL, O.OUTFLOW, 0, 0))
+        a, b, cc, rr = O.nh_matrix_1d(c, Hs[r], etas[r] + Hs[r], qs[r], np.zeros(n + 1), dt)
+        ref = b * xv[r]
+        ref[1:] += a[1:] * xv[r][:-1]
+        ref[:-1] += cc[:-1] * xv[r][1:]
+        assert rel(rhs[r], rr) < 1e-12 and rel(mx[r], ref) < 1e-12
+    for _ in range(10):
+        sim.step(dt)
+    g = sim.get_state()
+    for r in range(rows):
+        c = O.cfg(n, dx=0.2, bc=(O.WALL, O.OUTFLOW, 0, 0))
+        h, q, w, p, t, s = O.run_1d(c, Hs[r], etas[r] + Hs[r], qs[r], np.zeros(n + 1),
+                                    np.zeros(n + 1), max_steps=10, fixed_dt=dt)
+        assert rel(g["eta"][r] + Hs[r], h) < 1e-10 and rel(g["q1"][r], q) < 1e-10
+        assert rel(g["p"][r], p) < 1e-10
+
+
+def test_1d_long_channel_thomas_path_fp64():
+    """A channel longer than the shared-memory PCR limit takes the Thomas path."""
+    n = 6000
+    wl = inputs.solitary_1d(n=n, L=600.0, x0=300.0)
+    sim, c = make(wl)
+    sim.set_state(wl.eta, wl.q1)
+    sim.run(max_steps=5)
+    g = sim.get_state()
+    h, q, w, p, t, s = O.run_1d(c, wl.H, wl.h, wl.q1, np.zeros(n + 1), np.zeros(n + 1),
+                                max_steps=5)
+    assert rel(g["eta"][0] + wl.H, h) < 1e-10 and rel(g["p"][0], p) < 1e-10
+
+
+def test_full_size_shoals_one_step_fp64():
+    """The 1024^2 shoals workload: one step against the oracle, all cells."""
+    wl = inputs.shoals_2d()
+    sim, g, (h, q1, q2, w, p, t, s, it) = _run_both(wl, 1)
+    assert rel(g["eta"] + wl.H, h) < 1e-10
+    assert rel(g["q1"], q1) < 1e-10 and rel(g["q2"], q2) < 1e-10
+    assert rel(g["p"], p) < 1e-10
