@@ -114,6 +114,12 @@ def workload(name):
         desc = ("island_2d 4096x4096 dx=0.05 m FP32: conical island with dry top, solitary "
                 "wave A=0.064 m, wet/dry + breaking + Manning n=0.015, outflow BCs")
         return wl, prm, "fp32", desc
+    if name == "island_2048":
+        wl = inputs.island_2d(n=2048, L=102.4)
+        prm = dict(manning_n=0.015, breaking=1, B1=0.15, B2=0.5, cfl=0.9, tol=1e-6)
+        desc = ("island_2d 2048x2048 dx=0.05 m FP32 (profiling case of the 4096^2 run-up: "
+                "same dx, island and wave, smaller basin)")
+        return wl, prm, "fp32", desc
     if name == "shoals_1024":
         wl = inputs.shoals_2d(n=1024)
         prm = dict(cfl=0.9, tol=1e-6)

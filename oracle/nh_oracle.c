@@ -41,6 +41,10 @@
  *   - Runge-Kutta (Sec. 4.3, Sec. 6 "steps 1-4 are repeated twice"): the projection of the
  *     second stage acts on the Shu-Osher combination, so U^{n+1} itself satisfies the
  *     discrete constraint; p^{n+1} is that projection's pressure.
+ *   - Dry cells (h <= hdry) carry no discharge: q = 0 there at the end of each stage.  The
+ *     correction T_NH has a term p (2 eta - h)_x that does not vanish with h, so without
+ *     this dry cells gain momentum and the fully dry nodes gain pressure, against the
+ *     App. B A.2 analysis (q = w = 0 where h vanishes gives p = 0).
  *   - dt (Eq. 23) in 2D: CFL / max((|u|+c)/dx + (|v|+c)/dy), from the current state.
  *   - The 2D system is solved by unpreconditioned BiCGStab to a relative residual tol.
  */
@@ -433,6 +437,14 @@ int or1d_nh_solve(const or_cfg *c, const double *H, const double *h, const doubl
     return 0;
 }
 
+/* Dry cells carry no discharge (reading of Sec. 4.5 and App. B A.2, whose analysis takes
+ * q = w = 0 where the depth vanishes): q = 0 where h <= hdry, at the end of each stage. */
+static void dry_discharge_1d(const or_cfg *c, const double *h, double *q)
+{
+    for (int i = 0; i < c->nx; ++i)
+        if (h[i] <= c->hdry) q[i] = 0.0;
+}
+
 /* One stage of the TVD-RK2 method in Shu-Osher form (Sec. 4.3 and Sec. 6: "steps 1-4
  * twice"): the hyperbolic update of (h_in, q_in) (Eqs. 18-22, friction, clamp) is combined
  * as U* = a U_base + b U**, w* = a w_base + b w_in, then breaking terms and the pressure
@@ -457,6 +469,7 @@ static int stage1d(const or_cfg *c, const double *H, const double *hb, const dou
     if (c->breaking) breaking1d(c, H, ho, qo, wo, de);
     if (!c->nonhydro) {
         for (int k = 0; k <= n; ++k) p[k] = 0.0;
+        dry_discharge_1d(c, ho, qo);
         return clamped;
     }
     or1d_nh_solve(c, H, ho, qo, wo, de, p);
@@ -476,6 +489,7 @@ static int stage1d(const or_cfg *c, const double *H, const double *hb, const dou
         wo[k] += de * p[k] * desing(hn, 1.0, c->delta);
     }
     if (periodic1d(c)) wo[n] = wo[0];
+    dry_discharge_1d(c, ho, qo);
     free(he); free(se); free(xi);
     return clamped;
 }
@@ -973,6 +987,14 @@ int or2d_solve(const or_cfg *c, const double *H, const double *h, const double *
     return st;
 }
 
+/* Dry cells carry no discharge (see dry_discharge_1d). */
+static void dry_discharge_2d(const or_cfg *c, const double *h, double *q1, double *q2)
+{
+    size_t n = (size_t)c->nx * c->ny;
+    for (size_t k = 0; k < n; ++k)
+        if (h[k] <= c->hdry) { q1[k] = 0.0; q2[k] = 0.0; }
+}
+
 /* One stage of the TVD-RK2 method in Shu-Osher form for App. A (Eq. 41): hyperbolic update
  * of (h, q1, q2) (Eq. 30, friction, clamp), combination U* = a U_base + b U**, w* =
  * a w_base + b w, breaking terms, pressure solve and correction (Eq. 36, w += de p / h_c)
@@ -997,6 +1019,7 @@ static int stage2d(const or_cfg *c, const double *H, const double *hb, const dou
     *iters = 0; *resid = 0.0;
     if (!c->nonhydro) {
         for (size_t k = 0; k < nn; ++k) p[k] = 0.0;
+        dry_discharge_2d(c, ho, q1o, q2o);
         return clamped;
     }
     double *rhs = malloc(nn * sizeof(double));
@@ -1023,6 +1046,7 @@ static int stage2d(const or_cfg *c, const double *H, const double *hb, const dou
                                 + f.h[CE(I, J)]);
             wo[NI(I, J)] += de * p[NI(I, J)] * desing(hc, 1.0, c->delta);
         }
+    dry_discharge_2d(c, ho, q1o, q2o);
     free(rhs); free(pe); free(TN); free(TS); free(TE); free(TW);
     nh2d_free(&f);
     return clamped;

@@ -617,7 +617,8 @@ k_bicg_C(Rows<T> R, T* __restrict__ r, const T* __restrict__ rh, const T* __rest
 }
 
 // Correction (Eq. 36 and the w update of Eq. 41) at node (I, J) and cell (I, J):
-// q1 += de (T^Hor_N + T^Hor_S)/2, q2 += de (T^Ver_E + T^Ver_W)/2, w += de p / h_c.
+// q1 += de (T^Hor_N + T^Hor_S)/2, q2 += de (T^Ver_E + T^Ver_W)/2, w += de p / h_c;
+// dry cells (h <= hdry) keep q = 0, as App. B A.2 assumes where the depth vanishes.
 // In the final stage also the Eq. (23) rate max((|u|+c)/dx + (|v|+c)/dy).
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
@@ -681,6 +682,7 @@ k_corr2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
                 a1 += de * T(0.5) * (TN + TS);
                 a2 += de * T(0.5) * (TE + TW);
             }
+            if (h <= P.hdry) { a1 = T(0); a2 = T(0); }   // dry cells carry no discharge
             eo[c] = e; q1o[c] = a1; q2o[c] = a2;
             if (!isfinite(e) || !isfinite(a1) || !isfinite(a2)) bad = 1;
             if (final_stage) {
@@ -972,6 +974,7 @@ k_corr1d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
                 const T Tn = -T(0.5) * (h * (pe - pw) / P.dx + T(0.5) * (pe + pw) * xi / P.dx);
                 qn += de * Tn;
             }
+            if (h <= P.hdry) qn = T(0);   // dry cells carry no discharge
             eo[c] = e; qo[c] = qn;
             if (!isfinite(e) || !isfinite(qn)) bad = 1;
             if (final_stage) {
