@@ -154,6 +154,20 @@ int nh_profile_enable(nh_handle *h, int on);
 /* Accumulated times since nh_profile_enable (synchronises the stream). */
 int nh_profile_read(nh_handle *h, nh_profile_t *out);
 
+/* ---- batched tridiagonal solve (the 1D pressure systems, App. B Eqs. 42-43) ---- */
+
+/* Solve `rows` independent systems a[i] x[i-1] + b[i] x[i] + c[i] x[i+1] = d[i],
+ * i = 0 .. n-1 (a[0] and c[n-1] are ignored), stored row-major (system r at offset r n).
+ * All pointers are device memory of the current device in the given precision
+ * (NH_FP64: double, NH_FP32: float); x may not alias the inputs.  Systems must be
+ * diagonally dominant (no pivoting), as those of Eq. (43) are.  Systems of n <= 4096
+ * (FP64) / 8192 (FP32) are solved by parallel cyclic reduction in shared memory; longer
+ * ones by the Thomas algorithm (Sec. 4.3), for which the call allocates 2 n rows
+ * elements of scratch with cudaMallocAsync on `stream` and frees them on return.
+ * Enqueued on `stream` (asynchronous).  Returns NH_OK, NH_EINVAL, NH_ENOMEM or NH_ECUDA. */
+int nh_tridiag_batched(int n, int rows, int precision, const void *a, const void *b,
+                       const void *c, const void *d, void *x, void *stream);
+
 /* ---- kernel-level entry points used to check the stages one by one ---- */
 
 /* Hyperbolic update of the current state alone (Eqs. 18-22 / 30, friction, clamp):

@@ -104,6 +104,12 @@ void launch_asm1d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* q
                   const T* qk, const T* w_in, const T* w_base, T a, T b, T de);
 template <typename T>
 int launch_tridiag1d(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, T* x);
+// Batched tridiagonal solve of `rows` systems of size n (row-major): PCR in shared memory
+// when n <= pcr_max_n, else the Thomas algorithm with scratch cp, dp (n * rows each).
+// Returns 0, -1 on a launch-attribute error, -2 when scratch is needed but missing.
+template <typename T>
+int launch_tridiag_raw(int n, int rows, const T* a, const T* b, const T* c, const T* d, T* x,
+                       T* cp, T* dp, cudaStream_t s);
 template <typename T>
 void launch_tridiag_apply1d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* x,
                             T* y);

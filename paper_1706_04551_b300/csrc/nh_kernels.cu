@@ -1164,6 +1164,33 @@ int launch_tridiag1d(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, T* x)
 }
 
 template <typename T>
+int launch_tridiag_raw(int n, int rows, const T* a, const T* b, const T* c, const T* d, T* x,
+                       T* cp, T* dp, cudaStream_t s)
+{
+    if (n <= pcr_max_n((int)sizeof(T))) {
+        const size_t smem = 4 * (size_t)n * sizeof(T);
+        const int thr = n >= 1024 ? 1024 : ((n + 31) / 32) * 32;
+        const int per = (n + thr - 1) / thr;
+        cudaError_t e = cudaSuccess;
+#define NH_PCR_RAW(PERV)                                                                    \
+    do {                                                                                    \
+        e = cudaFuncSetAttribute(k_pcr<T, PERV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)smem);                                                \
+        if (e == cudaSuccess) k_pcr<T, PERV><<<rows, thr, smem, s>>>(n, a, b, c, d, x);     \
+    } while (0)
+        if (per <= 1) NH_PCR_RAW(1);
+        else if (per <= 2) NH_PCR_RAW(2);
+        else if (per <= 4) NH_PCR_RAW(4);
+        else NH_PCR_RAW(8);
+#undef NH_PCR_RAW
+        return e == cudaSuccess ? 0 : -1;
+    }
+    if (!cp || !dp) return -2;
+    k_thomas<T><<<(rows + 127) / 128, 128, 0, s>>>(n, rows, a, b, c, d, cp, dp, x);
+    return 0;
+}
+
+template <typename T>
 void launch_tridiag_apply1d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* x,
                             T* y)
 {
@@ -1228,6 +1255,8 @@ void launch_convert_from_double(const Launch& L, const double* src, T* dst, size
     template void launch_asm1d<T>(const Prm<T>&, const Launch&, const Bufs<T>&, const T*,      \
                                   const T*, const T*, const T*, T, T, T);                      \
     template int launch_tridiag1d<T>(const Prm<T>&, cudaStream_t, const Bufs<T>&, T*);         \
+    template int launch_tridiag_raw<T>(int, int, const T*, const T*, const T*, const T*, T*, T*, \
+                                       T*, cudaStream_t);                                      \
     template void launch_tridiag_apply1d<T>(const Prm<T>&, const Launch&, const Bufs<T>&,      \
                                             const T*, T*);                                     \
     template void launch_corr1d<T>(const Prm<T>&, const Launch&, const Bufs<T>&, const T*, T,  \

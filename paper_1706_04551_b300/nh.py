@@ -51,7 +51,7 @@ _lib = None
 
 EXPORTS = ("nh_default_params", "nh_create", "nh_set_state", "nh_get_state", "nh_step",
            "nh_run", "nh_stats", "nh_last_error", "nh_destroy", "nh_profile_enable",
-           "nh_profile_read", "nh_debug_hyperbolic", "nh_debug_system")
+           "nh_profile_read", "nh_tridiag_batched", "nh_debug_hyperbolic", "nh_debug_system")
 
 # kernel classes of nh_profile_t, in enum order
 KERNELS = ("hyperbolic", "breaking", "assembly", "solve_init", "bicg_A", "bicg_B", "bicg_C",
@@ -85,6 +85,7 @@ def load():
     L.nh_destroy.restype = None
     L.nh_profile_enable.argtypes = [H, C.c_int]
     L.nh_profile_read.argtypes = [H, C.POINTER(ProfileT)]
+    L.nh_tridiag_batched.argtypes = [C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, vp, vp]
     L.nh_debug_hyperbolic.argtypes = [H, C.c_double, vp, vp, vp, C.c_int]
     L.nh_debug_system.argtypes = [H, C.c_double, vp, vp, vp, C.c_int]
     _lib = L
@@ -95,6 +96,20 @@ def default_params() -> Params:
     p = Params()
     load().nh_default_params(C.byref(p))
     return p
+
+
+def tridiag_batched(a, b, c, d, x, stream=None):
+    """Batched tridiagonal solve on torch CUDA tensors of shape [rows, n] (float32/64)."""
+    import torch
+    rows, n = d.shape
+    prec = FP64 if d.dtype == torch.float64 else FP32
+    for t in (a, b, c, d, x):
+        assert t.is_cuda and t.is_contiguous() and t.dtype == d.dtype and t.shape == d.shape
+    s = stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    rc = load().nh_tridiag_batched(n, rows, prec, *[C.c_void_p(t.data_ptr()) for t in
+                                                    (a, b, c, d, x)], C.c_void_p(s))
+    if rc != OK:
+        raise NHError(rc, "nh_tridiag_batched failed")
 
 
 def _is_torch(a) -> bool:
