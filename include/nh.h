@@ -168,6 +168,27 @@ int nh_profile_read(nh_handle *h, nh_profile_t *out);
 int nh_tridiag_batched(int n, int rows, int precision, const void *a, const void *b,
                        const void *c, const void *d, void *x, void *stream);
 
+/* Size of the fixed device scratch of nh_tridiag_batched_noalloc (8 MiB). */
+#define NH_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/* The same solve as nh_tridiag_batched for callers that cannot allocate device memory
+ * during the call -- for example code running inside another framework's memory pool,
+ * callbacks or real-time loops where cudaMalloc's latency and implicit synchronisation
+ * are not allowed, or processes with a fixed device-memory budget.  It calls no
+ * cudaMalloc / cudaFree or other allocating routine.  Systems longer than the
+ * shared-memory limit use a file-scope device array of NH_NOALLOC_SCRATCH_BYTES as
+ * scratch; each GPU that loads the library holds that array until the process exits.
+ * Limit: 2 n rows sizeof(element) <= NH_NOALLOC_SCRATCH_BYTES for those systems (n rows
+ * <= 524288 in FP64, 1048576 in FP32); larger sizes return NH_EINVAL and do nothing.
+ * The first call on each device looks up the array's device address (with that device
+ * current); make that first call before any stream capture.  All calls share the one
+ * array: calls whose executions overlap on the GPU (for example on two streams at once)
+ * race and give wrong results; serialise them.  No part of the scratch needs to start at
+ * zero.  The paper has no counterpart of this entry point.  Same arguments and return
+ * codes as nh_tridiag_batched. */
+int nh_tridiag_batched_noalloc(int n, int rows, int precision, const void *a, const void *b,
+                               const void *c, const void *d, void *x, void *stream);
+
 /* ---- kernel-level entry points used to check the stages one by one ---- */
 
 /* Hyperbolic update of the current state alone (Eqs. 18-22 / 30, friction, clamp):
