@@ -10,8 +10,9 @@
  *       Sec. 4.5), semi-implicit Manning friction, optional breaking terms (Eq. 12);
  *     assembly of the compact finite-difference pressure system (App. B Eq. 43 in 1D,
  *       the five-point system of Eqs. 36-41 in 2D);
- *     pressure solve (1D: batched tridiagonal, parallel cyclic reduction; 2D:
- *       Jacobi-preconditioned BiCGStab with FP64 dot products);
+ *     pressure solve (1D: batched tridiagonal, parallel cyclic reduction; 2D: Jacobi
+ *       with Chebyshev-scheduled relaxation, or Jacobi-preconditioned BiCGStab with FP64
+ *       dot products);
  *     correction of the discharges and of w (Eqs. 26-28, 36, 41).
  *
  * Conventions.
@@ -48,7 +49,11 @@ extern "C" {
 #define NH_ENONFINITE (-5)  /* a non-finite value appeared in the state              */
 
 enum { NH_BC_WALL = 0, NH_BC_OUTFLOW = 1 };
-enum { NH_SOLVER_BICGSTAB = 0 };
+enum {
+    NH_SOLVER_BICGSTAB = 0,  /* Jacobi-preconditioned BiCGStab, FP64 dots                     */
+    NH_SOLVER_CHEBYSHEV = 1  /* Jacobi with Chebyshev-scheduled relaxation (Sec. 5's scheduled
+                                relaxation Jacobi) on the Gershgorin interval of D^-1 M        */
+};
 enum { NH_FP64 = 0, NH_FP32 = 1 };
 enum { NH_HOST = 0, NH_DEVICE = 1 };
 
@@ -68,11 +73,14 @@ typedef struct {
     double B1, B2;      /* breaking calibration coefficients, Eq. (9)                    */
     int breaking;       /* 1: breaking terms of Eq. (12)                                 */
     int nonhydrostatic; /* 1: full scheme; 0: hydrostatic shallow water only (p = 0)     */
-    int solver;         /* NH_SOLVER_BICGSTAB (2D)                                       */
-    double tol;         /* 2D solver: stop when ||b - M p||_2 <= tol ||b||_2              */
-    int max_iter;       /* 2D solver iteration cap                                       */
+    int solver;         /* 2D pressure solver, NH_SOLVER_CHEBYSHEV (default) or _BICGSTAB  */
+    double tol;         /* stop when ||b - M p||_2 <= tol ||b||_2 (BiCGStab), or
+                           ||D^-1 (b - M p)||_2 <= tol ||D^-1 b||_2 (Chebyshev; D = diag M)  */
+    int max_iter;       /* iteration cap (BiCGStab iterations / Chebyshev sweeps)         */
     int precision;      /* NH_FP64 or NH_FP32 (state and fluxes; dots are FP64 always)   */
     double fixed_dt;    /* > 0: nh_run uses this step instead of Eq. (23)                */
+    double eps_dp;      /* > 0 (Chebyshev): stop on ||p^(k+1) - p^(k)||_inf < eps_dp, the
+                           criterion of Eq. (32), instead of the residual test            */
 } nh_params;
 
 typedef struct {
@@ -90,8 +98,8 @@ typedef struct {
 typedef struct nh_handle nh_handle;
 
 /* Fill p with the paper's defaults: g = 9.81, CFL 0.9, delta = 1e-5, hdry = delta,
- * n = 0, B1 = 0.15, B2 = 0.5 (Sec. 7.4), breaking off, non-hydrostatic on, BiCGStab,
- * tol 1e-12, max_iter 500, FP64, fixed_dt 0. */
+ * n = 0, B1 = 0.15, B2 = 0.5 (Sec. 7.4), breaking off, non-hydrostatic on, Chebyshev
+ * solver, tol 1e-12, max_iter 2000, FP64, fixed_dt 0, eps_dp 0. */
 int nh_default_params(nh_params *p);
 
 /* Create a simulation on the current CUDA device.  H: host array [ny][nx] (double) of
@@ -137,6 +145,7 @@ enum {
     NH_K_BICG_A,          /* BiCGStab: p^ update and v = M D^-1 p^                       */
     NH_K_BICG_B,          /* BiCGStab: t = M D^-1 s                                      */
     NH_K_BICG_C,          /* BiCGStab: x, r updates and convergence test                */
+    NH_K_CHEB_PASS,       /* Chebyshev-scheduled Jacobi: K sweeps per launch             */
     NH_K_TRIDIAG,         /* 1D batched tridiagonal solve                               */
     NH_K_CORRECTION,      /* correction of q and w, Eq. (23) rate                        */
     NH_K_COUNT

@@ -14,6 +14,7 @@
 #include <cstring>
 #include <memory>
 #include <string>
+#include <utility>
 #include <vector>
 
 using namespace nh;
@@ -117,6 +118,7 @@ struct Impl : Base {
     SolveCtl* h_sctl = nullptr;   // pinned mirrors of the device control blocks
     StepCtl* h_stctl = nullptr;
     int last_solve_iters = 0;
+    int last_cheb_passes = 0;
 
     ~Impl() override
     {
@@ -176,12 +178,20 @@ struct Impl : Base {
         A(B.cC, nn); A(B.cW, nn); A(B.cE, nn); A(B.rhs, nn);
         A(B.r, nn); A(B.rh, nn);
         if (dim == 2) {
-            A(B.cS, nn); A(B.cN, nn);
+            A(B.cS, nn); A(B.cN, nn); A(B.dp, nn); A(B.palt, nn);
             A(B.ph[0], nn); A(B.ph[1], nn); A(B.v[0], nn); A(B.v[1], nn); A(B.t, nn);
         } else {
             B.cS = B.cN = B.ph[0] = B.ph[1] = B.v[0] = B.v[1] = B.t = nullptr;
+            B.dp = B.palt = nullptr;
         }
-        A(B.partials, (size_t)4 * nblk + 64);
+        {
+            size_t np = (size_t)4 * nblk + 64;
+            if (dim == 2) {
+                const size_t nt = 2 * cheb_tiles<T>(P) + 64;
+                if (nt > np) np = nt;
+            }
+            A(B.partials, np);
+        }
         A(B.sctl, 1);
         A(B.stctl, 1);
 #undef A
@@ -190,6 +200,9 @@ struct Impl : Base {
         if ((e = cudaMallocHost(&h_stctl, sizeof(StepCtl))) != cudaSuccess) return cuda_fail(hd, e, "cudaMallocHost");
         cudaMemsetAsync(B.sctl, 0, sizeof(SolveCtl), h->s);
         cudaMemsetAsync(B.stctl, 0, sizeof(StepCtl), h->s);
+        h_sctl->eps_dp = q.eps_dp;
+        cudaMemcpyAsync(&B.sctl->eps_dp, &h_sctl->eps_dp, sizeof(double), cudaMemcpyHostToDevice,
+                        h->s);
         // H (double on the host) -> device precision
         double* Htmp = nullptr;
         if ((e = cudaMalloc(&Htmp, nc * sizeof(double))) != cudaSuccess) {
@@ -219,7 +232,7 @@ struct Impl : Base {
 
     // Launch f (one kernel) between two recorded events when profiling.
     template <typename F>
-    void K(int cls, F&& f)
+    void K_(int cls, F&& f)
     {
         if (!prof.on) { f(); return; }
         if (prof.used + 2 > 16384) prof.flush();
@@ -307,20 +320,67 @@ struct Impl : Base {
         return NH_OK;
     }
 
-    // BiCGStab on the assembled system; the solution overwrites B.p (warm start).
-    int solve2d(int stage)
+    // Chebyshev-scheduled Jacobi (temporally blocked passes); B.p is the warm start and
+    // receives the solution, B.r holds the previous iterate.
+    int solve_cheb(int stage)
+    {
+        const int K = cheb_sweeps_per_pass<T>();
+        cudaMemsetAsync(B.r, 0, nn * sizeof(T), hd->s);
+        cudaMemsetAsync(B.dp, 0, nn * sizeof(T), hd->s);
+        int batch = last_cheb_passes > 2 ? last_cheb_passes - 1 : 4;
+        double best = 1e300;
+        int stale = 0;
+        for (;;) {
+            for (int k = 0; k < batch; ++k) {
+                int rc = 0;
+                K_(NH_K_CHEB_PASS, [&] { rc = launch_cheb_pass<T>(P, hd->s, B, B.r, B.partials); });
+                if (rc != 0) return fail(hd, NH_ECUDA, "Chebyshev pass launch failed");
+            }
+            cudaMemcpyAsync(h_sctl, B.sctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, hd->s);
+            cudaError_t e = cudaStreamSynchronize(hd->s);
+            if (e != cudaSuccess) return cuda_fail(hd, e, "pressure solve");
+            if (h_sctl->status == 4) return solve2d(stage, false);   // not diagonally dominant
+            if (h_sctl->done) break;
+            // stagnation (rounding floor of the precision, or a spectrum the Gershgorin
+            // interval does not describe): continue with BiCGStab from the current dp
+            if (h_sctl->rr < 0.81 * best) { best = h_sctl->rr; stale = 0; }
+            else if (++stale >= 4) {
+                const int done_sweeps = h_sctl->sweeps;
+                hd->solver_iters += done_sweeps;
+                last_cheb_passes = done_sweeps / K;
+                return solve2d(stage, true);
+            }
+            batch = 2;
+        }
+        const int sweeps = h_sctl->sweeps;
+        last_cheb_passes = sweeps / K;
+        hd->solver_iters += sweeps;
+        hd->last_iters[stage] = sweeps;
+        hd->last_resid[stage] = h_sctl->bdb > 0.0 ? std::sqrt(h_sctl->rr / h_sctl->bdb) : 0.0;
+        if (h_sctl->status != 1)
+            return fail(hd, NH_ENOCONV,
+                        "Chebyshev solve stopped after " + std::to_string(sweeps) +
+                            " sweeps with scaled residual " +
+                            std::to_string(hd->last_resid[stage]));
+        return NH_OK;
+    }
+
+    // BiCGStab on the correction system M dp = r0 (from dp = 0, or from the current dp when
+    // continuing a stalled Chebyshev solve).
+    int solve2d(int stage, bool keep_dp = false)
     {
         const nh_params& q = hd->prm;
-        K(NH_K_SOLVE_INIT, [&] { launch_bicg_init<T>(P, Ln, B, B.partials); });
+        if (!keep_dp) cudaMemsetAsync(B.dp, 0, nn * sizeof(T), hd->s);
+        K_(NH_K_SOLVE_INIT, [&] { launch_bicg_init<T>(P, Ln, B, B.partials); });
         int launched = 0, restarts = 0;
         int batch = last_solve_iters > 2 ? last_solve_iters - 1 : 2;
         int status = 0;
         for (;;) {
             for (int k = 0; k < batch; ++k) {
                 const int par = launched & 1;
-                K(NH_K_BICG_A, [&] { launch_bicg_phase<T>(P, Ln, B, par, 0, B.partials); });
-                K(NH_K_BICG_B, [&] { launch_bicg_phase<T>(P, Ln, B, par, 1, B.partials); });
-                K(NH_K_BICG_C, [&] { launch_bicg_phase<T>(P, Ln, B, par, 2, B.partials); });
+                K_(NH_K_BICG_A, [&] { launch_bicg_phase<T>(P, Ln, B, par, 0, B.partials); });
+                K_(NH_K_BICG_B, [&] { launch_bicg_phase<T>(P, Ln, B, par, 1, B.partials); });
+                K_(NH_K_BICG_C, [&] { launch_bicg_phase<T>(P, Ln, B, par, 2, B.partials); });
                 ++launched;
             }
             cudaMemcpyAsync(h_sctl, B.sctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, hd->s);
@@ -330,7 +390,7 @@ struct Impl : Base {
                 status = h_sctl->status;
                 if (status == 3 && restarts < 8 && h_sctl->iter < q.max_iter) {
                     ++restarts;
-                    K(NH_K_SOLVE_INIT, [&] { launch_bicg_init<T>(P, Ln, B, B.partials); });
+                    K_(NH_K_SOLVE_INIT, [&] { launch_bicg_init<T>(P, Ln, B, B.partials); });
                     launched = 0;
                     batch = 2;
                     continue;
@@ -366,24 +426,27 @@ struct Impl : Base {
         T* ao = s == 0 ? B.q11 : B.q1;
         T* bo = s == 0 ? B.q21 : B.q2;
         T* wo = s == 0 ? B.w1 : B.w;
-        K(NH_K_HYPERBOLIC, [&] {
+        K_(NH_K_HYPERBOLIC, [&] {
             launch_hyp2d<T>(P, Lc, ein, ain, bin, B.eta, B.q1, B.q2, B.H, a, b, dt, B.etas,
                             B.q1s, B.q2s, B.stctl);
         });
         if (q.breaking)
-            K(NH_K_BREAKING, [&] {
+            K_(NH_K_BREAKING, [&] {
                 launch_break2d<T>(P, Lc, B.etas, B.q1s, B.q2s, B.H, de, B.q1k, B.q2k);
             });
-        K(NH_K_ASSEMBLY, [&] {
+        K_(NH_K_ASSEMBLY, [&] {
             launch_asm2d<T>(P, Ln, B, win, B.w, a, b, de, q.nonhydrostatic ? 1 : 0,
-                            q.tol * q.tol, q.max_iter, B.partials, B.sctl);
+                            q.nonhydrostatic ? 1 : 0, q.tol * q.tol, q.max_iter,
+                            q.solver == NH_SOLVER_CHEBYSHEV ? cheb_sweeps_per_pass<T>() : 0,
+                            B.partials, B.sctl);
         });
         int rc = NH_OK;
-        if (q.nonhydrostatic) rc = solve2d(s);
-        K(NH_K_CORRECTION, [&] {
+        if (q.nonhydrostatic) rc = q.solver == NH_SOLVER_CHEBYSHEV ? solve_cheb(s) : solve2d(s, false);
+        K_(NH_K_CORRECTION, [&] {
             launch_corr2d<T>(P, Ln, B, B.q1k, B.q2k, de, q.nonhydrostatic ? 1 : 0, eo, ao, bo,
                              wo, s == 1 ? 1 : 0, B.partials, B.stctl);
         });
+        std::swap(B.p, B.palt);
         return rc;
     }
 
@@ -398,19 +461,19 @@ struct Impl : Base {
         T* eo = s == 0 ? B.eta1 : B.eta;
         T* ao = s == 0 ? B.q11 : B.q1;
         T* wo = s == 0 ? B.w1 : B.w;
-        K(NH_K_HYPERBOLIC, [&] {
+        K_(NH_K_HYPERBOLIC, [&] {
             launch_hyp1d<T>(P, Lc, ein, ain, B.eta, B.q1, B.H, a, b, dt, B.etas, B.q1s, B.stctl);
         });
         if (q.breaking)
-            K(NH_K_BREAKING, [&] { launch_break1d<T>(P, Lc, B.etas, B.q1s, B.H, de, B.q1k); });
-        K(NH_K_ASSEMBLY, [&] { launch_asm1d<T>(P, Ln, B, B.q1s, B.q1k, win, B.w, a, b, de); });
+            K_(NH_K_BREAKING, [&] { launch_break1d<T>(P, Lc, B.etas, B.q1s, B.H, de, B.q1k); });
+        K_(NH_K_ASSEMBLY, [&] { launch_asm1d<T>(P, Ln, B, B.q1s, B.q1k, win, B.w, a, b, de); });
         if (q.nonhydrostatic) {
             int trc = 0;
-            K(NH_K_TRIDIAG, [&] { trc = launch_tridiag1d<T>(P, hd->s, B, B.p); });
+            K_(NH_K_TRIDIAG, [&] { trc = launch_tridiag1d<T>(P, hd->s, B, B.p); });
             if (trc != 0) return fail(hd, NH_ECUDA, "tridiagonal solve launch failed");
             hd->last_iters[s] = 1;
         }
-        K(NH_K_CORRECTION, [&] {
+        K_(NH_K_CORRECTION, [&] {
             launch_corr1d<T>(P, Ln, B, B.q1k, de, q.nonhydrostatic ? 1 : 0, eo, ao, wo,
                              s == 1 ? 1 : 0, B.partials, B.stctl);
         });
@@ -459,7 +522,8 @@ struct Impl : Base {
         D.etas = B.eta; D.q1s = B.q1; D.q2s = B.q2; D.q1k = B.q1; D.q2k = B.q2;
         const T de = (T)dtd;
         if (dim == 2)
-            launch_asm2d<T>(P, Ln, D, B.w, B.w, T(0), T(1), de, 1, 0.0, 1, B.partials, B.sctl);
+            launch_asm2d<T>(P, Ln, D, B.w, B.w, T(0), T(1), de, 1, 0, 0.0, 1, 0, B.partials,
+                            B.sctl);
         else
             launch_asm1d<T>(P, Ln, D, B.q1, B.q1, B.w, B.w, T(0), T(1), de);
         if (rhs) cudaMemcpyAsync(rhs, B.rhs, nn * sizeof(T), kind_out(where), hd->s);
@@ -493,7 +557,8 @@ int check_grid(const nh_grid* g, const nh_params* p, std::string& why)
         return 0;
     }
     if (p->precision != NH_FP64 && p->precision != NH_FP32) { why = "precision must be FP64 or FP32"; return 0; }
-    if (p->solver != NH_SOLVER_BICGSTAB) { why = "unknown solver"; return 0; }
+    if (p->solver != NH_SOLVER_BICGSTAB && p->solver != NH_SOLVER_CHEBYSHEV) { why = "unknown solver"; return 0; }
+    if (p->eps_dp < 0.0) { why = "eps_dp must be >= 0"; return 0; }
     return 1;
 }
 
@@ -506,8 +571,8 @@ int nh_default_params(nh_params* p)
     if (!p) return NH_EINVAL;
     p->g = 9.81; p->cfl = 0.9; p->delta = 1e-5; p->hdry = 1e-5; p->manning_n = 0.0;
     p->B1 = 0.15; p->B2 = 0.5; p->breaking = 0; p->nonhydrostatic = 1;
-    p->solver = NH_SOLVER_BICGSTAB; p->tol = 1e-12; p->max_iter = 500;
-    p->precision = NH_FP64; p->fixed_dt = 0.0;
+    p->solver = NH_SOLVER_CHEBYSHEV; p->tol = 1e-12; p->max_iter = 2000;
+    p->precision = NH_FP64; p->fixed_dt = 0.0; p->eps_dp = 0.0;
     return NH_OK;
 }
 

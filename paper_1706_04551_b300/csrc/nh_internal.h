@@ -32,6 +32,15 @@ struct SolveCtl {
     double tol2;      // tol^2
     unsigned counter; // last-block-done ticket
     unsigned pad;
+    // Chebyshev-scheduled Jacobi
+    double bdb;       // ||D^-1 b||^2
+    double gersh;     // max Gershgorin radius of D^-1 M
+    double sigma1, delta, rho_prev;
+    double c1[8], c2[8];  // weights of the next pass's sweeps
+    double dpmax;     // max |x_{k+1} - x_k| of the last sweep
+    double eps_dp;    // > 0: stop when dpmax < eps_dp (criterion (32)); else residual test
+    int sweeps;       // sweeps done in this solve
+    int pad2;
 };
 
 // Device-side per-step scalars.
@@ -53,9 +62,10 @@ struct Bufs {
     T *etas, *q1s, *q2s;         // U* after the hyperbolic step (+ combination)
     T *q1k, *q2k;                // U* after the breaking terms (aliases q1s/q2s if off)
     T *w, *p, *w1, *ws;          // node fields
+    T *dp, *palt;                // 2D: pressure correction of a solve; next pressure buffer
     T *cC, *cW, *cE, *cS, *cN;   // 2D five-point coefficients (1D: a = cW, b = cC, c = cE)
     T *rhs;
-    T *r, *rh, *ph[2], *v[2], *t;  // BiCGStab vectors
+    T *r, *rh, *ph[2], *v[2], *t;  // BiCGStab vectors (r doubles as the Chebyshev x_{k-1})
     double *partials;             // per-block partial sums (>= 4 * nblk)
     SolveCtl *sctl;
     StepCtl *stctl;
@@ -68,6 +78,7 @@ struct Launch {
 };
 
 // ---- 2D ----
+// (the 2D correction writes p0 + dp into B.palt; the caller then swaps B.p and B.palt)
 template <typename T>
 void launch_hyp2d(const Prm<T>& P, const Launch& L, const T* eta, const T* q1, const T* q2,
                   const T* etab, const T* q1b, const T* q2b, const T* H, T a, T b, T dt,
@@ -77,8 +88,16 @@ void launch_break2d(const Prm<T>& P, const Launch& L, const T* eta, const T* q1,
                     const T* H, T de, T* q1o, T* q2o);
 template <typename T>
 void launch_asm2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* w_in,
-                  const T* w_base, T a, T b, T de, int with_coef, double tol2, int max_iter,
-                  double* partials, SolveCtl* ctl);
+                  const T* w_base, T a, T b, T de, int with_coef, int resid_form, double tol2,
+                  int max_iter, int kpass, double* partials, SolveCtl* ctl);
+// Chebyshev-scheduled Jacobi: sweeps per launch, number of tiles (blocks), one launch.
+template <typename T>
+int cheb_sweeps_per_pass();
+template <typename T>
+size_t cheb_tiles(const Prm<T>& P);
+template <typename T>
+int launch_cheb_pass(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, T* xprev,
+                     double* partials);
 template <typename T>
 void launch_matvec2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* x, T* y);
 template <typename T>

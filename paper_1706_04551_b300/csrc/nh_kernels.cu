@@ -158,14 +158,15 @@ __device__ __forceinline__ double warp_max(double v)
     return v;
 }
 
-// Reduce NV values over the block (sum, or max when IS_MAX); thread 0 gets the result.
-template <int NV, bool IS_MAX>
+// Reduce NV values over the block; value k is a max when bit k of MAXMASK is set, else a
+// sum.  Thread 0 gets the result.
+template <int NV, unsigned MAXMASK>
 __device__ __forceinline__ void block_reduce(double (&v)[NV])
 {
     __shared__ double sm[NV][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = IS_MAX ? warp_max(v[k]) : warp_sum(v[k]);
+    for (int k = 0; k < NV; ++k) v[k] = ((MAXMASK >> k) & 1u) ? warp_max(v[k]) : warp_sum(v[k]);
     if (lane == 0)
 #pragma unroll
         for (int k = 0; k < NV; ++k) sm[k][wid] = v[k];
@@ -173,40 +174,44 @@ __device__ __forceinline__ void block_reduce(double (&v)[NV])
     if (wid == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            double x = lane < nw ? sm[k][lane] : (IS_MAX ? -1.0e300 : 0.0);
-            v[k] = IS_MAX ? warp_max(x) : warp_sum(x);
+            const bool mx = (MAXMASK >> k) & 1u;
+            double x = lane < nw ? sm[k][lane] : (mx ? -1.0e300 : 0.0);
+            v[k] = mx ? warp_max(x) : warp_sum(x);
         }
     }
     __syncthreads();
 }
 
 // Write this block's partials, then return true in the last block to finish; that block
-// receives the grid totals (fixed summation order) in v.
-template <int NV, bool IS_MAX>
+// receives the grid totals (fixed summation order) in v.  Blocks are numbered linearly
+// over a 1D or 2D grid.
+template <int NV, unsigned MAXMASK>
 __device__ __forceinline__ bool grid_reduce(double (&v)[NV], double* partials,
                                             unsigned* counter)
 {
-    block_reduce<NV, IS_MAX>(v);
+    block_reduce<NV, MAXMASK>(v);
+    const unsigned nblocks = gridDim.x * gridDim.y;
+    const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
     __shared__ bool last;
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int k = 0; k < NV; ++k) partials[(size_t)blockIdx.x * NV + k] = v[k];
+        for (int k = 0; k < NV; ++k) partials[(size_t)bid * NV + k] = v[k];
         __threadfence();
-        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+        last = atomicAdd(counter, 1u) == nblocks - 1;
     }
     __syncthreads();
     if (!last) return false;
     __threadfence();
     double acc[NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) acc[k] = IS_MAX ? -1.0e300 : 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+    for (int k = 0; k < NV; ++k) acc[k] = ((MAXMASK >> k) & 1u) ? -1.0e300 : 0.0;
+    for (unsigned bb = threadIdx.x; bb < nblocks; bb += blockDim.x)
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            double x = __ldcg(partials + (size_t)b * NV + k);
-            acc[k] = IS_MAX ? fmax(acc[k], x) : acc[k] + x;
+            double x = __ldcg(partials + (size_t)bb * NV + k);
+            acc[k] = ((MAXMASK >> k) & 1u) ? fmax(acc[k], x) : acc[k] + x;
         }
-    block_reduce<NV, IS_MAX>(acc);
+    block_reduce<NV, MAXMASK>(acc);
 #pragma unroll
     for (int k = 0; k < NV; ++k) v[k] = acc[k];
     if (threadIdx.x == 0) *counter = 0u;
@@ -334,9 +339,13 @@ k_break2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ q1,
 }
 
 // Assembly at node (I, J) (App. A.2, Eqs. 36-41): w* (+ breaking), the five coefficients
-// of the row scaled by 8 dx dy / de, and rhs = -(8 dx dy / de) B(q*, w*).
+// of the row scaled by 8 dx dy / de, and the right-hand side b = -(8 dx dy / de) B(q*, w*).
 // Link (x) between nodes (I, J) and (I+1, J) carries alpha+- = 2 h~ + X~, X~ - 2 h~ (h~, X~
 // averages over cells (I, J-1), (I, J)); node terms beta-+ = Xi -+ 2 h_c.
+// B* is evaluated in FP64 from the stored (T) state: its terms nearly cancel (the
+// constraint holds up to O(dt)), so T rounding there would be amplified by the system's
+// conditioning.  With resid_form = 1 the kernel stores the defect r0 = b - M p0 (FP64, then
+// rounded) for a correction solve M dp = r0 started from the warm start p0; else b itself.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_asm2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
@@ -344,18 +353,20 @@ k_asm2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
         const T* __restrict__ q2s, const T* __restrict__ w_in, const T* __restrict__ w_b,
         T a, T b, T de, int with_coef, T* __restrict__ ws, T* __restrict__ cC,
         T* __restrict__ cW, T* __restrict__ cE, T* __restrict__ cS, T* __restrict__ cN,
-        T* __restrict__ rhs, double* partials, SolveCtl* ctl, double tol2, int max_iter)
+        T* __restrict__ rhs, const T* __restrict__ p0, int resid_form, double* partials,
+        SolveCtl* ctl, double tol2, int max_iter, int kpass)
 {
     const T d2 = P.delta * P.delta, d4 = d2 * d2;
     const int nxn = P.nx + 1;
-    double acc[1] = {0.0};
+    double acc[3] = {0.0, 0.0, 0.0};   // ||b||^2, ||D^-1 b||^2, max Gershgorin radius
     GRID_STRIDE(idx, (long long)(P.nx + 1) * (P.ny + 1))
     {
         const int I = (int)(idx % nxn), J = (int)(idx / nxn);
-        // s = 2 eta - h = eta - H at a 4x4 cross around the node; h at the 4 core cells
-        // sx[r][k]: rows J-1 (r=0), J (r=1); columns I-2 .. I+1
-        // sy[c][k]: columns I-1 (c=0), I (c=1); rows J-2 .. J+1
+        // s = 2 eta - h = eta - H on a 4x4 cross around the node; h at the 4 core cells.
+        // sx[r][k]: rows J-1 (r=0), J (r=1), columns I-2 .. I+1
+        // sy[c][k]: columns I-1 (c=0), I (c=1), rows J-2 .. J+1
         T sx[2][4], sy[2][4], hq[2][2];
+        double sd[2][2], hd2[2][2];   // FP64 s and h of the core cells
 #pragma unroll
         for (int r = 0; r < 2; ++r)
 #pragma unroll
@@ -364,8 +375,13 @@ k_asm2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
                 int ii = map_cell(I - 2 + k, P.nx, P.bcw, P.bce, rx);
                 int jj = map_cell(J - 1 + r, P.ny, P.bcs, P.bcn, ry);
                 size_t m = (size_t)jj * P.nx + ii;
-                sx[r][k] = eta[m] - H[m];
-                if (k == 1 || k == 2) hq[r][k - 1] = tmax(eta[m] + H[m], T(0));
+                const T e = eta[m], Hm = H[m];
+                sx[r][k] = e - Hm;
+                if (k == 1 || k == 2) {
+                    hq[r][k - 1] = tmax(e + Hm, T(0));
+                    sd[r][k - 1] = (double)e - (double)Hm;
+                    hd2[r][k - 1] = fmax((double)e + (double)Hm, 0.0);
+                }
             }
 #pragma unroll
         for (int cc = 0; cc < 2; ++cc)
@@ -379,17 +395,18 @@ k_asm2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
             }
         // core cells: a = (I-1, J-1), b = (I, J-1), d = (I-1, J), e = (I, J)
         const T ha = hq[0][0], hb = hq[0][1], hd = hq[1][0], he = hq[1][1];
-        const T sa = sx[0][1], sb = sx[0][2], sd = sx[1][1], se = sx[1][2];
+        const T sa = sx[0][1], sb = sx[0][2], sd_ = sx[1][1], se = sx[1][2];
         // X (x-differences of s) at a, b, d, e; Y (y-differences) at a, b, d, e
         const T Xa = T(0.5) * (sx[0][2] - sx[0][0]), Xb = T(0.5) * (sx[0][3] - sx[0][1]);
         const T Xd = T(0.5) * (sx[1][2] - sx[1][0]), Xe = T(0.5) * (sx[1][3] - sx[1][1]);
         const T Ya = T(0.5) * (sy[0][2] - sy[0][0]), Yd = T(0.5) * (sy[0][3] - sy[0][1]);
         const T Yb = T(0.5) * (sy[1][2] - sy[1][0]), Ye = T(0.5) * (sy[1][3] - sy[1][1]);
         const T hc = T(0.25) * (ha + hb + hd + he);
-        const T Xi = T(0.5) * (se + sb) - T(0.5) * (sd + sa);
-        const T Yi = T(0.5) * (sd + se) - T(0.5) * (sa + sb);
+        const T Xi = T(0.5) * (se + sb) - T(0.5) * (sd_ + sa);
+        const T Yi = T(0.5) * (sd_ + se) - T(0.5) * (sa + sb);
         // discharges of the core cells (post-breaking) with boundary parity
-        T Q1[4], Q2[4], P1[4], P2[4];
+        double Q1[4], Q2[4];
+        T P1[4], P2[4];
         const int ci[4] = {I - 1, I, I - 1, I}, cj[4] = {J - 1, J - 1, J, J};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -397,8 +414,8 @@ k_asm2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
             int ii = map_cell(ci[k], P.nx, P.bcw, P.bce, rx);
             int jj = map_cell(cj[k], P.ny, P.bcs, P.bcn, ry);
             size_t m = (size_t)jj * P.nx + ii;
-            Q1[k] = rx ? -q1k[m] : q1k[m];
-            Q2[k] = ry ? -q2k[m] : q2k[m];
+            Q1[k] = rx ? -(double)q1k[m] : (double)q1k[m];
+            Q2[k] = ry ? -(double)q2k[m] : (double)q2k[m];
             if (P.breaking) {
                 P1[k] = rx ? -q1s[m] : q1s[m];
                 P2[k] = ry ? -q2s[m] : q2s[m];
@@ -419,16 +436,18 @@ k_asm2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
             wv += de * T(2) * nu * du * desing(hc, T(1), d4);
         }
         ws[nidx] = wv;
-        // B(q*, w*) (Eqs. 37-40) with edge discharges of Eq. (41) at p = 0
-        const T q1E = T(0.5) * (Q1[3] + Q1[1]), q1W = T(0.5) * (Q1[2] + Q1[0]);
-        const T q2N = T(0.5) * (Q2[3] + Q2[2]), q2S = T(0.5) * (Q2[1] + Q2[0]);
-        const T Bs = ((T(2) * hc - Xi) * q1E - (T(2) * hc + Xi) * q1W) / (T(2) * P.dx)
-                   + ((T(2) * hc - Yi) * q2N - (T(2) * hc + Yi) * q2S) / (T(2) * P.dy)
-                   + T(2) * hc * wv;
-        const T sc = T(8) * P.dx * P.dy / de;
-        const T r = -sc * Bs;
-        rhs[nidx] = r;
-        acc[0] += (double)r * (double)r;
+        // B(q*, w*) (Eqs. 37-40) with the edge discharges of Eq. (41) at p = 0, in FP64
+        const double hcD = 0.25 * (hd2[0][0] + hd2[0][1] + hd2[1][0] + hd2[1][1]);
+        const double XiD = 0.5 * (sd[1][1] + sd[0][1]) - 0.5 * (sd[1][0] + sd[0][0]);
+        const double YiD = 0.5 * (sd[1][0] + sd[1][1]) - 0.5 * (sd[0][0] + sd[0][1]);
+        const double q1E = 0.5 * (Q1[3] + Q1[1]), q1W = 0.5 * (Q1[2] + Q1[0]);
+        const double q2N = 0.5 * (Q2[3] + Q2[2]), q2S = 0.5 * (Q2[1] + Q2[0]);
+        const double dxd = (double)P.dx, dyd = (double)P.dy;
+        const double Bs = ((2.0 * hcD - XiD) * q1E - (2.0 * hcD + XiD) * q1W) / (2.0 * dxd)
+                        + ((2.0 * hcD - YiD) * q2N - (2.0 * hcD + YiD) * q2S) / (2.0 * dyd)
+                        + 2.0 * hcD * (double)wv;
+        const double bval = -(8.0 * dxd * dyd / (double)de) * Bs;
+        acc[0] += bval * bval;
         if (with_coef) {
             const T apE = T(2) * T(0.5) * (hb + he) + T(0.5) * (Xb + Xe);
             const T amE = T(0.5) * (Xb + Xe) - T(2) * T(0.5) * (hb + he);
@@ -438,24 +457,66 @@ k_asm2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
             const T amN = T(0.5) * (Yd + Ye) - T(2) * T(0.5) * (hd + he);
             const T apS = T(2) * T(0.5) * (ha + hb) + T(0.5) * (Ya + Yb);
             const T amS = T(0.5) * (Ya + Yb) - T(2) * T(0.5) * (ha + hb);
-            const T bmx = Xi - T(2) * hc, bpx = Xi + T(2) * hc;
+            const T bmx = Xi - T(2) * hc, bpx = Xi + T(2) * hc;  // beta-, beta+ of the x links
             const T bmy = Yi - T(2) * hc, bpy = Yi + T(2) * hc;
-            const T rx = P.dy / P.dx, ry = P.dx / P.dy;
-            cE[nidx] = rx * bmx * apE;
-            cW[nidx] = rx * bpx * amW;
-            cN[nidx] = ry * bmy * apN;
-            cS[nidx] = ry * bpy * amS;
-            cC[nidx] = T(16) * P.dx * P.dy + rx * (bmx * amE + bpx * apW)
-                     + ry * (bmy * amN + bpy * apS);
+            const T rxl = P.dy / P.dx, ryl = P.dx / P.dy;
+            const T vE = rxl * bmx * apE, vW = rxl * bpx * amW;
+            const T vN = ryl * bmy * apN, vS = ryl * bpy * amS;
+            const T dC = T(16) * P.dx * P.dy + rxl * (bmx * amE + bpx * apW)
+                       + ryl * (bmy * amN + bpy * apS);
+            cE[nidx] = vE; cW[nidx] = vW; cN[nidx] = vN; cS[nidx] = vS; cC[nidx] = dC;
+            const double ad = fabs((double)dC);
+            acc[1] += (bval / ad) * (bval / ad);
+            acc[2] = fmax(acc[2], (fabs((double)vE) + fabs((double)vW) + fabs((double)vN) +
+                                   fabs((double)vS)) / ad);
+            if (resid_form) {
+                const int Iw = map_node(I - 1, P.nx), Ie = map_node(I + 1, P.nx);
+                const int Js = map_node(J - 1, P.ny), Jn = map_node(J + 1, P.ny);
+                const double mp = (double)dC * (double)p0[nidx]
+                                + (double)vW * (double)p0[(size_t)J * nxn + Iw]
+                                + (double)vE * (double)p0[(size_t)J * nxn + Ie]
+                                + (double)vS * (double)p0[(size_t)Js * nxn + I]
+                                + (double)vN * (double)p0[(size_t)Jn * nxn + I];
+                rhs[nidx] = (T)(bval - mp);
+            } else {
+                rhs[nidx] = (T)bval;
+            }
+        } else {
+            rhs[nidx] = (T)bval;
         }
     }
-    if (grid_reduce<1, false>(acc, partials, &ctl->counter) && threadIdx.x == 0) {
+    if (grid_reduce<3, 4u>(acc, partials, &ctl->counter) && threadIdx.x == 0) {
         ctl->bb = acc[0];
+        ctl->bdb = acc[1];
+        ctl->gersh = acc[2];
         ctl->tol2 = tol2;
         ctl->max_iter = max_iter;
         ctl->iter = 0;
+        ctl->sweeps = 0;
         ctl->done = 0;
         ctl->status = 0;
+        // Chebyshev semi-iteration on D^-1 M with spectrum in [1 - g, 1 + g] (Gershgorin):
+        // theta = 1, delta = g, sigma1 = 1 / g; sweep 0 is plain Jacobi (c1 = 0, c2 = 1).
+        if (with_coef && kpass > 0) {
+            if (!(acc[2] < 1.0)) {
+                ctl->status = 4;   // no diagonal dominance: the caller switches solver
+                ctl->done = 1;
+            } else {
+                const double dl = acc[2] > 1e-12 ? acc[2] : 1e-12;
+                ctl->delta = dl;
+                ctl->sigma1 = 1.0 / dl;
+                double rp = dl;   // rho_0 = 1 / sigma1
+                ctl->c1[0] = 0.0;
+                ctl->c2[0] = 1.0;
+                for (int k = 1; k < kpass; ++k) {
+                    const double rn = 1.0 / (2.0 * ctl->sigma1 - rp);
+                    ctl->c1[k] = rn * rp;
+                    ctl->c2[k] = 2.0 * rn / dl;
+                    rp = rn;
+                }
+                ctl->rho_prev = rp;
+            }
+        }
     }
 }
 
@@ -513,7 +574,7 @@ k_bicg_init(Rows<T> R, const T* __restrict__ b, T* __restrict__ x, T* __restrict
         r[idx] = rv; rh[idx] = rv; ph0[idx] = T(0); v0[idx] = T(0);
         acc[0] += (double)rv * (double)rv;
     }
-    if (grid_reduce<1, false>(acc, partials, &ctl->counter) && threadIdx.x == 0) {
+    if (grid_reduce<1, 0u>(acc, partials, &ctl->counter) && threadIdx.x == 0) {
         ctl->rho1 = acc[0];
         ctl->rr = acc[0];
         ctl->rho = 1.0; ctl->alpha = 1.0; ctl->omega = 1.0;
@@ -546,7 +607,7 @@ k_bicg_A(Rows<T> R, const T* __restrict__ r, const T* __restrict__ rh,
         v_new[idx] = vc;
         acc[0] += (double)rh[idx] * (double)vc;
     }
-    if (grid_reduce<1, false>(acc, partials, &ctl->counter) && threadIdx.x == 0) {
+    if (grid_reduce<1, 0u>(acc, partials, &ctl->counter) && threadIdx.x == 0) {
         ctl->rv = acc[0];
         ctl->rho = ctl->rho1;
         if (acc[0] == 0.0 || !isfinite(acc[0])) {
@@ -577,7 +638,7 @@ k_bicg_B(Rows<T> R, const T* __restrict__ r, const T* __restrict__ v, T* __restr
         acc[0] += (double)tc * (double)sc;
         acc[1] += (double)tc * (double)tc;
     }
-    if (grid_reduce<2, false>(acc, partials, &ctl->counter) && threadIdx.x == 0) {
+    if (grid_reduce<2, 0u>(acc, partials, &ctl->counter) && threadIdx.x == 0) {
         ctl->ts = acc[0];
         ctl->tt = acc[1];
         ctl->omega = acc[1] > 0.0 ? acc[0] / acc[1] : 0.0;
@@ -604,7 +665,7 @@ k_bicg_C(Rows<T> R, T* __restrict__ r, const T* __restrict__ rh, const T* __rest
         acc[0] += (double)rh[idx] * (double)rn;
         acc[1] += (double)rn * (double)rn;
     }
-    if (grid_reduce<2, false>(acc, partials, &ctl->counter) && threadIdx.x == 0) {
+    if (grid_reduce<2, 0u>(acc, partials, &ctl->counter) && threadIdx.x == 0) {
         ctl->rho1 = acc[0];
         ctl->rr = acc[1];
         ctl->iter += 1;
@@ -616,6 +677,106 @@ k_bicg_C(Rows<T> R, T* __restrict__ r, const T* __restrict__ rh, const T* __rest
     }
 }
 
+// Jacobi with Chebyshev-scheduled relaxation (the "scheduled relaxation" of Sec. 5 with
+// the Chebyshev weights of the Gershgorin interval [1 - g, 1 + g] of D^-1 M), K sweeps per
+// launch with temporal blocking: each block loads a TX x TY node tile plus a K-node halo
+// into shared memory, sweeps K times there (the valid region shrinking by one node per
+// sweep), and writes the tile back.  Sweep k: x_{k+1} = x_k + c1 (x_k - x_{k-1}) + c2 r_k,
+// r_k = D^-1 (b - M x_k).  The last sweep accumulates ||r||^2 (Jacobi-scaled) and
+// max |x_{k+1} - x_k|; the last block tests convergence and prepares the next K weights.
+template <typename T, int TX, int TY, int K>
+__global__ void __launch_bounds__(256)
+k_cheb_pass(Rows<T> R, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ xp,
+            double* partials, SolveCtl* ctl)
+{
+    if (ctl->done) return;
+    extern __shared__ unsigned char cheb_smem[];
+    constexpr int RW = TX + 2 * K, RH = TY + 2 * K, RN = RW * RH;
+    T* xa = reinterpret_cast<T*>(cheb_smem);   // x_{k-1}, then x_{k+1}
+    T* xb = xa + RN;                           // x_k
+    T* bd = xb + RN;
+    T* wW = bd + RN;
+    T* wE = wW + RN;
+    T* wS = wE + RN;
+    T* wN = wS + RN;
+    const int NX = R.nx + 1, NY = R.ny + 1;
+    const int I0 = blockIdx.x * TX, J0 = blockIdx.y * TY;
+    const int RI0 = I0 - K > 0 ? I0 - K : 0, RI1 = I0 + TX + K < NX ? I0 + TX + K : NX;
+    const int RJ0 = J0 - K > 0 ? J0 - K : 0, RJ1 = J0 + TY + K < NY ? J0 + TY + K : NY;
+    const int rw = RI1 - RI0, rh = RJ1 - RJ0;
+    for (int t = threadIdx.x; t < rw * rh; t += blockDim.x) {
+        const int li = t % rw, lj = t / rw;
+        const size_t g = (size_t)(RJ0 + lj) * NX + RI0 + li;
+        const int sidx = lj * RW + li;
+        const T ic = T(1) / R.cC[g];
+        xa[sidx] = xp[g];
+        xb[sidx] = x[g];
+        bd[sidx] = b[g] * ic;
+        wW[sidx] = R.cW[g] * ic;
+        wE[sidx] = R.cE[g] * ic;
+        wS[sidx] = R.cS[g] * ic;
+        wN[sidx] = R.cN[g] * ic;
+    }
+    T c1s[K], c2s[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) { c1s[k] = (T)ctl->c1[k]; c2s[k] = (T)ctl->c2[k]; }
+    __syncthreads();
+    const int TI1 = I0 + TX < NX ? I0 + TX : NX, TJ1 = J0 + TY < NY ? J0 + TY : NY;
+    double acc[2] = {0.0, 0.0};
+#pragma unroll
+    for (int sw = 0; sw < K; ++sw) {
+        const int vI0 = RI0 == 0 ? 0 : RI0 + sw + 1, vI1 = RI1 == NX ? NX : RI1 - (sw + 1);
+        const int vJ0 = RJ0 == 0 ? 0 : RJ0 + sw + 1, vJ1 = RJ1 == NY ? NY : RJ1 - (sw + 1);
+        const int vw = vI1 - vI0, vn = vw * (vJ1 - vJ0);
+        const T c1 = c1s[sw], c2 = c2s[sw];
+        for (int t = threadIdx.x; t < vn; t += blockDim.x) {
+            const int gI = vI0 + t % vw, gJ = vJ0 + t / vw;
+            const int li = gI - RI0, lj = gJ - RJ0;
+            const int sidx = lj * RW + li;
+            const int lW = map_node(gI - 1, NX - 1) - RI0, lE = map_node(gI + 1, NX - 1) - RI0;
+            const int lS = map_node(gJ - 1, NY - 1) - RJ0, lN = map_node(gJ + 1, NY - 1) - RJ0;
+            const T xc = xb[sidx];
+            const T r = bd[sidx] - xc -
+                        (wW[sidx] * xb[lj * RW + lW] + wE[sidx] * xb[lj * RW + lE] +
+                         wS[sidx] * xb[lS * RW + li] + wN[sidx] * xb[lN * RW + li]);
+            const T xn = xc + c1 * (xc - xa[sidx]) + c2 * r;
+            xa[sidx] = xn;
+            if (sw == K - 1 && gI >= I0 && gI < TI1 && gJ >= J0 && gJ < TJ1) {
+                acc[0] += (double)r * (double)r;
+                acc[1] = fmax(acc[1], fabs((double)(xn - xc)));
+            }
+        }
+        __syncthreads();
+        T* tmp = xa; xa = xb; xb = tmp;
+    }
+    for (int t = threadIdx.x; t < (TI1 - I0) * (TJ1 - J0); t += blockDim.x) {
+        const int gI = I0 + t % (TI1 - I0), gJ = J0 + t / (TI1 - I0);
+        const size_t g = (size_t)gJ * NX + gI;
+        const int sidx = (gJ - RJ0) * RW + (gI - RI0);
+        x[g] = xb[sidx];
+        xp[g] = xa[sidx];
+    }
+    if (grid_reduce<2, 2u>(acc, partials, &ctl->counter) && threadIdx.x == 0) {
+        ctl->rr = acc[0];
+        ctl->dpmax = acc[1];
+        ctl->sweeps += K;
+        ctl->iter = ctl->sweeps;
+        const bool conv = ctl->eps_dp > 0.0 ? acc[1] < ctl->eps_dp
+                                            : acc[0] <= ctl->tol2 * ctl->bdb;
+        if (conv) { ctl->done = 1; ctl->status = 1; }
+        else if (!isfinite(acc[0])) { ctl->done = 1; ctl->status = 3; }
+        else if (ctl->sweeps >= ctl->max_iter) { ctl->done = 1; ctl->status = 2; }
+        double rp = ctl->rho_prev;
+        for (int k = 0; k < K; ++k) {
+            const double rn = 1.0 / (2.0 * ctl->sigma1 - rp);
+            ctl->c1[k] = rn * rp;
+            ctl->c2[k] = 2.0 * rn / ctl->delta;
+            rp = rn;
+        }
+        ctl->rho_prev = rp;
+    }
+}
+
 // Correction (Eq. 36 and the w update of Eq. 41) at node (I, J) and cell (I, J):
 // q1 += de (T^Hor_N + T^Hor_S)/2, q2 += de (T^Ver_E + T^Ver_W)/2, w += de p / h_c;
 // dry cells (h <= hdry) keep q = 0, as App. B A.2 assumes where the depth vanishes.
@@ -624,7 +785,8 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_corr2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
          const T* __restrict__ q1k, const T* __restrict__ q2k, const T* __restrict__ ws,
-         T* __restrict__ p, T de, int with_p, T* __restrict__ eo, T* __restrict__ q1o,
+         const T* __restrict__ p, const T* __restrict__ dp, T* __restrict__ pout, T de,
+         int with_p, T* __restrict__ eo, T* __restrict__ q1o,
          T* __restrict__ q2o, T* __restrict__ wo, int final_stage, double* partials,
          StepCtl* st)
 {
@@ -638,7 +800,7 @@ k_corr2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
         // node
         T pc = T(0);
         if (with_p) {
-            pc = p[idx];
+            pc = p[idx] + dp[idx];
             T hs = T(0);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -651,10 +813,11 @@ k_corr2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
             const T hc = T(0.25) * hs;
             const T wn = ws[idx] + de * pc * desing(hc, T(1), d4);
             wo[idx] = wn;
+            pout[idx] = pc;
             if (!isfinite(wn) || !isfinite(pc)) bad = 1;
         } else {
             wo[idx] = ws[idx];
-            p[idx] = T(0);
+            pout[idx] = T(0);
         }
         // cell
         if (I < P.nx && J < P.ny) {
@@ -673,8 +836,9 @@ k_corr2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
                 const size_t ms = (size_t)js * P.nx + i, mn = (size_t)jn * P.nx + i;
                 const T X = T(0.5) * ((eta[me] - H[me]) - (eta[mw] - H[mw]));
                 const T Y = T(0.5) * ((eta[mn] - H[mn]) - (eta[ms] - H[ms]));
-                const T pSW = p[(size_t)J * nxn + I], pSE = p[(size_t)J * nxn + I + 1];
-                const T pNW = p[(size_t)(J + 1) * nxn + I], pNE = p[(size_t)(J + 1) * nxn + I + 1];
+                auto pat = [&](size_t m) { return p[m] + dp[m]; };
+                const T pSW = pat((size_t)J * nxn + I), pSE = pat((size_t)J * nxn + I + 1);
+                const T pNW = pat((size_t)(J + 1) * nxn + I), pNE = pat((size_t)(J + 1) * nxn + I + 1);
                 const T TN = -T(0.5) * h * (pNE - pNW) / P.dx - T(0.25) * (pNE + pNW) * X / P.dx;
                 const T TS = -T(0.5) * h * (pSE - pSW) / P.dx - T(0.25) * (pSE + pSW) * X / P.dx;
                 const T TE = -T(0.5) * h * (pNE - pSE) / P.dy - T(0.25) * (pNE + pSE) * Y / P.dy;
@@ -693,7 +857,7 @@ k_corr2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
     }
     if (bad) atomicOr(&st->nonfinite, 1);
     if (final_stage) {
-        if (grid_reduce<1, true>(acc, partials, &st->counter) && threadIdx.x == 0) st->lam = acc[0];
+        if (grid_reduce<1, 1u>(acc, partials, &st->counter) && threadIdx.x == 0) st->lam = acc[0];
     }
 }
 
@@ -985,7 +1149,7 @@ k_corr1d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
     }
     if (bad) atomicOr(&st->nonfinite, 1);
     if (final_stage) {
-        if (grid_reduce<1, true>(acc, partials, &st->counter) && threadIdx.x == 0) st->lam = acc[0];
+        if (grid_reduce<1, 1u>(acc, partials, &st->counter) && threadIdx.x == 0) st->lam = acc[0];
     }
 }
 
@@ -998,7 +1162,7 @@ k_mass(long long n, const T* __restrict__ eta, const T* __restrict__ H, double* 
 {
     double acc[1] = {0.0};
     GRID_STRIDE(idx, n) acc[0] += (double)tmax(eta[idx] + H[idx], T(0));
-    if (grid_reduce<1, false>(acc, partials, &st->counter) && threadIdx.x == 0) st->mass = acc[0];
+    if (grid_reduce<1, 0u>(acc, partials, &st->counter) && threadIdx.x == 0) st->mass = acc[0];
 }
 
 template <typename T>
@@ -1017,7 +1181,7 @@ k_lambda(Prm<T> P, int dim, const T* __restrict__ eta, const T* __restrict__ q1,
         if (dim == 2) l += (fabs(desing(h, q2[idx], d4)) + cw) / P.dy;
         acc[0] = fmax(acc[0], l);
     }
-    if (grid_reduce<1, true>(acc, partials, &st->counter) && threadIdx.x == 0) st->lam = acc[0];
+    if (grid_reduce<1, 1u>(acc, partials, &st->counter) && threadIdx.x == 0) st->lam = acc[0];
 }
 
 template <typename T>
@@ -1063,13 +1227,47 @@ void launch_break2d(const Prm<T>& P, const Launch& L, const T* eta, const T* q1,
 
 template <typename T>
 void launch_asm2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* w_in,
-                  const T* w_base, T a, T b, T de, int with_coef, double tol2, int max_iter,
-                  double* partials, SolveCtl* ctl)
+                  const T* w_base, T a, T b, T de, int with_coef, int resid_form, double tol2,
+                  int max_iter, int kpass, double* partials, SolveCtl* ctl)
 {
     k_asm2d<T><<<L.nblk, kThreads, 0, L.s>>>(P, B.etas, B.H, B.q1k, B.q2k, B.q1s, B.q2s, w_in,
                                              w_base, a, b, de, with_coef, B.ws, B.cC, B.cW,
-                                             B.cE, B.cS, B.cN, B.rhs, partials, ctl, tol2,
-                                             max_iter);
+                                             B.cE, B.cS, B.cN, B.rhs, B.p, resid_form, partials,
+                                             ctl, tol2, max_iter, kpass);
+}
+
+template <typename T> struct ChebCfg;
+template <> struct ChebCfg<float> { static constexpr int TX = 64, TY = 32, K = 4; };
+template <> struct ChebCfg<double> { static constexpr int TX = 32, TY = 32, K = 4; };
+
+template <typename T>
+int cheb_sweeps_per_pass() { return ChebCfg<T>::K; }
+
+template <typename T>
+size_t cheb_tiles(const Prm<T>& P)
+{
+    using C = ChebCfg<T>;
+    return (size_t)((P.nx + 1 + C::TX - 1) / C::TX) * ((P.ny + 1 + C::TY - 1) / C::TY);
+}
+
+template <typename T>
+int launch_cheb_pass(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, T* xprev,
+                     double* partials)
+{
+    using C = ChebCfg<T>;
+    constexpr size_t smem = 7 * (size_t)(C::TX + 2 * C::K) * (C::TY + 2 * C::K) * sizeof(T);
+    static bool attr_set = false;
+    if (!attr_set) {
+        if (cudaFuncSetAttribute(k_cheb_pass<T, C::TX, C::TY, C::K>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return -1;
+        attr_set = true;
+    }
+    dim3 grid((P.nx + 1 + C::TX - 1) / C::TX, (P.ny + 1 + C::TY - 1) / C::TY);
+    k_cheb_pass<T, C::TX, C::TY, C::K><<<grid, 256, smem, s>>>(rows_of(P, B), B.rhs, B.dp,
+                                                               xprev, partials, B.sctl);
+    return 0;
 }
 
 template <typename T>
@@ -1081,7 +1279,7 @@ void launch_matvec2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T
 template <typename T>
 void launch_bicg_init(const Prm<T>& P, const Launch& L, const Bufs<T>& B, double* partials)
 {
-    k_bicg_init<T><<<L.nblk, kThreads, 0, L.s>>>(rows_of(P, B), B.rhs, B.p, B.r, B.rh, B.ph[0],
+    k_bicg_init<T><<<L.nblk, kThreads, 0, L.s>>>(rows_of(P, B), B.rhs, B.dp, B.r, B.rh, B.ph[0],
                                                  B.v[0], partials, B.sctl);
 }
 
@@ -1099,7 +1297,7 @@ void launch_bicg_phase(const Prm<T>& P, const Launch& L, const Bufs<T>& B, int p
     else if (phase == 1)
         k_bicg_B<T><<<L.nblk, kThreads, 0, L.s>>>(R, B.r, vn, B.t, partials, B.sctl);
     else
-        k_bicg_C<T><<<L.nblk, kThreads, 0, L.s>>>(R, B.r, B.rh, phn, vn, B.t, B.p, partials,
+        k_bicg_C<T><<<L.nblk, kThreads, 0, L.s>>>(R, B.r, B.rh, phn, vn, B.t, B.dp, partials,
                                                   B.sctl);
 }
 
@@ -1108,8 +1306,9 @@ void launch_corr2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* 
                    const T* q2k, T de, int with_p, T* eo, T* q1o, T* q2o, T* wo, int final_stage,
                    double* partials, StepCtl* st)
 {
-    k_corr2d<T><<<L.nblk, kThreads, 0, L.s>>>(P, B.etas, B.H, q1k, q2k, B.ws, B.p, de, with_p,
-                                              eo, q1o, q2o, wo, final_stage, partials, st);
+    k_corr2d<T><<<L.nblk, kThreads, 0, L.s>>>(P, B.etas, B.H, q1k, q2k, B.ws, B.p, B.dp, B.palt,
+                                              de, with_p, eo, q1o, q2o, wo, final_stage, partials,
+                                              st);
 }
 
 template <typename T>
@@ -1240,7 +1439,11 @@ void launch_convert_from_double(const Launch& L, const double* src, T* dst, size
     template void launch_break2d<T>(const Prm<T>&, const Launch&, const T*, const T*, const T*,\
                                     const T*, T, T*, T*);                                      \
     template void launch_asm2d<T>(const Prm<T>&, const Launch&, const Bufs<T>&, const T*,      \
-                                  const T*, T, T, T, int, double, int, double*, SolveCtl*);    \
+                                  const T*, T, T, T, int, int, double, int, int, double*,      \
+                                  SolveCtl*);                                                  \
+    template int cheb_sweeps_per_pass<T>();                                                    \
+    template size_t cheb_tiles<T>(const Prm<T>&);                                              \
+    template int launch_cheb_pass<T>(const Prm<T>&, cudaStream_t, const Bufs<T>&, T*, double*);\
     template void launch_matvec2d<T>(const Prm<T>&, const Launch&, const Bufs<T>&, const T*,   \
                                      T*);                                                      \
     template void launch_bicg_init<T>(const Prm<T>&, const Launch&, const Bufs<T>&, double*);  \

@@ -77,7 +77,7 @@ def shoals_2d(n: int = 1024, L: float = 102.4, seed: int = 2, depth: float = 0.5
     x = (np.arange(n) + 0.5) * dx
     X, Y = np.meshgrid(x, x)
     s = seed
-    while True:
+    for _ in range(10000):
         rng = np.random.default_rng(s)
         amp = rng.uniform(0.1, 0.3, nshoal)
         sig = rng.uniform(2.0, 6.0, nshoal)
@@ -88,6 +88,8 @@ def shoals_2d(n: int = 1024, L: float = 102.4, seed: int = 2, depth: float = 0.5
         if H.min() >= min_depth:
             break
         s += 1
+    else:
+        raise ValueError("shoals_2d: no draw with min depth >= %g for L = %g" % (min_depth, L))
     eta = hump * np.exp(-((X - L / 2) ** 2 + (Y - L / 2) ** 2) / (2.0 * hump_sigma ** 2))
     z = np.zeros((n, n))
     return Workload("shoals_2d", n, n, dx, dx, H, eta, z, z.copy(),

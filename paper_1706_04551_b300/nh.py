@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libnh.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ENONFINITE = 0, -1, -2, -3, -4, -5
 WALL, OUTFLOW = 0, 1
+BICGSTAB, CHEBYSHEV = 0, 1
 FP64, FP32 = 0, 1
 HOST, DEVICE = 0, 1
 
@@ -31,7 +32,7 @@ class Params(C.Structure):
                 ("hdry", C.c_double), ("manning_n", C.c_double), ("B1", C.c_double),
                 ("B2", C.c_double), ("breaking", C.c_int), ("nonhydrostatic", C.c_int),
                 ("solver", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int),
-                ("precision", C.c_int), ("fixed_dt", C.c_double)]
+                ("precision", C.c_int), ("fixed_dt", C.c_double), ("eps_dp", C.c_double)]
 
 
 class StatsT(C.Structure):
@@ -55,7 +56,7 @@ EXPORTS = ("nh_default_params", "nh_create", "nh_set_state", "nh_get_state", "nh
 
 # kernel classes of nh_profile_t, in enum order
 KERNELS = ("hyperbolic", "breaking", "assembly", "solve_init", "bicg_A", "bicg_B", "bicg_C",
-           "tridiag", "correction")
+           "cheb_pass", "tridiag", "correction")
 
 
 class ProfileT(C.Structure):
