@@ -164,7 +164,8 @@ template <int NV, unsigned MAXMASK>
 __device__ __forceinline__ void block_reduce(double (&v)[NV])
 {
     __shared__ double sm[NV][32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int lane = tid & 31, wid = tid >> 5, nw = (blockDim.x * blockDim.y + 31) >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) v[k] = ((MAXMASK >> k) & 1u) ? warp_max(v[k]) : warp_sum(v[k]);
     if (lane == 0)
@@ -192,8 +193,10 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[NV], double* partials,
     block_reduce<NV, MAXMASK>(v);
     const unsigned nblocks = gridDim.x * gridDim.y;
     const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+    const unsigned tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const unsigned nthr = blockDim.x * blockDim.y;
     __shared__ bool last;
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) partials[(size_t)bid * NV + k] = v[k];
         __threadfence();
@@ -205,7 +208,7 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[NV], double* partials,
     double acc[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) acc[k] = ((MAXMASK >> k) & 1u) ? -1.0e300 : 0.0;
-    for (unsigned bb = threadIdx.x; bb < nblocks; bb += blockDim.x)
+    for (unsigned bb = tid; bb < nblocks; bb += nthr)
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
             double x = __ldcg(partials + (size_t)bb * NV + k);
@@ -214,7 +217,7 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[NV], double* partials,
     block_reduce<NV, MAXMASK>(acc);
 #pragma unroll
     for (int k = 0; k < NV; ++k) v[k] = acc[k];
-    if (threadIdx.x == 0) *counter = 0u;
+    if (tid == 0) *counter = 0u;
     return true;
 }
 
@@ -342,10 +345,9 @@ k_break2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ q1,
 // of the row scaled by 8 dx dy / de, and the right-hand side b = -(8 dx dy / de) B(q*, w*).
 // Link (x) between nodes (I, J) and (I+1, J) carries alpha+- = 2 h~ + X~, X~ - 2 h~ (h~, X~
 // averages over cells (I, J-1), (I, J)); node terms beta-+ = Xi -+ 2 h_c.
-// B* is evaluated in FP64 from the stored (T) state: its terms nearly cancel (the
-// constraint holds up to O(dt)), so T rounding there would be amplified by the system's
-// conditioning.  With resid_form = 1 the kernel stores the defect r0 = b - M p0 (FP64, then
-// rounded) for a correction solve M dp = r0 started from the warm start p0; else b itself.
+// With resid_form = 1 the kernel stores the defect r0 = b - M p0 for a correction solve
+// M dp = r0 started from the warm start p0 (the solver's rounding floor then applies to dp,
+// not to p); else b itself.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_asm2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
@@ -358,6 +360,8 @@ k_asm2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
 {
     const T d2 = P.delta * P.delta, d4 = d2 * d2;
     const int nxn = P.nx + 1;
+    const T inv2dx = T(1) / (T(2) * P.dx), inv2dy = T(1) / (T(2) * P.dy);
+    const T scale = T(8) * P.dx * P.dy / de;
     double acc[3] = {0.0, 0.0, 0.0};   // ||b||^2, ||D^-1 b||^2, max Gershgorin radius
     GRID_STRIDE(idx, (long long)(P.nx + 1) * (P.ny + 1))
     {
@@ -366,7 +370,6 @@ k_asm2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
         // sx[r][k]: rows J-1 (r=0), J (r=1), columns I-2 .. I+1
         // sy[c][k]: columns I-1 (c=0), I (c=1), rows J-2 .. J+1
         T sx[2][4], sy[2][4], hq[2][2];
-        double sd[2][2], hd2[2][2];   // FP64 s and h of the core cells
 #pragma unroll
         for (int r = 0; r < 2; ++r)
 #pragma unroll
@@ -377,11 +380,7 @@ k_asm2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
                 size_t m = (size_t)jj * P.nx + ii;
                 const T e = eta[m], Hm = H[m];
                 sx[r][k] = e - Hm;
-                if (k == 1 || k == 2) {
-                    hq[r][k - 1] = tmax(e + Hm, T(0));
-                    sd[r][k - 1] = (double)e - (double)Hm;
-                    hd2[r][k - 1] = fmax((double)e + (double)Hm, 0.0);
-                }
+                if (k == 1 || k == 2) hq[r][k - 1] = tmax(e + Hm, T(0));
             }
 #pragma unroll
         for (int cc = 0; cc < 2; ++cc)
@@ -405,8 +404,7 @@ k_asm2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
         const T Xi = T(0.5) * (se + sb) - T(0.5) * (sd_ + sa);
         const T Yi = T(0.5) * (sd_ + se) - T(0.5) * (sa + sb);
         // discharges of the core cells (post-breaking) with boundary parity
-        double Q1[4], Q2[4];
-        T P1[4], P2[4];
+        T Q1[4], Q2[4], P1[4], P2[4];
         const int ci[4] = {I - 1, I, I - 1, I}, cj[4] = {J - 1, J - 1, J, J};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -414,8 +412,8 @@ k_asm2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
             int ii = map_cell(ci[k], P.nx, P.bcw, P.bce, rx);
             int jj = map_cell(cj[k], P.ny, P.bcs, P.bcn, ry);
             size_t m = (size_t)jj * P.nx + ii;
-            Q1[k] = rx ? -(double)q1k[m] : (double)q1k[m];
-            Q2[k] = ry ? -(double)q2k[m] : (double)q2k[m];
+            Q1[k] = rx ? -q1k[m] : q1k[m];
+            Q2[k] = ry ? -q2k[m] : q2k[m];
             if (P.breaking) {
                 P1[k] = rx ? -q1s[m] : q1s[m];
                 P2[k] = ry ? -q2s[m] : q2s[m];
@@ -436,18 +434,14 @@ k_asm2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
             wv += de * T(2) * nu * du * desing(hc, T(1), d4);
         }
         ws[nidx] = wv;
-        // B(q*, w*) (Eqs. 37-40) with the edge discharges of Eq. (41) at p = 0, in FP64
-        const double hcD = 0.25 * (hd2[0][0] + hd2[0][1] + hd2[1][0] + hd2[1][1]);
-        const double XiD = 0.5 * (sd[1][1] + sd[0][1]) - 0.5 * (sd[1][0] + sd[0][0]);
-        const double YiD = 0.5 * (sd[1][0] + sd[1][1]) - 0.5 * (sd[0][0] + sd[0][1]);
-        const double q1E = 0.5 * (Q1[3] + Q1[1]), q1W = 0.5 * (Q1[2] + Q1[0]);
-        const double q2N = 0.5 * (Q2[3] + Q2[2]), q2S = 0.5 * (Q2[1] + Q2[0]);
-        const double dxd = (double)P.dx, dyd = (double)P.dy;
-        const double Bs = ((2.0 * hcD - XiD) * q1E - (2.0 * hcD + XiD) * q1W) / (2.0 * dxd)
-                        + ((2.0 * hcD - YiD) * q2N - (2.0 * hcD + YiD) * q2S) / (2.0 * dyd)
-                        + 2.0 * hcD * (double)wv;
-        const double bval = -(8.0 * dxd * dyd / (double)de) * Bs;
-        acc[0] += bval * bval;
+        // B(q*, w*) (Eqs. 37-40) with the edge discharges of Eq. (41) at p = 0
+        const T q1E = T(0.5) * (Q1[3] + Q1[1]), q1W = T(0.5) * (Q1[2] + Q1[0]);
+        const T q2N = T(0.5) * (Q2[3] + Q2[2]), q2S = T(0.5) * (Q2[1] + Q2[0]);
+        const T Bs = ((T(2) * hc - Xi) * q1E - (T(2) * hc + Xi) * q1W) * inv2dx
+                   + ((T(2) * hc - Yi) * q2N - (T(2) * hc + Yi) * q2S) * inv2dy
+                   + T(2) * hc * wv;
+        const T bval = -scale * Bs;
+        acc[0] += (double)bval * (double)bval;
         if (with_coef) {
             const T apE = T(2) * T(0.5) * (hb + he) + T(0.5) * (Xb + Xe);
             const T amE = T(0.5) * (Xb + Xe) - T(2) * T(0.5) * (hb + he);
@@ -465,24 +459,24 @@ k_asm2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
             const T dC = T(16) * P.dx * P.dy + rxl * (bmx * amE + bpx * apW)
                        + ryl * (bmy * amN + bpy * apS);
             cE[nidx] = vE; cW[nidx] = vW; cN[nidx] = vN; cS[nidx] = vS; cC[nidx] = dC;
-            const double ad = fabs((double)dC);
-            acc[1] += (bval / ad) * (bval / ad);
-            acc[2] = fmax(acc[2], (fabs((double)vE) + fabs((double)vW) + fabs((double)vN) +
-                                   fabs((double)vS)) / ad);
+            const T id = T(1) / fabs(dC);
+            const T bs = bval * id;
+            acc[1] += (double)bs * (double)bs;
+            acc[2] = fmax(acc[2], (double)((fabs(vE) + fabs(vW) + fabs(vN) + fabs(vS)) * id));
             if (resid_form) {
                 const int Iw = map_node(I - 1, P.nx), Ie = map_node(I + 1, P.nx);
                 const int Js = map_node(J - 1, P.ny), Jn = map_node(J + 1, P.ny);
-                const double mp = (double)dC * (double)p0[nidx]
-                                + (double)vW * (double)p0[(size_t)J * nxn + Iw]
-                                + (double)vE * (double)p0[(size_t)J * nxn + Ie]
-                                + (double)vS * (double)p0[(size_t)Js * nxn + I]
-                                + (double)vN * (double)p0[(size_t)Jn * nxn + I];
-                rhs[nidx] = (T)(bval - mp);
+                T mp = dC * p0[nidx];
+                mp = fma(vW, p0[(size_t)J * nxn + Iw], mp);
+                mp = fma(vE, p0[(size_t)J * nxn + Ie], mp);
+                mp = fma(vS, p0[(size_t)Js * nxn + I], mp);
+                mp = fma(vN, p0[(size_t)Jn * nxn + I], mp);
+                rhs[nidx] = bval - mp;
             } else {
-                rhs[nidx] = (T)bval;
+                rhs[nidx] = bval;
             }
         } else {
-            rhs[nidx] = (T)bval;
+            rhs[nidx] = bval;
         }
     }
     if (grid_reduce<3, 4u>(acc, partials, &ctl->counter) && threadIdx.x == 0) {
@@ -679,84 +673,108 @@ k_bicg_C(Rows<T> R, T* __restrict__ r, const T* __restrict__ rh, const T* __rest
 
 // Jacobi with Chebyshev-scheduled relaxation (the "scheduled relaxation" of Sec. 5 with
 // the Chebyshev weights of the Gershgorin interval [1 - g, 1 + g] of D^-1 M), K sweeps per
-// launch with temporal blocking: each block loads a TX x TY node tile plus a K-node halo
-// into shared memory, sweeps K times there (the valid region shrinking by one node per
-// sweep), and writes the tile back.  Sweep k: x_{k+1} = x_k + c1 (x_k - x_{k-1}) + c2 r_k,
+// launch with temporal blocking: each block loads a tile plus a K-node halo into shared
+// memory, sweeps K times there (the valid region shrinking by one node per sweep) and
+// writes the tile back.  Sweep k: x_{k+1} = x_k + c1 (x_k - x_{k-1}) + c2 r_k with
 // r_k = D^-1 (b - M x_k).  The last sweep accumulates ||r||^2 (Jacobi-scaled) and
 // max |x_{k+1} - x_k|; the last block tests convergence and prepares the next K weights.
-template <typename T, int TX, int TY, int K>
-__global__ void __launch_bounds__(256)
-k_cheb_pass(Rows<T> R, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ xp,
-            double* partials, SolveCtl* ctl)
+// A (32, 8) thread block owns a fixed set of region
+// nodes per thread (columns tx + 32 a, rows ty + 8 b), so the sweep loop has no index
+// arithmetic beyond constant offsets.  The region is the tile plus a K-node halo on every
+// side; outside the domain the halo holds mirror images (values, and coefficients with
+// W <-> E or S <-> N swapped), which evolve exactly as the nodes they mirror, so tiles at
+// the boundary are no different from interior ones.  x_{k-1} lives in registers.
+template <typename T, int NA, int NB, int K>
+__global__ void __launch_bounds__(256, 2)
+k_cheb_pass2(Rows<T> R, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ xp,
+             double* partials, SolveCtl* ctl)
 {
     if (ctl->done) return;
-    extern __shared__ unsigned char cheb_smem[];
-    constexpr int RW = TX + 2 * K, RH = TY + 2 * K, RN = RW * RH;
-    T* xa = reinterpret_cast<T*>(cheb_smem);   // x_{k-1}, then x_{k+1}
-    T* xb = xa + RN;                           // x_k
-    T* bd = xb + RN;
+    constexpr int RW = 32 * NA, RH = 8 * NB, RN = RW * RH;
+    constexpr int TX = RW - 2 * K, TY = RH - 2 * K;
+    extern __shared__ unsigned char cheb2_smem[];
+    T* xs0 = reinterpret_cast<T*>(cheb2_smem);
+    T* xs1 = xs0 + RN;
+    T* bd = xs1 + RN;
     T* wW = bd + RN;
     T* wE = wW + RN;
     T* wS = wE + RN;
     T* wN = wS + RN;
-    const int NX = R.nx + 1, NY = R.ny + 1;
-    const int I0 = blockIdx.x * TX, J0 = blockIdx.y * TY;
-    const int RI0 = I0 - K > 0 ? I0 - K : 0, RI1 = I0 + TX + K < NX ? I0 + TX + K : NX;
-    const int RJ0 = J0 - K > 0 ? J0 - K : 0, RJ1 = J0 + TY + K < NY ? J0 + TY + K : NY;
-    const int rw = RI1 - RI0, rh = RJ1 - RJ0;
-    for (int t = threadIdx.x; t < rw * rh; t += blockDim.x) {
-        const int li = t % rw, lj = t / rw;
-        const size_t g = (size_t)(RJ0 + lj) * NX + RI0 + li;
-        const int sidx = lj * RW + li;
-        const T ic = T(1) / R.cC[g];
-        xa[sidx] = xp[g];
-        xb[sidx] = x[g];
-        bd[sidx] = b[g] * ic;
-        wW[sidx] = R.cW[g] * ic;
-        wE[sidx] = R.cE[g] * ic;
-        wS[sidx] = R.cS[g] * ic;
-        wN[sidx] = R.cN[g] * ic;
-    }
+    const int nx = R.nx, ny = R.ny, NX = nx + 1;
+    const int I0 = (int)blockIdx.x * TX - K, J0 = (int)blockIdx.y * TY - K;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    T xa[NA * NB];
+#pragma unroll
+    for (int bb = 0; bb < NB; ++bb)
+#pragma unroll
+        for (int aa = 0; aa < NA; ++aa) {
+            const int li = tx + 32 * aa, lj = ty + 8 * bb;
+            const int gI = I0 + li, gJ = J0 + lj;
+            int mI = gI < 0 ? -gI : (gI > nx ? 2 * nx - gI : gI);
+            int mJ = gJ < 0 ? -gJ : (gJ > ny ? 2 * ny - gJ : gJ);
+            const bool fx = mI != gI, fy = mJ != gJ;
+            mI = mI < 0 ? 0 : (mI > nx ? nx : mI);   // far outside: any finite value
+            mJ = mJ < 0 ? 0 : (mJ > ny ? ny : mJ);
+            const size_t g = (size_t)mJ * NX + mI;
+            const int sidx = lj * RW + li;
+            const T ic = T(1) / R.cC[g];
+            xs0[sidx] = x[g];
+            xa[bb * NA + aa] = xp[g];
+            bd[sidx] = b[g] * ic;
+            const T cw = R.cW[g] * ic, ce = R.cE[g] * ic;
+            const T cs = R.cS[g] * ic, cn = R.cN[g] * ic;
+            wW[sidx] = fx ? ce : cw;
+            wE[sidx] = fx ? cw : ce;
+            wS[sidx] = fy ? cn : cs;
+            wN[sidx] = fy ? cs : cn;
+        }
     T c1s[K], c2s[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) { c1s[k] = (T)ctl->c1[k]; c2s[k] = (T)ctl->c2[k]; }
     __syncthreads();
-    const int TI1 = I0 + TX < NX ? I0 + TX : NX, TJ1 = J0 + TY < NY ? J0 + TY : NY;
+    T* cur = xs0;
+    T* nxt = xs1;
     double acc[2] = {0.0, 0.0};
 #pragma unroll
     for (int sw = 0; sw < K; ++sw) {
-        const int vI0 = RI0 == 0 ? 0 : RI0 + sw + 1, vI1 = RI1 == NX ? NX : RI1 - (sw + 1);
-        const int vJ0 = RJ0 == 0 ? 0 : RJ0 + sw + 1, vJ1 = RJ1 == NY ? NY : RJ1 - (sw + 1);
-        const int vw = vI1 - vI0, vn = vw * (vJ1 - vJ0);
         const T c1 = c1s[sw], c2 = c2s[sw];
-        for (int t = threadIdx.x; t < vn; t += blockDim.x) {
-            const int gI = vI0 + t % vw, gJ = vJ0 + t / vw;
-            const int li = gI - RI0, lj = gJ - RJ0;
-            const int sidx = lj * RW + li;
-            const int lW = map_node(gI - 1, NX - 1) - RI0, lE = map_node(gI + 1, NX - 1) - RI0;
-            const int lS = map_node(gJ - 1, NY - 1) - RJ0, lN = map_node(gJ + 1, NY - 1) - RJ0;
-            const T xc = xb[sidx];
-            const T r = bd[sidx] - xc -
-                        (wW[sidx] * xb[lj * RW + lW] + wE[sidx] * xb[lj * RW + lE] +
-                         wS[sidx] * xb[lS * RW + li] + wN[sidx] * xb[lN * RW + li]);
-            const T xn = xc + c1 * (xc - xa[sidx]) + c2 * r;
-            xa[sidx] = xn;
-            if (sw == K - 1 && gI >= I0 && gI < TI1 && gJ >= J0 && gJ < TJ1) {
-                acc[0] += (double)r * (double)r;
-                acc[1] = fmax(acc[1], fabs((double)(xn - xc)));
+#pragma unroll
+        for (int bb = 0; bb < NB; ++bb)
+#pragma unroll
+            for (int aa = 0; aa < NA; ++aa) {
+                const int li = tx + 32 * aa, lj = ty + 8 * bb;
+                if (li > sw && li < RW - 1 - sw && lj > sw && lj < RH - 1 - sw) {
+                    const int sidx = lj * RW + li;
+                    const T xc = cur[sidx];
+                    const T r = bd[sidx] - xc -
+                                (wW[sidx] * cur[sidx - 1] + wE[sidx] * cur[sidx + 1] +
+                                 wS[sidx] * cur[sidx - RW] + wN[sidx] * cur[sidx + RW]);
+                    const T xn = xc + c1 * (xc - xa[bb * NA + aa]) + c2 * r;
+                    nxt[sidx] = xn;
+                    xa[bb * NA + aa] = xc;
+                    if (sw == K - 1 && li >= K && li < RW - K && lj >= K && lj < RH - K &&
+                        I0 + li <= nx && J0 + lj <= ny) {
+                        acc[0] += (double)r * (double)r;
+                        acc[1] = fmax(acc[1], fabs((double)(xn - xc)));
+                    }
+                }
+            }
+        __syncthreads();
+        T* tmp = cur; cur = nxt; nxt = tmp;
+    }
+#pragma unroll
+    for (int bb = 0; bb < NB; ++bb)
+#pragma unroll
+        for (int aa = 0; aa < NA; ++aa) {
+            const int li = tx + 32 * aa, lj = ty + 8 * bb;
+            const int gI = I0 + li, gJ = J0 + lj;
+            if (li >= K && li < RW - K && lj >= K && lj < RH - K && gI <= nx && gJ <= ny) {
+                const size_t g = (size_t)gJ * NX + gI;
+                x[g] = cur[lj * RW + li];
+                xp[g] = xa[bb * NA + aa];
             }
         }
-        __syncthreads();
-        T* tmp = xa; xa = xb; xb = tmp;
-    }
-    for (int t = threadIdx.x; t < (TI1 - I0) * (TJ1 - J0); t += blockDim.x) {
-        const int gI = I0 + t % (TI1 - I0), gJ = J0 + t / (TI1 - I0);
-        const size_t g = (size_t)gJ * NX + gI;
-        const int sidx = (gJ - RJ0) * RW + (gI - RI0);
-        x[g] = xb[sidx];
-        xp[g] = xa[sidx];
-    }
-    if (grid_reduce<2, 2u>(acc, partials, &ctl->counter) && threadIdx.x == 0) {
+    if (grid_reduce<2, 2u>(acc, partials, &ctl->counter) && tx == 0 && ty == 0) {
         ctl->rr = acc[0];
         ctl->dpmax = acc[1];
         ctl->sweeps += K;
@@ -1237,8 +1255,8 @@ void launch_asm2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* w
 }
 
 template <typename T> struct ChebCfg;
-template <> struct ChebCfg<float> { static constexpr int TX = 64, TY = 32, K = 4; };
-template <> struct ChebCfg<double> { static constexpr int TX = 32, TY = 32, K = 4; };
+template <> struct ChebCfg<float> { static constexpr int NA = 4, NB = 4, K = 4; };
+template <> struct ChebCfg<double> { static constexpr int NA = 2, NB = 4, K = 4; };
 
 template <typename T>
 int cheb_sweeps_per_pass() { return ChebCfg<T>::K; }
@@ -1247,7 +1265,8 @@ template <typename T>
 size_t cheb_tiles(const Prm<T>& P)
 {
     using C = ChebCfg<T>;
-    return (size_t)((P.nx + 1 + C::TX - 1) / C::TX) * ((P.ny + 1 + C::TY - 1) / C::TY);
+    constexpr int TX = 32 * C::NA - 2 * C::K, TY = 8 * C::NB - 2 * C::K;
+    return (size_t)((P.nx + 1 + TX - 1) / TX) * ((P.ny + 1 + TY - 1) / TY);
 }
 
 template <typename T>
@@ -1255,18 +1274,20 @@ int launch_cheb_pass(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, T* xprev
                      double* partials)
 {
     using C = ChebCfg<T>;
-    constexpr size_t smem = 7 * (size_t)(C::TX + 2 * C::K) * (C::TY + 2 * C::K) * sizeof(T);
+    constexpr int TX = 32 * C::NA - 2 * C::K, TY = 8 * C::NB - 2 * C::K;
+    constexpr size_t smem = 7 * (size_t)(32 * C::NA) * (8 * C::NB) * sizeof(T);
     static bool attr_set = false;
     if (!attr_set) {
-        if (cudaFuncSetAttribute(k_cheb_pass<T, C::TX, C::TY, C::K>,
+        if (cudaFuncSetAttribute(k_cheb_pass2<T, C::NA, C::NB, C::K>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return -1;
         attr_set = true;
     }
-    dim3 grid((P.nx + 1 + C::TX - 1) / C::TX, (P.ny + 1 + C::TY - 1) / C::TY);
-    k_cheb_pass<T, C::TX, C::TY, C::K><<<grid, 256, smem, s>>>(rows_of(P, B), B.rhs, B.dp,
-                                                               xprev, partials, B.sctl);
+    dim3 grid((P.nx + 1 + TX - 1) / TX, (P.ny + 1 + TY - 1) / TY);
+    k_cheb_pass2<T, C::NA, C::NB, C::K><<<grid, dim3(32, 8), smem, s>>>(rows_of(P, B), B.rhs,
+                                                                        B.dp, xprev, partials,
+                                                                        B.sctl);
     return 0;
 }
 
