@@ -188,7 +188,9 @@ struct Impl : Base {
             size_t np = (size_t)4 * nblk + 64;
             if (dim == 2) {
                 const size_t nt = 2 * cheb_tiles<T>(P) + 64;
+                const size_t na = 3 * asm_tiles<T>(P) + 64;
                 if (nt > np) np = nt;
+                if (na > np) np = na;
             }
             A(B.partials, np);
         }

@@ -96,6 +96,8 @@ int cheb_sweeps_per_pass();
 template <typename T>
 size_t cheb_tiles(const Prm<T>& P);
 template <typename T>
+size_t asm_tiles(const Prm<T>& P);   // blocks of the 2D assembly (3 partials each)
+template <typename T>
 int launch_cheb_pass(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, T* xprev,
                      double* partials);
 template <typename T>

@@ -301,6 +301,114 @@ k_hyp2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ q1,
     if (nclamp) atomicAdd(&st->clamped, nclamp);
 }
 
+// Face-based form of the hyperbolic update for a TX x TY cell tile: the block stages the
+// tile plus a 2-cell halo (h, eta, u, v) in shared memory, then every face is evaluated
+// once: it reconstructs the two cells next to it (minmod slopes of its side only) and
+// stores, for the left cell, D^- + F_c(U^-) + (0, g h_L eta^-, 0) and, for the right cell,
+// D^+ - F_c(U^+) - (0, g h_R eta^+, 0) (normal frame), i.e. the fluctuation plus that
+// cell's half of the inner-cell term of Eq. (22) / (30).  A cell sums its four faces.
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(256)
+k_hyp2d_t(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ q1,
+          const T* __restrict__ q2, const T* __restrict__ etab, const T* __restrict__ q1b,
+          const T* __restrict__ q2b, const T* __restrict__ H, T a, T b, T dt,
+          T* __restrict__ eo, T* __restrict__ q1o, T* __restrict__ q2o, StepCtl* st)
+{
+    constexpr int LW = TX + 4, LH = TY + 4, LN = LW * LH;
+    constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
+    __shared__ T sh[LN], se[LN], su[LN], sv[LN];
+    __shared__ T CLx[3][NFX], CRx[3][NFX], CLy[3][NFY], CRy[3][NFY];
+    const T d2 = P.delta * P.delta, d4 = d2 * d2;
+    const T g = P.g, hdry = P.hdry;
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int t = tid; t < LN; t += nt) {
+        const int li = t % LW, lj = t / LW;
+        // cells more than 2 outside the domain only feed discarded faces: clamp them
+        int ci = i0 + li - 2, cj = j0 + lj - 2;
+        ci = ci > P.nx + 1 ? P.nx + 1 : ci;
+        cj = cj > P.ny + 1 ? P.ny + 1 : cj;
+        const St<T> c = load_st(P, eta, q1, q2, H, ci, cj, d4);
+        sh[t] = c.h; se[t] = c.e; su[t] = c.u; sv[t] = c.v;
+    }
+    __syncthreads();
+    auto L = [&](int i, int j) { return (j + 2) * LW + (i + 2); };   // local cell index
+    // x faces f = 0..TX between local cells f-1 and f, rows 0..TY-1
+    for (int t = tid; t < NFX + NFY; t += nt) {
+        const bool xf = t < NFX;
+        const int tt = xf ? t : t - NFX;
+        const int f = xf ? tt % (TX + 1) : tt % TX;
+        const int r = xf ? tt / (TX + 1) : tt / TX;
+        // cells along the face normal: m2 = cell -2, m1 = -1 (left), p0 = right, p1 = +1
+        const int s0 = xf ? 1 : LW;
+        const int cl = xf ? L(f - 1, r) : L(f, r - 1);   // left cell (west / south)
+        const int cr = cl + s0;                            // right cell
+        const int cm = cl - s0, cp = cr + s0;
+        // left cell: its high-side value; right cell: its low-side value
+        const T uL = xf ? su[cl] : sv[cl], uR = xf ? su[cr] : sv[cr];
+        const T tL = xf ? sv[cl] : su[cl], tR = xf ? sv[cr] : su[cr];
+        const T unm = xf ? su[cm] : sv[cm], unp = xf ? su[cp] : sv[cp];
+        const T utm = xf ? sv[cm] : su[cm], utp = xf ? sv[cp] : su[cp];
+        const T sLh = minmod(sh[cl] - sh[cm], sh[cr] - sh[cl]);
+        const T sLu = minmod(uL - unm, uR - uL);
+        const T sLt = minmod(tL - utm, tR - tL);
+        const bool dL = sh[cm] <= hdry || sh[cl] <= hdry || sh[cr] <= hdry;
+        const T sLe = dL ? T(0) : minmod(se[cl] - se[cm], se[cr] - se[cl]);
+        const T sRh = minmod(sh[cr] - sh[cl], sh[cp] - sh[cr]);
+        const T sRu = minmod(uR - uL, unp - uR);
+        const T sRt = minmod(tR - tL, utp - tR);
+        const bool dR = sh[cl] <= hdry || sh[cr] <= hdry || sh[cp] <= hdry;
+        const T sRe = dR ? T(0) : minmod(se[cr] - se[cl], se[cp] - se[cr]);
+        const T hL = sh[cl] + T(0.5) * sLh, eL = se[cl] + T(0.5) * sLe;
+        const T nL = uL + T(0.5) * sLu, tLv = tL + T(0.5) * sLt;
+        const T hR = sh[cr] - T(0.5) * sRh, eR = se[cr] - T(0.5) * sRe;
+        const T nR = uR - T(0.5) * sRu, tRv = tR - T(0.5) * sRt;
+        T Dm[3], Dp[3];
+        pvm(g, hdry, hL, eL, nL, tLv, hR, eR, nR, tRv, Dm, Dp);
+        const T qL = hL * nL, qR = hR * nR;
+        T* oL0 = xf ? &CLx[0][tt] : &CLy[0][tt];
+        T* oR0 = xf ? &CRx[0][tt] : &CRy[0][tt];
+        const int stride = xf ? NFX : NFY;
+        oL0[0] = Dm[0] + qL;
+        oL0[stride] = Dm[1] + qL * nL + g * sh[cl] * eL;
+        oL0[2 * stride] = Dm[2] + qL * tLv;
+        oR0[0] = Dp[0] - qR;
+        oR0[stride] = Dp[1] - (qR * nR + g * sh[cr] * eR);
+        oR0[2 * stride] = Dp[2] - qR * tRv;
+    }
+    __syncthreads();
+    int nclamp = 0;
+    for (int t = tid; t < TX * TY; t += nt) {
+        const int li = t % TX, lj = t / TX;
+        const int gi = i0 + li, gj = j0 + lj;
+        if (gi >= P.nx || gj >= P.ny) continue;
+        const int fe = lj * (TX + 1) + li + 1, fw = fe - 1;     // x faces east / west
+        const int fn = (lj + 1) * TX + li, fs = lj * TX + li;   // y faces north / south
+        const size_t c = (size_t)gj * P.nx + gi;
+        const T Hc = H[c];
+        const T rx = dt / P.dx, ry = dt / P.dy;
+        T en = eta[c] - rx * (CLx[0][fe] + CRx[0][fw]) - ry * (CLy[0][fn] + CRy[0][fs]);
+        T an = q1[c] - rx * (CLx[1][fe] + CRx[1][fw]) - ry * (CLy[2][fn] + CRy[2][fs]);
+        T bn = q2[c] - rx * (CLx[2][fe] + CRx[2][fw]) - ry * (CLy[1][fn] + CRy[1][fs]);
+        T hn = en + Hc;
+        if (P.manning > T(0) && hn > T(0)) {
+            T u = desing(hn, an, d4), v = desing(hn, bn, d4);
+            T hd = tmax(hn, P.delta);
+            T fr = T(1) + dt * g * P.manning * P.manning * sqrt(u * u + v * v) / (hd * cbrt(hd));
+            an /= fr;
+            bn /= fr;
+        }
+        if (hn < T(0)) { en = -Hc; an = T(0); bn = T(0); ++nclamp; }
+        if (a != T(0)) {
+            en = a * etab[c] + b * en;
+            an = a * q1b[c] + b * an;
+            bn = a * q2b[c] + b * bn;
+        }
+        eo[c] = en; q1o[c] = an; q2o[c] = bn;
+    }
+    if (nclamp) atomicAdd(&st->clamped, nclamp);
+}
+
 // Breaking terms at cells (Sec. 3 with q_x -> div q, u_x -> div u):
 // q += de 2 nu (div u) grad H, centred differences.
 template <typename T>
@@ -514,6 +622,172 @@ k_asm2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
     }
 }
 
+// Tiled form of the assembly for a TX x TY node tile: the block stages s = eta - H and h of
+// the cells around the tile (a 2-cell ring), computes the centred differences X, Y of every
+// cell once, stages the discharges of the cells touching the tile's nodes, and then builds
+// each node's row, right-hand side (or defect) and w* from shared memory.  Same arithmetic
+// as k_asm2d per node.
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(256)
+k_asm2d_t(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
+          const T* __restrict__ q1k, const T* __restrict__ q2k, const T* __restrict__ q1s,
+          const T* __restrict__ q2s, const T* __restrict__ w_in, const T* __restrict__ w_b,
+          T a, T b, T de, int with_coef, T* __restrict__ ws, T* __restrict__ cC,
+          T* __restrict__ cW, T* __restrict__ cE, T* __restrict__ cS, T* __restrict__ cN,
+          T* __restrict__ rhs, const T* __restrict__ p0, int resid_form, double* partials,
+          SolveCtl* ctl, double tol2, int max_iter, int kpass)
+{
+    // staged cells: columns I0-2 .. I0+TX, rows J0-2 .. J0+TY  (SW x SH)
+    constexpr int SW = TX + 3, SH = TY + 3, SN = SW * SH;
+    // core cells (touching the tile's nodes): columns I0-1 .. I0+TX-1, rows J0-1 .. J0+TY-1
+    constexpr int CW = TX + 1, CHh = TY + 1, CN = CW * CHh;
+    __shared__ T ss[SN], hs[SN];
+    __shared__ T Xc[CN], Yc[CN], Q1c[CN], Q2c[CN], U1c[CN], V1c[CN], P1c[CN], P2c[CN];
+    const T d2 = P.delta * P.delta, d4 = d2 * d2;
+    const int nxn = P.nx + 1;
+    const int I0 = blockIdx.x * TX, J0 = blockIdx.y * TY;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int t = tid; t < SN; t += nt) {
+        const int li = t % SW, lj = t / SW;
+        int ci = I0 - 2 + li, cj = J0 - 2 + lj;
+        ci = ci > P.nx + 1 ? P.nx + 1 : ci;
+        cj = cj > P.ny + 1 ? P.ny + 1 : cj;
+        bool rx, ry;
+        const int ii = map_cell(ci, P.nx, P.bcw, P.bce, rx);
+        const int jj = map_cell(cj, P.ny, P.bcs, P.bcn, ry);
+        const size_t m = (size_t)jj * P.nx + ii;
+        const T e = eta[m], Hm = H[m];
+        ss[t] = e - Hm;
+        hs[t] = tmax(e + Hm, T(0));
+    }
+    for (int t = tid; t < CN; t += nt) {
+        const int li = t % CW, lj = t / CW;
+        int ci = I0 - 1 + li, cj = J0 - 1 + lj;
+        ci = ci > P.nx + 1 ? P.nx + 1 : ci;
+        cj = cj > P.ny + 1 ? P.ny + 1 : cj;
+        bool rx, ry;
+        const int ii = map_cell(ci, P.nx, P.bcw, P.bce, rx);
+        const int jj = map_cell(cj, P.ny, P.bcs, P.bcn, ry);
+        const size_t m = (size_t)jj * P.nx + ii;
+        Q1c[t] = rx ? -q1k[m] : q1k[m];
+        Q2c[t] = ry ? -q2k[m] : q2k[m];
+        if (P.breaking) {
+            P1c[t] = rx ? -q1s[m] : q1s[m];
+            P2c[t] = ry ? -q2s[m] : q2s[m];
+        }
+    }
+    __syncthreads();
+    for (int t = tid; t < CN; t += nt) {
+        const int li = t % CW, lj = t / CW;
+        const int sidx = (lj + 1) * SW + (li + 1);   // staged index of this core cell
+        Xc[t] = T(0.5) * (ss[sidx + 1] - ss[sidx - 1]);
+        Yc[t] = T(0.5) * (ss[sidx + SW] - ss[sidx - SW]);
+        if (P.breaking) {
+            U1c[t] = desing(hs[sidx], P1c[t], d4);
+            V1c[t] = desing(hs[sidx], P2c[t], d4);
+        }
+    }
+    __syncthreads();
+    const T inv2dx = T(1) / (T(2) * P.dx), inv2dy = T(1) / (T(2) * P.dy);
+    const T scale = T(8) * P.dx * P.dy / de;
+    const T rxl = P.dy / P.dx, ryl = P.dx / P.dy;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int t = tid; t < TX * TY; t += nt) {
+        const int li = t % TX, lj = t / TX;
+        const int I = I0 + li, J = J0 + lj;
+        if (I > P.nx || J > P.ny) continue;
+        // core-local indices of cells a (I-1,J-1), b (I,J-1), d (I-1,J), e (I,J)
+        const int ka = lj * CW + li, kb = ka + 1, kd = ka + CW, ke = kd + 1;
+        const int sa = (lj + 1) * SW + (li + 1), sb = sa + 1, sd = sa + SW, se = sd + 1;
+        const T ha = hs[sa], hb = hs[sb], hd = hs[sd], he = hs[se];
+        const T hc = T(0.25) * (ha + hb + hd + he);
+        const T Xi = T(0.5) * (ss[se] + ss[sb]) - T(0.5) * (ss[sd] + ss[sa]);
+        const T Yi = T(0.5) * (ss[sd] + ss[se]) - T(0.5) * (ss[sa] + ss[sb]);
+        const size_t nidx = (size_t)J * nxn + I;
+        T wv = a != T(0) ? a * w_b[nidx] + b * w_in[nidx] : w_in[nidx];
+        if (P.breaking) {
+            T dq = (P1c[kb] + P1c[ke] - P1c[ka] - P1c[kd]) * inv2dx
+                 + (P2c[kd] + P2c[ke] - P2c[ka] - P2c[kb]) * inv2dy;
+            T du = (U1c[kb] + U1c[ke] - U1c[ka] - U1c[kd]) * inv2dx
+                 + (V1c[kd] + V1c[ke] - V1c[ka] - V1c[kb]) * inv2dy;
+            T nu = nu_break(hc, dq, P.g, P.B1, P.hdry);
+            wv += de * T(2) * nu * du * desing(hc, T(1), d4);
+        }
+        ws[nidx] = wv;
+        const T q1E = T(0.5) * (Q1c[ke] + Q1c[kb]), q1W = T(0.5) * (Q1c[kd] + Q1c[ka]);
+        const T q2N = T(0.5) * (Q2c[ke] + Q2c[kd]), q2S = T(0.5) * (Q2c[kb] + Q2c[ka]);
+        const T Bs = ((T(2) * hc - Xi) * q1E - (T(2) * hc + Xi) * q1W) * inv2dx
+                   + ((T(2) * hc - Yi) * q2N - (T(2) * hc + Yi) * q2S) * inv2dy
+                   + T(2) * hc * wv;
+        const T bval = -scale * Bs;
+        acc[0] += (double)bval * (double)bval;
+        if (with_coef) {
+            const T Xa = Xc[ka], Xb = Xc[kb], Xd = Xc[kd], Xe = Xc[ke];
+            const T Ya = Yc[ka], Yb = Yc[kb], Yd = Yc[kd], Ye = Yc[ke];
+            const T apE = (hb + he) + T(0.5) * (Xb + Xe), amE = T(0.5) * (Xb + Xe) - (hb + he);
+            const T apW = (ha + hd) + T(0.5) * (Xa + Xd), amW = T(0.5) * (Xa + Xd) - (ha + hd);
+            const T apN = (hd + he) + T(0.5) * (Yd + Ye), amN = T(0.5) * (Yd + Ye) - (hd + he);
+            const T apS = (ha + hb) + T(0.5) * (Ya + Yb), amS = T(0.5) * (Ya + Yb) - (ha + hb);
+            const T bmx = Xi - T(2) * hc, bpx = Xi + T(2) * hc;
+            const T bmy = Yi - T(2) * hc, bpy = Yi + T(2) * hc;
+            const T vE = rxl * bmx * apE, vW = rxl * bpx * amW;
+            const T vN = ryl * bmy * apN, vS = ryl * bpy * amS;
+            const T dC = T(16) * P.dx * P.dy + rxl * (bmx * amE + bpx * apW)
+                       + ryl * (bmy * amN + bpy * apS);
+            cE[nidx] = vE; cW[nidx] = vW; cN[nidx] = vN; cS[nidx] = vS; cC[nidx] = dC;
+            const T id = T(1) / fabs(dC);
+            const T bs = bval * id;
+            acc[1] += (double)bs * (double)bs;
+            acc[2] = fmax(acc[2], (double)((fabs(vE) + fabs(vW) + fabs(vN) + fabs(vS)) * id));
+            if (resid_form) {
+                const int Iw = map_node(I - 1, P.nx), Ie = map_node(I + 1, P.nx);
+                const int Js = map_node(J - 1, P.ny), Jn = map_node(J + 1, P.ny);
+                T mp = dC * p0[nidx];
+                mp = fma(vW, p0[(size_t)J * nxn + Iw], mp);
+                mp = fma(vE, p0[(size_t)J * nxn + Ie], mp);
+                mp = fma(vS, p0[(size_t)Js * nxn + I], mp);
+                mp = fma(vN, p0[(size_t)Jn * nxn + I], mp);
+                rhs[nidx] = bval - mp;
+            } else {
+                rhs[nidx] = bval;
+            }
+        } else {
+            rhs[nidx] = bval;
+        }
+    }
+    if (grid_reduce<3, 4u>(acc, partials, &ctl->counter) && tid == 0) {
+        ctl->bb = acc[0];
+        ctl->bdb = acc[1];
+        ctl->gersh = acc[2];
+        ctl->tol2 = tol2;
+        ctl->max_iter = max_iter;
+        ctl->iter = 0;
+        ctl->sweeps = 0;
+        ctl->done = 0;
+        ctl->status = 0;
+        if (with_coef && kpass > 0) {
+            if (!(acc[2] < 1.0)) {
+                ctl->status = 4;
+                ctl->done = 1;
+            } else {
+                const double dl = acc[2] > 1e-12 ? acc[2] : 1e-12;
+                ctl->delta = dl;
+                ctl->sigma1 = 1.0 / dl;
+                double rp = dl;
+                ctl->c1[0] = 0.0;
+                ctl->c2[0] = 1.0;
+                for (int k = 1; k < kpass; ++k) {
+                    const double rn = 1.0 / (2.0 * ctl->sigma1 - rp);
+                    ctl->c1[k] = rn * rp;
+                    ctl->c2[k] = 2.0 * rn / dl;
+                    rp = rn;
+                }
+                ctl->rho_prev = rp;
+            }
+        }
+    }
+}
+
 // (M x) at node (I, J) from the stored row and mirrored neighbours.
 template <typename T>
 struct Rows {
@@ -678,19 +952,19 @@ k_bicg_C(Rows<T> R, T* __restrict__ r, const T* __restrict__ rh, const T* __rest
 // writes the tile back.  Sweep k: x_{k+1} = x_k + c1 (x_k - x_{k-1}) + c2 r_k with
 // r_k = D^-1 (b - M x_k).  The last sweep accumulates ||r||^2 (Jacobi-scaled) and
 // max |x_{k+1} - x_k|; the last block tests convergence and prepares the next K weights.
-// A (32, 8) thread block owns a fixed set of region
+// A (32, BY) thread block owns a fixed set of region
 // nodes per thread (columns tx + 32 a, rows ty + 8 b), so the sweep loop has no index
 // arithmetic beyond constant offsets.  The region is the tile plus a K-node halo on every
 // side; outside the domain the halo holds mirror images (values, and coefficients with
 // W <-> E or S <-> N swapped), which evolve exactly as the nodes they mirror, so tiles at
 // the boundary are no different from interior ones.  x_{k-1} lives in registers.
-template <typename T, int NA, int NB, int K>
-__global__ void __launch_bounds__(256, 2)
+template <typename T, int NA, int NB, int BY, int K>
+__global__ void __launch_bounds__(32 * BY, 2)
 k_cheb_pass2(Rows<T> R, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ xp,
              double* partials, SolveCtl* ctl)
 {
     if (ctl->done) return;
-    constexpr int RW = 32 * NA, RH = 8 * NB, RN = RW * RH;
+    constexpr int RW = 32 * NA, RH = BY * NB, RN = RW * RH;
     constexpr int TX = RW - 2 * K, TY = RH - 2 * K;
     extern __shared__ unsigned char cheb2_smem[];
     T* xs0 = reinterpret_cast<T*>(cheb2_smem);
@@ -708,7 +982,7 @@ k_cheb_pass2(Rows<T> R, const T* __restrict__ b, T* __restrict__ x, T* __restric
     for (int bb = 0; bb < NB; ++bb)
 #pragma unroll
         for (int aa = 0; aa < NA; ++aa) {
-            const int li = tx + 32 * aa, lj = ty + 8 * bb;
+            const int li = tx + 32 * aa, lj = ty + BY * bb;
             const int gI = I0 + li, gJ = J0 + lj;
             int mI = gI < 0 ? -gI : (gI > nx ? 2 * nx - gI : gI);
             int mJ = gJ < 0 ? -gJ : (gJ > ny ? 2 * ny - gJ : gJ);
@@ -734,7 +1008,7 @@ k_cheb_pass2(Rows<T> R, const T* __restrict__ b, T* __restrict__ x, T* __restric
     __syncthreads();
     T* cur = xs0;
     T* nxt = xs1;
-    double acc[2] = {0.0, 0.0};
+    T rsum = T(0), dmax = T(0);   // per-thread (few terms): native precision is enough
 #pragma unroll
     for (int sw = 0; sw < K; ++sw) {
         const T c1 = c1s[sw], c2 = c2s[sw];
@@ -742,7 +1016,7 @@ k_cheb_pass2(Rows<T> R, const T* __restrict__ b, T* __restrict__ x, T* __restric
         for (int bb = 0; bb < NB; ++bb)
 #pragma unroll
             for (int aa = 0; aa < NA; ++aa) {
-                const int li = tx + 32 * aa, lj = ty + 8 * bb;
+                const int li = tx + 32 * aa, lj = ty + BY * bb;
                 if (li > sw && li < RW - 1 - sw && lj > sw && lj < RH - 1 - sw) {
                     const int sidx = lj * RW + li;
                     const T xc = cur[sidx];
@@ -754,8 +1028,8 @@ k_cheb_pass2(Rows<T> R, const T* __restrict__ b, T* __restrict__ x, T* __restric
                     xa[bb * NA + aa] = xc;
                     if (sw == K - 1 && li >= K && li < RW - K && lj >= K && lj < RH - K &&
                         I0 + li <= nx && J0 + lj <= ny) {
-                        acc[0] += (double)r * (double)r;
-                        acc[1] = fmax(acc[1], fabs((double)(xn - xc)));
+                        rsum = fma(r, r, rsum);
+                        dmax = tmax(dmax, T(fabs(xn - xc)));
                     }
                 }
             }
@@ -766,7 +1040,7 @@ k_cheb_pass2(Rows<T> R, const T* __restrict__ b, T* __restrict__ x, T* __restric
     for (int bb = 0; bb < NB; ++bb)
 #pragma unroll
         for (int aa = 0; aa < NA; ++aa) {
-            const int li = tx + 32 * aa, lj = ty + 8 * bb;
+            const int li = tx + 32 * aa, lj = ty + BY * bb;
             const int gI = I0 + li, gJ = J0 + lj;
             if (li >= K && li < RW - K && lj >= K && lj < RH - K && gI <= nx && gJ <= ny) {
                 const size_t g = (size_t)gJ * NX + gI;
@@ -774,6 +1048,7 @@ k_cheb_pass2(Rows<T> R, const T* __restrict__ b, T* __restrict__ x, T* __restric
                 xp[g] = xa[bb * NA + aa];
             }
         }
+    double acc[2] = {(double)rsum, (double)dmax};
     if (grid_reduce<2, 2u>(acc, partials, &ctl->counter) && tx == 0 && ty == 0) {
         ctl->rr = acc[0];
         ctl->dpmax = acc[1];
@@ -1232,8 +1507,10 @@ void launch_hyp2d(const Prm<T>& P, const Launch& L, const T* eta, const T* q1, c
                   const T* etab, const T* q1b, const T* q2b, const T* H, T a, T b, T dt,
                   T* eo, T* q1o, T* q2o, StepCtl* st)
 {
-    k_hyp2d<T><<<L.nblk, kThreads, 0, L.s>>>(P, eta, q1, q2, etab, q1b, q2b, H, a, b, dt, eo,
-                                             q1o, q2o, st);
+    constexpr int TX = 32, TY = sizeof(T) == 4 ? 16 : 8;
+    dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
+    k_hyp2d_t<T, TX, TY><<<grid, kThreads, 0, L.s>>>(P, eta, q1, q2, etab, q1b, q2b, H, a, b, dt,
+                                                    eo, q1o, q2o, st);
 }
 
 template <typename T>
@@ -1248,24 +1525,34 @@ void launch_asm2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* w
                   const T* w_base, T a, T b, T de, int with_coef, int resid_form, double tol2,
                   int max_iter, int kpass, double* partials, SolveCtl* ctl)
 {
-    k_asm2d<T><<<L.nblk, kThreads, 0, L.s>>>(P, B.etas, B.H, B.q1k, B.q2k, B.q1s, B.q2s, w_in,
-                                             w_base, a, b, de, with_coef, B.ws, B.cC, B.cW,
-                                             B.cE, B.cS, B.cN, B.rhs, B.p, resid_form, partials,
-                                             ctl, tol2, max_iter, kpass);
+    constexpr int TX = 32, TY = 16;
+    dim3 grid((P.nx + 1 + TX - 1) / TX, (P.ny + 1 + TY - 1) / TY);
+    k_asm2d_t<T, TX, TY><<<grid, kThreads, 0, L.s>>>(P, B.etas, B.H, B.q1k, B.q2k, B.q1s, B.q2s,
+                                                    w_in, w_base, a, b, de, with_coef, B.ws,
+                                                    B.cC, B.cW, B.cE, B.cS, B.cN, B.rhs, B.p,
+                                                    resid_form, partials, ctl, tol2, max_iter,
+                                                    kpass);
 }
 
 template <typename T> struct ChebCfg;
-template <> struct ChebCfg<float> { static constexpr int NA = 4, NB = 4, K = 4; };
-template <> struct ChebCfg<double> { static constexpr int NA = 2, NB = 4, K = 4; };
+// region 128 x 32 nodes (FP32) / 64 x 32 (FP64), 512 threads, 8 nodes per thread, 4 sweeps
+template <> struct ChebCfg<float> { static constexpr int NA = 4, NB = 2, BY = 16, K = 4; };
+template <> struct ChebCfg<double> { static constexpr int NA = 2, NB = 2, BY = 16, K = 4; };
 
 template <typename T>
 int cheb_sweeps_per_pass() { return ChebCfg<T>::K; }
 
 template <typename T>
+size_t asm_tiles(const Prm<T>& P)
+{
+    return (size_t)((P.nx + 1 + 31) / 32) * ((P.ny + 1 + 15) / 16);
+}
+
+template <typename T>
 size_t cheb_tiles(const Prm<T>& P)
 {
     using C = ChebCfg<T>;
-    constexpr int TX = 32 * C::NA - 2 * C::K, TY = 8 * C::NB - 2 * C::K;
+    constexpr int TX = 32 * C::NA - 2 * C::K, TY = C::BY * C::NB - 2 * C::K;
     return (size_t)((P.nx + 1 + TX - 1) / TX) * ((P.ny + 1 + TY - 1) / TY);
 }
 
@@ -1274,20 +1561,19 @@ int launch_cheb_pass(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, T* xprev
                      double* partials)
 {
     using C = ChebCfg<T>;
-    constexpr int TX = 32 * C::NA - 2 * C::K, TY = 8 * C::NB - 2 * C::K;
-    constexpr size_t smem = 7 * (size_t)(32 * C::NA) * (8 * C::NB) * sizeof(T);
+    constexpr int TX = 32 * C::NA - 2 * C::K, TY = C::BY * C::NB - 2 * C::K;
+    constexpr size_t smem = 7 * (size_t)(32 * C::NA) * (C::BY * C::NB) * sizeof(T);
     static bool attr_set = false;
     if (!attr_set) {
-        if (cudaFuncSetAttribute(k_cheb_pass2<T, C::NA, C::NB, C::K>,
+        if (cudaFuncSetAttribute(k_cheb_pass2<T, C::NA, C::NB, C::BY, C::K>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return -1;
         attr_set = true;
     }
     dim3 grid((P.nx + 1 + TX - 1) / TX, (P.ny + 1 + TY - 1) / TY);
-    k_cheb_pass2<T, C::NA, C::NB, C::K><<<grid, dim3(32, 8), smem, s>>>(rows_of(P, B), B.rhs,
-                                                                        B.dp, xprev, partials,
-                                                                        B.sctl);
+    k_cheb_pass2<T, C::NA, C::NB, C::BY, C::K><<<grid, dim3(32, C::BY), smem, s>>>(
+        rows_of(P, B), B.rhs, B.dp, xprev, partials, B.sctl);
     return 0;
 }
 
@@ -1464,6 +1750,7 @@ void launch_convert_from_double(const Launch& L, const double* src, T* dst, size
                                   SolveCtl*);                                                  \
     template int cheb_sweeps_per_pass<T>();                                                    \
     template size_t cheb_tiles<T>(const Prm<T>&);                                              \
+    template size_t asm_tiles<T>(const Prm<T>&);                                               \
     template int launch_cheb_pass<T>(const Prm<T>&, cudaStream_t, const Bufs<T>&, T*, double*);\
     template void launch_matvec2d<T>(const Prm<T>&, const Launch&, const Bufs<T>&, const T*,   \
                                      T*);                                                      \
