@@ -41,6 +41,7 @@ struct SolveCtl {
     double eps_dp;    // > 0: stop when dpmax < eps_dp (criterion (32)); else residual test
     int sweeps;       // sweeps done in this solve
     int pad2;
+    float c1f[8], c2f[8]; // FP32 copies of c1, c2 for FP32 sweeps
 };
 
 // Device-side per-step scalars.

@@ -221,6 +221,54 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[NV], double* partials,
     return true;
 }
 
+// Block partial of (sum, max) in FP32 (a few thousand terms per block), written as FP64
+// partials; the last block finishes in FP64 like grid_reduce.
+__device__ __forceinline__ bool grid_reduce_sum_max_f(float s, float m, double* partials,
+                                                      unsigned* counter, double out[2])
+{
+    __shared__ float fs[32], fm[32];
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int lane = tid & 31, wid = tid >> 5, nw = (blockDim.x * blockDim.y + 31) >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    if (lane == 0) { fs[wid] = s; fm[wid] = m; }
+    __syncthreads();
+    double v[2] = {0.0, 0.0};
+    if (wid == 0) {
+        float a = lane < nw ? fs[lane] : 0.f, b = lane < nw ? fm[lane] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, o));
+        }
+        v[0] = a; v[1] = b;
+    }
+    const unsigned nblocks = gridDim.x * gridDim.y;
+    const unsigned bid = blockIdx.y * gridDim.x + blockIdx.x;
+    const unsigned nthr = blockDim.x * blockDim.y;
+    __shared__ bool last;
+    if (tid == 0) {
+        partials[(size_t)bid * 2] = v[0];
+        partials[(size_t)bid * 2 + 1] = v[1];
+        __threadfence();
+        last = atomicAdd(counter, 1u) == nblocks - 1;
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double acc[2] = {0.0, 0.0};
+    for (unsigned bb = tid; bb < nblocks; bb += nthr) {
+        acc[0] += __ldcg(partials + (size_t)bb * 2);
+        acc[1] = fmax(acc[1], __ldcg(partials + (size_t)bb * 2 + 1));
+    }
+    block_reduce<2, 2u>(acc);
+    out[0] = acc[0];
+    out[1] = acc[1];
+    if (tid == 0) *counter = 0u;
+    return true;
+}
+
 #define GRID_STRIDE(idx, n) \
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < (long long)(n); \
          idx += (long long)gridDim.x * blockDim.x)
@@ -616,6 +664,10 @@ k_asm2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
                     ctl->c2[k] = 2.0 * rn / dl;
                     rp = rn;
                 }
+                for (int k = 0; k < kpass; ++k) {
+                    ctl->c1f[k] = (float)ctl->c1[k];
+                    ctl->c2f[k] = (float)ctl->c2[k];
+                }
                 ctl->rho_prev = rp;
             }
         }
@@ -781,6 +833,10 @@ k_asm2d_t(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
                     ctl->c1[k] = rn * rp;
                     ctl->c2[k] = 2.0 * rn / dl;
                     rp = rn;
+                }
+                for (int k = 0; k < kpass; ++k) {
+                    ctl->c1f[k] = (float)ctl->c1[k];
+                    ctl->c2f[k] = (float)ctl->c2[k];
                 }
                 ctl->rho_prev = rp;
             }
@@ -1004,7 +1060,10 @@ k_cheb_pass2(Rows<T> R, const T* __restrict__ b, T* __restrict__ x, T* __restric
         }
     T c1s[K], c2s[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) { c1s[k] = (T)ctl->c1[k]; c2s[k] = (T)ctl->c2[k]; }
+    for (int k = 0; k < K; ++k) {
+        if (sizeof(T) == 4) { c1s[k] = (T)ctl->c1f[k]; c2s[k] = (T)ctl->c2f[k]; }
+        else { c1s[k] = (T)ctl->c1[k]; c2s[k] = (T)ctl->c2[k]; }
+    }
     __syncthreads();
     T* cur = xs0;
     T* nxt = xs1;
@@ -1048,8 +1107,9 @@ k_cheb_pass2(Rows<T> R, const T* __restrict__ b, T* __restrict__ x, T* __restric
                 xp[g] = xa[bb * NA + aa];
             }
         }
-    double acc[2] = {(double)rsum, (double)dmax};
-    if (grid_reduce<2, 2u>(acc, partials, &ctl->counter) && tx == 0 && ty == 0) {
+    double acc[2];
+    if (grid_reduce_sum_max_f((float)rsum, (float)dmax, partials, &ctl->counter, acc) &&
+        tx == 0 && ty == 0) {
         ctl->rr = acc[0];
         ctl->dpmax = acc[1];
         ctl->sweeps += K;
@@ -1064,6 +1124,8 @@ k_cheb_pass2(Rows<T> R, const T* __restrict__ b, T* __restrict__ x, T* __restric
             const double rn = 1.0 / (2.0 * ctl->sigma1 - rp);
             ctl->c1[k] = rn * rp;
             ctl->c2[k] = 2.0 * rn / ctl->delta;
+            ctl->c1f[k] = (float)ctl->c1[k];
+            ctl->c2f[k] = (float)ctl->c2[k];
             rp = rn;
         }
         ctl->rho_prev = rp;
