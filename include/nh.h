@@ -198,6 +198,80 @@ int nh_tridiag_batched(int n, int rows, int precision, const void *a, const void
 int nh_tridiag_batched_noalloc(int n, int rows, int precision, const void *a, const void *b,
                                const void *c, const void *d, void *x, void *stream);
 
+/* ---- ensembles: many independent 2D domains of uneven sizes advanced together ----
+ *
+ * Every domain takes the same step as a single 2D handle (Sec. 5 / App. A scheme, the
+ * Chebyshev-scheduled Jacobi solve of NH_SOLVER_CHEBYSHEV), with its own grid, boundary
+ * conditions, state, time step and solver convergence; the parameters (nh_params) are
+ * shared.  Each kernel class runs as ONE launch for the whole ensemble over a work list of
+ * (domain, tile) items, largest domain first; a domain whose pressure solve has converged
+ * leaves the remaining Chebyshev passes of that stage.  The paper runs one domain at a
+ * time and has no counterpart of this form.
+ *
+ * Layout and precision of per-domain arrays are those of nh_set_state / nh_get_state for
+ * that domain's grid.  All work runs on `stream` (0: the batch creates its own non-blocking
+ * stream); every call below that returns data synchronises it. */
+typedef struct nh_batch nh_batch;
+
+enum {
+    NH_BATCH_AUTOTUNE = 1,  /* time the kernel-shape candidates on the ensemble's own state
+                               before the first step and keep the fastest               */
+    NH_BATCH_GRAPH = 2      /* run each step as one CUDA graph whose solver loops are
+                               device-side conditional WHILE nodes (no host round trip) */
+};
+
+/* Kernel shapes and launch forms of a batch (candidate indices: nh_batch_candidate). */
+typedef struct {
+    int hyp;          /* hyperbolic-kernel cell tile                                     */
+    int assembly;     /* assembly node tile                                              */
+    int cheb;         /* Chebyshev-pass node region                                      */
+    int persistent;   /* bit k set: kernel class k (0 hyperbolic, 1 assembly, 2 Chebyshev,
+                         3 correction and breaking) runs as a persistent grid of the
+                         blocks resident at once looping over the work list; clear: one
+                         block per work item                                              */
+    int graph;        /* 1: steps run as a CUDA graph (NH_BATCH_GRAPH)                   */
+    int tuned;        /* 1: chosen by the autotuner                                      */
+    double ms[3];     /* autotuner's time of the chosen hyperbolic launch, assembly launch
+                         and Chebyshev pass (ms, whole ensemble)                          */
+} nh_batch_tuning;
+
+/* Create a batch of n domains.  grids[d]: dim 2, nx, ny >= 2; H[d]: still-water depth of
+ * domain d ([ny][nx] doubles, host memory).  params->solver must be NH_SOLVER_CHEBYSHEV
+ * when nonhydrostatic is on.  Domains start at rest (eta = max(0, H) - H).  flags: OR of
+ * NH_BATCH_*.  Returns NH_OK, NH_EINVAL, NH_ENOMEM or NH_ECUDA. */
+int nh_create_batch(int n, const nh_grid *grids, const double *const *H,
+                    const nh_params *params, void *stream, int flags, nh_batch **out);
+
+/* Set / read the state of domain d (as nh_set_state / nh_get_state). */
+int nh_batch_set_state(nh_batch *b, int d, const void *eta, const void *q1, const void *q2,
+                       const void *w, const void *p, double t, int where);
+int nh_batch_get_state(nh_batch *b, int d, void *eta, void *q1, void *q2, void *w, void *p,
+                       double *t, int where);
+
+/* Advance every domain by nsteps steps, each of its own Eq. (23) step (params->fixed_dt
+ * when > 0).  Returns NH_ENOCONV when a solve stopped at the iteration cap, broke down or
+ * met a system that is not diagonally dominant (the domain's p then keeps its previous
+ * value for that stage), NH_ENONFINITE on a non-finite state.  A solve that stops
+ * improving before tol (the rounding floor of FP32) ends there and is not an error; its
+ * residual is in nh_batch_stats' last_resid. */
+int nh_batch_run(nh_batch *b, int nsteps);
+
+/* Counters, time step and FP64 mass of domain d. */
+int nh_batch_stats(nh_batch *b, int d, nh_stats_t *out);
+
+/* Current kernel choice; set one by hand (disables the autotuner for this batch). */
+int nh_batch_get_tuning(nh_batch *b, nh_batch_tuning *out);
+int nh_batch_set_tuning(nh_batch *b, const nh_batch_tuning *in);
+
+/* Candidate idx of kernel class kind (0 hyperbolic cell tile, 1 assembly node tile,
+ * 2 Chebyshev node region incl. its 4-node halo) for a precision; NH_EINVAL past the
+ * last one. */
+int nh_batch_candidate(int precision, int kind, int idx, int *tile_x, int *tile_y,
+                       int *threads);
+
+const char *nh_batch_last_error(const nh_batch *b);
+void nh_batch_destroy(nh_batch *b);
+
 /* ---- kernel-level entry points used to check the stages one by one ---- */
 
 /* Hyperbolic update of the current state alone (Eqs. 18-22 / 30, friction, clamp):

@@ -1,0 +1,1540 @@
+// nh_batch.cu -- ensembles of independent 2D domains of uneven sizes, advanced together.
+//
+// Every domain runs the same step as a single handle (the tile and element bodies of
+// nh_device.cuh, Chebyshev-scheduled Jacobi for the pressure), but each kernel class is
+// ONE launch for all domains: its blocks walk a work list of (domain, tile) items, sorted
+// largest domain first, either one block per item or a persistent grid of the blocks that
+// fit on the GPU at once.  Per domain the device keeps its own time step (Eq. 23 from its
+// own state, or a fixed step), its own solver control block and convergence, and its own
+// reductions (a last-block-done finish per domain).  A domain whose solve has converged
+// drops out of the remaining Chebyshev passes of that stage; the pass loop ends when no
+// domain is left.  With the graph option one whole step (two stages) is a CUDA graph whose
+// solver loops are device-side conditional WHILE nodes, so a run of n steps is n graph
+// launches and no host round trip.  Tile shapes and grid forms are chosen by a small
+// autotuner that times the candidates on the ensemble's own state before the first step.
+#include "../../include/nh.h"
+#include "nh_device.cuh"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <utility>
+#include <vector>
+
+namespace nh {
+namespace {
+
+using namespace dev;
+
+constexpr int kChunk = 2048;   // cells / nodes per element work item (8 per thread)
+
+template <typename T>
+struct Dom {
+    Prm<T> P;
+    long long coff, noff;   // first cell / node of the domain in the arenas
+    long long poff;         // first partial (doubles) of the domain
+    int ncc, nnc;           // element work items: cell chunks, node chunks
+};
+
+// Per-domain bookkeeping kept on the device.
+struct DomState {
+    double t, dt, lam, mass;
+    long long steps, sweeps;
+    double last_resid[2];
+    int last_sweeps[2];
+    int last_status[2];   // 1 converged, 2 cap, 3 breakdown, 4 not diagonally dominant, 5 stalled
+    int nonconv;          // solves that ended without converging (cap or breakdown)
+    int fallbacks;        // solves finished by BiCGStab (Chebyshev stalled: status 5, or
+                          // the system was not diagonally dominant: status 4)
+    int clamped, nonfinite;
+};
+
+template <typename T>
+struct Arena {
+    const Dom<T>* dom;
+    SolveCtl* sctl;
+    StepCtl* stctl;
+    DomState* ds;
+    double* partials;
+    unsigned* loop;        // [0] domains in Chebyshev passes, [1] passes launched this stage,
+                           // [2] domains in the BiCGStab fallback, [3] its iterations
+    double fixed_dt, cfl;
+};
+
+__host__ __device__ inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+// ---------------------------------------------------------------- kernels
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+kb_lambda(Arena<T> A, const int2* __restrict__ wl, int nw, const T* __restrict__ eta,
+          const T* __restrict__ q1, const T* __restrict__ q2, const T* __restrict__ H)
+{
+    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+        const int2 it = wl[w];
+        const Dom<T>& D = A.dom[it.x];
+        const Prm<T> P = D.P;
+        const long long c = D.coff, n = (long long)P.nx * P.ny;
+        double acc[1] = {0.0};
+        for (long long k = (long long)it.y * kChunk + threadIdx.x;
+             k < n && k < (long long)(it.y + 1) * kChunk; k += blockDim.x)
+            acc[0] = fmax(acc[0], lambda_cell(P, 2, eta + c, q1 + c, q2 + c, H + c, k));
+        if (dom_reduce<1, 1u>(acc, A.partials + D.poff, &A.stctl[it.x].counter, it.y, D.ncc) &&
+            threadIdx.x == 0) {
+            DomState& s = A.ds[it.x];
+            s.lam = acc[0];
+            s.dt = A.fixed_dt > 0.0 ? A.fixed_dt : (acc[0] > 0.0 ? A.cfl / acc[0] : 0.0);
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+kb_mass(Arena<T> A, const int2* __restrict__ wl, int nw, const T* __restrict__ eta,
+        const T* __restrict__ H)
+{
+    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+        const int2 it = wl[w];
+        const Dom<T>& D = A.dom[it.x];
+        const long long c = D.coff, n = (long long)D.P.nx * D.P.ny;
+        double acc[1] = {0.0};
+        for (long long k = (long long)it.y * kChunk + threadIdx.x;
+             k < n && k < (long long)(it.y + 1) * kChunk; k += blockDim.x)
+            acc[0] += (double)tmax(eta[c + k] + H[c + k], T(0));
+        if (dom_reduce<1, 0u>(acc, A.partials + D.poff, &A.stctl[it.x].counter, it.y, D.ncc) &&
+            threadIdx.x == 0)
+            A.ds[it.x].mass = acc[0] * (double)D.P.dx * (double)D.P.dy;
+        __syncthreads();
+    }
+}
+
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(256)
+kb_hyp(Arena<T> A, const int2* __restrict__ wl, int nw, const T* eta, const T* q1,
+       const T* q2, const T* etab, const T* q1b, const T* q2b, const T* H, T a, T b, T* eo,
+       T* q1o, T* q2o)
+{
+    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+        const int2 it = wl[w];
+        const Dom<T>& D = A.dom[it.x];
+        const Prm<T> P = D.P;
+        const long long c = D.coff;
+        const T dt = (T)A.ds[it.x].dt;
+        const int tx = cdiv(P.nx, TX);
+        const int nclamp = hyp_tile<T, TX, TY>(P, eta + c, q1 + c, q2 + c, etab + c, q1b + c,
+                                               q2b + c, H + c, a, b, dt, eo + c, q1o + c,
+                                               q2o + c, it.y % tx, it.y / tx);
+        if (nclamp) atomicAdd(&A.ds[it.x].clamped, nclamp);
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+kb_break(Arena<T> A, const int2* __restrict__ wl, int nw, const T* eta, const T* q1,
+         const T* q2, const T* H, T bfac, T* q1o, T* q2o)
+{
+    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+        const int2 it = wl[w];
+        const Dom<T>& D = A.dom[it.x];
+        const Prm<T> P = D.P;
+        const long long c = D.coff, n = (long long)P.nx * P.ny;
+        const T de = bfac * (T)A.ds[it.x].dt;
+        for (long long k = (long long)it.y * kChunk + threadIdx.x;
+             k < n && k < (long long)(it.y + 1) * kChunk; k += blockDim.x)
+            break_cell(P, eta + c, q1 + c, q2 + c, H + c, de, q1o + c, q2o + c, k);
+    }
+}
+
+struct AsmArgs {
+    double tol2;
+    int max_iter, kpass, with_coef, stage;
+};
+
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(256, 3)
+kb_asm(Arena<T> A, const int2* __restrict__ wl, int nw, const T* eta, const T* H,
+       const T* q1k, const T* q2k, const T* q1s, const T* q2s, const T* w_in, const T* w_b,
+       T a, T b, T* ws, T* cC, T* cW, T* cE, T* cS, T* cN, T* rhs, const T* p0, AsmArgs G)
+{
+    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+        const int2 it = wl[w];
+        const Dom<T>& D = A.dom[it.x];
+        const Prm<T> P = D.P;
+        const long long c = D.coff, n = D.noff;
+        const T de = b * (T)A.ds[it.x].dt;
+        const int tx = cdiv(P.nx + 1, TX), nt = tx * cdiv(P.ny + 1, TY);
+        double acc[3] = {0.0, 0.0, 0.0};
+        asm_tile<T, TX, TY>(P, eta + c, H + c, q1k + c, q2k + c, q1s + c, q2s + c, w_in + n,
+                            w_b + n, a, b, de, G.with_coef, ws + n, cC + n, cW + n, cE + n,
+                            cS + n, cN + n, rhs + n, p0 + n, /*resid_form=*/G.with_coef, it.y % tx,
+                            it.y / tx, acc);
+        SolveCtl* ctl = &A.sctl[it.x];
+        if (dom_reduce<3, 4u>(acc, A.partials + D.poff, &ctl->counter, it.y, nt) &&
+            threadIdx.x == 0) {
+            asm_finish(ctl, acc, G.tol2, G.max_iter, G.kpass, G.with_coef);
+            ctl->best = 1.0e300;
+            ctl->stale = 0;
+            ctl->fb = 0;
+            A.ds[it.x].last_sweeps[G.stage] = 0;
+            if (!G.with_coef) {
+                ctl->done = 1;
+            } else if (!ctl->done) {
+                atomicAdd(&A.loop[0], 1u);
+            } else {
+                // not diagonally dominant (status 4): the Chebyshev interval does not hold,
+                // solve with BiCGStab from dp = 0
+                ctl->fb = 1;
+                atomicAdd(&A.loop[2], 1u);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, int NA, int NB, int BY, int K>
+__global__ void __launch_bounds__(32 * BY, 2)
+kb_cheb(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const T* cW,
+        const T* cE, const T* cS, const T* cN, const T* rhs, T* x, T* xp, int stage)
+{
+    extern __shared__ unsigned char kb_cheb_smem[];
+    constexpr int TX = 32 * NA - 2 * K, TY = BY * NB - 2 * K;
+    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+        const int2 it = wl[w];
+        SolveCtl* ctl = &A.sctl[it.x];
+        if (ctl->done) continue;   // uniform: set only after all of this domain's items
+        const Dom<T>& D = A.dom[it.x];
+        const long long n = D.noff;
+        Rows<T> R;
+        R.cC = cC + n; R.cW = cW + n; R.cE = cE + n; R.cS = cS + n; R.cN = cN + n;
+        R.nx = D.P.nx; R.ny = D.P.ny;
+        const int tx = cdiv(R.nx + 1, TX), nt = tx * cdiv(R.ny + 1, TY);
+        T rsum, dmax;
+        cheb_tile<T, NA, NB, BY, K>(R, rhs + n, x + n, xp + n, ctl, it.y % tx, it.y / tx,
+                                    reinterpret_cast<T*>(kb_cheb_smem), rsum, dmax);
+        double acc[2];
+        if (dom_reduce_sum_max_f((float)rsum, (float)dmax, A.partials + D.poff, &ctl->counter,
+                                 acc, it.y, nt) &&
+            threadIdx.x == 0 && threadIdx.y == 0) {
+            cheb_finish(ctl, acc, K);
+            if (!ctl->done) {
+                // stall test: 8 passes without a 0.81 reduction of the best residual
+                if (acc[0] < 0.81 * ctl->best) { ctl->best = acc[0]; ctl->stale = 0; }
+                else if (++ctl->stale >= 8) { ctl->done = 1; ctl->status = 5; }
+            }
+            if (ctl->done) {
+                atomicSub(&A.loop[0], 1u);
+                DomState& s = A.ds[it.x];
+                s.sweeps += ctl->sweeps;
+                s.last_sweeps[stage] = ctl->sweeps;
+                if (ctl->status == 5) {
+                    // stalled (rounding floor of the precision, or a spectrum the
+                    // Gershgorin interval does not describe): BiCGStab from the current dp
+                    ctl->fb = 1;
+                    atomicAdd(&A.loop[2], 1u);
+                } else {
+                    s.last_status[stage] = ctl->status;
+                    s.last_resid[stage] = ctl->bdb > 0.0 ? sqrt(ctl->rr / ctl->bdb) : 0.0;
+                    if (ctl->status != 1) s.nonconv += 1;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Device side of the solver loops of a captured step: keep iterating while a domain is
+// still solving (loop[k]) and the iteration cap is not reached (counter loop[k + 1]).
+// count = 0 only evaluates the condition (before a loop's first body).
+__global__ void kb_loop_cond(cudaGraphConditionalHandle h, unsigned* loop, int k, unsigned cap,
+                             int count)
+{
+    if (threadIdx.x == 0) {
+        const unsigned it = count ? ++loop[k + 1] : loop[k + 1];
+        cudaGraphSetConditional(h, (loop[k] > 0u && it < cap) ? 1u : 0u);
+    }
+}
+
+// ---- BiCGStab fallback (the single-domain k_bicg_* arithmetic, per domain), over node
+// chunks; only domains with fb set take part.
+
+template <typename T>
+struct BiVec {
+    T *cC, *cW, *cE, *cS, *cN, *b, *x, *r, *rh, *ph[2], *v[2], *t;
+};
+
+template <typename T>
+__device__ __forceinline__ Rows<T> rows_at(const BiVec<T>& V, const Prm<T>& P, long long n)
+{
+    Rows<T> R;
+    R.cC = V.cC + n; R.cW = V.cW + n; R.cE = V.cE + n; R.cS = V.cS + n; R.cN = V.cN + n;
+    R.nx = P.nx; R.ny = P.ny;
+    return R;
+}
+
+// record the end of a domain's fallback solve
+__device__ __forceinline__ void bicg_end(SolveCtl* ctl, DomState& s, unsigned* loop, int stage,
+                                         int status)
+{
+    ctl->done = 1;
+    ctl->status = status;
+    ctl->fb = 0;
+    atomicSub(&loop[2], 1u);
+    s.fallbacks += 1;
+    s.sweeps += ctl->iter;
+    s.last_sweeps[stage] += ctl->iter;
+    s.last_status[stage] = status;
+    s.last_resid[stage] = ctl->bb > 0.0 ? sqrt(ctl->rr / ctl->bb) : 0.0;
+    if (status != 1) s.nonconv += 1;
+}
+
+#define BATCH_NODE_LOOP(k, nn, chunk)                                                    \
+    for (long long k = (long long)(chunk) * kChunk + threadIdx.x;                         \
+         k < (nn) && k < (long long)((chunk) + 1) * kChunk; k += blockDim.x)
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+kb_bicg_init(Arena<T> A, const int2* __restrict__ wl, int nw, BiVec<T> V, int stage)
+{
+    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+        const int2 it = wl[w];
+        SolveCtl* ctl = &A.sctl[it.x];
+        if (!ctl->fb) continue;
+        const Dom<T>& D = A.dom[it.x];
+        const long long n = D.noff, nn = (long long)(D.P.nx + 1) * (D.P.ny + 1);
+        const Rows<T> R = rows_at(V, D.P, n);
+        const int nxn = D.P.nx + 1;
+        const bool zero_rhs = ctl->bb == 0.0;
+        T* x = V.x + n;
+        const T* b = V.b + n;
+        double acc[1] = {0.0};
+        BATCH_NODE_LOOP(k, nn, it.y)
+        {
+            T rv;
+            if (zero_rhs) {
+                x[k] = T(0);
+                rv = T(0);
+            } else {
+                const int I = (int)(k % nxn), J = (int)(k / nxn);
+                rv = b[k] - row_apply(R, I, J, x[k], [&](size_t m) { return x[m]; });
+            }
+            V.r[n + k] = rv; V.rh[n + k] = rv; V.ph[0][n + k] = T(0); V.v[0][n + k] = T(0);
+            acc[0] += (double)rv * (double)rv;
+        }
+        if (dom_reduce<1, 0u>(acc, A.partials + D.poff, &ctl->counter, it.y, D.nnc) &&
+            threadIdx.x == 0) {
+            ctl->rho1 = acc[0];
+            ctl->rr = acc[0];
+            ctl->rho = 1.0; ctl->alpha = 1.0; ctl->omega = 1.0;
+            ctl->iter = 0;
+            ctl->done = 0;
+            ctl->status = 0;
+            if (zero_rhs || acc[0] <= ctl->tol2 * ctl->bb) bicg_end(ctl, A.ds[it.x], A.loop, stage, 1);
+        }
+        __syncthreads();
+    }
+}
+
+// phase A: p^ = r + beta (p^ - omega v); v = M D^-1 p^; alpha = rho1 / (rhat . v)
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+kb_bicg_A(Arena<T> A, const int2* __restrict__ wl, int nw, BiVec<T> V, int parity, int stage)
+{
+    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+        const int2 it = wl[w];
+        SolveCtl* ctl = &A.sctl[it.x];
+        if (!ctl->fb || ctl->done) continue;
+        const Dom<T>& D = A.dom[it.x];
+        const long long n = D.noff, nn = (long long)(D.P.nx + 1) * (D.P.ny + 1);
+        const Rows<T> R = rows_at(V, D.P, n);
+        const int nxn = D.P.nx + 1;
+        const double beta_d = (ctl->rho1 / ctl->rho) * (ctl->alpha / ctl->omega);
+        const T beta = (T)beta_d, om = (T)ctl->omega;
+        const T* r = V.r + n;
+        const T* ph_old = V.ph[parity] + n;
+        const T* v_old = V.v[parity] + n;
+        T* ph_new = V.ph[parity ^ 1] + n;
+        T* v_new = V.v[parity ^ 1] + n;
+        double acc[1] = {0.0};
+        BATCH_NODE_LOOP(k, nn, it.y)
+        {
+            const int I = (int)(k % nxn), J = (int)(k / nxn);
+            auto pnew = [&](size_t m) { return r[m] + beta * (ph_old[m] - om * v_old[m]); };
+            const T pc = pnew((size_t)k);
+            const T vc = row_apply(R, I, J, pc / R.cC[k], [&](size_t m) { return pnew(m) / R.cC[m]; });
+            ph_new[k] = pc;
+            v_new[k] = vc;
+            acc[0] += (double)V.rh[n + k] * (double)vc;
+        }
+        if (dom_reduce<1, 0u>(acc, A.partials + D.poff, &ctl->counter, it.y, D.nnc) &&
+            threadIdx.x == 0) {
+            ctl->rv = acc[0];
+            ctl->rho = ctl->rho1;
+            if (acc[0] == 0.0 || !isfinite(acc[0])) bicg_end(ctl, A.ds[it.x], A.loop, stage, 3);
+            else ctl->alpha = ctl->rho1 / acc[0];
+        }
+        __syncthreads();
+    }
+}
+
+// phase B: s = r - alpha v; t = M D^-1 s; omega = (t . s) / (t . t)
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+kb_bicg_B(Arena<T> A, const int2* __restrict__ wl, int nw, BiVec<T> V, int parity)
+{
+    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+        const int2 it = wl[w];
+        SolveCtl* ctl = &A.sctl[it.x];
+        if (!ctl->fb || ctl->done) continue;
+        const Dom<T>& D = A.dom[it.x];
+        const long long n = D.noff, nn = (long long)(D.P.nx + 1) * (D.P.ny + 1);
+        const Rows<T> R = rows_at(V, D.P, n);
+        const int nxn = D.P.nx + 1;
+        const T al = (T)ctl->alpha;
+        const T* r = V.r + n;
+        const T* v = V.v[parity ^ 1] + n;
+        double acc[2] = {0.0, 0.0};
+        BATCH_NODE_LOOP(k, nn, it.y)
+        {
+            const int I = (int)(k % nxn), J = (int)(k / nxn);
+            auto sat = [&](size_t m) { return r[m] - al * v[m]; };
+            const T sc = sat((size_t)k);
+            const T tc = row_apply(R, I, J, sc / R.cC[k], [&](size_t m) { return sat(m) / R.cC[m]; });
+            V.t[n + k] = tc;
+            acc[0] += (double)tc * (double)sc;
+            acc[1] += (double)tc * (double)tc;
+        }
+        if (dom_reduce<2, 0u>(acc, A.partials + D.poff, &ctl->counter, it.y, D.nnc) &&
+            threadIdx.x == 0) {
+            ctl->ts = acc[0];
+            ctl->tt = acc[1];
+            ctl->omega = acc[1] > 0.0 ? acc[0] / acc[1] : 0.0;
+        }
+        __syncthreads();
+    }
+}
+
+// phase C: x += alpha D^-1 p^ + omega D^-1 s; r = s - omega t; rho1 = rhat . r; test
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+kb_bicg_C(Arena<T> A, const int2* __restrict__ wl, int nw, BiVec<T> V, int parity, int stage)
+{
+    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+        const int2 it = wl[w];
+        SolveCtl* ctl = &A.sctl[it.x];
+        if (!ctl->fb || ctl->done) continue;
+        const Dom<T>& D = A.dom[it.x];
+        const long long n = D.noff, nn = (long long)(D.P.nx + 1) * (D.P.ny + 1);
+        const T al = (T)ctl->alpha, om = (T)ctl->omega;
+        const T* ph = V.ph[parity ^ 1] + n;
+        const T* v = V.v[parity ^ 1] + n;
+        double acc[2] = {0.0, 0.0};
+        BATCH_NODE_LOOP(k, nn, it.y)
+        {
+            const T s = V.r[n + k] - al * v[k];
+            const T dinv = T(1) / V.cC[n + k];
+            V.x[n + k] += (al * ph[k] + om * s) * dinv;
+            const T rn = s - om * V.t[n + k];
+            V.r[n + k] = rn;
+            acc[0] += (double)V.rh[n + k] * (double)rn;
+            acc[1] += (double)rn * (double)rn;
+        }
+        if (dom_reduce<2, 0u>(acc, A.partials + D.poff, &ctl->counter, it.y, D.nnc) &&
+            threadIdx.x == 0) {
+            ctl->rho1 = acc[0];
+            ctl->rr = acc[1];
+            ctl->iter += 1;
+            if (acc[1] <= ctl->tol2 * ctl->bb) bicg_end(ctl, A.ds[it.x], A.loop, stage, 1);
+            else if (ctl->iter >= ctl->max_iter) bicg_end(ctl, A.ds[it.x], A.loop, stage, 2);
+            else if (ctl->omega == 0.0 || acc[0] == 0.0 || !isfinite(acc[1]))
+                bicg_end(ctl, A.ds[it.x], A.loop, stage, 3);
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2)
+kb_corr(Arena<T> A, const int2* __restrict__ wl, int nw, const T* eta, const T* H,
+        const T* q1k, const T* q2k, const T* ws, const T* p, const T* dp, T* pout, T bfac,
+        int with_p, T* eo, T* q1o, T* q2o, T* wo, int final_stage)
+{
+    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+        const int2 it = wl[w];
+        const Dom<T>& D = A.dom[it.x];
+        const Prm<T> P = D.P;
+        const long long c = D.coff, n = D.noff;
+        const long long nn = (long long)(P.nx + 1) * (P.ny + 1);
+        DomState& s = A.ds[it.x];
+        const T de = bfac * (T)s.dt;
+        double acc[1] = {0.0};
+        int bad = 0;
+        for (long long k = (long long)it.y * kChunk + threadIdx.x;
+             k < nn && k < (long long)(it.y + 1) * kChunk; k += blockDim.x)
+            corr_node(P, eta + c, H + c, q1k + c, q2k + c, ws + n, p + n, dp + n, pout + n, de,
+                      with_p, eo + c, q1o + c, q2o + c, wo + n, final_stage, k, acc[0], bad);
+        if (bad) atomicOr(&s.nonfinite, 1);
+        if (final_stage) {
+            if (dom_reduce<1, 1u>(acc, A.partials + D.poff, &A.stctl[it.x].counter, it.y,
+                                  D.nnc) &&
+                threadIdx.x == 0) {
+                // every item of this domain has read s.dt: advance its clock and set the
+                // next step from the new state
+                s.t += s.dt;
+                s.steps += 1;
+                s.lam = acc[0];
+                s.dt = A.fixed_dt > 0.0 ? A.fixed_dt : (acc[0] > 0.0 ? A.cfl / acc[0] : 0.0);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- candidates
+
+// Kernel shapes the autotuner chooses from (per precision).
+struct Shape {
+    int tx, ty, threads;
+};
+
+template <typename T> struct Cands;
+
+template <typename T>
+using HypFn = void (*)(int grid, cudaStream_t, const Arena<T>&, const int2*, int, const T*,
+                       const T*, const T*, const T*, const T*, const T*, const T*, T, T, T*, T*,
+                       T*);
+template <typename T>
+using AsmFn = void (*)(int grid, cudaStream_t, const Arena<T>&, const int2*, int, const T*,
+                       const T*, const T*, const T*, const T*, const T*, const T*, const T*, T, T,
+                       T*, T*, T*, T*, T*, T*, T*, const T*, AsmArgs);
+template <typename T>
+using ChebFn = void (*)(int grid, cudaStream_t, const Arena<T>&, const int2*, int, const T*,
+                        const T*, const T*, const T*, const T*, const T*, T*, T*, int);
+
+template <typename T, int TX, int TY>
+void run_hyp(int grid, cudaStream_t s, const Arena<T>& A, const int2* wl, int nw, const T* e,
+             const T* a1, const T* a2, const T* eb, const T* ab, const T* bb, const T* H, T a,
+             T b, T* eo, T* ao, T* bo)
+{
+    kb_hyp<T, TX, TY><<<grid, 256, 0, s>>>(A, wl, nw, e, a1, a2, eb, ab, bb, H, a, b, eo, ao, bo);
+}
+
+template <typename T, int TX, int TY>
+void run_asm(int grid, cudaStream_t s, const Arena<T>& A, const int2* wl, int nw, const T* e,
+             const T* H, const T* q1k, const T* q2k, const T* q1s, const T* q2s, const T* win,
+             const T* wb, T a, T b, T* ws, T* cC, T* cW, T* cE, T* cS, T* cN, T* rhs,
+             const T* p0, AsmArgs G)
+{
+    kb_asm<T, TX, TY><<<grid, 256, 0, s>>>(A, wl, nw, e, H, q1k, q2k, q1s, q2s, win, wb, a, b,
+                                           ws, cC, cW, cE, cS, cN, rhs, p0, G);
+}
+
+template <typename T, int NA, int NB, int BY>
+constexpr size_t cheb_smem() { return 7 * (size_t)(32 * NA) * (BY * NB) * sizeof(T); }
+
+template <typename T, int NA, int NB, int BY>
+void run_cheb(int grid, cudaStream_t s, const Arena<T>& A, const int2* wl, int nw, const T* cC,
+              const T* cW, const T* cE, const T* cS, const T* cN, const T* rhs, T* x, T* xp,
+              int stage)
+{
+    kb_cheb<T, NA, NB, BY, 4><<<grid, dim3(32, BY), cheb_smem<T, NA, NB, BY>(), s>>>(
+        A, wl, nw, cC, cW, cE, cS, cN, rhs, x, xp, stage);
+}
+
+template <typename T>
+struct Cand {
+    Shape shape;
+    const void* kernel;   // for occupancy queries
+    size_t smem;
+};
+
+template <>
+struct Cands<float> {
+    static constexpr int nh = 3, na = 3, nc = 3;
+    static Shape hyp_shape(int k) { const Shape s[nh] = {{32, 16, 256}, {32, 8, 256}, {64, 8, 256}}; return s[k]; }
+    static HypFn<float> hyp(int k)
+    {
+        const HypFn<float> f[nh] = {run_hyp<float, 32, 16>, run_hyp<float, 32, 8>, run_hyp<float, 64, 8>};
+        return f[k];
+    }
+    static const void* hyp_kernel(int k)
+    {
+        const void* f[nh] = {(const void*)kb_hyp<float, 32, 16>, (const void*)kb_hyp<float, 32, 8>,
+                             (const void*)kb_hyp<float, 64, 8>};
+        return f[k];
+    }
+    static Shape asm_shape(int k) { const Shape s[na] = {{32, 16, 256}, {32, 8, 256}, {64, 8, 256}}; return s[k]; }
+    static AsmFn<float> assembly(int k)
+    {
+        const AsmFn<float> f[na] = {run_asm<float, 32, 16>, run_asm<float, 32, 8>, run_asm<float, 64, 8>};
+        return f[k];
+    }
+    static const void* asm_kernel(int k)
+    {
+        const void* f[na] = {(const void*)kb_asm<float, 32, 16>, (const void*)kb_asm<float, 32, 8>,
+                             (const void*)kb_asm<float, 64, 8>};
+        return f[k];
+    }
+    // Chebyshev: region (tile + 4-node halo on every side) and threads
+    static Shape cheb_shape(int k) { const Shape s[nc] = {{128, 32, 512}, {64, 64, 512}, {128, 32, 256}}; return s[k]; }
+    static ChebFn<float> cheb(int k)
+    {
+        const ChebFn<float> f[nc] = {run_cheb<float, 4, 2, 16>, run_cheb<float, 2, 4, 16>,
+                                     run_cheb<float, 4, 4, 8>};
+        return f[k];
+    }
+    static const void* cheb_kernel(int k)
+    {
+        const void* f[nc] = {(const void*)kb_cheb<float, 4, 2, 16, 4>,
+                             (const void*)kb_cheb<float, 2, 4, 16, 4>,
+                             (const void*)kb_cheb<float, 4, 4, 8, 4>};
+        return f[k];
+    }
+    static size_t cheb_smem_of(int k)
+    {
+        const size_t s[nc] = {cheb_smem<float, 4, 2, 16>(), cheb_smem<float, 2, 4, 16>(),
+                              cheb_smem<float, 4, 4, 8>()};
+        return s[k];
+    }
+};
+
+template <>
+struct Cands<double> {
+    static constexpr int nh = 2, na = 2, nc = 2;
+    static Shape hyp_shape(int k) { const Shape s[nh] = {{32, 8, 256}, {16, 16, 256}}; return s[k]; }
+    static HypFn<double> hyp(int k)
+    {
+        const HypFn<double> f[nh] = {run_hyp<double, 32, 8>, run_hyp<double, 16, 16>};
+        return f[k];
+    }
+    static const void* hyp_kernel(int k)
+    {
+        const void* f[nh] = {(const void*)kb_hyp<double, 32, 8>, (const void*)kb_hyp<double, 16, 16>};
+        return f[k];
+    }
+    static Shape asm_shape(int k) { const Shape s[na] = {{32, 16, 256}, {32, 8, 256}}; return s[k]; }
+    static AsmFn<double> assembly(int k)
+    {
+        const AsmFn<double> f[na] = {run_asm<double, 32, 16>, run_asm<double, 32, 8>};
+        return f[k];
+    }
+    static const void* asm_kernel(int k)
+    {
+        const void* f[na] = {(const void*)kb_asm<double, 32, 16>, (const void*)kb_asm<double, 32, 8>};
+        return f[k];
+    }
+    static Shape cheb_shape(int k) { const Shape s[nc] = {{64, 32, 512}, {64, 32, 256}}; return s[k]; }
+    static ChebFn<double> cheb(int k)
+    {
+        const ChebFn<double> f[nc] = {run_cheb<double, 2, 2, 16>, run_cheb<double, 2, 4, 8>};
+        return f[k];
+    }
+    static const void* cheb_kernel(int k)
+    {
+        const void* f[nc] = {(const void*)kb_cheb<double, 2, 2, 16, 4>,
+                             (const void*)kb_cheb<double, 2, 4, 8, 4>};
+        return f[k];
+    }
+    static size_t cheb_smem_of(int k)
+    {
+        const size_t s[nc] = {cheb_smem<double, 2, 2, 16>(), cheb_smem<double, 2, 4, 8>()};
+        return s[k];
+    }
+};
+
+constexpr int kChebK = 4;   // sweeps per Chebyshev pass (all candidates)
+
+}  // namespace
+}  // namespace nh
+
+using namespace nh;
+
+// ---------------------------------------------------------------- host runtime
+
+struct BatchBase {
+    virtual ~BatchBase() {}
+    virtual int set_state(int d, const void* eta, const void* q1, const void* q2, const void* w,
+                          const void* p, double t, int where) = 0;
+    virtual int get_state(int d, void* eta, void* q1, void* q2, void* w, void* p, double* t,
+                          int where) = 0;
+    virtual int run(int nsteps) = 0;
+    virtual int stats(int d, nh_stats_t* out) = 0;
+    virtual int get_tuning(nh_batch_tuning* out) = 0;
+    virtual int set_tuning(const nh_batch_tuning* in) = 0;
+};
+
+struct nh_batch {
+    int n = 0;
+    std::vector<nh_grid> grids;
+    nh_params prm;
+    int flags = 0;
+    cudaStream_t s = nullptr;
+    cudaStream_t own = nullptr;     // created when the caller passes the legacy stream
+    cudaStream_t side = nullptr;    // capture of the solver-loop bodies
+    std::unique_ptr<BatchBase> impl;
+    std::string err;
+};
+
+namespace {
+
+int bfail(nh_batch* b, int code, const std::string& msg)
+{
+    if (b) b->err = msg;
+    return code;
+}
+
+int bcuda(nh_batch* b, cudaError_t e, const char* where)
+{
+    return bfail(b, NH_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+template <typename T>
+struct BatchImpl : BatchBase {
+    using C = Cands<T>;
+    nh_batch* hb;
+    int n;
+    std::vector<Dom<T>> doms;
+    std::vector<int> order;            // domains, largest first
+    long long ncell = 0, nnode = 0;
+    int nsm = 148;
+    Bufs<T> B{};
+    Dom<T>* d_dom = nullptr;
+    DomState* d_ds = nullptr;
+    SolveCtl* d_sctl = nullptr;
+    StepCtl* d_stctl = nullptr;
+    unsigned* d_loop = nullptr;
+    unsigned* h_loop = nullptr;        // pinned
+    DomState* h_ds = nullptr;          // pinned
+    std::vector<void*> allocs;
+    // work lists: element items (cell chunks, node chunks) and one per tile candidate
+    int2 *wl_cell = nullptr, *wl_node = nullptr;
+    int nw_cell = 0, nw_node = 0;
+    std::vector<int2*> wl_hyp, wl_asm, wl_cheb;
+    std::vector<int> nw_hyp, nw_asm, nw_cheb;
+    nh_batch_tuning tun{};
+    bool need_lambda = true;
+    bool tuned_once = false;
+    cudaGraphExec_t exec = nullptr;
+    bool graph_failed = false;
+
+    ~BatchImpl() override
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        for (void* p : allocs) cudaFree(p);
+        if (h_loop) cudaFreeHost(h_loop);
+        if (h_ds) cudaFreeHost(h_ds);
+    }
+
+    template <typename U>
+    int alloc(U** p, size_t k)
+    {
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, k * sizeof(U) + 256);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return bfail(hb, NH_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        allocs.push_back(q);
+        *p = static_cast<U*>(q);
+        return NH_OK;
+    }
+
+    Arena<T> arena() const
+    {
+        Arena<T> A;
+        A.dom = d_dom; A.sctl = d_sctl; A.stctl = d_stctl; A.ds = d_ds;
+        A.partials = B.partials; A.loop = d_loop;
+        A.fixed_dt = hb->prm.fixed_dt; A.cfl = hb->prm.cfl;
+        return A;
+    }
+
+    // (domain, item) lists, largest domain first; items(d) = number of items of domain d
+    template <typename F>
+    int make_list(F items, int2** out, int* count)
+    {
+        std::vector<int2> v;
+        for (int d : order) {
+            const int k = items(d);
+            for (int i = 0; i < k; ++i) v.push_back(make_int2(d, i));
+        }
+        int rc = alloc(out, v.size() + 1);
+        if (rc != NH_OK) return rc;
+        cudaMemcpyAsync(*out, v.data(), v.size() * sizeof(int2), cudaMemcpyHostToDevice, hb->s);
+        *count = (int)v.size();
+        return NH_OK;
+    }
+
+    int init(const double* const* Hs)
+    {
+        const nh_params& q = hb->prm;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (nsm <= 0) nsm = 148;
+        doms.resize(n);
+        long long poff = 0;
+        for (int d = 0; d < n; ++d) {
+            const nh_grid& g = hb->grids[d];
+            Dom<T>& D = doms[d];
+            Prm<T>& P = D.P;
+            P.nx = g.nx; P.ny = g.ny;
+            P.bcw = g.bc[0]; P.bce = g.bc[1]; P.bcs = g.bc[2]; P.bcn = g.bc[3];
+            P.dx = (T)g.dx; P.dy = (T)g.dy;
+            P.g = (T)q.g; P.delta = (T)q.delta; P.hdry = (T)q.hdry; P.manning = (T)q.manning_n;
+            P.B1 = (T)q.B1; P.breaking = q.breaking;
+            const long long nc = (long long)g.nx * g.ny, nn = (long long)(g.nx + 1) * (g.ny + 1);
+            D.coff = ncell; D.noff = nnode;
+            // keep every domain's arrays 256-byte aligned
+            const long long al = 256 / (long long)sizeof(T);
+            ncell += (nc + al - 1) / al * al;
+            nnode += (nn + al - 1) / al * al;
+            D.ncc = (int)((nc + kChunk - 1) / kChunk);
+            D.nnc = (int)((nn + kChunk - 1) / kChunk);
+            long long np = std::max<long long>(D.ncc, 2LL * D.nnc);   // (BiCGStab: 2 per chunk)
+            for (int k = 0; k < C::na; ++k) {
+                const Shape s = C::asm_shape(k);
+                np = std::max<long long>(np, 3LL * cdiv(g.nx + 1, s.tx) * cdiv(g.ny + 1, s.ty));
+            }
+            for (int k = 0; k < C::nc; ++k) {
+                const Shape s = C::cheb_shape(k);
+                np = std::max<long long>(np, 2LL * cdiv(g.nx + 1, s.tx - 2 * kChebK) *
+                                                  cdiv(g.ny + 1, s.ty - 2 * kChebK));
+            }
+            D.poff = poff;
+            poff += (np + 31) / 32 * 32;
+        }
+        order.resize(n);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            return (long long)hb->grids[a].nx * hb->grids[a].ny >
+                   (long long)hb->grids[b].nx * hb->grids[b].ny;
+        });
+        int rc = NH_OK;
+#define A_(ptr, k) if ((rc = alloc(&(ptr), (k))) != NH_OK) return rc
+        A_(B.H, ncell);
+        A_(B.eta, ncell); A_(B.q1, ncell); A_(B.q2, ncell);
+        A_(B.eta1, ncell); A_(B.q11, ncell); A_(B.q21, ncell);
+        A_(B.etas, ncell); A_(B.q1s, ncell); A_(B.q2s, ncell);
+        if (q.breaking) { A_(B.q1k, ncell); A_(B.q2k, ncell); }
+        else { B.q1k = B.q1s; B.q2k = B.q2s; }
+        A_(B.w, nnode); A_(B.p, nnode); A_(B.w1, nnode); A_(B.ws, nnode);
+        A_(B.dp, nnode); A_(B.palt, nnode); A_(B.r, nnode);
+        A_(B.cC, nnode); A_(B.cW, nnode); A_(B.cE, nnode); A_(B.cS, nnode); A_(B.cN, nnode);
+        A_(B.rhs, nnode);
+        if (q.nonhydrostatic) {
+            A_(B.rh, nnode); A_(B.ph[0], nnode); A_(B.ph[1], nnode);
+            A_(B.v[0], nnode); A_(B.v[1], nnode); A_(B.t, nnode);
+        }
+        A_(B.partials, poff + 64);
+        A_(d_dom, n);
+        A_(d_ds, n);
+        A_(d_sctl, n);
+        A_(d_stctl, n);
+        A_(d_loop, 4);
+#undef A_
+        cudaError_t e;
+        if ((e = cudaMallocHost(&h_loop, 4 * sizeof(unsigned))) != cudaSuccess) return bcuda(hb, e, "cudaMallocHost");
+        if ((e = cudaMallocHost(&h_ds, n * sizeof(DomState))) != cudaSuccess) return bcuda(hb, e, "cudaMallocHost");
+        cudaStream_t s = hb->s;
+        cudaMemcpyAsync(d_dom, doms.data(), n * sizeof(Dom<T>), cudaMemcpyHostToDevice, s);
+        cudaMemsetAsync(d_ds, 0, n * sizeof(DomState), s);
+        cudaMemsetAsync(d_stctl, 0, n * sizeof(StepCtl), s);
+        cudaMemsetAsync(d_loop, 0, 4 * sizeof(unsigned), s);
+        {
+            std::vector<SolveCtl> sc(n);
+            std::memset(sc.data(), 0, n * sizeof(SolveCtl));
+            for (auto& c : sc) c.eps_dp = q.eps_dp;
+            cudaMemcpyAsync(d_sctl, sc.data(), n * sizeof(SolveCtl), cudaMemcpyHostToDevice, s);
+            cudaStreamSynchronize(s);
+        }
+        // all node and cell arrays start at zero (padding included), then H and eta
+        T* cell_arrays[] = {B.eta, B.q1, B.q2, B.eta1, B.q11, B.q21, B.etas, B.q1s, B.q2s, B.H};
+        for (T* a : cell_arrays) cudaMemsetAsync(a, 0, ncell * sizeof(T), s);
+        if (q.breaking) {
+            cudaMemsetAsync(B.q1k, 0, ncell * sizeof(T), s);
+            cudaMemsetAsync(B.q2k, 0, ncell * sizeof(T), s);
+        }
+        T* node_arrays[] = {B.w, B.p, B.w1, B.ws, B.dp, B.palt, B.r, B.cC, B.cW, B.cE, B.cS, B.cN, B.rhs,
+                            B.rh, B.ph[0], B.ph[1], B.v[0], B.v[1], B.t};
+        for (T* a : node_arrays)
+            if (a) cudaMemsetAsync(a, 0, nnode * sizeof(T), s);
+        for (int d = 0; d < n; ++d) {
+            const nh_grid& g = hb->grids[d];
+            const size_t nc = (size_t)g.nx * g.ny;
+            std::vector<T> Hv(nc), e0(nc);
+            for (size_t k = 0; k < nc; ++k) {
+                Hv[k] = (T)Hs[d][k];
+                e0[k] = (T)(Hs[d][k] > 0.0 ? 0.0 : -Hs[d][k]);
+            }
+            cudaMemcpyAsync(B.H + doms[d].coff, Hv.data(), nc * sizeof(T), cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(B.eta + doms[d].coff, e0.data(), nc * sizeof(T), cudaMemcpyHostToDevice, s);
+            cudaStreamSynchronize(s);   // host vectors go out of scope
+        }
+        if ((rc = make_list([&](int d) { return doms[d].ncc; }, &wl_cell, &nw_cell)) != NH_OK) return rc;
+        if ((rc = make_list([&](int d) { return doms[d].nnc; }, &wl_node, &nw_node)) != NH_OK) return rc;
+        wl_hyp.resize(C::nh); nw_hyp.resize(C::nh);
+        for (int k = 0; k < C::nh; ++k) {
+            const Shape sh = C::hyp_shape(k);
+            rc = make_list([&](int d) { return cdiv(doms[d].P.nx, sh.tx) * cdiv(doms[d].P.ny, sh.ty); },
+                           &wl_hyp[k], &nw_hyp[k]);
+            if (rc != NH_OK) return rc;
+        }
+        wl_asm.resize(C::na); nw_asm.resize(C::na);
+        for (int k = 0; k < C::na; ++k) {
+            const Shape sh = C::asm_shape(k);
+            rc = make_list([&](int d) { return cdiv(doms[d].P.nx + 1, sh.tx) * cdiv(doms[d].P.ny + 1, sh.ty); },
+                           &wl_asm[k], &nw_asm[k]);
+            if (rc != NH_OK) return rc;
+        }
+        wl_cheb.resize(C::nc); nw_cheb.resize(C::nc);
+        for (int k = 0; k < C::nc; ++k) {
+            const Shape sh = C::cheb_shape(k);
+            rc = make_list([&](int d) {
+                return cdiv(doms[d].P.nx + 1, sh.tx - 2 * kChebK) * cdiv(doms[d].P.ny + 1, sh.ty - 2 * kChebK);
+            }, &wl_cheb[k], &nw_cheb[k]);
+            if (rc != NH_OK) return rc;
+            if ((e = cudaFuncSetAttribute(C::cheb_kernel(k), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)C::cheb_smem_of(k))) != cudaSuccess)
+                return bcuda(hb, e, "cudaFuncSetAttribute");
+        }
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return bcuda(hb, e, "nh_create_batch");
+        if ((e = cudaGetLastError()) != cudaSuccess) return bcuda(hb, e, "nh_create_batch");
+        // defaults until tuned: the single-domain shapes, one block per item
+        tun = nh_batch_tuning{};
+        tun.hyp = 0; tun.assembly = 0; tun.cheb = 0;
+        tun.persistent = 0;
+        tun.graph = (hb->flags & NH_BATCH_GRAPH) ? 1 : 0;
+        tun.tuned = 0;
+        return NH_OK;
+    }
+
+    // grid of a launch: one block per item, or the resident capacity (persistent)
+    std::vector<std::pair<const void*, int>> occ;   // resident blocks per SM, per kernel
+    int grid_of(const void* kernel, int threads, size_t smem, int items, bool persistent)
+    {
+        if (items <= 0) return 1;
+        if (!persistent) return items;
+        int per = -1;
+        for (auto& o : occ)
+            if (o.first == kernel) per = o.second;
+        if (per < 0) {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess || per < 1) {
+                cudaGetLastError();
+                per = 1;
+            }
+            occ.emplace_back(kernel, per);
+        }
+        const int g = per * nsm;
+        return g < items ? g : items;
+    }
+    bool pers(int cls) const { return (tun.persistent >> cls) & 1; }
+
+    int launch_lambda()
+    {
+        kb_lambda<T><<<grid_of((const void*)kb_lambda<T>, kThreads, 0, nw_cell, true), kThreads, 0, hb->s>>>(
+            arena(), wl_cell, nw_cell, B.eta, B.q1, B.q2, B.H);
+        return cudaGetLastError() == cudaSuccess ? NH_OK : NH_ECUDA;
+    }
+
+    void hyp(int s, int cand, bool persistent)
+    {
+        const T a = s == 0 ? T(0) : T(0.5), b = s == 0 ? T(1) : T(0.5);
+        const T* ein = s == 0 ? B.eta : B.eta1;
+        const T* ain = s == 0 ? B.q1 : B.q11;
+        const T* bin = s == 0 ? B.q2 : B.q21;
+        const Shape sh = C::hyp_shape(cand);
+        C::hyp(cand)(grid_of(C::hyp_kernel(cand), sh.threads, 0, nw_hyp[cand], persistent), hb->s,
+                     arena(), wl_hyp[cand], nw_hyp[cand], ein, ain, bin, B.eta, B.q1, B.q2, B.H,
+                     a, b, B.etas, B.q1s, B.q2s);
+    }
+
+    void assembly(int s, int cand, bool persistent)
+    {
+        const nh_params& q = hb->prm;
+        const T a = s == 0 ? T(0) : T(0.5), b = s == 0 ? T(1) : T(0.5);
+        const T* win = s == 0 ? B.w : B.w1;
+        AsmArgs G;
+        G.tol2 = q.tol * q.tol;
+        G.max_iter = q.max_iter;
+        G.kpass = kChebK;
+        G.with_coef = q.nonhydrostatic ? 1 : 0;
+        G.stage = s;
+        const Shape sh = C::asm_shape(cand);
+        C::assembly(cand)(grid_of(C::asm_kernel(cand), sh.threads, 0, nw_asm[cand], persistent),
+                          hb->s, arena(), wl_asm[cand], nw_asm[cand], B.etas, B.H, B.q1k, B.q2k,
+                          B.q1s, B.q2s, win, B.w, a, b, B.ws, B.cC, B.cW, B.cE, B.cS, B.cN, B.rhs,
+                          B.p, G);
+    }
+
+    void cheb_pass(int s, int cand, bool persistent, cudaStream_t st)
+    {
+        const Shape sh = C::cheb_shape(cand);
+        C::cheb(cand)(grid_of(C::cheb_kernel(cand), sh.threads, C::cheb_smem_of(cand), nw_cheb[cand], persistent),
+                      st, arena(), wl_cheb[cand], nw_cheb[cand], B.cC, B.cW, B.cE, B.cS, B.cN,
+                      B.rhs, B.dp, B.r, s);
+    }
+
+    unsigned pass_cap() const { return (unsigned)(hb->prm.max_iter / kChebK + 16); }
+    unsigned bicg_cap() const { return (unsigned)(hb->prm.max_iter / 2 + 2); }
+
+    BiVec<T> bivec() const
+    {
+        BiVec<T> V;
+        V.cC = B.cC; V.cW = B.cW; V.cE = B.cE; V.cS = B.cS; V.cN = B.cN;
+        V.b = B.rhs; V.x = B.dp; V.r = B.r; V.rh = B.rh;
+        V.ph[0] = B.ph[0]; V.ph[1] = B.ph[1]; V.v[0] = B.v[0]; V.v[1] = B.v[1]; V.t = B.t;
+        return V;
+    }
+
+    void bicg_init(int s, cudaStream_t st)
+    {
+        kb_bicg_init<T><<<grid_of((const void*)kb_bicg_init<T>, kThreads, 0, nw_node, pers(3)), kThreads, 0, st>>>(
+            arena(), wl_node, nw_node, bivec(), s);
+    }
+
+    // two BiCGStab iterations (the p^ / v buffers alternate, so a pair restores them)
+    void bicg_pair(int s, cudaStream_t st)
+    {
+        const BiVec<T> V = bivec();
+        for (int parity = 0; parity < 2; ++parity) {
+            kb_bicg_A<T><<<grid_of((const void*)kb_bicg_A<T>, kThreads, 0, nw_node, pers(3)), kThreads, 0, st>>>(
+                arena(), wl_node, nw_node, V, parity, s);
+            kb_bicg_B<T><<<grid_of((const void*)kb_bicg_B<T>, kThreads, 0, nw_node, pers(3)), kThreads, 0, st>>>(
+                arena(), wl_node, nw_node, V, parity);
+            kb_bicg_C<T><<<grid_of((const void*)kb_bicg_C<T>, kThreads, 0, nw_node, pers(3)), kThreads, 0, st>>>(
+                arena(), wl_node, nw_node, V, parity, s);
+        }
+    }
+
+    // the stage up to the solve (hyperbolic step, breaking, assembly)
+    void pre_solve(int s)
+    {
+        const nh_params& q = hb->prm;
+        hyp(s, tun.hyp, pers(0));
+        if (q.breaking) {
+            const T b = s == 0 ? T(1) : T(0.5);
+            kb_break<T><<<grid_of((const void*)kb_break<T>, kThreads, 0, nw_cell, pers(3)), kThreads, 0, hb->s>>>(
+                arena(), wl_cell, nw_cell, B.etas, B.q1s, B.q2s, B.H, b, B.q1k, B.q2k);
+        }
+        cudaMemsetAsync(d_loop, 0, 4 * sizeof(unsigned), hb->s);
+        if (q.nonhydrostatic) cudaMemsetAsync(B.dp, 0, nnode * sizeof(T), hb->s);
+        assembly(s, tun.assembly, pers(1));
+    }
+
+    void post_solve(int s)
+    {
+        const nh_params& q = hb->prm;
+        T* eo = s == 0 ? B.eta1 : B.eta;
+        T* ao = s == 0 ? B.q11 : B.q1;
+        T* bo = s == 0 ? B.q21 : B.q2;
+        T* wo = s == 0 ? B.w1 : B.w;
+        const T b = s == 0 ? T(1) : T(0.5);
+        kb_corr<T><<<grid_of((const void*)kb_corr<T>, kThreads, 0, nw_node, pers(3)), kThreads, 0, hb->s>>>(
+            arena(), wl_node, nw_node, B.etas, B.H, B.q1k, B.q2k, B.ws, B.p, B.dp, B.palt, b,
+            q.nonhydrostatic ? 1 : 0, eo, ao, bo, wo, s == 1 ? 1 : 0);
+        std::swap(B.p, B.palt);
+    }
+
+    // eager solve: passes in batches, the host reads the number of domains still solving;
+    // then the BiCGStab fallback for the domains that need it
+    int solve_eager(int s)
+    {
+        unsigned passes = 0;
+        int batch = 4;
+        cudaError_t e;
+        for (;;) {
+            for (int k = 0; k < batch; ++k) cheb_pass(s, tun.cheb, pers(2), hb->s);
+            passes += batch;
+            cudaMemcpyAsync(h_loop, d_loop, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, hb->s);
+            if ((e = cudaStreamSynchronize(hb->s)) != cudaSuccess) return bcuda(hb, e, "batched pressure solve");
+            if (h_loop[0] == 0u || passes >= pass_cap()) break;
+            batch = 2;
+        }
+        if (h_loop[2] == 0u) return NH_OK;
+        bicg_init(s, hb->s);
+        for (unsigned pairs = 0; pairs < bicg_cap();) {
+            for (int k = 0; k < 2; ++k, ++pairs) bicg_pair(s, hb->s);
+            cudaMemcpyAsync(h_loop, d_loop, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, hb->s);
+            if ((e = cudaStreamSynchronize(hb->s)) != cudaSuccess) return bcuda(hb, e, "batched BiCGStab");
+            if (h_loop[2] == 0u) break;
+        }
+        return NH_OK;
+    }
+
+    int step_eager()
+    {
+        for (int s = 0; s < 2; ++s) {
+            pre_solve(s);
+            if (hb->prm.nonhydrostatic) {
+                int rc = solve_eager(s);
+                if (rc != NH_OK) return rc;
+            }
+            post_solve(s);
+        }
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? NH_OK : bcuda(hb, e, "batched step");
+    }
+
+    // Append to the capture on stream s a conditional WHILE node whose body is captured from
+    // body(side stream, handle); pre(handle), when given, is captured before the node and
+    // sets the first condition (the handle's default value is dflt).
+    template <typename Chk, typename Body, typename Pre>
+    void add_while(cudaStream_t s, Chk& chk, unsigned dflt, Body&& body, Pre&& pre)
+    {
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t g = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        chk(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+        cudaGraphConditionalHandle h = 0;
+        chk(cudaGraphConditionalHandleCreate(&h, g, dflt, cudaGraphCondAssignDefault));
+        call_pre(pre, h);
+        chk(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+        // (the params union has no default constructor: zeroed storage)
+        alignas(cudaGraphNodeParams) unsigned char npb[sizeof(cudaGraphNodeParams)] = {};
+        cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(npb);
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node = nullptr;
+        chk(cudaGraphAddNode(&node, g, deps, nullptr, nd, &np));
+        if (!node) return;
+        cudaGraph_t bodyg = np.conditional.phGraph_out[0];
+        chk(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+        chk(cudaStreamBeginCaptureToGraph(hb->side, bodyg, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal));
+        body(hb->side, h);
+        chk(cudaGetLastError());
+        cudaGraph_t bout = nullptr;
+        chk(cudaStreamEndCapture(hb->side, &bout));
+    }
+    template <typename Pre>
+    static void call_pre(Pre& pre, cudaGraphConditionalHandle h) { pre(h); }
+    static void call_pre(std::nullptr_t, cudaGraphConditionalHandle) {}
+
+    // one step as a graph; the solver loops are conditional WHILE nodes
+    int build_graph()
+    {
+        cudaStream_t s = hb->s;
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return bcuda(hb, e, "cudaStreamBeginCapture");
+        cudaError_t first = cudaSuccess;
+        auto chk = [&](cudaError_t x) { if (first == cudaSuccess && x != cudaSuccess) first = x; };
+        for (int st = 0; st < 2; ++st) {
+            pre_solve(st);
+            if (hb->prm.nonhydrostatic) {
+                // Chebyshev passes: WHILE (domains solving) { pass; test }
+                add_while(s, chk, 1, [&](cudaStream_t bs, cudaGraphConditionalHandle h) {
+                    cheb_pass(st, tun.cheb, pers(2), bs);
+                    kb_loop_cond<<<1, 32, 0, bs>>>(h, d_loop, 0, pass_cap(), 1);
+                }, nullptr);
+                // fallback: init; WHILE (domains in BiCGStab) { two iterations; test }
+                bicg_init(st, s);
+                add_while(s, chk, 0, [&](cudaStream_t bs, cudaGraphConditionalHandle h) {
+                    bicg_pair(st, bs);
+                    kb_loop_cond<<<1, 32, 0, bs>>>(h, d_loop, 2, bicg_cap(), 1);
+                }, [&](cudaGraphConditionalHandle h) {
+                    kb_loop_cond<<<1, 32, 0, s>>>(h, d_loop, 2, bicg_cap(), 0);
+                });
+            }
+            post_solve(st);
+        }
+        chk(cudaGetLastError());
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(s, &graph);
+        if (first == cudaSuccess) first = e;
+        if (first == cudaSuccess) first = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (first != cudaSuccess) {
+            cudaGetLastError();
+            exec = nullptr;
+            return bcuda(hb, first, "step graph");
+        }
+        return NH_OK;
+    }
+
+    float time_ms(const std::function<void()>& f, int reps)
+    {
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        f();   // warm-up
+        cudaEventRecord(a, hb->s);
+        for (int k = 0; k < reps; ++k) f();
+        cudaEventRecord(b, hb->s);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        return ms / reps;
+    }
+
+    // Time every candidate (and grid form) of the hyperbolic, assembly and Chebyshev
+    // kernels on the current state, stage-1 arguments; keep the fastest.  The state itself
+    // is not changed (only scratch arrays), and the per-domain counters are restored.
+    int autotune()
+    {
+        cudaStream_t s = hb->s;
+        cudaMemcpyAsync(h_ds, d_ds, n * sizeof(DomState), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        const int reps = 3;
+        float best = 1e30f;
+        for (int k = 0; k < C::nh; ++k)
+            for (int p = 0; p < 2; ++p) {
+                const float t = time_ms([&] { hyp(0, k, p == 1); }, reps);
+                if (t < best) { best = t; tun.hyp = k; tun.persistent = (tun.persistent & ~1) | p; }
+            }
+        tun.ms[0] = best;
+        hyp(0, tun.hyp, pers(0));
+        if (hb->prm.breaking)
+            kb_break<T><<<nw_cell, kThreads, 0, s>>>(arena(), wl_cell, nw_cell, B.etas, B.q1s,
+                                                    B.q2s, B.H, T(1), B.q1k, B.q2k);
+        best = 1e30f;
+        for (int k = 0; k < C::na; ++k)
+            for (int p = 0; p < 2; ++p) {
+                const float t = time_ms([&] { assembly(0, k, p == 1); }, reps);
+                if (t < best) { best = t; tun.assembly = k; tun.persistent = (tun.persistent & ~2) | (p << 1); }
+            }
+        tun.ms[1] = best;
+        if (hb->prm.nonhydrostatic) {
+            best = 1e30f;
+            for (int k = 0; k < C::nc; ++k)
+                for (int p = 0; p < 2; ++p) {
+                    cudaMemsetAsync(B.dp, 0, nnode * sizeof(T), s);
+                    assembly(0, tun.assembly, pers(1));
+                    const float t = time_ms([&] { cheb_pass(0, k, p == 1, s); }, 2 * reps);
+                    if (t < best) { best = t; tun.cheb = k; tun.persistent = (tun.persistent & ~4) | (p << 2); }
+                }
+            tun.ms[2] = best;
+        }
+        {
+            // element kernels (correction, breaking): compare the two grid forms on the correction
+            // of a stage-1 pass writing into the stage-1 outputs (overwritten by the real step)
+            float tb[2];
+            for (int p = 0; p < 2; ++p) {
+                const int gsz = grid_of((const void*)kb_corr<T>, kThreads, 0, nw_node, p == 1);
+                tb[p] = time_ms([&] {
+                    kb_corr<T><<<gsz, kThreads, 0, s>>>(arena(), wl_node, nw_node, B.etas, B.H, B.q1k,
+                                                       B.q2k, B.ws, B.p, B.dp, B.palt, T(1), 0, B.eta1,
+                                                       B.q11, B.q21, B.w1, 0);
+                }, reps);
+            }
+            tun.persistent = (tun.persistent & ~8) | ((tb[1] < tb[0] ? 1 : 0) << 3);
+        }
+        cudaMemsetAsync(d_loop, 0, 4 * sizeof(unsigned), s);
+        cudaMemcpyAsync(d_ds, h_ds, n * sizeof(DomState), cudaMemcpyHostToDevice, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) return bcuda(hb, e, "autotune");
+        tun.tuned = 1;
+        return NH_OK;
+    }
+
+    int set_state(int d, const void* eta, const void* q1, const void* q2, const void* w,
+                  const void* p, double t, int where) override
+    {
+        if (d < 0 || d >= n) return bfail(hb, NH_EINVAL, "domain index out of range");
+        if (!eta || !q1) return bfail(hb, NH_EINVAL, "eta and q1 are required");
+        const cudaMemcpyKind k = where == NH_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        const Dom<T>& D = doms[d];
+        const size_t nc = (size_t)D.P.nx * D.P.ny, nn = (size_t)(D.P.nx + 1) * (D.P.ny + 1);
+        cudaStream_t s = hb->s;
+        cudaMemcpyAsync(B.eta + D.coff, eta, nc * sizeof(T), k, s);
+        cudaMemcpyAsync(B.q1 + D.coff, q1, nc * sizeof(T), k, s);
+        if (q2) cudaMemcpyAsync(B.q2 + D.coff, q2, nc * sizeof(T), k, s);
+        else cudaMemsetAsync(B.q2 + D.coff, 0, nc * sizeof(T), s);
+        if (w) cudaMemcpyAsync(B.w + D.noff, w, nn * sizeof(T), k, s);
+        else cudaMemsetAsync(B.w + D.noff, 0, nn * sizeof(T), s);
+        if (p) cudaMemcpyAsync(B.p + D.noff, p, nn * sizeof(T), k, s);
+        else cudaMemsetAsync(B.p + D.noff, 0, nn * sizeof(T), s);
+        DomState z;
+        std::memset(&z, 0, sizeof(z));
+        z.t = t;
+        cudaMemcpyAsync(d_ds + d, &z, sizeof(DomState), cudaMemcpyHostToDevice, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) return bcuda(hb, e, "nh_batch_set_state");
+        need_lambda = true;
+        return NH_OK;
+    }
+
+    int get_state(int d, void* eta, void* q1, void* q2, void* w, void* p, double* t,
+                  int where) override
+    {
+        if (d < 0 || d >= n) return bfail(hb, NH_EINVAL, "domain index out of range");
+        const cudaMemcpyKind k = where == NH_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        const Dom<T>& D = doms[d];
+        const size_t nc = (size_t)D.P.nx * D.P.ny, nn = (size_t)(D.P.nx + 1) * (D.P.ny + 1);
+        cudaStream_t s = hb->s;
+        if (eta) cudaMemcpyAsync(eta, B.eta + D.coff, nc * sizeof(T), k, s);
+        if (q1) cudaMemcpyAsync(q1, B.q1 + D.coff, nc * sizeof(T), k, s);
+        if (q2) cudaMemcpyAsync(q2, B.q2 + D.coff, nc * sizeof(T), k, s);
+        if (w) cudaMemcpyAsync(w, B.w + D.noff, nn * sizeof(T), k, s);
+        if (p) cudaMemcpyAsync(p, B.p + D.noff, nn * sizeof(T), k, s);
+        cudaMemcpyAsync(h_ds + d, d_ds + d, sizeof(DomState), cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return bcuda(hb, e, "nh_batch_get_state");
+        if (t) *t = h_ds[d].t;
+        return NH_OK;
+    }
+
+    int run(int nsteps) override
+    {
+        if (nsteps < 0) return bfail(hb, NH_EINVAL, "nsteps must be >= 0");
+        int rc;
+        if (need_lambda) {
+            if ((rc = launch_lambda()) != NH_OK) return bcuda(hb, cudaGetLastError(), "lambda");
+            need_lambda = false;
+        }
+        if ((hb->flags & NH_BATCH_AUTOTUNE) && !tuned_once) {
+            if ((rc = autotune()) != NH_OK) return rc;
+            tuned_once = true;
+            if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
+        }
+        if (tun.graph && !exec && !graph_failed) {
+            if (build_graph() != NH_OK) {
+                graph_failed = true;   // keep the message; run eagerly
+                tun.graph = 0;
+            }
+        }
+        cudaMemcpyAsync(h_ds, d_ds, n * sizeof(DomState), cudaMemcpyDeviceToHost, hb->s);
+        cudaError_t e = cudaStreamSynchronize(hb->s);
+        if (e != cudaSuccess) return bcuda(hb, e, "nh_batch_run");
+        std::vector<int> nonconv0(n);
+        for (int d = 0; d < n; ++d) nonconv0[d] = h_ds[d].nonconv;
+        for (int k = 0; k < nsteps; ++k) {
+            if (exec) {
+                if ((e = cudaGraphLaunch(exec, hb->s)) != cudaSuccess) return bcuda(hb, e, "cudaGraphLaunch");
+            } else if ((rc = step_eager()) != NH_OK) {
+                return rc;
+            }
+        }
+        cudaMemcpyAsync(h_ds, d_ds, n * sizeof(DomState), cudaMemcpyDeviceToHost, hb->s);
+        e = cudaStreamSynchronize(hb->s);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) return bcuda(hb, e, "nh_batch_run");
+        for (int d = 0; d < n; ++d)
+            if (h_ds[d].nonfinite)
+                return bfail(hb, NH_ENONFINITE, "non-finite value in domain " + std::to_string(d));
+        for (int d = 0; d < n; ++d)
+            if (h_ds[d].nonconv != nonconv0[d])
+                return bfail(hb, NH_ENOCONV, "pressure solve of domain " + std::to_string(d) +
+                                                 " stopped with status " +
+                                                 std::to_string(h_ds[d].last_status[0] != 1
+                                                                    ? h_ds[d].last_status[0]
+                                                                    : h_ds[d].last_status[1]));
+        return NH_OK;
+    }
+
+    int stats(int d, nh_stats_t* out) override
+    {
+        if (d < 0 || d >= n) return bfail(hb, NH_EINVAL, "domain index out of range");
+        kb_mass<T><<<grid_of((const void*)kb_mass<T>, kThreads, 0, nw_cell, true), kThreads, 0, hb->s>>>(
+            arena(), wl_cell, nw_cell, B.eta, B.H);
+        cudaMemcpyAsync(h_ds, d_ds, n * sizeof(DomState), cudaMemcpyDeviceToHost, hb->s);
+        cudaError_t e = cudaStreamSynchronize(hb->s);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) return bcuda(hb, e, "nh_batch_stats");
+        const DomState& s = h_ds[d];
+        std::memset(out, 0, sizeof(*out));
+        out->t = s.t;
+        out->dt = s.dt;
+        out->dt_next = s.dt;
+        out->steps = s.steps;
+        out->solver_iters = s.sweeps;
+        out->last_iters[0] = s.last_sweeps[0];
+        out->last_iters[1] = s.last_sweeps[1];
+        out->last_resid[0] = s.last_resid[0];
+        out->last_resid[1] = s.last_resid[1];
+        out->mass = s.mass;
+        out->nonfinite = s.nonfinite;
+        return NH_OK;
+    }
+
+    int get_tuning(nh_batch_tuning* out) override
+    {
+        *out = tun;
+        return NH_OK;
+    }
+
+    int set_tuning(const nh_batch_tuning* in) override
+    {
+        if (in->hyp < 0 || in->hyp >= C::nh || in->assembly < 0 || in->assembly >= C::na ||
+            in->cheb < 0 || in->cheb >= C::nc || in->persistent < 0 || in->persistent > 15)
+            return bfail(hb, NH_EINVAL, "tuning: candidate index out of range");
+        tun.hyp = in->hyp;
+        tun.assembly = in->assembly;
+        tun.cheb = in->cheb;
+        tun.persistent = in->persistent;
+        tun.graph = in->graph ? 1 : 0;
+        tun.tuned = 0;
+        tuned_once = true;   // a hand-picked choice is not re-tuned
+        graph_failed = false;
+        if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
+        return NH_OK;
+    }
+};
+
+int check_batch(int n, const nh_grid* grids, const double* const* H, const nh_params* p,
+                std::string& why)
+{
+    if (n < 1 || !grids || !H || !p) { why = "need n >= 1, grids, H and params"; return 0; }
+    if (p->precision != NH_FP64 && p->precision != NH_FP32) { why = "precision must be FP64 or FP32"; return 0; }
+    if (!(p->g > 0.0) || !(p->cfl > 0.0) || !(p->delta > 0.0) || p->hdry < 0.0 ||
+        p->manning_n < 0.0 || !(p->tol > 0.0) || p->max_iter < 1 || p->eps_dp < 0.0) {
+        why = "invalid physical or solver parameter";
+        return 0;
+    }
+    if (p->nonhydrostatic && p->solver != NH_SOLVER_CHEBYSHEV) {
+        why = "the batched form solves with NH_SOLVER_CHEBYSHEV only";
+        return 0;
+    }
+    double total = 0.0;
+    for (int d = 0; d < n; ++d) {
+        const nh_grid& g = grids[d];
+        if (!H[d]) { why = "H of domain " + std::to_string(d) + " is null"; return 0; }
+        if (g.dim != 2 || g.nx < 2 || g.ny < 2 || !(g.dx > 0.0) || !(g.dy > 0.0)) {
+            why = "domain " + std::to_string(d) + ": need dim 2, nx, ny >= 2, dx, dy > 0";
+            return 0;
+        }
+        for (int k = 0; k < 4; ++k)
+            if (g.bc[k] != NH_BC_WALL && g.bc[k] != NH_BC_OUTFLOW) { why = "bc must be WALL or OUTFLOW"; return 0; }
+        total += (double)(g.nx + 1) * (g.ny + 1);
+    }
+    if (total > 1.5e9) { why = "ensemble too large"; return 0; }
+    return 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nh_create_batch(int n, const nh_grid* grids, const double* const* H, const nh_params* params,
+                    void* stream, int flags, nh_batch** out)
+{
+    if (!out) return NH_EINVAL;
+    *out = nullptr;
+    std::string why;
+    if (!check_batch(n, grids, H, params, why)) return NH_EINVAL;
+    nh_batch* b = new nh_batch();
+    b->n = n;
+    b->grids.assign(grids, grids + n);
+    b->prm = *params;
+    b->flags = flags;
+    b->s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (!b->s) {
+        e = cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking);
+        b->s = b->own;
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return NH_ECUDA;
+    }
+    int rc;
+    if (params->precision == NH_FP32) {
+        auto* im = new BatchImpl<float>();
+        im->hb = b; im->n = n;
+        b->impl.reset(im);
+        rc = im->init(H);
+    } else {
+        auto* im = new BatchImpl<double>();
+        im->hb = b; im->n = n;
+        b->impl.reset(im);
+        rc = im->init(H);
+    }
+    if (rc != NH_OK) {
+        nh_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return NH_OK;
+}
+
+int nh_batch_set_state(nh_batch* b, int d, const void* eta, const void* q1, const void* q2,
+                       const void* w, const void* p, double t, int where)
+{
+    if (!b) return NH_EINVAL;
+    return b->impl->set_state(d, eta, q1, q2, w, p, t, where);
+}
+
+int nh_batch_get_state(nh_batch* b, int d, void* eta, void* q1, void* q2, void* w, void* p,
+                       double* t, int where)
+{
+    if (!b) return NH_EINVAL;
+    return b->impl->get_state(d, eta, q1, q2, w, p, t, where);
+}
+
+int nh_batch_run(nh_batch* b, int nsteps)
+{
+    if (!b) return NH_EINVAL;
+    return b->impl->run(nsteps);
+}
+
+int nh_batch_stats(nh_batch* b, int d, nh_stats_t* out)
+{
+    if (!b || !out) return NH_EINVAL;
+    return b->impl->stats(d, out);
+}
+
+int nh_batch_get_tuning(nh_batch* b, nh_batch_tuning* out)
+{
+    if (!b || !out) return NH_EINVAL;
+    return b->impl->get_tuning(out);
+}
+
+int nh_batch_set_tuning(nh_batch* b, const nh_batch_tuning* in)
+{
+    if (!b || !in) return NH_EINVAL;
+    return b->impl->set_tuning(in);
+}
+
+int nh_batch_candidate(int precision, int kind, int idx, int* tile_x, int* tile_y, int* threads)
+{
+    Shape s;
+    if (precision == NH_FP32) {
+        using C = Cands<float>;
+        const int lim = kind == 0 ? C::nh : kind == 1 ? C::na : kind == 2 ? C::nc : 0;
+        if (idx < 0 || idx >= lim) return NH_EINVAL;
+        s = kind == 0 ? C::hyp_shape(idx) : kind == 1 ? C::asm_shape(idx) : C::cheb_shape(idx);
+    } else if (precision == NH_FP64) {
+        using C = Cands<double>;
+        const int lim = kind == 0 ? C::nh : kind == 1 ? C::na : kind == 2 ? C::nc : 0;
+        if (idx < 0 || idx >= lim) return NH_EINVAL;
+        s = kind == 0 ? C::hyp_shape(idx) : kind == 1 ? C::asm_shape(idx) : C::cheb_shape(idx);
+    } else {
+        return NH_EINVAL;
+    }
+    if (tile_x) *tile_x = s.tx;
+    if (tile_y) *tile_y = s.ty;
+    if (threads) *threads = s.threads;
+    return NH_OK;
+}
+
+const char* nh_batch_last_error(const nh_batch* b)
+{
+    return b ? b->err.c_str() : "null batch";
+}
+
+void nh_batch_destroy(nh_batch* b)
+{
+    if (!b) return;
+    if (b->s) cudaStreamSynchronize(b->s);
+    b->impl.reset();
+    if (b->side) cudaStreamDestroy(b->side);
+    if (b->own) cudaStreamDestroy(b->own);
+    delete b;
+}
+
+}  // extern "C"

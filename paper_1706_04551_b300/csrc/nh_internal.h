@@ -42,6 +42,10 @@ struct SolveCtl {
     int sweeps;       // sweeps done in this solve
     int pad2;
     float c1f[8], c2f[8]; // FP32 copies of c1, c2 for FP32 sweeps
+    // batched form: stall test of the Chebyshev passes and the BiCGStab fallback
+    double best;      // smallest ||D^-1 r||^2 of the passes so far
+    int stale;        // passes since best improved by the stall factor
+    int fb;           // 1 while the domain's BiCGStab fallback runs
 };
 
 // Device-side per-step scalars.

@@ -42,6 +42,12 @@ class StatsT(C.Structure):
                 ("mass", C.c_double), ("nonfinite", C.c_int)]
 
 
+class BatchTuning(C.Structure):
+    _fields_ = [("hyp", C.c_int), ("assembly", C.c_int), ("cheb", C.c_int),
+                ("persistent", C.c_int), ("graph", C.c_int), ("tuned", C.c_int),
+                ("ms", C.c_double * 3)]
+
+
 class NHError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"libnh error {code}: {msg}")
@@ -52,7 +58,12 @@ _lib = None
 
 EXPORTS = ("nh_default_params", "nh_create", "nh_set_state", "nh_get_state", "nh_step",
            "nh_run", "nh_stats", "nh_last_error", "nh_destroy", "nh_profile_enable",
-           "nh_profile_read", "nh_tridiag_batched", "nh_debug_hyperbolic", "nh_debug_system")
+           "nh_profile_read", "nh_tridiag_batched", "nh_debug_hyperbolic", "nh_debug_system",
+           "nh_create_batch", "nh_batch_set_state", "nh_batch_get_state", "nh_batch_run",
+           "nh_batch_stats", "nh_batch_get_tuning", "nh_batch_set_tuning",
+           "nh_batch_candidate", "nh_batch_last_error", "nh_batch_destroy")
+
+BATCH_AUTOTUNE, BATCH_GRAPH = 1, 2
 
 # kernel classes of nh_profile_t, in enum order
 KERNELS = ("hyperbolic", "breaking", "assembly", "solve_init", "bicg_A", "bicg_B", "bicg_C",
@@ -89,6 +100,21 @@ def load():
     L.nh_tridiag_batched.argtypes = [C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, vp, vp]
     L.nh_debug_hyperbolic.argtypes = [H, C.c_double, vp, vp, vp, C.c_int]
     L.nh_debug_system.argtypes = [H, C.c_double, vp, vp, vp, C.c_int]
+    L.nh_create_batch.argtypes = [C.c_int, C.POINTER(Grid), C.POINTER(C.c_void_p),
+                                  C.POINTER(Params), vp, C.c_int, C.POINTER(H)]
+    L.nh_batch_set_state.argtypes = [H, C.c_int, vp, vp, vp, vp, vp, C.c_double, C.c_int]
+    L.nh_batch_get_state.argtypes = [H, C.c_int, vp, vp, vp, vp, vp, C.POINTER(C.c_double),
+                                     C.c_int]
+    L.nh_batch_run.argtypes = [H, C.c_int]
+    L.nh_batch_stats.argtypes = [H, C.c_int, C.POINTER(StatsT)]
+    L.nh_batch_get_tuning.argtypes = [H, C.POINTER(BatchTuning)]
+    L.nh_batch_set_tuning.argtypes = [H, C.POINTER(BatchTuning)]
+    L.nh_batch_candidate.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int),
+                                     C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.nh_batch_last_error.argtypes = [H]
+    L.nh_batch_last_error.restype = C.c_char_p
+    L.nh_batch_destroy.argtypes = [H]
+    L.nh_batch_destroy.restype = None
     _lib = L
     return L
 
@@ -247,6 +273,146 @@ class Sim:
     def close(self):
         if self._h:
             load().nh_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_candidates(precision="fp32"):
+    """Kernel-shape candidates of the batched form: {kind: [(tile_x, tile_y, threads)]}."""
+    L = load()
+    prec = FP32 if precision == "fp32" else FP64
+    out = {}
+    for kind, name in enumerate(("hyp", "assembly", "cheb")):
+        lst = []
+        while True:
+            tx, ty, th = C.c_int(), C.c_int(), C.c_int()
+            if L.nh_batch_candidate(prec, kind, len(lst), C.byref(tx), C.byref(ty),
+                                    C.byref(th)) != OK:
+                break
+            lst.append((tx.value, ty.value, th.value))
+        out[name] = lst
+    return out
+
+
+class Batch:
+    """An ensemble of independent 2D domains of uneven sizes advanced together
+    (nh_create_batch).  Hs: list of [ny][nx] still-water depths; grids share dx unless
+    `dxs` is given; bcs: one (w, e, s, n) tuple for all or one per domain."""
+
+    def __init__(self, Hs, dx=0.1, dxs=None, bcs=(WALL,) * 4, precision="fp32", stream=None,
+                 autotune=False, graph=False, **params):
+        L = load()
+        self.Hs = [np.ascontiguousarray(np.asarray(H, dtype=np.float64)) for H in Hs]
+        n = len(self.Hs)
+        self.n = n
+        self.dtype = np.float32 if precision == "fp32" else np.float64
+        grids = (Grid * n)()
+        per_bc = len(bcs) == n and not isinstance(bcs[0], int)
+        for d, H in enumerate(self.Hs):
+            ny, nx = H.shape
+            g = grids[d]
+            g.dim, g.nx, g.ny = 2, nx, ny
+            g.dx = g.dy = float(dx if dxs is None else dxs[d])
+            bc = bcs[d] if per_bc else bcs
+            for k in range(4):
+                g.bc[k] = int(bc[k])
+        self.shapes = [H.shape for H in self.Hs]
+        p = default_params()
+        p.precision = FP32 if precision == "fp32" else FP64
+        for k, v in params.items():
+            if not hasattr(p, k):
+                raise TypeError(f"unknown parameter {k}")
+            setattr(p, k, v)
+        self.params = p
+        ptrs = (C.c_void_p * n)(*[H.ctypes.data for H in self.Hs])
+        flags = (BATCH_AUTOTUNE if autotune else 0) | (BATCH_GRAPH if graph else 0)
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+        self._h = C.c_void_p()
+        rc = L.nh_create_batch(n, grids, ptrs, C.byref(p), C.c_void_p(s), flags,
+                               C.byref(self._h))
+        if rc != OK:
+            raise NHError(rc, "nh_create_batch failed")
+        self._keep = []
+
+    def _check(self, rc):
+        if rc != OK:
+            raise NHError(rc, load().nh_batch_last_error(self._h).decode())
+
+    def _arr(self, a, n):
+        if a is None:
+            return None, HOST
+        if _is_torch(a):
+            assert a.is_contiguous() and a.numel() == n
+            assert a.element_size() == np.dtype(self.dtype).itemsize
+            return C.c_void_p(a.data_ptr()), (DEVICE if a.is_cuda else HOST)
+        a = np.ascontiguousarray(np.asarray(a, dtype=self.dtype)).reshape(-1)
+        assert a.size == n, (a.size, n)
+        self._keep.append(a)
+        return C.c_void_p(a.ctypes.data), HOST
+
+    def set_state(self, d, eta, q1, q2=None, w=None, p=None, t=0.0):
+        ny, nx = self.shapes[d]
+        nc, nn = nx * ny, (nx + 1) * (ny + 1)
+        args = [self._arr(eta, nc), self._arr(q1, nc), self._arr(q2, nc), self._arr(w, nn),
+                self._arr(p, nn)]
+        wheres = {wh for ptr, wh in args if ptr is not None}
+        assert len(wheres) == 1, "mixing host and device arrays"
+        self._check(load().nh_batch_set_state(self._h, d, *[a[0] for a in args], float(t),
+                                              wheres.pop()))
+        self._keep.clear()
+
+    def get_state(self, d):
+        ny, nx = self.shapes[d]
+        out = {k: np.empty((ny, nx), self.dtype) for k in ("eta", "q1", "q2")}
+        out["w"] = np.empty((ny + 1, nx + 1), self.dtype)
+        out["p"] = np.empty((ny + 1, nx + 1), self.dtype)
+        t = C.c_double()
+        self._check(load().nh_batch_get_state(self._h, d, *[C.c_void_p(out[k].ctypes.data)
+                                                            for k in ("eta", "q1", "q2", "w",
+                                                                      "p")],
+                                              C.byref(t), HOST))
+        out["t"] = t.value
+        return out
+
+    def get_state_into(self, d, eta=None, q1=None, q2=None, w=None, p=None):
+        ny, nx = self.shapes[d]
+        nc, nn = nx * ny, (nx + 1) * (ny + 1)
+        args = [self._arr(eta, nc), self._arr(q1, nc), self._arr(q2, nc), self._arr(w, nn),
+                self._arr(p, nn)]
+        wheres = {wh for ptr, wh in args if ptr is not None}
+        where = wheres.pop() if wheres else HOST
+        self._check(load().nh_batch_get_state(self._h, d, *[a[0] for a in args], None, where))
+        self._keep.clear()
+
+    def run(self, nsteps=1):
+        self._check(load().nh_batch_run(self._h, int(nsteps)))
+
+    def stats(self, d):
+        st = StatsT()
+        self._check(load().nh_batch_stats(self._h, d, C.byref(st)))
+        return dict(t=st.t, dt=st.dt, dt_next=st.dt_next, steps=st.steps,
+                    solver_iters=st.solver_iters, last_iters=tuple(st.last_iters),
+                    last_resid=tuple(st.last_resid), mass=st.mass, nonfinite=st.nonfinite)
+
+    def tuning(self):
+        t = BatchTuning()
+        self._check(load().nh_batch_get_tuning(self._h, C.byref(t)))
+        return dict(hyp=t.hyp, assembly=t.assembly, cheb=t.cheb, persistent=t.persistent,
+                    graph=t.graph, tuned=t.tuned, ms=tuple(t.ms))
+
+    def set_tuning(self, hyp=0, assembly=0, cheb=0, persistent=0, graph=0):
+        t = BatchTuning()
+        t.hyp, t.assembly, t.cheb, t.persistent, t.graph = hyp, assembly, cheb, persistent, graph
+        self._check(load().nh_batch_set_tuning(self._h, C.byref(t)))
+
+    def close(self):
+        if self._h:
+            load().nh_batch_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

@@ -43,3 +43,33 @@ def test_create_rejects_bad_grid_without_touching_the_gpu():
     rc = L.nh_create(ctypes.byref(g), H.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                      ctypes.byref(p), None, ctypes.byref(h))
     assert rc == nh.EINVAL and not h.value
+
+
+def test_create_batch_rejects_bad_input_without_touching_the_gpu():
+    import numpy as np
+    B.build()
+    L = nh.load()
+    grids = (nh.Grid * 2)()
+    for g in grids:
+        g.dim, g.nx, g.ny, g.dx, g.dy = 2, 8, 8, 0.1, 0.1
+    H = [np.ones(64), np.ones(64)]
+    ptrs = (ctypes.c_void_p * 2)(*[h.ctypes.data for h in H])
+    p = nh.default_params()
+    h = ctypes.c_void_p()
+    # the batched form solves with the Chebyshev-scheduled Jacobi only
+    p.solver = nh.BICGSTAB
+    assert L.nh_create_batch(2, grids, ptrs, ctypes.byref(p), None, 0, ctypes.byref(h)) == nh.EINVAL
+    p.solver = nh.CHEBYSHEV
+    grids[1].dim = 1   # 2D domains only
+    assert L.nh_create_batch(2, grids, ptrs, ctypes.byref(p), None, 0, ctypes.byref(h)) == nh.EINVAL
+    assert L.nh_create_batch(0, grids, ptrs, ctypes.byref(p), None, 0, ctypes.byref(h)) == nh.EINVAL
+    assert not h.value
+
+
+def test_batch_candidates_listed():
+    B.build()
+    for prec in ("fp32", "fp64"):
+        c = nh.batch_candidates(prec)
+        assert all(len(c[k]) >= 2 for k in ("hyp", "assembly", "cheb"))
+        for tx, ty, th in c["cheb"]:
+            assert tx > 8 and ty > 8 and th in (256, 512)
