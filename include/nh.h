@@ -93,6 +93,9 @@ typedef struct {
     double last_resid[2];  /* relative residuals of those solves                         */
     double mass;           /* sum of h dx dy over all cells (FP64)                        */
     int nonfinite;         /* 1 if a non-finite value was detected                       */
+    int fallbacks;         /* Chebyshev solves finished by BiCGStab (stalled, or a system
+                              that is not diagonally dominant)                           */
+    long long fallback_iters; /* BiCGStab iterations of those (part of solver_iters)     */
 } nh_stats_t;
 
 typedef struct nh_handle nh_handle;
@@ -258,6 +261,12 @@ int nh_batch_run(nh_batch *b, int nsteps);
 
 /* Counters, time step and FP64 mass of domain d. */
 int nh_batch_stats(nh_batch *b, int d, nh_stats_t *out);
+
+/* Per-kernel-class device times of the batch (as nh_profile_enable / nh_profile_read;
+ * SOLVE_INIT and BICG_* count the BiCGStab fallback).  While profiling is on, steps run
+ * eagerly (not as a graph) so that every launch is bracketed by events. */
+int nh_batch_profile_enable(nh_batch *b, int on);
+int nh_batch_profile_read(nh_batch *b, nh_profile_t *out);
 
 /* Current kernel choice; set one by hand (disables the autotuner for this batch). */
 int nh_batch_get_tuning(nh_batch *b, nh_batch_tuning *out);

@@ -89,6 +89,8 @@ struct nh_handle {
     int last_iters[2] = {0, 0};
     double last_resid[2] = {0.0, 0.0};
     int nonfinite = 0;
+    int fallbacks = 0;
+    long long fallback_iters = 0;
     std::string err;
 };
 
@@ -341,7 +343,7 @@ struct Impl : Base {
             cudaMemcpyAsync(h_sctl, B.sctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, hd->s);
             cudaError_t e = cudaStreamSynchronize(hd->s);
             if (e != cudaSuccess) return cuda_fail(hd, e, "pressure solve");
-            if (h_sctl->status == 4) return solve2d(stage, false);   // not diagonally dominant
+            if (h_sctl->status == 4) return fallback(stage, false);   // not diagonally dominant
             if (h_sctl->done) break;
             // stagnation (rounding floor of the precision, or a spectrum the Gershgorin
             // interval does not describe): continue with BiCGStab from the current dp
@@ -350,7 +352,7 @@ struct Impl : Base {
                 const int done_sweeps = h_sctl->sweeps;
                 hd->solver_iters += done_sweeps;
                 last_cheb_passes = done_sweeps / K;
-                return solve2d(stage, true);
+                return fallback(stage, true);
             }
             batch = 2;
         }
@@ -365,6 +367,16 @@ struct Impl : Base {
                             " sweeps with scaled residual " +
                             std::to_string(hd->last_resid[stage]));
         return NH_OK;
+    }
+
+    // A Chebyshev solve handed over to BiCGStab (counted in the statistics).
+    int fallback(int stage, bool keep_dp)
+    {
+        const long long before = hd->solver_iters;
+        const int rc = solve2d(stage, keep_dp);
+        hd->fallbacks += 1;
+        hd->fallback_iters += hd->solver_iters - before;
+        return rc;
     }
 
     // BiCGStab on the correction system M dp = r0 (from dp = 0, or from the current dp when
@@ -674,6 +686,8 @@ int nh_stats(nh_handle* h, nh_stats_t* out)
     out->last_resid[0] = h->last_resid[0];
     out->last_resid[1] = h->last_resid[1];
     out->nonfinite = h->nonfinite;
+    out->fallbacks = h->fallbacks;
+    out->fallback_iters = h->fallback_iters;
     return h->impl->mass(&out->mass);
 }
 

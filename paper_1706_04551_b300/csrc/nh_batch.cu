@@ -45,7 +45,7 @@ struct Dom {
 // Per-domain bookkeeping kept on the device.
 struct DomState {
     double t, dt, lam, mass;
-    long long steps, sweeps;
+    long long steps, sweeps, bicg_iters;   // sweeps: Chebyshev sweeps + BiCGStab iterations
     double last_resid[2];
     int last_sweeps[2];
     int last_status[2];   // 1 converged, 2 cap, 3 breakdown, 4 not diagonally dominant, 5 stalled
@@ -289,6 +289,7 @@ __device__ __forceinline__ void bicg_end(SolveCtl* ctl, DomState& s, unsigned* l
     atomicSub(&loop[2], 1u);
     s.fallbacks += 1;
     s.sweeps += ctl->iter;
+    s.bicg_iters += ctl->iter;
     s.last_sweeps[stage] += ctl->iter;
     s.last_status[stage] = status;
     s.last_resid[stage] = ctl->bb > 0.0 ? sqrt(ctl->rr / ctl->bb) : 0.0;
@@ -667,6 +668,8 @@ struct BatchBase {
     virtual int run(int nsteps) = 0;
     virtual int stats(int d, nh_stats_t* out) = 0;
     virtual int get_tuning(nh_batch_tuning* out) = 0;
+    virtual int profile_enable(int on) = 0;
+    virtual int profile_read(nh_profile_t* out) = 0;
     virtual int set_tuning(const nh_batch_tuning* in) = 0;
 };
 
@@ -694,6 +697,47 @@ int bcuda(nh_batch* b, cudaError_t e, const char* where)
 {
     return bfail(b, NH_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
+
+// CUDA-event pairs around launches, summed per kernel class (nh_profile_t).
+struct BProf {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    std::vector<int> cls;
+    size_t used = 0;
+    long long launches[NH_K_COUNT] = {};
+    double ms[NH_K_COUNT] = {};
+    ~BProf()
+    {
+        for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    }
+    cudaEvent_t next()
+    {
+        if (used == pool.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+    void flush()
+    {
+        if (used == 0) return;
+        cudaEventSynchronize(pool[used - 1]);
+        for (size_t k = 0; k < cls.size(); ++k) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, pool[2 * k], pool[2 * k + 1]);
+            ms[cls[k]] += t;
+            launches[cls[k]] += 1;
+        }
+        used = 0;
+        cls.clear();
+    }
+    void reset()
+    {
+        flush();
+        for (int k = 0; k < NH_K_COUNT; ++k) { launches[k] = 0; ms[k] = 0.0; }
+    }
+};
 
 template <typename T>
 struct BatchImpl : BatchBase {
@@ -723,6 +767,19 @@ struct BatchImpl : BatchBase {
     bool tuned_once = false;
     cudaGraphExec_t exec = nullptr;
     bool graph_failed = false;
+    BProf prof;
+
+    // launch f (one kernel on stream st) between two recorded events when profiling
+    template <typename F>
+    void K_(int c, cudaStream_t st, F&& f)
+    {
+        if (!prof.on) { f(); return; }
+        if (prof.used + 2 > 16384) prof.flush();
+        cudaEventRecord(prof.next(), st);
+        f();
+        cudaEventRecord(prof.next(), st);
+        prof.cls.push_back(c);
+    }
 
     ~BatchImpl() override
     {
@@ -995,8 +1052,10 @@ struct BatchImpl : BatchBase {
 
     void bicg_init(int s, cudaStream_t st)
     {
-        kb_bicg_init<T><<<grid_of((const void*)kb_bicg_init<T>, kThreads, 0, nw_node, pers(3)), kThreads, 0, st>>>(
-            arena(), wl_node, nw_node, bivec(), s);
+        K_(NH_K_SOLVE_INIT, st, [&] {
+            kb_bicg_init<T><<<grid_of((const void*)kb_bicg_init<T>, kThreads, 0, nw_node, pers(3)), kThreads, 0, st>>>(
+                arena(), wl_node, nw_node, bivec(), s);
+        });
     }
 
     // two BiCGStab iterations (the p^ / v buffers alternate, so a pair restores them)
@@ -1004,12 +1063,18 @@ struct BatchImpl : BatchBase {
     {
         const BiVec<T> V = bivec();
         for (int parity = 0; parity < 2; ++parity) {
-            kb_bicg_A<T><<<grid_of((const void*)kb_bicg_A<T>, kThreads, 0, nw_node, pers(3)), kThreads, 0, st>>>(
-                arena(), wl_node, nw_node, V, parity, s);
-            kb_bicg_B<T><<<grid_of((const void*)kb_bicg_B<T>, kThreads, 0, nw_node, pers(3)), kThreads, 0, st>>>(
-                arena(), wl_node, nw_node, V, parity);
-            kb_bicg_C<T><<<grid_of((const void*)kb_bicg_C<T>, kThreads, 0, nw_node, pers(3)), kThreads, 0, st>>>(
-                arena(), wl_node, nw_node, V, parity, s);
+            K_(NH_K_BICG_A, st, [&] {
+                kb_bicg_A<T><<<grid_of((const void*)kb_bicg_A<T>, kThreads, 0, nw_node, pers(3)), kThreads, 0, st>>>(
+                    arena(), wl_node, nw_node, V, parity, s);
+            });
+            K_(NH_K_BICG_B, st, [&] {
+                kb_bicg_B<T><<<grid_of((const void*)kb_bicg_B<T>, kThreads, 0, nw_node, pers(3)), kThreads, 0, st>>>(
+                    arena(), wl_node, nw_node, V, parity);
+            });
+            K_(NH_K_BICG_C, st, [&] {
+                kb_bicg_C<T><<<grid_of((const void*)kb_bicg_C<T>, kThreads, 0, nw_node, pers(3)), kThreads, 0, st>>>(
+                    arena(), wl_node, nw_node, V, parity, s);
+            });
         }
     }
 
@@ -1017,15 +1082,17 @@ struct BatchImpl : BatchBase {
     void pre_solve(int s)
     {
         const nh_params& q = hb->prm;
-        hyp(s, tun.hyp, pers(0));
+        K_(NH_K_HYPERBOLIC, hb->s, [&] { hyp(s, tun.hyp, pers(0)); });
         if (q.breaking) {
             const T b = s == 0 ? T(1) : T(0.5);
-            kb_break<T><<<grid_of((const void*)kb_break<T>, kThreads, 0, nw_cell, pers(3)), kThreads, 0, hb->s>>>(
-                arena(), wl_cell, nw_cell, B.etas, B.q1s, B.q2s, B.H, b, B.q1k, B.q2k);
+            K_(NH_K_BREAKING, hb->s, [&] {
+                kb_break<T><<<grid_of((const void*)kb_break<T>, kThreads, 0, nw_cell, pers(3)), kThreads, 0, hb->s>>>(
+                    arena(), wl_cell, nw_cell, B.etas, B.q1s, B.q2s, B.H, b, B.q1k, B.q2k);
+            });
         }
         cudaMemsetAsync(d_loop, 0, 4 * sizeof(unsigned), hb->s);
         if (q.nonhydrostatic) cudaMemsetAsync(B.dp, 0, nnode * sizeof(T), hb->s);
-        assembly(s, tun.assembly, pers(1));
+        K_(NH_K_ASSEMBLY, hb->s, [&] { assembly(s, tun.assembly, pers(1)); });
     }
 
     void post_solve(int s)
@@ -1036,9 +1103,11 @@ struct BatchImpl : BatchBase {
         T* bo = s == 0 ? B.q21 : B.q2;
         T* wo = s == 0 ? B.w1 : B.w;
         const T b = s == 0 ? T(1) : T(0.5);
-        kb_corr<T><<<grid_of((const void*)kb_corr<T>, kThreads, 0, nw_node, pers(3)), kThreads, 0, hb->s>>>(
-            arena(), wl_node, nw_node, B.etas, B.H, B.q1k, B.q2k, B.ws, B.p, B.dp, B.palt, b,
-            q.nonhydrostatic ? 1 : 0, eo, ao, bo, wo, s == 1 ? 1 : 0);
+        K_(NH_K_CORRECTION, hb->s, [&] {
+            kb_corr<T><<<grid_of((const void*)kb_corr<T>, kThreads, 0, nw_node, pers(3)), kThreads, 0, hb->s>>>(
+                arena(), wl_node, nw_node, B.etas, B.H, B.q1k, B.q2k, B.ws, B.p, B.dp, B.palt, b,
+                q.nonhydrostatic ? 1 : 0, eo, ao, bo, wo, s == 1 ? 1 : 0);
+        });
         std::swap(B.p, B.palt);
     }
 
@@ -1050,7 +1119,8 @@ struct BatchImpl : BatchBase {
         int batch = 4;
         cudaError_t e;
         for (;;) {
-            for (int k = 0; k < batch; ++k) cheb_pass(s, tun.cheb, pers(2), hb->s);
+            for (int k = 0; k < batch; ++k)
+                K_(NH_K_CHEB_PASS, hb->s, [&] { cheb_pass(s, tun.cheb, pers(2), hb->s); });
             passes += batch;
             cudaMemcpyAsync(h_loop, d_loop, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, hb->s);
             if ((e = cudaStreamSynchronize(hb->s)) != cudaSuccess) return bcuda(hb, e, "batched pressure solve");
@@ -1300,7 +1370,7 @@ struct BatchImpl : BatchBase {
             tuned_once = true;
             if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
         }
-        if (tun.graph && !exec && !graph_failed) {
+        if (tun.graph && !exec && !graph_failed && !prof.on) {
             if (build_graph() != NH_OK) {
                 graph_failed = true;   // keep the message; run eagerly
                 tun.graph = 0;
@@ -1312,7 +1382,7 @@ struct BatchImpl : BatchBase {
         std::vector<int> nonconv0(n);
         for (int d = 0; d < n; ++d) nonconv0[d] = h_ds[d].nonconv;
         for (int k = 0; k < nsteps; ++k) {
-            if (exec) {
+            if (exec && !prof.on) {
                 if ((e = cudaGraphLaunch(exec, hb->s)) != cudaSuccess) return bcuda(hb, e, "cudaGraphLaunch");
             } else if ((rc = step_eager()) != NH_OK) {
                 return rc;
@@ -1357,6 +1427,22 @@ struct BatchImpl : BatchBase {
         out->last_resid[1] = s.last_resid[1];
         out->mass = s.mass;
         out->nonfinite = s.nonfinite;
+        out->fallbacks = s.fallbacks;
+        out->fallback_iters = s.bicg_iters;
+        return NH_OK;
+    }
+
+    int profile_enable(int on) override
+    {
+        prof.reset();
+        prof.on = on != 0;
+        return NH_OK;
+    }
+
+    int profile_read(nh_profile_t* out) override
+    {
+        prof.flush();
+        for (int k = 0; k < NH_K_COUNT; ++k) { out->launches[k] = prof.launches[k]; out->ms[k] = prof.ms[k]; }
         return NH_OK;
     }
 
@@ -1520,6 +1606,18 @@ int nh_batch_candidate(int precision, int kind, int idx, int* tile_x, int* tile_
     if (tile_y) *tile_y = s.ty;
     if (threads) *threads = s.threads;
     return NH_OK;
+}
+
+int nh_batch_profile_enable(nh_batch* b, int on)
+{
+    if (!b) return NH_EINVAL;
+    return b->impl->profile_enable(on);
+}
+
+int nh_batch_profile_read(nh_batch* b, nh_profile_t* out)
+{
+    if (!b || !out) return NH_EINVAL;
+    return b->impl->profile_read(out);
 }
 
 const char* nh_batch_last_error(const nh_batch* b)

@@ -39,7 +39,8 @@ class StatsT(C.Structure):
     _fields_ = [("t", C.c_double), ("dt", C.c_double), ("dt_next", C.c_double),
                 ("steps", C.c_longlong), ("solver_iters", C.c_longlong),
                 ("last_iters", C.c_int * 2), ("last_resid", C.c_double * 2),
-                ("mass", C.c_double), ("nonfinite", C.c_int)]
+                ("mass", C.c_double), ("nonfinite", C.c_int), ("fallbacks", C.c_int),
+                ("fallback_iters", C.c_longlong)]
 
 
 class BatchTuning(C.Structure):
@@ -61,7 +62,8 @@ EXPORTS = ("nh_default_params", "nh_create", "nh_set_state", "nh_get_state", "nh
            "nh_profile_read", "nh_tridiag_batched", "nh_debug_hyperbolic", "nh_debug_system",
            "nh_create_batch", "nh_batch_set_state", "nh_batch_get_state", "nh_batch_run",
            "nh_batch_stats", "nh_batch_get_tuning", "nh_batch_set_tuning",
-           "nh_batch_candidate", "nh_batch_last_error", "nh_batch_destroy")
+           "nh_batch_candidate", "nh_batch_last_error", "nh_batch_destroy",
+           "nh_batch_profile_enable", "nh_batch_profile_read")
 
 BATCH_AUTOTUNE, BATCH_GRAPH = 1, 2
 
@@ -115,6 +117,8 @@ def load():
     L.nh_batch_last_error.restype = C.c_char_p
     L.nh_batch_destroy.argtypes = [H]
     L.nh_batch_destroy.restype = None
+    L.nh_batch_profile_enable.argtypes = [H, C.c_int]
+    L.nh_batch_profile_read.argtypes = [H, C.POINTER(ProfileT)]
     _lib = L
     return L
 
@@ -244,7 +248,8 @@ class Sim:
         self._check(load().nh_stats(self._h, C.byref(st)))
         return dict(t=st.t, dt=st.dt, dt_next=st.dt_next, steps=st.steps,
                     solver_iters=st.solver_iters, last_iters=tuple(st.last_iters),
-                    last_resid=tuple(st.last_resid), mass=st.mass, nonfinite=st.nonfinite)
+                    last_resid=tuple(st.last_resid), mass=st.mass, nonfinite=st.nonfinite,
+                    fallbacks=st.fallbacks, fallback_iters=st.fallback_iters)
 
     def profile(self, on=True):
         """Record CUDA events around every kernel launch (resets the counters)."""
@@ -397,7 +402,17 @@ class Batch:
         self._check(load().nh_batch_stats(self._h, d, C.byref(st)))
         return dict(t=st.t, dt=st.dt, dt_next=st.dt_next, steps=st.steps,
                     solver_iters=st.solver_iters, last_iters=tuple(st.last_iters),
-                    last_resid=tuple(st.last_resid), mass=st.mass, nonfinite=st.nonfinite)
+                    last_resid=tuple(st.last_resid), mass=st.mass, nonfinite=st.nonfinite,
+                    fallbacks=st.fallbacks, fallback_iters=st.fallback_iters)
+
+    def profile(self, on=True):
+        """Record CUDA events around every kernel launch (steps then run eagerly)."""
+        self._check(load().nh_batch_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self):
+        pr = ProfileT()
+        self._check(load().nh_batch_profile_read(self._h, C.byref(pr)))
+        return {k: (pr.launches[i], pr.ms[i]) for i, k in enumerate(KERNELS)}
 
     def tuning(self):
         t = BatchTuning()

@@ -66,6 +66,19 @@ def test_batch_fp64_matches_oracle_per_domain():
         assert rel_q(g["q1"], g["q2"], q1, q2) < 1e-10, d
         assert rel(g["p"], p) < 1e-10, d
         assert abs(g["t"] - t) <= 1e-12 * t and b.stats(d)["steps"] == 8
+    # the steep small-domain systems fail the Gershgorin test: BiCGStab finished those
+    assert sum(b.stats(d)["fallbacks"] for d in range(len(wls))) > 0
+
+
+def test_batch_profile_counts_launches():
+    wls = small_members()
+    b = make_batch(wls, "fp32", graph=True)
+    b.profile(True)
+    b.run(1)
+    pr = b.profile_read()
+    b.profile(False)
+    assert pr["hyperbolic"][0] == 2 and pr["assembly"][0] == 2 and pr["correction"][0] == 2
+    assert pr["cheb_pass"][0] >= 2 and all(v[1] >= 0 for v in pr.values())
 
 
 def test_batch_fp32_matches_oracle_and_single_domain():
