@@ -204,6 +204,110 @@ ENSEMBLE_DESC = ("ensemble of 256 independent 2D domains FP32, sides drawn from 
                  "autotuned kernel shapes")
 
 
+ADJOINT_DESC = ("adjoint_2d 512x512 dx=0.1 m walls, Gaussian-sum depth 0.3-0.8 m, hump "
+                "A=0.05 m sigma=3 m; J = sum over 2000 fixed-dt steps and 16 gauges of the "
+                "squared eta misfit to a target run (bathymetry + seeded 0.02 m Gaussian); "
+                "gradient w.r.t. H and eta0 by the hand-written adjoint (frozen-limiter "
+                "linearisation) with checkpoints every 100 steps")
+
+
+def run_adjoint(args, torch, ws, rank, local, dist):
+    """Forward + adjoint of the gauge misfit: value = forward Mcell-steps/s (FP32), plus the
+    adjoint/forward device-time ratio and the gradient's error (FP32 against FP64, FP64
+    against central differences of the FP64 forward)."""
+    from paper_1706_04551_b300 import inputs
+    from paper_1706_04551_b300.adjoint import gauge_series, misfit
+    nsteps = int(os.environ.get("NH_ADJ_STEPS", "2000"))
+    nexact = int(os.environ.get("NH_ADJ_EXACT_STEPS", "100"))
+    wl = inputs.adjoint_2d(n=512)
+    gauges = [tuple(int(v) for v in g) for g in wl.extra["gauges"]]
+    h0 = wl.eta + wl.H
+    dt = 0.9 / float(np.max(2 * np.sqrt(9.81 * h0) / wl.dx))   # CFL step of U0 (at rest)
+    T = lambda a: torch.tensor(a, dtype=torch.float64)
+    kw = dict(dx=wl.dx, dt=dt, nsteps=nsteps, gauges=gauges, checkpoint=100,
+              adjoint_frozen_limiter=1)
+    with torch.no_grad():
+        target = gauge_series(T(wl.extra["H_target"]), T(wl.eta), precision="fp64",
+                              tol=1e-12, **kw)
+
+    def grad(precision, tol, kwx=None, prof=False):
+        kk = kw if kwx is None else kwx
+        H, e0 = T(wl.H).requires_grad_(True), T(wl.eta).requires_grad_(True)
+        st = {"profile": prof}
+        J = misfit(gauge_series(H, e0, precision=precision, tol=tol, stats=st, **kk),
+                   target[:kk["nsteps"]])
+        J.backward()
+        return float(J.detach()), H.grad.numpy(), e0.grad.numpy(), st
+
+    for _ in range(max(0, args.warmup - 2)):
+        with torch.no_grad():
+            gauge_series(T(wl.H), T(wl.eta), precision="fp32", tol=1e-5, **dict(kw, nsteps=20))
+    with Clocks(local) as clk:
+        J32, gH32, ge32, st32 = grad("fp32", 1e-5)
+    J64, gH64, ge64, st64 = grad("fp64", 1e-12)
+    _, _, _, stp = grad("fp32", 1e-5, prof=True)   # per-kernel times (event-bracketed run)
+    # exact derivative on a horizon where it stays meaningful
+    kwe = dict(kw, nsteps=nexact, adjoint_frozen_limiter=0)
+    Je, gHe, gee, ste = grad("fp64", 1e-12, kwe)
+
+    def Jf(HH, ee):
+        with torch.no_grad():
+            return float(misfit(gauge_series(T(HH), T(ee), precision="fp64", tol=1e-12, **kw),
+                                target))
+
+    n = wl.nx
+    y, x = np.mgrid[0:n, 0:n] / float(n)
+    d = np.sin(2 * 3.1 * x + 0.4) * np.cos(2.3 * y + 1.7)
+    eps = 1e-4
+    fdH = (Jf(wl.H + eps * d, wl.eta) - Jf(wl.H - eps * d, wl.eta)) / (2 * eps)
+    fde = (Jf(wl.H, wl.eta + eps * d) - Jf(wl.H, wl.eta - eps * d)) / (2 * eps)
+
+    def Jfe(HH, ee):
+        with torch.no_grad():
+            return float(misfit(gauge_series(T(HH), T(ee), precision="fp64", tol=1e-12, **kwe),
+                                target[:nexact]))
+
+    fd_exact = {}
+    for e_ in (1e-4, 1e-5):
+        fd_exact[str(e_)] = {
+            "H": (Jfe(wl.H + e_ * d, wl.eta) - Jfe(wl.H - e_ * d, wl.eta)) / (2 * e_),
+            "eta0": (Jfe(wl.H, wl.eta + e_ * d) - Jfe(wl.H, wl.eta - e_ * d)) / (2 * e_)}
+    kshare = lambda kd: {k: {"launches": v[0], "ms": v[1]} for k, v in kd.items() if v[0]}
+    relinf = lambda a, b: float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+    cells = n * n
+    value = cells * nsteps / (st32["forward_ms"] / 1e3) / 1e6
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": nsteps,
+            "warmup": args.warmup, "ms_per_step": st32["forward_ms"] / nsteps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": ADJOINT_DESC, "cells": cells, "dt": dt,
+                       "l2": "state 6 MB (fits in L2); checkpoints + tapes 1.6 GB"},
+            "adjoint": {
+                "forward_ms": st32["forward_ms"], "backward_ms": st32["backward_ms"],
+                "adjoint_over_forward": st32["backward_ms"] / st32["forward_ms"],
+                "fp64_adjoint_over_forward": st64["backward_ms"] / st64["forward_ms"],
+                "J_fp32": J32, "J_fp64": J64,
+                "fp32_vs_fp64_relinf": {"dJ_dH": relinf(gH32, gH64), "dJ_deta0": relinf(ge32, ge64)},
+                "fp64_vs_central_fd": {
+                    "eps": eps,
+                    "H": {"adjoint": float((gH64 * d).sum()), "fd": fdH,
+                          "rel": abs(float((gH64 * d).sum()) - fdH) / abs(fdH)},
+                    "eta0": {"adjoint": float((ge64 * d).sum()), "fd": fde,
+                             "rel": abs(float((ge64 * d).sum()) - fde) / abs(fde)}},
+                "linearisation": "frozen limiter (exact branch derivative grows by a grid-scale mode)",
+                "exact": {"steps": nexact, "adjoint_over_forward": ste["backward_ms"] / ste["forward_ms"],
+                          "adjoint_H": float((gHe * d).sum()), "adjoint_eta0": float((gee * d).sum()),
+                          "max_abs_dJ_deta0": float(np.abs(gee).max()), "central_fd": fd_exact},
+                "forward_kernels": kshare(stp["forward_kernels"]),
+                "backward_kernels": kshare(stp["backward_kernels"])},
+            "clocks": clk.summary(),
+            "e2e": None,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def run_ensemble(args, torch, ws, rank, local, dist):
     """Batched form: 256 uneven domains advanced together (graph + autotuned shapes)."""
     from paper_1706_04551_b300 import inputs, nh
@@ -347,8 +451,9 @@ def main():
     from paper_1706_04551_b300 import build as nhbuild
     from paper_1706_04551_b300 import nh
     nhbuild.build()
-    if args.workload == "ensemble_256":
-        run_ensemble(args, torch, ws, rank, local, dist)
+    if args.workload in ("ensemble_256", "adjoint_512"):
+        (run_ensemble if args.workload == "ensemble_256" else run_adjoint)(
+            args, torch, ws, rank, local, dist)
         if dist:
             dist.destroy_process_group()
         return

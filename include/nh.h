@@ -37,6 +37,8 @@
 #ifndef NH_H
 #define NH_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -81,6 +83,8 @@ typedef struct {
     double fixed_dt;    /* > 0: nh_run uses this step instead of Eq. (23)                */
     double eps_dp;      /* > 0 (Chebyshev): stop on ||p^(k+1) - p^(k)||_inf < eps_dp, the
                            criterion of Eq. (32), instead of the residual test            */
+    int adjoint_frozen_limiter; /* nh_adjoint_step: 0 = exact derivative of the step; 1 =
+                           reconstruction linearised with the limiter ratio held fixed   */
 } nh_params;
 
 typedef struct {
@@ -151,6 +155,9 @@ enum {
     NH_K_CHEB_PASS,       /* Chebyshev-scheduled Jacobi: K sweeps per launch             */
     NH_K_TRIDIAG,         /* 1D batched tridiagonal solve                               */
     NH_K_CORRECTION,      /* correction of q and w, Eq. (23) rate                        */
+    NH_K_ADJ_HYPERBOLIC,  /* adjoint: hyperbolic step (faces, cells)                     */
+    NH_K_ADJ_ASSEMBLY,    /* adjoint: transposed rows, assembly / solve terms            */
+    NH_K_ADJ_CORRECTION,  /* adjoint: correction terms                                   */
     NH_K_COUNT
 };
 
@@ -200,6 +207,41 @@ int nh_tridiag_batched(int n, int rows, int precision, const void *a, const void
  * codes as nh_tridiag_batched. */
 int nh_tridiag_batched_noalloc(int n, int rows, int precision, const void *a, const void *b,
                                const void *c, const void *d, void *x, void *stream);
+
+/* ---- adjoint (reverse-mode derivative) of nh_step ----
+ *
+ * The paper has no adjoint; these entry points differentiate the discrete 2D step that
+ * nh_step takes (Sec. 5 / App. A: the Eq. (30) hyperbolic update with MUSCL-minmod and the
+ * PVM-HLL fluctuations of Eqs. (18)-(19), the pressure system of Eqs. (36)-(41) solved
+ * exactly (the adjoint solves the transposed system with the handle's solver and tol; a
+ * Chebyshev solve that stops improving at the precision's rounding floor is accepted there),
+ * and the correction), for a fixed dt.  Limits: 2D handles with the non-hydrostatic step
+ * on, no friction (manning_n = 0) and no breaking; minmod, min / max and |.| are
+ * differentiated along the branch the forward takes, and depth clamps are not
+ * differentiated (states should stay wet).
+ *
+ * Use: nh_step_taped records what the reverse needs of one step into `tape` (device
+ * memory of nh_tape_bytes bytes, 256-byte aligned, in the handle's precision); later,
+ * nh_adjoint_step(tape) maps the adjoint of the state after that step to the adjoint of
+ * the state before it.  Checkpointing is the caller's: keep the state every K steps
+ * (nh_get_state), and before reversing a segment restore it (nh_set_state with p) and
+ * retake its K steps with tapes. */
+
+/* Bytes of one step's tape (15 state-sized arrays). */
+size_t nh_tape_bytes(nh_handle *h);
+
+/* nh_step (dt <= 0: the Eq. (23) step) that also writes the tape.  2D only. */
+int nh_step_taped(nh_handle *h, double dt, void *tape, double *dt_taken);
+
+/* Reverse of the taped step of size dt.  eta_bar, q1_bar, q2_bar ([ny][nx]) and w_bar
+ * ([ny+1][nx+1]), device memory in the handle's precision: on entry the adjoint of
+ * (eta, q1, q2, w) after the step, on return the adjoint of the state before it.  H_bar
+ * ([ny][nx]) accumulates (+=) the derivative with respect to the still-water depth H.
+ * p does not carry an adjoint (the solve is exact, so p^{n+1} does not depend on p^n).
+ * Returns NH_EINVAL outside the limits above, NH_ENOCONV when a transposed solve does not
+ * converge. */
+int nh_adjoint_step(nh_handle *h, double dt, const void *tape, void *eta_bar, void *q1_bar,
+                    void *q2_bar, void *w_bar, void *H_bar);
 
 /* ---- ensembles: many independent 2D domains of uneven sizes advanced together ----
  *

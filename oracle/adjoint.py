@@ -47,6 +47,7 @@ class Cfg2:
     g: float = 9.81
     delta: float = 1e-5
     hdry: float = 1e-5
+    frozen_limiter: bool = False   # derivative with the limiter ratio held fixed (see slope())
 
 
 def desing(h, q, delta):
@@ -63,6 +64,20 @@ def minmod(a, b):
     lo = torch.where(a < b, a, b)
     hi = torch.where(a > b, a, b)
     return torch.where(pos, lo, torch.where(neg, hi, torch.zeros_like(a)))
+
+
+def slope(c: Cfg2, cm, c0, cp):
+    """MUSCL slope minmod(c0 - cm, cp - c0).  Exact derivative by default; with
+    c.frozen_limiter the derivative is that of phi * (cp - cm) / 2 with the ratio
+    phi = slope / ((cp - cm) / 2) held at its value (0 where the centred difference is 0),
+    a linearisation without the unlimited one-sided branches."""
+    s = minmod(c0 - cm, cp - c0)
+    if not c.frozen_limiter:
+        return s
+    cc = 0.5 * (cp - cm)
+    nz = (cc != 0) & (s != 0)
+    phi = torch.where(nz, s / torch.where(nz, cc, torch.ones_like(cc)), torch.zeros_like(s))
+    return s.detach() + phi.detach() * (cc - cc.detach())
 
 
 def pad_cells(c: Cfg2, v, px, py):
@@ -140,7 +155,7 @@ def hyperbolic(c: Cfg2, H, h, q1, q2, dt):
     xE, xW = [], []
     for f, v in enumerate(fld):
         c0, cm, cp = v[rows, 1:nx + 3], v[rows, 0:nx + 2], v[rows, 2:nx + 4]
-        s = minmod(c0 - cm, cp - c0)
+        s = slope(c, cm, c0, cp)
         if f == 1:
             s = torch.where(dry, torch.zeros_like(s), s)
         xE.append(c0 + 0.5 * s)
@@ -152,7 +167,7 @@ def hyperbolic(c: Cfg2, H, h, q1, q2, dt):
     yN, yS = [], []
     for f, v in enumerate(fld):
         c0, cm, cp = v[1:ny + 3, cols], v[0:ny + 2, cols], v[2:ny + 4, cols]
-        s = minmod(c0 - cm, cp - c0)
+        s = slope(c, cm, c0, cp)
         if f == 1:
             s = torch.where(dry, torch.zeros_like(s), s)
         yN.append(c0 + 0.5 * s)

@@ -8,7 +8,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libnh.so")
-SOURCES = ["nh_kernels.cu", "nh_api.cu", "nh_tridiag.cu", "nh_batch.cu"]
+SOURCES = ["nh_kernels.cu", "nh_api.cu", "nh_tridiag.cu", "nh_batch.cu", "nh_adjoint.cu"]
 HEADERS = ["nh_internal.h", "nh_device.cuh", os.path.join("..", "..", "include", "nh.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",

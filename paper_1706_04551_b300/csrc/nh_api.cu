@@ -33,6 +33,10 @@ struct Base {
     virtual int debug_system(double dt, const void* x, void* rhs, void* mx, int where) = 0;
     virtual int profile_enable(int on) = 0;
     virtual int profile_read(nh_profile_t* out) = 0;
+    virtual size_t tape_bytes() = 0;
+    virtual int step_taped(double dt, void* tape) = 0;
+    virtual int adjoint_step(double dt, const void* tape, void* eb, void* a1b, void* a2b,
+                             void* wb, void* Hb) = 0;
 };
 
 // Event pairs around kernel launches, accumulated per kernel class.
@@ -352,6 +356,12 @@ struct Impl : Base {
                 const int done_sweeps = h_sctl->sweeps;
                 hd->solver_iters += done_sweeps;
                 last_cheb_passes = done_sweeps / K;
+                if (accept_stall) {   // adjoint solves: the precision's floor is accepted
+                    hd->last_iters[stage] = done_sweeps;
+                    hd->last_resid[stage] =
+                        h_sctl->bdb > 0.0 ? std::sqrt(h_sctl->rr / h_sctl->bdb) : 0.0;
+                    return NH_OK;
+                }
                 return fallback(stage, true);
             }
             batch = 2;
@@ -494,14 +504,47 @@ struct Impl : Base {
         return NH_OK;
     }
 
-    int step(double dtd) override
+    int step(double dtd) override { return step_impl(dtd, nullptr); }
+
+    // ---- tape of one step for the adjoint: U^n, U1, the stage-1 q* and p, eta^{n+1}, the
+    // stage-2 q* and p (15 arrays, each starting on a 256-byte boundary)
+    size_t padded(size_t n) const
+    {
+        const size_t al = 256 / sizeof(T);
+        return (n + al - 1) / al * al;
+    }
+    static bool tape_is_node(int k) { return k == 3 || k == 7 || k == 10 || k == 14; }
+    T* tape_at(void* tape, int k) const
+    {
+        size_t off = 0;
+        for (int j = 0; j < k; ++j) off += padded(tape_is_node(j) ? nn : nc);
+        return static_cast<T*>(tape) + off;
+    }
+    size_t tape_bytes() override { return (11 * padded(nc) + 4 * padded(nn)) * sizeof(T); }
+    void tcopy(void* tape, int k, const T* src)
+    {
+        cudaMemcpyAsync(tape_at(tape, k), src, (tape_is_node(k) ? nn : nc) * sizeof(T),
+                        cudaMemcpyDeviceToDevice, hd->s);
+    }
+    int step_taped(double dtd, void* tape) override { return step_impl(dtd, tape); }
+
+    int step_impl(double dtd, void* tape)
     {
         const T dt = (T)dtd;
         cudaMemsetAsync(&B.stctl->clamped, 0, sizeof(int), hd->s);
+        if (tape) { tcopy(tape, 0, B.eta); tcopy(tape, 1, B.q1); tcopy(tape, 2, B.q2); tcopy(tape, 3, B.w); }
         int rc1 = dim == 2 ? stage2d(0, dt) : stage1d(0, dt);
         if (rc1 != NH_OK && rc1 != NH_ENOCONV) return rc1;
+        if (tape) {
+            tcopy(tape, 4, B.eta1); tcopy(tape, 5, B.q11); tcopy(tape, 6, B.q21); tcopy(tape, 7, B.w1);
+            tcopy(tape, 8, B.q1k); tcopy(tape, 9, B.q2k); tcopy(tape, 10, B.p);
+        }
         int rc2 = dim == 2 ? stage2d(1, dt) : stage1d(1, dt);
         if (rc2 != NH_OK && rc2 != NH_ENOCONV) return rc2;
+        if (tape) {
+            tcopy(tape, 11, B.eta); tcopy(tape, 12, B.q1k); tcopy(tape, 13, B.q2k);
+            tcopy(tape, 14, B.p);
+        }
         cudaMemcpyAsync(h_stctl, B.stctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, hd->s);
         cudaError_t e = cudaStreamSynchronize(hd->s);
         if (e != cudaSuccess) return cuda_fail(hd, e, "nh_step");
@@ -513,6 +556,148 @@ struct Impl : Base {
         }
         return rc1 != NH_OK ? rc1 : rc2;
     }
+
+    // ---- adjoint of one step (reverse of the two stages; see nh_adjoint.cu)
+    T *aEs = nullptr, *aA1 = nullptr, *aA2 = nullptr, *aHh = nullptr, *aSb = nullptr;
+    T *aGh = nullptr, *aGe = nullptr, *aGu = nullptr, *aGv = nullptr;
+    T *aE1 = nullptr, *aQ11 = nullptr, *aQ21 = nullptr, *aW1 = nullptr;
+    T *aE0 = nullptr, *aQ10 = nullptr, *aQ20 = nullptr, *aW0 = nullptr;
+    T *tW = nullptr, *tE = nullptr, *tS = nullptr, *tN = nullptr;
+
+    int adjoint_alloc()
+    {
+        if (aEs) return NH_OK;
+        int rc = NH_OK;
+#define A(ptr, n) if ((rc = alloc(&(ptr), (n))) != NH_OK) return rc
+        A(aEs, nc); A(aA1, nc); A(aA2, nc); A(aHh, nc); A(aSb, nc);
+        A(aGh, nc); A(aGe, nc); A(aGu, nc); A(aGv, nc);
+        A(aE1, nc); A(aQ11, nc); A(aQ21, nc); A(aW1, nn);
+        A(aE0, nc); A(aQ10, nc); A(aQ20, nc); A(aW0, nn);
+        A(tW, nn); A(tE, nn); A(tS, nn); A(tN, nn);
+#undef A
+        return NH_OK;
+    }
+
+    // Transposed solve M^T lambda = B.rhs into B.dp with the handle's solver.
+    int solve_transposed(int stage)
+    {
+        const nh_params& q = hd->prm;
+        const int cheb = q.solver == NH_SOLVER_CHEBYSHEV;
+        K_(NH_K_ADJ_ASSEMBLY, [&] {
+            launch_transpose<T>(P, Ln, B, B.rhs, tW, tE, tS, tN, q.tol * q.tol, q.max_iter,
+                                cheb ? cheb_sweeps_per_pass<T>() : 0);
+        });
+        std::swap(B.cW, tW); std::swap(B.cE, tE); std::swap(B.cS, tS); std::swap(B.cN, tN);
+        accept_stall = true;
+        const int rc = cheb ? solve_cheb(stage) : solve2d(stage, false);
+        accept_stall = false;
+        std::swap(B.cW, tW); std::swap(B.cE, tE); std::swap(B.cS, tS); std::swap(B.cN, tN);
+        return rc;
+    }
+
+    // Reverse of stage s (0: a = 0, b = 1; 1: a = b = 1/2).  in*: the stage's input state,
+    // es, q1s, q2s, ps: its eta*, q*, p; o*: adjoint of its output (read); in*_b: adjoint of
+    // the input (assigned when s == 1, accumulated when s == 0); base adjoint accumulated
+    // into aE0, aQ10, aQ20, aW0.
+    int adjoint_stage(int s, T dt, const T* ein, const T* q1in, const T* q2in, const T* win,
+                      const T* wbase, const T* es, const T* q1s, const T* q2s, const T* ps,
+                      const T* eob, const T* a1ob, const T* a2ob, const T* wob, T* ein_b,
+                      T* a1in_b, T* a2in_b, T* win_b, T* Hb)
+    {
+        const nh_params& q = hd->prm;
+        const T a = s == 0 ? T(0) : T(0.5), b = s == 0 ? T(1) : T(0.5);
+        const T de = b * dt;
+        // rows of the stage's system and w* (into B.ws), exactly as in the forward
+        Bufs<T> D = B;
+        D.etas = const_cast<T*>(es); D.q1s = const_cast<T*>(q1s); D.q2s = const_cast<T*>(q2s);
+        D.q1k = D.q1s; D.q2k = D.q2s;
+        K_(NH_K_ASSEMBLY, [&] {
+            launch_asm2d<T>(P, Ln, D, win, wbase, a, b, de, 1, 0, 0.0, 1, 0, B.partials, B.sctl);
+        });
+        // p_bar, then lambda = M^-T p_bar
+        K_(NH_K_ADJ_CORRECTION, [&] { launch_adj_pbar<T>(P, Ln, es, B.H, a1ob, a2ob, wob, de, B.rhs); });
+        int rc = solve_transposed(s);
+        if (rc != NH_OK) return rc;
+        for (T* z : {aEs, aA1, aA2, aHh, aSb, aGh, aGe, aGu, aGv})
+            cudaMemsetAsync(z, 0, nc * sizeof(T), hd->s);
+        const double scale = 8.0 * (double)P.dx * (double)P.dy / (double)de;
+        K_(NH_K_ADJ_ASSEMBLY, [&] {
+            launch_adj_node<T>(P, Ln, es, B.H, q1s, q2s, B.ws, ps, B.dp, wob, scale, (double)de,
+                               (double)a, (double)b, s == 1 ? 1 : 0, aHh, aSb, aA1, aA2, win_b,
+                               aW0);
+        });
+        K_(NH_K_ADJ_CORRECTION, [&] {
+            launch_adj_cell_corr<T>(P, Lc, es, B.H, ps, eob, a1ob, a2ob, de, aEs, aHh, aSb, aA1,
+                                    aA2);
+        });
+        K_(NH_K_ADJ_CORRECTION, [&] { launch_adj_combine<T>(Lc, (long long)nc, aEs, aHh, aSb, Hb); });
+        K_(NH_K_ADJ_HYPERBOLIC, [&] {
+            launch_adj_face<T>(P, Lc, ein, q1in, q2in, B.H, aEs, aA1, aA2, b, dt,
+                               q.adjoint_frozen_limiter, aGh, aGe, aGu, aGv);
+        });
+        K_(NH_K_ADJ_HYPERBOLIC, [&] {
+            launch_adj_cell_hyp<T>(P, Lc, ein, q1in, q2in, B.H, aEs, aA1, aA2, aGh, aGe, aGu, aGv,
+                                   a, b, s == 1 ? 1 : 0, ein_b, a1in_b, a2in_b, aE0, aQ10, aQ20,
+                                   Hb);
+        });
+        (void)q;
+        return NH_OK;
+    }
+
+    int adjoint_step(double dtd, const void* tape, void* ebv, void* a1bv, void* a2bv, void* wbv,
+                     void* Hbv) override
+    {
+        const nh_params& q = hd->prm;
+        if (dim != 2 || !q.nonhydrostatic || q.breaking || q.manning_n > 0.0)
+            return fail(hd, NH_EINVAL,
+                        "nh_adjoint_step: 2D non-hydrostatic steps without friction or "
+                        "breaking only");
+        int rc = adjoint_alloc();
+        if (rc != NH_OK) return rc;
+        T* eb = static_cast<T*>(ebv);
+        T* a1b = static_cast<T*>(a1bv);
+        T* a2b = static_cast<T*>(a2bv);
+        T* wb = static_cast<T*>(wbv);
+        T* Hb = static_cast<T*>(Hbv);
+        void* tp = const_cast<void*>(tape);
+        const T dt = (T)dtd;
+        // the forward's solver statistics and polling state are left as they were
+        const long long it0 = hd->solver_iters;
+        const int li0 = hd->last_iters[0], li1 = hd->last_iters[1];
+        const double lr0 = hd->last_resid[0], lr1 = hd->last_resid[1];
+        const int lsi = last_solve_iters, lcp = last_cheb_passes;
+        const int fb0 = hd->fallbacks;
+        const long long fbi0 = hd->fallback_iters;
+        for (T* z : {aE0, aQ10, aQ20}) cudaMemsetAsync(z, 0, nc * sizeof(T), hd->s);
+        cudaMemsetAsync(aW0, 0, nn * sizeof(T), hd->s);
+        // stage 2: input U1, base U^n; its output is U^{n+1}
+        rc = adjoint_stage(1, dt, tape_at(tp, 4), tape_at(tp, 5), tape_at(tp, 6), tape_at(tp, 7),
+                           tape_at(tp, 3), tape_at(tp, 11), tape_at(tp, 12), tape_at(tp, 13),
+                           tape_at(tp, 14), eb, a1b, a2b, wb, aE1, aQ11, aQ21, aW1, Hb);
+        // stage 1: input U^n; its output is U1
+        if (rc == NH_OK)
+            rc = adjoint_stage(0, dt, tape_at(tp, 0), tape_at(tp, 1), tape_at(tp, 2),
+                               tape_at(tp, 3), tape_at(tp, 3), tape_at(tp, 4), tape_at(tp, 8),
+                               tape_at(tp, 9), tape_at(tp, 10), aE1, aQ11, aQ21, aW1, aE0, aQ10,
+                               aQ20, aW0, Hb);
+        adjoint_iters += hd->solver_iters - it0;
+        hd->solver_iters = it0;
+        hd->last_iters[0] = li0; hd->last_iters[1] = li1;
+        hd->last_resid[0] = lr0; hd->last_resid[1] = lr1;
+        last_solve_iters = lsi; last_cheb_passes = lcp;
+        hd->fallbacks = fb0; hd->fallback_iters = fbi0;
+        if (rc != NH_OK) return rc;
+        cudaMemcpyAsync(eb, aE0, nc * sizeof(T), cudaMemcpyDeviceToDevice, hd->s);
+        cudaMemcpyAsync(a1b, aQ10, nc * sizeof(T), cudaMemcpyDeviceToDevice, hd->s);
+        cudaMemcpyAsync(a2b, aQ20, nc * sizeof(T), cudaMemcpyDeviceToDevice, hd->s);
+        cudaMemcpyAsync(wb, aW0, nn * sizeof(T), cudaMemcpyDeviceToDevice, hd->s);
+        cudaError_t e = cudaStreamSynchronize(hd->s);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(hd, e, "nh_adjoint_step");
+        return NH_OK;
+    }
+    long long adjoint_iters = 0;
+    bool accept_stall = false;   // set during the adjoint's transposed solves
 
     int debug_hyp(double dtd, void* e, void* a, void* b, int where) override
     {
@@ -573,6 +758,10 @@ int check_grid(const nh_grid* g, const nh_params* p, std::string& why)
     if (p->precision != NH_FP64 && p->precision != NH_FP32) { why = "precision must be FP64 or FP32"; return 0; }
     if (p->solver != NH_SOLVER_BICGSTAB && p->solver != NH_SOLVER_CHEBYSHEV) { why = "unknown solver"; return 0; }
     if (p->eps_dp < 0.0) { why = "eps_dp must be >= 0"; return 0; }
+    if (p->adjoint_frozen_limiter != 0 && p->adjoint_frozen_limiter != 1) {
+        why = "adjoint_frozen_limiter must be 0 or 1";
+        return 0;
+    }
     return 1;
 }
 
@@ -587,6 +776,7 @@ int nh_default_params(nh_params* p)
     p->B1 = 0.15; p->B2 = 0.5; p->breaking = 0; p->nonhydrostatic = 1;
     p->solver = NH_SOLVER_CHEBYSHEV; p->tol = 1e-12; p->max_iter = 2000;
     p->precision = NH_FP64; p->fixed_dt = 0.0; p->eps_dp = 0.0;
+    p->adjoint_frozen_limiter = 0;
     return NH_OK;
 }
 
@@ -721,6 +911,35 @@ int nh_debug_hyperbolic(nh_handle* h, double dt, void* eta_out, void* q1_out, vo
 {
     if (!h || !(dt > 0.0)) return NH_EINVAL;
     return h->impl->debug_hyp(dt, eta_out, q1_out, q2_out, where);
+}
+
+size_t nh_tape_bytes(nh_handle* h)
+{
+    return h ? h->impl->tape_bytes() : 0;
+}
+
+int nh_step_taped(nh_handle* h, double dt, void* tape, double* dt_taken)
+{
+    if (!h || !tape) return NH_EINVAL;
+    if (h->grid.dim != 2) return fail(h, NH_EINVAL, "nh_step_taped: 2D only");
+    const double d = dt > 0.0 ? dt : h->dt_next;
+    if (!(d > 0.0)) return fail(h, NH_EINVAL, "no positive time step");
+    int rc = h->impl->step_taped(d, tape);
+    if (rc == NH_OK || rc == NH_ENOCONV) {
+        h->t += d;
+        h->dt_last = d;
+        h->steps += 1;
+        if (dt_taken) *dt_taken = d;
+    }
+    return rc;
+}
+
+int nh_adjoint_step(nh_handle* h, double dt, const void* tape, void* eta_bar, void* q1_bar,
+                    void* q2_bar, void* w_bar, void* H_bar)
+{
+    if (!h || !tape || !eta_bar || !q1_bar || !q2_bar || !w_bar || !H_bar || !(dt > 0.0))
+        return NH_EINVAL;
+    return h->impl->adjoint_step(dt, tape, eta_bar, q1_bar, q2_bar, w_bar, H_bar);
 }
 
 int nh_debug_system(nh_handle* h, double dt, const void* x, void* rhs_out, void* mx_out,

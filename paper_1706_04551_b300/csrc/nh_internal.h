@@ -118,6 +118,36 @@ void launch_corr2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* 
                    const T* q2k, T de, int with_p, T* eo, T* q1o, T* q2o, T* wo, int final_stage,
                    double* partials, StepCtl* st);
 
+// ---- adjoint of the 2D step (nh_adjoint.cu) ----
+template <typename T>
+void launch_adj_pbar(const Prm<T>& P, const Launch& L, const T* eta, const T* H, const T* a1o,
+                     const T* a2o, const T* wo, T de, T* pbar);
+// rows of M^T into tW..tN (coefficients of B), reductions of b, solve set-up in B.sctl
+template <typename T>
+void launch_transpose(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* b, T* tW,
+                      T* tE, T* tS, T* tN, double tol2, int max_iter, int kpass);
+template <typename T>
+void launch_adj_node(const Prm<T>& P, const Launch& L, const T* eta, const T* H, const T* q1,
+                     const T* q2, const T* ws, const T* p, const T* lam, const T* wo,
+                     double scale, double de, double a, double b, int assign_in, T* Hh, T* Sb,
+                     T* A1, T* A2, T* w_in_bar, T* w_base_bar);
+template <typename T>
+void launch_adj_cell_corr(const Prm<T>& P, const Launch& L, const T* eta, const T* H,
+                          const T* p, const T* eo_bar, const T* a1o, const T* a2o, T de, T* Es,
+                          T* Hh, T* Sb, T* A1, T* A2);
+template <typename T>
+void launch_adj_combine(const Launch& L, long long n, T* Es, const T* Hh, const T* Sb, T* Hbar);
+template <typename T>
+void launch_adj_face(const Prm<T>& P, const Launch& L, const T* eta, const T* q1, const T* q2,
+                     const T* H, const T* Es, const T* A1, const T* A2, T bfac, T dt,
+                     int frozen, T* Gh, T* Ge, T* Gu, T* Gv);
+template <typename T>
+void launch_adj_cell_hyp(const Prm<T>& P, const Launch& L, const T* eta, const T* q1,
+                         const T* q2, const T* H, const T* Es, const T* A1, const T* A2,
+                         const T* Gh, const T* Ge, const T* Gu, const T* Gv, T a, T b,
+                         int assign_in, T* ein_b, T* a1in_b, T* a2in_b, T* eb_b, T* a1b_b,
+                         T* a2b_b, T* Hbar);
+
 // ---- batched 1D ----
 template <typename T>
 void launch_hyp1d(const Prm<T>& P, const Launch& L, const T* eta, const T* q, const T* etab,

@@ -32,7 +32,8 @@ class Params(C.Structure):
                 ("hdry", C.c_double), ("manning_n", C.c_double), ("B1", C.c_double),
                 ("B2", C.c_double), ("breaking", C.c_int), ("nonhydrostatic", C.c_int),
                 ("solver", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int),
-                ("precision", C.c_int), ("fixed_dt", C.c_double), ("eps_dp", C.c_double)]
+                ("precision", C.c_int), ("fixed_dt", C.c_double), ("eps_dp", C.c_double),
+                ("adjoint_frozen_limiter", C.c_int)]
 
 
 class StatsT(C.Structure):
@@ -63,13 +64,15 @@ EXPORTS = ("nh_default_params", "nh_create", "nh_set_state", "nh_get_state", "nh
            "nh_create_batch", "nh_batch_set_state", "nh_batch_get_state", "nh_batch_run",
            "nh_batch_stats", "nh_batch_get_tuning", "nh_batch_set_tuning",
            "nh_batch_candidate", "nh_batch_last_error", "nh_batch_destroy",
-           "nh_batch_profile_enable", "nh_batch_profile_read")
+           "nh_batch_profile_enable", "nh_batch_profile_read", "nh_tape_bytes",
+           "nh_step_taped", "nh_adjoint_step")
 
 BATCH_AUTOTUNE, BATCH_GRAPH = 1, 2
 
 # kernel classes of nh_profile_t, in enum order
 KERNELS = ("hyperbolic", "breaking", "assembly", "solve_init", "bicg_A", "bicg_B", "bicg_C",
-           "cheb_pass", "tridiag", "correction")
+           "cheb_pass", "tridiag", "correction", "adj_hyperbolic", "adj_assembly",
+           "adj_correction")
 
 
 class ProfileT(C.Structure):
@@ -117,6 +120,10 @@ def load():
     L.nh_batch_last_error.restype = C.c_char_p
     L.nh_batch_destroy.argtypes = [H]
     L.nh_batch_destroy.restype = None
+    L.nh_tape_bytes.argtypes = [H]
+    L.nh_tape_bytes.restype = C.c_size_t
+    L.nh_step_taped.argtypes = [H, C.c_double, vp, C.POINTER(C.c_double)]
+    L.nh_adjoint_step.argtypes = [H, C.c_double, vp, vp, vp, vp, vp, vp]
     L.nh_batch_profile_enable.argtypes = [H, C.c_int]
     L.nh_batch_profile_read.argtypes = [H, C.POINTER(ProfileT)]
     _lib = L
@@ -274,6 +281,26 @@ class Sim:
                                            C.c_void_p(rhs.ctypes.data),
                                            C.c_void_p(mx.ctypes.data), HOST))
         return rhs, mx
+
+    # -------------------------------------------------------------- adjoint
+    def tape_bytes(self):
+        return int(load().nh_tape_bytes(self._h))
+
+    def step_taped(self, tape, dt=0.0):
+        """nh_step_taped into a device buffer (torch tensor of >= tape_bytes bytes)."""
+        d = C.c_double()
+        self._check(load().nh_step_taped(self._h, float(dt), C.c_void_p(tape.data_ptr()),
+                                         C.byref(d)))
+        return d.value
+
+    def adjoint_step(self, tape, dt, eta_bar, q1_bar, q2_bar, w_bar, H_bar):
+        """nh_adjoint_step on torch CUDA tensors (in place; H_bar accumulates)."""
+        for t in (eta_bar, q1_bar, q2_bar, w_bar, H_bar):
+            assert t.is_cuda and t.is_contiguous()
+            assert t.element_size() == np.dtype(self.dtype).itemsize
+        self._check(load().nh_adjoint_step(self._h, float(dt), C.c_void_p(tape.data_ptr()),
+                                           *[C.c_void_p(t.data_ptr()) for t in
+                                             (eta_bar, q1_bar, q2_bar, w_bar, H_bar)]))
 
     def close(self):
         if self._h:
