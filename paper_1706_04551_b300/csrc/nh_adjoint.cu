@@ -407,10 +407,11 @@ __device__ __forceinline__ void face_adjoint(const FaceIn<T>& c, T g, T hdry, co
     // ---- forward: PVM (as pvm())
     const T qnL = hL * nL, qnR = hR * nR, qtL = hL * tL, qtR = hR * tR;
     const T hb = T(0.5) * (hL + hR);
-    const T sL = sqrt(hL), sR = sqrt(hR), ss = sL + sR;
+    const T sL = qsqrt(hL), sR = qsqrt(hR), ss = sL + sR;
     const bool ssp = ss > T(0);
-    const T ub = ssp ? (nL * sL + nR * sR) / ss : T(0);
-    const T cb = sqrt(g * hb), cL = sqrt(g * hL), cR = sqrt(g * hR);
+    const T ub = ssp ? qdiv(nL * sL + nR * sR, ss) : T(0);
+    const T sg = qsqrt(g);
+    const T cb = qsqrt(g * hb), cL = sg * sL, cR = sg * sR;
     const T sl1 = ub - cb, sl2 = nL - cL;
     const bool slb = sl1 < sl2;
     const T SL = slb ? sl1 : sl2;
@@ -429,8 +430,9 @@ __device__ __forceinline__ void face_adjoint(const FaceIn<T>& c, T g, T hdry, co
         const T aSL = fabs(SL), aSR = fabs(SR);
         const T sgL = SL > T(0) ? T(1) : (SL < T(0) ? T(-1) : T(0));
         const T sgR = SR > T(0) ? T(1) : (SR < T(0) ? T(-1) : T(0));
-        const T a0 = (SR * aSL - SL * aSR) / span;
-        const T a1 = (aSR - aSL) / span;
+        const T isp = qdiv(T(1), span);
+        const T a0 = (SR * aSL - SL * aSR) * isp;
+        const T a1 = (aSR - aSL) * isp;
         const T R0 = qnR - qnL;
         const T R1 = qnR * nR - qnL * nL + g * hb * de;
         const T R2 = qnR * tR - qnL * tL;
@@ -458,8 +460,8 @@ __device__ __forceinline__ void face_adjoint(const FaceIn<T>& c, T g, T hdry, co
         T ubb = T(0), cbb = T(0), cLb = T(0), cRb = T(0);
         if (slb) { ubb += SLb; cbb -= SLb; } else { nLb += SLb; cLb -= SLb; }
         if (srb) { ubb += SRb; cbb += SRb; } else { nRb += SRb; cRb += SRb; }
-        if (cL > T(0)) hLb += cLb * g / (T(2) * cL);
-        if (cR > T(0)) hRb += cRb * g / (T(2) * cR);
+        if (sL > T(0)) hLb += cLb * sg / (T(2) * sL);
+        if (sR > T(0)) hRb += cRb * sg / (T(2) * sR);
         if (cb > T(0)) hbb += cbb * g / (T(2) * cb);
         if (ssp) {
             nLb += ubb * sL / ss;

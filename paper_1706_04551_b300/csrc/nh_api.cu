@@ -131,6 +131,8 @@ struct Impl : Base {
         for (void* p : allocs) cudaFree(p);
         if (h_sctl) cudaFreeHost(h_sctl);
         if (h_stctl) cudaFreeHost(h_stctl);
+        for (cudaEvent_t e : vt_ev)
+            if (e) cudaEventDestroy(e);
     }
 
     template <typename U>
@@ -205,6 +207,8 @@ struct Impl : Base {
 #undef A
         cudaError_t e;
         if ((e = cudaMallocHost(&h_sctl, sizeof(SolveCtl))) != cudaSuccess) return cuda_fail(hd, e, "cudaMallocHost");
+        for (cudaEvent_t& ev : vt_ev)
+            if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(hd, e, "cudaEventCreate");
         if ((e = cudaMallocHost(&h_stctl, sizeof(StepCtl))) != cudaSuccess) return cuda_fail(hd, e, "cudaMallocHost");
         cudaMemsetAsync(B.sctl, 0, sizeof(SolveCtl), h->s);
         cudaMemsetAsync(B.stctl, 0, sizeof(StepCtl), h->s);
@@ -330,24 +334,52 @@ struct Impl : Base {
 
     // Chebyshev-scheduled Jacobi (temporally blocked passes); B.p is the warm start and
     // receives the solution, B.r holds the previous iterate.
+    // After `passes` executed passes the iterate is in (v[0], v[1]) when passes is odd:
+    // make (dp, r) hold it.
+    void settle_passes(int passes)
+    {
+        if (passes & 1) { std::swap(B.dp, B.v[0]); std::swap(B.r, B.v[1]); }
+    }
+
     int solve_cheb(int stage)
     {
         const int K = cheb_sweeps_per_pass<T>();
         cudaMemsetAsync(B.r, 0, nn * sizeof(T), hd->s);
         cudaMemsetAsync(B.dp, 0, nn * sizeof(T), hd->s);
+        int passes_launched = 0;
         int batch = last_cheb_passes > 2 ? last_cheb_passes - 1 : 4;
         double best = 1e300;
         int stale = 0;
         for (;;) {
             for (int k = 0; k < batch; ++k) {
                 int rc = 0;
-                K_(NH_K_CHEB_PASS, [&] { rc = launch_cheb_pass<T>(P, hd->s, B, B.r, B.partials); });
+                // until the faster pass form is known, alternate the two (their sweeps are
+                // identical, so the solve does not depend on the choice) and time them
+                const int v = pass_variant >= 0 ? pass_variant : (vt_next++ & 1);
+                const bool timed = pass_variant < 0 && vt_used + 2 <= kVT;
+                if (timed) cudaEventRecord(vt_ev[vt_used], hd->s);
+                // pass j reads buffer pair j % 2 and writes the other
+                const bool odd = (passes_launched++ & 1) != 0;
+                T* xa = odd ? B.v[0] : B.dp;
+                T* pa = odd ? B.v[1] : B.r;
+                T* xb = odd ? B.dp : B.v[0];
+                T* pb = odd ? B.r : B.v[1];
+                K_(NH_K_CHEB_PASS, [&] {
+                    rc = launch_cheb_pass<T>(P, hd->s, B, xa, pa, xb, pb, B.partials, v);
+                });
+                if (timed) {
+                    cudaEventRecord(vt_ev[vt_used + 1], hd->s);
+                    vt_var[vt_used / 2] = v;
+                    vt_used += 2;
+                }
                 if (rc != 0) return fail(hd, NH_ECUDA, "Chebyshev pass launch failed");
             }
             cudaMemcpyAsync(h_sctl, B.sctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, hd->s);
             cudaError_t e = cudaStreamSynchronize(hd->s);
             if (e != cudaSuccess) return cuda_fail(hd, e, "pressure solve");
+            if (pass_variant < 0 && vt_used >= kVT) choose_pass_variant();
             if (h_sctl->status == 4) return fallback(stage, false);   // not diagonally dominant
+            if (h_sctl->done) settle_passes(h_sctl->sweeps / K);
             if (h_sctl->done) break;
             // stagnation (rounding floor of the precision, or a spectrum the Gershgorin
             // interval does not describe): continue with BiCGStab from the current dp
@@ -356,6 +388,8 @@ struct Impl : Base {
                 const int done_sweeps = h_sctl->sweeps;
                 hd->solver_iters += done_sweeps;
                 last_cheb_passes = done_sweeps / K;
+                // the passes launched so far all ran (the solve is not done)
+                settle_passes(passes_launched);
                 if (accept_stall) {   // adjoint solves: the precision's floor is accepted
                     hd->last_iters[stage] = done_sweeps;
                     hd->last_resid[stage] =
@@ -697,6 +731,27 @@ struct Impl : Base {
         return NH_OK;
     }
     long long adjoint_iters = 0;
+    // choice between the two Chebyshev pass forms (shared-memory or register weights)
+    static constexpr int kVT = 32;   // event slots: 16 timed passes
+    int pass_variant = -1;
+    int vt_next = 0, vt_used = 0;
+    int vt_var[kVT / 2] = {};
+    cudaEvent_t vt_ev[kVT] = {};
+    void choose_pass_variant()
+    {
+        double sum[2] = {0.0, 0.0};
+        int cnt[2] = {0, 0};
+        // the first pass of each form warms it up and is not counted
+        for (int k = 2; k < vt_used / 2; ++k) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, vt_ev[2 * k], vt_ev[2 * k + 1]) == cudaSuccess) {
+                sum[vt_var[k]] += ms;
+                cnt[vt_var[k]] += 1;
+            }
+        }
+        cudaGetLastError();
+        pass_variant = (cnt[0] && cnt[1] && sum[1] / cnt[1] < sum[0] / cnt[0]) ? 1 : 0;
+    }
     bool accept_stall = false;   // set during the adjoint's transposed solves
 
     int debug_hyp(double dtd, void* e, void* a, void* b, int where) override

@@ -199,10 +199,11 @@ kb_asm(Arena<T> A, const int2* __restrict__ wl, int nw, const T* eta, const T* H
     }
 }
 
-template <typename T, int NA, int NB, int BY, int K>
-__global__ void __launch_bounds__(32 * BY, 2)
+template <typename T, int NA, int NB, int BY, int K, bool REGW>
+__global__ void __launch_bounds__(32 * BY, REGW ? 1 : 2)
 kb_cheb(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const T* cW,
-        const T* cE, const T* cS, const T* cN, const T* rhs, T* x, T* xp, int stage)
+        const T* cE, const T* cS, const T* cN, const T* rhs, const T* xi, const T* xpi, T* xo,
+        T* xpo, int stage)
 {
     extern __shared__ unsigned char kb_cheb_smem[];
     constexpr int TX = 32 * NA - 2 * K, TY = BY * NB - 2 * K;
@@ -217,7 +218,8 @@ kb_cheb(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const T* c
         R.nx = D.P.nx; R.ny = D.P.ny;
         const int tx = cdiv(R.nx + 1, TX), nt = tx * cdiv(R.ny + 1, TY);
         T rsum, dmax;
-        cheb_tile<T, NA, NB, BY, K>(R, rhs + n, x + n, xp + n, ctl, it.y % tx, it.y / tx,
+        cheb_tile<T, NA, NB, BY, K, REGW>(R, rhs + n, xi + n, xpi + n, xo + n, xpo + n, ctl,
+                                          it.y % tx, it.y / tx,
                                     reinterpret_cast<T*>(kb_cheb_smem), rsum, dmax);
         double acc[2];
         if (dom_reduce_sum_max_f((float)rsum, (float)dmax, A.partials + D.poff, &ctl->counter,
@@ -247,6 +249,24 @@ kb_cheb(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const T* c
             }
         }
         __syncthreads();
+    }
+}
+
+// After the Chebyshev passes of a stage: a domain that ran an odd number of passes holds
+// its iterate in the second buffer; copy it to dp (the correction and the fallback read dp).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+kb_settle(Arena<T> A, const int2* __restrict__ wl, int nw, const T* __restrict__ x2,
+          T* __restrict__ dp, int K)
+{
+    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+        const int2 it = wl[w];
+        if (((A.sctl[it.x].sweeps / K) & 1) == 0) continue;
+        const Dom<T>& D = A.dom[it.x];
+        const long long n = D.noff, nn = (long long)(D.P.nx + 1) * (D.P.ny + 1);
+        for (long long k = (long long)it.y * kChunk + threadIdx.x;
+             k < nn && k < (long long)(it.y + 1) * kChunk; k += blockDim.x)
+            dp[n + k] = x2[n + k];
     }
 }
 
@@ -517,7 +537,8 @@ using AsmFn = void (*)(int grid, cudaStream_t, const Arena<T>&, const int2*, int
                        T*, T*, T*, T*, T*, T*, T*, const T*, AsmArgs);
 template <typename T>
 using ChebFn = void (*)(int grid, cudaStream_t, const Arena<T>&, const int2*, int, const T*,
-                        const T*, const T*, const T*, const T*, const T*, T*, T*, int);
+                        const T*, const T*, const T*, const T*, const T*, const T*, const T*,
+                        T*, T*, int);
 
 template <typename T, int TX, int TY>
 void run_hyp(int grid, cudaStream_t s, const Arena<T>& A, const int2* wl, int nw, const T* e,
@@ -537,16 +558,16 @@ void run_asm(int grid, cudaStream_t s, const Arena<T>& A, const int2* wl, int nw
                                            ws, cC, cW, cE, cS, cN, rhs, p0, G);
 }
 
-template <typename T, int NA, int NB, int BY>
-constexpr size_t cheb_smem() { return 7 * (size_t)(32 * NA) * (BY * NB) * sizeof(T); }
+template <typename T, int NA, int NB, int BY, bool REGW = false>
+constexpr size_t cheb_smem() { return (REGW ? 2 : 7) * (size_t)(32 * NA) * (BY * NB) * sizeof(T); }
 
-template <typename T, int NA, int NB, int BY>
+template <typename T, int NA, int NB, int BY, bool REGW = false>
 void run_cheb(int grid, cudaStream_t s, const Arena<T>& A, const int2* wl, int nw, const T* cC,
-              const T* cW, const T* cE, const T* cS, const T* cN, const T* rhs, T* x, T* xp,
-              int stage)
+              const T* cW, const T* cE, const T* cS, const T* cN, const T* rhs, const T* xi,
+              const T* xpi, T* xo, T* xpo, int stage)
 {
-    kb_cheb<T, NA, NB, BY, 4><<<grid, dim3(32, BY), cheb_smem<T, NA, NB, BY>(), s>>>(
-        A, wl, nw, cC, cW, cE, cS, cN, rhs, x, xp, stage);
+    kb_cheb<T, NA, NB, BY, 4, REGW><<<grid, dim3(32, BY), cheb_smem<T, NA, NB, BY, REGW>(), s>>>(
+        A, wl, nw, cC, cW, cE, cS, cN, rhs, xi, xpi, xo, xpo, stage);
 }
 
 template <typename T>
@@ -558,7 +579,7 @@ struct Cand {
 
 template <>
 struct Cands<float> {
-    static constexpr int nh = 3, na = 3, nc = 3;
+    static constexpr int nh = 3, na = 3, nc = 4;
     static Shape hyp_shape(int k) { const Shape s[nh] = {{32, 16, 256}, {32, 8, 256}, {64, 8, 256}}; return s[k]; }
     static HypFn<float> hyp(int k)
     {
@@ -584,24 +605,26 @@ struct Cands<float> {
         return f[k];
     }
     // Chebyshev: region (tile + 4-node halo on every side) and threads
-    static Shape cheb_shape(int k) { const Shape s[nc] = {{128, 32, 512}, {64, 64, 512}, {128, 32, 256}}; return s[k]; }
+    // (the fourth: the first shape with the weights in registers)
+    static Shape cheb_shape(int k) { const Shape s[nc] = {{128, 32, 512}, {64, 64, 512}, {128, 32, 256}, {128, 32, 512}}; return s[k]; }
     static ChebFn<float> cheb(int k)
     {
         const ChebFn<float> f[nc] = {run_cheb<float, 4, 2, 16>, run_cheb<float, 2, 4, 16>,
-                                     run_cheb<float, 4, 4, 8>};
+                                     run_cheb<float, 4, 4, 8>, run_cheb<float, 4, 2, 16, true>};
         return f[k];
     }
     static const void* cheb_kernel(int k)
     {
-        const void* f[nc] = {(const void*)kb_cheb<float, 4, 2, 16, 4>,
-                             (const void*)kb_cheb<float, 2, 4, 16, 4>,
-                             (const void*)kb_cheb<float, 4, 4, 8, 4>};
+        const void* f[nc] = {(const void*)kb_cheb<float, 4, 2, 16, 4, false>,
+                             (const void*)kb_cheb<float, 2, 4, 16, 4, false>,
+                             (const void*)kb_cheb<float, 4, 4, 8, 4, false>,
+                             (const void*)kb_cheb<float, 4, 2, 16, 4, true>};
         return f[k];
     }
     static size_t cheb_smem_of(int k)
     {
         const size_t s[nc] = {cheb_smem<float, 4, 2, 16>(), cheb_smem<float, 2, 4, 16>(),
-                              cheb_smem<float, 4, 4, 8>()};
+                              cheb_smem<float, 4, 4, 8>(), cheb_smem<float, 4, 2, 16, true>()};
         return s[k];
     }
 };
@@ -639,8 +662,8 @@ struct Cands<double> {
     }
     static const void* cheb_kernel(int k)
     {
-        const void* f[nc] = {(const void*)kb_cheb<double, 2, 2, 16, 4>,
-                             (const void*)kb_cheb<double, 2, 4, 8, 4>};
+        const void* f[nc] = {(const void*)kb_cheb<double, 2, 2, 16, 4, false>,
+                             (const void*)kb_cheb<double, 2, 4, 8, 4, false>};
         return f[k];
     }
     static size_t cheb_smem_of(int k)
@@ -1030,15 +1053,31 @@ struct BatchImpl : BatchBase {
                           B.p, G);
     }
 
-    void cheb_pass(int s, int cand, bool persistent, cudaStream_t st)
+    // pass `odd`: reads (dp, r) and writes (v[0], v[1]) when 0, the other way when 1
+    void cheb_pass(int s, int cand, bool persistent, cudaStream_t st, int odd)
     {
         const Shape sh = C::cheb_shape(cand);
+        T* xa = odd ? B.v[0] : B.dp;
+        T* pa = odd ? B.v[1] : B.r;
+        T* xb = odd ? B.dp : B.v[0];
+        T* pb = odd ? B.r : B.v[1];
         C::cheb(cand)(grid_of(C::cheb_kernel(cand), sh.threads, C::cheb_smem_of(cand), nw_cheb[cand], persistent),
                       st, arena(), wl_cheb[cand], nw_cheb[cand], B.cC, B.cW, B.cE, B.cS, B.cN,
-                      B.rhs, B.dp, B.r, s);
+                      B.rhs, xa, pa, xb, pb, s);
+    }
+    // two passes (the buffer pairs alternate, so a pair of passes restores them)
+    void cheb_pair(int s, cudaStream_t st)
+    {
+        for (int odd = 0; odd < 2; ++odd)
+            K_(NH_K_CHEB_PASS, st, [&] { cheb_pass(s, tun.cheb, pers(2), st, odd); });
+    }
+    void settle(cudaStream_t st)
+    {
+        kb_settle<T><<<grid_of((const void*)kb_settle<T>, kThreads, 0, nw_node, true), kThreads, 0, st>>>(
+            arena(), wl_node, nw_node, B.v[0], B.dp, kChebK);
     }
 
-    unsigned pass_cap() const { return (unsigned)(hb->prm.max_iter / kChebK + 16); }
+    unsigned pass_cap() const { return (unsigned)((hb->prm.max_iter / kChebK + 16) / 2); }   // pairs
     unsigned bicg_cap() const { return (unsigned)(hb->prm.max_iter / 2 + 2); }
 
     BiVec<T> bivec() const
@@ -1115,18 +1154,18 @@ struct BatchImpl : BatchBase {
     // then the BiCGStab fallback for the domains that need it
     int solve_eager(int s)
     {
-        unsigned passes = 0;
-        int batch = 4;
+        unsigned passes = 0;   // pairs of passes
+        int batch = 2;
         cudaError_t e;
         for (;;) {
-            for (int k = 0; k < batch; ++k)
-                K_(NH_K_CHEB_PASS, hb->s, [&] { cheb_pass(s, tun.cheb, pers(2), hb->s); });
+            for (int k = 0; k < batch; ++k) cheb_pair(s, hb->s);
             passes += batch;
             cudaMemcpyAsync(h_loop, d_loop, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, hb->s);
             if ((e = cudaStreamSynchronize(hb->s)) != cudaSuccess) return bcuda(hb, e, "batched pressure solve");
             if (h_loop[0] == 0u || passes >= pass_cap()) break;
-            batch = 2;
+            batch = 1;
         }
+        settle(hb->s);
         if (h_loop[2] == 0u) return NH_OK;
         bicg_init(s, hb->s);
         for (unsigned pairs = 0; pairs < bicg_cap();) {
@@ -1203,9 +1242,10 @@ struct BatchImpl : BatchBase {
             if (hb->prm.nonhydrostatic) {
                 // Chebyshev passes: WHILE (domains solving) { pass; test }
                 add_while(s, chk, 1, [&](cudaStream_t bs, cudaGraphConditionalHandle h) {
-                    cheb_pass(st, tun.cheb, pers(2), bs);
+                    cheb_pair(st, bs);
                     kb_loop_cond<<<1, 32, 0, bs>>>(h, d_loop, 0, pass_cap(), 1);
                 }, nullptr);
+                settle(s);
                 // fallback: init; WHILE (domains in BiCGStab) { two iterations; test }
                 bicg_init(st, s);
                 add_while(s, chk, 0, [&](cudaStream_t bs, cudaGraphConditionalHandle h) {
@@ -1281,7 +1321,8 @@ struct BatchImpl : BatchBase {
                 for (int p = 0; p < 2; ++p) {
                     cudaMemsetAsync(B.dp, 0, nnode * sizeof(T), s);
                     assembly(0, tun.assembly, pers(1));
-                    const float t = time_ms([&] { cheb_pass(0, k, p == 1, s); }, 2 * reps);
+                    int odd = 0;
+                    const float t = time_ms([&] { cheb_pass(0, k, p == 1, s, odd); odd ^= 1; }, 2 * reps);
                     if (t < best) { best = t; tun.cheb = k; tun.persistent = (tun.persistent & ~4) | (p << 2); }
                 }
             tun.ms[2] = best;

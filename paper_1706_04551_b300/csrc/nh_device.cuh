@@ -32,13 +32,26 @@ __device__ __forceinline__ T minmod(T a, T b)
     return T(0);
 }
 
+// Square root and quotient of the hot FP32 paths: the hardware approximations
+// (sqrt.approx, __fdividef; a few ulp, flush-to-zero), which the FP32 form's tolerance
+// covers; FP64 keeps the correctly rounded operations.
+__device__ __forceinline__ float qsqrt(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ double qsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float qdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double qdiv(double a, double b) { return a / b; }
+
 // Desingularised q / h (Sec. 4.5): sqrt(2) h q / sqrt(h^4 + max(h^4, delta^4)); d4 = delta^4.
 template <typename T>
 __device__ __forceinline__ T desing(T h, T q, T d4)
 {
     T h2 = h * h;
     T h4 = h2 * h2;
-    return T(1.4142135623730951) * h * q / sqrt(h4 + tmax(h4, d4));
+    return qdiv(T(1.4142135623730951) * h * q, qsqrt(h4 + tmax(h4, d4)));
 }
 
 // Cell index under the boundary condition of each side: wall = mirror (refl = true),
@@ -104,17 +117,18 @@ __device__ __forceinline__ void recon(const St<T>* c, int k, T hdry, St<T>& lo, 
 
 // PVM-HLL fluctuations (Eqs. 18-19) at a face in its normal frame from the left state
 // (hL, eL, unL, utL) and the right one.  Components: h, normal, tangential discharge.
+// sg = sqrt(g): the one-sided celerities sqrt(g h_L), sqrt(g h_R) reuse sqrt(h_L), sqrt(h_R).
 template <typename T>
-__device__ __forceinline__ void pvm(T g, T hdry, T hL, T eL, T unL, T utL, T hR, T eR,
+__device__ __forceinline__ void pvm(T g, T sg, T hdry, T hL, T eL, T unL, T utL, T hR, T eR,
                                     T unR, T utR, T Dm[3], T Dp[3])
 {
     T qnL = hL * unL, qnR = hR * unR, qtL = hL * utL, qtR = hR * utR;
     T hb = T(0.5) * (hL + hR);
-    T sL = sqrt(hL), sR = sqrt(hR), ss = sL + sR;
-    T ub = ss > T(0) ? (unL * sL + unR * sR) / ss : T(0);   // Roe velocity
-    T cb = sqrt(g * hb);
-    T SL = tmin(ub - cb, unL - sqrt(g * hL));
-    T SR = tmax(ub + cb, unR + sqrt(g * hR));
+    T sL = qsqrt(hL), sR = qsqrt(hR), ss = sL + sR;
+    T ub = ss > T(0) ? qdiv(unL * sL + unR * sR, ss) : T(0);   // Roe velocity
+    T cb = qsqrt(g * hb);
+    T SL = tmin(ub - cb, unL - sg * sL);
+    T SR = tmax(ub + cb, unR + sg * sR);
     // emerging bottom (Sec. 4.5): dry side's bed at or above the wet free surface
     T de = eR - eL;
     if (hR <= hdry && (eR - hR) >= eL) de = T(0);
@@ -124,8 +138,9 @@ __device__ __forceinline__ void pvm(T g, T hdry, T hL, T eL, T unL, T utL, T hR,
         Dm[0] = Dm[1] = Dm[2] = Dp[0] = Dp[1] = Dp[2] = T(0);
         return;
     }
-    T a0 = (SR * fabs(SL) - SL * fabs(SR)) / span;
-    T a1 = (fabs(SR) - fabs(SL)) / span;
+    const T isp = qdiv(T(1), span);
+    T a0 = (SR * fabs(SL) - SL * fabs(SR)) * isp;
+    T a1 = (fabs(SR) - fabs(SL)) * isp;
     T R0 = qnR - qnL;
     T R1 = qnR * unR - qnL * unL + g * hb * de;
     T R2 = qnR * utR - qnL * utL;
@@ -318,30 +333,21 @@ hyp_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ q1,
     }
     __syncthreads();
     auto L = [&](int i, int j) { return (j + 2) * LW + (i + 2); };   // local cell index
-    // x faces f = 0..TX between local cells f-1 and f, rows 0..TY-1
-    for (int t = tid; t < NFX + NFY; t += nt) {
-        const bool xf = t < NFX;
-        const int tt = xf ? t : t - NFX;
-        const int f = xf ? tt % (TX + 1) : tt % TX;
-        const int r = xf ? tt / (TX + 1) : tt / TX;
-        // cells along the face normal: m2 = cell -2, m1 = -1 (left), p0 = right, p1 = +1
-        const int s0 = xf ? 1 : LW;
-        const int cl = xf ? L(f - 1, r) : L(f, r - 1);   // left cell (west / south)
-        const int cr = cl + s0;                            // right cell
-        const int cm = cl - s0, cp = cr + s0;
-        // left cell: its high-side value; right cell: its low-side value
-        const T uL = xf ? su[cl] : sv[cl], uR = xf ? su[cr] : sv[cr];
-        const T tL = xf ? sv[cl] : su[cl], tR = xf ? sv[cr] : su[cr];
-        const T unm = xf ? su[cm] : sv[cm], unp = xf ? su[cp] : sv[cp];
-        const T utm = xf ? sv[cm] : su[cm], utp = xf ? sv[cp] : su[cp];
+    const T sg = qsqrt(g);
+    // one face: cells cm, cl | cr, cp along the normal (stride s0 in the staged tile);
+    // un, ut: the staged normal and tangential velocities; writes the left cell's and the
+    // right cell's outputs (stride `stride` between the three components)
+    auto face = [&](int cl, int s0, const T* un, const T* ut, T* oL0, T* oR0, int stride) {
+        const int cr = cl + s0, cm = cl - s0, cp = cr + s0;
+        const T uL = un[cl], uR = un[cr], tL = ut[cl], tR = ut[cr];
         const T sLh = minmod(sh[cl] - sh[cm], sh[cr] - sh[cl]);
-        const T sLu = minmod(uL - unm, uR - uL);
-        const T sLt = minmod(tL - utm, tR - tL);
+        const T sLu = minmod(uL - un[cm], uR - uL);
+        const T sLt = minmod(tL - ut[cm], tR - tL);
         const bool dL = sh[cm] <= hdry || sh[cl] <= hdry || sh[cr] <= hdry;
         const T sLe = dL ? T(0) : minmod(se[cl] - se[cm], se[cr] - se[cl]);
         const T sRh = minmod(sh[cr] - sh[cl], sh[cp] - sh[cr]);
-        const T sRu = minmod(uR - uL, unp - uR);
-        const T sRt = minmod(tR - tL, utp - tR);
+        const T sRu = minmod(uR - uL, un[cp] - uR);
+        const T sRt = minmod(tR - tL, ut[cp] - tR);
         const bool dR = sh[cl] <= hdry || sh[cr] <= hdry || sh[cp] <= hdry;
         const T sRe = dR ? T(0) : minmod(se[cr] - se[cl], se[cp] - se[cr]);
         const T hL = sh[cl] + T(0.5) * sLh, eL = se[cl] + T(0.5) * sLe;
@@ -349,17 +355,24 @@ hyp_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ q1,
         const T hR = sh[cr] - T(0.5) * sRh, eR = se[cr] - T(0.5) * sRe;
         const T nR = uR - T(0.5) * sRu, tRv = tR - T(0.5) * sRt;
         T Dm[3], Dp[3];
-        pvm(g, hdry, hL, eL, nL, tLv, hR, eR, nR, tRv, Dm, Dp);
+        pvm(g, sg, hdry, hL, eL, nL, tLv, hR, eR, nR, tRv, Dm, Dp);
         const T qL = hL * nL, qR = hR * nR;
-        T* oL0 = xf ? &CLx[0][tt] : &CLy[0][tt];
-        T* oR0 = xf ? &CRx[0][tt] : &CRy[0][tt];
-        const int stride = xf ? NFX : NFY;
         oL0[0] = Dm[0] + qL;
         oL0[stride] = Dm[1] + qL * nL + g * sh[cl] * eL;
         oL0[2 * stride] = Dm[2] + qL * tLv;
         oR0[0] = Dp[0] - qR;
         oR0[stride] = Dp[1] - (qR * nR + g * sh[cr] * eR);
         oR0[2 * stride] = Dp[2] - qR * tRv;
+    };
+    // x faces f = 0..TX between local cells f-1 and f, rows 0..TY-1
+    for (int t = tid; t < NFX; t += nt) {
+        const int f = t % (TX + 1), r = t / (TX + 1);
+        face(L(f - 1, r), 1, su, sv, &CLx[0][t], &CRx[0][t], NFX);
+    }
+    // y faces f = 0..TY between local rows f-1 and f, columns 0..TX-1
+    for (int t = tid; t < NFY; t += nt) {
+        const int f = t % TX, r = t / TX;
+        face(L(f, r - 1), LW, sv, su, &CLy[0][t], &CRy[0][t], NFY);
     }
     __syncthreads();
     int nclamp = 0;
@@ -639,26 +652,34 @@ __device__ __forceinline__ T row_apply(const Rows<T>& R, int I, int J, T xc, F x
 // side; outside the domain the halo holds mirror images (values, and coefficients with
 // W <-> E or S <-> N swapped), which evolve exactly as the nodes they mirror, so tiles at
 // the boundary are no different from interior ones.  x_{k-1} lives in registers.
-// One tile (bx, by); smem holds 7 region arrays; returns the last sweep's per-thread sum of
-// r^2 and max |dx| in rsum, dmax.
-template <typename T, int NA, int NB, int BY, int K>
+// One tile (bx, by): reads x, x_{k-1} of the tile and its halo from (xi, xpi) and writes the
+// tile's new values to (xo, xpo) -- separate buffers, so that no block reads a halo that
+// another block of the same pass has already advanced.  Returns the last sweep's per-thread
+// sum of r^2 and max |dx| in rsum, dmax.  The Jacobi-scaled right-hand side and the four off-diagonal weights of a node are
+// read only by the thread that owns the node, so they live either in shared memory (REGW =
+// false: smem holds 7 region arrays) or in that thread's registers (REGW = true: smem holds
+// only the two x buffers).  Both forms do the same arithmetic in the same order.
+template <typename T, int NA, int NB, int BY, int K, bool REGW>
 __device__ __forceinline__ void
-cheb_tile(const Rows<T>& R, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ xp,
+cheb_tile(const Rows<T>& R, const T* __restrict__ b, const T* __restrict__ xi,
+          const T* __restrict__ xpi, T* __restrict__ xo, T* __restrict__ xpo,
           const SolveCtl* ctl, int bx, int by, T* smem, T& rsum, T& dmax)
 {
-    constexpr int RW = 32 * NA, RH = BY * NB, RN = RW * RH;
+    constexpr int RW = 32 * NA, RH = BY * NB, RN = RW * RH, NN = NA * NB;
     constexpr int TX = RW - 2 * K, TY = RH - 2 * K;
     T* xs0 = smem;
     T* xs1 = xs0 + RN;
-    T* bd = xs1 + RN;
+    T* bd = xs1 + RN;   // (REGW = false only)
     T* wW = bd + RN;
     T* wE = wW + RN;
     T* wS = wE + RN;
     T* wN = wS + RN;
+    T rbd[REGW ? NN : 1], rwW[REGW ? NN : 1], rwE[REGW ? NN : 1], rwS[REGW ? NN : 1],
+        rwN[REGW ? NN : 1];
     const int nx = R.nx, ny = R.ny, NX = nx + 1;
     const int I0 = bx * TX - K, J0 = by * TY - K;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    T xa[NA * NB];
+    T xa[NN];
 #pragma unroll
     for (int bb = 0; bb < NB; ++bb)
 #pragma unroll
@@ -672,16 +693,26 @@ cheb_tile(const Rows<T>& R, const T* __restrict__ b, T* __restrict__ x, T* __res
             mJ = mJ < 0 ? 0 : (mJ > ny ? ny : mJ);
             const size_t g = (size_t)mJ * NX + mI;
             const int sidx = lj * RW + li;
-            const T ic = T(1) / R.cC[g];
-            xs0[sidx] = x[g];
-            xa[bb * NA + aa] = xp[g];
-            bd[sidx] = b[g] * ic;
+            const int q = bb * NA + aa;
+            const T ic = qdiv(T(1), R.cC[g]);
+            xs0[sidx] = xi[g];
+            xa[q] = xpi[g];
+            const T bv = b[g] * ic;
             const T cw = R.cW[g] * ic, ce = R.cE[g] * ic;
             const T cs = R.cS[g] * ic, cn = R.cN[g] * ic;
-            wW[sidx] = fx ? ce : cw;
-            wE[sidx] = fx ? cw : ce;
-            wS[sidx] = fy ? cn : cs;
-            wN[sidx] = fy ? cs : cn;
+            if constexpr (REGW) {
+                rbd[q] = bv;
+                rwW[q] = fx ? ce : cw;
+                rwE[q] = fx ? cw : ce;
+                rwS[q] = fy ? cn : cs;
+                rwN[q] = fy ? cs : cn;
+            } else {
+                bd[sidx] = bv;
+                wW[sidx] = fx ? ce : cw;
+                wE[sidx] = fx ? cw : ce;
+                wS[sidx] = fy ? cn : cs;
+                wN[sidx] = fy ? cs : cn;
+            }
         }
     T c1s[K], c2s[K];
 #pragma unroll
@@ -704,13 +735,20 @@ cheb_tile(const Rows<T>& R, const T* __restrict__ b, T* __restrict__ x, T* __res
                 const int li = tx + 32 * aa, lj = ty + BY * bb;
                 if (li > sw && li < RW - 1 - sw && lj > sw && lj < RH - 1 - sw) {
                     const int sidx = lj * RW + li;
+                    const int q = bb * NA + aa;
                     const T xc = cur[sidx];
-                    const T r = bd[sidx] - xc -
-                                (wW[sidx] * cur[sidx - 1] + wE[sidx] * cur[sidx + 1] +
-                                 wS[sidx] * cur[sidx - RW] + wN[sidx] * cur[sidx + RW]);
-                    const T xn = xc + c1 * (xc - xa[bb * NA + aa]) + c2 * r;
+                    T r;
+                    if constexpr (REGW)
+                        r = rbd[q] - xc -
+                            (rwW[q] * cur[sidx - 1] + rwE[q] * cur[sidx + 1] +
+                             rwS[q] * cur[sidx - RW] + rwN[q] * cur[sidx + RW]);
+                    else
+                        r = bd[sidx] - xc -
+                            (wW[sidx] * cur[sidx - 1] + wE[sidx] * cur[sidx + 1] +
+                             wS[sidx] * cur[sidx - RW] + wN[sidx] * cur[sidx + RW]);
+                    const T xn = xc + c1 * (xc - xa[q]) + c2 * r;
                     nxt[sidx] = xn;
-                    xa[bb * NA + aa] = xc;
+                    xa[q] = xc;
                     if (sw == K - 1 && li >= K && li < RW - K && lj >= K && lj < RH - K &&
                         I0 + li <= nx && J0 + lj <= ny) {
                         rsum = fma(r, r, rsum);
@@ -729,8 +767,8 @@ cheb_tile(const Rows<T>& R, const T* __restrict__ b, T* __restrict__ x, T* __res
             const int gI = I0 + li, gJ = J0 + lj;
             if (li >= K && li < RW - K && lj >= K && lj < RH - K && gI <= nx && gJ <= ny) {
                 const size_t g = (size_t)gJ * NX + gI;
-                x[g] = cur[lj * RW + li];
-                xp[g] = xa[bb * NA + aa];
+                xo[g] = cur[lj * RW + li];
+                xpo[g] = xa[bb * NA + aa];
             }
         }
 }

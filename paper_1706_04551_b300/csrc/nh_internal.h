@@ -70,7 +70,8 @@ struct Bufs {
     T *dp, *palt;                // 2D: pressure correction of a solve; next pressure buffer
     T *cC, *cW, *cE, *cS, *cN;   // 2D five-point coefficients (1D: a = cW, b = cC, c = cE)
     T *rhs;
-    T *r, *rh, *ph[2], *v[2], *t;  // BiCGStab vectors (r doubles as the Chebyshev x_{k-1})
+    T *r, *rh, *ph[2], *v[2], *t;  // BiCGStab vectors; the Chebyshev passes alternate
+                                   // (dp, r) and (v[0], v[1]) as (x, x_{k-1})
     double *partials;             // per-block partial sums (>= 4 * nblk)
     SolveCtl *sctl;
     StepCtl *stctl;
@@ -102,9 +103,11 @@ template <typename T>
 size_t cheb_tiles(const Prm<T>& P);
 template <typename T>
 size_t asm_tiles(const Prm<T>& P);   // blocks of the 2D assembly (3 partials each)
+// One pass: (x, x_{k-1}) from (xi, xpi) to (xo, xpo); variant 0: weights in shared memory
+// (2 blocks / SM); 1: weights in registers (1 block)
 template <typename T>
-int launch_cheb_pass(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, T* xprev,
-                     double* partials);
+int launch_cheb_pass(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, const T* xi,
+                     const T* xpi, T* xo, T* xpo, double* partials, int variant);
 template <typename T>
 void launch_matvec2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* x, T* y);
 template <typename T>

@@ -194,16 +194,17 @@ k_bicg_C(Rows<T> R, T* __restrict__ r, const T* __restrict__ rh, const T* __rest
     }
 }
 
-template <typename T, int NA, int NB, int BY, int K>
-__global__ void __launch_bounds__(32 * BY, 2)
-k_cheb_pass2(Rows<T> R, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ xp,
+template <typename T, int NA, int NB, int BY, int K, bool REGW>
+__global__ void __launch_bounds__(32 * BY, REGW ? 1 : 2)
+k_cheb_pass2(Rows<T> R, const T* __restrict__ b, const T* __restrict__ xi,
+             const T* __restrict__ xpi, T* __restrict__ xo, T* __restrict__ xpo,
              double* partials, SolveCtl* ctl)
 {
     if (ctl->done) return;
     extern __shared__ unsigned char cheb2_smem[];
     T rsum, dmax;
-    cheb_tile<T, NA, NB, BY, K>(R, b, x, xp, ctl, blockIdx.x, blockIdx.y,
-                                reinterpret_cast<T*>(cheb2_smem), rsum, dmax);
+    cheb_tile<T, NA, NB, BY, K, REGW>(R, b, xi, xpi, xo, xpo, ctl, blockIdx.x, blockIdx.y,
+                                      reinterpret_cast<T*>(cheb2_smem), rsum, dmax);
     double acc[2];
     if (dom_reduce_sum_max_f((float)rsum, (float)dmax, partials, &ctl->counter, acc,
                              blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y) &&
@@ -271,8 +272,9 @@ k_hyp1d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ q,
 #pragma unroll
         for (int k = 1; k <= 3; ++k) recon(cx, k, hdry, lo[k - 1], hi[k - 1]);
         T DmW[3], DpW[3], DmE[3], DpE[3];
-        pvm(g, hdry, hi[0].h, hi[0].e, hi[0].u, T(0), lo[1].h, lo[1].e, lo[1].u, T(0), DmW, DpW);
-        pvm(g, hdry, hi[1].h, hi[1].e, hi[1].u, T(0), lo[2].h, lo[2].e, lo[2].u, T(0), DmE, DpE);
+        const T sg = qsqrt(g);
+        pvm(g, sg, hdry, hi[0].h, hi[0].e, hi[0].u, T(0), lo[1].h, lo[1].e, lo[1].u, T(0), DmW, DpW);
+        pvm(g, sg, hdry, hi[1].h, hi[1].e, hi[1].u, T(0), lo[2].h, lo[2].e, lo[2].u, T(0), DmE, DpE);
         const St<T>& E = hi[1]; const St<T>& W = lo[1];
         const T hc = cx[2].h;
         T I0 = E.h * E.u - W.h * W.u;
@@ -625,25 +627,33 @@ size_t cheb_tiles(const Prm<T>& P)
     return (size_t)((P.nx + 1 + TX - 1) / TX) * ((P.ny + 1 + TY - 1) / TY);
 }
 
-template <typename T>
-int launch_cheb_pass(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, T* xprev,
-                     double* partials)
+template <typename T, bool REGW>
+int launch_cheb_pass_v(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, const T* xi,
+                       const T* xpi, T* xo, T* xpo, double* partials)
 {
     using C = ChebCfg<T>;
     constexpr int TX = 32 * C::NA - 2 * C::K, TY = C::BY * C::NB - 2 * C::K;
-    constexpr size_t smem = 7 * (size_t)(32 * C::NA) * (C::BY * C::NB) * sizeof(T);
+    constexpr size_t smem = (REGW ? 2 : 7) * (size_t)(32 * C::NA) * (C::BY * C::NB) * sizeof(T);
     static bool attr_set = false;
     if (!attr_set) {
-        if (cudaFuncSetAttribute(k_cheb_pass2<T, C::NA, C::NB, C::BY, C::K>,
+        if (cudaFuncSetAttribute(k_cheb_pass2<T, C::NA, C::NB, C::BY, C::K, REGW>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return -1;
         attr_set = true;
     }
     dim3 grid((P.nx + 1 + TX - 1) / TX, (P.ny + 1 + TY - 1) / TY);
-    k_cheb_pass2<T, C::NA, C::NB, C::BY, C::K><<<grid, dim3(32, C::BY), smem, s>>>(
-        rows_of(P, B), B.rhs, B.dp, xprev, partials, B.sctl);
+    k_cheb_pass2<T, C::NA, C::NB, C::BY, C::K, REGW><<<grid, dim3(32, C::BY), smem, s>>>(
+        rows_of(P, B), B.rhs, xi, xpi, xo, xpo, partials, B.sctl);
     return 0;
+}
+
+template <typename T>
+int launch_cheb_pass(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, const T* xi,
+                     const T* xpi, T* xo, T* xpo, double* partials, int variant)
+{
+    return variant == 1 ? launch_cheb_pass_v<T, true>(P, s, B, xi, xpi, xo, xpo, partials)
+                        : launch_cheb_pass_v<T, false>(P, s, B, xi, xpi, xo, xpo, partials);
 }
 
 template <typename T>
@@ -820,7 +830,8 @@ void launch_convert_from_double(const Launch& L, const double* src, T* dst, size
     template int cheb_sweeps_per_pass<T>();                                                    \
     template size_t cheb_tiles<T>(const Prm<T>&);                                              \
     template size_t asm_tiles<T>(const Prm<T>&);                                               \
-    template int launch_cheb_pass<T>(const Prm<T>&, cudaStream_t, const Bufs<T>&, T*, double*);\
+    template int launch_cheb_pass<T>(const Prm<T>&, cudaStream_t, const Bufs<T>&, const T*,   \
+                                     const T*, T*, T*, double*, int);                           \
     template void launch_matvec2d<T>(const Prm<T>&, const Launch&, const Bufs<T>&, const T*,   \
                                      T*);                                                      \
     template void launch_bicg_init<T>(const Prm<T>&, const Launch&, const Bufs<T>&, double*);  \
