@@ -347,6 +347,7 @@ struct Impl : Base {
         cudaMemsetAsync(B.r, 0, nn * sizeof(T), hd->s);
         cudaMemsetAsync(B.dp, 0, nn * sizeof(T), hd->s);
         int passes_launched = 0;
+        ++solves;
         int batch = last_cheb_passes > 2 ? last_cheb_passes - 1 : 4;
         double best = 1e300;
         int stale = 0;
@@ -355,9 +356,10 @@ struct Impl : Base {
                 int rc = 0;
                 // until the faster pass form is known, alternate the two (their sweeps are
                 // identical, so the solve does not depend on the choice) and time them
-                const int v = pass_variant >= 0 ? pass_variant : (vt_next++ & 1);
+                const int v = pass_variant >= 0 ? pass_variant : (vt_next++ % cheb_pass_forms<T>());
                 const bool timed = pass_variant < 0 && vt_used + 2 <= kVT;
                 if (timed) cudaEventRecord(vt_ev[vt_used], hd->s);
+                if (timed) { vt_pass[vt_used / 2] = passes_launched; vt_solve[vt_used / 2] = solves; }
                 // pass j reads buffer pair j % 2 and writes the other
                 const bool odd = (passes_launched++ & 1) != 0;
                 T* xa = odd ? B.v[0] : B.dp;
@@ -377,7 +379,14 @@ struct Impl : Base {
             cudaMemcpyAsync(h_sctl, B.sctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, hd->s);
             cudaError_t e = cudaStreamSynchronize(hd->s);
             if (e != cudaSuccess) return cuda_fail(hd, e, "pressure solve");
-            if (pass_variant < 0 && vt_used >= kVT) choose_pass_variant();
+            if (pass_variant < 0) {
+                // passes launched after the solve converged return at once: only the timed
+                // passes that ran count
+                const int ran = h_sctl->done ? h_sctl->sweeps / K : passes_launched;
+                for (int k = 0; k < vt_used / 2; ++k)
+                    if (vt_solve[k] == solves) vt_ok[k] = vt_pass[k] < ran ? 1 : 0;
+                if (vt_used >= kVT || (vt_next > 0 && solves >= 12)) choose_pass_variant();
+            }
             if (h_sctl->status == 4) return fallback(stage, false);   // not diagonally dominant
             if (h_sctl->done) settle_passes(h_sctl->sweeps / K);
             if (h_sctl->done) break;
@@ -732,25 +741,29 @@ struct Impl : Base {
     }
     long long adjoint_iters = 0;
     // choice between the two Chebyshev pass forms (shared-memory or register weights)
-    static constexpr int kVT = 32;   // event slots: 16 timed passes
+    static constexpr int kVT = 128;   // event slots: 64 timed passes
     int pass_variant = -1;
-    int vt_next = 0, vt_used = 0;
-    int vt_var[kVT / 2] = {};
+    int vt_next = 0, vt_used = 0, solves = 0;
+    int vt_var[kVT / 2] = {}, vt_pass[kVT / 2] = {}, vt_solve[kVT / 2] = {}, vt_ok[kVT / 2] = {};
     cudaEvent_t vt_ev[kVT] = {};
     void choose_pass_variant()
     {
-        double sum[2] = {0.0, 0.0};
-        int cnt[2] = {0, 0};
+        const int nv = cheb_pass_forms<T>();
+        double sum[8] = {};
+        int cnt[8] = {};
         // the first pass of each form warms it up and is not counted
-        for (int k = 2; k < vt_used / 2; ++k) {
+        for (int k = nv; k < vt_used / 2; ++k) {
             float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, vt_ev[2 * k], vt_ev[2 * k + 1]) == cudaSuccess) {
+            if (vt_ok[k] && cudaEventElapsedTime(&ms, vt_ev[2 * k], vt_ev[2 * k + 1]) == cudaSuccess) {
                 sum[vt_var[k]] += ms;
                 cnt[vt_var[k]] += 1;
             }
         }
         cudaGetLastError();
-        pass_variant = (cnt[0] && cnt[1] && sum[1] / cnt[1] < sum[0] / cnt[0]) ? 1 : 0;
+        int best = 0;
+        for (int v = 1; v < nv; ++v)
+            if (cnt[v] && (!cnt[best] || sum[v] / cnt[v] < sum[best] / cnt[best])) best = v;
+        pass_variant = best;
     }
     bool accept_stall = false;   // set during the adjoint's transposed solves
 

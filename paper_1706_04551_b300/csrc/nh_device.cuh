@@ -773,6 +773,151 @@ cheb_tile(const Rows<T>& R, const T* __restrict__ b, const T* __restrict__ xi,
         }
 }
 
+// ---- pipelined form of the pass: a persistent block walks tiles t, t + G, ...; the eight
+// node arrays of the next tile are copied into shared memory with cp.async while the
+// current tile is swept, so the copies overlap the sweeps.
+
+__device__ __forceinline__ void cp_async_elem(void* smem_dst, const float* src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(void* smem_dst, const double* src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" :: "r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Region geometry of tile `tile` (row-major over ntx tiles per row).
+template <int TX, int TY, int K>
+__device__ __forceinline__ void tile_origin(int tile, int ntx, int& I0, int& J0)
+{
+    I0 = (tile % ntx) * TX - K;
+    J0 = (tile / ntx) * TY - K;
+}
+
+// Issue the copies of this thread's region nodes of the tile with origin (I0, J0) into the
+// staging arrays st[8][RN] (x, x_{k-1}, b, cC, cW, cE, cS, cN), mirrored outside the domain.
+template <typename T, int NA, int NB, int BY>
+__device__ __forceinline__ void cheb_fetch(const Rows<T>& R, const T* b, const T* xi,
+                                           const T* xpi, int I0, int J0, T* st)
+{
+    constexpr int RW = 32 * NA, RH = BY * NB, RN = RW * RH;
+    const int nx = R.nx, ny = R.ny, NX = nx + 1;
+#pragma unroll
+    for (int bb = 0; bb < NB; ++bb)
+#pragma unroll
+        for (int aa = 0; aa < NA; ++aa) {
+            const int li = threadIdx.x + 32 * aa, lj = threadIdx.y + BY * bb;
+            const int gI = I0 + li, gJ = J0 + lj;
+            int mI = gI < 0 ? -gI : (gI > nx ? 2 * nx - gI : gI);
+            int mJ = gJ < 0 ? -gJ : (gJ > ny ? 2 * ny - gJ : gJ);
+            mI = mI < 0 ? 0 : (mI > nx ? nx : mI);
+            mJ = mJ < 0 ? 0 : (mJ > ny ? ny : mJ);
+            const size_t g = (size_t)mJ * NX + mI;
+            const int sidx = lj * RW + li;
+            cp_async_elem(st + 0 * RN + sidx, xi + g);
+            cp_async_elem(st + 1 * RN + sidx, xpi + g);
+            cp_async_elem(st + 2 * RN + sidx, b + g);
+            cp_async_elem(st + 3 * RN + sidx, R.cC + g);
+            cp_async_elem(st + 4 * RN + sidx, R.cW + g);
+            cp_async_elem(st + 5 * RN + sidx, R.cE + g);
+            cp_async_elem(st + 6 * RN + sidx, R.cS + g);
+            cp_async_elem(st + 7 * RN + sidx, R.cN + g);
+        }
+}
+
+// Sweep one staged tile (origin I0, J0) and write it back; same arithmetic as cheb_tile.
+template <typename T, int NA, int NB, int BY, int K>
+__device__ __forceinline__ void cheb_sweep_staged(const Rows<T>& R, const T* st, T* xs0, T* xs1,
+                                                  int I0, int J0, const T (&c1s)[K],
+                                                  const T (&c2s)[K], T* __restrict__ xo,
+                                                  T* __restrict__ xpo, T& rsum, T& dmax,
+                                                  int next_tile, int ntx, int ntiles,
+                                                  const T* b, const T* xi, const T* xpi, T* stn)
+{
+    constexpr int RW = 32 * NA, RH = BY * NB, RN = RW * RH, NN = NA * NB;
+    constexpr int TX = RW - 2 * K, TY = RH - 2 * K;
+    const int nx = R.nx, ny = R.ny, NX = nx + 1;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    T xa[NN], rbd[NN], rwW[NN], rwE[NN], rwS[NN], rwN[NN];
+    // the thread's own staged nodes (its own copies: complete after wait_group)
+#pragma unroll
+    for (int bb = 0; bb < NB; ++bb)
+#pragma unroll
+        for (int aa = 0; aa < NA; ++aa) {
+            const int li = tx + 32 * aa, lj = ty + BY * bb;
+            const int gI = I0 + li, gJ = J0 + lj;
+            const bool fx = gI < 0 || gI > nx, fy = gJ < 0 || gJ > ny;
+            const int sidx = lj * RW + li, q = bb * NA + aa;
+            const T ic = qdiv(T(1), st[3 * RN + sidx]);
+            xs0[sidx] = st[sidx];
+            xa[q] = st[RN + sidx];
+            rbd[q] = st[2 * RN + sidx] * ic;
+            const T cw = st[4 * RN + sidx] * ic, ce = st[5 * RN + sidx] * ic;
+            const T cs = st[6 * RN + sidx] * ic, cn = st[7 * RN + sidx] * ic;
+            rwW[q] = fx ? ce : cw;
+            rwE[q] = fx ? cw : ce;
+            rwS[q] = fy ? cn : cs;
+            rwN[q] = fy ? cs : cn;
+        }
+    // the next tile's copies refill this thread's staging slots (already taken above) while
+    // the current tile is swept
+    if (next_tile < ntiles) {
+        int In, Jn;
+        tile_origin<TX, TY, K>(next_tile, ntx, In, Jn);
+        cheb_fetch<T, NA, NB, BY>(R, b, xi, xpi, In, Jn, stn);
+    }
+    cp_async_commit();
+    __syncthreads();
+    T* cur = xs0;
+    T* nxt = xs1;
+    rsum = T(0);
+    dmax = T(0);
+#pragma unroll
+    for (int sw = 0; sw < K; ++sw) {
+        const T c1 = c1s[sw], c2 = c2s[sw];
+#pragma unroll
+        for (int bb = 0; bb < NB; ++bb)
+#pragma unroll
+            for (int aa = 0; aa < NA; ++aa) {
+                const int li = tx + 32 * aa, lj = ty + BY * bb;
+                if (li > sw && li < RW - 1 - sw && lj > sw && lj < RH - 1 - sw) {
+                    const int sidx = lj * RW + li;
+                    const int q = bb * NA + aa;
+                    const T xc = cur[sidx];
+                    const T r = rbd[q] - xc -
+                                (rwW[q] * cur[sidx - 1] + rwE[q] * cur[sidx + 1] +
+                                 rwS[q] * cur[sidx - RW] + rwN[q] * cur[sidx + RW]);
+                    const T xn = xc + c1 * (xc - xa[q]) + c2 * r;
+                    nxt[sidx] = xn;
+                    xa[q] = xc;
+                    if (sw == K - 1 && li >= K && li < RW - K && lj >= K && lj < RH - K &&
+                        I0 + li <= nx && J0 + lj <= ny) {
+                        rsum = fma(r, r, rsum);
+                        dmax = tmax(dmax, T(fabs(xn - xc)));
+                    }
+                }
+            }
+        __syncthreads();
+        T* tmp = cur; cur = nxt; nxt = tmp;
+    }
+#pragma unroll
+    for (int bb = 0; bb < NB; ++bb)
+#pragma unroll
+        for (int aa = 0; aa < NA; ++aa) {
+            const int li = tx + 32 * aa, lj = ty + BY * bb;
+            const int gI = I0 + li, gJ = J0 + lj;
+            if (li >= K && li < RW - K && lj >= K && lj < RH - K && gI <= nx && gJ <= ny) {
+                const size_t g = (size_t)gJ * NX + gI;
+                xo[g] = cur[lj * RW + li];
+                xpo[g] = xa[bb * NA + aa];
+            }
+        }
+}
+
 // Last block of a pass: residual test (or criterion (32) on max |dx|), and the next K weights.
 __device__ __forceinline__ void cheb_finish(SolveCtl* ctl, const double (&acc)[2], int K)
 {

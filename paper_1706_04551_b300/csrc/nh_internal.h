@@ -104,10 +104,13 @@ size_t cheb_tiles(const Prm<T>& P);
 template <typename T>
 size_t asm_tiles(const Prm<T>& P);   // blocks of the 2D assembly (3 partials each)
 // One pass: (x, x_{k-1}) from (xi, xpi) to (xo, xpo); variant 0: weights in shared memory
-// (2 blocks / SM); 1: weights in registers (1 block)
+// (2 blocks / SM); 1: weights in registers (1 block); 2: pipelined persistent grid (copies
+// of the next tile overlap the sweeps of the current one)
 template <typename T>
 int launch_cheb_pass(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, const T* xi,
                      const T* xpi, T* xo, T* xpo, double* partials, int variant);
+template <typename T>
+int cheb_pass_forms();   // number of pass forms (variants 0 .. n-1)
 template <typename T>
 void launch_matvec2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* x, T* y);
 template <typename T>
