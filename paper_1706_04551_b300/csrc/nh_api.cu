@@ -749,8 +749,8 @@ struct Impl : Base {
     void choose_pass_variant()
     {
         const int nv = cheb_pass_forms<T>();
-        double sum[8] = {};
-        int cnt[8] = {};
+        double sum[16] = {};
+        int cnt[16] = {};
         // the first pass of each form warms it up and is not counted
         for (int k = nv; k < vt_used / 2; ++k) {
             float ms = 0.f;

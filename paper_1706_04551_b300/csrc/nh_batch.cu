@@ -495,12 +495,13 @@ kb_corr(Arena<T> A, const int2* __restrict__ wl, int nw, const T* eta, const T* 
         const long long nn = (long long)(P.nx + 1) * (P.ny + 1);
         DomState& s = A.ds[it.x];
         const T de = bfac * (T)s.dt;
-        double acc[1] = {0.0};
+        T lam = T(0);
         int bad = 0;
         for (long long k = (long long)it.y * kChunk + threadIdx.x;
              k < nn && k < (long long)(it.y + 1) * kChunk; k += blockDim.x)
             corr_node(P, eta + c, H + c, q1k + c, q2k + c, ws + n, p + n, dp + n, pout + n, de,
-                      with_p, eo + c, q1o + c, q2o + c, wo + n, final_stage, k, acc[0], bad);
+                      with_p, eo + c, q1o + c, q2o + c, wo + n, final_stage, k, lam, bad);
+        double acc[1] = {(double)lam};
         if (bad) atomicOr(&s.nonfinite, 1);
         if (final_stage) {
             if (dom_reduce<1, 1u>(acc, A.partials + D.poff, &A.stctl[it.x].counter, it.y,

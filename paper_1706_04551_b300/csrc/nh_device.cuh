@@ -516,6 +516,8 @@ asm_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
     const T inv2dx = T(1) / (T(2) * P.dx), inv2dy = T(1) / (T(2) * P.dy);
     const T scale = T(8) * P.dx * P.dy / de;
     const T rxl = P.dy / P.dx, ryl = P.dx / P.dy;
+    // per-thread sums over its few nodes in T; the block and grid sums are FP64
+    T s0 = T(0), s1 = T(0), s2 = T(0);
     for (int t = tid; t < TX * TY; t += nt) {
         const int li = t % TX, lj = t / TX;
         const int I = I0 + li, J = J0 + lj;
@@ -544,7 +546,7 @@ asm_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
                    + ((T(2) * hc - Yi) * q2N - (T(2) * hc + Yi) * q2S) * inv2dy
                    + T(2) * hc * wv;
         const T bval = -scale * Bs;
-        acc[0] += (double)bval * (double)bval;
+        s0 = fma(bval, bval, s0);
         if (with_coef) {
             const T Xa = Xc[ka], Xb = Xc[kb], Xd = Xc[kd], Xe = Xc[ke];
             const T Ya = Yc[ka], Yb = Yc[kb], Yd = Yc[kd], Ye = Yc[ke];
@@ -559,10 +561,10 @@ asm_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
             const T dC = T(16) * P.dx * P.dy + rxl * (bmx * amE + bpx * apW)
                        + ryl * (bmy * amN + bpy * apS);
             cE[nidx] = vE; cW[nidx] = vW; cN[nidx] = vN; cS[nidx] = vS; cC[nidx] = dC;
-            const T id = T(1) / fabs(dC);
+            const T id = qdiv(T(1), fabs(dC));
             const T bs = bval * id;
-            acc[1] += (double)bs * (double)bs;
-            acc[2] = fmax(acc[2], (double)((fabs(vE) + fabs(vW) + fabs(vN) + fabs(vS)) * id));
+            s1 = fma(bs, bs, s1);
+            s2 = tmax(s2, (fabs(vE) + fabs(vW) + fabs(vN) + fabs(vS)) * id);
             if (resid_form) {
                 const int Iw = map_node(I - 1, P.nx), Ie = map_node(I + 1, P.nx);
                 const int Js = map_node(J - 1, P.ny), Jn = map_node(J + 1, P.ny);
@@ -579,6 +581,9 @@ asm_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
             rhs[nidx] = bval;
         }
     }
+    acc[0] += (double)s0;
+    acc[1] += (double)s1;
+    acc[2] = fmax(acc[2], (double)s2);
 }
 
 // Last block of an assembly: store the reductions, reset the solve and, for the
@@ -773,104 +778,64 @@ cheb_tile(const Rows<T>& R, const T* __restrict__ b, const T* __restrict__ xi,
         }
 }
 
-// ---- pipelined form of the pass: a persistent block walks tiles t, t + G, ...; the eight
-// node arrays of the next tile are copied into shared memory with cp.async while the
-// current tile is swept, so the copies overlap the sweeps.
-
-__device__ __forceinline__ void cp_async_elem(void* smem_dst, const float* src)
-{
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_elem(void* smem_dst, const double* src)
-{
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" :: "r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-// Region geometry of tile `tile` (row-major over ntx tiles per row).
-template <int TX, int TY, int K>
-__device__ __forceinline__ void tile_origin(int tile, int ntx, int& I0, int& J0)
-{
-    I0 = (tile % ntx) * TX - K;
-    J0 = (tile / ntx) * TY - K;
-}
-
-// Issue the copies of this thread's region nodes of the tile with origin (I0, J0) into the
-// staging arrays st[8][RN] (x, x_{k-1}, b, cC, cW, cE, cS, cN), mirrored outside the domain.
-template <typename T, int NA, int NB, int BY>
-__device__ __forceinline__ void cheb_fetch(const Rows<T>& R, const T* b, const T* xi,
-                                           const T* xpi, int I0, int J0, T* st)
-{
-    constexpr int RW = 32 * NA, RH = BY * NB, RN = RW * RH;
-    const int nx = R.nx, ny = R.ny, NX = nx + 1;
-#pragma unroll
-    for (int bb = 0; bb < NB; ++bb)
-#pragma unroll
-        for (int aa = 0; aa < NA; ++aa) {
-            const int li = threadIdx.x + 32 * aa, lj = threadIdx.y + BY * bb;
-            const int gI = I0 + li, gJ = J0 + lj;
-            int mI = gI < 0 ? -gI : (gI > nx ? 2 * nx - gI : gI);
-            int mJ = gJ < 0 ? -gJ : (gJ > ny ? 2 * ny - gJ : gJ);
-            mI = mI < 0 ? 0 : (mI > nx ? nx : mI);
-            mJ = mJ < 0 ? 0 : (mJ > ny ? ny : mJ);
-            const size_t g = (size_t)mJ * NX + mI;
-            const int sidx = lj * RW + li;
-            cp_async_elem(st + 0 * RN + sidx, xi + g);
-            cp_async_elem(st + 1 * RN + sidx, xpi + g);
-            cp_async_elem(st + 2 * RN + sidx, b + g);
-            cp_async_elem(st + 3 * RN + sidx, R.cC + g);
-            cp_async_elem(st + 4 * RN + sidx, R.cW + g);
-            cp_async_elem(st + 5 * RN + sidx, R.cE + g);
-            cp_async_elem(st + 6 * RN + sidx, R.cS + g);
-            cp_async_elem(st + 7 * RN + sidx, R.cN + g);
-        }
-}
-
-// Sweep one staged tile (origin I0, J0) and write it back; same arithmetic as cheb_tile.
+// Form of cheb_tile with the weights in registers and the two x buffers padded by one node
+// on every side (zeros): every sweep updates all of the thread's region nodes without
+// bounds tests (values near the region edge go stale, one node per sweep, and never reach
+// the tile interior within the K sweeps).  Same arithmetic for the interior nodes.
 template <typename T, int NA, int NB, int BY, int K>
-__device__ __forceinline__ void cheb_sweep_staged(const Rows<T>& R, const T* st, T* xs0, T* xs1,
-                                                  int I0, int J0, const T (&c1s)[K],
-                                                  const T (&c2s)[K], T* __restrict__ xo,
-                                                  T* __restrict__ xpo, T& rsum, T& dmax,
-                                                  int next_tile, int ntx, int ntiles,
-                                                  const T* b, const T* xi, const T* xpi, T* stn)
+__device__ __forceinline__ void
+cheb_tile_pad(const Rows<T>& R, const T* __restrict__ b, const T* __restrict__ xi,
+              const T* __restrict__ xpi, T* __restrict__ xo, T* __restrict__ xpo,
+              const SolveCtl* ctl, int bx, int by, T* smem, T& rsum, T& dmax)
 {
-    constexpr int RW = 32 * NA, RH = BY * NB, RN = RW * RH, NN = NA * NB;
+    constexpr int RW = 32 * NA, RH = BY * NB, NN = NA * NB;
+    constexpr int PW = RW + 2, PN = PW * (RH + 2);
     constexpr int TX = RW - 2 * K, TY = RH - 2 * K;
+    T* xs0 = smem;
+    T* xs1 = xs0 + PN;
+    T rbd[NN], rwW[NN], rwE[NN], rwS[NN], rwN[NN], xa[NN];
     const int nx = R.nx, ny = R.ny, NX = nx + 1;
+    const int I0 = bx * TX - K, J0 = by * TY - K;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    T xa[NN], rbd[NN], rwW[NN], rwE[NN], rwS[NN], rwN[NN];
-    // the thread's own staged nodes (its own copies: complete after wait_group)
+    const int tid = ty * 32 + tx, nthr = 32 * BY;
+    // the pad ring of both buffers: rows 0 and RH + 1 (PW each), then columns 0 and RW + 1
+    // of rows 1 .. RH
+    for (int t = tid; t < 2 * (PW + RH); t += nthr) {
+        const int k = t % (PW + RH);
+        T* buf = t < PW + RH ? xs0 : xs1;
+        if (k < PW) { buf[k] = T(0); buf[(RH + 1) * PW + k] = T(0); }
+        else { const int r = k - PW + 1; buf[r * PW] = T(0); buf[r * PW + RW + 1] = T(0); }
+    }
 #pragma unroll
     for (int bb = 0; bb < NB; ++bb)
 #pragma unroll
         for (int aa = 0; aa < NA; ++aa) {
             const int li = tx + 32 * aa, lj = ty + BY * bb;
             const int gI = I0 + li, gJ = J0 + lj;
-            const bool fx = gI < 0 || gI > nx, fy = gJ < 0 || gJ > ny;
-            const int sidx = lj * RW + li, q = bb * NA + aa;
-            const T ic = qdiv(T(1), st[3 * RN + sidx]);
-            xs0[sidx] = st[sidx];
-            xa[q] = st[RN + sidx];
-            rbd[q] = st[2 * RN + sidx] * ic;
-            const T cw = st[4 * RN + sidx] * ic, ce = st[5 * RN + sidx] * ic;
-            const T cs = st[6 * RN + sidx] * ic, cn = st[7 * RN + sidx] * ic;
+            int mI = gI < 0 ? -gI : (gI > nx ? 2 * nx - gI : gI);
+            int mJ = gJ < 0 ? -gJ : (gJ > ny ? 2 * ny - gJ : gJ);
+            const bool fx = mI != gI, fy = mJ != gJ;
+            mI = mI < 0 ? 0 : (mI > nx ? nx : mI);
+            mJ = mJ < 0 ? 0 : (mJ > ny ? ny : mJ);
+            const size_t g = (size_t)mJ * NX + mI;
+            const int q = bb * NA + aa;
+            const T ic = qdiv(T(1), R.cC[g]);
+            xs0[(lj + 1) * PW + li + 1] = xi[g];
+            xa[q] = xpi[g];
+            rbd[q] = b[g] * ic;
+            const T cw = R.cW[g] * ic, ce = R.cE[g] * ic;
+            const T cs = R.cS[g] * ic, cn = R.cN[g] * ic;
             rwW[q] = fx ? ce : cw;
             rwE[q] = fx ? cw : ce;
             rwS[q] = fy ? cn : cs;
             rwN[q] = fy ? cs : cn;
         }
-    // the next tile's copies refill this thread's staging slots (already taken above) while
-    // the current tile is swept
-    if (next_tile < ntiles) {
-        int In, Jn;
-        tile_origin<TX, TY, K>(next_tile, ntx, In, Jn);
-        cheb_fetch<T, NA, NB, BY>(R, b, xi, xpi, In, Jn, stn);
+    T c1s[K], c2s[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        if (sizeof(T) == 4) { c1s[k] = (T)ctl->c1f[k]; c2s[k] = (T)ctl->c2f[k]; }
+        else { c1s[k] = (T)ctl->c1[k]; c2s[k] = (T)ctl->c2[k]; }
     }
-    cp_async_commit();
     __syncthreads();
     T* cur = xs0;
     T* nxt = xs1;
@@ -884,21 +849,19 @@ __device__ __forceinline__ void cheb_sweep_staged(const Rows<T>& R, const T* st,
 #pragma unroll
             for (int aa = 0; aa < NA; ++aa) {
                 const int li = tx + 32 * aa, lj = ty + BY * bb;
-                if (li > sw && li < RW - 1 - sw && lj > sw && lj < RH - 1 - sw) {
-                    const int sidx = lj * RW + li;
-                    const int q = bb * NA + aa;
-                    const T xc = cur[sidx];
-                    const T r = rbd[q] - xc -
-                                (rwW[q] * cur[sidx - 1] + rwE[q] * cur[sidx + 1] +
-                                 rwS[q] * cur[sidx - RW] + rwN[q] * cur[sidx + RW]);
-                    const T xn = xc + c1 * (xc - xa[q]) + c2 * r;
-                    nxt[sidx] = xn;
-                    xa[q] = xc;
-                    if (sw == K - 1 && li >= K && li < RW - K && lj >= K && lj < RH - K &&
-                        I0 + li <= nx && J0 + lj <= ny) {
-                        rsum = fma(r, r, rsum);
-                        dmax = tmax(dmax, T(fabs(xn - xc)));
-                    }
+                const int p = (lj + 1) * PW + li + 1;
+                const int q = bb * NA + aa;
+                const T xc = cur[p];
+                const T r = rbd[q] - xc -
+                            (rwW[q] * cur[p - 1] + rwE[q] * cur[p + 1] + rwS[q] * cur[p - PW] +
+                             rwN[q] * cur[p + PW]);
+                const T xn = xc + c1 * (xc - xa[q]) + c2 * r;
+                nxt[p] = xn;
+                xa[q] = xc;
+                if (sw == K - 1 && li >= K && li < RW - K && lj >= K && lj < RH - K &&
+                    I0 + li <= nx && J0 + lj <= ny) {
+                    rsum = fma(r, r, rsum);
+                    dmax = tmax(dmax, T(fabs(xn - xc)));
                 }
             }
         __syncthreads();
@@ -912,7 +875,7 @@ __device__ __forceinline__ void cheb_sweep_staged(const Rows<T>& R, const T* st,
             const int gI = I0 + li, gJ = J0 + lj;
             if (li >= K && li < RW - K && lj >= K && lj < RH - K && gI <= nx && gJ <= ny) {
                 const size_t g = (size_t)gJ * NX + gI;
-                xo[g] = cur[lj * RW + li];
+                xo[g] = cur[(lj + 1) * PW + li + 1];
                 xpo[g] = xa[bb * NA + aa];
             }
         }
@@ -954,7 +917,7 @@ corr_node(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
           const T* __restrict__ q1k, const T* __restrict__ q2k, const T* __restrict__ ws,
           const T* __restrict__ p, const T* __restrict__ dp, T* __restrict__ pout, T de,
           int with_p, T* __restrict__ eo, T* __restrict__ q1o, T* __restrict__ q2o,
-          T* __restrict__ wo, int final_stage, long long idx, double& lam, int& bad)
+          T* __restrict__ wo, int final_stage, long long idx, T& lam, int& bad)
 {
     const T d2 = P.delta * P.delta, d4 = d2 * d2;
     const int nxn = P.nx + 1;
@@ -1014,7 +977,7 @@ corr_node(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
             if (!isfinite(e) || !isfinite(a1) || !isfinite(a2)) bad = 1;
             if (final_stage) {
                 const T u = desing(h, a1, d4), v = desing(h, a2, d4), cw = sqrt(P.g * h);
-                lam = fmax(lam, (double)((fabs(u) + cw) / P.dx + (fabs(v) + cw) / P.dy));
+                lam = tmax(lam, (fabs(u) + cw) / P.dx + (fabs(v) + cw) / P.dy);
             }
         }
     }

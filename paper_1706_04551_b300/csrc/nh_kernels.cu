@@ -194,7 +194,7 @@ k_bicg_C(Rows<T> R, T* __restrict__ r, const T* __restrict__ rh, const T* __rest
     }
 }
 
-template <typename T, int NA, int NB, int BY, int K, bool REGW, int MINB>
+template <typename T, int NA, int NB, int BY, int K, bool REGW, int MINB, bool PAD>
 __global__ void __launch_bounds__(32 * BY, MINB)
 k_cheb_pass2(Rows<T> R, const T* __restrict__ b, const T* __restrict__ xi,
              const T* __restrict__ xpi, T* __restrict__ xo, T* __restrict__ xpo,
@@ -203,61 +203,17 @@ k_cheb_pass2(Rows<T> R, const T* __restrict__ b, const T* __restrict__ xi,
     if (ctl->done) return;
     extern __shared__ unsigned char cheb2_smem[];
     T rsum, dmax;
-    cheb_tile<T, NA, NB, BY, K, REGW>(R, b, xi, xpi, xo, xpo, ctl, blockIdx.x, blockIdx.y,
-                                      reinterpret_cast<T*>(cheb2_smem), rsum, dmax);
+    if constexpr (PAD)
+        cheb_tile_pad<T, NA, NB, BY, K>(R, b, xi, xpi, xo, xpo, ctl, blockIdx.x, blockIdx.y,
+                                        reinterpret_cast<T*>(cheb2_smem), rsum, dmax);
+    else
+        cheb_tile<T, NA, NB, BY, K, REGW>(R, b, xi, xpi, xo, xpo, ctl, blockIdx.x, blockIdx.y,
+                                          reinterpret_cast<T*>(cheb2_smem), rsum, dmax);
     double acc[2];
     if (dom_reduce_sum_max_f((float)rsum, (float)dmax, partials, &ctl->counter, acc,
                              blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y) &&
         threadIdx.x == 0 && threadIdx.y == 0)
         cheb_finish(ctl, acc, K);
-}
-
-// Pipelined pass: a persistent grid (one block per SM) walks the tiles; the copies of tile
-// t + G into the staging arrays are issued as soon as each thread has taken its own staged
-// nodes of tile t (a thread only ever reads and fills its own staging slots), so they
-// overlap the sweeps of tile t.  The residual sums are reduced per tile exactly as in
-// k_cheb_pass2, so both give the same iterates.
-template <typename T, int NA, int NB, int BY, int K>
-__global__ void __launch_bounds__(32 * BY, 1)
-k_cheb_pipe(Rows<T> R, const T* __restrict__ b, const T* __restrict__ xi,
-            const T* __restrict__ xpi, T* __restrict__ xo, T* __restrict__ xpo,
-            double* partials, SolveCtl* ctl, int ntx, int ntiles)
-{
-    if (ctl->done) return;
-    constexpr int RN = 32 * NA * BY * NB;
-    constexpr int TX = 32 * NA - 2 * K, TY = BY * NB - 2 * K;
-    extern __shared__ unsigned char cheb_pipe_smem[];
-    T* st = reinterpret_cast<T*>(cheb_pipe_smem);
-    T* xs0 = st + 8 * RN;
-    T* xs1 = xs0 + RN;
-    T c1s[K], c2s[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        if (sizeof(T) == 4) { c1s[k] = (T)ctl->c1f[k]; c2s[k] = (T)ctl->c2f[k]; }
-        else { c1s[k] = (T)ctl->c1[k]; c2s[k] = (T)ctl->c2[k]; }
-    }
-    int tile = blockIdx.x;
-    if (tile < ntiles) {
-        int I0, J0;
-        tile_origin<TX, TY, K>(tile, ntx, I0, J0);
-        cheb_fetch<T, NA, NB, BY>(R, b, xi, xpi, I0, J0, st);
-    }
-    cp_async_commit();
-    for (; tile < ntiles; tile += gridDim.x) {
-        cp_async_wait_all();   // this thread's copies of `tile` (the next ones are issued below)
-        __syncthreads();       // previous tile's write-back done before xs0 is refilled
-        int I0, J0;
-        tile_origin<TX, TY, K>(tile, ntx, I0, J0);
-        T rsum, dmax;
-        cheb_sweep_staged<T, NA, NB, BY, K>(R, st, xs0, xs1, I0, J0, c1s, c2s, xo, xpo, rsum,
-                                            dmax, tile + gridDim.x, ntx, ntiles, b, xi, xpi, st);
-        double acc[2];
-        if (dom_reduce_sum_max_f((float)rsum, (float)dmax, partials, &ctl->counter, acc,
-                                 (unsigned)tile, (unsigned)ntiles) &&
-            threadIdx.x == 0 && threadIdx.y == 0)
-            cheb_finish(ctl, acc, K);
-    }
-    cp_async_wait_all();
 }
 
 template <typename T>
@@ -269,11 +225,12 @@ k_corr2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
          T* __restrict__ q2o, T* __restrict__ wo, int final_stage, double* partials,
          StepCtl* st)
 {
-    double acc[1] = {0.0};
+    T lam = T(0);
     int bad = 0;
     GRID_STRIDE(idx, (long long)(P.nx + 1) * (P.ny + 1))
         corr_node(P, eta, H, q1k, q2k, ws, p, dp, pout, de, with_p, eo, q1o, q2o, wo, final_stage,
-                  idx, acc[0], bad);
+                  idx, lam, bad);
+    double acc[1] = {(double)lam};
     if (bad) atomicOr(&st->nonfinite, 1);
     if (final_stage) {
         if (grid_reduce<1, 1u>(acc, partials, &st->counter) && threadIdx.x == 0) st->lam = acc[0];
@@ -677,78 +634,56 @@ size_t cheb_tiles(const Prm<T>& P)
 
 // One form of the pass: region (32 NA) x (BY NB) nodes, 32 x BY threads, weights in
 // registers (REGW) or shared memory, at least MINB blocks per SM.
-template <typename T, int NA, int NB, int BY, bool REGW, int MINB>
+template <typename T, int NA, int NB, int BY, bool REGW, int MINB, bool PAD = false>
 int launch_cheb_cfg(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, const T* xi,
                     const T* xpi, T* xo, T* xpo, double* partials)
 {
     constexpr int K = 4;
     constexpr int TX = 32 * NA - 2 * K, TY = BY * NB - 2 * K;
-    constexpr size_t smem = (REGW ? 2 : 7) * (size_t)(32 * NA) * (BY * NB) * sizeof(T);
+    constexpr size_t smem = PAD ? 2 * (size_t)(32 * NA + 2) * (BY * NB + 2) * sizeof(T)
+                                : (REGW ? 2 : 7) * (size_t)(32 * NA) * (BY * NB) * sizeof(T);
     static bool attr_set = false;
     if (!attr_set) {
-        if (cudaFuncSetAttribute(k_cheb_pass2<T, NA, NB, BY, K, REGW, MINB>,
+        if (cudaFuncSetAttribute(k_cheb_pass2<T, NA, NB, BY, K, REGW, MINB, PAD>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return -1;
         attr_set = true;
     }
     dim3 grid((P.nx + 1 + TX - 1) / TX, (P.ny + 1 + TY - 1) / TY);
-    k_cheb_pass2<T, NA, NB, BY, K, REGW, MINB><<<grid, dim3(32, BY), smem, s>>>(
+    k_cheb_pass2<T, NA, NB, BY, K, REGW, MINB, PAD><<<grid, dim3(32, BY), smem, s>>>(
         rows_of(P, B), B.rhs, xi, xpi, xo, xpo, partials, B.sctl);
     return 0;
 }
 
-template <typename T>
-int launch_cheb_pipe(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, const T* xi,
-                     const T* xpi, T* xo, T* xpo, double* partials)
-{
-    using C = ChebCfg<T>;
-    constexpr int TX = 32 * C::NA - 2 * C::K, TY = C::BY * C::NB - 2 * C::K;
-    constexpr size_t smem = 10 * (size_t)(32 * C::NA) * (C::BY * C::NB) * sizeof(T);
-    static int nsm = 0;
-    if (!nsm) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        if (nsm <= 0) nsm = 148;
-        if (cudaFuncSetAttribute(k_cheb_pipe<T, C::NA, C::NB, C::BY, C::K>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess) {
-            nsm = 0;
-            return -1;
-        }
-    }
-    const int ntx = (P.nx + 1 + TX - 1) / TX, nty = (P.ny + 1 + TY - 1) / TY;
-    const int ntiles = ntx * nty;
-    const int grid = ntiles < nsm ? ntiles : nsm;
-    k_cheb_pipe<T, C::NA, C::NB, C::BY, C::K><<<grid, dim3(32, C::BY), smem, s>>>(
-        rows_of(P, B), B.rhs, xi, xpi, xo, xpo, partials, B.sctl, ntx, ntiles);
-    return 0;
-}
 
 // The pass forms the handle chooses from (by timing its first passes; all give the same
-// iterates): FP32 0: 128x32 region, shared-memory weights, 2 blocks / SM; 1: the same with
-// register weights; 2: pipelined persistent; 3, 4: 64x32 with register weights, 2 / 3
-// blocks; 5: 64x64, shared-memory weights; 6: 64x32, shared-memory weights, 3 blocks.
-// FP64 0: 64x32, shared memory; 1: 64x32, registers; 2: pipelined.
-template <typename T> int cheb_pass_forms() { return sizeof(T) == 4 ? 7 : 3; }
+// iterates).  FP32 0: 128x32 region, shared-memory weights, 2 blocks / SM; 1: the same
+// with register weights, 1 block; 2, 3: 64x32 with register weights, 2 / 3 blocks;
+// 4: 64x64, shared-memory weights; 5: 64x32, shared-memory weights, 3 blocks; 6: 64x48,
+// register weights, 2 blocks; 7, 8: forms 3 and 6 with padded buffers and no bounds tests.
+// FP64 0: 64x32, shared memory; 1: 64x32, registers; 2: 64x32, registers, padded.
+template <typename T> int cheb_pass_forms() { return sizeof(T) == 4 ? 9 : 3; }
 
 template <typename T>
 int launch_cheb_pass(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, const T* xi,
                      const T* xpi, T* xo, T* xpo, double* partials, int variant)
 {
-    if (variant == 2) return launch_cheb_pipe<T>(P, s, B, xi, xpi, xo, xpo, partials);
     if constexpr (sizeof(T) == 4) {
         switch (variant) {
         case 1: return launch_cheb_cfg<T, 4, 2, 16, true, 1>(P, s, B, xi, xpi, xo, xpo, partials);
-        case 3: return launch_cheb_cfg<T, 2, 2, 16, true, 2>(P, s, B, xi, xpi, xo, xpo, partials);
-        case 4: return launch_cheb_cfg<T, 2, 2, 16, true, 3>(P, s, B, xi, xpi, xo, xpo, partials);
-        case 5: return launch_cheb_cfg<T, 2, 4, 16, false, 2>(P, s, B, xi, xpi, xo, xpo, partials);
-        case 6: return launch_cheb_cfg<T, 2, 2, 16, false, 3>(P, s, B, xi, xpi, xo, xpo, partials);
+        case 2: return launch_cheb_cfg<T, 2, 2, 16, true, 2>(P, s, B, xi, xpi, xo, xpo, partials);
+        case 3: return launch_cheb_cfg<T, 2, 2, 16, true, 3>(P, s, B, xi, xpi, xo, xpo, partials);
+        case 4: return launch_cheb_cfg<T, 2, 4, 16, false, 2>(P, s, B, xi, xpi, xo, xpo, partials);
+        case 5: return launch_cheb_cfg<T, 2, 2, 16, false, 3>(P, s, B, xi, xpi, xo, xpo, partials);
+        case 6: return launch_cheb_cfg<T, 2, 3, 16, true, 2>(P, s, B, xi, xpi, xo, xpo, partials);
+        case 7: return launch_cheb_cfg<T, 2, 2, 16, true, 3, true>(P, s, B, xi, xpi, xo, xpo, partials);
+        case 8: return launch_cheb_cfg<T, 2, 3, 16, true, 2, true>(P, s, B, xi, xpi, xo, xpo, partials);
         default: return launch_cheb_cfg<T, 4, 2, 16, false, 2>(P, s, B, xi, xpi, xo, xpo, partials);
         }
     } else {
         if (variant == 1) return launch_cheb_cfg<T, 2, 2, 16, true, 1>(P, s, B, xi, xpi, xo, xpo, partials);
+        if (variant == 2) return launch_cheb_cfg<T, 2, 2, 16, true, 1, true>(P, s, B, xi, xpi, xo, xpo, partials);
         return launch_cheb_cfg<T, 2, 2, 16, false, 2>(P, s, B, xi, xpi, xo, xpo, partials);
     }
 }
