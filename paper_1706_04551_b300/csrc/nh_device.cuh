@@ -437,9 +437,10 @@ break_cell(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ q1,
         }
         const size_t c = (size_t)idx;
         T h = tmax(eta[c] + H[c], T(0));
-        T dq = (qq[1] - qq[0]) / (T(2) * P.dx) + (qq[3] - qq[2]) / (T(2) * P.dy);
-        T du = (uu[1] - uu[0]) / (T(2) * P.dx) + (uu[3] - uu[2]) / (T(2) * P.dy);
-        T Hx = (HH[1] - HH[0]) / (T(2) * P.dx), Hy = (HH[3] - HH[2]) / (T(2) * P.dy);
+        const T i2x = T(1) / (T(2) * P.dx), i2y = T(1) / (T(2) * P.dy);
+        T dq = (qq[1] - qq[0]) * i2x + (qq[3] - qq[2]) * i2y;
+        T du = (uu[1] - uu[0]) * i2x + (uu[3] - uu[2]) * i2y;
+        T Hx = (HH[1] - HH[0]) * i2x, Hy = (HH[3] - HH[2]) * i2y;
         T nu = nu_break(h, dq, P.g, P.B1, P.hdry);
         q1o[c] = q1[c] + de * T(2) * nu * du * Hx;
         q2o[c] = q2[c] + de * T(2) * nu * du * Hy;
@@ -965,10 +966,11 @@ corr_node(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
                 auto pat = [&](size_t m) { return p[m] + dp[m]; };
                 const T pSW = pat((size_t)J * nxn + I), pSE = pat((size_t)J * nxn + I + 1);
                 const T pNW = pat((size_t)(J + 1) * nxn + I), pNE = pat((size_t)(J + 1) * nxn + I + 1);
-                const T TN = -T(0.5) * h * (pNE - pNW) / P.dx - T(0.25) * (pNE + pNW) * X / P.dx;
-                const T TS = -T(0.5) * h * (pSE - pSW) / P.dx - T(0.25) * (pSE + pSW) * X / P.dx;
-                const T TE = -T(0.5) * h * (pNE - pSE) / P.dy - T(0.25) * (pNE + pSE) * Y / P.dy;
-                const T TW = -T(0.5) * h * (pNW - pSW) / P.dy - T(0.25) * (pNW + pSW) * Y / P.dy;
+                const T idx_ = T(1) / P.dx, idy_ = T(1) / P.dy;
+                const T TN = (-T(0.5) * h * (pNE - pNW) - T(0.25) * (pNE + pNW) * X) * idx_;
+                const T TS = (-T(0.5) * h * (pSE - pSW) - T(0.25) * (pSE + pSW) * X) * idx_;
+                const T TE = (-T(0.5) * h * (pNE - pSE) - T(0.25) * (pNE + pSE) * Y) * idy_;
+                const T TW = (-T(0.5) * h * (pNW - pSW) - T(0.25) * (pNW + pSW) * Y) * idy_;
                 a1 += de * T(0.5) * (TN + TS);
                 a2 += de * T(0.5) * (TE + TW);
             }
@@ -976,8 +978,100 @@ corr_node(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
             eo[c] = e; q1o[c] = a1; q2o[c] = a2;
             if (!isfinite(e) || !isfinite(a1) || !isfinite(a2)) bad = 1;
             if (final_stage) {
-                const T u = desing(h, a1, d4), v = desing(h, a2, d4), cw = sqrt(P.g * h);
-                lam = tmax(lam, (fabs(u) + cw) / P.dx + (fabs(v) + cw) / P.dy);
+                const T u = desing(h, a1, d4), v = desing(h, a2, d4), cw = qsqrt(P.g * h);
+                lam = tmax(lam, (fabs(u) + cw) * (T(1) / P.dx) + (fabs(v) + cw) * (T(1) / P.dy));
+            }
+        }
+    }
+}
+
+// Tiled form of corr_node for a TX x TY tile of nodes (and the cells with the same (i, j)):
+// the block stages eta and H of the cells around the tile (a 1-cell ring) and p + dp of the
+// tile's nodes plus one row and column, so each value is loaded once per tile.  Same
+// arithmetic as corr_node.
+template <typename T, int TX, int TY>
+__device__ __forceinline__ void
+corr_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
+          const T* __restrict__ q1k, const T* __restrict__ q2k, const T* __restrict__ ws,
+          const T* __restrict__ p, const T* __restrict__ dp, T* __restrict__ pout, T de,
+          int with_p, T* __restrict__ eo, T* __restrict__ q1o, T* __restrict__ q2o,
+          T* __restrict__ wo, int final_stage, int bx, int by, T& lam, int& bad)
+{
+    constexpr int CW = TX + 2, CH = TY + 2, CN = CW * CH;   // cells I0-1 .. I0+TX
+    constexpr int NW = TX + 1, NH = TY + 1, NNd = NW * NH;  // nodes I0 .. I0+TX
+    __shared__ T se[CN], sH[CN], pn[NNd];
+    const T d2 = P.delta * P.delta, d4 = d2 * d2;
+    const int nx = P.nx, ny = P.ny, nxn = nx + 1;
+    const int I0 = bx * TX, J0 = by * TY;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int t = tid; t < CN; t += nt) {
+        const int li = t % CW, lj = t / CW;
+        int ci = I0 - 1 + li, cj = J0 - 1 + lj;
+        ci = ci > nx + 1 ? nx + 1 : ci;
+        cj = cj > ny + 1 ? ny + 1 : cj;
+        bool rx, ry;
+        const int ii = map_cell(ci, nx, P.bcw, P.bce, rx);
+        const int jj = map_cell(cj, ny, P.bcs, P.bcn, ry);
+        const size_t m = (size_t)jj * nx + ii;
+        se[t] = eta[m];
+        sH[t] = H[m];
+    }
+    if (with_p)
+        for (int t = tid; t < NNd; t += nt) {
+            const int I = I0 + t % NW, J = J0 + t / NW;
+            const size_t m = (size_t)(J > ny ? ny : J) * nxn + (I > nx ? nx : I);
+            pn[t] = p[m] + dp[m];
+        }
+    __syncthreads();
+    for (int t = tid; t < TX * TY; t += nt) {
+        const int li = t % TX, lj = t / TX;
+        const int I = I0 + li, J = J0 + lj;
+        if (I > nx || J > ny) continue;
+        const size_t nidx = (size_t)J * nxn + I;
+        const int ca = lj * CW + li;   // staged cell (I-1, J-1); b = ca + 1, d = ca + CW, e = d + 1
+        // node
+        T pc = T(0);
+        if (with_p) {
+            pc = pn[lj * NW + li];
+            const T hs = tmax(se[ca] + sH[ca], T(0)) + tmax(se[ca + 1] + sH[ca + 1], T(0)) +
+                         tmax(se[ca + CW] + sH[ca + CW], T(0)) +
+                         tmax(se[ca + CW + 1] + sH[ca + CW + 1], T(0));
+            const T hc = T(0.25) * hs;
+            const T wn = ws[nidx] + de * pc * desing(hc, T(1), d4);
+            wo[nidx] = wn;
+            pout[nidx] = pc;
+            if (!isfinite(wn) || !isfinite(pc)) bad = 1;
+        } else {
+            wo[nidx] = ws[nidx];
+            pout[nidx] = T(0);
+        }
+        // cell (i, j) = (I, J)
+        if (I < nx && J < ny) {
+            const size_t c = (size_t)J * nx + I;
+            const int ce = ca + CW + 1;   // staged cell (I, J)
+            const T e = se[ce], Hc = sH[ce];
+            const T h = tmax(e + Hc, T(0));
+            T a1 = q1k[c], a2 = q2k[c];
+            if (with_p) {
+                const T X = T(0.5) * ((se[ce + 1] - sH[ce + 1]) - (se[ce - 1] - sH[ce - 1]));
+                const T Y = T(0.5) * ((se[ce + CW] - sH[ce + CW]) - (se[ce - CW] - sH[ce - CW]));
+                const int nsw = lj * NW + li;
+                const T pSW = pn[nsw], pSE = pn[nsw + 1];
+                const T pNW = pn[nsw + NW], pNE = pn[nsw + NW + 1];
+                const T idx_ = T(1) / P.dx, idy_ = T(1) / P.dy;
+                const T TN = (-T(0.5) * h * (pNE - pNW) - T(0.25) * (pNE + pNW) * X) * idx_;
+                const T TS = (-T(0.5) * h * (pSE - pSW) - T(0.25) * (pSE + pSW) * X) * idx_;
+                const T TE = (-T(0.5) * h * (pNE - pSE) - T(0.25) * (pNE + pSE) * Y) * idy_;
+                const T TW = (-T(0.5) * h * (pNW - pSW) - T(0.25) * (pNW + pSW) * Y) * idy_;
+                a1 += de * T(0.5) * (TN + TS);
+                a2 += de * T(0.5) * (TE + TW);
+            }
+            if (h <= P.hdry) { a1 = T(0); a2 = T(0); }   // dry cells carry no discharge
+            eo[c] = e; q1o[c] = a1; q2o[c] = a2;
+            if (!isfinite(e) || !isfinite(a1) || !isfinite(a2)) bad = 1;
+            if (final_stage) {
+                const T u = desing(h, a1, d4), v = desing(h, a2, d4), cw = qsqrt(P.g * h);
+                lam = tmax(lam, (fabs(u) + cw) * (T(1) / P.dx) + (fabs(v) + cw) * (T(1) / P.dy));
             }
         }
     }

@@ -216,6 +216,25 @@ k_cheb_pass2(Rows<T> R, const T* __restrict__ b, const T* __restrict__ xi,
         cheb_finish(ctl, acc, K);
 }
 
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(256)
+k_corr2d_t(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
+           const T* __restrict__ q1k, const T* __restrict__ q2k, const T* __restrict__ ws,
+           const T* __restrict__ p, const T* __restrict__ dp, T* __restrict__ pout, T de,
+           int with_p, T* __restrict__ eo, T* __restrict__ q1o, T* __restrict__ q2o,
+           T* __restrict__ wo, int final_stage, double* partials, StepCtl* st)
+{
+    T lam = T(0);
+    int bad = 0;
+    corr_tile<T, TX, TY>(P, eta, H, q1k, q2k, ws, p, dp, pout, de, with_p, eo, q1o, q2o, wo,
+                         final_stage, blockIdx.x, blockIdx.y, lam, bad);
+    if (bad) atomicOr(&st->nonfinite, 1);
+    if (final_stage) {
+        double acc[1] = {(double)lam};
+        if (grid_reduce<1, 1u>(acc, partials, &st->counter) && threadIdx.x == 0) st->lam = acc[0];
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_corr2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
@@ -724,9 +743,11 @@ void launch_corr2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* 
                    const T* q2k, T de, int with_p, T* eo, T* q1o, T* q2o, T* wo, int final_stage,
                    double* partials, StepCtl* st)
 {
-    k_corr2d<T><<<L.nblk, kThreads, 0, L.s>>>(P, B.etas, B.H, q1k, q2k, B.ws, B.p, B.dp, B.palt,
-                                              de, with_p, eo, q1o, q2o, wo, final_stage, partials,
-                                              st);
+    constexpr int TX = 32, TY = 8;
+    dim3 grid((P.nx + 1 + TX - 1) / TX, (P.ny + 1 + TY - 1) / TY);
+    k_corr2d_t<T, TX, TY><<<grid, 256, 0, L.s>>>(P, B.etas, B.H, q1k, q2k, B.ws, B.p, B.dp,
+                                                 B.palt, de, with_p, eo, q1o, q2o, wo,
+                                                 final_stage, partials, st);
 }
 
 template <typename T>
