@@ -644,15 +644,16 @@ struct Cands<double> {
         const void* f[nh] = {(const void*)kb_hyp<double, 32, 8>, (const void*)kb_hyp<double, 16, 16>};
         return f[k];
     }
-    static Shape asm_shape(int k) { const Shape s[na] = {{32, 16, 256}, {32, 8, 256}}; return s[k]; }
+    // (static shared memory stays under 48 KB)
+    static Shape asm_shape(int k) { const Shape s[na] = {{32, 8, 256}, {16, 16, 256}}; return s[k]; }
     static AsmFn<double> assembly(int k)
     {
-        const AsmFn<double> f[na] = {run_asm<double, 32, 16>, run_asm<double, 32, 8>};
+        const AsmFn<double> f[na] = {run_asm<double, 32, 8>, run_asm<double, 16, 16>};
         return f[k];
     }
     static const void* asm_kernel(int k)
     {
-        const void* f[na] = {(const void*)kb_asm<double, 32, 16>, (const void*)kb_asm<double, 32, 8>};
+        const void* f[na] = {(const void*)kb_asm<double, 32, 8>, (const void*)kb_asm<double, 16, 16>};
         return f[k];
     }
     static Shape cheb_shape(int k) { const Shape s[nc] = {{64, 32, 512}, {64, 32, 256}}; return s[k]; }

@@ -469,6 +469,9 @@ asm_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
     constexpr int CW = TX + 1, CHh = TY + 1, CN = CW * CHh;
     __shared__ T ss[SN], hs[SN];
     __shared__ T Xc[CN], Yc[CN], Q1c[CN], Q2c[CN], U1c[CN], V1c[CN], P1c[CN], P2c[CN];
+    // previous pressure of the tile's nodes and a 1-node ring (residual form)
+    constexpr int PW = TX + 2, PN = PW * (TY + 2);
+    __shared__ T P0s[PN];
     const T d2 = P.delta * P.delta, d4 = d2 * d2;
     const int nxn = P.nx + 1;
     const int I0 = bx * TX, J0 = by * TY;
@@ -502,6 +505,13 @@ asm_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
             P2c[t] = ry ? -q2s[m] : q2s[m];
         }
     }
+    if (resid_form)
+        for (int t = tid; t < PN; t += nt) {
+            int I = I0 - 1 + t % PW, J = J0 - 1 + t / PW;
+            I = I > P.nx + 1 ? P.nx + 1 : I;   // beyond the mirror: feeds no node of the tile
+            J = J > P.ny + 1 ? P.ny + 1 : J;
+            P0s[t] = p0[(size_t)map_node(J, P.ny) * nxn + map_node(I, P.nx)];
+        }
     __syncthreads();
     for (int t = tid; t < CN; t += nt) {
         const int li = t % CW, lj = t / CW;
@@ -567,13 +577,12 @@ asm_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
             s1 = fma(bs, bs, s1);
             s2 = tmax(s2, (fabs(vE) + fabs(vW) + fabs(vN) + fabs(vS)) * id);
             if (resid_form) {
-                const int Iw = map_node(I - 1, P.nx), Ie = map_node(I + 1, P.nx);
-                const int Js = map_node(J - 1, P.ny), Jn = map_node(J + 1, P.ny);
-                T mp = dC * p0[nidx];
-                mp = fma(vW, p0[(size_t)J * nxn + Iw], mp);
-                mp = fma(vE, p0[(size_t)J * nxn + Ie], mp);
-                mp = fma(vS, p0[(size_t)Js * nxn + I], mp);
-                mp = fma(vN, p0[(size_t)Jn * nxn + I], mp);
+                const int pc = (lj + 1) * PW + li + 1;
+                T mp = dC * P0s[pc];
+                mp = fma(vW, P0s[pc - 1], mp);
+                mp = fma(vE, P0s[pc + 1], mp);
+                mp = fma(vS, P0s[pc - PW], mp);
+                mp = fma(vN, P0s[pc + PW], mp);
                 rhs[nidx] = bval - mp;
             } else {
                 rhs[nidx] = bval;

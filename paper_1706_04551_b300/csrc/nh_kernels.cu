@@ -620,7 +620,7 @@ void launch_asm2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* w
                   const T* w_base, T a, T b, T de, int with_coef, int resid_form, double tol2,
                   int max_iter, int kpass, double* partials, SolveCtl* ctl)
 {
-    constexpr int TX = 32, TY = 16;
+    constexpr int TX = 32, TY = sizeof(T) == 4 ? 16 : 8;   // FP64: static shared memory < 48 KB
     dim3 grid((P.nx + 1 + TX - 1) / TX, (P.ny + 1 + TY - 1) / TY);
     k_asm2d_t<T, TX, TY><<<grid, kThreads, 0, L.s>>>(P, B.etas, B.H, B.q1k, B.q2k, B.q1s, B.q2s,
                                                     w_in, w_base, a, b, de, with_coef, B.ws,
@@ -640,7 +640,8 @@ int cheb_sweeps_per_pass() { return ChebCfg<T>::K; }
 template <typename T>
 size_t asm_tiles(const Prm<T>& P)
 {
-    return (size_t)((P.nx + 1 + 31) / 32) * ((P.ny + 1 + 15) / 16);
+    constexpr int TY = sizeof(T) == 4 ? 16 : 8;
+    return (size_t)((P.nx + 1 + 31) / 32) * ((P.ny + 1 + TY - 1) / TY);
 }
 
 template <typename T>
