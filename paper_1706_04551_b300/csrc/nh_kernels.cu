@@ -629,13 +629,9 @@ void launch_asm2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* w
                                                     kpass);
 }
 
-template <typename T> struct ChebCfg;
-// region 128 x 32 nodes (FP32) / 64 x 32 (FP64), 512 threads, 8 nodes per thread, 4 sweeps
-template <> struct ChebCfg<float> { static constexpr int NA = 4, NB = 2, BY = 16, K = 4; };
-template <> struct ChebCfg<double> { static constexpr int NA = 2, NB = 2, BY = 16, K = 4; };
-
+// Sweeps per Chebyshev pass: 8 in FP32, 4 in FP64 (the forms below).
 template <typename T>
-int cheb_sweeps_per_pass() { return ChebCfg<T>::K; }
+int cheb_sweeps_per_pass() { return sizeof(T) == 4 ? 8 : 4; }
 
 template <typename T>
 size_t asm_tiles(const Prm<T>& P)
@@ -654,11 +650,11 @@ size_t cheb_tiles(const Prm<T>& P)
 
 // One form of the pass: region (32 NA) x (BY NB) nodes, 32 x BY threads, weights in
 // registers (REGW) or shared memory, at least MINB blocks per SM.
-template <typename T, int NA, int NB, int BY, bool REGW, int MINB, bool PAD = false>
+template <typename T, int NA, int NB, int BY, bool REGW, int MINB, bool PAD = false,
+          int K = 4>
 int launch_cheb_cfg(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, const T* xi,
                     const T* xpi, T* xo, T* xpo, double* partials)
 {
-    constexpr int K = 4;
     constexpr int TX = 32 * NA - 2 * K, TY = BY * NB - 2 * K;
     constexpr size_t smem = PAD ? 2 * (size_t)(32 * NA + 2) * (BY * NB + 2) * sizeof(T)
                                 : (REGW ? 2 : 7) * (size_t)(32 * NA) * (BY * NB) * sizeof(T);
@@ -677,13 +673,14 @@ int launch_cheb_cfg(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, const T* 
 }
 
 
-// The pass forms the handle chooses from (by timing its first passes; all give the same
-// iterates).  FP32 0: 128x32 region, shared-memory weights, 2 blocks / SM; 1: the same
-// with register weights, 1 block; 2, 3: 64x32 with register weights, 2 / 3 blocks;
-// 4: 64x64, shared-memory weights; 5: 64x32, shared-memory weights, 3 blocks; 6: 64x48,
-// register weights, 2 blocks; 7, 8: forms 3 and 6 with padded buffers and no bounds tests.
-// FP64 0: 64x32, shared memory; 1: 64x32, registers; 2: 64x32, registers, padded.
-template <typename T> int cheb_pass_forms() { return sizeof(T) == 4 ? 9 : 3; }
+// The pass forms the handle chooses from by timing its first passes; all forms of a
+// precision sweep the same number of times per pass (K) and give the same iterates.
+// FP32 (K = 8, weights in registers, padded buffers): 0: 64x64 region, 1024 threads;
+// 1: 128x64, 1024 threads; 2: 64x64, 512 threads, 2 blocks / SM; 3: 64x64, 512 threads,
+// 1 block; 4: 128x64, 512 threads, 1 block.
+// FP64 (K = 4): 0: 64x32, shared-memory weights; 1: 64x32, registers; 2: 64x32, registers,
+// padded.
+template <typename T> int cheb_pass_forms() { return sizeof(T) == 4 ? 5 : 3; }
 
 template <typename T>
 int launch_cheb_pass(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, const T* xi,
@@ -691,15 +688,11 @@ int launch_cheb_pass(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, const T*
 {
     if constexpr (sizeof(T) == 4) {
         switch (variant) {
-        case 1: return launch_cheb_cfg<T, 4, 2, 16, true, 1>(P, s, B, xi, xpi, xo, xpo, partials);
-        case 2: return launch_cheb_cfg<T, 2, 2, 16, true, 2>(P, s, B, xi, xpi, xo, xpo, partials);
-        case 3: return launch_cheb_cfg<T, 2, 2, 16, true, 3>(P, s, B, xi, xpi, xo, xpo, partials);
-        case 4: return launch_cheb_cfg<T, 2, 4, 16, false, 2>(P, s, B, xi, xpi, xo, xpo, partials);
-        case 5: return launch_cheb_cfg<T, 2, 2, 16, false, 3>(P, s, B, xi, xpi, xo, xpo, partials);
-        case 6: return launch_cheb_cfg<T, 2, 3, 16, true, 2>(P, s, B, xi, xpi, xo, xpo, partials);
-        case 7: return launch_cheb_cfg<T, 2, 2, 16, true, 3, true>(P, s, B, xi, xpi, xo, xpo, partials);
-        case 8: return launch_cheb_cfg<T, 2, 3, 16, true, 2, true>(P, s, B, xi, xpi, xo, xpo, partials);
-        default: return launch_cheb_cfg<T, 4, 2, 16, false, 2>(P, s, B, xi, xpi, xo, xpo, partials);
+        case 1: return launch_cheb_cfg<T, 4, 2, 32, true, 1, true, 8>(P, s, B, xi, xpi, xo, xpo, partials);
+        case 2: return launch_cheb_cfg<T, 2, 4, 16, true, 2, true, 8>(P, s, B, xi, xpi, xo, xpo, partials);
+        case 3: return launch_cheb_cfg<T, 2, 4, 16, true, 1, true, 8>(P, s, B, xi, xpi, xo, xpo, partials);
+        case 4: return launch_cheb_cfg<T, 4, 4, 16, true, 1, true, 8>(P, s, B, xi, xpi, xo, xpo, partials);
+        default: return launch_cheb_cfg<T, 2, 2, 32, true, 1, true, 8>(P, s, B, xi, xpi, xo, xpo, partials);
         }
     } else {
         if (variant == 1) return launch_cheb_cfg<T, 2, 2, 16, true, 1>(P, s, B, xi, xpi, xo, xpo, partials);
