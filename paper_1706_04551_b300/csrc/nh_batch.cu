@@ -199,8 +199,8 @@ kb_asm(Arena<T> A, const int2* __restrict__ wl, int nw, const T* eta, const T* H
     }
 }
 
-template <typename T, int NA, int NB, int BY, int K, bool REGW>
-__global__ void __launch_bounds__(32 * BY, REGW ? 1 : 2)
+template <typename T, int NA, int NB, int BY, int K, bool REGW, int MINB, bool PAD>
+__global__ void __launch_bounds__(32 * BY, MINB)
 kb_cheb(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const T* cW,
         const T* cE, const T* cS, const T* cN, const T* rhs, const T* xi, const T* xpi, T* xo,
         T* xpo, int stage)
@@ -218,9 +218,14 @@ kb_cheb(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const T* c
         R.nx = D.P.nx; R.ny = D.P.ny;
         const int tx = cdiv(R.nx + 1, TX), nt = tx * cdiv(R.ny + 1, TY);
         T rsum, dmax;
-        cheb_tile<T, NA, NB, BY, K, REGW>(R, rhs + n, xi + n, xpi + n, xo + n, xpo + n, ctl,
-                                          it.y % tx, it.y / tx,
-                                    reinterpret_cast<T*>(kb_cheb_smem), rsum, dmax);
+        if constexpr (PAD)
+            cheb_tile_pad<T, NA, NB, BY, K>(R, rhs + n, xi + n, xpi + n, xo + n, xpo + n, ctl,
+                                            it.y % tx, it.y / tx,
+                                            reinterpret_cast<T*>(kb_cheb_smem), rsum, dmax);
+        else
+            cheb_tile<T, NA, NB, BY, K, REGW>(R, rhs + n, xi + n, xpi + n, xo + n, xpo + n, ctl,
+                                              it.y % tx, it.y / tx,
+                                              reinterpret_cast<T*>(kb_cheb_smem), rsum, dmax);
         double acc[2];
         if (dom_reduce_sum_max_f((float)rsum, (float)dmax, A.partials + D.poff, &ctl->counter,
                                  acc, it.y, nt) &&
@@ -559,17 +564,27 @@ void run_asm(int grid, cudaStream_t s, const Arena<T>& A, const int2* wl, int nw
                                            ws, cC, cW, cE, cS, cN, rhs, p0, G);
 }
 
-template <typename T, int NA, int NB, int BY, bool REGW = false>
-constexpr size_t cheb_smem() { return (REGW ? 2 : 7) * (size_t)(32 * NA) * (BY * NB) * sizeof(T); }
+// sweeps per pass of the batched Chebyshev passes (all candidates of a precision)
+template <typename T> struct ChebK { static constexpr int value = sizeof(T) == 4 ? 8 : 4; };
 
-template <typename T, int NA, int NB, int BY, bool REGW = false>
+template <typename T, int NA, int NB, int BY, bool REGW, bool PAD>
+constexpr size_t cheb_smem()
+{
+    return PAD ? 2 * (size_t)(32 * NA + 2) * (BY * NB + 2) * sizeof(T)
+               : (REGW ? 2 : 7) * (size_t)(32 * NA) * (BY * NB) * sizeof(T);
+}
+
+template <typename T, int NA, int NB, int BY, bool REGW, int MINB, bool PAD>
 void run_cheb(int grid, cudaStream_t s, const Arena<T>& A, const int2* wl, int nw, const T* cC,
               const T* cW, const T* cE, const T* cS, const T* cN, const T* rhs, const T* xi,
               const T* xpi, T* xo, T* xpo, int stage)
 {
-    kb_cheb<T, NA, NB, BY, 4, REGW><<<grid, dim3(32, BY), cheb_smem<T, NA, NB, BY, REGW>(), s>>>(
-        A, wl, nw, cC, cW, cE, cS, cN, rhs, xi, xpi, xo, xpo, stage);
+    kb_cheb<T, NA, NB, BY, ChebK<T>::value, REGW, MINB, PAD>
+        <<<grid, dim3(32, BY), cheb_smem<T, NA, NB, BY, REGW, PAD>(), s>>>(
+            A, wl, nw, cC, cW, cE, cS, cN, rhs, xi, xpi, xo, xpo, stage);
 }
+
+#define KB_CHEB(T, NA, NB, BY, REGW, MINB, PAD) kb_cheb<T, NA, NB, BY, ChebK<T>::value, REGW, MINB, PAD>
 
 template <typename T>
 struct Cand {
@@ -606,26 +621,31 @@ struct Cands<float> {
         return f[k];
     }
     // Chebyshev: region (tile + 4-node halo on every side) and threads
-    // (the fourth: the first shape with the weights in registers)
-    static Shape cheb_shape(int k) { const Shape s[nc] = {{128, 32, 512}, {64, 64, 512}, {128, 32, 256}, {128, 32, 512}}; return s[k]; }
+    // 8 sweeps per pass, weights in registers, padded buffers: regions 64x64 (1024 threads),
+    // 64x64 (512 threads, 1 block / SM), 128x64 (1024 threads), 128x64 (512 threads)
+    static Shape cheb_shape(int k) { const Shape s[nc] = {{64, 64, 1024}, {64, 64, 512}, {128, 64, 1024}, {128, 64, 512}}; return s[k]; }
     static ChebFn<float> cheb(int k)
     {
-        const ChebFn<float> f[nc] = {run_cheb<float, 4, 2, 16>, run_cheb<float, 2, 4, 16>,
-                                     run_cheb<float, 4, 4, 8>, run_cheb<float, 4, 2, 16, true>};
+        const ChebFn<float> f[nc] = {run_cheb<float, 2, 2, 32, true, 1, true>,
+                                     run_cheb<float, 2, 4, 16, true, 1, true>,
+                                     run_cheb<float, 4, 2, 32, true, 1, true>,
+                                     run_cheb<float, 4, 4, 16, true, 1, true>};
         return f[k];
     }
     static const void* cheb_kernel(int k)
     {
-        const void* f[nc] = {(const void*)kb_cheb<float, 4, 2, 16, 4, false>,
-                             (const void*)kb_cheb<float, 2, 4, 16, 4, false>,
-                             (const void*)kb_cheb<float, 4, 4, 8, 4, false>,
-                             (const void*)kb_cheb<float, 4, 2, 16, 4, true>};
+        const void* f[nc] = {(const void*)KB_CHEB(float, 2, 2, 32, true, 1, true),
+                             (const void*)KB_CHEB(float, 2, 4, 16, true, 1, true),
+                             (const void*)KB_CHEB(float, 4, 2, 32, true, 1, true),
+                             (const void*)KB_CHEB(float, 4, 4, 16, true, 1, true)};
         return f[k];
     }
     static size_t cheb_smem_of(int k)
     {
-        const size_t s[nc] = {cheb_smem<float, 4, 2, 16>(), cheb_smem<float, 2, 4, 16>(),
-                              cheb_smem<float, 4, 4, 8>(), cheb_smem<float, 4, 2, 16, true>()};
+        const size_t s[nc] = {cheb_smem<float, 2, 2, 32, true, true>(),
+                              cheb_smem<float, 2, 4, 16, true, true>(),
+                              cheb_smem<float, 4, 2, 32, true, true>(),
+                              cheb_smem<float, 4, 4, 16, true, true>()};
         return s[k];
     }
 };
@@ -659,23 +679,24 @@ struct Cands<double> {
     static Shape cheb_shape(int k) { const Shape s[nc] = {{64, 32, 512}, {64, 32, 256}}; return s[k]; }
     static ChebFn<double> cheb(int k)
     {
-        const ChebFn<double> f[nc] = {run_cheb<double, 2, 2, 16>, run_cheb<double, 2, 4, 8>};
+        const ChebFn<double> f[nc] = {run_cheb<double, 2, 2, 16, false, 2, false>,
+                                      run_cheb<double, 2, 4, 8, false, 2, false>};
         return f[k];
     }
     static const void* cheb_kernel(int k)
     {
-        const void* f[nc] = {(const void*)kb_cheb<double, 2, 2, 16, 4, false>,
-                             (const void*)kb_cheb<double, 2, 4, 8, 4, false>};
+        const void* f[nc] = {(const void*)KB_CHEB(double, 2, 2, 16, false, 2, false),
+                             (const void*)KB_CHEB(double, 2, 4, 8, false, 2, false)};
         return f[k];
     }
     static size_t cheb_smem_of(int k)
     {
-        const size_t s[nc] = {cheb_smem<double, 2, 2, 16>(), cheb_smem<double, 2, 4, 8>()};
+        const size_t s[nc] = {cheb_smem<double, 2, 2, 16, false, false>(),
+                              cheb_smem<double, 2, 4, 8, false, false>()};
         return s[k];
     }
 };
 
-constexpr int kChebK = 4;   // sweeps per Chebyshev pass (all candidates)
 
 }  // namespace
 }  // namespace nh
@@ -886,8 +907,8 @@ struct BatchImpl : BatchBase {
             }
             for (int k = 0; k < C::nc; ++k) {
                 const Shape s = C::cheb_shape(k);
-                np = std::max<long long>(np, 2LL * cdiv(g.nx + 1, s.tx - 2 * kChebK) *
-                                                  cdiv(g.ny + 1, s.ty - 2 * kChebK));
+                np = std::max<long long>(np, 2LL * cdiv(g.nx + 1, s.tx - 2 * ChebK<T>::value) *
+                                                  cdiv(g.ny + 1, s.ty - 2 * ChebK<T>::value));
             }
             D.poff = poff;
             poff += (np + 31) / 32 * 32;
@@ -979,7 +1000,7 @@ struct BatchImpl : BatchBase {
         for (int k = 0; k < C::nc; ++k) {
             const Shape sh = C::cheb_shape(k);
             rc = make_list([&](int d) {
-                return cdiv(doms[d].P.nx + 1, sh.tx - 2 * kChebK) * cdiv(doms[d].P.ny + 1, sh.ty - 2 * kChebK);
+                return cdiv(doms[d].P.nx + 1, sh.tx - 2 * ChebK<T>::value) * cdiv(doms[d].P.ny + 1, sh.ty - 2 * ChebK<T>::value);
             }, &wl_cheb[k], &nw_cheb[k]);
             if (rc != NH_OK) return rc;
             if ((e = cudaFuncSetAttribute(C::cheb_kernel(k), cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1045,7 +1066,7 @@ struct BatchImpl : BatchBase {
         AsmArgs G;
         G.tol2 = q.tol * q.tol;
         G.max_iter = q.max_iter;
-        G.kpass = kChebK;
+        G.kpass = ChebK<T>::value;
         G.with_coef = q.nonhydrostatic ? 1 : 0;
         G.stage = s;
         const Shape sh = C::asm_shape(cand);
@@ -1076,10 +1097,10 @@ struct BatchImpl : BatchBase {
     void settle(cudaStream_t st)
     {
         kb_settle<T><<<grid_of((const void*)kb_settle<T>, kThreads, 0, nw_node, true), kThreads, 0, st>>>(
-            arena(), wl_node, nw_node, B.v[0], B.dp, kChebK);
+            arena(), wl_node, nw_node, B.v[0], B.dp, ChebK<T>::value);
     }
 
-    unsigned pass_cap() const { return (unsigned)((hb->prm.max_iter / kChebK + 16) / 2); }   // pairs
+    unsigned pass_cap() const { return (unsigned)((hb->prm.max_iter / ChebK<T>::value + 16) / 2); }   // pairs
     unsigned bicg_cap() const { return (unsigned)(hb->prm.max_iter / 2 + 2); }
 
     BiVec<T> bivec() const

@@ -72,4 +72,4 @@ def test_batch_candidates_listed():
         c = nh.batch_candidates(prec)
         assert all(len(c[k]) >= 2 for k in ("hyp", "assembly", "cheb"))
         for tx, ty, th in c["cheb"]:
-            assert tx > 8 and ty > 8 and th in (256, 512)
+            assert tx > 16 and ty > 16 and th in (256, 512, 1024)
