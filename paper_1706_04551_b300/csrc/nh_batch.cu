@@ -304,6 +304,19 @@ __device__ __forceinline__ Rows<T> rows_at(const BiVec<T>& V, const Prm<T>& P, l
     return R;
 }
 
+// Compact the (domain, chunk) list of the domains whose solve continues with BiCGStab
+// (one thread per domain; the order of the domains in the list is immaterial: every
+// reduction slot is the chunk's own index).
+template <typename T>
+__global__ void kb_build_fb(Arena<T> A, int n, int2* __restrict__ wl, int* __restrict__ count)
+{
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= n || !A.sctl[d].fb) return;
+    const int k = A.dom[d].nnc;
+    const int base = atomicAdd(count, k);
+    for (int i = 0; i < k; ++i) wl[base + i] = make_int2(d, i);
+}
+
 // record the end of a domain's fallback solve
 __device__ __forceinline__ void bicg_end(SolveCtl* ctl, DomState& s, unsigned* loop, int stage,
                                          int status)
@@ -327,8 +340,9 @@ __device__ __forceinline__ void bicg_end(SolveCtl* ctl, DomState& s, unsigned* l
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-kb_bicg_init(Arena<T> A, const int2* __restrict__ wl, int nw, BiVec<T> V, int stage)
+kb_bicg_init(Arena<T> A, const int2* __restrict__ wl, const int* __restrict__ nwp, BiVec<T> V, int stage)
 {
+    const int nw = *nwp;   // compacted list of the domains in the fallback
     for (int w = blockIdx.x; w < nw; w += gridDim.x) {
         const int2 it = wl[w];
         SolveCtl* ctl = &A.sctl[it.x];
@@ -371,8 +385,9 @@ kb_bicg_init(Arena<T> A, const int2* __restrict__ wl, int nw, BiVec<T> V, int st
 // phase A: p^ = r + beta (p^ - omega v); v = M D^-1 p^; alpha = rho1 / (rhat . v)
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-kb_bicg_A(Arena<T> A, const int2* __restrict__ wl, int nw, BiVec<T> V, int parity, int stage)
+kb_bicg_A(Arena<T> A, const int2* __restrict__ wl, const int* __restrict__ nwp, BiVec<T> V, int parity, int stage)
 {
+    const int nw = *nwp;   // compacted list of the domains in the fallback
     for (int w = blockIdx.x; w < nw; w += gridDim.x) {
         const int2 it = wl[w];
         SolveCtl* ctl = &A.sctl[it.x];
@@ -413,8 +428,9 @@ kb_bicg_A(Arena<T> A, const int2* __restrict__ wl, int nw, BiVec<T> V, int parit
 // phase B: s = r - alpha v; t = M D^-1 s; omega = (t . s) / (t . t)
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-kb_bicg_B(Arena<T> A, const int2* __restrict__ wl, int nw, BiVec<T> V, int parity)
+kb_bicg_B(Arena<T> A, const int2* __restrict__ wl, const int* __restrict__ nwp, BiVec<T> V, int parity)
 {
+    const int nw = *nwp;   // compacted list of the domains in the fallback
     for (int w = blockIdx.x; w < nw; w += gridDim.x) {
         const int2 it = wl[w];
         SolveCtl* ctl = &A.sctl[it.x];
@@ -450,8 +466,9 @@ kb_bicg_B(Arena<T> A, const int2* __restrict__ wl, int nw, BiVec<T> V, int parit
 // phase C: x += alpha D^-1 p^ + omega D^-1 s; r = s - omega t; rho1 = rhat . r; test
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-kb_bicg_C(Arena<T> A, const int2* __restrict__ wl, int nw, BiVec<T> V, int parity, int stage)
+kb_bicg_C(Arena<T> A, const int2* __restrict__ wl, const int* __restrict__ nwp, BiVec<T> V, int parity, int stage)
 {
+    const int nw = *nwp;   // compacted list of the domains in the fallback
     for (int w = blockIdx.x; w < nw; w += gridDim.x) {
         const int2 it = wl[w];
         SolveCtl* ctl = &A.sctl[it.x];
@@ -804,7 +821,7 @@ struct BatchImpl : BatchBase {
     DomState* h_ds = nullptr;          // pinned
     std::vector<void*> allocs;
     // work lists: element items (cell chunks, node chunks) and one per tile candidate
-    int2 *wl_cell = nullptr, *wl_node = nullptr;
+    int2 *wl_cell = nullptr, *wl_node = nullptr, *wl_fb = nullptr;
     int nw_cell = 0, nw_node = 0;
     std::vector<int2*> wl_hyp, wl_asm, wl_cheb;
     std::vector<int> nw_hyp, nw_asm, nw_cheb;
@@ -940,7 +957,7 @@ struct BatchImpl : BatchBase {
         A_(d_ds, n);
         A_(d_sctl, n);
         A_(d_stctl, n);
-        A_(d_loop, 4);
+        A_(d_loop, 8);   // [0..3] solver loops, [4] length of the fallback list
 #undef A_
         cudaError_t e;
         if ((e = cudaMallocHost(&h_loop, 4 * sizeof(unsigned))) != cudaSuccess) return bcuda(hb, e, "cudaMallocHost");
@@ -949,7 +966,7 @@ struct BatchImpl : BatchBase {
         cudaMemcpyAsync(d_dom, doms.data(), n * sizeof(Dom<T>), cudaMemcpyHostToDevice, s);
         cudaMemsetAsync(d_ds, 0, n * sizeof(DomState), s);
         cudaMemsetAsync(d_stctl, 0, n * sizeof(StepCtl), s);
-        cudaMemsetAsync(d_loop, 0, 4 * sizeof(unsigned), s);
+        cudaMemsetAsync(d_loop, 0, 8 * sizeof(unsigned), s);
         {
             std::vector<SolveCtl> sc(n);
             std::memset(sc.data(), 0, n * sizeof(SolveCtl));
@@ -982,6 +999,7 @@ struct BatchImpl : BatchBase {
         }
         if ((rc = make_list([&](int d) { return doms[d].ncc; }, &wl_cell, &nw_cell)) != NH_OK) return rc;
         if ((rc = make_list([&](int d) { return doms[d].nnc; }, &wl_node, &nw_node)) != NH_OK) return rc;
+        if ((rc = alloc(&wl_fb, (size_t)nw_node + 1)) != NH_OK) return rc;
         wl_hyp.resize(C::nh); nw_hyp.resize(C::nh);
         for (int k = 0; k < C::nh; ++k) {
             const Shape sh = C::hyp_shape(k);
@@ -1112,11 +1130,16 @@ struct BatchImpl : BatchBase {
         return V;
     }
 
+    const int* nfb() const { return reinterpret_cast<const int*>(d_loop + 4); }
+
+    // compacted list of the fallback domains' chunks, then the BiCGStab initial residual
     void bicg_init(int s, cudaStream_t st)
     {
+        kb_build_fb<T><<<(n + 127) / 128, 128, 0, st>>>(arena(), n, wl_fb,
+                                                       reinterpret_cast<int*>(d_loop + 4));
         K_(NH_K_SOLVE_INIT, st, [&] {
-            kb_bicg_init<T><<<grid_of((const void*)kb_bicg_init<T>, kThreads, 0, nw_node, pers(3)), kThreads, 0, st>>>(
-                arena(), wl_node, nw_node, bivec(), s);
+            kb_bicg_init<T><<<grid_of((const void*)kb_bicg_init<T>, kThreads, 0, nw_node, true), kThreads, 0, st>>>(
+                arena(), wl_fb, nfb(), bivec(), s);
         });
     }
 
@@ -1126,16 +1149,16 @@ struct BatchImpl : BatchBase {
         const BiVec<T> V = bivec();
         for (int parity = 0; parity < 2; ++parity) {
             K_(NH_K_BICG_A, st, [&] {
-                kb_bicg_A<T><<<grid_of((const void*)kb_bicg_A<T>, kThreads, 0, nw_node, pers(3)), kThreads, 0, st>>>(
-                    arena(), wl_node, nw_node, V, parity, s);
+                kb_bicg_A<T><<<grid_of((const void*)kb_bicg_A<T>, kThreads, 0, nw_node, true), kThreads, 0, st>>>(
+                    arena(), wl_fb, nfb(), V, parity, s);
             });
             K_(NH_K_BICG_B, st, [&] {
-                kb_bicg_B<T><<<grid_of((const void*)kb_bicg_B<T>, kThreads, 0, nw_node, pers(3)), kThreads, 0, st>>>(
-                    arena(), wl_node, nw_node, V, parity);
+                kb_bicg_B<T><<<grid_of((const void*)kb_bicg_B<T>, kThreads, 0, nw_node, true), kThreads, 0, st>>>(
+                    arena(), wl_fb, nfb(), V, parity);
             });
             K_(NH_K_BICG_C, st, [&] {
-                kb_bicg_C<T><<<grid_of((const void*)kb_bicg_C<T>, kThreads, 0, nw_node, pers(3)), kThreads, 0, st>>>(
-                    arena(), wl_node, nw_node, V, parity, s);
+                kb_bicg_C<T><<<grid_of((const void*)kb_bicg_C<T>, kThreads, 0, nw_node, true), kThreads, 0, st>>>(
+                    arena(), wl_fb, nfb(), V, parity, s);
             });
         }
     }
@@ -1152,7 +1175,7 @@ struct BatchImpl : BatchBase {
                     arena(), wl_cell, nw_cell, B.etas, B.q1s, B.q2s, B.H, b, B.q1k, B.q2k);
             });
         }
-        cudaMemsetAsync(d_loop, 0, 4 * sizeof(unsigned), hb->s);
+        cudaMemsetAsync(d_loop, 0, 8 * sizeof(unsigned), hb->s);
         if (q.nonhydrostatic) cudaMemsetAsync(B.dp, 0, nnode * sizeof(T), hb->s);
         K_(NH_K_ASSEMBLY, hb->s, [&] { assembly(s, tun.assembly, pers(1)); });
     }
@@ -1364,7 +1387,7 @@ struct BatchImpl : BatchBase {
             }
             tun.persistent = (tun.persistent & ~8) | ((tb[1] < tb[0] ? 1 : 0) << 3);
         }
-        cudaMemsetAsync(d_loop, 0, 4 * sizeof(unsigned), s);
+        cudaMemsetAsync(d_loop, 0, 8 * sizeof(unsigned), s);
         cudaMemcpyAsync(d_ds, h_ds, n * sizeof(DomState), cudaMemcpyHostToDevice, s);
         cudaError_t e = cudaStreamSynchronize(s);
         if (e == cudaSuccess) e = cudaGetLastError();
