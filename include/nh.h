@@ -85,6 +85,10 @@ typedef struct {
                            criterion of Eq. (32), instead of the residual test            */
     int adjoint_frozen_limiter; /* nh_adjoint_step: 0 = exact derivative of the step; 1 =
                            reconstruction linearised with the limiter ratio held fixed   */
+    int cheb_form;      /* single-domain handles, Chebyshev solver: -1 (default) = the
+                           kernel form of the pass is chosen by timing the first passes;
+                           0 .. nh_cheb_forms(precision) - 1 = that form.  All forms give
+                           the same iterates.                                            */
 } nh_params;
 
 typedef struct {
@@ -106,8 +110,14 @@ typedef struct nh_handle nh_handle;
 
 /* Fill p with the paper's defaults: g = 9.81, CFL 0.9, delta = 1e-5, hdry = delta,
  * n = 0, B1 = 0.15, B2 = 0.5 (Sec. 7.4), breaking off, non-hydrostatic on, Chebyshev
- * solver, tol 1e-12, max_iter 2000, FP64, fixed_dt 0, eps_dp 0. */
+ * solver, tol 1e-12, max_iter 2000, FP64, fixed_dt 0, eps_dp 0, exact adjoint, pass
+ * form chosen by timing (cheb_form = -1). */
 int nh_default_params(nh_params *p);
+
+/* Number of kernel forms of the Chebyshev-scheduled Jacobi pass (Sec. 5's scheduled
+ * relaxation; nh_params.cheb_form) for precision NH_FP32 or NH_FP64; NH_EINVAL otherwise.
+ * No GPU work. */
+int nh_cheb_forms(int precision);
 
 /* Create a simulation on the current CUDA device.  H: host array [ny][nx] (double) of
  * still-water depths.  stream: a cudaStream_t (or 0).  The state is lake at rest

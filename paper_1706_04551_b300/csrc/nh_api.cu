@@ -160,6 +160,7 @@ struct Impl : Base {
         P.dx = (T)g.dx; P.dy = (T)(dim == 2 ? g.dy : g.dx);
         P.g = (T)q.g; P.delta = (T)q.delta; P.hdry = (T)q.hdry; P.manning = (T)q.manning_n;
         P.B1 = (T)q.B1; P.breaking = q.breaking;
+        pass_variant = q.cheb_form;
         nc = (size_t)g.nx * g.ny;
         nn = dim == 2 ? (size_t)(g.nx + 1) * (g.ny + 1) : (size_t)(g.nx + 1) * g.ny;
         int dev = 0, nsm = 0;
@@ -830,6 +831,8 @@ int check_grid(const nh_grid* g, const nh_params* p, std::string& why)
         why = "adjoint_frozen_limiter must be 0 or 1";
         return 0;
     }
+    const int nforms = p->precision == NH_FP32 ? cheb_pass_forms<float>() : cheb_pass_forms<double>();
+    if (p->cheb_form < -1 || p->cheb_form >= nforms) { why = "cheb_form out of range"; return 0; }
     return 1;
 }
 
@@ -845,7 +848,15 @@ int nh_default_params(nh_params* p)
     p->solver = NH_SOLVER_CHEBYSHEV; p->tol = 1e-12; p->max_iter = 2000;
     p->precision = NH_FP64; p->fixed_dt = 0.0; p->eps_dp = 0.0;
     p->adjoint_frozen_limiter = 0;
+    p->cheb_form = -1;
     return NH_OK;
+}
+
+int nh_cheb_forms(int precision)
+{
+    if (precision == NH_FP32) return cheb_pass_forms<float>();
+    if (precision == NH_FP64) return cheb_pass_forms<double>();
+    return NH_EINVAL;
 }
 
 int nh_create(const nh_grid* grid, const double* H, const nh_params* params, void* stream,

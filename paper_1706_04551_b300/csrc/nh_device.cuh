@@ -654,6 +654,31 @@ __device__ __forceinline__ T row_apply(const Rows<T>& R, int I, int J, T xc, F x
          + R.cS[k] * xat((size_t)Js * nxn + I) + R.cN[k] * xat((size_t)Jn * nxn + I);
 }
 
+
+// One node of a Chebyshev-scheduled Jacobi sweep with every rounding fixed by explicit fused
+// multiply-adds, so that all kernel forms of the pass give the same bits: the scaled
+// residual r = D^-1 b - x - D^-1 (M - D) x from the node's four weights and neighbours,
+// and the update x_new = x + c1 (x - x_prev) + c2 r.
+template <typename T>
+__device__ __forceinline__ T cheb_resid(T rb, T xc, T wW, T xW, T wE, T xE, T wS, T xS, T wN,
+                                        T xN)
+{
+    T s = fma(wE, xE, wW * xW);
+    s = fma(wS, xS, s);
+    s = fma(wN, xN, s);
+    return (rb - xc) - s;
+}
+
+template <typename T>
+__device__ __forceinline__ T cheb_next(T xc, T xa, T c1, T c2, T r)
+{
+    return fma(c2, r, fma(c1, xc - xa, xc));
+}
+
+// Product that the compiler may not fuse into a later addition (the Jacobi scaling of b
+// and of the weights), so that every form rounds it alike.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 // Jacobi with Chebyshev-scheduled relaxation (the "scheduled relaxation" of Sec. 5 with
 // the Chebyshev weights of the Gershgorin interval [1 - g, 1 + g] of D^-1 M), K sweeps per
 // launch with temporal blocking: each block loads a tile plus a K-node halo into shared
@@ -712,9 +737,9 @@ cheb_tile(const Rows<T>& R, const T* __restrict__ b, const T* __restrict__ xi,
             const T ic = qdiv(T(1), R.cC[g]);
             xs0[sidx] = xi[g];
             xa[q] = xpi[g];
-            const T bv = b[g] * ic;
-            const T cw = R.cW[g] * ic, ce = R.cE[g] * ic;
-            const T cs = R.cS[g] * ic, cn = R.cN[g] * ic;
+            const T bv = mul_rn(b[g], ic);
+            const T cw = mul_rn(R.cW[g], ic), ce = mul_rn(R.cE[g], ic);
+            const T cs = mul_rn(R.cS[g], ic), cn = mul_rn(R.cN[g], ic);
             if constexpr (REGW) {
                 rbd[q] = bv;
                 rwW[q] = fx ? ce : cw;
@@ -754,14 +779,13 @@ cheb_tile(const Rows<T>& R, const T* __restrict__ b, const T* __restrict__ xi,
                     const T xc = cur[sidx];
                     T r;
                     if constexpr (REGW)
-                        r = rbd[q] - xc -
-                            (rwW[q] * cur[sidx - 1] + rwE[q] * cur[sidx + 1] +
-                             rwS[q] * cur[sidx - RW] + rwN[q] * cur[sidx + RW]);
+                        r = cheb_resid(rbd[q], xc, rwW[q], cur[sidx - 1], rwE[q], cur[sidx + 1],
+                                       rwS[q], cur[sidx - RW], rwN[q], cur[sidx + RW]);
                     else
-                        r = bd[sidx] - xc -
-                            (wW[sidx] * cur[sidx - 1] + wE[sidx] * cur[sidx + 1] +
-                             wS[sidx] * cur[sidx - RW] + wN[sidx] * cur[sidx + RW]);
-                    const T xn = xc + c1 * (xc - xa[q]) + c2 * r;
+                        r = cheb_resid(bd[sidx], xc, wW[sidx], cur[sidx - 1], wE[sidx],
+                                       cur[sidx + 1], wS[sidx], cur[sidx - RW], wN[sidx],
+                                       cur[sidx + RW]);
+                    const T xn = cheb_next(xc, xa[q], c1, c2, r);
                     nxt[sidx] = xn;
                     xa[q] = xc;
                     if (sw == K - 1 && li >= K && li < RW - K && lj >= K && lj < RH - K &&
@@ -788,6 +812,35 @@ cheb_tile(const Rows<T>& R, const T* __restrict__ b, const T* __restrict__ xi,
         }
 }
 
+// The zero ring around a padded (PW = RW + 2) x (RH + 2) region, for both buffers of the
+// pair (the second starts PN = PW (RH + 2) elements after the first): slot t < 2 (PW + RH)
+// zeroes two elements -- rows 0 and RH + 1 for t % (PW + RH) < PW, else columns 0 and
+// RW + 1 of row t % (PW + RH) - PW + 1.
+struct RingPair { int a, b; };
+
+template <int RW, int RH>
+__host__ __device__ constexpr RingPair pad_ring_slots(int t)
+{
+    constexpr int PW = RW + 2, PN = PW * (RH + 2);
+    const int k = t % (PW + RH);
+    const int base = t < PW + RH ? 0 : PN;
+    if (k < PW) return RingPair{base + k, base + (RH + 1) * PW + k};
+    const int r = k - PW + 1;
+    return RingPair{base + r * PW, base + r * PW + RW + 1};
+}
+
+// every slot inside [0, 2 PN), evaluated at compile time for each region form
+template <int RW, int RH>
+__host__ __device__ constexpr bool pad_ring_in_bounds()
+{
+    constexpr int PW = RW + 2, PN = PW * (RH + 2);
+    for (int t = 0; t < 2 * (PW + RH); ++t) {
+        const RingPair z = pad_ring_slots<RW, RH>(t);
+        if (z.a < 0 || z.b < 0 || z.a >= 2 * PN || z.b >= 2 * PN) return false;
+    }
+    return true;
+}
+
 // Form of cheb_tile with the weights in registers and the two x buffers padded by one node
 // on every side (zeros): every sweep updates all of the thread's region nodes without
 // bounds tests (values near the region edge go stale, one node per sweep, and never reach
@@ -808,13 +861,11 @@ cheb_tile_pad(const Rows<T>& R, const T* __restrict__ b, const T* __restrict__ x
     const int I0 = bx * TX - K, J0 = by * TY - K;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * 32 + tx, nthr = 32 * BY;
-    // the pad ring of both buffers: rows 0 and RH + 1 (PW each), then columns 0 and RW + 1
-    // of rows 1 .. RH
+    static_assert(pad_ring_in_bounds<RW, RH>(), "pad ring outside the two shared buffers");
     for (int t = tid; t < 2 * (PW + RH); t += nthr) {
-        const int k = t % (PW + RH);
-        T* buf = t < PW + RH ? xs0 : xs1;
-        if (k < PW) { buf[k] = T(0); buf[(RH + 1) * PW + k] = T(0); }
-        else { const int r = k - PW + 1; buf[r * PW] = T(0); buf[r * PW + RW + 1] = T(0); }
+        const RingPair z = pad_ring_slots<RW, RH>(t);
+        xs0[z.a] = T(0);
+        xs0[z.b] = T(0);
     }
 #pragma unroll
     for (int bb = 0; bb < NB; ++bb)
@@ -832,9 +883,9 @@ cheb_tile_pad(const Rows<T>& R, const T* __restrict__ b, const T* __restrict__ x
             const T ic = qdiv(T(1), R.cC[g]);
             xs0[(lj + 1) * PW + li + 1] = xi[g];
             xa[q] = xpi[g];
-            rbd[q] = b[g] * ic;
-            const T cw = R.cW[g] * ic, ce = R.cE[g] * ic;
-            const T cs = R.cS[g] * ic, cn = R.cN[g] * ic;
+            rbd[q] = mul_rn(b[g], ic);
+            const T cw = mul_rn(R.cW[g], ic), ce = mul_rn(R.cE[g], ic);
+            const T cs = mul_rn(R.cS[g], ic), cn = mul_rn(R.cN[g], ic);
             rwW[q] = fx ? ce : cw;
             rwE[q] = fx ? cw : ce;
             rwS[q] = fy ? cn : cs;
@@ -862,10 +913,9 @@ cheb_tile_pad(const Rows<T>& R, const T* __restrict__ b, const T* __restrict__ x
                 const int p = (lj + 1) * PW + li + 1;
                 const int q = bb * NA + aa;
                 const T xc = cur[p];
-                const T r = rbd[q] - xc -
-                            (rwW[q] * cur[p - 1] + rwE[q] * cur[p + 1] + rwS[q] * cur[p - PW] +
-                             rwN[q] * cur[p + PW]);
-                const T xn = xc + c1 * (xc - xa[q]) + c2 * r;
+                const T r = cheb_resid(rbd[q], xc, rwW[q], cur[p - 1], rwE[q], cur[p + 1], rwS[q],
+                                       cur[p - PW], rwN[q], cur[p + PW]);
+                const T xn = cheb_next(xc, xa[q], c1, c2, r);
                 nxt[p] = xn;
                 xa[q] = xc;
                 if (sw == K - 1 && li >= K && li < RW - K && lj >= K && lj < RH - K &&
@@ -889,6 +939,308 @@ cheb_tile_pad(const Rows<T>& R, const T* __restrict__ b, const T* __restrict__ x
                 xpo[g] = xa[bb * NA + aa];
             }
         }
+}
+
+// ---- Chebyshev pass with the sweeps in registers (persistent blocks, prefetched inputs)
+// A region of RW = 32 C by RH = R NW nodes is swept by NW warps: warp w holds rows
+// R w .. R w + R - 1, lane l columns C l .. C l + C - 1 of each, with x, x_prev, D^-1 b and
+// the four off-diagonal weights of D^-1 M in registers.  Per sweep the west / east
+// neighbours come from the neighbouring lanes (shuffles), the south / north ones from the
+// thread's own rows, and the two rows next to another warp from a small exchange buffer
+// (one barrier per sweep).  The eight input planes of the next region (x, x_prev, b and the
+// five coefficients) are copied into shared memory with cp.async while the current region is
+// swept, so the global loads of one region overlap the sweeps of the previous one.  Nodes
+// on the region's rim use their own value for a missing neighbour: like every node within
+// K of the rim they go stale, and none of them reaches the tile interior within K sweeps.
+// Same node arithmetic, in the same order, as cheb_tile_pad: the iterates are identical.
+
+__device__ __forceinline__ unsigned smem_u32(const void* p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(unsigned dst, const void* src)
+{
+    static_assert(BYTES == 4 || BYTES == 8, "4- or 8-byte elements");
+    if constexpr (BYTES == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Planes of a staged region, each RW x RH (row-major, x fastest).
+enum { kPlX = 0, kPlXp, kPlB, kPlC, kPlW, kPlE, kPlS, kPlN, kPlanes };
+
+// Shared memory of the register form: the staged planes, then the row-exchange buffer
+// (2 parities x NW warps x 2 rows x RW).
+template <typename T, int C, int R, int NW>
+constexpr size_t cheb_reg_smem()
+{
+    return ((size_t)kPlanes * (32 * C) * (R * NW) + (size_t)2 * NW * 2 * (32 * C)) * sizeof(T);
+}
+
+// Issue the copies of part `part` of `nparts` of region (I0, J0)'s eight planes (nodes
+// outside the grid read their mirror image, as the wall and outflow rows of M prescribe) and
+// commit them as one group.  A thread's elements t = tid + e NTHR are split round-robin
+// over the parts, so that the copies can be spread over the sweeps of the previous region.
+template <typename T, int RW, int RH, int NTHR>
+__device__ __forceinline__ void cheb_stage_region(const Rows<T>& R, const T* __restrict__ b,
+                                                  const T* __restrict__ xi,
+                                                  const T* __restrict__ xpi, int I0, int J0,
+                                                  T* planes, int part, int nparts)
+{
+    constexpr int RN = RW * RH;
+    constexpr unsigned PB = RN * sizeof(T);
+    // a thread keeps one column when the block is a multiple of the region width
+    constexpr bool COL = NTHR % RW == 0;
+    const int tid = threadIdx.x;
+    const int nx = R.nx, ny = R.ny, NX = nx + 1;
+    const unsigned s0 = smem_u32(planes);
+    int li = tid % RW, mI = 0;
+    auto mirror_x = [&](int l) {
+        const int gI = I0 + l;
+        int m = gI < 0 ? -gI : (gI > nx ? 2 * nx - gI : gI);
+        return m < 0 ? 0 : (m > nx ? nx : m);
+    };
+    if (COL) mI = mirror_x(li);
+    for (int t = tid + part * NTHR; t < RN; t += nparts * NTHR) {
+        const int lj = t / RW;
+        if (!COL) {
+            li = t % RW;
+            mI = mirror_x(li);
+        }
+        const int gJ = J0 + lj;
+        int mJ = gJ < 0 ? -gJ : (gJ > ny ? 2 * ny - gJ : gJ);
+        mJ = mJ < 0 ? 0 : (mJ > ny ? ny : mJ);
+        const size_t g = (size_t)mJ * NX + mI;
+        const unsigned s = s0 + (unsigned)((lj * RW + li) * sizeof(T));
+        cp_async_elem<sizeof(T)>(s + kPlX * PB, xi + g);
+        cp_async_elem<sizeof(T)>(s + kPlXp * PB, xpi + g);
+        cp_async_elem<sizeof(T)>(s + kPlB * PB, b + g);
+        cp_async_elem<sizeof(T)>(s + kPlC * PB, R.cC + g);
+        cp_async_elem<sizeof(T)>(s + kPlW * PB, R.cW + g);
+        cp_async_elem<sizeof(T)>(s + kPlE * PB, R.cE + g);
+        cp_async_elem<sizeof(T)>(s + kPlS * PB, R.cS + g);
+        cp_async_elem<sizeof(T)>(s + kPlN * PB, R.cN + g);
+    }
+    cp_async_commit();
+}
+
+// One staged region (I0, J0): registers from the planes, then K sweeps, each preceded by
+// `stage_next(sw, K)` (the planes are free once every warp holds its registers), so that
+// the copies of the next region go out in K slices between the sweeps; writes the tile
+// interior's x and x_prev and adds the last sweep's squared scaled residuals and largest
+// change over the interior nodes to rsum / dmax.  c1s / c2s: the K sweep weights.
+template <typename T, int C, int R, int NW, int K, typename F>
+__device__ __forceinline__ void cheb_region_reg(const Rows<T>& Rw, const T* planes, T* exch,
+                                                const T* c1s, const T* c2s, int I0, int J0,
+                                                T* __restrict__ xo, T* __restrict__ xpo,
+                                                T& rsum, T& dmax, F stage_next)
+{
+    constexpr int RW = 32 * C, RH = R * NW, RN = RW * RH;
+    const int nx = Rw.nx, ny = Rw.ny, NX = nx + 1;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T x[R][C], xa[R][C], rb[R][C], wW[R][C], wE[R][C], wS[R][C], wN[R][C];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int lj = R * w + r, gJ = J0 + lj;
+        const bool fy = gJ < 0 || gJ > ny;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int li = C * lane + c, gI = I0 + li;
+            const bool fx = gI < 0 || gI > nx;
+            const int t = lj * RW + li;
+            const T ic = qdiv(T(1), planes[kPlC * RN + t]);
+            x[r][c] = planes[kPlX * RN + t];
+            xa[r][c] = planes[kPlXp * RN + t];
+            rb[r][c] = mul_rn(planes[kPlB * RN + t], ic);
+            const T cw = mul_rn(planes[kPlW * RN + t], ic);
+            const T ce = mul_rn(planes[kPlE * RN + t], ic);
+            const T cs = mul_rn(planes[kPlS * RN + t], ic);
+            const T cn = mul_rn(planes[kPlN * RN + t], ic);
+            wW[r][c] = fx ? ce : cw;
+            wE[r][c] = fx ? cw : ce;
+            wS[r][c] = fy ? cn : cs;
+            wN[r][c] = fy ? cs : cn;
+        }
+    }
+    __syncthreads();   // every warp has its registers: the planes may be refilled
+#pragma unroll
+    for (int sw = 0; sw < K; ++sw) {
+        stage_next(sw, K);
+        T* e = exch + (sw & 1) * (NW * 2 * RW);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            e[(2 * w) * RW + C * lane + c] = x[0][c];
+            e[(2 * w + 1) * RW + C * lane + c] = x[R - 1][c];
+        }
+        __syncthreads();
+        T lo[C], hi[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            lo[c] = w > 0 ? e[(2 * w - 1) * RW + C * lane + c] : x[0][c];
+            hi[c] = w < NW - 1 ? e[(2 * w + 2) * RW + C * lane + c] : x[R - 1][c];
+        }
+        const T c1 = c1s[sw], c2 = c2s[sw];
+        T xn[R][C];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            T left = __shfl_up_sync(0xffffffffu, x[r][C - 1], 1);
+            T right = __shfl_down_sync(0xffffffffu, x[r][0], 1);
+            if (lane == 0) left = x[r][0];
+            if (lane == 31) right = x[r][C - 1];
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const T xc = x[r][c];
+                const T xw = c == 0 ? left : x[r][c - 1];
+                const T xe = c == C - 1 ? right : x[r][c + 1];
+                const T xs = r == 0 ? lo[c] : x[r - 1][c];
+                const T xnn = r == R - 1 ? hi[c] : x[r + 1][c];
+                const T res = cheb_resid(rb[r][c], xc, wW[r][c], xw, wE[r][c], xe, wS[r][c], xs,
+                                         wN[r][c], xnn);
+                const T v = cheb_next(xc, xa[r][c], c1, c2, res);
+                xn[r][c] = v;
+                if (sw == K - 1) {
+                    const int li = C * lane + c, lj = R * w + r;
+                    if (li >= K && li < RW - K && lj >= K && lj < RH - K && I0 + li <= nx &&
+                        J0 + lj <= ny) {
+                        rsum = fma(res, res, rsum);
+                        dmax = tmax(dmax, T(fabs(v - xc)));
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                xa[r][c] = x[r][c];
+                x[r][c] = xn[r][c];
+            }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int lj = R * w + r, gJ = J0 + lj;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int li = C * lane + c, gI = I0 + li;
+            if (li >= K && li < RW - K && lj >= K && lj < RH - K && gI <= nx && gJ <= ny) {
+                const size_t g = (size_t)gJ * NX + gI;
+                xo[g] = x[r][c];
+                xpo[g] = xa[r][c];
+            }
+        }
+    }
+}
+
+
+// Packed FP32 form of cheb_region_reg for C = 2: a lane's two columns are one float2 and
+// every sweep operation acts on both with one Blackwell packed instruction (FFMA2 / FMUL2;
+// differences as fma(a, -1, b), which rounds like b - a).  Each packed lane rounds like the
+// scalar code, so the iterates are the same bits as every other form's.
+template <int R, int NW, int K, typename F>
+__device__ __forceinline__ void cheb_region_reg2(const Rows<float>& Rw, const float* planes,
+                                                 float* exch, const float* c1s,
+                                                 const float* c2s, int I0, int J0,
+                                                 float* __restrict__ xo, float* __restrict__ xpo,
+                                                 float& rsum, float& dmax, F stage_next)
+{
+    constexpr int RW = 64, RH = R * NW, RN = RW * RH;
+    const int nx = Rw.nx, ny = Rw.ny, NX = nx + 1;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const float2 m1 = make_float2(-1.f, -1.f);
+    float2 x[R], xa[R], rb[R], wW[R], wE[R], wS[R], wN[R];
+    const int gI0 = I0 + 2 * lane, gI1 = gI0 + 1;
+    const bool fx0 = gI0 < 0 || gI0 > nx, fx1 = gI1 < 0 || gI1 > nx;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int lj = R * w + r, gJ = J0 + lj;
+        const bool fy = gJ < 0 || gJ > ny;
+        const int t = lj * RW + 2 * lane;
+        auto ld = [&](int plane) { return *reinterpret_cast<const float2*>(planes + plane * RN + t); };
+        const float2 cc = ld(kPlC);
+        const float2 ic = make_float2(qdiv(1.f, cc.x), qdiv(1.f, cc.y));
+        x[r] = ld(kPlX);
+        xa[r] = ld(kPlXp);
+        rb[r] = __fmul2_rn(ld(kPlB), ic);
+        const float2 cw = __fmul2_rn(ld(kPlW), ic), ce = __fmul2_rn(ld(kPlE), ic);
+        const float2 cs = __fmul2_rn(ld(kPlS), ic), cn = __fmul2_rn(ld(kPlN), ic);
+        wW[r] = make_float2(fx0 ? ce.x : cw.x, fx1 ? ce.y : cw.y);
+        wE[r] = make_float2(fx0 ? cw.x : ce.x, fx1 ? cw.y : ce.y);
+        wS[r] = fy ? cn : cs;
+        wN[r] = fy ? cs : cn;
+    }
+    __syncthreads();   // every warp has its registers: the planes may be refilled
+#pragma unroll
+    for (int sw = 0; sw < K; ++sw) {
+        stage_next(sw, K);
+        float* e = exch + (sw & 1) * (NW * 2 * RW);
+        *reinterpret_cast<float2*>(e + (2 * w) * RW + 2 * lane) = x[0];
+        *reinterpret_cast<float2*>(e + (2 * w + 1) * RW + 2 * lane) = x[R - 1];
+        __syncthreads();
+        const float2 lo = w > 0 ? *reinterpret_cast<const float2*>(e + (2 * w - 1) * RW + 2 * lane)
+                                : x[0];
+        const float2 hi = w < NW - 1
+                              ? *reinterpret_cast<const float2*>(e + (2 * w + 2) * RW + 2 * lane)
+                              : x[R - 1];
+        const float2 c1 = make_float2(c1s[sw], c1s[sw]), c2 = make_float2(c2s[sw], c2s[sw]);
+        float2 xn[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            float left = __shfl_up_sync(0xffffffffu, x[r].y, 1);
+            float right = __shfl_down_sync(0xffffffffu, x[r].x, 1);
+            if (lane == 0) left = x[r].x;
+            if (lane == 31) right = x[r].y;
+            const float2 xw = make_float2(left, x[r].x), xe = make_float2(x[r].y, right);
+            const float2 xs = r == 0 ? lo : x[r - 1];
+            const float2 xnn = r == R - 1 ? hi : x[r + 1];
+            float2 s = __ffma2_rn(wE[r], xe, __fmul2_rn(wW[r], xw));
+            s = __ffma2_rn(wS[r], xs, s);
+            s = __ffma2_rn(wN[r], xnn, s);
+            const float2 res = __ffma2_rn(s, m1, __ffma2_rn(x[r], m1, rb[r]));
+            const float2 v = __ffma2_rn(c2, res, __ffma2_rn(c1, __ffma2_rn(xa[r], m1, x[r]), x[r]));
+            xn[r] = v;
+            if (sw == K - 1) {
+                const int lj = R * w + r;
+                if (lj >= K && lj < RH - K && J0 + lj <= ny) {
+                    const int li = 2 * lane;
+                    if (li >= K && li < RW - K && gI0 <= nx) {
+                        rsum = fma(res.x, res.x, rsum);
+                        dmax = fmaxf(dmax, fabsf(v.x - x[r].x));
+                    }
+                    if (li + 1 >= K && li + 1 < RW - K && gI1 <= nx) {
+                        rsum = fma(res.y, res.y, rsum);
+                        dmax = fmaxf(dmax, fabsf(v.y - x[r].y));
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            xa[r] = x[r];
+            x[r] = xn[r];
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int lj = R * w + r, gJ = J0 + lj;
+        if (lj < K || lj >= RH - K || gJ > ny) continue;
+        const int li = 2 * lane;
+        const size_t g = (size_t)gJ * NX + gI0;
+        if (li >= K && li < RW - K && gI0 <= nx) { xo[g] = x[r].x; xpo[g] = xa[r].x; }
+        if (li + 1 >= K && li + 1 < RW - K && gI1 <= nx) { xo[g + 1] = x[r].y; xpo[g + 1] = xa[r].y; }
+    }
 }
 
 // Last block of a pass: residual test (or criterion (32) on max |dx|), and the next K weights.

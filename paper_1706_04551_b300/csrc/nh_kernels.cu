@@ -39,18 +39,21 @@ k_break2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ q1,
 }
 
 template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 1)
 k_asm2d_t(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
           const T* __restrict__ q1k, const T* __restrict__ q2k, const T* __restrict__ q1s,
           const T* __restrict__ q2s, const T* __restrict__ w_in, const T* __restrict__ w_b,
           T a, T b, T de, int with_coef, T* __restrict__ ws, T* __restrict__ cC,
           T* __restrict__ cW, T* __restrict__ cE, T* __restrict__ cS, T* __restrict__ cN,
           T* __restrict__ rhs, const T* __restrict__ p0, int resid_form, double* partials,
-          SolveCtl* ctl, double tol2, int max_iter, int kpass)
+          SolveCtl* ctl, double tol2, int max_iter, int kpass, int ntx, int ntiles)
 {
     double acc[3] = {0.0, 0.0, 0.0};
-    asm_tile<T, TX, TY>(P, eta, H, q1k, q2k, q1s, q2s, w_in, w_b, a, b, de, with_coef, ws, cC, cW,
-                        cE, cS, cN, rhs, p0, resid_form, blockIdx.x, blockIdx.y, acc);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        asm_tile<T, TX, TY>(P, eta, H, q1k, q2k, q1s, q2s, w_in, w_b, a, b, de, with_coef, ws, cC,
+                            cW, cE, cS, cN, rhs, p0, resid_form, t % ntx, t / ntx, acc);
+        __syncthreads();   // the tile's shared arrays are restaged by the next tile
+    }
     if (grid_reduce<3, 4u>(acc, partials, &ctl->counter) && threadIdx.x == 0)
         asm_finish(ctl, acc, tol2, max_iter, kpass, with_coef);
 }
@@ -216,18 +219,70 @@ k_cheb_pass2(Rows<T> R, const T* __restrict__ b, const T* __restrict__ xi,
         cheb_finish(ctl, acc, K);
 }
 
+// Register form of the pass (cheb_region_reg): persistent blocks walk the regions
+// blockIdx.x, blockIdx.x + gridDim.x, ... (row-major over nrx columns of regions), each
+// prefetching its next region while it sweeps the current one.
+template <typename T, int C, int R, int NW, int K>
+__global__ void __launch_bounds__(32 * NW, 1)
+k_cheb_reg(Rows<T> Rw, const T* __restrict__ b, const T* __restrict__ xi,
+           const T* __restrict__ xpi, T* __restrict__ xo, T* __restrict__ xpo,
+           double* partials, SolveCtl* ctl, int nrx, int nreg)
+{
+    if (ctl->done) return;
+    constexpr int RW = 32 * C, RH = R * NW, TX = RW - 2 * K, TY = RH - 2 * K;
+    extern __shared__ __align__(16) unsigned char cheb_reg_raw[];
+    T* planes = reinterpret_cast<T*>(cheb_reg_raw);
+    T* exch = planes + kPlanes * RW * RH;
+    __shared__ T c1s[K], c2s[K];
+    if (threadIdx.x < K) {
+        const int k = threadIdx.x;
+        c1s[k] = sizeof(T) == 4 ? (T)ctl->c1f[k] : (T)ctl->c1[k];
+        c2s[k] = sizeof(T) == 4 ? (T)ctl->c2f[k] : (T)ctl->c2[k];
+    }
+    auto stage = [&](int g, int part, int nparts) {
+        cheb_stage_region<T, RW, RH, 32 * NW>(Rw, b, xi, xpi, (g % nrx) * TX - K,
+                                              (g / nrx) * TY - K, planes, part, nparts);
+    };
+    T rsum = T(0), dmax = T(0);
+    int g = blockIdx.x;
+    if (g < nreg) stage(g, 0, 1);
+    for (; g < nreg; g += gridDim.x) {
+        cp_async_wait_all();
+        __syncthreads();
+        const int nxt = g + gridDim.x;
+        auto next = [&](int part, int nparts) {
+            if (nxt < nreg) stage(nxt, part, nparts);
+        };
+        if constexpr (sizeof(T) == 4 && C == 2)
+            cheb_region_reg2<R, NW, K>(Rw, planes, exch, c1s, c2s, (g % nrx) * TX - K,
+                                       (g / nrx) * TY - K, xo, xpo, rsum, dmax, next);
+        else
+            cheb_region_reg<T, C, R, NW, K>(Rw, planes, exch, c1s, c2s, (g % nrx) * TX - K,
+                                            (g / nrx) * TY - K, xo, xpo, rsum, dmax, next);
+    }
+    double acc[2];
+    if (dom_reduce_sum_max_f((float)rsum, (float)dmax, partials, &ctl->counter, acc, blockIdx.x,
+                             gridDim.x) &&
+        threadIdx.x == 0)
+        cheb_finish(ctl, acc, K);
+}
+
 template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 7 : 1)
 k_corr2d_t(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
            const T* __restrict__ q1k, const T* __restrict__ q2k, const T* __restrict__ ws,
            const T* __restrict__ p, const T* __restrict__ dp, T* __restrict__ pout, T de,
            int with_p, T* __restrict__ eo, T* __restrict__ q1o, T* __restrict__ q2o,
-           T* __restrict__ wo, int final_stage, double* partials, StepCtl* st)
+           T* __restrict__ wo, int final_stage, double* partials, StepCtl* st, int ntx,
+           int ntiles)
 {
     T lam = T(0);
     int bad = 0;
-    corr_tile<T, TX, TY>(P, eta, H, q1k, q2k, ws, p, dp, pout, de, with_p, eo, q1o, q2o, wo,
-                         final_stage, blockIdx.x, blockIdx.y, lam, bad);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        corr_tile<T, TX, TY>(P, eta, H, q1k, q2k, ws, p, dp, pout, de, with_p, eo, q1o, q2o, wo,
+                             final_stage, t % ntx, t / ntx, lam, bad);
+        __syncthreads();   // the tile's shared arrays are restaged by the next tile
+    }
     if (bad) atomicOr(&st->nonfinite, 1);
     if (final_stage) {
         double acc[1] = {(double)lam};
@@ -597,6 +652,22 @@ Rows<T> rows_of(const Prm<T>& P, const Bufs<T>& B)
 
 // ================================================================ launchers
 
+// Resident blocks of `kernel` on the current device: SMs x blocks per SM (at least one per
+// SM).  The tiled kernels that end in a grid reduction walk their tiles with this many
+// blocks, so that the reduction has one partial per resident block.
+template <typename K>
+int resident_grid(K kernel, int threads, size_t smem)
+{
+    int dev = 0, nsm = 0, occ = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+        nsm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) != cudaSuccess ||
+        occ < 1)
+        occ = 1;
+    return nsm * occ;
+}
+
 template <typename T>
 void launch_hyp2d(const Prm<T>& P, const Launch& L, const T* eta, const T* q1, const T* q2,
                   const T* etab, const T* q1b, const T* q2b, const T* H, T a, T b, T dt,
@@ -621,12 +692,12 @@ void launch_asm2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* w
                   int max_iter, int kpass, double* partials, SolveCtl* ctl)
 {
     constexpr int TX = 32, TY = sizeof(T) == 4 ? 16 : 8;   // FP64: static shared memory < 48 KB
-    dim3 grid((P.nx + 1 + TX - 1) / TX, (P.ny + 1 + TY - 1) / TY);
-    k_asm2d_t<T, TX, TY><<<grid, kThreads, 0, L.s>>>(P, B.etas, B.H, B.q1k, B.q2k, B.q1s, B.q2s,
-                                                    w_in, w_base, a, b, de, with_coef, B.ws,
-                                                    B.cC, B.cW, B.cE, B.cS, B.cN, B.rhs, B.p,
-                                                    resid_form, partials, ctl, tol2, max_iter,
-                                                    kpass);
+    static const int res = resident_grid(k_asm2d_t<T, TX, TY>, kThreads, 0);
+    const int ntx = (P.nx + 1 + TX - 1) / TX, ntiles = ntx * ((P.ny + 1 + TY - 1) / TY);
+    k_asm2d_t<T, TX, TY><<<ntiles < res ? ntiles : res, kThreads, 0, L.s>>>(
+        P, B.etas, B.H, B.q1k, B.q2k, B.q1s, B.q2s, w_in, w_base, a, b, de, with_coef, B.ws, B.cC,
+        B.cW, B.cE, B.cS, B.cN, B.rhs, B.p, resid_form, partials, ctl, tol2, max_iter, kpass, ntx,
+        ntiles);
 }
 
 // Sweeps per Chebyshev pass: 8 in FP32, 4 in FP64 (the forms below).
@@ -673,14 +744,46 @@ int launch_cheb_cfg(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, const T* 
 }
 
 
+// Register form: region (32 C) x (R NW) nodes, 32 NW threads, one resident block per SM
+// (the staged planes take most of the shared memory), K sweeps per pass.
+template <typename T, int C, int R, int NW, int K>
+int launch_cheb_reg(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, const T* xi,
+                    const T* xpi, T* xo, T* xpo, double* partials)
+{
+    constexpr int TX = 32 * C - 2 * K, TY = R * NW - 2 * K;
+    constexpr size_t smem = cheb_reg_smem<T, C, R, NW>();
+    static int nblk = 0;
+    if (nblk == 0) {
+        if (cudaFuncSetAttribute(k_cheb_reg<T, C, R, NW, K>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return -1;
+        int dev = 0, nsm = 0, occ = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cheb_reg<T, C, R, NW, K>,
+                                                          32 * NW, smem) != cudaSuccess ||
+            occ < 1)
+            return -1;
+        nblk = nsm * occ;
+    }
+    const int nrx = (P.nx + 1 + TX - 1) / TX, nry = (P.ny + 1 + TY - 1) / TY;
+    const int nreg = nrx * nry;
+    k_cheb_reg<T, C, R, NW, K><<<nreg < nblk ? nreg : nblk, 32 * NW, smem, s>>>(
+        rows_of(P, B), B.rhs, xi, xpi, xo, xpo, partials, B.sctl, nrx, nreg);
+    return 0;
+}
+
 // The pass forms the handle chooses from by timing its first passes; all forms of a
 // precision sweep the same number of times per pass (K) and give the same iterates.
 // FP32 (K = 8, weights in registers, padded buffers): 0: 64x64 region, 1024 threads;
 // 1: 128x64, 1024 threads; 2: 64x64, 512 threads, 2 blocks / SM; 3: 64x64, 512 threads,
-// 1 block; 4: 128x64, 512 threads, 1 block.
+// 1 block; 4: 128x64, 512 threads, 1 block; register forms (sweeps in registers,
+// persistent blocks with prefetched regions): 5: 64x64, 512 threads; 6: 64x64, 1024
+// threads; 7: 96x64, 512 threads.
 // FP64 (K = 4): 0: 64x32, shared-memory weights; 1: 64x32, registers; 2: 64x32, registers,
-// padded.
-template <typename T> int cheb_pass_forms() { return sizeof(T) == 4 ? 5 : 3; }
+// padded; 3: register form, 64x32, 512 threads.
+template <typename T> int cheb_pass_forms() { return sizeof(T) == 4 ? 8 : 4; }
 
 template <typename T>
 int launch_cheb_pass(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, const T* xi,
@@ -692,11 +795,15 @@ int launch_cheb_pass(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, const T*
         case 2: return launch_cheb_cfg<T, 2, 4, 16, true, 2, true, 8>(P, s, B, xi, xpi, xo, xpo, partials);
         case 3: return launch_cheb_cfg<T, 2, 4, 16, true, 1, true, 8>(P, s, B, xi, xpi, xo, xpo, partials);
         case 4: return launch_cheb_cfg<T, 4, 4, 16, true, 1, true, 8>(P, s, B, xi, xpi, xo, xpo, partials);
+        case 5: return launch_cheb_reg<T, 2, 4, 16, 8>(P, s, B, xi, xpi, xo, xpo, partials);
+        case 6: return launch_cheb_reg<T, 2, 2, 32, 8>(P, s, B, xi, xpi, xo, xpo, partials);
+        case 7: return launch_cheb_reg<T, 3, 4, 16, 8>(P, s, B, xi, xpi, xo, xpo, partials);
         default: return launch_cheb_cfg<T, 2, 2, 32, true, 1, true, 8>(P, s, B, xi, xpi, xo, xpo, partials);
         }
     } else {
         if (variant == 1) return launch_cheb_cfg<T, 2, 2, 16, true, 1>(P, s, B, xi, xpi, xo, xpo, partials);
         if (variant == 2) return launch_cheb_cfg<T, 2, 2, 16, true, 1, true>(P, s, B, xi, xpi, xo, xpo, partials);
+        if (variant == 3) return launch_cheb_reg<T, 2, 2, 16, 4>(P, s, B, xi, xpi, xo, xpo, partials);
         return launch_cheb_cfg<T, 2, 2, 16, false, 2>(P, s, B, xi, xpi, xo, xpo, partials);
     }
 }
@@ -738,10 +845,11 @@ void launch_corr2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* 
                    double* partials, StepCtl* st)
 {
     constexpr int TX = 32, TY = 8;
-    dim3 grid((P.nx + 1 + TX - 1) / TX, (P.ny + 1 + TY - 1) / TY);
-    k_corr2d_t<T, TX, TY><<<grid, 256, 0, L.s>>>(P, B.etas, B.H, q1k, q2k, B.ws, B.p, B.dp,
-                                                 B.palt, de, with_p, eo, q1o, q2o, wo,
-                                                 final_stage, partials, st);
+    static const int res = resident_grid(k_corr2d_t<T, TX, TY>, 256, 0);
+    const int ntx = (P.nx + 1 + TX - 1) / TX, ntiles = ntx * ((P.ny + 1 + TY - 1) / TY);
+    k_corr2d_t<T, TX, TY><<<ntiles < res ? ntiles : res, 256, 0, L.s>>>(
+        P, B.etas, B.H, q1k, q2k, B.ws, B.p, B.dp, B.palt, de, with_p, eo, q1o, q2o, wo,
+        final_stage, partials, st, ntx, ntiles);
 }
 
 template <typename T>

@@ -33,7 +33,7 @@ class Params(C.Structure):
                 ("B2", C.c_double), ("breaking", C.c_int), ("nonhydrostatic", C.c_int),
                 ("solver", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int),
                 ("precision", C.c_int), ("fixed_dt", C.c_double), ("eps_dp", C.c_double),
-                ("adjoint_frozen_limiter", C.c_int)]
+                ("adjoint_frozen_limiter", C.c_int), ("cheb_form", C.c_int)]
 
 
 class StatsT(C.Structure):
@@ -65,7 +65,7 @@ EXPORTS = ("nh_default_params", "nh_create", "nh_set_state", "nh_get_state", "nh
            "nh_batch_stats", "nh_batch_get_tuning", "nh_batch_set_tuning",
            "nh_batch_candidate", "nh_batch_last_error", "nh_batch_destroy",
            "nh_batch_profile_enable", "nh_batch_profile_read", "nh_tape_bytes",
-           "nh_step_taped", "nh_adjoint_step")
+           "nh_step_taped", "nh_adjoint_step", "nh_cheb_forms")
 
 BATCH_AUTOTUNE, BATCH_GRAPH = 1, 2
 
@@ -126,6 +126,7 @@ def load():
     L.nh_adjoint_step.argtypes = [H, C.c_double, vp, vp, vp, vp, vp, vp]
     L.nh_batch_profile_enable.argtypes = [H, C.c_int]
     L.nh_batch_profile_read.argtypes = [H, C.POINTER(ProfileT)]
+    L.nh_cheb_forms.argtypes = [C.c_int]
     _lib = L
     return L
 
@@ -134,6 +135,14 @@ def default_params() -> Params:
     p = Params()
     load().nh_default_params(C.byref(p))
     return p
+
+
+def cheb_forms(precision: str = "fp32") -> int:
+    """Number of kernel forms of the Chebyshev pass (values of the cheb_form parameter)."""
+    n = load().nh_cheb_forms(FP32 if precision == "fp32" else FP64)
+    if n < 0:
+        raise ValueError(precision)
+    return n
 
 
 def tridiag_batched(a, b, c, d, x, stream=None):

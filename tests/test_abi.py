@@ -45,6 +45,25 @@ def test_create_rejects_bad_grid_without_touching_the_gpu():
     assert rc == nh.EINVAL and not h.value
 
 
+def test_cheb_forms_and_bad_form_rejected_without_touching_the_gpu():
+    import numpy as np
+    B.build()
+    L = nh.load()
+    assert nh.cheb_forms("fp32") == 8 and nh.cheb_forms("fp64") == 4
+    assert L.nh_cheb_forms(7) == nh.EINVAL
+    p = nh.default_params()
+    assert p.cheb_form == -1
+    g = nh.Grid()
+    g.dim, g.nx, g.ny, g.dx, g.dy = 2, 8, 8, 0.1, 0.1
+    H = np.ones(64)
+    for prec, bad in ((nh.FP32, 8), (nh.FP64, 4), (nh.FP32, -2)):
+        p.precision, p.cheb_form = prec, bad
+        h = ctypes.c_void_p()
+        rc = L.nh_create(ctypes.byref(g), H.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                         ctypes.byref(p), None, ctypes.byref(h))
+        assert rc == nh.EINVAL and not h.value
+
+
 def test_create_batch_rejects_bad_input_without_touching_the_gpu():
     import numpy as np
     B.build()
