@@ -948,11 +948,13 @@ cheb_tile_pad(const Rows<T>& R, const T* __restrict__ b, const T* __restrict__ x
 // neighbours come from the neighbouring lanes (shuffles), the south / north ones from the
 // thread's own rows, and the two rows next to another warp from a small exchange buffer
 // (one barrier per sweep).  The eight input planes of the next region (x, x_prev, b and the
-// five coefficients) are copied into shared memory with cp.async while the current region is
-// swept, so the global loads of one region overlap the sweeps of the previous one.  Nodes
-// on the region's rim use their own value for a missing neighbour: like every node within
-// K of the rim they go stale, and none of them reaches the tile interior within K sweeps.
-// Same node arithmetic, in the same order, as cheb_tile_pad: the iterates are identical.
+// five coefficients) are copied into shared memory while the current region is swept: one
+// bulk copy (TMA engine, completion on an mbarrier) per plane row where the region's
+// columns lie inside the grid, element copies (cp.async) with mirrored columns at the west
+// and east edges.  Nodes on the region's rim use their own value for a missing neighbour:
+// like every node within K of the rim they go stale, and none of them reaches the tile
+// interior within K sweeps.  The node arithmetic (cheb_resid / cheb_next) is the one of
+// every other form, so the iterates are the same bits.
 
 __device__ __forceinline__ unsigned smem_u32(const void* p)
 {
@@ -979,76 +981,152 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
-// Planes of a staged region, each RW x RH (row-major, x fastest).
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+// One arrival on `bar` that also announces `bytes` of bulk copies completing on it.
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test_parity(unsigned long long* bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of `bar` to complete, at most `limit` polls; false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity,
+                                                  unsigned limit)
+{
+    for (unsigned k = 0; k < limit; ++k)
+        if (mbar_test_parity(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes,
+                                              unsigned long long* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Order this thread's shared-memory reads before later bulk copies into the same memory.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+// Planes of a staged region (row-major, x fastest).
 enum { kPlX = 0, kPlXp, kPlB, kPlC, kPlW, kPlE, kPlS, kPlN, kPlanes };
 
-// Shared memory of the register form: the staged planes, then the row-exchange buffer
-// (2 parities x NW warps x 2 rows x RW).
+// Staged region of RW x RH nodes: each plane row has SP = RW + A elements (A = elements per
+// 16 bytes).  A row copied in bulk starts at the 16-byte boundary at or below its first node,
+// which then sits at offset (first node's index mod A) of the shared row; rows staged by
+// element copies start at offset 0.
+template <typename T, int RW, int RH>
+struct RegionGeom {
+    static constexpr int A = 16 / (int)sizeof(T);
+    static constexpr int SP = RW + A;
+    static constexpr int PLN = SP * RH;
+    static constexpr unsigned ROWB = SP * sizeof(T);   // bytes of one bulk row copy
+    static_assert(ROWB % 16 == 0, "bulk copies move multiples of 16 bytes");
+    // every row of a region starting at column I0 is one bulk copy inside the node array
+    __device__ static bool bulk(int I0, int NX) { return I0 >= 0 && I0 + SP <= NX; }
+};
+
 template <typename T, int C, int R, int NW>
 constexpr size_t cheb_reg_smem()
 {
-    return ((size_t)kPlanes * (32 * C) * (R * NW) + (size_t)2 * NW * 2 * (32 * C)) * sizeof(T);
+    using G = RegionGeom<T, 32 * C, R * NW>;
+    return ((size_t)kPlanes * G::PLN + (size_t)2 * NW * 2 * (32 * C)) * sizeof(T);
 }
 
-// Issue the copies of part `part` of `nparts` of region (I0, J0)'s eight planes (nodes
-// outside the grid read their mirror image, as the wall and outflow rows of M prescribe) and
-// commit them as one group.  A thread's elements t = tid + e NTHR are split round-robin
-// over the parts, so that the copies can be spread over the sweeps of the previous region.
-template <typename T, int RW, int RH, int NTHR>
-__device__ __forceinline__ void cheb_stage_region(const Rows<T>& R, const T* __restrict__ b,
-                                                  const T* __restrict__ xi,
-                                                  const T* __restrict__ xpi, int I0, int J0,
-                                                  T* planes, int part, int nparts)
+__device__ __forceinline__ int mirror_node(int g, int n)
 {
-    constexpr int RN = RW * RH;
-    constexpr unsigned PB = RN * sizeof(T);
-    // a thread keeps one column when the block is a multiple of the region width
-    constexpr bool COL = NTHR % RW == 0;
+    int m = g < 0 ? -g : (g > n ? 2 * n - g : g);
+    return m < 0 ? 0 : (m > n ? n : m);   // far outside: any node (a finite value)
+}
+
+// Offset of node row lj of region (I0, J0) in its shared row.
+template <typename T, int RW, int RH>
+__device__ __forceinline__ int region_row_off(int I0, int J0, int lj, int nx, int ny)
+{
+    using G = RegionGeom<T, RW, RH>;
+    const int NX = nx + 1;
+    if (!G::bulk(I0, NX)) return 0;
+    return (int)(((size_t)mirror_node(J0 + lj, ny) * NX + I0) & (size_t)(G::A - 1));
+}
+
+// Bytes the bulk copies of region (I0, J0) will complete on the mbarrier (0: element copies).
+template <typename T, int RW, int RH>
+__device__ __forceinline__ unsigned region_bulk_bytes(int I0, int nx)
+{
+    using G = RegionGeom<T, RW, RH>;
+    return G::bulk(I0, nx + 1) ? (unsigned)kPlanes * RH * G::ROWB : 0u;
+}
+
+// Issue the copies of region (I0, J0)'s eight planes (nodes outside the grid read their
+// mirror image, as the wall and outflow rows of M prescribe).  bases: the eight source
+// arrays in plane order.  Bulk copies complete on `bar` (whose expected bytes the caller
+// announced); element copies are committed as one cp.async group.
+template <typename T, int RW, int RH, int NTHR>
+__device__ __forceinline__ void cheb_stage_region(const T* const* bases, int nx, int ny,
+                                                  int I0, int J0, T* planes,
+                                                  unsigned long long* bar)
+{
+    using G = RegionGeom<T, RW, RH>;
+    const int NX = nx + 1;
     const int tid = threadIdx.x;
-    const int nx = R.nx, ny = R.ny, NX = nx + 1;
-    const unsigned s0 = smem_u32(planes);
-    int li = tid % RW, mI = 0;
-    auto mirror_x = [&](int l) {
-        const int gI = I0 + l;
-        int m = gI < 0 ? -gI : (gI > nx ? 2 * nx - gI : gI);
-        return m < 0 ? 0 : (m > nx ? nx : m);
-    };
-    if (COL) mI = mirror_x(li);
-    for (int t = tid + part * NTHR; t < RN; t += nparts * NTHR) {
-        const int lj = t / RW;
-        if (!COL) {
-            li = t % RW;
-            mI = mirror_x(li);
+    if (G::bulk(I0, NX)) {
+        for (int c = tid; c < kPlanes * RH; c += NTHR) {
+            const int p = c / RH, lj = c - p * RH;
+            const size_t e0 = (size_t)mirror_node(J0 + lj, ny) * NX + I0;
+            const size_t a0 = e0 & ~(size_t)(G::A - 1);
+            bulk_copy_g2s(planes + p * G::PLN + lj * G::SP, bases[p] + a0, G::ROWB, bar);
         }
-        const int gJ = J0 + lj;
-        int mJ = gJ < 0 ? -gJ : (gJ > ny ? 2 * ny - gJ : gJ);
-        mJ = mJ < 0 ? 0 : (mJ > ny ? ny : mJ);
-        const size_t g = (size_t)mJ * NX + mI;
-        const unsigned s = s0 + (unsigned)((lj * RW + li) * sizeof(T));
-        cp_async_elem<sizeof(T)>(s + kPlX * PB, xi + g);
-        cp_async_elem<sizeof(T)>(s + kPlXp * PB, xpi + g);
-        cp_async_elem<sizeof(T)>(s + kPlB * PB, b + g);
-        cp_async_elem<sizeof(T)>(s + kPlC * PB, R.cC + g);
-        cp_async_elem<sizeof(T)>(s + kPlW * PB, R.cW + g);
-        cp_async_elem<sizeof(T)>(s + kPlE * PB, R.cE + g);
-        cp_async_elem<sizeof(T)>(s + kPlS * PB, R.cS + g);
-        cp_async_elem<sizeof(T)>(s + kPlN * PB, R.cN + g);
+        return;
+    }
+    const unsigned s0 = smem_u32(planes);
+    constexpr unsigned PB = G::PLN * sizeof(T);
+    for (int t = tid; t < RW * RH; t += NTHR) {
+        const int li = t % RW, lj = t / RW;
+        const size_t g = (size_t)mirror_node(J0 + lj, ny) * NX + mirror_node(I0 + li, nx);
+        const unsigned s = s0 + (unsigned)((lj * G::SP + li) * sizeof(T));
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) cp_async_elem<sizeof(T)>(s + p * PB, bases[p] + g);
     }
     cp_async_commit();
 }
 
-// One staged region (I0, J0): registers from the planes, then K sweeps, each preceded by
-// `stage_next(sw, K)` (the planes are free once every warp holds its registers), so that
-// the copies of the next region go out in K slices between the sweeps; writes the tile
-// interior's x and x_prev and adds the last sweep's squared scaled residuals and largest
-// change over the interior nodes to rsum / dmax.  c1s / c2s: the K sweep weights.
+// One staged region (I0, J0): registers from the planes, then `stage_next(-1)` (before the
+// barrier that frees the planes: fences and announces the next region's copies), then K
+// sweeps, the first preceded by `stage_next(0)` (issues the next region's copies); writes
+// the tile interior's x and x_prev and adds the last sweep's squared scaled residuals and
+// largest change over the interior nodes to rsum / dmax.  c1s / c2s: the K sweep weights.
 template <typename T, int C, int R, int NW, int K, typename F>
 __device__ __forceinline__ void cheb_region_reg(const Rows<T>& Rw, const T* planes, T* exch,
                                                 const T* c1s, const T* c2s, int I0, int J0,
                                                 T* __restrict__ xo, T* __restrict__ xpo,
                                                 T& rsum, T& dmax, F stage_next)
 {
-    constexpr int RW = 32 * C, RH = R * NW, RN = RW * RH;
+    constexpr int RW = 32 * C, RH = R * NW;
+    using G = RegionGeom<T, RW, RH>;
     const int nx = Rw.nx, ny = Rw.ny, NX = nx + 1;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     T x[R][C], xa[R][C], rb[R][C], wW[R][C], wE[R][C], wS[R][C], wN[R][C];
@@ -1056,29 +1134,31 @@ __device__ __forceinline__ void cheb_region_reg(const Rows<T>& Rw, const T* plan
     for (int r = 0; r < R; ++r) {
         const int lj = R * w + r, gJ = J0 + lj;
         const bool fy = gJ < 0 || gJ > ny;
+        const int row = lj * G::SP + region_row_off<T, RW, RH>(I0, J0, lj, nx, ny);
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             const int li = C * lane + c, gI = I0 + li;
             const bool fx = gI < 0 || gI > nx;
-            const int t = lj * RW + li;
-            const T ic = qdiv(T(1), planes[kPlC * RN + t]);
-            x[r][c] = planes[kPlX * RN + t];
-            xa[r][c] = planes[kPlXp * RN + t];
-            rb[r][c] = mul_rn(planes[kPlB * RN + t], ic);
-            const T cw = mul_rn(planes[kPlW * RN + t], ic);
-            const T ce = mul_rn(planes[kPlE * RN + t], ic);
-            const T cs = mul_rn(planes[kPlS * RN + t], ic);
-            const T cn = mul_rn(planes[kPlN * RN + t], ic);
+            const int t = row + li;
+            const T ic = qdiv(T(1), planes[kPlC * G::PLN + t]);
+            x[r][c] = planes[kPlX * G::PLN + t];
+            xa[r][c] = planes[kPlXp * G::PLN + t];
+            rb[r][c] = mul_rn(planes[kPlB * G::PLN + t], ic);
+            const T cw = mul_rn(planes[kPlW * G::PLN + t], ic);
+            const T ce = mul_rn(planes[kPlE * G::PLN + t], ic);
+            const T cs = mul_rn(planes[kPlS * G::PLN + t], ic);
+            const T cn = mul_rn(planes[kPlN * G::PLN + t], ic);
             wW[r][c] = fx ? ce : cw;
             wE[r][c] = fx ? cw : ce;
             wS[r][c] = fy ? cn : cs;
             wN[r][c] = fy ? cs : cn;
         }
     }
+    stage_next(-1);
     __syncthreads();   // every warp has its registers: the planes may be refilled
+    stage_next(0);
 #pragma unroll
     for (int sw = 0; sw < K; ++sw) {
-        stage_next(sw, K);
         T* e = exch + (sw & 1) * (NW * 2 * RW);
 #pragma unroll
         for (int c = 0; c < C; ++c) {
@@ -1144,7 +1224,6 @@ __device__ __forceinline__ void cheb_region_reg(const Rows<T>& Rw, const T* plan
     }
 }
 
-
 // Packed FP32 form of cheb_region_reg for C = 2: a lane's two columns are one float2 and
 // every sweep operation acts on both with one Blackwell packed instruction (FFMA2 / FMUL2;
 // differences as fma(a, -1, b), which rounds like b - a).  Each packed lane rounds like the
@@ -1156,7 +1235,8 @@ __device__ __forceinline__ void cheb_region_reg2(const Rows<float>& Rw, const fl
                                                  float* __restrict__ xo, float* __restrict__ xpo,
                                                  float& rsum, float& dmax, F stage_next)
 {
-    constexpr int RW = 64, RH = R * NW, RN = RW * RH;
+    constexpr int RW = 64, RH = R * NW;
+    using G = RegionGeom<float, RW, RH>;
     const int nx = Rw.nx, ny = Rw.ny, NX = nx + 1;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const float2 m1 = make_float2(-1.f, -1.f);
@@ -1167,8 +1247,13 @@ __device__ __forceinline__ void cheb_region_reg2(const Rows<float>& Rw, const fl
     for (int r = 0; r < R; ++r) {
         const int lj = R * w + r, gJ = J0 + lj;
         const bool fy = gJ < 0 || gJ > ny;
-        const int t = lj * RW + 2 * lane;
-        auto ld = [&](int plane) { return *reinterpret_cast<const float2*>(planes + plane * RN + t); };
+        const int off = region_row_off<float, RW, RH>(I0, J0, lj, nx, ny);
+        const int t = lj * G::SP + off + 2 * lane;
+        // an odd row offset leaves the pair 4-byte aligned only
+        auto ld = [&](int plane) {
+            const float* q = planes + plane * G::PLN + t;
+            return (off & 1) ? make_float2(q[0], q[1]) : *reinterpret_cast<const float2*>(q);
+        };
         const float2 cc = ld(kPlC);
         const float2 ic = make_float2(qdiv(1.f, cc.x), qdiv(1.f, cc.y));
         x[r] = ld(kPlX);
@@ -1181,10 +1266,11 @@ __device__ __forceinline__ void cheb_region_reg2(const Rows<float>& Rw, const fl
         wS[r] = fy ? cn : cs;
         wN[r] = fy ? cs : cn;
     }
+    stage_next(-1);
     __syncthreads();   // every warp has its registers: the planes may be refilled
+    stage_next(0);
 #pragma unroll
     for (int sw = 0; sw < K; ++sw) {
-        stage_next(sw, K);
         float* e = exch + (sw & 1) * (NW * 2 * RW);
         *reinterpret_cast<float2*>(e + (2 * w) * RW + 2 * lane) = x[0];
         *reinterpret_cast<float2*>(e + (2 * w + 1) * RW + 2 * lane) = x[R - 1];
@@ -1246,6 +1332,10 @@ __device__ __forceinline__ void cheb_region_reg2(const Rows<float>& Rw, const fl
 // Last block of a pass: residual test (or criterion (32) on max |dx|), and the next K weights.
 __device__ __forceinline__ void cheb_finish(SolveCtl* ctl, const double (&acc)[2], int K)
 {
+    if (ctl->status == 5) {   // a block of the register form gave up waiting for its copies
+        ctl->done = 1;
+        return;
+    }
     ctl->rr = acc[0];
     ctl->dpmax = acc[1];
     ctl->sweeps += K;

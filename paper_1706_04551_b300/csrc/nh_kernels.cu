@@ -221,7 +221,11 @@ k_cheb_pass2(Rows<T> R, const T* __restrict__ b, const T* __restrict__ xi,
 
 // Register form of the pass (cheb_region_reg): persistent blocks walk the regions
 // blockIdx.x, blockIdx.x + gridDim.x, ... (row-major over nrx columns of regions), each
-// prefetching its next region while it sweeps the current one.
+// prefetching its next region while it sweeps the current one.  A wait for a region's
+// copies gives up after kSpinLimit polls: the block then marks the solve failed (status 5)
+// and leaves the region walk.
+constexpr unsigned kSpinLimit = 1u << 22;
+
 template <typename T, int C, int R, int NW, int K>
 __global__ void __launch_bounds__(32 * NW, 1)
 k_cheb_reg(Rows<T> Rw, const T* __restrict__ b, const T* __restrict__ xi,
@@ -230,40 +234,66 @@ k_cheb_reg(Rows<T> Rw, const T* __restrict__ b, const T* __restrict__ xi,
 {
     if (ctl->done) return;
     constexpr int RW = 32 * C, RH = R * NW, TX = RW - 2 * K, TY = RH - 2 * K;
+    using G = RegionGeom<T, RW, RH>;
     extern __shared__ __align__(16) unsigned char cheb_reg_raw[];
     T* planes = reinterpret_cast<T*>(cheb_reg_raw);
-    T* exch = planes + kPlanes * RW * RH;
+    T* exch = planes + kPlanes * G::PLN;
     __shared__ T c1s[K], c2s[K];
-    if (threadIdx.x < K) {
-        const int k = threadIdx.x;
-        c1s[k] = sizeof(T) == 4 ? (T)ctl->c1f[k] : (T)ctl->c1[k];
-        c2s[k] = sizeof(T) == 4 ? (T)ctl->c2f[k] : (T)ctl->c2[k];
+    __shared__ const T* bases[kPlanes];
+    __shared__ __align__(8) unsigned long long bar;
+    const int tid = threadIdx.x, nx = Rw.nx, ny = Rw.ny;
+    if (tid < K) {
+        c1s[tid] = sizeof(T) == 4 ? (T)ctl->c1f[tid] : (T)ctl->c1[tid];
+        c2s[tid] = sizeof(T) == 4 ? (T)ctl->c2f[tid] : (T)ctl->c2[tid];
     }
-    auto stage = [&](int g, int part, int nparts) {
-        cheb_stage_region<T, RW, RH, 32 * NW>(Rw, b, xi, xpi, (g % nrx) * TX - K,
-                                              (g / nrx) * TY - K, planes, part, nparts);
-    };
-    T rsum = T(0), dmax = T(0);
+    auto I0of = [&](int g) { return (g % nrx) * TX - K; };
+    auto J0of = [&](int g) { return (g / nrx) * TY - K; };
     int g = blockIdx.x;
-    if (g < nreg) stage(g, 0, 1);
+    if (tid == 0) {
+        bases[kPlX] = xi; bases[kPlXp] = xpi; bases[kPlB] = b; bases[kPlC] = Rw.cC;
+        bases[kPlW] = Rw.cW; bases[kPlE] = Rw.cE; bases[kPlS] = Rw.cS; bases[kPlN] = Rw.cN;
+        mbar_init(&bar, 1);
+        if (g < nreg) mbar_arrive_expect_tx(&bar, region_bulk_bytes<T, RW, RH>(I0of(g), nx));
+    }
+    __syncthreads();
+    if (g < nreg) cheb_stage_region<T, RW, RH, 32 * NW>(bases, nx, ny, I0of(g), J0of(g), planes, &bar);
+    T rsum = T(0), dmax = T(0);
+    unsigned phase = 0;
+    bool ok = true;
     for (; g < nreg; g += gridDim.x) {
         cp_async_wait_all();
-        __syncthreads();
+        const bool got = mbar_wait_bounded(&bar, phase, kSpinLimit);
+        if (__syncthreads_or(!got)) { ok = false; break; }
+        phase ^= 1u;
         const int nxt = g + gridDim.x;
-        auto next = [&](int part, int nparts) {
-            if (nxt < nreg) stage(nxt, part, nparts);
+        auto next = [&](int part) {
+            if (nxt >= nreg) return;
+            if (part < 0) {   // before the barrier that frees the planes
+                fence_proxy_async_smem();
+                if (tid == 0)
+                    mbar_arrive_expect_tx(&bar, region_bulk_bytes<T, RW, RH>(I0of(nxt), nx));
+            } else {
+                cheb_stage_region<T, RW, RH, 32 * NW>(bases, nx, ny, I0of(nxt), J0of(nxt),
+                                                      planes, &bar);
+            }
         };
         if constexpr (sizeof(T) == 4 && C == 2)
-            cheb_region_reg2<R, NW, K>(Rw, planes, exch, c1s, c2s, (g % nrx) * TX - K,
-                                       (g / nrx) * TY - K, xo, xpo, rsum, dmax, next);
+            cheb_region_reg2<R, NW, K>(Rw, planes, exch, c1s, c2s, I0of(g), J0of(g), xo, xpo,
+                                       rsum, dmax, next);
         else
-            cheb_region_reg<T, C, R, NW, K>(Rw, planes, exch, c1s, c2s, (g % nrx) * TX - K,
-                                            (g / nrx) * TY - K, xo, xpo, rsum, dmax, next);
+            cheb_region_reg<T, C, R, NW, K>(Rw, planes, exch, c1s, c2s, I0of(g), J0of(g), xo,
+                                            xpo, rsum, dmax, next);
+    }
+    if (!ok) {
+        // the region's copies may still be in flight: give them one more bounded wait
+        mbar_wait_bounded(&bar, phase, kSpinLimit);
+        cp_async_wait_all();
+        if (tid == 0) { ctl->status = 5; ctl->done = 1; }
     }
     double acc[2];
     if (dom_reduce_sum_max_f((float)rsum, (float)dmax, partials, &ctl->counter, acc, blockIdx.x,
                              gridDim.x) &&
-        threadIdx.x == 0)
+        threadIdx.x == 0 && ok)
         cheb_finish(ctl, acc, K);
 }
 
