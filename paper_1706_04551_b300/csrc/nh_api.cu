@@ -388,7 +388,7 @@ struct Impl : Base {
                     if (vt_solve[k] == solves) vt_ok[k] = vt_pass[k] < ran ? 1 : 0;
                 if (vt_used >= kVT || (vt_next > 0 && solves >= 12)) choose_pass_variant();
             }
-            if (h_sctl->status == 5)
+            if (h_sctl->status == 6)
                 return fail(hd, NH_ECUDA, "Chebyshev pass: a wait for staged copies timed out");
             if (h_sctl->status == 4) return fallback(stage, false);   // not diagonally dominant
             if (h_sctl->done) settle_passes(h_sctl->sweeps / K);

@@ -148,8 +148,10 @@ kb_break(Arena<T> A, const int2* __restrict__ wl, int nw, const T* eta, const T*
         const long long c = D.coff, n = (long long)P.nx * P.ny;
         const T de = bfac * (T)A.ds[it.x].dt;
         for (long long k = (long long)it.y * kChunk + threadIdx.x;
-             k < n && k < (long long)(it.y + 1) * kChunk; k += blockDim.x)
-            break_cell(P, eta + c, q1 + c, q2 + c, H + c, de, q1o + c, q2o + c, k);
+             k < n && k < (long long)(it.y + 1) * kChunk; k += blockDim.x) {
+            const int kk = (int)k, j = kk / P.nx;   // a domain holds < 2^31 cells
+            break_cell(P, eta + c, q1 + c, q2 + c, H + c, de, q1o + c, q2o + c, kk - j * P.nx, j);
+        }
     }
 }
 
@@ -199,6 +201,36 @@ kb_asm(Arena<T> A, const int2* __restrict__ wl, int nw, const T* eta, const T* H
     }
 }
 
+// Last block of a domain's items in a pass: convergence test and next weights, the stall
+// test (8 passes without a 0.81 reduction of the best residual: status 5, BiCGStab takes
+// over from the current dp), and the loop counters and statistics of a finished domain.
+template <typename T>
+__device__ __forceinline__ void kb_cheb_finish(const Arena<T>& A, int d, SolveCtl* ctl,
+                                               const double (&acc)[2], int K, int stage)
+{
+    cheb_finish(ctl, acc, K);
+    if (!ctl->done) {
+        if (acc[0] < 0.81 * ctl->best) { ctl->best = acc[0]; ctl->stale = 0; }
+        else if (++ctl->stale >= 8) { ctl->done = 1; ctl->status = 5; }
+    }
+    if (ctl->done) {
+        atomicSub(&A.loop[0], 1u);
+        DomState& s = A.ds[d];
+        s.sweeps += ctl->sweeps;
+        s.last_sweeps[stage] = ctl->sweeps;
+        if (ctl->status == 5) {
+            // stalled (rounding floor of the precision, or a spectrum the Gershgorin
+            // interval does not describe)
+            ctl->fb = 1;
+            atomicAdd(&A.loop[2], 1u);
+        } else {
+            s.last_status[stage] = ctl->status;
+            s.last_resid[stage] = ctl->bdb > 0.0 ? sqrt(ctl->rr / ctl->bdb) : 0.0;
+            if (ctl->status != 1) s.nonconv += 1;
+        }
+    }
+}
+
 template <typename T, int NA, int NB, int BY, int K, bool REGW, int MINB, bool PAD>
 __global__ void __launch_bounds__(32 * BY, MINB)
 kb_cheb(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const T* cW,
@@ -229,31 +261,115 @@ kb_cheb(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const T* c
         double acc[2];
         if (dom_reduce_sum_max_f((float)rsum, (float)dmax, A.partials + D.poff, &ctl->counter,
                                  acc, it.y, nt) &&
-            threadIdx.x == 0 && threadIdx.y == 0) {
-            cheb_finish(ctl, acc, K);
-            if (!ctl->done) {
-                // stall test: 8 passes without a 0.81 reduction of the best residual
-                if (acc[0] < 0.81 * ctl->best) { ctl->best = acc[0]; ctl->stale = 0; }
-                else if (++ctl->stale >= 8) { ctl->done = 1; ctl->status = 5; }
-            }
-            if (ctl->done) {
-                atomicSub(&A.loop[0], 1u);
-                DomState& s = A.ds[it.x];
-                s.sweeps += ctl->sweeps;
-                s.last_sweeps[stage] = ctl->sweeps;
-                if (ctl->status == 5) {
-                    // stalled (rounding floor of the precision, or a spectrum the
-                    // Gershgorin interval does not describe): BiCGStab from the current dp
-                    ctl->fb = 1;
-                    atomicAdd(&A.loop[2], 1u);
-                } else {
-                    s.last_status[stage] = ctl->status;
-                    s.last_resid[stage] = ctl->bdb > 0.0 ? sqrt(ctl->rr / ctl->bdb) : 0.0;
-                    if (ctl->status != 1) s.nonconv += 1;
-                }
-            }
-        }
+            threadIdx.x == 0 && threadIdx.y == 0)
+            kb_cheb_finish(A, it.x, ctl, acc, K, stage);
         __syncthreads();
+    }
+}
+
+// Register form of the batched pass: persistent blocks walk the work list (items of
+// domains that have converged are skipped: a domain's done flag cannot change while one of
+// its items of this pass is unprocessed), each prefetching its next item's region (bulk
+// copies on an mbarrier, element copies at the domain's west and east edges) while it
+// sweeps the current one; every item ends in its domain's reduction as in kb_cheb.  A wait
+// that runs out of polls marks the item's domain failed (status 6, counted as a
+// non-converged solve) and ends the block's walk.
+template <typename T, int C, int R, int NW, int K>
+__global__ void __launch_bounds__(32 * NW, 1)
+kb_cheb_reg(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const T* cW,
+            const T* cE, const T* cS, const T* cN, const T* rhs, const T* xi, const T* xpi,
+            T* xo, T* xpo, int stage)
+{
+    constexpr int RW = 32 * C, RH = R * NW, TX = RW - 2 * K, TY = RH - 2 * K;
+    constexpr unsigned kPolls = 1u << 22;
+    using G = RegionGeom<T, RW, RH>;
+    extern __shared__ __align__(16) unsigned char kb_reg_raw[];
+    T* planes = reinterpret_cast<T*>(kb_reg_raw);
+    T* exch = planes + kPlanes * G::PLN;
+    __shared__ T c1s[K], c2s[K];
+    __shared__ const T* bases[kPlanes];
+    __shared__ __align__(8) unsigned long long bar;
+    const int tid = threadIdx.x;
+    auto next_active = [&](int w) {
+        for (; w < nw; w += gridDim.x)
+            if (!A.sctl[wl[w].x].done) return w;
+        return nw;
+    };
+    // region origin of item w (nx, ny of its domain)
+    auto origin = [&](int w, int& I0, int& J0, int& nx, int& ny) {
+        const int2 it = wl[w];
+        const Prm<T>& P = A.dom[it.x].P;
+        nx = P.nx; ny = P.ny;
+        const int ntx = cdiv(nx + 1, TX);
+        I0 = (it.y % ntx) * TX - K;
+        J0 = (it.y / ntx) * TY - K;
+    };
+    auto announce = [&](int w) {   // thread 0: the item's sources and expected bytes
+        const long long n = A.dom[wl[w].x].noff;
+        bases[kPlX] = xi + n; bases[kPlXp] = xpi + n; bases[kPlB] = rhs + n; bases[kPlC] = cC + n;
+        bases[kPlW] = cW + n; bases[kPlE] = cE + n; bases[kPlS] = cS + n; bases[kPlN] = cN + n;
+        int I0, J0, nx, ny;
+        origin(w, I0, J0, nx, ny);
+        mbar_arrive_expect_tx(&bar, region_bulk_bytes<T, RW, RH>(I0, nx));
+    };
+    auto stage_item = [&](int w) {
+        int I0, J0, nx, ny;
+        origin(w, I0, J0, nx, ny);
+        cheb_stage_region<T, RW, RH, 32 * NW>(bases, nx, ny, I0, J0, planes, &bar);
+    };
+    int w = next_active(blockIdx.x);
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        if (w < nw) announce(w);
+    }
+    __syncthreads();
+    if (w < nw) stage_item(w);
+    unsigned phase = 0;
+    while (w < nw) {
+        cp_async_wait_all();
+        const bool got = mbar_wait_bounded(&bar, phase, kPolls);
+        const int2 it = wl[w];
+        SolveCtl* ctl = &A.sctl[it.x];
+        if (__syncthreads_or(!got)) {
+            mbar_wait_bounded(&bar, phase, kPolls);   // copies possibly still in flight
+            if (tid == 0) { ctl->status = 6; atomicAdd(&A.ds[it.x].nonconv, 1); }
+            break;
+        }
+        phase ^= 1u;
+        const Dom<T>& D = A.dom[it.x];
+        const long long n = D.noff;
+        Rows<T> Rw;
+        Rw.cC = cC + n; Rw.cW = cW + n; Rw.cE = cE + n; Rw.cS = cS + n; Rw.cN = cN + n;
+        Rw.nx = D.P.nx; Rw.ny = D.P.ny;
+        if (tid < K) {
+            c1s[tid] = sizeof(T) == 4 ? (T)ctl->c1f[tid] : (T)ctl->c1[tid];
+            c2s[tid] = sizeof(T) == 4 ? (T)ctl->c2f[tid] : (T)ctl->c2[tid];
+        }
+        const int ntx = cdiv(Rw.nx + 1, TX), nt = ntx * cdiv(Rw.ny + 1, TY);
+        const int I0 = (it.y % ntx) * TX - K, J0 = (it.y / ntx) * TY - K;
+        const int wn = next_active(w + gridDim.x);
+        auto next = [&](int part) {
+            if (wn >= nw) return;
+            if (part < 0) {   // before the barrier that frees the planes
+                fence_proxy_async_smem();
+                if (tid == 0) announce(wn);
+            } else {
+                stage_item(wn);
+            }
+        };
+        T rsum = T(0), dmax = T(0);
+        if constexpr (sizeof(T) == 4 && C == 2)
+            cheb_region_reg2<R, NW, K>(Rw, planes, exch, c1s, c2s, I0, J0, xo + n, xpo + n, rsum,
+                                       dmax, next);
+        else
+            cheb_region_reg<T, C, R, NW, K>(Rw, planes, exch, c1s, c2s, I0, J0, xo + n, xpo + n,
+                                            rsum, dmax, next);
+        double acc[2];
+        if (dom_reduce_sum_max_f((float)rsum, (float)dmax, A.partials + D.poff, &ctl->counter,
+                                 acc, it.y, nt) &&
+            tid == 0)
+            kb_cheb_finish(A, it.x, ctl, acc, K, stage);
+        w = wn;
     }
 }
 
@@ -603,6 +719,19 @@ void run_cheb(int grid, cudaStream_t s, const Arena<T>& A, const int2* wl, int n
 
 #define KB_CHEB(T, NA, NB, BY, REGW, MINB, PAD) kb_cheb<T, NA, NB, BY, ChebK<T>::value, REGW, MINB, PAD>
 
+// register form: region (32 C) x (R NW), 32 NW threads
+template <typename T, int C, int R, int NW>
+void run_cheb_reg(int grid, cudaStream_t s, const Arena<T>& A, const int2* wl, int nw,
+                  const T* cC, const T* cW, const T* cE, const T* cS, const T* cN, const T* rhs,
+                  const T* xi, const T* xpi, T* xo, T* xpo, int stage)
+{
+    kb_cheb_reg<T, C, R, NW, ChebK<T>::value>
+        <<<grid, 32 * NW, cheb_reg_smem<T, C, R, NW>(), s>>>(A, wl, nw, cC, cW, cE, cS, cN, rhs,
+                                                             xi, xpi, xo, xpo, stage);
+}
+
+#define KB_CHEB_REG(T, C, R, NW) kb_cheb_reg<T, C, R, NW, ChebK<T>::value>
+
 template <typename T>
 struct Cand {
     Shape shape;
@@ -612,7 +741,7 @@ struct Cand {
 
 template <>
 struct Cands<float> {
-    static constexpr int nh = 3, na = 3, nc = 4;
+    static constexpr int nh = 3, na = 3, nc = 6;
     static Shape hyp_shape(int k) { const Shape s[nh] = {{32, 16, 256}, {32, 8, 256}, {64, 8, 256}}; return s[k]; }
     static HypFn<float> hyp(int k)
     {
@@ -637,16 +766,25 @@ struct Cands<float> {
                              (const void*)kb_asm<float, 64, 8>};
         return f[k];
     }
-    // Chebyshev: region (tile + 4-node halo on every side) and threads
-    // 8 sweeps per pass, weights in registers, padded buffers: regions 64x64 (1024 threads),
-    // 64x64 (512 threads, 1 block / SM), 128x64 (1024 threads), 128x64 (512 threads)
-    static Shape cheb_shape(int k) { const Shape s[nc] = {{64, 64, 1024}, {64, 64, 512}, {128, 64, 1024}, {128, 64, 512}}; return s[k]; }
+    // Chebyshev: region (tile + 8-node halo on every side) and threads, 8 sweeps per pass.
+    // 0-3: weights in registers, padded buffers: regions 64x64 (1024 threads), 64x64 (512
+    // threads, 1 block / SM), 128x64 (1024 threads), 128x64 (512 threads); 4-5: register
+    // form (sweeps in registers, prefetched regions): 96x64 (512 threads), 64x64 (512
+    // threads, packed FP32 pairs)
+    static Shape cheb_shape(int k)
+    {
+        const Shape s[nc] = {{64, 64, 1024}, {64, 64, 512}, {128, 64, 1024},
+                             {128, 64, 512}, {96, 64, 512},  {64, 64, 512}};
+        return s[k];
+    }
     static ChebFn<float> cheb(int k)
     {
         const ChebFn<float> f[nc] = {run_cheb<float, 2, 2, 32, true, 1, true>,
                                      run_cheb<float, 2, 4, 16, true, 1, true>,
                                      run_cheb<float, 4, 2, 32, true, 1, true>,
-                                     run_cheb<float, 4, 4, 16, true, 1, true>};
+                                     run_cheb<float, 4, 4, 16, true, 1, true>,
+                                     run_cheb_reg<float, 3, 4, 16>,
+                                     run_cheb_reg<float, 2, 4, 16>};
         return f[k];
     }
     static const void* cheb_kernel(int k)
@@ -654,7 +792,9 @@ struct Cands<float> {
         const void* f[nc] = {(const void*)KB_CHEB(float, 2, 2, 32, true, 1, true),
                              (const void*)KB_CHEB(float, 2, 4, 16, true, 1, true),
                              (const void*)KB_CHEB(float, 4, 2, 32, true, 1, true),
-                             (const void*)KB_CHEB(float, 4, 4, 16, true, 1, true)};
+                             (const void*)KB_CHEB(float, 4, 4, 16, true, 1, true),
+                             (const void*)KB_CHEB_REG(float, 3, 4, 16),
+                             (const void*)KB_CHEB_REG(float, 2, 4, 16)};
         return f[k];
     }
     static size_t cheb_smem_of(int k)
@@ -662,14 +802,16 @@ struct Cands<float> {
         const size_t s[nc] = {cheb_smem<float, 2, 2, 32, true, true>(),
                               cheb_smem<float, 2, 4, 16, true, true>(),
                               cheb_smem<float, 4, 2, 32, true, true>(),
-                              cheb_smem<float, 4, 4, 16, true, true>()};
+                              cheb_smem<float, 4, 4, 16, true, true>(),
+                              cheb_reg_smem<float, 3, 4, 16>(),
+                              cheb_reg_smem<float, 2, 4, 16>()};
         return s[k];
     }
 };
 
 template <>
 struct Cands<double> {
-    static constexpr int nh = 2, na = 2, nc = 2;
+    static constexpr int nh = 2, na = 2, nc = 3;
     static Shape hyp_shape(int k) { const Shape s[nh] = {{32, 8, 256}, {16, 16, 256}}; return s[k]; }
     static HypFn<double> hyp(int k)
     {
@@ -693,23 +835,28 @@ struct Cands<double> {
         const void* f[na] = {(const void*)kb_asm<double, 32, 8>, (const void*)kb_asm<double, 16, 16>};
         return f[k];
     }
-    static Shape cheb_shape(int k) { const Shape s[nc] = {{64, 32, 512}, {64, 32, 256}}; return s[k]; }
+    // 4 sweeps per pass: 64x32 regions, shared-memory weights (512 or 256 threads), and the
+    // register form (512 threads)
+    static Shape cheb_shape(int k) { const Shape s[nc] = {{64, 32, 512}, {64, 32, 256}, {64, 32, 512}}; return s[k]; }
     static ChebFn<double> cheb(int k)
     {
         const ChebFn<double> f[nc] = {run_cheb<double, 2, 2, 16, false, 2, false>,
-                                      run_cheb<double, 2, 4, 8, false, 2, false>};
+                                      run_cheb<double, 2, 4, 8, false, 2, false>,
+                                      run_cheb_reg<double, 2, 2, 16>};
         return f[k];
     }
     static const void* cheb_kernel(int k)
     {
         const void* f[nc] = {(const void*)KB_CHEB(double, 2, 2, 16, false, 2, false),
-                             (const void*)KB_CHEB(double, 2, 4, 8, false, 2, false)};
+                             (const void*)KB_CHEB(double, 2, 4, 8, false, 2, false),
+                             (const void*)KB_CHEB_REG(double, 2, 2, 16)};
         return f[k];
     }
     static size_t cheb_smem_of(int k)
     {
         const size_t s[nc] = {cheb_smem<double, 2, 2, 16, false, false>(),
-                              cheb_smem<double, 2, 4, 8, false, false>()};
+                              cheb_smem<double, 2, 4, 8, false, false>(),
+                              cheb_reg_smem<double, 2, 2, 16>()};
         return s[k];
     }
 };

@@ -24,12 +24,13 @@ template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return a < b
 template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
 
 // minmod slope limiter of the MUSCL reconstruction (Sec. 4.1).
+// Branch-free: sign(a) max(0, min(|a|, sign(a) b)) is the smaller of a, b in magnitude when
+// they have one sign and zero otherwise.
 template <typename T>
 __device__ __forceinline__ T minmod(T a, T b)
 {
-    if (a > T(0) && b > T(0)) return tmin(a, b);
-    if (a < T(0) && b < T(0)) return tmax(a, b);
-    return T(0);
+    const T s = copysign(T(1), a);
+    return s * tmax(T(0), tmin(fabs(a), s * b));
 }
 
 // Square root and quotient of the hot FP32 paths: the hardware approximations
@@ -158,9 +159,9 @@ template <typename T>
 __device__ __forceinline__ T nu_break(T h, T d, T g, T B1, T hdry)
 {
     if (!(h > hdry)) return T(0);
-    T U1 = B1 * sqrt(g * h);
+    T U1 = B1 * qsqrt(g * h);
     if (!(fabs(d) >= U1) || !(U1 > T(0))) return T(0);
-    T B = T(1) - d / U1;
+    T B = T(1) - qdiv(d, U1);
     return B > T(0) ? B * h * fabs(d) : T(0);
 }
 
@@ -343,12 +344,12 @@ hyp_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ q1,
         const T sLh = minmod(sh[cl] - sh[cm], sh[cr] - sh[cl]);
         const T sLu = minmod(uL - un[cm], uR - uL);
         const T sLt = minmod(tL - ut[cm], tR - tL);
-        const bool dL = sh[cm] <= hdry || sh[cl] <= hdry || sh[cr] <= hdry;
+        const bool dL = (sh[cm] <= hdry) | (sh[cl] <= hdry) | (sh[cr] <= hdry);
         const T sLe = dL ? T(0) : minmod(se[cl] - se[cm], se[cr] - se[cl]);
         const T sRh = minmod(sh[cr] - sh[cl], sh[cp] - sh[cr]);
         const T sRu = minmod(uR - uL, un[cp] - uR);
         const T sRt = minmod(tR - tL, ut[cp] - tR);
-        const bool dR = sh[cl] <= hdry || sh[cr] <= hdry || sh[cp] <= hdry;
+        const bool dR = (sh[cl] <= hdry) | (sh[cr] <= hdry) | (sh[cp] <= hdry);
         const T sRe = dR ? T(0) : minmod(se[cr] - se[cl], se[cp] - se[cr]);
         const T hL = sh[cl] + T(0.5) * sLh, eL = se[cl] + T(0.5) * sLe;
         const T nL = uL + T(0.5) * sLu, tLv = tL + T(0.5) * sLt;
@@ -376,6 +377,8 @@ hyp_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ q1,
     }
     __syncthreads();
     int nclamp = 0;
+    const T rx = dt / P.dx, ry = dt / P.dy;
+    const T fric = dt * g * P.manning * P.manning;
     for (int t = tid; t < TX * TY; t += nt) {
         const int li = t % TX, lj = t / TX;
         const int gi = i0 + li, gj = j0 + lj;
@@ -384,7 +387,6 @@ hyp_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ q1,
         const int fn = (lj + 1) * TX + li, fs = lj * TX + li;   // y faces north / south
         const size_t c = (size_t)gj * P.nx + gi;
         const T Hc = H[c];
-        const T rx = dt / P.dx, ry = dt / P.dy;
         T en = eta[c] - rx * (CLx[0][fe] + CRx[0][fw]) - ry * (CLy[0][fn] + CRy[0][fs]);
         T an = q1[c] - rx * (CLx[1][fe] + CRx[1][fw]) - ry * (CLy[2][fn] + CRy[2][fs]);
         T bn = q2[c] - rx * (CLx[2][fe] + CRx[2][fw]) - ry * (CLy[1][fn] + CRy[1][fs]);
@@ -392,9 +394,18 @@ hyp_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ q1,
         if (P.manning > T(0) && hn > T(0)) {
             T u = desing(hn, an, d4), v = desing(hn, bn, d4);
             T hd = tmax(hn, P.delta);
-            T fr = T(1) + dt * g * P.manning * P.manning * sqrt(u * u + v * v) / (hd * cbrt(hd));
-            an /= fr;
-            bn /= fr;
+            if constexpr (sizeof(T) == 4) {
+                // FP32: hd^(-4/3) and 1 / fr from the hardware exp2 / log2 / reciprocal
+                // approximations (relative error ~1e-6 at hd = delta, inside the FP32 bar)
+                const float fr = 1.f + fric * qsqrt(u * u + v * v) * __powf(hd, -4.f / 3.f);
+                const float ifr = qdiv(1.f, fr);
+                an *= ifr;
+                bn *= ifr;
+            } else {
+                T fr = T(1) + fric * sqrt(u * u + v * v) / (hd * cbrt(hd));
+                an /= fr;
+                bn /= fr;
+            }
         }
         if (hn < T(0)) { en = -Hc; an = T(0); bn = T(0); ++nclamp; }
         if (a != T(0)) {
@@ -413,11 +424,10 @@ template <typename T>
 __device__ __forceinline__ void
 break_cell(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ q1,
            const T* __restrict__ q2, const T* __restrict__ H, T de, T* __restrict__ q1o,
-           T* __restrict__ q2o, long long idx)
+           T* __restrict__ q2o, int i, int j)
 {
     const T d2 = P.delta * P.delta, d4 = d2 * d2;
     {
-        const int i = (int)(idx % P.nx), j = (int)(idx / P.nx);
         // neighbours W, E, S, N with parity; velocities desingularised
         T qq[4], uu[4], HH[4];
         const int di[4] = {-1, 1, 0, 0}, dj[4] = {0, 0, -1, 1};
@@ -435,7 +445,7 @@ break_cell(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ q1,
             uu[k] = desing(h, qq[k], d4);
             HH[k] = H[m];
         }
-        const size_t c = (size_t)idx;
+        const size_t c = (size_t)j * P.nx + i;
         T h = tmax(eta[c] + H[c], T(0));
         const T i2x = T(1) / (T(2) * P.dx), i2y = T(1) / (T(2) * P.dy);
         T dq = (qq[1] - qq[0]) * i2x + (qq[3] - qq[2]) * i2y;
@@ -1332,7 +1342,7 @@ __device__ __forceinline__ void cheb_region_reg2(const Rows<float>& Rw, const fl
 // Last block of a pass: residual test (or criterion (32) on max |dx|), and the next K weights.
 __device__ __forceinline__ void cheb_finish(SolveCtl* ctl, const double (&acc)[2], int K)
 {
-    if (ctl->status == 5) {   // a block of the register form gave up waiting for its copies
+    if (ctl->status == 6) {   // a block of the register form gave up waiting for its copies
         ctl->done = 1;
         return;
     }

@@ -28,7 +28,8 @@ struct SolveCtl {
     int iter;         // iterations done in this solve
     int done;         // 1: stop (converged, cap reached or breakdown)
     int status;       // 0 running, 1 converged, 2 iteration cap, 3 breakdown, 4 Gershgorin
-                      // bound >= 1, 5 a register-form pass timed out waiting for its copies
+                      // bound >= 1, 5 stalled (batched form), 6 a register-form pass timed
+                      // out waiting for its copies
     int max_iter;
     double tol2;      // tol^2
     unsigned counter; // last-block-done ticket

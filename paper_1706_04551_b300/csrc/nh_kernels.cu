@@ -35,7 +35,11 @@ k_break2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ q1,
           const T* __restrict__ q2, const T* __restrict__ H, T de, T* __restrict__ q1o,
           T* __restrict__ q2o)
 {
-    GRID_STRIDE(idx, (long long)P.nx * P.ny) break_cell(P, eta, q1, q2, H, de, q1o, q2o, idx);
+    // one cell per thread of 32 x 8 block tiles (rows strided by the grid): no index division
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    if (i >= P.nx) return;
+    for (int j = blockIdx.y * 8 + threadIdx.y; j < P.ny; j += gridDim.y * 8)
+        break_cell(P, eta, q1, q2, H, de, q1o, q2o, i, j);
 }
 
 template <typename T, int TX, int TY>
@@ -222,7 +226,7 @@ k_cheb_pass2(Rows<T> R, const T* __restrict__ b, const T* __restrict__ xi,
 // Register form of the pass (cheb_region_reg): persistent blocks walk the regions
 // blockIdx.x, blockIdx.x + gridDim.x, ... (row-major over nrx columns of regions), each
 // prefetching its next region while it sweeps the current one.  A wait for a region's
-// copies gives up after kSpinLimit polls: the block then marks the solve failed (status 5)
+// copies gives up after kSpinLimit polls: the block then marks the solve failed (status 6)
 // and leaves the region walk.
 constexpr unsigned kSpinLimit = 1u << 22;
 
@@ -288,7 +292,7 @@ k_cheb_reg(Rows<T> Rw, const T* __restrict__ b, const T* __restrict__ xi,
         // the region's copies may still be in flight: give them one more bounded wait
         mbar_wait_bounded(&bar, phase, kSpinLimit);
         cp_async_wait_all();
-        if (tid == 0) { ctl->status = 5; ctl->done = 1; }
+        if (tid == 0) { ctl->status = 6; ctl->done = 1; }
     }
     double acc[2];
     if (dom_reduce_sum_max_f((float)rsum, (float)dmax, partials, &ctl->counter, acc, blockIdx.x,
@@ -713,7 +717,9 @@ template <typename T>
 void launch_break2d(const Prm<T>& P, const Launch& L, const T* eta, const T* q1, const T* q2,
                     const T* H, T de, T* q1o, T* q2o)
 {
-    k_break2d<T><<<L.nblk, kThreads, 0, L.s>>>(P, eta, q1, q2, H, de, q1o, q2o);
+    const int gy = (P.ny + 7) / 8;
+    const dim3 grid((P.nx + 31) / 32, gy < 65535 ? gy : 65535);
+    k_break2d<T><<<grid, dim3(32, 8), 0, L.s>>>(P, eta, q1, q2, H, de, q1o, q2o);
 }
 
 template <typename T>
