@@ -104,6 +104,9 @@ typedef struct {
     int fallbacks;         /* Chebyshev solves finished by BiCGStab (stalled, or a system
                               that is not diagonally dominant)                           */
     long long fallback_iters; /* BiCGStab iterations of those (part of solver_iters)     */
+    int cheb_form;         /* kernel form of the Chebyshev pass in use (nh_params.cheb_form,
+                              or the one chosen by timing); -1 while the forms are timed, or
+                              for a batch / a handle that does not run the Chebyshev solver */
 } nh_stats_t;
 
 typedef struct nh_handle nh_handle;

@@ -29,6 +29,7 @@ struct Base {
     virtual int step(double dt) = 0;
     virtual int lambda(double* lam) = 0;
     virtual int mass(double* m) = 0;
+    virtual int cheb_form() const = 0;   // pass form in use, -1 while timing
     virtual int debug_hyp(double dt, void* e, void* a, void* b, int where) = 0;
     virtual int debug_system(double dt, const void* x, void* rhs, void* mx, int where) = 0;
     virtual int profile_enable(int on) = 0;
@@ -746,6 +747,7 @@ struct Impl : Base {
     // choice between the two Chebyshev pass forms (shared-memory or register weights)
     static constexpr int kVT = 128;   // event slots: 64 timed passes
     int pass_variant = -1;
+    int cheb_form() const override { return pass_variant; }
     int vt_next = 0, vt_used = 0, solves = 0;
     int vt_var[kVT / 2] = {}, vt_pass[kVT / 2] = {}, vt_solve[kVT / 2] = {}, vt_ok[kVT / 2] = {};
     cudaEvent_t vt_ev[kVT] = {};
@@ -959,6 +961,8 @@ int nh_stats(nh_handle* h, nh_stats_t* out)
     out->nonfinite = h->nonfinite;
     out->fallbacks = h->fallbacks;
     out->fallback_iters = h->fallback_iters;
+    out->cheb_form =
+        h->prm.solver == NH_SOLVER_CHEBYSHEV && h->grid.dim == 2 ? h->impl->cheb_form() : -1;
     return h->impl->mass(&out->mass);
 }
 

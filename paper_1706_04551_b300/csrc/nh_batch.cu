@@ -1663,6 +1663,7 @@ struct BatchImpl : BatchBase {
         out->nonfinite = s.nonfinite;
         out->fallbacks = s.fallbacks;
         out->fallback_iters = s.bicg_iters;
+        out->cheb_form = -1;
         return NH_OK;
     }
 

@@ -41,7 +41,7 @@ class StatsT(C.Structure):
                 ("steps", C.c_longlong), ("solver_iters", C.c_longlong),
                 ("last_iters", C.c_int * 2), ("last_resid", C.c_double * 2),
                 ("mass", C.c_double), ("nonfinite", C.c_int), ("fallbacks", C.c_int),
-                ("fallback_iters", C.c_longlong)]
+                ("fallback_iters", C.c_longlong), ("cheb_form", C.c_int)]
 
 
 class BatchTuning(C.Structure):
@@ -265,7 +265,8 @@ class Sim:
         return dict(t=st.t, dt=st.dt, dt_next=st.dt_next, steps=st.steps,
                     solver_iters=st.solver_iters, last_iters=tuple(st.last_iters),
                     last_resid=tuple(st.last_resid), mass=st.mass, nonfinite=st.nonfinite,
-                    fallbacks=st.fallbacks, fallback_iters=st.fallback_iters)
+                    fallbacks=st.fallbacks, fallback_iters=st.fallback_iters,
+                    cheb_form=st.cheb_form)
 
     def profile(self, on=True):
         """Record CUDA events around every kernel launch (resets the counters)."""
@@ -439,7 +440,8 @@ class Batch:
         return dict(t=st.t, dt=st.dt, dt_next=st.dt_next, steps=st.steps,
                     solver_iters=st.solver_iters, last_iters=tuple(st.last_iters),
                     last_resid=tuple(st.last_resid), mass=st.mass, nonfinite=st.nonfinite,
-                    fallbacks=st.fallbacks, fallback_iters=st.fallback_iters)
+                    fallbacks=st.fallbacks, fallback_iters=st.fallback_iters,
+                    cheb_form=st.cheb_form)
 
     def profile(self, on=True):
         """Record CUDA events around every kernel launch (steps then run eagerly)."""
