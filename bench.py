@@ -31,8 +31,9 @@ UNIT = "Mcell-steps/s"
 # breaking on): reads of every input field once plus writes of every output field once.
 WORDS = {
     "hyperbolic": 8.5,    # eta q1 q2 H (+ base eta q1 q2 in stage 2) -> eta* q1* q2*
-    "breaking": 6.0,      # eta* q1* q2* H -> q1** q2**
-    "assembly": 14.5,     # eta* H q1** q2** q1* q2* w (+ w_base) -> w* 5 coefs rhs
+    "breaking": 6.0,      # (1D only) eta* q1* q2* H -> q1** q2**
+    "assembly": 15.5,     # eta* H q1* q2* w (+ w_base) p0 -> w* 5 coefs rhs q1** q2**
+                          # (breaking terms fused); without breaking 13.5 (q1** = q1*)
     "solve_init": 11.0,   # b x 5 coefs -> r rhat p^ v
     "bicg_A": 11.0,       # r rhat p^ v 5 coefs -> p^ v
     "bicg_B": 8.0,        # r v 5 coefs -> t
@@ -527,7 +528,10 @@ def main():
     nl, tms = prof[top]
     esize = 4 if prec == "fp32" else 8
     units = cells if top in ("hyperbolic", "breaking") else nn
-    algo_bytes = WORDS[top] * esize * units
+    words = dict(WORDS)
+    if not prm.get("breaking"):
+        words["assembly"] = 13.5
+    algo_bytes = words[top] * esize * units
     achieved = algo_bytes / (tms / nl / 1e3) / 1e9
     peak, peak_kind = peaks()
     traffic = None
@@ -546,9 +550,9 @@ def main():
     for k, (n_l, _) in prof.items():
         if n_l and k in WORDS:
             u = cells if k in ("hyperbolic", "breaking") else nn
-            algo_step += WORDS[k] * esize * u * n_l
+            algo_step += words[k] * esize * u * n_l
     sweeps_stage = iters / (2.0 * args.steps)
-    stencil_words = sum(WORDS[k] * prof[k][0] for k in ("hyperbolic", "breaking", "assembly",
+    stencil_words = sum(words[k] * prof[k][0] for k in ("hyperbolic", "breaking", "assembly",
                                                          "correction") if k in prof) / args.steps
     model_words = stencil_words + 2.0 * sweeps_stage * 5.0
     step_roof = {

@@ -501,15 +501,12 @@ struct Impl : Base {
             launch_hyp2d<T>(P, Lc, ein, ain, bin, B.eta, B.q1, B.q2, B.H, a, b, dt, B.etas,
                             B.q1s, B.q2s, B.stctl);
         });
-        if (q.breaking)
-            K_(NH_K_BREAKING, [&] {
-                launch_break2d<T>(P, Lc, B.etas, B.q1s, B.q2s, B.H, de, B.q1k, B.q2k);
-            });
+        // the breaking terms (q* -> q**) run inside the assembly
         K_(NH_K_ASSEMBLY, [&] {
             launch_asm2d<T>(P, Ln, B, win, B.w, a, b, de, q.nonhydrostatic ? 1 : 0,
                             q.nonhydrostatic ? 1 : 0, q.tol * q.tol, q.max_iter,
                             q.solver == NH_SOLVER_CHEBYSHEV ? cheb_sweeps_per_pass<T>() : 0,
-                            B.partials, B.sctl);
+                            B.partials, B.sctl, 1);
         });
         int rc = NH_OK;
         if (q.nonhydrostatic) rc = q.solver == NH_SOLVER_CHEBYSHEV ? solve_cheb(s) : solve2d(s, false);

@@ -136,34 +136,16 @@ kb_hyp(Arena<T> A, const int2* __restrict__ wl, int nw, const T* eta, const T* q
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-kb_break(Arena<T> A, const int2* __restrict__ wl, int nw, const T* eta, const T* q1,
-         const T* q2, const T* H, T bfac, T* q1o, T* q2o)
-{
-    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
-        const int2 it = wl[w];
-        const Dom<T>& D = A.dom[it.x];
-        const Prm<T> P = D.P;
-        const long long c = D.coff, n = (long long)P.nx * P.ny;
-        const T de = bfac * (T)A.ds[it.x].dt;
-        for (long long k = (long long)it.y * kChunk + threadIdx.x;
-             k < n && k < (long long)(it.y + 1) * kChunk; k += blockDim.x) {
-            const int kk = (int)k, j = kk / P.nx;   // a domain holds < 2^31 cells
-            break_cell(P, eta + c, q1 + c, q2 + c, H + c, de, q1o + c, q2o + c, kk - j * P.nx, j);
-        }
-    }
-}
-
 struct AsmArgs {
     double tol2;
     int max_iter, kpass, with_coef, stage;
+    int fuse;   // breaking terms inside the assembly (q* -> q** into q1k / q2k)
 };
 
 template <typename T, int TX, int TY>
 __global__ void __launch_bounds__(256, 3)
 kb_asm(Arena<T> A, const int2* __restrict__ wl, int nw, const T* eta, const T* H,
-       const T* q1k, const T* q2k, const T* q1s, const T* q2s, const T* w_in, const T* w_b,
+       T* q1k, T* q2k, const T* q1s, const T* q2s, const T* w_in, const T* w_b,
        T a, T b, T* ws, T* cC, T* cW, T* cE, T* cS, T* cN, T* rhs, const T* p0, AsmArgs G)
 {
     for (int w = blockIdx.x; w < nw; w += gridDim.x) {
@@ -174,10 +156,13 @@ kb_asm(Arena<T> A, const int2* __restrict__ wl, int nw, const T* eta, const T* H
         const T de = b * (T)A.ds[it.x].dt;
         const int tx = cdiv(P.nx + 1, TX), nt = tx * cdiv(P.ny + 1, TY);
         double acc[3] = {0.0, 0.0, 0.0};
-        asm_tile<T, TX, TY>(P, eta + c, H + c, q1k + c, q2k + c, q1s + c, q2s + c, w_in + n,
-                            w_b + n, a, b, de, G.with_coef, ws + n, cC + n, cW + n, cE + n,
-                            cS + n, cN + n, rhs + n, p0 + n, /*resid_form=*/G.with_coef, it.y % tx,
-                            it.y / tx, acc);
+        // fused breaking: q** is computed in the tile and written to q1k / q2k (not read)
+        const bool fuse = G.fuse && P.breaking;
+        asm_tile<T, TX, TY>(P, eta + c, H + c, fuse ? nullptr : q1k + c, fuse ? nullptr : q2k + c,
+                            q1s + c, q2s + c, w_in + n, w_b + n, a, b, de, G.with_coef, ws + n,
+                            cC + n, cW + n, cE + n, cS + n, cN + n, rhs + n, p0 + n,
+                            /*resid_form=*/G.with_coef, it.y % tx, it.y / tx, acc,
+                            fuse ? q1k + c : nullptr, fuse ? q2k + c : nullptr);
         SolveCtl* ctl = &A.sctl[it.x];
         if (dom_reduce<3, 4u>(acc, A.partials + D.poff, &ctl->counter, it.y, nt) &&
             threadIdx.x == 0) {
@@ -672,7 +657,7 @@ using HypFn = void (*)(int grid, cudaStream_t, const Arena<T>&, const int2*, int
                        T*);
 template <typename T>
 using AsmFn = void (*)(int grid, cudaStream_t, const Arena<T>&, const int2*, int, const T*,
-                       const T*, const T*, const T*, const T*, const T*, const T*, const T*, T, T,
+                       const T*, T*, T*, const T*, const T*, const T*, const T*, T, T,
                        T*, T*, T*, T*, T*, T*, T*, const T*, AsmArgs);
 template <typename T>
 using ChebFn = void (*)(int grid, cudaStream_t, const Arena<T>&, const int2*, int, const T*,
@@ -689,7 +674,7 @@ void run_hyp(int grid, cudaStream_t s, const Arena<T>& A, const int2* wl, int nw
 
 template <typename T, int TX, int TY>
 void run_asm(int grid, cudaStream_t s, const Arena<T>& A, const int2* wl, int nw, const T* e,
-             const T* H, const T* q1k, const T* q2k, const T* q1s, const T* q2s, const T* win,
+             const T* H, T* q1k, T* q2k, const T* q1s, const T* q2s, const T* win,
              const T* wb, T a, T b, T* ws, T* cC, T* cW, T* cE, T* cS, T* cN, T* rhs,
              const T* p0, AsmArgs G)
 {
@@ -1234,6 +1219,7 @@ struct BatchImpl : BatchBase {
         G.kpass = ChebK<T>::value;
         G.with_coef = q.nonhydrostatic ? 1 : 0;
         G.stage = s;
+        G.fuse = 1;
         const Shape sh = C::asm_shape(cand);
         C::assembly(cand)(grid_of(C::asm_kernel(cand), sh.threads, 0, nw_asm[cand], persistent),
                           hb->s, arena(), wl_asm[cand], nw_asm[cand], B.etas, B.H, B.q1k, B.q2k,
@@ -1315,13 +1301,7 @@ struct BatchImpl : BatchBase {
     {
         const nh_params& q = hb->prm;
         K_(NH_K_HYPERBOLIC, hb->s, [&] { hyp(s, tun.hyp, pers(0)); });
-        if (q.breaking) {
-            const T b = s == 0 ? T(1) : T(0.5);
-            K_(NH_K_BREAKING, hb->s, [&] {
-                kb_break<T><<<grid_of((const void*)kb_break<T>, kThreads, 0, nw_cell, pers(3)), kThreads, 0, hb->s>>>(
-                    arena(), wl_cell, nw_cell, B.etas, B.q1s, B.q2s, B.H, b, B.q1k, B.q2k);
-            });
-        }
+        // the breaking terms (q* -> q**) run inside the assembly
         cudaMemsetAsync(d_loop, 0, 8 * sizeof(unsigned), hb->s);
         if (q.nonhydrostatic) cudaMemsetAsync(B.dp, 0, nnode * sizeof(T), hb->s);
         K_(NH_K_ASSEMBLY, hb->s, [&] { assembly(s, tun.assembly, pers(1)); });
@@ -1498,9 +1478,6 @@ struct BatchImpl : BatchBase {
             }
         tun.ms[0] = best;
         hyp(0, tun.hyp, pers(0));
-        if (hb->prm.breaking)
-            kb_break<T><<<nw_cell, kThreads, 0, s>>>(arena(), wl_cell, nw_cell, B.etas, B.q1s,
-                                                    B.q2s, B.H, T(1), B.q1k, B.q2k);
         best = 1e30f;
         for (int k = 0; k < C::na; ++k)
             for (int p = 0; p < 2; ++p) {

@@ -418,45 +418,32 @@ hyp_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ q1,
     return nclamp;
 }
 
-// Breaking terms at cells (Sec. 3 with q_x -> div q, u_x -> div u):
-// q += de 2 nu (div u) grad H, centred differences.
+// Breaking terms at a cell (Sec. 3 with q_x -> div q, u_x -> div u): q** = q* + de 2 nu
+// (div u) grad H, centred differences, velocities desingularised, nu of Eq. (9) -- for the
+// staged cell sm of a tile whose staged q* (mirror / copy ghosts with the side's parity),
+// h and H (row stride SW) hold the cell and its four neighbours.
 template <typename T>
-__device__ __forceinline__ void
-break_cell(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ q1,
-           const T* __restrict__ q2, const T* __restrict__ H, T de, T* __restrict__ q1o,
-           T* __restrict__ q2o, int i, int j)
+__device__ __forceinline__ void break_staged(const Prm<T>& P, const T* sq1, const T* sq2,
+                                             const T* hs, const T* sHH, int sm, int SW, T de,
+                                             T d4, T& q1o, T& q2o)
 {
-    const T d2 = P.delta * P.delta, d4 = d2 * d2;
-    {
-        // neighbours W, E, S, N with parity; velocities desingularised
-        T qq[4], uu[4], HH[4];
-        const int di[4] = {-1, 1, 0, 0}, dj[4] = {0, 0, -1, 1};
+    const int nb[4] = {sm - 1, sm + 1, sm - SW, sm + SW};   // W, E, S, N
+    T qq[4], uu[4], HH[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            bool rx, ry;
-            int ii = map_cell(i + di[k], P.nx, P.bcw, P.bce, rx);
-            int jj = map_cell(j + dj[k], P.ny, P.bcs, P.bcn, ry);
-            size_t m = (size_t)jj * P.nx + ii;
-            T h = tmax(eta[m] + H[m], T(0));
-            T a = q1[m], b = q2[m];
-            if (rx) a = -a;
-            if (ry) b = -b;
-            qq[k] = k < 2 ? a : b;
-            uu[k] = desing(h, qq[k], d4);
-            HH[k] = H[m];
-        }
-        const size_t c = (size_t)j * P.nx + i;
-        T h = tmax(eta[c] + H[c], T(0));
-        const T i2x = T(1) / (T(2) * P.dx), i2y = T(1) / (T(2) * P.dy);
-        T dq = (qq[1] - qq[0]) * i2x + (qq[3] - qq[2]) * i2y;
-        T du = (uu[1] - uu[0]) * i2x + (uu[3] - uu[2]) * i2y;
-        T Hx = (HH[1] - HH[0]) * i2x, Hy = (HH[3] - HH[2]) * i2y;
-        T nu = nu_break(h, dq, P.g, P.B1, P.hdry);
-        q1o[c] = q1[c] + de * T(2) * nu * du * Hx;
-        q2o[c] = q2[c] + de * T(2) * nu * du * Hy;
+    for (int k = 0; k < 4; ++k) {
+        qq[k] = k < 2 ? sq1[nb[k]] : sq2[nb[k]];
+        uu[k] = desing(hs[nb[k]], qq[k], d4);
+        HH[k] = sHH[nb[k]];
     }
+    const T h = hs[sm];
+    const T i2x = T(1) / (T(2) * P.dx), i2y = T(1) / (T(2) * P.dy);
+    T dq = (qq[1] - qq[0]) * i2x + (qq[3] - qq[2]) * i2y;
+    T du = (uu[1] - uu[0]) * i2x + (uu[3] - uu[2]) * i2y;
+    T Hx = (HH[1] - HH[0]) * i2x, Hy = (HH[3] - HH[2]) * i2y;
+    T nu = nu_break(h, dq, P.g, P.B1, P.hdry);
+    q1o = sq1[sm] + de * T(2) * nu * du * Hx;
+    q2o = sq2[sm] + de * T(2) * nu * du * Hy;
 }
-
 // Tiled form of the assembly for a TX x TY node tile: the block stages s = eta - H and h of
 // the cells around the tile (a 2-cell ring), computes the centred differences X, Y of every
 // cell once, stages the discharges of the cells touching the tile's nodes, and then builds
@@ -471,13 +458,17 @@ asm_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
           T a, T b, T de, int with_coef, T* __restrict__ ws, T* __restrict__ cC,
           T* __restrict__ cW, T* __restrict__ cE, T* __restrict__ cS, T* __restrict__ cN,
           T* __restrict__ rhs, const T* __restrict__ p0, int resid_form, int bx, int by,
-          double (&acc)[3])
+          double (&acc)[3], T* __restrict__ q1k_out = nullptr, T* __restrict__ q2k_out = nullptr)
 {
     // staged cells: columns I0-2 .. I0+TX, rows J0-2 .. J0+TY  (SW x SH)
     constexpr int SW = TX + 3, SH = TY + 3, SN = SW * SH;
     // core cells (touching the tile's nodes): columns I0-1 .. I0+TX-1, rows J0-1 .. J0+TY-1
     constexpr int CW = TX + 1, CHh = TY + 1, CN = CW * CHh;
     __shared__ T ss[SN], hs[SN];
+    // fused breaking (q1k_out set): q*, H of the staged cells; the core cells' q** are
+    // computed here (break_staged) and the tile's own cells written to q1k_out / q2k_out
+    const bool fuse = P.breaking && q1k_out != nullptr;
+    __shared__ T sq1[SN], sq2[SN], sHH[SN];
     __shared__ T Xc[CN], Yc[CN], Q1c[CN], Q2c[CN], U1c[CN], V1c[CN], P1c[CN], P2c[CN];
     // previous pressure of the tile's nodes and a 1-node ring (residual form)
     constexpr int PW = TX + 2, PN = PW * (TY + 2);
@@ -498,7 +489,13 @@ asm_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
         const T e = eta[m], Hm = H[m];
         ss[t] = e - Hm;
         hs[t] = tmax(e + Hm, T(0));
+        if (fuse) {
+            sHH[t] = Hm;
+            sq1[t] = rx ? -q1s[m] : q1s[m];
+            sq2[t] = ry ? -q2s[m] : q2s[m];
+        }
     }
+    if (!fuse)
     for (int t = tid; t < CN; t += nt) {
         const int li = t % CW, lj = t / CW;
         int ci = I0 - 1 + li, cj = J0 - 1 + lj;
@@ -528,6 +525,27 @@ asm_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
         const int sidx = (lj + 1) * SW + (li + 1);   // staged index of this core cell
         Xc[t] = T(0.5) * (ss[sidx + 1] - ss[sidx - 1]);
         Yc[t] = T(0.5) * (ss[sidx + SW] - ss[sidx - SW]);
+        if (fuse) {
+            P1c[t] = sq1[sidx];
+            P2c[t] = sq2[sidx];
+            const int ci = I0 - 1 + li, cj = J0 - 1 + lj;
+            T b1 = T(0), b2 = T(0);
+            bool rx = false, ry = false;
+            if (ci <= P.nx && cj <= P.ny) {   // cells beyond the first ghost feed no node
+                // a ghost cell holds its real cell's q** under the side's mirror / copy
+                const int mi = map_cell(ci, P.nx, P.bcw, P.bce, rx);
+                const int mj = map_cell(cj, P.ny, P.bcs, P.bcn, ry);
+                const int sm = (mj - (J0 - 2)) * SW + (mi - (I0 - 2));
+                break_staged(P, sq1, sq2, hs, sHH, sm, SW, de, d4, b1, b2);
+                if (li >= 1 && lj >= 1 && ci < P.nx && cj < P.ny) {   // this tile's own cells
+                    const size_t c = (size_t)cj * P.nx + ci;
+                    q1k_out[c] = b1;
+                    q2k_out[c] = b2;
+                }
+            }
+            Q1c[t] = rx ? -b1 : b1;
+            Q2c[t] = ry ? -b2 : b2;
+        }
         if (P.breaking) {
             U1c[t] = desing(hs[sidx], P1c[t], d4);
             V1c[t] = desing(hs[sidx], P2c[t], d4);

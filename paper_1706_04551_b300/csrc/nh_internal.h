@@ -92,12 +92,11 @@ void launch_hyp2d(const Prm<T>& P, const Launch& L, const T* eta, const T* q1, c
                   const T* etab, const T* q1b, const T* q2b, const T* H, T a, T b, T dt,
                   T* eo, T* q1o, T* q2o, StepCtl* st);
 template <typename T>
-void launch_break2d(const Prm<T>& P, const Launch& L, const T* eta, const T* q1, const T* q2,
-                    const T* H, T de, T* q1o, T* q2o);
-template <typename T>
 void launch_asm2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* w_in,
                   const T* w_base, T a, T b, T de, int with_coef, int resid_form, double tol2,
-                  int max_iter, int kpass, double* partials, SolveCtl* ctl);
+                  int max_iter, int kpass, double* partials, SolveCtl* ctl, int fuse_break = 0);
+// fuse_break (with breaking on): the breaking terms are computed inside the assembly from
+// B.q1s / B.q2s, and q** is written to B.q1k / B.q2k (no separate breaking launch)
 // Chebyshev-scheduled Jacobi: sweeps per launch, number of tiles (blocks), one launch.
 template <typename T>
 int cheb_sweeps_per_pass();

@@ -29,19 +29,6 @@ k_hyp2d_t(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ q1,
     if (nclamp) atomicAdd(&st->clamped, nclamp);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_break2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ q1,
-          const T* __restrict__ q2, const T* __restrict__ H, T de, T* __restrict__ q1o,
-          T* __restrict__ q2o)
-{
-    // one cell per thread of 32 x 8 block tiles (rows strided by the grid): no index division
-    const int i = blockIdx.x * 32 + threadIdx.x;
-    if (i >= P.nx) return;
-    for (int j = blockIdx.y * 8 + threadIdx.y; j < P.ny; j += gridDim.y * 8)
-        break_cell(P, eta, q1, q2, H, de, q1o, q2o, i, j);
-}
-
 template <typename T, int TX, int TY>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 1)
 k_asm2d_t(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
@@ -50,12 +37,14 @@ k_asm2d_t(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
           T a, T b, T de, int with_coef, T* __restrict__ ws, T* __restrict__ cC,
           T* __restrict__ cW, T* __restrict__ cE, T* __restrict__ cS, T* __restrict__ cN,
           T* __restrict__ rhs, const T* __restrict__ p0, int resid_form, double* partials,
-          SolveCtl* ctl, double tol2, int max_iter, int kpass, int ntx, int ntiles)
+          SolveCtl* ctl, double tol2, int max_iter, int kpass, int ntx, int ntiles,
+          T* __restrict__ q1k_out, T* __restrict__ q2k_out)
 {
     double acc[3] = {0.0, 0.0, 0.0};
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         asm_tile<T, TX, TY>(P, eta, H, q1k, q2k, q1s, q2s, w_in, w_b, a, b, de, with_coef, ws, cC,
-                            cW, cE, cS, cN, rhs, p0, resid_form, t % ntx, t / ntx, acc);
+                            cW, cE, cS, cN, rhs, p0, resid_form, t % ntx, t / ntx, acc, q1k_out,
+                            q2k_out);
         __syncthreads();   // the tile's shared arrays are restaged by the next tile
     }
     if (grid_reduce<3, 4u>(acc, partials, &ctl->counter) && threadIdx.x == 0)
@@ -714,26 +703,19 @@ void launch_hyp2d(const Prm<T>& P, const Launch& L, const T* eta, const T* q1, c
 }
 
 template <typename T>
-void launch_break2d(const Prm<T>& P, const Launch& L, const T* eta, const T* q1, const T* q2,
-                    const T* H, T de, T* q1o, T* q2o)
-{
-    const int gy = (P.ny + 7) / 8;
-    const dim3 grid((P.nx + 31) / 32, gy < 65535 ? gy : 65535);
-    k_break2d<T><<<grid, dim3(32, 8), 0, L.s>>>(P, eta, q1, q2, H, de, q1o, q2o);
-}
-
-template <typename T>
 void launch_asm2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* w_in,
                   const T* w_base, T a, T b, T de, int with_coef, int resid_form, double tol2,
-                  int max_iter, int kpass, double* partials, SolveCtl* ctl)
+                  int max_iter, int kpass, double* partials, SolveCtl* ctl, int fuse_break)
 {
     constexpr int TX = 32, TY = sizeof(T) == 4 ? 16 : 8;   // FP64: static shared memory < 48 KB
     static const int res = resident_grid(k_asm2d_t<T, TX, TY>, kThreads, 0);
     const int ntx = (P.nx + 1 + TX - 1) / TX, ntiles = ntx * ((P.ny + 1 + TY - 1) / TY);
+    // fused breaking: q** is computed from q* and written to B.q1k / B.q2k (not read)
+    const bool fuse = fuse_break && P.breaking;
     k_asm2d_t<T, TX, TY><<<ntiles < res ? ntiles : res, kThreads, 0, L.s>>>(
-        P, B.etas, B.H, B.q1k, B.q2k, B.q1s, B.q2s, w_in, w_base, a, b, de, with_coef, B.ws, B.cC,
-        B.cW, B.cE, B.cS, B.cN, B.rhs, B.p, resid_form, partials, ctl, tol2, max_iter, kpass, ntx,
-        ntiles);
+        P, B.etas, B.H, fuse ? nullptr : B.q1k, fuse ? nullptr : B.q2k, B.q1s, B.q2s, w_in, w_base,
+        a, b, de, with_coef, B.ws, B.cC, B.cW, B.cE, B.cS, B.cN, B.rhs, B.p, resid_form, partials,
+        ctl, tol2, max_iter, kpass, ntx, ntiles, fuse ? B.q1k : nullptr, fuse ? B.q2k : nullptr);
 }
 
 // Sweeps per Chebyshev pass: 8 in FP32, 4 in FP64 (the forms below).
@@ -1013,11 +995,9 @@ void launch_convert_from_double(const Launch& L, const double* src, T* dst, size
     template void launch_hyp2d<T>(const Prm<T>&, const Launch&, const T*, const T*, const T*,  \
                                   const T*, const T*, const T*, const T*, T, T, T, T*, T*, T*, \
                                   StepCtl*);                                                   \
-    template void launch_break2d<T>(const Prm<T>&, const Launch&, const T*, const T*, const T*,\
-                                    const T*, T, T*, T*);                                      \
     template void launch_asm2d<T>(const Prm<T>&, const Launch&, const Bufs<T>&, const T*,      \
                                   const T*, T, T, T, int, int, double, int, int, double*,      \
-                                  SolveCtl*);                                                  \
+                                  SolveCtl*, int);                                             \
     template int cheb_sweeps_per_pass<T>();                                                    \
     template size_t cheb_tiles<T>(const Prm<T>&);                                              \
     template size_t asm_tiles<T>(const Prm<T>&);                                               \
