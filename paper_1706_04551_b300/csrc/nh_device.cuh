@@ -19,6 +19,7 @@ namespace nh {
 namespace dev {
 
 constexpr int kThreads = 256;
+constexpr int kCorrThreads = 256;   // threads of a correction tile block
 
 template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
 template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
@@ -1483,6 +1484,23 @@ corr_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
     const int nx = P.nx, ny = P.ny, nxn = nx + 1;
     const int I0 = bx * TX, J0 = by * TY;
     const int tid = threadIdx.x, nt = blockDim.x;
+    // the thread's own node / cell operands (node t = tid + k nt), loaded before the staging
+    // so that their latency overlaps it (nt = kCorrThreads)
+    constexpr int NPT = (TX * TY + kCorrThreads - 1) / kCorrThreads;
+    T wsv[NPT], a1v[NPT], a2v[NPT];
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int t = tid + k * kCorrThreads;
+        const int I = I0 + t % TX, J = J0 + t / TX;
+        wsv[k] = a1v[k] = a2v[k] = T(0);
+        if (t < TX * TY && I <= nx && J <= ny) {
+            wsv[k] = ws[(size_t)J * nxn + I];
+            if (I < nx && J < ny) {
+                a1v[k] = q1k[(size_t)J * nx + I];
+                a2v[k] = q2k[(size_t)J * nx + I];
+            }
+        }
+    }
     for (int t = tid; t < CN; t += nt) {
         const int li = t % CW, lj = t / CW;
         int ci = I0 - 1 + li, cj = J0 - 1 + lj;
@@ -1502,10 +1520,13 @@ corr_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
             pn[t] = p[m] + dp[m];
         }
     __syncthreads();
-    for (int t = tid; t < TX * TY; t += nt) {
+    const T idx_ = T(1) / P.dx, idy_ = T(1) / P.dy;
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+        const int t = tid + k * kCorrThreads;
         const int li = t % TX, lj = t / TX;
         const int I = I0 + li, J = J0 + lj;
-        if (I > nx || J > ny) continue;
+        if (t >= TX * TY || I > nx || J > ny) continue;
         const size_t nidx = (size_t)J * nxn + I;
         const int ca = lj * CW + li;   // staged cell (I-1, J-1); b = ca + 1, d = ca + CW, e = d + 1
         // node
@@ -1516,12 +1537,12 @@ corr_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
                          tmax(se[ca + CW] + sH[ca + CW], T(0)) +
                          tmax(se[ca + CW + 1] + sH[ca + CW + 1], T(0));
             const T hc = T(0.25) * hs;
-            const T wn = ws[nidx] + de * pc * desing(hc, T(1), d4);
+            const T wn = wsv[k] + de * pc * desing(hc, T(1), d4);
             wo[nidx] = wn;
             pout[nidx] = pc;
             if (!isfinite(wn) || !isfinite(pc)) bad = 1;
         } else {
-            wo[nidx] = ws[nidx];
+            wo[nidx] = wsv[k];
             pout[nidx] = T(0);
         }
         // cell (i, j) = (I, J)
@@ -1530,14 +1551,13 @@ corr_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
             const int ce = ca + CW + 1;   // staged cell (I, J)
             const T e = se[ce], Hc = sH[ce];
             const T h = tmax(e + Hc, T(0));
-            T a1 = q1k[c], a2 = q2k[c];
+            T a1 = a1v[k], a2 = a2v[k];
             if (with_p) {
                 const T X = T(0.5) * ((se[ce + 1] - sH[ce + 1]) - (se[ce - 1] - sH[ce - 1]));
                 const T Y = T(0.5) * ((se[ce + CW] - sH[ce + CW]) - (se[ce - CW] - sH[ce - CW]));
                 const int nsw = lj * NW + li;
                 const T pSW = pn[nsw], pSE = pn[nsw + 1];
                 const T pNW = pn[nsw + NW], pNE = pn[nsw + NW + 1];
-                const T idx_ = T(1) / P.dx, idy_ = T(1) / P.dy;
                 const T TN = (-T(0.5) * h * (pNE - pNW) - T(0.25) * (pNE + pNW) * X) * idx_;
                 const T TS = (-T(0.5) * h * (pSE - pSW) - T(0.25) * (pSE + pSW) * X) * idx_;
                 const T TE = (-T(0.5) * h * (pNE - pSE) - T(0.25) * (pNE + pSE) * Y) * idy_;
