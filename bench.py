@@ -116,6 +116,13 @@ def workload(name):
         desc = ("island_2d 4096x4096 dx=0.05 m FP32: conical island with dry top, solitary "
                 "wave A=0.064 m, wet/dry + breaking + Manning n=0.015, outflow BCs")
         return wl, prm, "fp32", desc
+    if name == "island_4096_fp64":
+        wl = inputs.island_2d(n=4096)
+        prm = dict(manning_n=0.015, breaking=1, B1=0.15, B2=0.5, cfl=0.9, tol=1e-10)
+        desc = ("island_2d 4096x4096 dx=0.05 m, plain FP64 (the FP32 default's comparison): "
+                "conical island with dry top, solitary wave A=0.064 m, wet/dry + breaking + "
+                "Manning n=0.015, outflow BCs, solver tol 1e-10")
+        return wl, prm, "fp64", desc
     if name == "island_2048":
         wl = inputs.island_2d(n=2048, L=102.4)
         prm = dict(manning_n=0.015, breaking=1, B1=0.15, B2=0.5, cfl=0.9, tol=1e-5)
@@ -311,6 +318,70 @@ def run_adjoint(args, torch, ws, rank, local, dist):
         print(json.dumps(line), flush=True)
 
 
+# Sec. 7.7, Table 2 of the paper: seconds to t = 1 of its FP64 CUDA codes on one GTX Titan
+# Black (SWE; NH with criterion (32) at eps = 1e-3, 1e-4, 1e-5) -- other hardware, context
+PAPER_TABLE2 = {250: (0.64, 0.64, 1.88, 3.47), 500: (2.29, 5.79, 8.44, 33.54),
+                750: (7.17, 17.33, 25.78, 99.58), 1000: (16.75, 40.47, 57.23, 198.91),
+                1250: (33.88, 79.67, 143.19, 381.89), 1500: (56.38, 136.12, 243.86, 662.51)}
+DAMBREAK_MODES = (("swe", dict(nonhydrostatic=0)), ("nh_eps1e-3", dict(eps_dp=1e-3)),
+                  ("nh_eps1e-4", dict(eps_dp=1e-4)), ("nh_eps1e-5", dict(eps_dp=1e-5)))
+
+
+def run_dambreak(args, torch, ws, rank, local, dist):
+    """Circular dam-break of Sec. 7.7 in FP64 to t = 1 (CFL 0.9, open boundaries): the SWE
+    step (non-hydrostatic part off) and the NH step stopped by criterion (32) at three eps,
+    on the n^2 meshes of Table 2 (`--workload dambreak`) or one of them (`dambreak_<n>`).
+    value = NH (eps = 1e-3) Mcell-steps/s on the largest mesh run."""
+    from paper_1706_04551_b300 import inputs, nh
+    sizes = ((250, 500, 750, 1000, 1250, 1500) if args.workload == "dambreak"
+             else (int(args.workload.split("_")[1]),))
+    stream = torch.cuda.current_stream()
+    table = {}
+    with Clocks(local) as clk:
+        for n in sizes:
+            wl = inputs.dambreak_2d(n)
+            row = {}
+            for name, kw in DAMBREAK_MODES:
+                sim = nh.Sim(wl.H, wl.dx, wl.dy, bc=wl.bc, precision="fp64", stream=stream,
+                             cfl=0.9, tol=1e-12, max_iter=200000, **kw)
+                sim.set_state(wl.eta, wl.q1, wl.q2)
+                sim.step()   # first launches and the pass-form timing stay out of the run
+                sim.set_state(wl.eta, wl.q1, wl.q2, t=0.0)
+                it0 = sim.stats()["solver_iters"]
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                ev0.record(stream)
+                steps = sim.run(t_end=1.0)
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                sec = ev0.elapsed_time(ev1) / 1e3
+                st = sim.stats()
+                sim.close()
+                k = DAMBREAK_MODES.index((name, kw))
+                row[name] = {"seconds": sec, "steps": steps,
+                             "sweeps_per_stage": (st["solver_iters"] - it0) / max(2 * steps, 1),
+                             "mcell_steps_per_s": n * n * steps / sec / 1e6,
+                             "paper_seconds_titan_black": PAPER_TABLE2.get(n, (None,) * 4)[k]}
+            for name, _ in DAMBREAK_MODES[1:]:
+                row[name]["nh_over_swe"] = row[name]["seconds"] / row["swe"]["seconds"]
+            table[str(n)] = row
+    last = table[str(sizes[-1])]["nh_eps1e-3"]
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": last["mcell_steps_per_s"], "unit": UNIT, "n_gpus": ws,
+            "steps": last["steps"], "warmup": 1, "ms_per_step": 1e3 * last["seconds"] / last["steps"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"circular dam-break (Sec. 7.7) FP64 {sizes[-1]}^2 to t = 1, "
+                                   "CFL 0.9, open boundaries; NH solve stopped by criterion "
+                                   "(32) at eps = 1e-3", "meshes": list(sizes),
+                       "parallelism": "replicas only"},
+            "table2": table,
+            "roofline": None, "e2e": None, "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+
+
 def run_ensemble(args, torch, ws, rank, local, dist):
     """Batched form: 256 uneven domains advanced together (graph + autotuned shapes)."""
     from paper_1706_04551_b300 import inputs, nh
@@ -456,9 +527,10 @@ def main():
     from paper_1706_04551_b300 import build as nhbuild
     from paper_1706_04551_b300 import nh
     nhbuild.build()
-    if args.workload in ("ensemble_256", "adjoint_512"):
-        (run_ensemble if args.workload == "ensemble_256" else run_adjoint)(
-            args, torch, ws, rank, local, dist)
+    if args.workload in ("ensemble_256", "adjoint_512") or args.workload.startswith("dambreak"):
+        run = {"ensemble_256": run_ensemble, "adjoint_512": run_adjoint}.get(args.workload,
+                                                                             run_dambreak)
+        run(args, torch, ws, rank, local, dist)
         if dist:
             dist.destroy_process_group()
         return

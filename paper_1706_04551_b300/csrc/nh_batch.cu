@@ -605,7 +605,7 @@ kb_bicg_C(Arena<T> A, const int2* __restrict__ wl, const int* __restrict__ nwp, 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 2)
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 2)
 kb_corr(Arena<T> A, const int2* __restrict__ wl, int nw, const T* eta, const T* H,
         const T* q1k, const T* q2k, const T* ws, const T* p, const T* dp, T* pout, T bfac,
         int with_p, T* eo, T* q1o, T* q2o, T* wo, int final_stage)

@@ -190,3 +190,18 @@ def adjoint_2d(n: int = 512, dx: float = 0.1, seed: int = 5, target_seed: int = 
     return Workload("adjoint_2d", n, n, dx, dx, H, eta, z, z.copy(),
                     params=dict(g=G, cfl=0.9),
                     extra=dict(H_target=H_target, gauges=gauges))
+
+
+def dambreak_2d(n: int = 1000, L: float = 10.0) -> Workload:
+    """Circular dam-break of Sec. 7.7: [-L/2, L/2]^2, H = 1 - 0.25 exp(-x^2 - y^2), h0 = H
+    for r <= 0.5 and H + 0.25 outside (eta0 = 0 inside, 0.25 outside), q = 0, open
+    (outflow) boundaries; the paper runs t in [0, 1] at CFL 0.9 on n^2 meshes, n from 250
+    to 1500."""
+    dx = L / n
+    x = (np.arange(n) + 0.5) * dx - L / 2
+    X, Y = np.meshgrid(x, x)
+    H = 1.0 - 0.25 * np.exp(-X * X - Y * Y)
+    eta = np.where(np.sqrt(X * X + Y * Y) <= 0.5, 0.0, 0.25)
+    z = np.zeros((n, n))
+    return Workload("dambreak_2d", n, n, dx, dx, H, eta, z, z.copy(), bc=(1, 1, 1, 1),
+                    params=dict(g=G, cfl=0.9, t_end=1.0))

@@ -170,6 +170,44 @@ def test_lake_at_rest_exact_both_precisions():
         assert not g["q1"].any() and not g["q2"].any() and not g["p"].any()
 
 
+def _island_full_size(bc=None):
+    """The 4096^2 island workload in the bench's launch configuration (FP32, Chebyshev
+    passes in the form the timing chooser picks, tol 1e-5, Manning and breaking on)."""
+    wl = inputs.island_2d()
+    prm = dict(manning_n=0.015, breaking=1, tol=1e-5)
+    sim = nh.Sim(wl.H, wl.dx, wl.dy, bc=wl.bc if bc is None else bc, precision="fp32", **prm)
+    return wl, sim
+
+
+def test_full_size_island_lake_at_rest_fp32():
+    """Lake at rest over the full 4096^2 wet/dry island bathymetry stays exact (any size)."""
+    wl, sim = _island_full_size()
+    eta0 = np.where(wl.H > 0, 0.0, -wl.H).astype(np.float32)
+    z = np.zeros_like(eta0)
+    sim.set_state(eta0, z, z)
+    for _ in range(6):
+        sim.step()
+    g = sim.get_state()
+    sim.close()
+    assert np.array_equal(g["eta"], eta0)
+    assert not g["q1"].any() and not g["q2"].any() and not g["p"].any()
+
+
+def test_full_size_island_mass_with_walls_fp32():
+    """The full 4096^2 island wave (wet/dry, breaking, friction) between walls conserves
+    mass to FP32 rounding (the FP64 device sum of h over 16.8 M cells) over 12 steps, and
+    the pass form the chooser settled on is reported."""
+    wl, sim = _island_full_size(bc=(nh.WALL,) * 4)
+    sim.set_state(wl.eta.astype(np.float32), wl.q1.astype(np.float32), wl.q2.astype(np.float32))
+    m0 = sim.stats()["mass"]
+    for _ in range(12):
+        sim.step()
+    st = sim.stats()
+    sim.close()
+    assert abs(st["mass"] - m0) <= 1e-7 * m0, (st["mass"], m0)
+    assert 0 <= st["cheb_form"] < nh.cheb_forms("fp32")
+
+
 def test_fp32_full_size_shoals_within_1e4_of_fp64_oracle():
     """The 1024^2 shoals workload in FP32 (dx = 0.1 m) against the FP64 oracle: eta within
     1e-4 relative L-infinity after 4 steps."""
@@ -314,3 +352,33 @@ def test_full_size_shoals_one_step_fp64():
     assert rel(g["eta"] + wl.H, h) < 1e-10
     assert rel(g["q1"], q1) < 1e-10 and rel(g["q2"], q2) < 1e-10
     assert rel(g["p"], p) < 1e-10
+
+
+# ------------------------------------------------------------------ circular dam-break
+
+
+@pytest.mark.parametrize("mode", ["swe", "nh_eps"])
+def test_dambreak_fp64_against_oracle(mode):
+    """The Sec. 7.7 circular dam-break (open boundaries) on a 96^2 mesh: the SWE step (the
+    non-hydrostatic part off) and the NH step stopped by criterion (32), 10 steps, against
+    the oracle (the oracle solves to 1e-14, so the NH case is held to the criterion's
+    reach)."""
+    wl = inputs.dambreak_2d(96)
+    kw = dict(nonhydrostatic=0) if mode == "swe" else dict(eps_dp=1e-12)
+    sim = nh.Sim(wl.H, wl.dx, wl.dy, bc=wl.bc, precision="fp64", tol=1e-13, **kw)
+    sim.set_state(wl.eta, wl.q1, wl.q2)
+    for _ in range(10):
+        sim.step()
+    g = sim.get_state()
+    sim.close()
+    c = O.cfg(wl.nx, wl.ny, dx=wl.dx, dy=wl.dy, bc=wl.bc, nonhydro=(mode != "swe"), tol=1e-14)
+    zn = np.zeros((wl.ny + 1, wl.nx + 1))
+    h, q1, q2, w, p, t, s, it = O.run_2d(c, wl.H, np.maximum(wl.eta + wl.H, 0), wl.q1, wl.q2,
+                                         zn, zn, max_steps=10)
+    tolr = 1e-10 if mode == "swe" else 1e-9
+    assert rel(g["eta"] + wl.H, h) < tolr
+    assert rel_q(g["q1"], g["q2"], q1, q2) < tolr
+    if mode == "swe":
+        assert not g["p"].any() and not g["w"].any()
+    else:
+        assert rel(g["p"], p) < 1e-8
