@@ -179,6 +179,21 @@ def cpu_baseline(steps=2):
                       f"single-threaded C oracle, FP64, solver tol 1e-13 ({el:.1f} s)"}
 
 
+def max_over_ranks(torch, dist, x, device="cuda"):
+    """The largest x over the ranks (after a barrier); x itself on one process."""
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    if dist:
+        dist.barrier()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(cells_per_rank, steps, ws, seconds):
+    """Whole-job Mcell-steps/s: every rank advanced its own replica `steps` times, and the
+    job took the slowest rank's time."""
+    return cells_per_rank * steps * ws / seconds / 1e6
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -358,6 +373,9 @@ def run_dambreak(args, torch, ws, rank, local, dist):
                 st = sim.stats()
                 sim.close()
                 k = DAMBREAK_MODES.index((name, kw))
+                print(f"dambreak {n}^2 {name}: {sec:.3f} s, {steps} steps, "
+                      f"{(st['solver_iters'] - it0) / max(2 * steps, 1):.1f} sweeps per stage",
+                      file=sys.stderr, flush=True)
                 row[name] = {"seconds": sec, "steps": steps,
                              "sweeps_per_stage": (st["solver_iters"] - it0) / max(2 * steps, 1),
                              "mcell_steps_per_s": n * n * steps / sec / 1e6,
@@ -406,12 +424,8 @@ def run_ensemble(args, torch, ws, rank, local, dist):
         ev1.record(stream)
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
-    t_max = torch.tensor([ms], device="cuda")
-    if dist:
-        dist.barrier()
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms_max = float(t_max.item())
-    value = cells * args.steps * ws / (ms_max / 1e3) / 1e6
+    ms_max = max_over_ranks(torch, dist, ms)
+    value = job_rate(cells, args.steps, ws, ms_max / 1e3)
 
     # per-kernel shares: two eagerly launched, event-bracketed steps after the timed region
     s0 = [b.stats(d) for d in range(len(wls))]
@@ -460,7 +474,7 @@ def run_ensemble(args, torch, ws, rank, local, dist):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     bytes_io = sum(v.numel() * v.element_size() for hb in host for v in hb.values())
-    e2e_val = cells * e2e_steps * ws / e2e_s / 1e6
+    e2e_val = job_rate(cells, e2e_steps, ws, max_over_ranks(torch, dist, e2e_s))
     tun = b.tuning()
     cand = nh.batch_candidates("fp32")
     if rank == 0:
@@ -566,12 +580,8 @@ def main():
     sim.profile(False)
     st = sim.stats()
     iters = st["solver_iters"] - it0
-    t_max = torch.tensor([ms], device="cuda")
-    if dist:
-        dist.barrier()
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms_max = float(t_max.item())
-    value = cells * args.steps * ws / (ms_max / 1e3) / 1e6
+    ms_max = max_over_ranks(torch, dist, ms)
+    value = job_rate(cells, args.steps, ws, ms_max / 1e3)
 
     # end to end through the C-ABI: pinned host state in, one step, state out, every step
     tdt = torch.float32 if prec == "fp32" else torch.float64
@@ -589,10 +599,7 @@ def main():
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     bytes_io = sum(v.numel() * v.element_size() for v in host.values())
-    e2e_t = torch.tensor([e2e_s], device="cuda")
-    if dist:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_val = cells * e2e_steps * ws / float(e2e_t.item()) / 1e6
+    e2e_val = job_rate(cells, e2e_steps, ws, max_over_ranks(torch, dist, e2e_s))
 
     # roofline of the kernel class with the largest device-time share
     total_ms = sum(v[1] for v in prof.values())

@@ -396,7 +396,10 @@ struct Impl : Base {
             if (h_sctl->done) break;
             // stagnation (rounding floor of the precision, or a spectrum the Gershgorin
             // interval does not describe): continue with BiCGStab from the current dp
-            if (h_sctl->rr < 0.81 * best) { best = h_sctl->rr; stale = 0; }
+            // (with criterion (32) the solve is the paper's relaxation run to its own stop:
+            // only a residual that no longer falls at all is a stall)
+            const double fall = hd->prm.eps_dp > 0.0 ? 0.99 : 0.81;
+            if (h_sctl->rr < fall * best) { best = h_sctl->rr; stale = 0; }
             else if (++stale >= 4) {
                 const int done_sweeps = h_sctl->sweeps;
                 hd->solver_iters += done_sweeps;
