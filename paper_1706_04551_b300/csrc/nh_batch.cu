@@ -312,6 +312,22 @@ kb_cheb_reg(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const 
     __syncthreads();
     if (w < nw) stage_item(w);
     unsigned phase = 0;
+    // consecutive items of one domain pool their residual sums: one publication (fence and
+    // ticket) per group instead of one per item
+    int gd = -1, gy = 0;
+    unsigned gn = 0;
+    double gs = 0.0, gm = 0.0;   // (thread 0)
+    auto flush = [&]() {
+        if (gn == 0) return;
+        const Dom<T>& Dg = A.dom[gd];
+        const int ntg = cdiv(Dg.P.nx + 1, TX) * cdiv(Dg.P.ny + 1, TY);
+        double acc[2];
+        if (dom_publish_sum_max(gs, gm, A.partials + Dg.poff, &A.sctl[gd].counter, gy, gn, ntg,
+                                acc) &&
+            tid == 0)
+            kb_cheb_finish(A, gd, &A.sctl[gd], acc, K, stage);
+        gn = 0;
+    };
     while (w < nw) {
         cp_async_wait_all();
         const bool got = mbar_wait_bounded(&bar, phase, kPolls);
@@ -351,13 +367,26 @@ kb_cheb_reg(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const 
         else
             cheb_region_reg<T, C, R, NW, K>(Rw, planes, exch, c1s, c2s, I0, J0, xo + n, xpo + n,
                                             rsum, dmax, next);
-        double acc[2];
-        if (dom_reduce_sum_max_f((float)rsum, (float)dmax, A.partials + D.poff, &ctl->counter,
-                                 acc, it.y, nt) &&
-            tid == 0)
-            kb_cheb_finish(A, it.x, ctl, acc, K, stage);
+        float bs = (float)rsum, bm = (float)dmax;
+        block_sum_max_f(bs, bm);
+        if (it.x != gd) {
+            flush();
+            gd = it.x;
+            gy = it.y;
+            gs = gm = 0.0;
+        } else if (tid == 0) {   // pooled into the group's slot: this item's slot is zero
+            A.partials[D.poff + 2 * (long long)it.y] = 0.0;
+            A.partials[D.poff + 2 * (long long)it.y + 1] = 0.0;
+        }
+        if (tid == 0) {
+            gs += bs;
+            gm = fmax(gm, (double)bm);
+        }
+        ++gn;
+        (void)nt;
         w = wn;
     }
+    flush();
 }
 
 // After the Chebyshev passes of a stage: a domain that ran an odd number of passes holds

@@ -296,6 +296,64 @@ __device__ __forceinline__ bool dom_reduce_sum_max_f(float s, float m, double* p
     return true;
 }
 
+// Sum and max of the block's (s, m), FP32, into thread 0.
+__device__ __forceinline__ void block_sum_max_f(float& s, float& m)
+{
+    __shared__ float gs[32], gm[32];
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int lane = tid & 31, wid = tid >> 5, nw = (blockDim.x * blockDim.y + 31) >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    if (lane == 0) { gs[wid] = s; gm[wid] = m; }
+    __syncthreads();
+    if (wid == 0) {
+        float a = lane < nw ? gs[lane] : 0.f, b = lane < nw ? gm[lane] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, o));
+        }
+        s = a;
+        m = b;
+    }
+    __syncthreads();
+}
+
+// Publish a block's (sum, max) for `cnt` items of a domain at once: thread 0 writes it to
+// partial slot `slot` (the block has written zeros to the slots of its other `cnt - 1`
+// items) and counts `cnt` arrivals.  Returns true, in every thread, in the block whose
+// arrivals complete the domain's `nitems`; that block receives the totals (fixed order over
+// the slots) in out.  Non-negative maxima only (a zero slot is neutral).
+__device__ __forceinline__ bool dom_publish_sum_max(double s, double m, double* partials,
+                                                    unsigned* counter, unsigned slot,
+                                                    unsigned cnt, unsigned nitems,
+                                                    double out[2])
+{
+    const unsigned tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const unsigned nthr = blockDim.x * blockDim.y;
+    __shared__ bool last;
+    if (tid == 0) {
+        partials[(size_t)slot * 2] = s;
+        partials[(size_t)slot * 2 + 1] = m;
+        __threadfence();
+        last = atomicAdd(counter, cnt) + cnt == nitems;
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double acc[2] = {0.0, 0.0};
+    for (unsigned bb = tid; bb < nitems; bb += nthr) {
+        acc[0] += __ldcg(partials + (size_t)bb * 2);
+        acc[1] = fmax(acc[1], __ldcg(partials + (size_t)bb * 2 + 1));
+    }
+    block_reduce<2, 2u>(acc);
+    out[0] = acc[0];
+    out[1] = acc[1];
+    if (tid == 0) *counter = 0u;
+    return true;
+}
+
 #define GRID_STRIDE(idx, n) \
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < (long long)(n); \
          idx += (long long)gridDim.x * blockDim.x)
