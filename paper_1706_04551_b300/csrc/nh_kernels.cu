@@ -313,27 +313,6 @@ k_corr2d_t(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_corr2d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
-         const T* __restrict__ q1k, const T* __restrict__ q2k, const T* __restrict__ ws,
-         const T* __restrict__ p, const T* __restrict__ dp, T* __restrict__ pout, T de,
-         int with_p, T* __restrict__ eo, T* __restrict__ q1o,
-         T* __restrict__ q2o, T* __restrict__ wo, int final_stage, double* partials,
-         StepCtl* st)
-{
-    T lam = T(0);
-    int bad = 0;
-    GRID_STRIDE(idx, (long long)(P.nx + 1) * (P.ny + 1))
-        corr_node(P, eta, H, q1k, q2k, ws, p, dp, pout, de, with_p, eo, q1o, q2o, wo, final_stage,
-                  idx, lam, bad);
-    double acc[1] = {(double)lam};
-    if (bad) atomicOr(&st->nonfinite, 1);
-    if (final_stage) {
-        if (grid_reduce<1, 1u>(acc, partials, &st->counter) && threadIdx.x == 0) st->lam = acc[0];
-    }
-}
-
 // ================================================================ batched 1D kernels
 // Row r of the ny rows is an independent channel: cells (i, r), nodes (k, r) with
 // row stride nx + 1.
