@@ -50,7 +50,7 @@ extern "C" {
 #define NH_ENOCONV (-4)     /* pressure solve did not reach tol within max_iter      */
 #define NH_ENONFINITE (-5)  /* a non-finite value appeared in the state              */
 
-enum { NH_BC_WALL = 0, NH_BC_OUTFLOW = 1 };
+enum { NH_BC_WALL = 0, NH_BC_OUTFLOW = 1, NH_BC_PERIODIC = 2 /* 1D only, west and east */ };
 enum {
     NH_SOLVER_BICGSTAB = 0,  /* Jacobi-preconditioned BiCGStab, FP64 dots                     */
     NH_SOLVER_CHEBYSHEV = 1  /* Jacobi with Chebyshev-scheduled relaxation (Sec. 5's scheduled
@@ -63,7 +63,8 @@ typedef struct {
     int dim;            /* 1 or 2                                                        */
     int nx, ny;         /* cells (2D: nx, ny >= 2; 1D: ny = number of independent rows)  */
     double dx, dy;      /* cell sizes (dy unused in 1D)                                  */
-    int bc[4];          /* west, east, south, north: NH_BC_WALL / NH_BC_OUTFLOW          */
+    int bc[4];          /* west, east, south, north: NH_BC_WALL / NH_BC_OUTFLOW, or
+                           NH_BC_PERIODIC on both west and east of a 1D channel         */
 } nh_grid;
 
 typedef struct {

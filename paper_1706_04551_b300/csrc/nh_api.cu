@@ -820,8 +820,16 @@ int check_grid(const nh_grid* g, const nh_params* p, std::string& why)
         return 0;
     }
     if (!(g->dx > 0.0) || (g->dim == 2 && !(g->dy > 0.0))) { why = "dx, dy must be > 0"; return 0; }
+    const bool periodic = g->bc[0] == NH_BC_PERIODIC || g->bc[1] == NH_BC_PERIODIC;
+    if (periodic && (g->dim != 1 || g->bc[0] != g->bc[1])) {
+        why = "periodic boundaries: 1D channels, west and east both periodic";
+        return 0;
+    }
     for (int k = 0; k < 4; ++k)
-        if (g->bc[k] != NH_BC_WALL && g->bc[k] != NH_BC_OUTFLOW) { why = "bc must be WALL or OUTFLOW"; return 0; }
+        if (g->bc[k] != NH_BC_WALL && g->bc[k] != NH_BC_OUTFLOW && !(k < 2 && periodic)) {
+            why = "bc must be WALL or OUTFLOW (or PERIODIC on both ends of a 1D channel)";
+            return 0;
+        }
     if ((double)g->nx * (double)g->ny > 2.0e9) { why = "grid too large"; return 0; }
     if (!(p->g > 0.0) || !(p->cfl > 0.0) || !(p->delta > 0.0) || p->hdry < 0.0 ||
         p->manning_n < 0.0 || !(p->tol > 0.0) || p->max_iter < 1) {

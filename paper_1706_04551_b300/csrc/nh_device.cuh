@@ -57,17 +57,18 @@ __device__ __forceinline__ T desing(T h, T q, T d4)
 }
 
 // Cell index under the boundary condition of each side: wall = mirror (refl = true),
-// outflow = copy of the first interior cell.  Valid for up to n cells outside.
+// outflow = copy of the first interior cell, periodic (1D channels) = the cell n away.
+// Valid for up to n cells outside.
 __device__ __forceinline__ int map_cell(int i, int n, int bclo, int bchi, bool& refl)
 {
     refl = false;
     if (i < 0) {
         if (bclo == 0) { refl = true; return -1 - i; }
-        return 0;
+        return bclo == 2 ? i + n : 0;
     }
     if (i >= n) {
         if (bchi == 0) { refl = true; return 2 * n - 1 - i; }
-        return n - 1;
+        return bchi == 2 ? i - n : n - 1;
     }
     return i;
 }

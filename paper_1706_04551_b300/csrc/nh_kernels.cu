@@ -449,8 +449,10 @@ k_asm1d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
         T bk = T(16) * dx * dx + xin * (xiL + xiR + T(2) * hL - T(2) * hR)
              + T(2) * hn * (xiL - xiR + T(4) * hn);
         T ck = (xiR + T(2) * hR) * (xin - T(2) * hn);
-        if (k == 0) { ck += ak; ak = T(0); }
-        if (k == P.nx) { ak += ck; ck = T(0); }
+        // walls / outflow fold the outside node onto its mirror; a periodic channel keeps
+        // the cyclic coupling (node nx is node 0 again)
+        if (k == 0 && P.bcw != 2) { ck += ak; ak = T(0); }
+        if (k == P.nx && P.bce != 2) { ak += ck; ck = T(0); }
         const size_t nidx = (size_t)idx;
         T wv = a != T(0) ? a * w_b[nidx] + b * w_in[nidx] : w_in[nidx];
         if (P.breaking) {
@@ -519,28 +521,89 @@ __global__ void k_thomas(int n, int rows, const T* __restrict__ A, const T* __re
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= rows) return;
     const size_t o = (size_t)row * n;
-    cp[o] = Cc[o] / Bd[o];
-    dp[o] = D[o] / Bd[o];
+    // the recurrences run in registers; the arrays are only streamed
+    T cpv = Cc[o] / Bd[o], dpv = D[o] / Bd[o];
+    cp[o] = cpv;
+    dp[o] = dpv;
     for (int i = 1; i < n; ++i) {
-        const T m = Bd[o + i] - A[o + i] * cp[o + i - 1];
-        cp[o + i] = Cc[o + i] / m;
-        dp[o + i] = (D[o + i] - A[o + i] * dp[o + i - 1]) / m;
+        const T ai = A[o + i];
+        const T m = Bd[o + i] - ai * cpv;
+        cpv = Cc[o + i] / m;
+        dpv = (D[o + i] - ai * dpv) / m;
+        cp[o + i] = cpv;
+        dp[o + i] = dpv;
     }
-    x[o + n - 1] = dp[o + n - 1];
-    for (int i = n - 2; i >= 0; --i) x[o + i] = dp[o + i] - cp[o + i] * x[o + i + 1];
+    T xv = dpv;
+    x[o + n - 1] = xv;
+    for (int i = n - 2; i >= 0; --i) {
+        xv = dp[o + i] - cp[o + i] * xv;
+        x[o + i] = xv;
+    }
 }
 
+// Cyclic tridiagonal solve (periodic channels, Sec. 4.4's modified Thomas algorithm), one
+// channel per thread: Sherman-Morrison over two Thomas sweeps that share their elimination
+// (right-hand sides d and u = (gamma, 0, ..., 0, alpha)).  Channel rows start every ld
+// entries and hold n unknowns; cp and z are scratch; x[n] = x[0] afterwards (the node past
+// the last one is the first again).
+template <typename T>
+__global__ void k_thomas_cyclic(int n, int ld, int rows, const T* __restrict__ A,
+                                const T* __restrict__ Bd, const T* __restrict__ Cc,
+                                const T* __restrict__ D, T* __restrict__ cp,
+                                T* __restrict__ z, T* __restrict__ x)
+{
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= rows) return;
+    const size_t o = (size_t)row * ld;
+    const T alpha = Cc[o + n - 1], beta = A[o], gam = -Bd[o];
+    auto bb = [&](int i) {   // diagonal with the rank-one part taken out
+        T v = Bd[o + i];
+        if (i == 0) v -= gam;
+        if (i == n - 1) v -= alpha * beta / gam;
+        return v;
+    };
+    // the recurrences run in registers; the arrays are only streamed
+    T m = bb(0);
+    T cpv = Cc[o] / m, xv = D[o] / m, zv = gam / m;
+    cp[o] = cpv; x[o] = xv; z[o] = zv;
+    for (int i = 1; i < n; ++i) {
+        const T ai = A[o + i];
+        m = bb(i) - ai * cpv;
+        cpv = Cc[o + i] / m;
+        xv = (D[o + i] - ai * xv) / m;
+        zv = ((i == n - 1 ? alpha : T(0)) - ai * zv) / m;
+        cp[o + i] = cpv; x[o + i] = xv; z[o + i] = zv;
+    }
+    for (int i = n - 2; i >= 0; --i) {
+        const T c = cp[o + i];
+        xv = x[o + i] - c * xv;
+        zv = z[o + i] - c * zv;
+        x[o + i] = xv; z[o + i] = zv;
+    }
+    const T fact = (x[o] + beta * x[o + n - 1] / gam) / (T(1) + z[o] + beta * z[o + n - 1] / gam);
+    for (int i = 0; i < n; ++i) x[o + i] -= fact * z[o + i];
+    x[o + n] = x[o];
+}
+
+// y = M x for the channel systems (rows of ld entries); cyclic: n = ld - 1 unknowns with
+// wrap-around coupling, and entry n repeats entry 0.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_tri_apply(int n, long long total, const T* __restrict__ A, const T* __restrict__ Bd,
-            const T* __restrict__ Cc, const T* __restrict__ x, T* __restrict__ y)
+k_tri_apply(int ld, long long total, int cyclic, const T* __restrict__ A,
+            const T* __restrict__ Bd, const T* __restrict__ Cc, const T* __restrict__ x,
+            T* __restrict__ y)
 {
     GRID_STRIDE(idx, total)
     {
-        const int k = (int)(idx % n);
-        T v = Bd[idx] * x[idx];
-        if (k > 0) v += A[idx] * x[idx - 1];
-        if (k < n - 1) v += Cc[idx] * x[idx + 1];
+        int k = (int)(idx % ld);
+        const long long o = idx - k;
+        if (cyclic && k == ld - 1) k = 0;   // the repeated first node
+        const int n = cyclic ? ld - 1 : ld;
+        T v = Bd[o + k] * x[o + k];
+        if (k > 0) v += A[o + k] * x[o + k - 1];
+        else if (cyclic) v += A[o + k] * x[o + n - 1];
+        if (k < n - 1) v += Cc[o + k] * x[o + k + 1];
+        else if (cyclic) v += Cc[o + k] * x[o];
         y[idx] = v;
     }
 }
@@ -876,6 +939,11 @@ int pcr_max_n(int elem_bytes) { return elem_bytes == 8 ? 4096 : 8192; }
 template <typename T>
 int launch_tridiag1d(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, T* x)
 {
+    if (P.bcw == 2) {   // periodic channels: nx unknowns with cyclic coupling
+        k_thomas_cyclic<T><<<(P.ny + 127) / 128, 128, 0, s>>>(P.nx, P.nx + 1, P.ny, B.cW, B.cC,
+                                                              B.cE, B.rhs, B.r, B.rh, x);
+        return 0;
+    }
     const int n = P.nx + 1;
     if (n <= pcr_max_n((int)sizeof(T))) {
         const size_t smem = 4 * (size_t)n * sizeof(T);
@@ -931,8 +999,8 @@ template <typename T>
 void launch_tridiag_apply1d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* x,
                             T* y)
 {
-    k_tri_apply<T><<<L.nblk, kThreads, 0, L.s>>>(P.nx + 1, (long long)(P.nx + 1) * P.ny, B.cW,
-                                                 B.cC, B.cE, x, y);
+    k_tri_apply<T><<<L.nblk, kThreads, 0, L.s>>>(P.nx + 1, (long long)(P.nx + 1) * P.ny,
+                                                 P.bcw == 2 ? 1 : 0, B.cW, B.cC, B.cE, x, y);
 }
 
 template <typename T>

@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libnh.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ENONFINITE = 0, -1, -2, -3, -4, -5
-WALL, OUTFLOW = 0, 1
+WALL, OUTFLOW, PERIODIC = 0, 1, 2
 BICGSTAB, CHEBYSHEV = 0, 1
 FP64, FP32 = 0, 1
 HOST, DEVICE = 0, 1

@@ -64,6 +64,23 @@ def test_cheb_forms_and_bad_form_rejected_without_touching_the_gpu():
         assert rc == nh.EINVAL and not h.value
 
 
+def test_periodic_only_on_both_ends_of_1d_channels():
+    import numpy as np
+    B.build()
+    L = nh.load()
+    p = nh.default_params()
+    H = np.ones(64)
+    for dim, bc in ((2, (2, 2, 0, 0)), (1, (2, 0, 0, 0)), (1, (0, 2, 0, 0)), (1, (0, 0, 2, 2))):
+        g = nh.Grid()
+        g.dim, g.nx, g.ny, g.dx, g.dy = dim, 8, 8, 0.1, 0.1
+        for k in range(4):
+            g.bc[k] = bc[k]
+        h = ctypes.c_void_p()
+        rc = L.nh_create(ctypes.byref(g), H.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                         ctypes.byref(p), None, ctypes.byref(h))
+        assert rc == nh.EINVAL and not h.value, (dim, bc)
+
+
 def test_create_batch_rejects_bad_input_without_touching_the_gpu():
     import numpy as np
     B.build()
