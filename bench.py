@@ -26,6 +26,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Mcell-steps/s full NH step"
 UNIT = "Mcell-steps/s"
+FP64_TFLOPS = 1.25   # nominal dense FP64 rate of a B300 (no measured figure in the peaks file)
 
 # Algorithmic words moved per node / cell by one launch of each kernel class (stage-averaged,
 # breaking on): reads of every input field once plus writes of every output field once.
@@ -622,6 +623,20 @@ def main():
         if ent and (top != "cheb_pass" or ent.get("cheb_form") == st["cheb_form"]):
             traffic = ent.get("bytes_per_launch")
     gpu_launches = int(sum(v[0] for v in prof.values()))
+    roof = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+            "peak_source": peak_kind, "algo_bytes_per_launch": algo_bytes,
+            "ms_per_launch": tms / nl, "share": tms / total_ms}
+    if prec == "fp64" and top == "cheb_pass":
+        # FP64 runs on B300's FP64 units (about 1/60 of the FP32 rate): the pass is bound by
+        # FP64 arithmetic, 14 flops per node and sweep (residual 9, update 5; an FMA is 2)
+        flops = 14.0 * nn * 4 * nl
+        roof = {"bound": "alu", "kernel": top, "achieved": flops / (tms / 1e3) / 1e12,
+                "peak": FP64_TFLOPS, "unit": "TFLOP/s",
+                "frac": flops / (tms / 1e3) / 1e12 / FP64_TFLOPS, "traffic": None,
+                "peak_source": "nominal B300 FP64 rate (1.25 TFLOP/s)",
+                "algo_flops_per_launch": flops / nl, "ms_per_launch": tms / nl,
+                "share": tms / total_ms, "hbm_frac": achieved / peak}
     # whole-step rooflines: (a) the algorithmic bytes of every launch of the timed region
     # over its device time; (b) the per-cell-step model of a plain (unblocked) step: the
     # stencil passes' words plus 5 words per Jacobi sweep (read p, eta*, H, r, write p)
@@ -661,10 +676,7 @@ def main():
                                   f"BiCGStab+Jacobi tol {prm['tol']}"),
                        "solver_iters_per_stage": iters / (2.0 * args.steps),
                        "cheb_form": st["cheb_form"]},
-            "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                         "peak_source": peak_kind, "algo_bytes_per_launch": algo_bytes,
-                         "ms_per_launch": tms / nl, "share": tms / total_ms},
+            "roofline": roof,
             "step_roofline": step_roof,
             "kernels": {k: {"launches": v[0], "ms": v[1], "share": v[1] / total_ms}
                         for k, v in prof.items() if v[0]},
