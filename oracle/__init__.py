@@ -8,7 +8,9 @@ the C file lists the readings taken where the paper is silent or garbled.
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py`` except the breaking
 terms (Sec. 3, Eq. 12), which are "parity unpinned" beyond invariants (lake at rest with
-breaking on, the switch-off limit, dissipation).
+breaking on, the switch-off limit, dissipation).  ``cfg(w_transport=True)`` selects the
+energy-consistent w equation of Sec. 2 (pinned by donor-cell upwind on uniform flow and
+by invariants).
 """
 from __future__ import annotations
 
@@ -38,6 +40,7 @@ class Cfg(C.Structure):
         ("manning", C.c_double), ("B1", C.c_double), ("B2", C.c_double),
         ("breaking", C.c_int), ("nonhydro", C.c_int),
         ("tol", C.c_double), ("max_iter", C.c_int),
+        ("w_transport", C.c_int),
     ]
 
 
@@ -105,7 +108,8 @@ def _f64(a) -> np.ndarray:
 def cfg(nx: int, ny: int = 1, dx: float = 1.0, dy: float | None = None, bc=(WALL,) * 4,
         g: float = 9.81, cfl: float = 0.9, delta: float = 1e-5, hdry: float | None = None,
         manning: float = 0.0, B1: float = 0.15, B2: float = 0.5, breaking: bool = False,
-        nonhydro: bool = True, tol: float = 1e-13, max_iter: int = 4000) -> Cfg:
+        nonhydro: bool = True, tol: float = 1e-13, max_iter: int = 4000,
+        w_transport: bool = False) -> Cfg:
     c = Cfg()
     c.nx, c.ny = int(nx), int(ny)
     c.dx = float(dx)
@@ -117,6 +121,7 @@ def cfg(nx: int, ny: int = 1, dx: float = 1.0, dy: float | None = None, bc=(WALL
     c.manning, c.B1, c.B2 = float(manning), float(B1), float(B2)
     c.breaking, c.nonhydro = int(bool(breaking)), int(bool(nonhydro))
     c.tol, c.max_iter = float(tol), int(max_iter)
+    c.w_transport = int(bool(w_transport))
     return c
 
 

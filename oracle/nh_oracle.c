@@ -47,6 +47,10 @@
  *     App. B A.2 analysis (q = w = 0 where h vanishes gives p = 0).
  *   - dt (Eq. 23) in 2D: CFL / max((|u|+c)/dx + (|v|+c)/dy), from the current state.
  *   - The 2D system is solved by unpreconditioned BiCGStab to a relative residual tol.
+ *   - Energy-consistent w equation (w_transport = 1; Sec. 2 names the system of [7] and
+ *     says the scheme extends to it, without a discretisation): hw is moved on the node
+ *     (dual) cells by the hyperbolic step's face mass fluxes, upwind in w, and the
+ *     Runge-Kutta combination acts on hw (wtransport1d / wtransport2d).
  */
 #include "nh_oracle.h"
 
@@ -186,9 +190,10 @@ double or1d_cfl_dt(const or_cfg *c, const double *H, const double *h, const doub
 }
 
 /* Hyperbolic step of Sec. 4.1 (Eqs. 18-22) plus semi-implicit Manning friction and the
- * non-negative depth clamp; writes U^{n+1/2}. */
+ * non-negative depth clamp; writes U^{n+1/2}.  Fm (n + 1 entries, or NULL): the mass flux
+ * of every face, F_h(U^-) + D^-_h, seen from its left cell. */
 static int hyp1d(const or_cfg *c, const double *H, const double *h, const double *q,
-                 double dt, double *ho, double *qo)
+                 double dt, double *ho, double *qo, double *Fm)
 {
     const int n = c->nx, ne = n + 2 * G1;
     const double dx = c->dx, g = c->g;
@@ -228,6 +233,7 @@ static int hyp1d(const or_cfg *c, const double *H, const double *h, const double
         pvm_face(g, c->hdry, hE[L], eE[L], uE[L], 0.0, hW[R], eW[R], uW[R], 0.0, dm, dp);
         Dm[2 * k] = dm[0]; Dm[2 * k + 1] = dm[1];
         Dp[2 * k] = dp[0]; Dp[2 * k + 1] = dp[1];
+        if (Fm) Fm[k] = hE[L] * uE[L] + dm[0];
     }
 
     /* Cell update, Eq. (20), with the inner-cell term of Eq. (22) in free-surface form:
@@ -256,7 +262,7 @@ static int hyp1d(const or_cfg *c, const double *H, const double *h, const double
 int or1d_hyperbolic(const or_cfg *c, const double *H, const double *h, const double *q,
                     double dt, double *ho, double *qo)
 {
-    return hyp1d(c, H, h, q, dt, ho, qo);
+    return hyp1d(c, H, h, q, dt, ho, qo, NULL);
 }
 
 /* Breaking terms of Eq. (12)/(14) in 1D: q += dt * 2 nu u_x H_x at cells (centred
@@ -437,6 +443,48 @@ int or1d_nh_solve(const or_cfg *c, const double *H, const double *h, const doubl
     return 0;
 }
 
+/* Energy-consistent w equation (Sec. 2, the system of [7]): (hw)_t + (hwu)_x = p in place
+ * of h w_t = p.  The paper gives no discretisation; the reading used here: hw lives on the
+ * nodes like w.  Node k owns the dual cell between the centres of cells k-1 and k (its
+ * inner half at a wall or outflow end), whose depth is the mean depth of those two cells.
+ * A dual face at the centre of cell i carries the mean of the mass fluxes of cell i's two
+ * faces in the hyperbolic step (F = F_h(U^-) + D^-_h per face); at a wall or outflow end
+ * the outer dual face is the boundary face itself.  w is taken upwind at every dual face
+ * (first order), and the node's own w at the boundary faces.  Those dual fluxes move the
+ * dual-cell depth exactly as the mean of the two cell depths moves, so a uniform w stays
+ * uniform and sum(h w) over the dual cells changes only through the boundary faces.  The
+ * Runge-Kutta combination acts on the conserved hw:
+ *   (hw)* = a h_b w_b + b (h w - dt div(F w)),   w* = (hw)* / h* (desingularised),
+ * the node depths h_b, h, h* being those of the base, input and combined states. */
+static void wtransport1d(const or_cfg *c, const double *hb, const double *wb,
+                         const double *h, const double *w, const double *F,
+                         const double *hs, double a, double bw, double dt, double *wo)
+{
+    const int n = c->nx, ne = n + 2 * G1, per = periodic1d(c);
+    double *eb = calloc(ne, sizeof(double)), *ei = calloc(ne, sizeof(double));
+    double *es = calloc(ne, sizeof(double));
+    for (int i = 0; i < n; ++i) { eb[i + G1] = hb[i]; ei[i + G1] = h[i]; es[i + G1] = hs[i]; }
+    ghost1d(c, n, eb, 1.0); ghost1d(c, n, ei, 1.0); ghost1d(c, n, es, 1.0);
+    const int nk = per ? n : n + 1;          /* distinct nodes (periodic: node n is node 0) */
+    for (int k = 0; k < nk; ++k) {
+        const int west_end = !per && k == 0, east_end = !per && k == n;
+        const double area = (west_end || east_end) ? 0.5 : 1.0;
+        const int kw = k == 0 ? n - 1 : k - 1;   /* west neighbour (periodic wrap at 0) */
+        const double FE = east_end ? F[n] : 0.5 * (F[k] + F[k + 1]);
+        const double FW = west_end ? F[0] : 0.5 * (F[kw] + F[kw + 1]);
+        const double wE = east_end ? w[k] : (FE > 0.0 ? w[k] : w[k + 1]);
+        const double wW = west_end ? w[k] : (FW > 0.0 ? w[kw] : w[k]);
+        const double hin = 0.5 * (ei[k + 1] + ei[k + 2]);
+        const double hbn = 0.5 * (eb[k + 1] + eb[k + 2]);
+        const double hsn = 0.5 * (es[k + 1] + es[k + 2]);
+        const double m = area * hin * w[k] - dt / c->dx * (FE * wE - FW * wW);
+        const double hw = a * hbn * wb[k] + bw * m / area;
+        wo[k] = hw * desing(hsn, 1.0, c->delta);
+    }
+    if (per) wo[n] = wo[0];
+    free(eb); free(ei); free(es);
+}
+
 /* Dry cells carry no discharge (reading of Sec. 4.5 and App. B A.2, whose analysis takes
  * q = w = 0 where the depth vanishes): q = 0 where h <= hdry, at the end of each stage. */
 static void dry_discharge_1d(const or_cfg *c, const double *h, double *q)
@@ -459,12 +507,18 @@ static int stage1d(const or_cfg *c, const double *H, const double *hb, const dou
 {
     const int n = c->nx, ne = n + 2 * G1;
     const double dx = c->dx;
-    int clamped = hyp1d(c, H, h, q, dt, ho, qo);
+    double *Fm = c->w_transport ? calloc(n + 1, sizeof(double)) : NULL;
+    int clamped = hyp1d(c, H, h, q, dt, ho, qo, Fm);
     for (int i = 0; i < n; ++i) {
         ho[i] = a * hb[i] + bw * ho[i];
         qo[i] = a * qb[i] + bw * qo[i];
     }
-    for (int k = 0; k <= n; ++k) wo[k] = a * wb[k] + bw * w[k];
+    if (c->w_transport) {
+        wtransport1d(c, hb, wb, h, w, Fm, ho, a, bw, dt, wo);
+        free(Fm);
+    } else {
+        for (int k = 0; k <= n; ++k) wo[k] = a * wb[k] + bw * w[k];
+    }
     const double de = bw * dt;                   /* effective projection step */
     if (c->breaking) breaking1d(c, H, ho, qo, wo, de);
     if (!c->nonhydro) {
@@ -610,9 +664,12 @@ double or2d_cfl_dt(const or_cfg *c, const double *H, const double *h, const doub
 }
 
 /* Hyperbolic step of Sec. 5 / Eq. (30): second-order PVM-HLL with MUSCL-minmod, the
- * cell integral by the midpoint rule, then friction and the depth clamp. */
+ * cell integral by the midpoint rule, then friction and the depth clamp.  FX ([ny][nx+1])
+ * and FY ([ny+1][nx]), or NULL: the mass flux of every x / y face, F_h(U^-) + D^-_h, seen
+ * from its west / south cell. */
 static int hyp2d(const or_cfg *c, const double *H, const double *h, const double *q1,
-                 const double *q2, double dt, double *ho, double *q1o, double *q2o)
+                 const double *q2, double dt, double *ho, double *q1o, double *q2o,
+                 double *FX, double *FY)
 {
     const int nx = c->nx, ny = c->ny;
     const double dx = c->dx, dy = c->dy, g = c->g;
@@ -671,6 +728,7 @@ static int hyp2d(const or_cfg *c, const double *H, const double *h, const double
             size_t L = CE(I - 1, j), R = CE(I, j), f = 3 * ((size_t)j * (nx + 1) + I);
             pvm_face(g, c->hdry, xE[0][L], xE[1][L], xE[2][L], xE[3][L],
                      xW[0][R], xW[1][R], xW[2][R], xW[3][R], DmX + f, DpX + f);
+            if (FX) FX[(size_t)j * (nx + 1) + I] = xE[0][L] * xE[2][L] + DmX[f];
         }
     /* y faces (i, J), J = 0 .. ny: normal = y (q2), tangential = x (q1) */
     double *DmY = calloc(3 * (size_t)nx * (ny + 1), sizeof(double));
@@ -680,6 +738,7 @@ static int hyp2d(const or_cfg *c, const double *H, const double *h, const double
             size_t L = CE(i, J - 1), R = CE(i, J), f = 3 * ((size_t)J * nx + i);
             pvm_face(g, c->hdry, yN[0][L], yN[1][L], yN[3][L], yN[2][L],
                      yS[0][R], yS[1][R], yS[3][R], yS[2][R], DmY + f, DpY + f);
+            if (FY) FY[(size_t)J * nx + i] = yN[0][L] * yN[3][L] + DmY[f];
         }
 
     /* cell update, Eq. (30) */
@@ -723,7 +782,7 @@ static int hyp2d(const or_cfg *c, const double *H, const double *h, const double
 int or2d_hyperbolic(const or_cfg *c, const double *H, const double *h, const double *q1,
                     const double *q2, double dt, double *ho, double *q1o, double *q2o)
 {
-    return hyp2d(c, H, h, q1, q2, dt, ho, q1o, q2o);
+    return hyp2d(c, H, h, q1, q2, dt, ho, q1o, q2o, NULL, NULL);
 }
 
 /* 2D breaking terms: Sec. 3 with q_x -> div q, u_x -> div u (reading).  Cells: q +=
@@ -987,6 +1046,63 @@ int or2d_solve(const or_cfg *c, const double *H, const double *h, const double *
     return st;
 }
 
+/* Node depth: the mean of the four cells around node (I, J) of an extended, ghosted cell
+ * array (at a wall or outflow side the mean of the cells inside). */
+static double node_depth2d(const or_cfg *c, const double *e, int I, int J)
+{
+    const int nx = c->nx;
+    return 0.25 * (e[CE(I - 1, J - 1)] + e[CE(I, J - 1)] + e[CE(I - 1, J)] + e[CE(I, J)]);
+}
+
+/* 2D form of wtransport1d (energy-consistent w equation (hw)_t + div(hw u) = p): node
+ * (I, J) owns the dual cell [x_I - dx/2, x_I + dx/2] x [y_J - dy/2, y_J + dy/2] clipped to
+ * the domain (area fraction 1, 1/2 or 1/4 of dx dy), a quarter of each cell around it.  Its
+ * east face runs along the centre line of the cells (I, J-1), (I, J) (those inside the
+ * grid), through half of each; the x mass flux across a cell's centre line is the mean of
+ * its two x faces' fluxes.  On the domain boundary the dual face is the boundary face. */
+static void wtransport2d(const or_cfg *c, const double *hb, const double *wb,
+                         const double *h, const double *w, const double *FX,
+                         const double *FY, const double *hs, double a, double bw, double dt,
+                         double *wo)
+{
+    const int nx = c->nx, ny = c->ny;
+    double *eb = ext_cells(c), *ei = ext_cells(c), *es = ext_cells(c);
+    load_cells(c, hb, eb); load_cells(c, h, ei); load_cells(c, hs, es);
+    ghost2d(c, eb, 1.0, 1.0); ghost2d(c, ei, 1.0, 1.0); ghost2d(c, es, 1.0, 1.0);
+    for (int J = 0; J <= ny; ++J)
+        for (int I = 0; I <= nx; ++I) {
+            const double ax = (I == 0 || I == nx) ? 0.5 : 1.0;
+            const double ay = (J == 0 || J == ny) ? 0.5 : 1.0;
+            /* cs[d]: x-face fluxes of face column I-1+d summed over the rows J-1, J inside;
+             * rs[d]: y-face fluxes of face row J-1+d summed over the columns I-1, I inside */
+            double cs[3] = {0.0, 0.0, 0.0}, rs[3] = {0.0, 0.0, 0.0};
+            for (int d = 0; d < 3; ++d) {
+                const int If = I - 1 + d, Jf = J - 1 + d;
+                if (If >= 0 && If <= nx)
+                    for (int j = J - 1; j <= J; ++j)
+                        if (j >= 0 && j < ny) cs[d] += FX[(size_t)j * (nx + 1) + If];
+                if (Jf >= 0 && Jf <= ny)
+                    for (int i = I - 1; i <= I; ++i)
+                        if (i >= 0 && i < nx) rs[d] += FY[(size_t)Jf * nx + i];
+            }
+            const double FE = I == nx ? 0.5 * cs[1] : 0.25 * (cs[1] + cs[2]);
+            const double FW = I == 0 ? 0.5 * cs[1] : 0.25 * (cs[0] + cs[1]);
+            const double FN = J == ny ? 0.5 * rs[1] : 0.25 * (rs[1] + rs[2]);
+            const double FS = J == 0 ? 0.5 * rs[1] : 0.25 * (rs[0] + rs[1]);
+            const double wc = w[NI(I, J)];
+            const double wE = I == nx ? wc : (FE > 0.0 ? wc : w[NI(I + 1, J)]);
+            const double wW = I == 0 ? wc : (FW > 0.0 ? w[NI(I - 1, J)] : wc);
+            const double wN = J == ny ? wc : (FN > 0.0 ? wc : w[NI(I, J + 1)]);
+            const double wS = J == 0 ? wc : (FS > 0.0 ? w[NI(I, J - 1)] : wc);
+            const double area = ax * ay;
+            const double m = area * node_depth2d(c, ei, I, J) * wc
+                           - dt / c->dx * (FE * wE - FW * wW) - dt / c->dy * (FN * wN - FS * wS);
+            const double hw = a * node_depth2d(c, eb, I, J) * wb[NI(I, J)] + bw * m / area;
+            wo[NI(I, J)] = hw * desing(node_depth2d(c, es, I, J), 1.0, c->delta);
+        }
+    free(eb); free(ei); free(es);
+}
+
 /* Dry cells carry no discharge (see dry_discharge_1d). */
 static void dry_discharge_2d(const or_cfg *c, const double *h, double *q1, double *q2)
 {
@@ -1007,13 +1123,23 @@ static int stage2d(const or_cfg *c, const double *H, const double *hb, const dou
 {
     const int nx = c->nx, ny = c->ny;
     const size_t n = (size_t)nx * ny, nn = (size_t)(nx + 1) * (ny + 1);
-    int clamped = hyp2d(c, H, h, q1, q2, dt, ho, q1o, q2o);
+    double *FX = NULL, *FY = NULL;
+    if (c->w_transport) {
+        FX = calloc((size_t)(nx + 1) * ny, sizeof(double));
+        FY = calloc((size_t)nx * (ny + 1), sizeof(double));
+    }
+    int clamped = hyp2d(c, H, h, q1, q2, dt, ho, q1o, q2o, FX, FY);
     for (size_t k = 0; k < n; ++k) {
         ho[k] = a * hb[k] + bw * ho[k];
         q1o[k] = a * q1b[k] + bw * q1o[k];
         q2o[k] = a * q2b[k] + bw * q2o[k];
     }
-    for (size_t k = 0; k < nn; ++k) wo[k] = a * wb[k] + bw * w[k];
+    if (c->w_transport) {
+        wtransport2d(c, hb, wb, h, w, FX, FY, ho, a, bw, dt, wo);
+        free(FX); free(FY);
+    } else {
+        for (size_t k = 0; k < nn; ++k) wo[k] = a * wb[k] + bw * w[k];
+    }
     const double de = bw * dt;
     if (c->breaking) breaking2d(c, H, ho, q1o, q2o, wo, de);
     *iters = 0; *resid = 0.0;

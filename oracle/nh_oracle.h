@@ -21,6 +21,9 @@
  *                                           Table 1 orders, 2D == 1D on y-invariant data)
  *   breaking terms (Sec. 3, Eq. 12) ........ parity unpinned beyond invariants (lake at rest
  *                                           with breaking on, switch-off limit, dissipation)
+ *   w transport (w_transport = 1, Sec. 2) .. pinned (donor-cell upwind on uniform flow,
+ *                                           uniform w kept, sum of h w kept between walls,
+ *                                           no new extrema)
  */
 #ifndef NH_ORACLE_H
 #define NH_ORACLE_H
@@ -45,6 +48,9 @@ typedef struct {
     int nonhydro;        /* 1: full scheme; 0: hydrostatic SWE only (p = 0)            */
     double tol;          /* 2D Krylov relative-residual tolerance                       */
     int max_iter;
+    int w_transport;     /* 1: energy-consistent w equation (hw)_t + div(hw u) = p of the
+                            system of [7] (Sec. 2), hw moved upwind on the node (dual)
+                            cells; 0: Yamazaki's h w_t = p                                */
 } or_cfg;
 
 typedef struct {
