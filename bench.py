@@ -42,6 +42,9 @@ WORDS = {
     "cheb_pass": 10.0,    # x x_prev b 5 coefs -> x x_prev (K sweeps in shared memory)
     "tridiag": 5.0,
     "correction": 10.0,   # eta* H q1** q2** w* p -> eta q1 q2 w
+    "w_transport": 11.0,  # (hw)_t + div(hw u) = p form, per node: face mass fluxes (2),
+                          # eta base / input / combined, H, w base / input -> w* (8 + 1);
+                          # the hyperbolic launch then also writes the 2 face fluxes
 }
 
 
@@ -528,6 +531,8 @@ def main():
     ap.add_argument("--solver", type=int, default=None, help="0 BiCGStab, 1 Chebyshev")
     ap.add_argument("--cheb-form", type=int, default=None,
                     help="kernel form of the Chebyshev pass (default: chosen by timing)")
+    ap.add_argument("--w-equation", default="yamazaki", choices=["yamazaki", "transport"],
+                    help="h w_t = p (default) or the energy-consistent (hw)_t + div(hw u) = p")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -555,6 +560,9 @@ def main():
         prm["solver"] = args.solver
     if args.cheb_form is not None:
         prm["cheb_form"] = args.cheb_form
+    if args.w_equation == "transport":
+        prm["w_equation"] = nh.W_TRANSPORT
+        desc = desc + ", w equation (hw)_t + div(hw u) = p"
     stream = torch.cuda.current_stream()
     sim = nh.Sim(wl.H, wl.dx, wl.dy, bc=wl.bc, precision=prec, stream=stream, **prm)
     dt_np = np.float32 if prec == "fp32" else np.float64
@@ -611,6 +619,8 @@ def main():
     words = dict(WORDS)
     if not prm.get("breaking"):
         words["assembly"] = 13.5
+    if prm.get("w_equation"):
+        words["hyperbolic"] += 2.0   # the face mass fluxes of the w transport
     algo_bytes = words[top] * esize * units
     achieved = algo_bytes / (tms / nl / 1e3) / 1e9
     peak, peak_kind = peaks()
@@ -647,7 +657,8 @@ def main():
             algo_step += words[k] * esize * u * n_l
     sweeps_stage = iters / (2.0 * args.steps)
     stencil_words = sum(words[k] * prof[k][0] for k in ("hyperbolic", "breaking", "assembly",
-                                                         "correction") if k in prof) / args.steps
+                                                         "correction", "w_transport")
+                        if k in prof) / args.steps
     model_words = stencil_words + 2.0 * sweeps_stage * 5.0
     step_roof = {
         "algorithmic": {"achieved": algo_step / (total_ms / 1e3) / 1e9, "unit": "GB/s",

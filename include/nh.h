@@ -57,6 +57,11 @@ enum {
                                 relaxation Jacobi) on the Gershgorin interval of D^-1 M        */
 };
 enum { NH_FP64 = 0, NH_FP32 = 1 };
+enum {
+    NH_W_YAMAZAKI = 0,   /* h w_t = p (Eq. 7)                                             */
+    NH_W_TRANSPORT = 1   /* (hw)_t + div(hw u) = p, the energy-consistent system of Sec. 2's
+                            reference [7]: hw moved with the hyperbolic step's mass fluxes */
+};
 enum { NH_HOST = 0, NH_DEVICE = 1 };
 
 typedef struct {
@@ -90,6 +95,11 @@ typedef struct {
                            kernel form of the pass is chosen by timing the first passes;
                            0 .. nh_cheb_forms(precision) - 1 = that form.  All forms give
                            the same iterates.                                            */
+    int w_equation;     /* NH_W_YAMAZAKI (default) or NH_W_TRANSPORT.  With NH_W_TRANSPORT
+                           hw lives on the node (dual) cells: each stage moves it with the
+                           mean of the surrounding cells' face mass fluxes, upwind in w,
+                           and the Runge-Kutta combination acts on hw.  Single-domain
+                           handles only; batches and nh_step_taped reject it.            */
 } nh_params;
 
 typedef struct {
@@ -115,7 +125,7 @@ typedef struct nh_handle nh_handle;
 /* Fill p with the paper's defaults: g = 9.81, CFL 0.9, delta = 1e-5, hdry = delta,
  * n = 0, B1 = 0.15, B2 = 0.5 (Sec. 7.4), breaking off, non-hydrostatic on, Chebyshev
  * solver, tol 1e-12, max_iter 2000, FP64, fixed_dt 0, eps_dp 0, exact adjoint, pass
- * form chosen by timing (cheb_form = -1). */
+ * form chosen by timing (cheb_form = -1), w equation h w_t = p (NH_W_YAMAZAKI). */
 int nh_default_params(nh_params *p);
 
 /* Number of kernel forms of the Chebyshev-scheduled Jacobi pass (Sec. 5's scheduled
@@ -172,6 +182,7 @@ enum {
     NH_K_ADJ_HYPERBOLIC,  /* adjoint: hyperbolic step (faces, cells)                     */
     NH_K_ADJ_ASSEMBLY,    /* adjoint: transposed rows, assembly / solve terms            */
     NH_K_ADJ_CORRECTION,  /* adjoint: correction terms                                   */
+    NH_K_W_TRANSPORT,     /* w* of the (hw)_t + div(hw u) = p form (NH_W_TRANSPORT)      */
     NH_K_COUNT
 };
 

@@ -119,7 +119,7 @@ struct Impl : Base {
     int dim;
     size_t nc, nn;           // cells, nodes
     Launch Lc, Ln;
-    Bufs<T> B;
+    Bufs<T> B{};
     std::vector<void*> allocs;
     Prof prof;
     SolveCtl* h_sctl = nullptr;   // pinned mirrors of the device control blocks
@@ -206,6 +206,12 @@ struct Impl : Base {
         }
         A(B.sctl, 1);
         A(B.stctl, 1);
+        if (q.w_equation == NH_W_TRANSPORT) {
+            // face mass fluxes: x faces [ny][nx+1] (1D: [rows][nx+1]), y faces [ny+1][nx]
+            A(B.fmx, (size_t)(g.nx + 1) * g.ny);
+            if (dim == 2) A(B.fmy, (size_t)g.nx * (g.ny + 1));
+            A(B.wt, nn);
+        }
 #undef A
         cudaError_t e;
         if ((e = cudaMallocHost(&h_sctl, sizeof(SolveCtl))) != cudaSuccess) return cuda_fail(hd, e, "cudaMallocHost");
@@ -500,13 +506,21 @@ struct Impl : Base {
         T* ao = s == 0 ? B.q11 : B.q1;
         T* bo = s == 0 ? B.q21 : B.q2;
         T* wo = s == 0 ? B.w1 : B.w;
+        const bool wt = B.wt != nullptr;   // w equation (hw)_t + div(hw u) = p
         K_(NH_K_HYPERBOLIC, [&] {
             launch_hyp2d<T>(P, Lc, ein, ain, bin, B.eta, B.q1, B.q2, B.H, a, b, dt, B.etas,
-                            B.q1s, B.q2s, B.stctl);
+                            B.q1s, B.q2s, B.stctl, B.fmx, B.fmy);
         });
+        // transported w* (the assembly then takes it as it is: a = 0, b = 1)
+        if (wt)
+            K_(NH_K_W_TRANSPORT, [&] {
+                launch_wtrans2d<T>(P, Ln, B.eta, ein, B.etas, B.H, B.w, win, B.fmx, B.fmy, a,
+                                   b, dt, B.wt);
+            });
         // the breaking terms (q* -> q**) run inside the assembly
         K_(NH_K_ASSEMBLY, [&] {
-            launch_asm2d<T>(P, Ln, B, win, B.w, a, b, de, q.nonhydrostatic ? 1 : 0,
+            launch_asm2d<T>(P, Ln, B, wt ? B.wt : win, wt ? B.wt : B.w, wt ? T(0) : a,
+                            wt ? T(1) : b, de, q.nonhydrostatic ? 1 : 0,
                             q.nonhydrostatic ? 1 : 0, q.tol * q.tol, q.max_iter,
                             q.solver == NH_SOLVER_CHEBYSHEV ? cheb_sweeps_per_pass<T>() : 0,
                             B.partials, B.sctl, 1);
@@ -532,12 +546,22 @@ struct Impl : Base {
         T* eo = s == 0 ? B.eta1 : B.eta;
         T* ao = s == 0 ? B.q11 : B.q1;
         T* wo = s == 0 ? B.w1 : B.w;
+        const bool wt = B.wt != nullptr;   // w equation (hw)_t + (hw u)_x = p
         K_(NH_K_HYPERBOLIC, [&] {
-            launch_hyp1d<T>(P, Lc, ein, ain, B.eta, B.q1, B.H, a, b, dt, B.etas, B.q1s, B.stctl);
+            launch_hyp1d<T>(P, Lc, ein, ain, B.eta, B.q1, B.H, a, b, dt, B.etas, B.q1s, B.stctl,
+                            B.fmx);
         });
+        if (wt)
+            K_(NH_K_W_TRANSPORT, [&] {
+                launch_wtrans1d<T>(P, Ln, B.eta, ein, B.etas, B.H, B.w, win, B.fmx, a, b, dt,
+                                   B.wt);
+            });
         if (q.breaking)
             K_(NH_K_BREAKING, [&] { launch_break1d<T>(P, Lc, B.etas, B.q1s, B.H, de, B.q1k); });
-        K_(NH_K_ASSEMBLY, [&] { launch_asm1d<T>(P, Ln, B, B.q1s, B.q1k, win, B.w, a, b, de); });
+        K_(NH_K_ASSEMBLY, [&] {
+            launch_asm1d<T>(P, Ln, B, B.q1s, B.q1k, wt ? B.wt : win, wt ? B.wt : B.w,
+                            wt ? T(0) : a, wt ? T(1) : b, de);
+        });
         if (q.nonhydrostatic) {
             int trc = 0;
             K_(NH_K_TRIDIAG, [&] { trc = launch_tridiag1d<T>(P, hd->s, B, B.p); });
@@ -695,10 +719,11 @@ struct Impl : Base {
                      void* Hbv) override
     {
         const nh_params& q = hd->prm;
-        if (dim != 2 || !q.nonhydrostatic || q.breaking || q.manning_n > 0.0)
+        if (dim != 2 || !q.nonhydrostatic || q.breaking || q.manning_n > 0.0 ||
+            q.w_equation != NH_W_YAMAZAKI)
             return fail(hd, NH_EINVAL,
-                        "nh_adjoint_step: 2D non-hydrostatic steps without friction or "
-                        "breaking only");
+                        "nh_adjoint_step: 2D non-hydrostatic steps of the h w_t = p form "
+                        "without friction or breaking only");
         int rc = adjoint_alloc();
         if (rc != NH_OK) return rc;
         T* eb = static_cast<T*>(ebv);
@@ -845,6 +870,10 @@ int check_grid(const nh_grid* g, const nh_params* p, std::string& why)
     }
     const int nforms = p->precision == NH_FP32 ? cheb_pass_forms<float>() : cheb_pass_forms<double>();
     if (p->cheb_form < -1 || p->cheb_form >= nforms) { why = "cheb_form out of range"; return 0; }
+    if (p->w_equation != NH_W_YAMAZAKI && p->w_equation != NH_W_TRANSPORT) {
+        why = "w_equation must be NH_W_YAMAZAKI or NH_W_TRANSPORT";
+        return 0;
+    }
     return 1;
 }
 
@@ -861,6 +890,7 @@ int nh_default_params(nh_params* p)
     p->precision = NH_FP64; p->fixed_dt = 0.0; p->eps_dp = 0.0;
     p->adjoint_frozen_limiter = 0;
     p->cheb_form = -1;
+    p->w_equation = NH_W_YAMAZAKI;
     return NH_OK;
 }
 
@@ -1015,6 +1045,8 @@ int nh_step_taped(nh_handle* h, double dt, void* tape, double* dt_taken)
 {
     if (!h || !tape) return NH_EINVAL;
     if (h->grid.dim != 2) return fail(h, NH_EINVAL, "nh_step_taped: 2D only");
+    if (h->prm.w_equation != NH_W_YAMAZAKI)
+        return fail(h, NH_EINVAL, "nh_step_taped: the adjoint covers the h w_t = p form only");
     const double d = dt > 0.0 ? dt : h->dt_next;
     if (!(d > 0.0)) return fail(h, NH_EINVAL, "no positive time step");
     int rc = h->impl->step_taped(d, tape);

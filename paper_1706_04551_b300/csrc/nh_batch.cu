@@ -1727,6 +1727,10 @@ int check_batch(int n, const nh_grid* grids, const double* const* H, const nh_pa
         why = "the batched form solves with NH_SOLVER_CHEBYSHEV only";
         return 0;
     }
+    if (p->w_equation != NH_W_YAMAZAKI) {
+        why = "the batched form runs the h w_t = p form only";
+        return 0;
+    }
     double total = 0.0;
     for (int d = 0; d < n; ++d) {
         const nh_grid& g = grids[d];

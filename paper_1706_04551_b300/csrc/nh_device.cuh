@@ -367,13 +367,16 @@ __device__ __forceinline__ bool dom_publish_sum_max(double s, double m, double* 
 // stores, for the left cell, D^- + F_c(U^-) + (0, g h_L eta^-, 0) and, for the right cell,
 // D^+ - F_c(U^+) - (0, g h_R eta^+, 0) (normal frame), i.e. the fluctuation plus that
 // cell's half of the inner-cell term of Eq. (22) / (30).  A cell sums its four faces.
-// Returns this thread's count of depth clamps.
+// fmx / fmy (or null): every face's mass flux F_h(U^-) + D^-_h (its left cell's output)
+// into [ny][nx+1] / [ny+1][nx]; the faces a tile shares with its east / north neighbour
+// are written by that neighbour.  Returns this thread's count of depth clamps.
 template <typename T, int TX, int TY>
 __device__ __forceinline__ int
 hyp_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ q1,
           const T* __restrict__ q2, const T* __restrict__ etab, const T* __restrict__ q1b,
           const T* __restrict__ q2b, const T* __restrict__ H, T a, T b, T dt,
-          T* __restrict__ eo, T* __restrict__ q1o, T* __restrict__ q2o, int bx, int by)
+          T* __restrict__ eo, T* __restrict__ q1o, T* __restrict__ q2o, int bx, int by,
+          T* __restrict__ fmx = nullptr, T* __restrict__ fmy = nullptr)
 {
     constexpr int LW = TX + 4, LH = TY + 4, LN = LW * LH;
     constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
@@ -436,6 +439,20 @@ hyp_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ q1,
         face(L(f, r - 1), LW, sv, su, &CLy[0][t], &CRy[0][t], NFY);
     }
     __syncthreads();
+    if (fmx != nullptr) {
+        for (int t = tid; t < NFX; t += nt) {
+            const int f = t % (TX + 1), r = t / (TX + 1);
+            const int I = i0 + f, j = j0 + r;
+            if (j < P.ny && I <= P.nx && (f < TX || I == P.nx))
+                fmx[(size_t)j * (P.nx + 1) + I] = CLx[0][t];
+        }
+        for (int t = tid; t < NFY; t += nt) {
+            const int f = t % TX, r = t / TX;
+            const int i = i0 + f, J = j0 + r;
+            if (i < P.nx && J <= P.ny && (r < TY || J == P.ny))
+                fmy[(size_t)J * P.nx + i] = CLy[0][t];
+        }
+    }
     int nclamp = 0;
     const T rx = dt / P.dx, ry = dt / P.dy;
     const T fric = dt * g * P.manning * P.manning;

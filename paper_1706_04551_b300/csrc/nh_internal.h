@@ -77,6 +77,10 @@ struct Bufs {
     double *partials;             // per-block partial sums (>= 4 * nblk)
     SolveCtl *sctl;
     StepCtl *stctl;
+    // w equation (hw)_t + div(hw u) = p only (else null): face mass fluxes of the stage's
+    // hyperbolic step (x faces [ny][nx+1], y faces [ny+1][nx]; 1D: [rows][nx+1] in fmx)
+    // and the transported w*
+    T *fmx, *fmy, *wt;
 };
 
 struct Launch {
@@ -87,10 +91,20 @@ struct Launch {
 
 // ---- 2D ----
 // (the 2D correction writes p0 + dp into B.palt; the caller then swaps B.p and B.palt)
+// fmx / fmy (or null): the mass flux of every x / y face, F_h(U^-) + D^-_h from its
+// west / south cell ([ny][nx+1] and [ny+1][nx])
 template <typename T>
 void launch_hyp2d(const Prm<T>& P, const Launch& L, const T* eta, const T* q1, const T* q2,
                   const T* etab, const T* q1b, const T* q2b, const T* H, T a, T b, T dt,
-                  T* eo, T* q1o, T* q2o, StepCtl* st);
+                  T* eo, T* q1o, T* q2o, StepCtl* st, T* fmx = nullptr, T* fmy = nullptr);
+// w* of the w equation (hw)_t + div(hw u) = p at every node: hw moved on the node (dual)
+// cells with the face mass fluxes fmx / fmy of the stage's hyperbolic step (input state
+// etain, win), combined with the base state (etab, wb) as (hw)* = a h_b w_b + b (hw)**,
+// divided by the node depth of the combined state etas.
+template <typename T>
+void launch_wtrans2d(const Prm<T>& P, const Launch& L, const T* etab, const T* etain,
+                     const T* etas, const T* H, const T* wb, const T* win, const T* fmx,
+                     const T* fmy, T a, T b, T dt, T* wo);
 template <typename T>
 void launch_asm2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* w_in,
                   const T* w_base, T a, T b, T de, int with_coef, int resid_form, double tol2,
@@ -158,7 +172,13 @@ void launch_adj_cell_hyp(const Prm<T>& P, const Launch& L, const T* eta, const T
 // ---- batched 1D ----
 template <typename T>
 void launch_hyp1d(const Prm<T>& P, const Launch& L, const T* eta, const T* q, const T* etab,
-                  const T* qb, const T* H, T a, T b, T dt, T* eo, T* qo, StepCtl* st);
+                  const T* qb, const T* H, T a, T b, T dt, T* eo, T* qo, StepCtl* st,
+                  T* fm = nullptr);
+// 1D form of launch_wtrans2d (fm: [rows][nx+1] face mass fluxes)
+template <typename T>
+void launch_wtrans1d(const Prm<T>& P, const Launch& L, const T* etab, const T* etain,
+                     const T* etas, const T* H, const T* wb, const T* win, const T* fm, T a,
+                     T b, T dt, T* wo);
 template <typename T>
 void launch_break1d(const Prm<T>& P, const Launch& L, const T* eta, const T* q, const T* H,
                     T de, T* qo);

@@ -22,11 +22,87 @@ __global__ void __launch_bounds__(256)
 k_hyp2d_t(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ q1,
           const T* __restrict__ q2, const T* __restrict__ etab, const T* __restrict__ q1b,
           const T* __restrict__ q2b, const T* __restrict__ H, T a, T b, T dt,
-          T* __restrict__ eo, T* __restrict__ q1o, T* __restrict__ q2o, StepCtl* st)
+          T* __restrict__ eo, T* __restrict__ q1o, T* __restrict__ q2o, StepCtl* st,
+          T* __restrict__ fmx, T* __restrict__ fmy)
 {
     const int nclamp = hyp_tile<T, TX, TY>(P, eta, q1, q2, etab, q1b, q2b, H, a, b, dt, eo, q1o,
-                                           q2o, blockIdx.x, blockIdx.y);
+                                           q2o, blockIdx.x, blockIdx.y, fmx, fmy);
     if (nclamp) atomicAdd(&st->clamped, nclamp);
+}
+
+// Node depth of the w transport: the mean of the four cells around node (I, J), outside
+// cells mapped onto their wall / outflow images (the assembly's node depth).
+template <typename T>
+__device__ __forceinline__ T node_depth(const Prm<T>& P, const T* __restrict__ eta,
+                                        const T* __restrict__ H, int I, int J)
+{
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {   // (I-1, J-1), (I, J-1), (I-1, J), (I, J)
+        bool r;
+        const int ii = map_cell(I - 1 + (k & 1), P.nx, P.bcw, P.bce, r);
+        const int jj = map_cell(J - 1 + (k >> 1), P.ny, P.bcs, P.bcn, r);
+        const size_t m = (size_t)jj * P.nx + ii;
+        s = k == 0 ? tmax(eta[m] + H[m], T(0)) : s + tmax(eta[m] + H[m], T(0));
+    }
+    return T(0.25) * s;
+}
+
+// w* of the energy-consistent w equation (hw)_t + div(hw u) = p (Sec. 2, the system of
+// the paper's reference [7]) at node (I, J).  The node owns the dual cell [x_I - dx/2,
+// x_I + dx/2] x [y_J - dy/2, y_J + dy/2] clipped to the domain (area fraction ax * ay),
+// a quarter of each cell around it.  Its east face runs along the centre lines of the
+// cells (I, J-1), (I, J) inside the grid, through half of each, where the x mass flux is
+// the mean of the cell's two x-face fluxes; on the domain boundary the dual face is the
+// boundary face.  w is taken upwind (the node's own at boundary faces), and
+//   (hw)* = a h_b w_b + b (h w - dt div(F w)),   w* = (hw)* / h*  (desingularised),
+// with the node depths of the base, input and combined states.  Those dual fluxes move
+// the dual depth exactly as the cell depths move, so a uniform w stays uniform.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_wtrans2d(Prm<T> P, const T* __restrict__ etab, const T* __restrict__ etain,
+           const T* __restrict__ etas, const T* __restrict__ H, const T* __restrict__ wb,
+           const T* __restrict__ win, const T* __restrict__ fmx, const T* __restrict__ fmy,
+           T a, T b, T dt, T* __restrict__ wo)
+{
+    const T d2 = P.delta * P.delta, d4 = d2 * d2;
+    const int nx = P.nx, ny = P.ny, nxn = nx + 1;
+    GRID_STRIDE(idx, (long long)nxn * (ny + 1))
+    {
+        const int I = (int)(idx % nxn), J = (int)(idx / nxn);
+        // cs[d]: x-face fluxes of face column I-1+d over the cell rows J-1, J inside;
+        // rs[d]: y-face fluxes of face row J-1+d over the cell columns I-1, I inside
+        T cs[3], rs[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int If = I - 1 + d, Jf = J - 1 + d;
+            T c = T(0), r = T(0);
+            if (If >= 0 && If <= nx) {
+                if (J >= 1) c = fmx[(size_t)(J - 1) * nxn + If];
+                if (J < ny) c = c + fmx[(size_t)J * nxn + If];
+            }
+            if (Jf >= 0 && Jf <= ny) {
+                if (I >= 1) r = fmy[(size_t)Jf * nx + I - 1];
+                if (I < nx) r = r + fmy[(size_t)Jf * nx + I];
+            }
+            cs[d] = c;
+            rs[d] = r;
+        }
+        const T FE = I == nx ? T(0.5) * cs[1] : T(0.25) * (cs[1] + cs[2]);
+        const T FW = I == 0 ? T(0.5) * cs[1] : T(0.25) * (cs[0] + cs[1]);
+        const T FN = J == ny ? T(0.5) * rs[1] : T(0.25) * (rs[1] + rs[2]);
+        const T FS = J == 0 ? T(0.5) * rs[1] : T(0.25) * (rs[0] + rs[1]);
+        const T wc = win[idx];
+        const T wE = I == nx ? wc : (FE > T(0) ? wc : win[idx + 1]);
+        const T wW = I == 0 ? wc : (FW > T(0) ? win[idx - 1] : wc);
+        const T wN = J == ny ? wc : (FN > T(0) ? wc : win[idx + nxn]);
+        const T wS = J == 0 ? wc : (FS > T(0) ? win[idx - nxn] : wc);
+        const T area = ((I == 0 || I == nx) ? T(0.5) : T(1)) * ((J == 0 || J == ny) ? T(0.5) : T(1));
+        const T m = area * node_depth(P, etain, H, I, J) * wc
+                  - dt / P.dx * (FE * wE - FW * wW) - dt / P.dy * (FN * wN - FS * wS);
+        const T hw = a * node_depth(P, etab, H, I, J) * wb[idx] + b * m / area;
+        wo[idx] = hw * desing(node_depth(P, etas, H, I, J), T(1), d4);
+    }
 }
 
 template <typename T, int TX, int TY>
@@ -338,7 +414,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_hyp1d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ q,
         const T* __restrict__ etab, const T* __restrict__ qb, const T* __restrict__ H, T a,
-        T b, T dt, T* __restrict__ eo, T* __restrict__ qo, StepCtl* st)
+        T b, T dt, T* __restrict__ eo, T* __restrict__ qo, StepCtl* st, T* __restrict__ fm)
 {
     const T d2 = P.delta * P.delta, d4 = d2 * d2;
     const T g = P.g, hdry = P.hdry;
@@ -357,6 +433,11 @@ k_hyp1d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ q,
         pvm(g, sg, hdry, hi[0].h, hi[0].e, hi[0].u, T(0), lo[1].h, lo[1].e, lo[1].u, T(0), DmW, DpW);
         pvm(g, sg, hdry, hi[1].h, hi[1].e, hi[1].u, T(0), lo[2].h, lo[2].e, lo[2].u, T(0), DmE, DpE);
         const St<T>& E = hi[1]; const St<T>& W = lo[1];
+        if (fm != nullptr) {   // face mass fluxes F_h(U^-) + D^-_h (the w transport's)
+            const size_t f = (size_t)row * (P.nx + 1) + i;
+            fm[f] = hi[0].h * hi[0].u + DmW[0];
+            if (i == P.nx - 1) fm[f + 1] = E.h * E.u + DmE[0];
+        }
         const T hc = cx[2].h;
         T I0 = E.h * E.u - W.h * W.u;
         T I1 = E.h * E.u * E.u - W.h * W.u * W.u + g * hc * (E.e - W.e);
@@ -379,6 +460,47 @@ k_hyp1d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ q,
         eo[c] = en; qo[c] = qn;
     }
     if (nclamp) atomicAdd(&st->clamped, nclamp);
+}
+
+// 1D form of k_wtrans2d: node k of a channel owns the dual cell between the centres of
+// cells k-1 and k (its inner half at a wall or outflow end); the dual faces carry the
+// mean of a cell's two face mass fluxes (the boundary face at an end).  Periodic
+// channels wrap (node nx is node 0).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_wtrans1d(Prm<T> P, const T* __restrict__ etab, const T* __restrict__ etain,
+           const T* __restrict__ etas, const T* __restrict__ H, const T* __restrict__ wb,
+           const T* __restrict__ win, const T* __restrict__ fm, T a, T b, T dt,
+           T* __restrict__ wo)
+{
+    const T d2 = P.delta * P.delta, d4 = d2 * d2;
+    const int n = P.nx, nn = n + 1;
+    const bool per = P.bcw == 2;
+    GRID_STRIDE(idx, (long long)nn * P.ny)
+    {
+        const int row = (int)(idx / nn), ko = (int)(idx % nn);
+        const int k = per && ko == n ? 0 : ko;   // periodic: node n is node 0
+        const T* F = fm + (size_t)row * nn;
+        const T* w = win + (size_t)row * nn;
+        const size_t c0 = (size_t)row * n;
+        auto depth = [&](const T* e) {   // mean of the cells k-1 and k (mapped)
+            bool r;
+            const int il = map_cell(k - 1, n, P.bcw, P.bce, r);
+            const int ir = map_cell(k, n, P.bcw, P.bce, r);
+            return T(0.5) * (tmax(e[c0 + il] + H[c0 + il], T(0)) +
+                             tmax(e[c0 + ir] + H[c0 + ir], T(0)));
+        };
+        const bool west_end = !per && k == 0, east_end = !per && k == n;
+        const T area = (west_end || east_end) ? T(0.5) : T(1);
+        const int kw = k == 0 ? n - 1 : k - 1;
+        const T FE = east_end ? F[n] : T(0.5) * (F[k] + F[k + 1]);
+        const T FW = west_end ? F[0] : T(0.5) * (F[kw] + F[kw + 1]);
+        const T wE = east_end ? w[k] : (FE > T(0) ? w[k] : w[k + 1]);
+        const T wW = west_end ? w[k] : (FW > T(0) ? w[kw] : w[k]);
+        const T m = area * depth(etain) * w[k] - dt / P.dx * (FE * wE - FW * wW);
+        const T hw = a * depth(etab) * wb[(size_t)row * nn + k] + b * m / area;
+        wo[idx] = hw * desing(depth(etas), T(1), d4);
+    }
 }
 
 // 1D breaking terms at cells: q += de 2 nu u_x H_x (centred differences, Sec. 4.3).
@@ -736,12 +858,21 @@ int resident_grid(K kernel, int threads, size_t smem)
 template <typename T>
 void launch_hyp2d(const Prm<T>& P, const Launch& L, const T* eta, const T* q1, const T* q2,
                   const T* etab, const T* q1b, const T* q2b, const T* H, T a, T b, T dt,
-                  T* eo, T* q1o, T* q2o, StepCtl* st)
+                  T* eo, T* q1o, T* q2o, StepCtl* st, T* fmx, T* fmy)
 {
     constexpr int TX = 32, TY = sizeof(T) == 4 ? 16 : 8;
     dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
     k_hyp2d_t<T, TX, TY><<<grid, kThreads, 0, L.s>>>(P, eta, q1, q2, etab, q1b, q2b, H, a, b, dt,
-                                                    eo, q1o, q2o, st);
+                                                    eo, q1o, q2o, st, fmx, fmy);
+}
+
+template <typename T>
+void launch_wtrans2d(const Prm<T>& P, const Launch& L, const T* etab, const T* etain,
+                     const T* etas, const T* H, const T* wb, const T* win, const T* fmx,
+                     const T* fmy, T a, T b, T dt, T* wo)
+{
+    k_wtrans2d<T><<<L.nblk, kThreads, 0, L.s>>>(P, etab, etain, etas, H, wb, win, fmx, fmy, a, b,
+                                                dt, wo);
 }
 
 template <typename T>
@@ -914,9 +1045,18 @@ void launch_corr2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* 
 
 template <typename T>
 void launch_hyp1d(const Prm<T>& P, const Launch& L, const T* eta, const T* q, const T* etab,
-                  const T* qb, const T* H, T a, T b, T dt, T* eo, T* qo, StepCtl* st)
+                  const T* qb, const T* H, T a, T b, T dt, T* eo, T* qo, StepCtl* st, T* fm)
 {
-    k_hyp1d<T><<<L.nblk, kThreads, 0, L.s>>>(P, eta, q, etab, qb, H, a, b, dt, eo, qo, st);
+    k_hyp1d<T><<<L.nblk, kThreads, 0, L.s>>>(P, eta, q, etab, qb, H, a, b, dt, eo, qo, st, fm);
+}
+
+template <typename T>
+void launch_wtrans1d(const Prm<T>& P, const Launch& L, const T* etab, const T* etain,
+                     const T* etas, const T* H, const T* wb, const T* win, const T* fm, T a,
+                     T b, T dt, T* wo)
+{
+    k_wtrans1d<T><<<L.nblk, kThreads, 0, L.s>>>(P, etab, etain, etas, H, wb, win, fm, a, b, dt,
+                                                wo);
 }
 
 template <typename T>
@@ -1041,7 +1181,13 @@ void launch_convert_from_double(const Launch& L, const double* src, T* dst, size
 #define NH_INSTANTIATE(T)                                                                       \
     template void launch_hyp2d<T>(const Prm<T>&, const Launch&, const T*, const T*, const T*,  \
                                   const T*, const T*, const T*, const T*, T, T, T, T*, T*, T*, \
-                                  StepCtl*);                                                   \
+                                  StepCtl*, T*, T*);                                           \
+    template void launch_wtrans2d<T>(const Prm<T>&, const Launch&, const T*, const T*,         \
+                                     const T*, const T*, const T*, const T*, const T*,         \
+                                     const T*, T, T, T, T*);                                   \
+    template void launch_wtrans1d<T>(const Prm<T>&, const Launch&, const T*, const T*,         \
+                                     const T*, const T*, const T*, const T*, const T*, T, T,   \
+                                     T, T*);                                                   \
     template void launch_asm2d<T>(const Prm<T>&, const Launch&, const Bufs<T>&, const T*,      \
                                   const T*, T, T, T, int, int, double, int, int, double*,      \
                                   SolveCtl*, int);                                             \
@@ -1059,7 +1205,7 @@ void launch_convert_from_double(const Launch& L, const double* src, T* dst, size
     template void launch_corr2d<T>(const Prm<T>&, const Launch&, const Bufs<T>&, const T*,     \
                                    const T*, T, int, T*, T*, T*, T*, int, double*, StepCtl*);  \
     template void launch_hyp1d<T>(const Prm<T>&, const Launch&, const T*, const T*, const T*,  \
-                                  const T*, const T*, T, T, T, T*, T*, StepCtl*);              \
+                                  const T*, const T*, T, T, T, T*, T*, StepCtl*, T*);          \
     template void launch_break1d<T>(const Prm<T>&, const Launch&, const T*, const T*, const T*,\
                                     T, T*);                                                    \
     template void launch_asm1d<T>(const Prm<T>&, const Launch&, const Bufs<T>&, const T*,      \

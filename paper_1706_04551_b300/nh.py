@@ -20,6 +20,7 @@ WALL, OUTFLOW, PERIODIC = 0, 1, 2
 BICGSTAB, CHEBYSHEV = 0, 1
 FP64, FP32 = 0, 1
 HOST, DEVICE = 0, 1
+W_YAMAZAKI, W_TRANSPORT = 0, 1   # w equation: h w_t = p, or (hw)_t + div(hw u) = p
 
 
 class Grid(C.Structure):
@@ -33,7 +34,8 @@ class Params(C.Structure):
                 ("B2", C.c_double), ("breaking", C.c_int), ("nonhydrostatic", C.c_int),
                 ("solver", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int),
                 ("precision", C.c_int), ("fixed_dt", C.c_double), ("eps_dp", C.c_double),
-                ("adjoint_frozen_limiter", C.c_int), ("cheb_form", C.c_int)]
+                ("adjoint_frozen_limiter", C.c_int), ("cheb_form", C.c_int),
+                ("w_equation", C.c_int)]
 
 
 class StatsT(C.Structure):
@@ -72,7 +74,7 @@ BATCH_AUTOTUNE, BATCH_GRAPH = 1, 2
 # kernel classes of nh_profile_t, in enum order
 KERNELS = ("hyperbolic", "breaking", "assembly", "solve_init", "bicg_A", "bicg_B", "bicg_C",
            "cheb_pass", "tridiag", "correction", "adj_hyperbolic", "adj_assembly",
-           "adj_correction")
+           "adj_correction", "w_transport")
 
 
 class ProfileT(C.Structure):

@@ -109,3 +109,20 @@ def test_batch_candidates_listed():
         assert all(len(c[k]) >= 2 for k in ("hyp", "assembly", "cheb"))
         for tx, ty, th in c["cheb"]:
             assert tx > 16 and ty > 16 and th in (256, 512, 1024)
+
+
+def test_w_equation_default_and_bad_value_rejected_without_touching_the_gpu():
+    import numpy as np
+    B.build()
+    L = nh.load()
+    p = nh.default_params()
+    assert p.w_equation == nh.W_YAMAZAKI
+    g = nh.Grid()
+    g.dim, g.nx, g.ny, g.dx, g.dy = 2, 8, 8, 0.1, 0.1
+    H = np.ones(64)
+    for bad in (2, -1):
+        p.w_equation = bad
+        h = ctypes.c_void_p()
+        rc = L.nh_create(ctypes.byref(g), H.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                         ctypes.byref(p), None, ctypes.byref(h))
+        assert rc == nh.EINVAL and not h.value
