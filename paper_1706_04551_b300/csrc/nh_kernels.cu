@@ -30,78 +30,117 @@ k_hyp2d_t(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ q1,
     if (nclamp) atomicAdd(&st->clamped, nclamp);
 }
 
-// Node depth of the w transport: the mean of the four cells around node (I, J), outside
-// cells mapped onto their wall / outflow images (the assembly's node depth).
-template <typename T>
-__device__ __forceinline__ T node_depth(const Prm<T>& P, const T* __restrict__ eta,
-                                        const T* __restrict__ H, int I, int J)
-{
-    T s = T(0);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {   // (I-1, J-1), (I, J-1), (I-1, J), (I, J)
-        bool r;
-        const int ii = map_cell(I - 1 + (k & 1), P.nx, P.bcw, P.bce, r);
-        const int jj = map_cell(J - 1 + (k >> 1), P.ny, P.bcs, P.bcn, r);
-        const size_t m = (size_t)jj * P.nx + ii;
-        s = k == 0 ? tmax(eta[m] + H[m], T(0)) : s + tmax(eta[m] + H[m], T(0));
-    }
-    return T(0.25) * s;
-}
-
 // w* of the energy-consistent w equation (hw)_t + div(hw u) = p (Sec. 2, the system of
-// the paper's reference [7]) at node (I, J).  The node owns the dual cell [x_I - dx/2,
-// x_I + dx/2] x [y_J - dy/2, y_J + dy/2] clipped to the domain (area fraction ax * ay),
-// a quarter of each cell around it.  Its east face runs along the centre lines of the
-// cells (I, J-1), (I, J) inside the grid, through half of each, where the x mass flux is
-// the mean of the cell's two x-face fluxes; on the domain boundary the dual face is the
-// boundary face.  w is taken upwind (the node's own at boundary faces), and
+// the paper's reference [7]) for a TX x TY tile of nodes.  Node (I, J) owns the dual cell
+// [x_I - dx/2, x_I + dx/2] x [y_J - dy/2, y_J + dy/2] clipped to the domain (area fraction
+// ax * ay), a quarter of each cell around it.  Its east face runs along the centre lines
+// of the cells (I, J-1), (I, J) inside the grid, through half of each, where the x mass
+// flux is the mean of the cell's two x-face fluxes; on the domain boundary the dual face
+// is the boundary face.  w is taken upwind (the node's own at boundary faces), and
 //   (hw)* = a h_b w_b + b (h w - dt div(F w)),   w* = (hw)* / h*  (desingularised),
-// with the node depths of the base, input and combined states.  Those dual fluxes move
-// the dual depth exactly as the cell depths move, so a uniform w stays uniform.
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_wtrans2d(Prm<T> P, const T* __restrict__ etab, const T* __restrict__ etain,
-           const T* __restrict__ etas, const T* __restrict__ H, const T* __restrict__ wb,
-           const T* __restrict__ win, const T* __restrict__ fmx, const T* __restrict__ fmy,
-           T a, T b, T dt, T* __restrict__ wo)
+// with the node depths (mean of the four cells, outside cells mapped onto their wall /
+// outflow images) of the base, input and combined states.  Those dual fluxes move the
+// dual depth exactly as the cell depths move, so a uniform w stays uniform.  The block
+// stages the depths of the cells around the tile, the face fluxes next to it and w of
+// the tile with a 1-node ring.
+template <typename T, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT)
+k_wtrans2d_t(Prm<T> P, const T* __restrict__ etab, const T* __restrict__ etain,
+             const T* __restrict__ etas, const T* __restrict__ H, const T* __restrict__ wb,
+             const T* __restrict__ win, const T* __restrict__ fmx, const T* __restrict__ fmy,
+             T a, T b, T dt, T* __restrict__ wo)
 {
+    constexpr int CW = TX + 1, CN = CW * (TY + 1);          // cells I0-1.., J0-1..
+    constexpr int XW = TX + 2, XN = XW * (TY + 1);          // x faces I0-1..I0+TX
+    constexpr int YW = TX + 1, YN = YW * (TY + 2);          // y faces J0-1..J0+TY
+    constexpr int WW = TX + 2, WN = WW * (TY + 2);          // nodes with a 1-node ring
+    // every thread stages at most NS entries of each array and issues all its loads
+    // before the first store, so the block waits on one round of memory latency
+    constexpr int NS = (WN + NT - 1) / NT;
+    static_assert(CN <= NS * NT && XN <= NS * NT && YN <= NS * NT, "staging slots");
+    static_assert((TX * TY) % NT == 0, "whole nodes per thread");
+    __shared__ T hB[CN], hI[CN], hS[CN], sx[XN], sy[YN], sw[WN];
     const T d2 = P.delta * P.delta, d4 = d2 * d2;
     const int nx = P.nx, ny = P.ny, nxn = nx + 1;
-    GRID_STRIDE(idx, (long long)nxn * (ny + 1))
-    {
-        const int I = (int)(idx % nxn), J = (int)(idx / nxn);
-        // cs[d]: x-face fluxes of face column I-1+d over the cell rows J-1, J inside;
-        // rs[d]: y-face fluxes of face row J-1+d over the cell columns I-1, I inside
+    const int I0 = blockIdx.x * TX, J0 = blockIdx.y * TY;
+    const int tid = threadIdx.x;
+    T vb[NS], vi[NS], vs[NS], vh[NS], vx[NS], vy[NS], vw[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+        const int t = tid + k * NT;
+        vb[k] = vi[k] = vs[k] = vh[k] = vx[k] = vy[k] = vw[k] = T(0);
+        if (t < CN) {
+            int ci = I0 - 1 + t % CW, cj = J0 - 1 + t / CW;
+            ci = ci > nx ? nx : ci;   // beyond the first ghost: feeds no node of the tile
+            cj = cj > ny ? ny : cj;
+            bool r;
+            const int ii = map_cell(ci, nx, P.bcw, P.bce, r);
+            const int jj = map_cell(cj, ny, P.bcs, P.bcn, r);
+            const size_t m = (size_t)jj * nx + ii;
+            vh[k] = H[m]; vb[k] = etab[m]; vi[k] = etain[m]; vs[k] = etas[m];
+        }
+        if (t < XN) {   // faces outside the grid carry nothing
+            const int If = I0 - 1 + t % XW, j = J0 - 1 + t / XW;
+            if (If >= 0 && If <= nx && j >= 0 && j < ny) vx[k] = fmx[(size_t)j * nxn + If];
+        }
+        if (t < YN) {
+            const int i = I0 - 1 + t % YW, Jf = J0 - 1 + t / YW;
+            if (i >= 0 && i < nx && Jf >= 0 && Jf <= ny) vy[k] = fmy[(size_t)Jf * nx + i];
+        }
+        if (t < WN) {
+            const int I = I0 - 1 + t % WW, J = J0 - 1 + t / WW;
+            if (I >= 0 && I <= nx && J >= 0 && J <= ny) vw[k] = win[(size_t)J * nxn + I];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+        const int t = tid + k * NT;
+        if (t < CN) {
+            hB[t] = tmax(vb[k] + vh[k], T(0));
+            hI[t] = tmax(vi[k] + vh[k], T(0));
+            hS[t] = tmax(vs[k] + vh[k], T(0));
+        }
+        if (t < XN) sx[t] = vx[k];
+        if (t < YN) sy[t] = vy[k];
+        if (t < WN) sw[t] = vw[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < TX * TY / NT; ++r) {
+        const int li = tid % TX, lj = tid / TX + r * (NT / TX);
+        const int I = I0 + li, J = J0 + lj;
+        if (I > nx || J > ny) continue;
+        // cells (I-1, J-1), (I, J-1), (I-1, J), (I, J) at ka, ka + 1, ka + CW, ka + CW + 1
+        const int ka = lj * CW + li;
+        auto depth = [&](const T* h) {
+            return T(0.25) * (((h[ka] + h[ka + 1]) + h[ka + CW]) + h[ka + CW + 1]);
+        };
+        // column sums of the x faces I-1+d over the cell rows J-1, J; row sums of the y
+        // faces J-1+d over the cell columns I-1, I
+        const int xa = lj * XW + li, ya = lj * YW + li;
         T cs[3], rs[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const int If = I - 1 + d, Jf = J - 1 + d;
-            T c = T(0), r = T(0);
-            if (If >= 0 && If <= nx) {
-                if (J >= 1) c = fmx[(size_t)(J - 1) * nxn + If];
-                if (J < ny) c = c + fmx[(size_t)J * nxn + If];
-            }
-            if (Jf >= 0 && Jf <= ny) {
-                if (I >= 1) r = fmy[(size_t)Jf * nx + I - 1];
-                if (I < nx) r = r + fmy[(size_t)Jf * nx + I];
-            }
-            cs[d] = c;
-            rs[d] = r;
+            cs[d] = sx[xa + d] + sx[xa + XW + d];
+            rs[d] = sy[ya + d * YW] + sy[ya + d * YW + 1];
         }
         const T FE = I == nx ? T(0.5) * cs[1] : T(0.25) * (cs[1] + cs[2]);
         const T FW = I == 0 ? T(0.5) * cs[1] : T(0.25) * (cs[0] + cs[1]);
         const T FN = J == ny ? T(0.5) * rs[1] : T(0.25) * (rs[1] + rs[2]);
         const T FS = J == 0 ? T(0.5) * rs[1] : T(0.25) * (rs[0] + rs[1]);
-        const T wc = win[idx];
-        const T wE = I == nx ? wc : (FE > T(0) ? wc : win[idx + 1]);
-        const T wW = I == 0 ? wc : (FW > T(0) ? win[idx - 1] : wc);
-        const T wN = J == ny ? wc : (FN > T(0) ? wc : win[idx + nxn]);
-        const T wS = J == 0 ? wc : (FS > T(0) ? win[idx - nxn] : wc);
-        const T area = ((I == 0 || I == nx) ? T(0.5) : T(1)) * ((J == 0 || J == ny) ? T(0.5) : T(1));
-        const T m = area * node_depth(P, etain, H, I, J) * wc
-                  - dt / P.dx * (FE * wE - FW * wW) - dt / P.dy * (FN * wN - FS * wS);
-        const T hw = a * node_depth(P, etab, H, I, J) * wb[idx] + b * m / area;
-        wo[idx] = hw * desing(node_depth(P, etas, H, I, J), T(1), d4);
+        const int wc_i = (lj + 1) * WW + li + 1;
+        const T wc = sw[wc_i];
+        const T wE = I == nx ? wc : (FE > T(0) ? wc : sw[wc_i + 1]);
+        const T wW = I == 0 ? wc : (FW > T(0) ? sw[wc_i - 1] : wc);
+        const T wN = J == ny ? wc : (FN > T(0) ? wc : sw[wc_i + WW]);
+        const T wS = J == 0 ? wc : (FS > T(0) ? sw[wc_i - WW] : wc);
+        const T area = ((I == 0 || I == nx) ? T(0.5) : T(1)) *
+                       ((J == 0 || J == ny) ? T(0.5) : T(1));
+        const size_t idx = (size_t)J * nxn + I;
+        const T m = area * depth(hI) * wc - dt / P.dx * (FE * wE - FW * wW)
+                  - dt / P.dy * (FN * wN - FS * wS);
+        const T hw = a * depth(hB) * wb[idx] + b * m / area;
+        wo[idx] = hw * desing(depth(hS), T(1), d4);
     }
 }
 
@@ -462,7 +501,7 @@ k_hyp1d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ q,
     if (nclamp) atomicAdd(&st->clamped, nclamp);
 }
 
-// 1D form of k_wtrans2d: node k of a channel owns the dual cell between the centres of
+// 1D form of k_wtrans2d_t: node k of a channel owns the dual cell between the centres of
 // cells k-1 and k (its inner half at a wall or outflow end); the dual faces carry the
 // mean of a cell's two face mass fluxes (the boundary face at an end).  Periodic
 // channels wrap (node nx is node 0).
@@ -871,8 +910,10 @@ void launch_wtrans2d(const Prm<T>& P, const Launch& L, const T* etab, const T* e
                      const T* etas, const T* H, const T* wb, const T* win, const T* fmx,
                      const T* fmy, T a, T b, T dt, T* wo)
 {
-    k_wtrans2d<T><<<L.nblk, kThreads, 0, L.s>>>(P, etab, etain, etas, H, wb, win, fmx, fmy, a, b,
-                                                dt, wo);
+    constexpr int TX = 32, TY = 16, NT = 256;
+    dim3 grid((P.nx + 1 + TX - 1) / TX, (P.ny + 1 + TY - 1) / TY);
+    k_wtrans2d_t<T, TX, TY, NT><<<grid, NT, 0, L.s>>>(P, etab, etain, etas, H, wb, win, fmx,
+                                                       fmy, a, b, dt, wo);
 }
 
 template <typename T>
