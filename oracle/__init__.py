@@ -10,7 +10,8 @@ Parity status: every function is pinned by ``tests/test_oracle_*.py`` except the
 terms (Sec. 3, Eq. 12), which are "parity unpinned" beyond invariants (lake at rest with
 breaking on, the switch-off limit, dissipation).  ``cfg(w_transport=True)`` selects the
 energy-consistent w equation of Sec. 2 (pinned by donor-cell upwind on uniform flow and
-by invariants).
+by invariants); ``relax_1d`` / ``relax_2d`` and ``cfg(relax=...)`` the relaxation zones of
+Sec. 4.4 (pinned by their end values, special distances and wave absorption / generation).
 """
 from __future__ import annotations
 
@@ -41,6 +42,7 @@ class Cfg(C.Structure):
         ("breaking", C.c_int), ("nonhydro", C.c_int),
         ("tol", C.c_double), ("max_iter", C.c_int),
         ("w_transport", C.c_int),
+        ("relax", C.c_double * 4),
     ]
 
 
@@ -89,6 +91,8 @@ def lib():
         L.or2d_rhs.argtypes = [cp, dp, dp, dp, dp, dp, C.c_double, dp]
         L.or2d_apply_M.argtypes = [cp, dp, dp, dp, C.c_double, dp]
         L.or2d_solve.argtypes = [cp, dp, dp, dp, C.c_double, dp, C.POINTER(C.c_int), dp]
+        L.or1d_relax.argtypes = [cp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
+        L.or2d_relax.argtypes = [cp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
         L.or2d_run.restype = C.c_longlong
         L.or2d_run.argtypes = [cp, dp, dp, dp, dp, dp, dp, C.c_double, C.c_longlong,
                                C.c_double, dp, C.POINTER(C.c_longlong)]
@@ -109,7 +113,7 @@ def cfg(nx: int, ny: int = 1, dx: float = 1.0, dy: float | None = None, bc=(WALL
         g: float = 9.81, cfl: float = 0.9, delta: float = 1e-5, hdry: float | None = None,
         manning: float = 0.0, B1: float = 0.15, B2: float = 0.5, breaking: bool = False,
         nonhydro: bool = True, tol: float = 1e-13, max_iter: int = 4000,
-        w_transport: bool = False) -> Cfg:
+        w_transport: bool = False, relax=(0.0, 0.0, 0.0, 0.0)) -> Cfg:
     c = Cfg()
     c.nx, c.ny = int(nx), int(ny)
     c.dx = float(dx)
@@ -122,6 +126,8 @@ def cfg(nx: int, ny: int = 1, dx: float = 1.0, dy: float | None = None, bc=(WALL
     c.breaking, c.nonhydro = int(bool(breaking)), int(bool(nonhydro))
     c.tol, c.max_iter = float(tol), int(max_iter)
     c.w_transport = int(bool(w_transport))
+    for k in range(4):
+        c.relax[k] = float(relax[k])
     return c
 
 
@@ -264,3 +270,27 @@ def run_2d(c: Cfg, H, h, q1, q2, w, p, t_end: float = 0.0, max_steps: int = 1 <<
     s = lib().or2d_run(C.byref(c), _p(H), _p(h), _p(q1), _p(q2), _p(w), _p(p), float(t_end),
                        int(max_steps), float(fixed_dt), C.byref(t), C.byref(it))
     return h, q1, q2, w, p, t.value, s, it.value
+
+
+def _opt(a):
+    return None if a is None else _p(a)
+
+
+def relax_1d(c: Cfg, H, h, q, w, p, eta_t=None, q_t=None, w_t=None, p_t=None):
+    """Sec. 4.4 relaxation zones (widths c.relax) toward the target; None = lake at rest."""
+    H = _f64(H)
+    h, q, w, p = (_f64(a).copy() for a in (h, q, w, p))
+    tg = [None if a is None else _f64(a) for a in (eta_t, q_t, w_t, p_t)]
+    lib().or1d_relax(C.byref(c), _p(H), _p(h), _p(q), _p(w), _p(p), *[_opt(a) for a in tg])
+    return h, q, w, p
+
+
+def relax_2d(c: Cfg, H, h, q1, q2, w, p, eta_t=None, q1_t=None, q2_t=None, w_t=None,
+             p_t=None):
+    """Sec. 4.4 relaxation zones on the four sides (m = m_x m_y) toward the target."""
+    H = _f64(H)
+    h, q1, q2, w, p = (_f64(a).copy() for a in (h, q1, q2, w, p))
+    tg = [None if a is None else _f64(a) for a in (eta_t, q1_t, q2_t, w_t, p_t)]
+    lib().or2d_relax(C.byref(c), _p(H), _p(h), _p(q1), _p(q2), _p(w), _p(p),
+                     *[_opt(a) for a in tg])
+    return h, q1, q2, w, p

@@ -51,6 +51,11 @@
  *     says the scheme extends to it, without a discretisation): hw is moved on the node
  *     (dual) cells by the hyperbolic step's face mass fluxes, upwind in w, and the
  *     Runge-Kutta combination acts on hw (wtransport1d / wtransport2d).
+ *   - Relaxation zones (Sec. 4.4): each zone is the k + 1 cells nearest its boundary, the
+ *     distance in m is measured from the zone's inner cell on both sides (the paper's two
+ *     index sets disagree), m is clamped at 0, overlapping zones multiply, the absorbing
+ *     target is the lake at rest (eta* = max(H, 0) - H, not h* = 0), and the blend acts on
+ *     the state after each whole time step (relax_m1, or1d_relax, or2d_relax).
  */
 #include "nh_oracle.h"
 
@@ -176,6 +181,68 @@ static void ghost1d(const or_cfg *c, int n, double *v, double parity)
 }
 
 static int periodic1d(const or_cfg *c) { return c->bc[0] == OR_PERIODIC; }
+
+/* Relaxation coefficient of Sec. 4.4 for cell i (0-based) of a line of n cells of size d,
+ * with zone widths Llo (low side) and Lhi (high side); 1 outside both zones.  k is the
+ * first natural number with k d >= L; m = sqrt(1 - (dist / L)^2), clamped at 0.
+ * Reading (the paper lists the zone cells as {1..k} on the left, measuring the distance
+ * from I_1, and {N-k..N} on the right, measuring it from I_{N-k}; the two disagree, and
+ * the left form would leave the boundary cell unrelaxed): each zone is the k + 1 cells
+ * nearest its boundary and dist is measured from the zone's inner cell, so m = 1 there
+ * and m = 0 at the boundary cell, on both sides.  Where zones overlap the two factors
+ * multiply (the two blends applied one after the other). */
+static int relax_k(double L, double d)
+{
+    int k = 0;
+    while ((double)k * d < L) ++k;
+    return k;
+}
+static double relax_m1(int i, int n, double d, double Llo, double Lhi)
+{
+    double m = 1.0;
+    if (Llo > 0.0) {
+        int k = relax_k(Llo, d);
+        if (i <= k) {
+            double r = (double)(k - i) * d / Llo, v = 1.0 - r * r;
+            m *= v > 0.0 ? sqrt(v) : 0.0;
+        }
+    }
+    if (Lhi > 0.0) {
+        int k = relax_k(Lhi, d);
+        if (i >= n - 1 - k) {
+            double r = (double)(i - (n - 1 - k)) * d / Lhi, v = 1.0 - r * r;
+            m *= v > 0.0 ? sqrt(v) : 0.0;
+        }
+    }
+    return m;
+}
+/* Node coefficient m_{i-1/2} = (m_{i-1} + m_i) / 2 for node I between cells I-1 and I
+ * (Sec. 4.4); the cell beyond an end takes the end cell's m. */
+static double relax_node1(int I, int n, double d, double Llo, double Lhi)
+{
+    int a = I - 1 < 0 ? 0 : I - 1, b = I > n - 1 ? n - 1 : I;
+    return 0.5 * (relax_m1(a, n, d, Llo, Lhi) + relax_m1(b, n, d, Llo, Lhi));
+}
+
+void or1d_relax(const or_cfg *c, const double *H, double *h, double *q, double *w, double *p,
+                const double *eta_t, const double *q_t, const double *w_t, const double *p_t)
+{
+    const int n = c->nx;
+    for (int i = 0; i < n; ++i) {
+        double m = relax_m1(i, n, c->dx, c->relax[0], c->relax[1]);
+        if (m == 1.0) continue;
+        double hs = eta_t ? eta_t[i] + H[i] : (H[i] > 0.0 ? H[i] : 0.0);
+        if (hs < 0.0) hs = 0.0;
+        h[i] = m * h[i] + (1.0 - m) * hs;
+        q[i] = m * q[i] + (1.0 - m) * (q_t ? q_t[i] : 0.0);
+    }
+    for (int I = 0; I <= n; ++I) {
+        double m = relax_node1(I, n, c->dx, c->relax[0], c->relax[1]);
+        if (m == 1.0) continue;
+        w[I] = m * w[I] + (1.0 - m) * (w_t ? w_t[I] : 0.0);
+        p[I] = m * p[I] + (1.0 - m) * (p_t ? p_t[I] : 0.0);
+    }
+}
 
 double or1d_cfl_dt(const or_cfg *c, const double *H, const double *h, const double *q)
 {
@@ -579,6 +646,8 @@ long long or1d_run(const or_cfg *c, const double *H, double *h, double *q, doubl
         if (!(dt > 0.0)) break;
         if (t_end > 0.0 && t + dt > t_end) dt = t_end - t;
         or1d_step(c, H, h, q, w, p, dt, NULL);
+        if (c->relax[0] > 0.0 || c->relax[1] > 0.0)
+            or1d_relax(c, H, h, q, w, p, NULL, NULL, NULL, NULL);
         t += dt;
         ++s;
     }
@@ -1228,6 +1297,8 @@ long long or2d_run(const or_cfg *c, const double *H, double *h, double *q1, doub
         if (t_end > 0.0 && t + dt > t_end) dt = t_end - t;
         or_stats st;
         or2d_step(c, H, h, q1, q2, w, p, dt, &st);
+        if (c->relax[0] > 0.0 || c->relax[1] > 0.0 || c->relax[2] > 0.0 || c->relax[3] > 0.0)
+            or2d_relax(c, H, h, q1, q2, w, p, NULL, NULL, NULL, NULL, NULL);
         it += st.iters[0] + st.iters[1];
         t += dt;
         ++s;
@@ -1235,4 +1306,35 @@ long long or2d_run(const or_cfg *c, const double *H, double *h, double *q1, doub
     if (t_out) *t_out = t;
     if (iters_total) *iters_total = it;
     return s;
+}
+
+/* 2D relaxation zones (Sec. 4.4 on each side): m(i, j) = m_x(i) m_y(j) at cells, the
+ * product of the node means m_x(I - 1/2) m_y(J - 1/2) at nodes (the x and y blends applied
+ * one after the other); see or1d_relax. */
+void or2d_relax(const or_cfg *c, const double *H, double *h, double *q1, double *q2,
+                double *w, double *p, const double *eta_t, const double *q1_t,
+                const double *q2_t, const double *w_t, const double *p_t)
+{
+    const int nx = c->nx, ny = c->ny;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            double m = relax_m1(i, nx, c->dx, c->relax[0], c->relax[1]) *
+                       relax_m1(j, ny, c->dy, c->relax[2], c->relax[3]);
+            if (m == 1.0) continue;
+            size_t k = CI(i, j);
+            double hs = eta_t ? eta_t[k] + H[k] : (H[k] > 0.0 ? H[k] : 0.0);
+            if (hs < 0.0) hs = 0.0;
+            h[k] = m * h[k] + (1.0 - m) * hs;
+            q1[k] = m * q1[k] + (1.0 - m) * (q1_t ? q1_t[k] : 0.0);
+            q2[k] = m * q2[k] + (1.0 - m) * (q2_t ? q2_t[k] : 0.0);
+        }
+    for (int J = 0; J <= ny; ++J)
+        for (int I = 0; I <= nx; ++I) {
+            double m = relax_node1(I, nx, c->dx, c->relax[0], c->relax[1]) *
+                       relax_node1(J, ny, c->dy, c->relax[2], c->relax[3]);
+            if (m == 1.0) continue;
+            size_t k = NI(I, J);
+            w[k] = m * w[k] + (1.0 - m) * (w_t ? w_t[k] : 0.0);
+            p[k] = m * p[k] + (1.0 - m) * (p_t ? p_t[k] : 0.0);
+        }
 }

@@ -24,6 +24,9 @@
  *   w transport (w_transport = 1, Sec. 2) .. pinned (donor-cell upwind on uniform flow,
  *                                           uniform w kept, sum of h w kept between walls,
  *                                           no new extrema)
+ *   relaxation zones (Sec. 4.4) ............ pinned (interior untouched, fixed point at the
+ *                                           target, boundary cell = target, absorption of
+ *                                           an outgoing solitary wave against a wall)
  */
 #ifndef NH_ORACLE_H
 #define NH_ORACLE_H
@@ -51,6 +54,8 @@ typedef struct {
     int w_transport;     /* 1: energy-consistent w equation (hw)_t + div(hw u) = p of the
                             system of [7] (Sec. 2), hw moved upwind on the node (dual)
                             cells; 0: Yamazaki's h w_t = p                                */
+    double relax[4];     /* L_Rel of the generating / absorbing zone (Sec. 4.4) on the west,
+                            east, south, north side; 0: none (1D: west, east)             */
 } or_cfg;
 
 typedef struct {
@@ -75,6 +80,13 @@ int or1d_thomas(int n, const double *a, const double *b, const double *c, const 
                 double *x);
 long long or1d_run(const or_cfg *c, const double *H, double *h, double *q, double *w,
                    double *p, double t_end, long long max_steps, double fixed_dt, double *t_out);
+/* Generating / absorbing relaxation zones of Sec. 4.4 (zone widths c->relax): blends
+ * (h, q) at the zone cells and (w, p) at the zone nodes toward the target (eta_t = h* - H,
+ * q_t, w_t, p_t); a NULL target is the lake at rest (h* = max(H, 0), q* = w* = p* = 0),
+ * which makes the zone absorbing.  or1d_run / or2d_run apply the absorbing form after
+ * every step when a width is set; or1d_step / or2d_step never relax. */
+void or1d_relax(const or_cfg *c, const double *H, double *h, double *q, double *w, double *p,
+                const double *eta_t, const double *q_t, const double *w_t, const double *p_t);
 
 /* ---- 2D (Sec. 5, App. A) ---- */
 double or2d_cfl_dt(const or_cfg *c, const double *H, const double *h, const double *q1,
@@ -95,6 +107,9 @@ int or2d_solve(const or_cfg *c, const double *H, const double *h, const double *
 long long or2d_run(const or_cfg *c, const double *H, double *h, double *q1, double *q2,
                    double *w, double *p, double t_end, long long max_steps, double fixed_dt,
                    double *t_out, long long *iters_total);
+void or2d_relax(const or_cfg *c, const double *H, double *h, double *q1, double *q2,
+                double *w, double *p, const double *eta_t, const double *q1_t,
+                const double *q2_t, const double *w_t, const double *p_t);
 
 #ifdef __cplusplus
 }
