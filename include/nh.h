@@ -100,6 +100,16 @@ typedef struct {
                            mean of the surrounding cells' face mass fluxes, upwind in w,
                            and the Runge-Kutta combination acts on hw.  Single-domain
                            handles only; batches and nh_step_taped reject it.            */
+    double relax_width[4]; /* L_Rel of the generating / absorbing relaxation zone of Sec.
+                           4.4 on the west, east, south, north side (0: none; 1D: west and
+                           east only; not on periodic sides; at most the domain's length).
+                           After every step, the k + 1 cells nearest the side (k the first
+                           natural number with k dx >= L_Rel) blend toward a target as
+                           U <- m U + (1 - m) U*, m = sqrt(max(0, 1 - (d / L_Rel)^2)), d the
+                           distance from the zone's inner cell (m = 0 at the boundary
+                           cell); w, p at the nodes with the mean m of the two cells.  The
+                           target is the lake at rest (absorbing) until
+                           nh_set_relax_target sets another.  Single-domain handles only. */
 } nh_params;
 
 typedef struct {
@@ -158,6 +168,15 @@ int nh_step(nh_handle *h, double dt, double *dt_taken);
  * limit) or max_steps steps.  *steps_taken may be NULL. */
 int nh_run(nh_handle *h, double t_end, long long max_steps, long long *steps_taken);
 
+/* Target (eta*, q1*, q2*, w*, p*) of the relaxation zones (Sec. 4.4), used from the next
+ * step on: cell arrays [ny][nx], node arrays as in nh_set_state, handle precision; only
+ * the zone entries are read.  A NULL pointer leaves that field's target as it is (the
+ * lake at rest: eta* = max(H, 0) - H, q* = w* = p* = 0, until set).  A target depth
+ * eta* + H below 0 counts as 0.  NH_EINVAL when the handle has no zone.  For a generating
+ * boundary, set the target of time t + dt before each step. */
+int nh_set_relax_target(nh_handle *h, const void *eta, const void *q1, const void *q2,
+                        const void *w, const void *p, int where);
+
 /* Counters and the FP64 mass of the current state (synchronises the stream). */
 int nh_stats(nh_handle *h, nh_stats_t *out);
 
@@ -183,6 +202,7 @@ enum {
     NH_K_ADJ_ASSEMBLY,    /* adjoint: transposed rows, assembly / solve terms            */
     NH_K_ADJ_CORRECTION,  /* adjoint: correction terms                                   */
     NH_K_W_TRANSPORT,     /* w* of the (hw)_t + div(hw u) = p form (NH_W_TRANSPORT)      */
+    NH_K_RELAX,           /* relaxation zones (Sec. 4.4) and the Eq. (23) rate after them */
     NH_K_COUNT
 };
 

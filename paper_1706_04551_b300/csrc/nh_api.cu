@@ -27,6 +27,8 @@ struct Base {
                           const void* p, int where) = 0;
     virtual int get_state(void* eta, void* q1, void* q2, void* w, void* p, int where) = 0;
     virtual int step(double dt) = 0;
+    virtual int set_relax_target(const void* eta, const void* q1, const void* q2,
+                                 const void* w, const void* p, int where) = 0;
     virtual int lambda(double* lam) = 0;
     virtual int mass(double* m) = 0;
     virtual int cheb_form() const = 0;   // pass form in use, -1 while timing
@@ -126,6 +128,8 @@ struct Impl : Base {
     StepCtl* h_stctl = nullptr;
     int last_solve_iters = 0;
     int last_cheb_passes = 0;
+    RelaxZ Z{};                 // relaxation zones (Sec. 4.4); relax_on: any side has one
+    bool relax_on = false;
 
     ~Impl() override
     {
@@ -206,6 +210,21 @@ struct Impl : Base {
         }
         A(B.sctl, 1);
         A(B.stctl, 1);
+        for (int k = 0; k < 4; ++k) {   // k: the first natural number with k d >= L_Rel
+            Z.L[k] = q.relax_width[k];
+            const double d = k < 2 ? g.dx : g.dy;
+            int kk = 0;
+            if (Z.L[k] > 0.0)
+                while ((double)kk * d < Z.L[k]) ++kk;
+            Z.k[k] = kk;
+            relax_on = relax_on || kk > 0;
+        }
+        Z.d[0] = g.dx;
+        Z.d[1] = dim == 2 ? g.dy : g.dx;
+        if (relax_on) {
+            A(B.rz_eta, nc); A(B.rz_q1, nc); A(B.rz_w, nn); A(B.rz_p, nn);
+            if (dim == 2) A(B.rz_q2, nc);
+        }
         if (q.w_equation == NH_W_TRANSPORT) {
             // face mass fluxes: x faces [ny][nx+1] (1D: [rows][nx+1]), y faces [ny+1][nx]
             A(B.fmx, (size_t)(g.nx + 1) * g.ny);
@@ -242,6 +261,13 @@ struct Impl : Base {
         launch_fill<T>(Lc, B.q2, nc, T(0));
         launch_fill<T>(Ln, B.w, nn, T(0));
         launch_fill<T>(Ln, B.p, nn, T(0));
+        if (relax_on) {   // absorbing target: the lake at rest
+            cudaMemcpyAsync(B.rz_eta, eta0.data(), nc * sizeof(T), cudaMemcpyHostToDevice, h->s);
+            launch_fill<T>(Lc, B.rz_q1, nc, T(0));
+            if (B.rz_q2) launch_fill<T>(Lc, B.rz_q2, nc, T(0));
+            launch_fill<T>(Ln, B.rz_w, nn, T(0));
+            launch_fill<T>(Ln, B.rz_p, nn, T(0));
+        }
         if ((e = cudaStreamSynchronize(h->s)) != cudaSuccess) return cuda_fail(hd, e, "nh_create");
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(hd, e, "nh_create launch");
         double lam = 0.0;
@@ -317,6 +343,21 @@ struct Impl : Base {
         if (p) cudaMemcpyAsync(p, B.p, nn * sizeof(T), kind_out(where), s);
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(hd, e, "nh_get_state");
+        return NH_OK;
+    }
+
+    int set_relax_target(const void* eta, const void* q1, const void* q2, const void* w,
+                         const void* p, int where) override
+    {
+        if (!relax_on) return fail(hd, NH_EINVAL, "nh_set_relax_target: no relaxation zone");
+        cudaStream_t s = hd->s;
+        if (eta) cudaMemcpyAsync(B.rz_eta, eta, nc * sizeof(T), kind_in(where), s);
+        if (q1) cudaMemcpyAsync(B.rz_q1, q1, nc * sizeof(T), kind_in(where), s);
+        if (q2 && B.rz_q2) cudaMemcpyAsync(B.rz_q2, q2, nc * sizeof(T), kind_in(where), s);
+        if (w) cudaMemcpyAsync(B.rz_w, w, nn * sizeof(T), kind_in(where), s);
+        if (p) cudaMemcpyAsync(B.rz_p, p, nn * sizeof(T), kind_in(where), s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(hd, e, "nh_set_relax_target");
         return NH_OK;
     }
 
@@ -612,6 +653,15 @@ struct Impl : Base {
         }
         int rc2 = dim == 2 ? stage2d(1, dt) : stage1d(1, dt);
         if (rc2 != NH_OK && rc2 != NH_ENOCONV) return rc2;
+        if (relax_on) {   // zones after the step, then the Eq. (23) rate of the result
+            K_(NH_K_RELAX, [&] {
+                launch_relax<T>(P, Ln, Z, dim, B.eta, B.q1, B.q2, B.w, B.p, B.H, B.rz_eta,
+                                B.rz_q1, B.rz_q2, B.rz_w, B.rz_p);
+            });
+            K_(NH_K_RELAX, [&] {
+                launch_lambda<T>(P, Lc, B.eta, B.q1, B.q2, B.H, dim, B.partials, B.stctl);
+            });
+        }
         if (tape) {
             tcopy(tape, 11, B.eta); tcopy(tape, 12, B.q1k); tcopy(tape, 13, B.q2k);
             tcopy(tape, 14, B.p);
@@ -874,6 +924,18 @@ int check_grid(const nh_grid* g, const nh_params* p, std::string& why)
         why = "w_equation must be NH_W_YAMAZAKI or NH_W_TRANSPORT";
         return 0;
     }
+    for (int k = 0; k < 4; ++k) {
+        const double L = p->relax_width[k];
+        const double len = k < 2 ? g->nx * g->dx : (double)g->ny * g->dy;
+        if (!(L >= 0.0) || L > len) {
+            why = "relax_width must be in [0, the domain's length]";
+            return 0;
+        }
+        if (L > 0.0 && ((k < 2 && periodic) || (k >= 2 && g->dim == 1))) {
+            why = "relaxation zones: not on periodic sides, west / east only in 1D";
+            return 0;
+        }
+    }
     return 1;
 }
 
@@ -891,6 +953,7 @@ int nh_default_params(nh_params* p)
     p->adjoint_frozen_limiter = 0;
     p->cheb_form = -1;
     p->w_equation = NH_W_YAMAZAKI;
+    for (int k = 0; k < 4; ++k) p->relax_width[k] = 0.0;
     return NH_OK;
 }
 
@@ -1029,6 +1092,14 @@ int nh_profile_read(nh_handle* h, nh_profile_t* out)
     return h->impl->profile_read(out);
 }
 
+int nh_set_relax_target(nh_handle* h, const void* eta, const void* q1, const void* q2,
+                        const void* w, const void* p, int where)
+{
+    if (!h) return NH_EINVAL;
+    if (where != NH_HOST && where != NH_DEVICE) return fail(h, NH_EINVAL, "bad where");
+    return h->impl->set_relax_target(eta, q1, q2, w, p, where);
+}
+
 int nh_debug_hyperbolic(nh_handle* h, double dt, void* eta_out, void* q1_out, void* q2_out,
                         int where)
 {
@@ -1047,6 +1118,10 @@ int nh_step_taped(nh_handle* h, double dt, void* tape, double* dt_taken)
     if (h->grid.dim != 2) return fail(h, NH_EINVAL, "nh_step_taped: 2D only");
     if (h->prm.w_equation != NH_W_YAMAZAKI)
         return fail(h, NH_EINVAL, "nh_step_taped: the adjoint covers the h w_t = p form only");
+    for (int k = 0; k < 4; ++k)
+        if (h->prm.relax_width[k] > 0.0)
+            return fail(h, NH_EINVAL, "nh_step_taped: the adjoint covers steps without "
+                                      "relaxation zones only");
     const double d = dt > 0.0 ? dt : h->dt_next;
     if (!(d > 0.0)) return fail(h, NH_EINVAL, "no positive time step");
     int rc = h->impl->step_taped(d, tape);

@@ -1731,6 +1731,11 @@ int check_batch(int n, const nh_grid* grids, const double* const* H, const nh_pa
         why = "the batched form runs the h w_t = p form only";
         return 0;
     }
+    for (int k = 0; k < 4; ++k)
+        if (p->relax_width[k] != 0.0) {
+            why = "the batched form has no relaxation zones";
+            return 0;
+        }
     double total = 0.0;
     for (int d = 0; d < n; ++d) {
         const nh_grid& g = grids[d];

@@ -81,6 +81,8 @@ struct Bufs {
     // hyperbolic step (x faces [ny][nx+1], y faces [ny+1][nx]; 1D: [rows][nx+1] in fmx)
     // and the transported w*
     T *fmx, *fmy, *wt;
+    // relaxation zones only (else null): target eta*, q1*, q2* (cells), w*, p* (nodes)
+    T *rz_eta, *rz_q1, *rz_q2, *rz_w, *rz_p;
 };
 
 struct Launch {
@@ -200,6 +202,21 @@ template <typename T>
 void launch_corr1d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* qk, T de,
                    int with_p, T* eo, T* qo, T* wo, int final_stage, double* partials,
                    StepCtl* st);
+
+// ---- relaxation zones (Sec. 4.4) ----
+// Per side (west, east, south, north): zone width L, k = the first natural number with
+// k d >= L (0: no zone), and the cell sizes d = (dx, dy) in FP64.
+struct RelaxZ {
+    double L[4];
+    int k[4];
+    double d[2];
+};
+// Blend the zone cells (eta, q1, q2) and nodes (w, p) toward the target (et .. pt) after
+// a step; dim 1: rows of 1D channels (west / east zones only).
+template <typename T>
+void launch_relax(const Prm<T>& P, const Launch& L, const RelaxZ& Z, int dim, T* eta, T* q1,
+                  T* q2, T* w, T* p, const T* H, const T* et, const T* q1t, const T* q2t,
+                  const T* wt, const T* pt);
 
 // ---- shared ----
 template <typename T>

@@ -501,6 +501,74 @@ k_hyp1d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ q,
     if (nclamp) atomicAdd(&st->clamped, nclamp);
 }
 
+// Relaxation coefficient of Sec. 4.4 for cell i of a line of n cells (FP64, as the zone
+// geometry): the zone on the low side is the klo + 1 cells nearest it, the distance is
+// measured from the zone's inner cell (m = 1 there, 0 at the boundary cell); the same on
+// the high side; overlapping zones multiply.  k = 0: no zone.
+__device__ __forceinline__ double relax_coef(int i, int n, double d, double Llo, int klo,
+                                             double Lhi, int khi)
+{
+    double m = 1.0;
+    if (klo > 0 && i <= klo) {
+        const double r = (double)(klo - i) * d / Llo, v = 1.0 - r * r;
+        m *= v > 0.0 ? sqrt(v) : 0.0;
+    }
+    if (khi > 0 && i >= n - 1 - khi) {
+        const double r = (double)(i - (n - 1 - khi)) * d / Lhi, v = 1.0 - r * r;
+        m *= v > 0.0 ? sqrt(v) : 0.0;
+    }
+    return m;
+}
+
+// Node I (between cells I-1 and I): the mean of its two cells' coefficients (the cell
+// beyond an end takes the end cell's).
+__device__ __forceinline__ double relax_node_coef(int I, int n, double d, double Llo, int klo,
+                                                  double Lhi, int khi)
+{
+    const int a = I - 1 < 0 ? 0 : I - 1, b = I > n - 1 ? n - 1 : I;
+    return 0.5 * (relax_coef(a, n, d, Llo, klo, Lhi, khi) +
+                  relax_coef(b, n, d, Llo, klo, Lhi, khi));
+}
+
+// Relaxation zones of Sec. 4.4 after a step: U <- m U + (1 - m) U* at the zone cells
+// (depth h = eta + H blended toward max(eta* + H, 0)), w and p at the zone nodes; 2D
+// coefficients are the products of the x and y ones.  One thread per cell, then per node.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_relax(Prm<T> P, RelaxZ Z, int dim, T* __restrict__ eta, T* __restrict__ q1,
+        T* __restrict__ q2, T* __restrict__ w, T* __restrict__ p, const T* __restrict__ H,
+        const T* __restrict__ et, const T* __restrict__ q1t, const T* __restrict__ q2t,
+        const T* __restrict__ wt, const T* __restrict__ pt)
+{
+    const int nx = P.nx, ny = P.ny;
+    const long long nc = (long long)nx * ny;
+    const long long nn = dim == 2 ? (long long)(nx + 1) * (ny + 1) : (long long)(nx + 1) * ny;
+    GRID_STRIDE(idx, nc + nn)
+    {
+        if (idx < nc) {
+            const int i = (int)(idx % nx), j = (int)(idx / nx);
+            double m = relax_coef(i, nx, Z.d[0], Z.L[0], Z.k[0], Z.L[1], Z.k[1]);
+            if (dim == 2) m *= relax_coef(j, ny, Z.d[1], Z.L[2], Z.k[2], Z.L[3], Z.k[3]);
+            if (m == 1.0) continue;
+            const T mt = (T)m, mc = (T)(1.0 - m);
+            const T Hc = H[idx];
+            const T hs = tmax(et[idx] + Hc, T(0));
+            eta[idx] = (mt * (eta[idx] + Hc) + mc * hs) - Hc;
+            q1[idx] = mt * q1[idx] + mc * q1t[idx];
+            if (dim == 2) q2[idx] = mt * q2[idx] + mc * q2t[idx];
+        } else {
+            const long long k = idx - nc;
+            const int I = (int)(k % (nx + 1)), J = (int)(k / (nx + 1));
+            double m = relax_node_coef(I, nx, Z.d[0], Z.L[0], Z.k[0], Z.L[1], Z.k[1]);
+            if (dim == 2) m *= relax_node_coef(J, ny, Z.d[1], Z.L[2], Z.k[2], Z.L[3], Z.k[3]);
+            if (m == 1.0) continue;
+            const T mt = (T)m, mc = (T)(1.0 - m);
+            w[k] = mt * w[k] + mc * wt[k];
+            p[k] = mt * p[k] + mc * pt[k];
+        }
+    }
+}
+
 // 1D form of k_wtrans2d_t: node k of a channel owns the dual cell between the centres of
 // cells k-1 and k (its inner half at a wall or outflow end); the dual faces carry the
 // mean of a cell's two face mass fluxes (the boundary face at an end).  Periodic
@@ -1092,6 +1160,15 @@ void launch_hyp1d(const Prm<T>& P, const Launch& L, const T* eta, const T* q, co
 }
 
 template <typename T>
+void launch_relax(const Prm<T>& P, const Launch& L, const RelaxZ& Z, int dim, T* eta, T* q1,
+                  T* q2, T* w, T* p, const T* H, const T* et, const T* q1t, const T* q2t,
+                  const T* wt, const T* pt)
+{
+    k_relax<T><<<L.nblk, kThreads, 0, L.s>>>(P, Z, dim, eta, q1, q2, w, p, H, et, q1t, q2t, wt,
+                                             pt);
+}
+
+template <typename T>
 void launch_wtrans1d(const Prm<T>& P, const Launch& L, const T* etab, const T* etain,
                      const T* etas, const T* H, const T* wb, const T* win, const T* fm, T a,
                      T b, T dt, T* wo)
@@ -1226,6 +1303,9 @@ void launch_convert_from_double(const Launch& L, const double* src, T* dst, size
     template void launch_wtrans2d<T>(const Prm<T>&, const Launch&, const T*, const T*,         \
                                      const T*, const T*, const T*, const T*, const T*,         \
                                      const T*, T, T, T, T*);                                   \
+    template void launch_relax<T>(const Prm<T>&, const Launch&, const RelaxZ&, int, T*, T*,    \
+                                  T*, T*, T*, const T*, const T*, const T*, const T*,          \
+                                  const T*, const T*);                                         \
     template void launch_wtrans1d<T>(const Prm<T>&, const Launch&, const T*, const T*,         \
                                      const T*, const T*, const T*, const T*, const T*, T, T,   \
                                      T, T*);                                                   \

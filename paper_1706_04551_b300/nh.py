@@ -35,7 +35,7 @@ class Params(C.Structure):
                 ("solver", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int),
                 ("precision", C.c_int), ("fixed_dt", C.c_double), ("eps_dp", C.c_double),
                 ("adjoint_frozen_limiter", C.c_int), ("cheb_form", C.c_int),
-                ("w_equation", C.c_int)]
+                ("w_equation", C.c_int), ("relax_width", C.c_double * 4)]
 
 
 class StatsT(C.Structure):
@@ -67,14 +67,14 @@ EXPORTS = ("nh_default_params", "nh_create", "nh_set_state", "nh_get_state", "nh
            "nh_batch_stats", "nh_batch_get_tuning", "nh_batch_set_tuning",
            "nh_batch_candidate", "nh_batch_last_error", "nh_batch_destroy",
            "nh_batch_profile_enable", "nh_batch_profile_read", "nh_tape_bytes",
-           "nh_step_taped", "nh_adjoint_step", "nh_cheb_forms")
+           "nh_step_taped", "nh_adjoint_step", "nh_cheb_forms", "nh_set_relax_target")
 
 BATCH_AUTOTUNE, BATCH_GRAPH = 1, 2
 
 # kernel classes of nh_profile_t, in enum order
 KERNELS = ("hyperbolic", "breaking", "assembly", "solve_init", "bicg_A", "bicg_B", "bicg_C",
            "cheb_pass", "tridiag", "correction", "adj_hyperbolic", "adj_assembly",
-           "adj_correction", "w_transport")
+           "adj_correction", "w_transport", "relax")
 
 
 class ProfileT(C.Structure):
@@ -107,6 +107,7 @@ def load():
     L.nh_tridiag_batched.argtypes = [C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, vp, vp]
     L.nh_debug_hyperbolic.argtypes = [H, C.c_double, vp, vp, vp, C.c_int]
     L.nh_debug_system.argtypes = [H, C.c_double, vp, vp, vp, C.c_int]
+    L.nh_set_relax_target.argtypes = [H, vp, vp, vp, vp, vp, C.c_int]
     L.nh_create_batch.argtypes = [C.c_int, C.POINTER(Grid), C.POINTER(C.c_void_p),
                                   C.POINTER(Params), vp, C.c_int, C.POINTER(H)]
     L.nh_batch_set_state.argtypes = [H, C.c_int, vp, vp, vp, vp, vp, C.c_double, C.c_int]
@@ -188,6 +189,8 @@ class Sim:
         for k, v in params.items():
             if not hasattr(p, k):
                 raise TypeError(f"unknown parameter {k}")
+            if isinstance(getattr(p, k), C.Array):   # e.g. relax_width = (w, e, s, n)
+                v = type(getattr(p, k))(*v)
             setattr(p, k, v)
         self.params = p
         self._h = C.c_void_p()
@@ -228,6 +231,17 @@ class Sim:
         wheres = {wh for ptr, wh in args if ptr is not None}
         assert len(wheres) == 1, "mixing host and device arrays"
         self._check(load().nh_set_state(self._h, *[a[0] for a in args], float(t), wheres.pop()))
+        self._keep.clear()
+
+    def set_relax_target(self, eta=None, q1=None, q2=None, w=None, p=None):
+        """nh_set_relax_target: target of the Sec. 4.4 relaxation zones (None: unchanged)."""
+        nc = self.nx * self.ny
+        args = [self._arr(eta, nc), self._arr(q1, nc), self._arr(q2, nc),
+                self._arr(w, self.nnode), self._arr(p, self.nnode)]
+        wheres = {wh for ptr, wh in args if ptr is not None}
+        assert len(wheres) <= 1, "mixing host and device arrays"
+        self._check(load().nh_set_relax_target(self._h, *[a[0] for a in args],
+                                               wheres.pop() if wheres else HOST))
         self._keep.clear()
 
     def get_state(self):
@@ -371,6 +385,8 @@ class Batch:
         for k, v in params.items():
             if not hasattr(p, k):
                 raise TypeError(f"unknown parameter {k}")
+            if isinstance(getattr(p, k), C.Array):   # e.g. relax_width = (w, e, s, n)
+                v = type(getattr(p, k))(*v)
             setattr(p, k, v)
         self.params = p
         ptrs = (C.c_void_p * n)(*[H.ctypes.data for H in self.Hs])

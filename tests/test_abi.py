@@ -126,3 +126,30 @@ def test_w_equation_default_and_bad_value_rejected_without_touching_the_gpu():
         rc = L.nh_create(ctypes.byref(g), H.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                          ctypes.byref(p), None, ctypes.byref(h))
         assert rc == nh.EINVAL and not h.value
+
+
+def test_relaxation_zone_rules_without_touching_the_gpu():
+    import numpy as np
+    B.build()
+    L = nh.load()
+    p0 = nh.default_params()
+    assert list(p0.relax_width) == [0.0] * 4
+    H = np.ones(64)
+    cases = (  # (dim, bc, widths) that nh_create must reject before any device work
+        (1, (2, 2, 0, 0), (0.2, 0, 0, 0)),     # zone on a periodic side
+        (1, (0, 0, 0, 0), (0, 0, 0.2, 0)),     # south zone of a 1D channel
+        (2, (0, 0, 0, 0), (-0.1, 0, 0, 0)),    # negative width
+        (2, (0, 0, 0, 0), (0, 0.9, 0, 0)),     # wider than the domain (8 x 0.1)
+    )
+    for dim, bc, wd in cases:
+        g = nh.Grid()
+        g.dim, g.nx, g.ny, g.dx, g.dy = dim, 8, 8, 0.1, 0.1
+        for k in range(4):
+            g.bc[k] = bc[k]
+        p = nh.default_params()
+        for k in range(4):
+            p.relax_width[k] = wd[k]
+        h = ctypes.c_void_p()
+        rc = L.nh_create(ctypes.byref(g), H.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                         ctypes.byref(p), None, ctypes.byref(h))
+        assert rc == nh.EINVAL and not h.value
