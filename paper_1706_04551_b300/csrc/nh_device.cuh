@@ -554,22 +554,53 @@ asm_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
     const int nxn = P.nx + 1;
     const int I0 = bx * TX, J0 = by * TY;
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int t = tid; t < SN; t += nt) {
-        const int li = t % SW, lj = t / SW;
-        int ci = I0 - 2 + li, cj = J0 - 2 + lj;
-        ci = ci > P.nx + 1 ? P.nx + 1 : ci;
-        cj = cj > P.ny + 1 ? P.ny + 1 : cj;
-        bool rx, ry;
-        const int ii = map_cell(ci, P.nx, P.bcw, P.bce, rx);
-        const int jj = map_cell(cj, P.ny, P.bcs, P.bcn, ry);
-        const size_t m = (size_t)jj * P.nx + ii;
-        const T e = eta[m], Hm = H[m];
-        ss[t] = e - Hm;
-        hs[t] = tmax(e + Hm, T(0));
-        if (fuse) {
-            sHH[t] = Hm;
-            sq1[t] = rx ? -q1s[m] : q1s[m];
-            sq2[t] = ry ? -q2s[m] : q2s[m];
+    // staged cells (and the previous pressure ring, PN < SN) in rounds of NS entries per
+    // thread: every load of a round is issued before its first shared store, so a 256-thread
+    // block waits on one round of memory latency instead of one per loop
+    constexpr int NS = 3;
+    for (int base = tid; base < SN; base += NS * nt) {
+        T ve[NS], vH[NS], v1[NS], v2[NS], vp[NS];
+        bool fx[NS], fy[NS];
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            const int t = base + k * nt;
+            ve[k] = vH[k] = v1[k] = v2[k] = vp[k] = T(0);
+            fx[k] = fy[k] = false;
+            if (t < SN) {
+                const int li = t % SW, lj = t / SW;
+                int ci = I0 - 2 + li, cj = J0 - 2 + lj;
+                ci = ci > P.nx + 1 ? P.nx + 1 : ci;
+                cj = cj > P.ny + 1 ? P.ny + 1 : cj;
+                const int ii = map_cell(ci, P.nx, P.bcw, P.bce, fx[k]);
+                const int jj = map_cell(cj, P.ny, P.bcs, P.bcn, fy[k]);
+                const size_t m = (size_t)jj * P.nx + ii;
+                ve[k] = eta[m];
+                vH[k] = H[m];
+                if (fuse) {
+                    v1[k] = q1s[m];
+                    v2[k] = q2s[m];
+                }
+            }
+            if (resid_form && t < PN) {
+                int I = I0 - 1 + t % PW, J = J0 - 1 + t / PW;
+                I = I > P.nx + 1 ? P.nx + 1 : I;   // beyond the mirror: feeds no node of the tile
+                J = J > P.ny + 1 ? P.ny + 1 : J;
+                vp[k] = p0[(size_t)map_node(J, P.ny) * nxn + map_node(I, P.nx)];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            const int t = base + k * nt;
+            if (t < SN) {
+                ss[t] = ve[k] - vH[k];
+                hs[t] = tmax(ve[k] + vH[k], T(0));
+                if (fuse) {
+                    sHH[t] = vH[k];
+                    sq1[t] = fx[k] ? -v1[k] : v1[k];
+                    sq2[t] = fy[k] ? -v2[k] : v2[k];
+                }
+            }
+            if (resid_form && t < PN) P0s[t] = vp[k];
         }
     }
     if (!fuse)
@@ -589,13 +620,7 @@ asm_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
             P2c[t] = ry ? -q2s[m] : q2s[m];
         }
     }
-    if (resid_form)
-        for (int t = tid; t < PN; t += nt) {
-            int I = I0 - 1 + t % PW, J = J0 - 1 + t / PW;
-            I = I > P.nx + 1 ? P.nx + 1 : I;   // beyond the mirror: feeds no node of the tile
-            J = J > P.ny + 1 ? P.ny + 1 : J;
-            P0s[t] = p0[(size_t)map_node(J, P.ny) * nxn + map_node(I, P.nx)];
-        }
+    static_assert(PN < SN, "the pressure ring is staged with the cells");
     __syncthreads();
     for (int t = tid; t < CN; t += nt) {
         const int li = t % CW, lj = t / CW;
@@ -1577,24 +1602,45 @@ corr_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
             }
         }
     }
-    for (int t = tid; t < CN; t += nt) {
-        const int li = t % CW, lj = t / CW;
-        int ci = I0 - 1 + li, cj = J0 - 1 + lj;
-        ci = ci > nx + 1 ? nx + 1 : ci;
-        cj = cj > ny + 1 ? ny + 1 : cj;
-        bool rx, ry;
-        const int ii = map_cell(ci, nx, P.bcw, P.bce, rx);
-        const int jj = map_cell(cj, ny, P.bcs, P.bcn, ry);
-        const size_t m = (size_t)jj * nx + ii;
-        se[t] = eta[m];
-        sH[t] = H[m];
-    }
-    if (with_p)
-        for (int t = tid; t < NNd; t += nt) {
-            const int I = I0 + t % NW, J = J0 + t / NW;
-            const size_t m = (size_t)(J > ny ? ny : J) * nxn + (I > nx ? nx : I);
-            pn[t] = p[m] + dp[m];
+    // staged cells and nodes (NNd < CN) in rounds of NS entries per thread, all loads of a
+    // round issued before its first shared store (one round of memory latency per tile)
+    static_assert(NNd < CN, "the nodes are staged with the cells");
+    constexpr int NS = 2;
+    for (int base = tid; base < CN; base += NS * nt) {
+        T ve[NS], vH[NS], vp[NS], vd[NS];
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            const int t = base + k * nt;
+            ve[k] = vH[k] = vp[k] = vd[k] = T(0);
+            if (t < CN) {
+                const int li = t % CW, lj = t / CW;
+                int ci = I0 - 1 + li, cj = J0 - 1 + lj;
+                ci = ci > nx + 1 ? nx + 1 : ci;
+                cj = cj > ny + 1 ? ny + 1 : cj;
+                bool rx, ry;
+                const int ii = map_cell(ci, nx, P.bcw, P.bce, rx);
+                const int jj = map_cell(cj, ny, P.bcs, P.bcn, ry);
+                const size_t m = (size_t)jj * nx + ii;
+                ve[k] = eta[m];
+                vH[k] = H[m];
+            }
+            if (with_p && t < NNd) {
+                const int I = I0 + t % NW, J = J0 + t / NW;
+                const size_t m = (size_t)(J > ny ? ny : J) * nxn + (I > nx ? nx : I);
+                vp[k] = p[m];
+                vd[k] = dp[m];
+            }
         }
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+            const int t = base + k * nt;
+            if (t < CN) {
+                se[t] = ve[k];
+                sH[t] = vH[k];
+            }
+            if (with_p && t < NNd) pn[t] = vp[k] + vd[k];
+        }
+    }
     __syncthreads();
     const T idx_ = T(1) / P.dx, idy_ = T(1) / P.dy;
 #pragma unroll
