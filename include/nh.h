@@ -87,8 +87,10 @@ typedef struct {
     int max_iter;       /* iteration cap (BiCGStab iterations / Chebyshev sweeps)         */
     int precision;      /* NH_FP64 or NH_FP32 (state and fluxes; dots are FP64 always)   */
     double fixed_dt;    /* > 0: nh_run uses this step instead of Eq. (23)                */
-    double eps_dp;      /* > 0 (Chebyshev): stop on ||p^(k+1) - p^(k)||_inf < eps_dp, the
-                           criterion of Eq. (32), instead of the residual test            */
+    double eps_dp;      /* > 0: stop a pressure solve on ||p^(k+1) - p^(k)||_inf < eps_dp,
+                           the criterion of Eq. (32), instead of the residual test (the
+                           Chebyshev sweeps, and BiCGStab -- chosen, or as the fallback --
+                           on the change of its iterate per iteration)                   */
     int adjoint_frozen_limiter; /* nh_adjoint_step: 0 = exact derivative of the step; 1 =
                            reconstruction linearised with the limiter ratio held fixed   */
     int cheb_form;      /* single-domain handles, Chebyshev solver: -1 (default) = the

@@ -610,23 +610,28 @@ kb_bicg_C(Arena<T> A, const int2* __restrict__ wl, const int* __restrict__ nwp, 
         const T al = (T)ctl->alpha, om = (T)ctl->omega;
         const T* ph = V.ph[parity ^ 1] + n;
         const T* v = V.v[parity ^ 1] + n;
-        double acc[2] = {0.0, 0.0};
+        double acc[3] = {0.0, 0.0, 0.0};
         BATCH_NODE_LOOP(k, nn, it.y)
         {
             const T s = V.r[n + k] - al * v[k];
             const T dinv = T(1) / V.cC[n + k];
-            V.x[n + k] += (al * ph[k] + om * s) * dinv;
+            const T dx = (al * ph[k] + om * s) * dinv;
+            V.x[n + k] += dx;
             const T rn = s - om * V.t[n + k];
             V.r[n + k] = rn;
             acc[0] += (double)V.rh[n + k] * (double)rn;
             acc[1] += (double)rn * (double)rn;
+            acc[2] = fmax(acc[2], (double)fabs(dx));
         }
-        if (dom_reduce<2, 0u>(acc, A.partials + D.poff, &ctl->counter, it.y, D.nnc) &&
+        if (dom_reduce<3, 4u>(acc, A.partials + D.poff, &ctl->counter, it.y, D.nnc) &&
             threadIdx.x == 0) {
             ctl->rho1 = acc[0];
             ctl->rr = acc[1];
+            ctl->dpmax = acc[2];
             ctl->iter += 1;
-            if (acc[1] <= ctl->tol2 * ctl->bb) bicg_end(ctl, A.ds[it.x], A.loop, stage, 1);
+            // residual test, or criterion (32) on the iterate's change when eps_dp > 0
+            if (acc[1] <= ctl->tol2 * ctl->bb || (ctl->eps_dp > 0.0 && acc[2] < ctl->eps_dp))
+                bicg_end(ctl, A.ds[it.x], A.loop, stage, 1);
             else if (ctl->iter >= ctl->max_iter) bicg_end(ctl, A.ds[it.x], A.loop, stage, 2);
             else if (ctl->omega == 0.0 || acc[0] == 0.0 || !isfinite(acc[1]))
                 bicg_end(ctl, A.ds[it.x], A.loop, stage, 3);
@@ -1080,7 +1085,7 @@ struct BatchImpl : BatchBase {
             nnode += (nn + al - 1) / al * al;
             D.ncc = (int)((nc + kChunk - 1) / kChunk);
             D.nnc = (int)((nn + kChunk - 1) / kChunk);
-            long long np = std::max<long long>(D.ncc, 2LL * D.nnc);   // (BiCGStab: 2 per chunk)
+            long long np = std::max<long long>(D.ncc, 3LL * D.nnc);   // (BiCGStab: 3 per chunk)
             for (int k = 0; k < C::na; ++k) {
                 const Shape s = C::asm_shape(k);
                 np = std::max<long long>(np, 3LL * cdiv(g.nx + 1, s.tx) * cdiv(g.ny + 1, s.ty));

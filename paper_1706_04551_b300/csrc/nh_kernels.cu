@@ -274,6 +274,7 @@ k_bicg_B(Rows<T> R, const T* __restrict__ r, const T* __restrict__ v, T* __restr
 }
 
 // phase C: x += alpha D^-1 p^ + omega D^-1 s; r = s - omega t; rho1 = rhat . r; test
+// (residual test, or criterion (32) on the iterate's change when eps_dp > 0)
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_bicg_C(Rows<T> R, T* __restrict__ r, const T* __restrict__ rh, const T* __restrict__ ph,
@@ -282,22 +283,28 @@ k_bicg_C(Rows<T> R, T* __restrict__ r, const T* __restrict__ rh, const T* __rest
 {
     if (ctl->done) return;
     const T al = (T)ctl->alpha, om = (T)ctl->omega;
-    double acc[2] = {0.0, 0.0};
+    double acc[3] = {0.0, 0.0, 0.0};
     GRID_STRIDE(idx, (long long)(R.nx + 1) * (R.ny + 1))
     {
         const T s = r[idx] - al * v[idx];
         const T dinv = T(1) / R.cC[idx];
-        x[idx] += (al * ph[idx] + om * s) * dinv;
+        const T dx = (al * ph[idx] + om * s) * dinv;
+        x[idx] += dx;
         const T rn = s - om * t[idx];
         r[idx] = rn;
         acc[0] += (double)rh[idx] * (double)rn;
         acc[1] += (double)rn * (double)rn;
+        acc[2] = fmax(acc[2], (double)fabs(dx));
     }
-    if (grid_reduce<2, 0u>(acc, partials, &ctl->counter) && threadIdx.x == 0) {
+    if (grid_reduce<3, 4u>(acc, partials, &ctl->counter) && threadIdx.x == 0) {
         ctl->rho1 = acc[0];
         ctl->rr = acc[1];
+        ctl->dpmax = acc[2];
         ctl->iter += 1;
-        if (acc[1] <= ctl->tol2 * ctl->bb) { ctl->done = 1; ctl->status = 1; }
+        if (acc[1] <= ctl->tol2 * ctl->bb || (ctl->eps_dp > 0.0 && acc[2] < ctl->eps_dp)) {
+            ctl->done = 1;
+            ctl->status = 1;
+        }
         else if (ctl->iter >= ctl->max_iter) { ctl->done = 1; ctl->status = 2; }
         else if (ctl->omega == 0.0 || acc[0] == 0.0 || !isfinite(acc[1])) {
             ctl->done = 1; ctl->status = 3;

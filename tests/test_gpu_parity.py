@@ -382,3 +382,17 @@ def test_dambreak_fp64_against_oracle(mode):
         assert not g["p"].any() and not g["w"].any()
     else:
         assert rel(g["p"], p) < 1e-8
+
+
+def test_bicgstab_stops_on_criterion_eq32():
+    """BiCGStab under eps_dp stops on the change of its iterate (criterion (32)): fewer
+    iterations than the residual test at tol 1e-13, and p still close to the oracle's."""
+    wl = shoals(64)
+    its = {}
+    for name, kw in (("residual", {}), ("eq32", dict(eps_dp=1e-7))):
+        sim, g, (h, q1, q2, w, p, t, s, it) = _run_both(wl, 3, solver=nh.BICGSTAB, **kw)
+        its[name] = sim.stats()["solver_iters"]
+        sim.close()
+        assert rel(g["p"], p) < (1e-10 if name == "residual" else 1e-4)
+        assert rel(g["eta"] + wl.H, h) < (1e-10 if name == "residual" else 1e-6)
+    assert its["eq32"] < its["residual"]
