@@ -6,9 +6,8 @@ ctypes.  Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s cpu_bas
 no code.  Each wrapper cites the section / equation of the paper its C function follows;
 the C file lists the readings taken where the paper is silent or garbled.
 
-Parity status: every function is pinned by ``tests/test_oracle_*.py`` except the breaking
-terms (Sec. 3, Eq. 12), which are "parity unpinned" beyond invariants (lake at rest with
-breaking on, the switch-off limit, dissipation).  ``cfg(w_transport=True)`` selects the
+Parity status: every function is pinned by ``tests/test_oracle_*.py``; the breaking terms
+(Sec. 3, Eq. 12) by closed forms on linear fields and by invariants.  ``cfg(w_transport=True)`` selects the
 energy-consistent w equation of Sec. 2 (pinned by donor-cell upwind on uniform flow and
 by invariants); ``relax_1d`` / ``relax_2d`` and ``cfg(relax=...)`` the relaxation zones of
 Sec. 4.4 (pinned by their end values, special distances and wave absorption / generation).
@@ -92,6 +91,8 @@ def lib():
         L.or2d_apply_M.argtypes = [cp, dp, dp, dp, C.c_double, dp]
         L.or2d_solve.argtypes = [cp, dp, dp, dp, C.c_double, dp, C.POINTER(C.c_int), dp]
         L.or1d_relax.argtypes = [cp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
+        L.or1d_breaking.argtypes = [cp, dp, dp, dp, dp, C.c_double]
+        L.or2d_breaking.argtypes = [cp, dp, dp, dp, dp, dp, C.c_double]
         L.or2d_relax.argtypes = [cp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
         L.or2d_run.restype = C.c_longlong
         L.or2d_run.argtypes = [cp, dp, dp, dp, dp, dp, dp, C.c_double, C.c_longlong,
@@ -294,3 +295,19 @@ def relax_2d(c: Cfg, H, h, q1, q2, w, p, eta_t=None, q1_t=None, q2_t=None, w_t=N
     lib().or2d_relax(C.byref(c), _p(H), _p(h), _p(q1), _p(q2), _p(w), _p(p),
                      *[_opt(a) for a in tg])
     return h, q1, q2, w, p
+
+
+def breaking_1d(c: Cfg, H, h, q, w, dt: float):
+    """Sec. 3 / Eq. (12) breaking terms alone: returns (q, w) after them."""
+    H, h = _f64(H), _f64(h)
+    q, w = _f64(q).copy(), _f64(w).copy()
+    lib().or1d_breaking(C.byref(c), _p(H), _p(h), _p(q), _p(w), float(dt))
+    return q, w
+
+
+def breaking_2d(c: Cfg, H, h, q1, q2, w, dt: float):
+    """2D breaking terms (q_x -> div q, u_x -> div u): returns (q1, q2, w) after them."""
+    H, h = _f64(H), _f64(h)
+    q1, q2, w = _f64(q1).copy(), _f64(q2).copy(), _f64(w).copy()
+    lib().or2d_breaking(C.byref(c), _p(H), _p(h), _p(q1), _p(q2), _p(w), float(dt))
+    return q1, q2, w

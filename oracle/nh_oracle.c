@@ -1338,3 +1338,17 @@ void or2d_relax(const or_cfg *c, const double *H, double *h, double *q1, double 
             p[k] = m * p[k] + (1.0 - m) * (p_t ? p_t[k] : 0.0);
         }
 }
+
+/* The breaking terms of Sec. 3 (Eq. 12) alone, as the stages apply them to U* and w*
+ * with the step dt: public for the tests' closed-form pins. */
+void or1d_breaking(const or_cfg *c, const double *H, const double *h, double *q, double *w,
+                   double dt)
+{
+    breaking1d(c, H, h, q, w, dt);
+}
+
+void or2d_breaking(const or_cfg *c, const double *H, const double *h, double *q1, double *q2,
+                   double *w, double dt)
+{
+    breaking2d(c, H, h, q1, q2, w, dt);
+}

@@ -19,8 +19,9 @@
  *   or2d_apply_M / or2d_rhs / or2d_solve ... pinned (dense LU, y-invariant reduction to Eq. 43)
  *   full step 1D/2D ........................ pinned (dispersion relation, solitary wave,
  *                                           Table 1 orders, 2D == 1D on y-invariant data)
- *   breaking terms (Sec. 3, Eq. 12) ........ parity unpinned beyond invariants (lake at rest
- *                                           with breaking on, switch-off limit, dissipation)
+ *   breaking terms (Sec. 3, Eq. 12) ........ pinned (closed forms on linear fields in 1D and
+ *                                           2D, both sides of the switch; lake at rest,
+ *                                           switch-off limit, dissipation)
  *   w transport (w_transport = 1, Sec. 2) .. pinned (donor-cell upwind on uniform flow,
  *                                           uniform w kept, sum of h w kept between walls,
  *                                           no new extrema)
@@ -87,6 +88,10 @@ long long or1d_run(const or_cfg *c, const double *H, double *h, double *q, doubl
  * every step when a width is set; or1d_step / or2d_step never relax. */
 void or1d_relax(const or_cfg *c, const double *H, double *h, double *q, double *w, double *p,
                 const double *eta_t, const double *q_t, const double *w_t, const double *p_t);
+/* The breaking terms of Sec. 3 / Eq. (12) alone (cells: q += dt 2 nu u_x H_x; nodes:
+ * w += dt 2 nu u_x / h), in place. */
+void or1d_breaking(const or_cfg *c, const double *H, const double *h, double *q, double *w,
+                   double dt);
 
 /* ---- 2D (Sec. 5, App. A) ---- */
 double or2d_cfl_dt(const or_cfg *c, const double *H, const double *h, const double *q1,
@@ -110,6 +115,8 @@ long long or2d_run(const or_cfg *c, const double *H, double *h, double *q1, doub
 void or2d_relax(const or_cfg *c, const double *H, double *h, double *q1, double *q2,
                 double *w, double *p, const double *eta_t, const double *q1_t,
                 const double *q2_t, const double *w_t, const double *p_t);
+void or2d_breaking(const or_cfg *c, const double *H, const double *h, double *q1, double *q2,
+                   double *w, double dt);
 
 #ifdef __cplusplus
 }
