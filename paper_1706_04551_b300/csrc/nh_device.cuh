@@ -1287,40 +1287,43 @@ __device__ __forceinline__ void cheb_region_reg(const Rows<T>& Rw, const T* plan
     stage_next(-1);
     __syncthreads();   // every warp has its registers: the planes may be refilled
     stage_next(0);
-#pragma unroll
-    for (int sw = 0; sw < K; ++sw) {
+    // One sweep from the iterate `cur` (and the one before it, `prv`): each node's new
+    // value overwrites its own `prv` entry, which no other node reads, so the sweeps
+    // alternate the two arrays' roles and no copy is made; K is even, so x ends as the
+    // latest iterate and xa as the one before.
+    static_assert(K % 2 == 0, "sweeps alternate the two iterate arrays");
+    auto sweep = [&](T (&cur)[R][C], T (&prv)[R][C], int sw) {
         T* e = exch + (sw & 1) * (NW * 2 * RW);
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            e[(2 * w) * RW + C * lane + c] = x[0][c];
-            e[(2 * w + 1) * RW + C * lane + c] = x[R - 1][c];
+            e[(2 * w) * RW + C * lane + c] = cur[0][c];
+            e[(2 * w + 1) * RW + C * lane + c] = cur[R - 1][c];
         }
         __syncthreads();
         T lo[C], hi[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            lo[c] = w > 0 ? e[(2 * w - 1) * RW + C * lane + c] : x[0][c];
-            hi[c] = w < NW - 1 ? e[(2 * w + 2) * RW + C * lane + c] : x[R - 1][c];
+            lo[c] = w > 0 ? e[(2 * w - 1) * RW + C * lane + c] : cur[0][c];
+            hi[c] = w < NW - 1 ? e[(2 * w + 2) * RW + C * lane + c] : cur[R - 1][c];
         }
         const T c1 = c1s[sw], c2 = c2s[sw];
-        T xn[R][C];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            T left = __shfl_up_sync(0xffffffffu, x[r][C - 1], 1);
-            T right = __shfl_down_sync(0xffffffffu, x[r][0], 1);
-            if (lane == 0) left = x[r][0];
-            if (lane == 31) right = x[r][C - 1];
+            T left = __shfl_up_sync(0xffffffffu, cur[r][C - 1], 1);
+            T right = __shfl_down_sync(0xffffffffu, cur[r][0], 1);
+            if (lane == 0) left = cur[r][0];
+            if (lane == 31) right = cur[r][C - 1];
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                const T xc = x[r][c];
-                const T xw = c == 0 ? left : x[r][c - 1];
-                const T xe = c == C - 1 ? right : x[r][c + 1];
-                const T xs = r == 0 ? lo[c] : x[r - 1][c];
-                const T xnn = r == R - 1 ? hi[c] : x[r + 1][c];
+                const T xc = cur[r][c];
+                const T xw = c == 0 ? left : cur[r][c - 1];
+                const T xe = c == C - 1 ? right : cur[r][c + 1];
+                const T xs = r == 0 ? lo[c] : cur[r - 1][c];
+                const T xnn = r == R - 1 ? hi[c] : cur[r + 1][c];
                 const T res = cheb_resid(rb[r][c], xc, wW[r][c], xw, wE[r][c], xe, wS[r][c], xs,
                                          wN[r][c], xnn);
-                const T v = cheb_next(xc, xa[r][c], c1, c2, res);
-                xn[r][c] = v;
+                const T v = cheb_next(xc, prv[r][c], c1, c2, res);
+                prv[r][c] = v;
                 if (sw == K - 1) {
                     const int li = C * lane + c, lj = R * w + r;
                     if (li >= K && li < RW - K && lj >= K && lj < RH - K && I0 + li <= nx &&
@@ -1331,13 +1334,11 @@ __device__ __forceinline__ void cheb_region_reg(const Rows<T>& Rw, const T* plan
                 }
             }
         }
+    };
 #pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                xa[r][c] = x[r][c];
-                x[r][c] = xn[r][c];
-            }
+    for (int sw = 0; sw < K; sw += 2) {
+        sweep(x, xa, sw);
+        sweep(xa, x, sw + 1);
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -1399,54 +1400,55 @@ __device__ __forceinline__ void cheb_region_reg2(const Rows<float>& Rw, const fl
     stage_next(-1);
     __syncthreads();   // every warp has its registers: the planes may be refilled
     stage_next(0);
-#pragma unroll
-    for (int sw = 0; sw < K; ++sw) {
+    // sweeps alternate the roles of x and xa, as in cheb_region_reg (no copies)
+    static_assert(K % 2 == 0, "sweeps alternate the two iterate arrays");
+    auto sweep = [&](float2 (&cur)[R], float2 (&prv)[R], int sw) {
         float* e = exch + (sw & 1) * (NW * 2 * RW);
-        *reinterpret_cast<float2*>(e + (2 * w) * RW + 2 * lane) = x[0];
-        *reinterpret_cast<float2*>(e + (2 * w + 1) * RW + 2 * lane) = x[R - 1];
+        *reinterpret_cast<float2*>(e + (2 * w) * RW + 2 * lane) = cur[0];
+        *reinterpret_cast<float2*>(e + (2 * w + 1) * RW + 2 * lane) = cur[R - 1];
         __syncthreads();
         const float2 lo = w > 0 ? *reinterpret_cast<const float2*>(e + (2 * w - 1) * RW + 2 * lane)
-                                : x[0];
+                                : cur[0];
         const float2 hi = w < NW - 1
                               ? *reinterpret_cast<const float2*>(e + (2 * w + 2) * RW + 2 * lane)
-                              : x[R - 1];
+                              : cur[R - 1];
         const float2 c1 = make_float2(c1s[sw], c1s[sw]), c2 = make_float2(c2s[sw], c2s[sw]);
-        float2 xn[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            float left = __shfl_up_sync(0xffffffffu, x[r].y, 1);
-            float right = __shfl_down_sync(0xffffffffu, x[r].x, 1);
-            if (lane == 0) left = x[r].x;
-            if (lane == 31) right = x[r].y;
-            const float2 xw = make_float2(left, x[r].x), xe = make_float2(x[r].y, right);
-            const float2 xs = r == 0 ? lo : x[r - 1];
-            const float2 xnn = r == R - 1 ? hi : x[r + 1];
+            float left = __shfl_up_sync(0xffffffffu, cur[r].y, 1);
+            float right = __shfl_down_sync(0xffffffffu, cur[r].x, 1);
+            if (lane == 0) left = cur[r].x;
+            if (lane == 31) right = cur[r].y;
+            const float2 xw = make_float2(left, cur[r].x), xe = make_float2(cur[r].y, right);
+            const float2 xs = r == 0 ? lo : cur[r - 1];
+            const float2 xnn = r == R - 1 ? hi : cur[r + 1];
             float2 s = __ffma2_rn(wE[r], xe, __fmul2_rn(wW[r], xw));
             s = __ffma2_rn(wS[r], xs, s);
             s = __ffma2_rn(wN[r], xnn, s);
-            const float2 res = __ffma2_rn(s, m1, __ffma2_rn(x[r], m1, rb[r]));
-            const float2 v = __ffma2_rn(c2, res, __ffma2_rn(c1, __ffma2_rn(xa[r], m1, x[r]), x[r]));
-            xn[r] = v;
+            const float2 res = __ffma2_rn(s, m1, __ffma2_rn(cur[r], m1, rb[r]));
+            const float2 v =
+                __ffma2_rn(c2, res, __ffma2_rn(c1, __ffma2_rn(prv[r], m1, cur[r]), cur[r]));
             if (sw == K - 1) {
                 const int lj = R * w + r;
                 if (lj >= K && lj < RH - K && J0 + lj <= ny) {
                     const int li = 2 * lane;
                     if (li >= K && li < RW - K && gI0 <= nx) {
                         rsum = fma(res.x, res.x, rsum);
-                        dmax = fmaxf(dmax, fabsf(v.x - x[r].x));
+                        dmax = fmaxf(dmax, fabsf(v.x - cur[r].x));
                     }
                     if (li + 1 >= K && li + 1 < RW - K && gI1 <= nx) {
                         rsum = fma(res.y, res.y, rsum);
-                        dmax = fmaxf(dmax, fabsf(v.y - x[r].y));
+                        dmax = fmaxf(dmax, fabsf(v.y - cur[r].y));
                     }
                 }
             }
+            prv[r] = v;
         }
+    };
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            xa[r] = x[r];
-            x[r] = xn[r];
-        }
+    for (int sw = 0; sw < K; sw += 2) {
+        sweep(x, xa, sw);
+        sweep(xa, x, sw + 1);
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
