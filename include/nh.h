@@ -109,7 +109,8 @@ typedef struct {
                            natural number with k dx >= L_Rel) blend toward a target as
                            U <- m U + (1 - m) U*, m = sqrt(max(0, 1 - (d / L_Rel)^2)), d the
                            distance from the zone's inner cell (m = 0 at the boundary
-                           cell); w, p at the nodes with the mean m of the two cells.  The
+                           cell); w, p at the nodes with the mean m of the two cells.  In
+                           2D m is the product of the x and y factors.  The
                            target is the lake at rest (absorbing) until
                            nh_set_relax_target sets another.  Single-domain handles only. */
 } nh_params;
