@@ -413,7 +413,7 @@ k_cheb_reg(Rows<T> Rw, const T* __restrict__ b, const T* __restrict__ xi,
 }
 
 template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
 k_corr2d_t(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
            const T* __restrict__ q1k, const T* __restrict__ q2k, const T* __restrict__ ws,
            const T* __restrict__ p, const T* __restrict__ dp, T* __restrict__ pout, T de,
