@@ -14,6 +14,10 @@
  *       with Chebyshev-scheduled relaxation, or Jacobi-preconditioned BiCGStab with FP64
  *       dot products);
  *     correction of the discharges and of w (Eqs. 26-28, 36, 41).
+ * Options: the energy-consistent w equation (hw)_t + div(hw u) = p (nh_params.w_equation),
+ * generating / absorbing relaxation zones of Sec. 4.4 (nh_params.relax_width,
+ * nh_set_relax_target), periodic 1D channels (NH_BC_PERIODIC), the hydrostatic step alone
+ * (nh_params.nonhydrostatic = 0) and the stopping criterion of Eq. (32) (nh_params.eps_dp).
  *
  * Conventions.
  *   - Cells: row-major [ny][nx], x fastest; cell (i, j) is centred at ((i+1/2)dx, (j+1/2)dy).
