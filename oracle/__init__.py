@@ -7,7 +7,12 @@ no code.  Each wrapper cites the section / equation of the paper its C function 
 the C file lists the readings taken where the paper is silent or garbled.
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py``; the breaking terms
-(Sec. 3, Eq. 12) by closed forms on linear fields and by invariants.  ``cfg(w_transport=True)`` selects the
+(Sec. 3, Eq. 12) by closed forms on linear fields and by invariants; Manning friction by the
+decay of a uniform flow (first-order convergence to its ODE) and the Eq. (23) rate by closed
+forms on uniform states (``tests/test_oracle_friction_rate.py``).  Wet/dry fronts follow
+Sec. 4.5 literally (no truncation); ``cfg(dry_zero=True)`` sets q = 0 in dry cells after
+each stage instead (``tests/test_oracle_wetdry.py``).  The 2D loops run under OpenMP
+(``set_threads``) with results bitwise independent of the thread count.  ``cfg(w_transport=True)`` selects the
 energy-consistent w equation of Sec. 2 (pinned by donor-cell upwind on uniform flow and
 by invariants); ``relax_1d`` / ``relax_2d`` and ``cfg(relax=...)`` the relaxation zones of
 Sec. 4.4 (pinned by their end values, special distances and wave absorption / generation).
@@ -42,6 +47,7 @@ class Cfg(C.Structure):
         ("tol", C.c_double), ("max_iter", C.c_int),
         ("w_transport", C.c_int),
         ("relax", C.c_double * 4),
+        ("dry_zero", C.c_int),
     ]
 
 
@@ -50,13 +56,15 @@ class Stats(C.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile nh_oracle.c into liboracle.so (gcc -O2, FP64, no fast-math, no contraction)."""
+    """Compile nh_oracle.c into liboracle.so (gcc -O2 -fopenmp, FP64, no fast-math, no
+    contraction).  OpenMP runs the 2D loops over disjoint entries in parallel; sums stay
+    serial, so results do not depend on the thread count."""
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".{os.getpid()}.tmp"
         subprocess.check_call([
             "gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
-            "-ffp-contract=off", "-o", tmp, _SRC, "-lm",
+            "-ffp-contract=off", "-fopenmp", "-o", tmp, _SRC, "-lm",
         ])
         os.replace(tmp, _LIB)
     return _LIB
@@ -71,6 +79,8 @@ def lib():
         L = C.CDLL(build())
         dp = C.POINTER(C.c_double)
         cp = C.POINTER(Cfg)
+        L.or_set_threads.restype = C.c_int
+        L.or_set_threads.argtypes = [C.c_int]
         L.or1d_cfl_dt.restype = C.c_double
         L.or1d_cfl_dt.argtypes = [cp, dp, dp, dp]
         L.or1d_step.argtypes = [cp, dp, dp, dp, dp, dp, C.c_double, C.POINTER(Stats)]
@@ -114,7 +124,8 @@ def cfg(nx: int, ny: int = 1, dx: float = 1.0, dy: float | None = None, bc=(WALL
         g: float = 9.81, cfl: float = 0.9, delta: float = 1e-5, hdry: float | None = None,
         manning: float = 0.0, B1: float = 0.15, B2: float = 0.5, breaking: bool = False,
         nonhydro: bool = True, tol: float = 1e-13, max_iter: int = 4000,
-        w_transport: bool = False, relax=(0.0, 0.0, 0.0, 0.0)) -> Cfg:
+        w_transport: bool = False, relax=(0.0, 0.0, 0.0, 0.0),
+        dry_zero: bool = False) -> Cfg:
     c = Cfg()
     c.nx, c.ny = int(nx), int(ny)
     c.dx = float(dx)
@@ -129,7 +140,14 @@ def cfg(nx: int, ny: int = 1, dx: float = 1.0, dy: float | None = None, bc=(WALL
     c.w_transport = int(bool(w_transport))
     for k in range(4):
         c.relax[k] = float(relax[k])
+    c.dry_zero = int(bool(dry_zero))
     return c
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's 2D loops (n <= 0: unchanged); returns the previous count.
+    Results are the same, bit for bit, for every count."""
+    return int(lib().or_set_threads(int(n)))
 
 
 # ----------------------------------------------------------------------------- 1D (Sec. 4)

@@ -41,10 +41,11 @@
  *   - Runge-Kutta (Sec. 4.3, Sec. 6 "steps 1-4 are repeated twice"): the projection of the
  *     second stage acts on the Shu-Osher combination, so U^{n+1} itself satisfies the
  *     discrete constraint; p^{n+1} is that projection's pressure.
- *   - Dry cells (h <= hdry) carry no discharge: q = 0 there at the end of each stage.  The
- *     correction T_NH has a term p (2 eta - h)_x that does not vanish with h, so without
- *     this dry cells gain momentum and the fully dry nodes gain pressure, against the
- *     App. B A.2 analysis (q = w = 0 where h vanishes gives p = 0).
+ *   - Wet/dry fronts in the second step (Sec. 4.5): no special treatment, as the paper
+ *     states.  The correction T_NH has a term p (2 eta - h)_x that does not vanish with h,
+ *     so a dry cell next to the shoreline takes up a small discharge; its velocity stays 0
+ *     through the desingularisation.  The option dry_zero = 1 sets q = 0 in dry cells
+ *     after each stage instead (App. B A.2 takes q = w = 0 where the depth vanishes).
  *   - dt (Eq. 23) in 2D: CFL / max((|u|+c)/dx + (|v|+c)/dy), from the current state.
  *   - The 2D system is solved by unpreconditioned BiCGStab to a relative residual tol.
  *   - Energy-consistent w equation (w_transport = 1; Sec. 2 names the system of [7] and
@@ -62,6 +63,24 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the 2D loops.  Only loops whose iterations write disjoint entries carry an
+ * OpenMP pragma; every sum (the dot products of BiCGStab) stays serial, so the results
+ * do not depend on the thread count, bit for bit. */
+int or_set_threads(int n)
+{
+#ifdef _OPENMP
+    int old = omp_get_max_threads();
+    if (n > 0) omp_set_num_threads(n);
+    return old;
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------- */
 /* scalar helpers                                                             */
@@ -552,10 +571,13 @@ static void wtransport1d(const or_cfg *c, const double *hb, const double *wb,
     free(eb); free(ei); free(es);
 }
 
-/* Dry cells carry no discharge (reading of Sec. 4.5 and App. B A.2, whose analysis takes
- * q = w = 0 where the depth vanishes): q = 0 where h <= hdry, at the end of each stage. */
+/* Option dry_zero = 1: dry cells carry no discharge, q = 0 where h <= hdry at the end of
+ * each stage (the premise of App. B A.2, q = w = 0 where the depth vanishes, imposed).
+ * The default (dry_zero = 0) is the second step as Sec. 4.5 states it, with no special
+ * treatment and no truncation at wet/dry fronts. */
 static void dry_discharge_1d(const or_cfg *c, const double *h, double *q)
 {
+    if (!c->dry_zero) return;
     for (int i = 0; i < c->nx; ++i)
         if (h[i] <= c->hdry) q[i] = 0.0;
 }
@@ -672,6 +694,7 @@ long long or1d_run(const or_cfg *c, const double *H, double *h, double *q, doubl
 static void ghost2d(const or_cfg *c, double *v, double px, double py)
 {
     const int nx = c->nx, ny = c->ny;
+#pragma omp parallel for
     for (int j = 0; j < ny; ++j) {
         /* first ghost layer, then second (handles nx == 1) */
         v[CE(-1, j)] = c->bc[0] == OR_WALL ? px * v[CE(0, j)] : v[CE(0, j)];
@@ -679,6 +702,7 @@ static void ghost2d(const or_cfg *c, double *v, double px, double py)
         v[CE(-2, j)] = c->bc[0] == OR_WALL ? px * v[CE(1, j)] : v[CE(0, j)];
         v[CE(nx + 1, j)] = c->bc[1] == OR_WALL ? px * v[CE(nx - 2, j)] : v[CE(nx - 1, j)];
     }
+#pragma omp parallel for
     for (int i = -2; i < nx + 2; ++i) {
         v[CE(i, -1)] = c->bc[2] == OR_WALL ? py * v[CE(i, 0)] : v[CE(i, 0)];
         v[CE(i, ny)] = c->bc[3] == OR_WALL ? py * v[CE(i, ny - 1)] : v[CE(i, ny - 1)];
@@ -713,6 +737,7 @@ static double *ext_nodes(const or_cfg *c)
 static void load_cells(const or_cfg *c, const double *src, double *dst)
 {
     const int nx = c->nx, ny = c->ny;
+#pragma omp parallel for
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) dst[CE(i, j)] = src[CI(i, j)];
 }
@@ -723,6 +748,7 @@ double or2d_cfl_dt(const or_cfg *c, const double *H, const double *h, const doub
     (void)H;
     double lmax = 0.0;
     size_t n = (size_t)c->nx * (size_t)c->ny;
+#pragma omp parallel for reduction(max : lmax)
     for (size_t k = 0; k < n; ++k) {
         double u = desing(h[k], q1[k], c->delta), v = desing(h[k], q2[k], c->delta);
         double cc = sqrt(c->g * h[k]);
@@ -749,6 +775,7 @@ static int hyp2d(const or_cfg *c, const double *H, const double *h, const double
     ghost2d(c, he, 1.0, 1.0); ghost2d(c, He, 1.0, 1.0);
     ghost2d(c, ae, -1.0, 1.0); ghost2d(c, be, 1.0, -1.0);
     size_t ne = (size_t)(nx + 4) * (ny + 4);
+#pragma omp parallel for
     for (size_t k = 0; k < ne; ++k) {
         ee[k] = he[k] - He[k];
         ue[k] = desing(he[k], ae[k], c->delta);
@@ -763,6 +790,7 @@ static int hyp2d(const or_cfg *c, const double *H, const double *h, const double
     double *fld[4] = {he, ee, ue, ve};
 
     /* x-direction reconstruction for cells i = -1 .. nx of interior rows */
+#pragma omp parallel for
     for (int j = 0; j < ny; ++j)
         for (int i = -1; i <= nx; ++i) {
             int dry = he[CE(i - 1, j)] <= c->hdry || he[CE(i, j)] <= c->hdry ||
@@ -776,6 +804,7 @@ static int hyp2d(const or_cfg *c, const double *H, const double *h, const double
             }
         }
     /* y-direction reconstruction for cells j = -1 .. ny of interior columns */
+#pragma omp parallel for
     for (int j = -1; j <= ny; ++j)
         for (int i = 0; i < nx; ++i) {
             int dry = he[CE(i, j - 1)] <= c->hdry || he[CE(i, j)] <= c->hdry ||
@@ -792,6 +821,7 @@ static int hyp2d(const or_cfg *c, const double *H, const double *h, const double
     /* x faces (I, j), I = 0 .. nx: normal = x (q1), tangential = y (q2) */
     double *DmX = calloc(3 * (size_t)(nx + 1) * ny, sizeof(double));
     double *DpX = calloc(3 * (size_t)(nx + 1) * ny, sizeof(double));
+#pragma omp parallel for
     for (int j = 0; j < ny; ++j)
         for (int I = 0; I <= nx; ++I) {
             size_t L = CE(I - 1, j), R = CE(I, j), f = 3 * ((size_t)j * (nx + 1) + I);
@@ -802,6 +832,7 @@ static int hyp2d(const or_cfg *c, const double *H, const double *h, const double
     /* y faces (i, J), J = 0 .. ny: normal = y (q2), tangential = x (q1) */
     double *DmY = calloc(3 * (size_t)nx * (ny + 1), sizeof(double));
     double *DpY = calloc(3 * (size_t)nx * (ny + 1), sizeof(double));
+#pragma omp parallel for
     for (int J = 0; J <= ny; ++J)
         for (int i = 0; i < nx; ++i) {
             size_t L = CE(i, J - 1), R = CE(i, J), f = 3 * ((size_t)J * nx + i);
@@ -811,6 +842,7 @@ static int hyp2d(const or_cfg *c, const double *H, const double *h, const double
         }
 
     /* cell update, Eq. (30) */
+#pragma omp parallel for reduction(+ : clamped)
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             size_t e = CE(i, j);
@@ -871,6 +903,7 @@ static void breaking2d(const or_cfg *c, const double *H, const double *h, double
         ue[k] = desing(he[k], ae[k], c->delta);
         ve[k] = desing(he[k], be[k], c->delta);
     }
+#pragma omp parallel for
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             double dq = (ae[CE(i + 1, j)] - ae[CE(i - 1, j)]) / (2 * dx)
@@ -883,6 +916,7 @@ static void breaking2d(const or_cfg *c, const double *H, const double *h, double
             q1[CI(i, j)] += dt * 2.0 * nu * du * Hx;
             q2[CI(i, j)] += dt * 2.0 * nu * du * Hy;
         }
+#pragma omp parallel for
     for (int J = 0; J <= ny; ++J)
         for (int I = 0; I <= nx; ++I) {
             size_t a = CE(I - 1, J - 1), b = CE(I, J - 1), d = CE(I - 1, J), e = CE(I, J);
@@ -909,7 +943,9 @@ static nh2d_cells nh2d_fields(const or_cfg *c, const double *H, const double *h)
     load_cells(c, h, f.h); load_cells(c, H, He);
     ghost2d(c, f.h, 1.0, 1.0); ghost2d(c, He, 1.0, 1.0);
     size_t ne = (size_t)(nx + 4) * (ny + 4);
+#pragma omp parallel for
     for (size_t k = 0; k < ne; ++k) f.s[k] = 2.0 * (f.h[k] - He[k]) - f.h[k];
+#pragma omp parallel for
     for (int j = -1; j <= ny; ++j)
         for (int i = -1; i <= nx; ++i) {
             f.X[CE(i, j)] = 0.5 * (f.s[CE(i + 1, j)] - f.s[CE(i - 1, j)]);
@@ -927,6 +963,7 @@ static void half_T(const or_cfg *c, const nh2d_cells *f, const double *pe, doubl
 {
     const int nx = c->nx, ny = c->ny;
     const double dx = c->dx, dy = c->dy;
+#pragma omp parallel for
     for (int j = -1; j <= ny; ++j)
         for (int i = -1; i <= nx; ++i) {
             size_t e = CE(i, j);
@@ -952,6 +989,7 @@ static void B_nodes(const or_cfg *c, const nh2d_cells *f, const double *Q1, cons
 {
     const int nx = c->nx, ny = c->ny;
     const double dx = c->dx, dy = c->dy;
+#pragma omp parallel for
     for (int J = 0; J <= ny; ++J)
         for (int I = 0; I <= nx; ++I) {
             size_t a = CE(I - 1, J - 1), b = CE(I, J - 1), d = CE(I - 1, J), e = CE(I, J);
@@ -982,6 +1020,7 @@ int or2d_rhs(const or_cfg *c, const double *H, const double *h, const double *q1
     double *Q1 = ext_cells(c), *Q2 = ext_cells(c), *tw = calloc(nn, sizeof(double));
     load_cells(c, q1, Q1); load_cells(c, q2, Q2);
     ghost2d(c, Q1, -1.0, 1.0); ghost2d(c, Q2, 1.0, -1.0);
+#pragma omp parallel for
     for (int J = 0; J <= ny; ++J)
         for (int I = 0; I <= nx; ++I) {
             double hc = 0.25 * (f.h[CE(I - 1, J - 1)] + f.h[CE(I, J - 1)] + f.h[CE(I - 1, J)]
@@ -990,6 +1029,7 @@ int or2d_rhs(const or_cfg *c, const double *H, const double *h, const double *q1
         }
     B_nodes(c, &f, Q1, Q2, NULL, NULL, NULL, NULL, tw, rhs);
     double sc = -8.0 * c->dx * c->dy / dt;
+#pragma omp parallel for
     for (size_t k = 0; k < nn; ++k) rhs[k] *= sc;
     free(Q1); free(Q2); free(tw);
     nh2d_free(&f);
@@ -1017,13 +1057,16 @@ static void apply_M_f(const or_cfg *c, const nh2d_cells *f, const double *p, dou
 {
     const int nx = c->nx, ny = c->ny;
     const size_t nn = (size_t)(nx + 1) * (ny + 1);
+#pragma omp parallel for
     for (int J = 0; J <= ny; ++J)
         for (int I = 0; I <= nx; ++I) m->pe[NE(I, J)] = p[NI(I, J)];
     ghostnodes2d(c, m->pe);
     half_T(c, f, m->pe, dt, m->TN, m->TS, m->TE, m->TW);
+#pragma omp parallel for
     for (size_t k = 0; k < nn; ++k) m->tw[k] = 2.0 * dt * p[k];   /* 2 h (dt p / h) */
     B_nodes(c, f, m->Z, m->Z, m->TN, m->TS, m->TE, m->TW, m->tw, out);
     double sc = 8.0 * c->dx * c->dy / dt;
+#pragma omp parallel for
     for (size_t k = 0; k < nn; ++k) out[k] *= sc;
 }
 
@@ -1061,31 +1104,37 @@ static int solve_f(const or_cfg *c, const nh2d_cells *f, const double *b, double
     int it = 0, status = -1;
     for (int restart = 0; restart < 20 && it < c->max_iter; ++restart) {
         apply_M_f(c, f, x, dt, r, &m);
+#pragma omp parallel for
         for (size_t k = 0; k < n; ++k) r[k] = b[k] - r[k];
         double rn = sqrt(dot(n, r, r));
         *resid = rn / bn;
         if (rn <= c->tol * bn) { status = 0; break; }
         memcpy(rh, r, n * sizeof(double));
         double rho = 1.0, alpha = 1.0, omega = 1.0;
+#pragma omp parallel for
         for (size_t k = 0; k < n; ++k) { pv[k] = 0.0; v[k] = 0.0; }
         while (it < c->max_iter) {
             ++it;
             double rho1 = dot(n, rh, r);
             if (rho1 == 0.0) break;
             double beta = (rho1 / rho) * (alpha / omega);
+#pragma omp parallel for
             for (size_t k = 0; k < n; ++k) pv[k] = r[k] + beta * (pv[k] - omega * v[k]);
             apply_M_f(c, f, pv, dt, v, &m);
             double rv = dot(n, rh, v);
             if (rv == 0.0) break;
             alpha = rho1 / rv;
+#pragma omp parallel for
             for (size_t k = 0; k < n; ++k) s[k] = r[k] - alpha * v[k];
             if (sqrt(dot(n, s, s)) <= 0.1 * c->tol * bn) {
+#pragma omp parallel for
                 for (size_t k = 0; k < n; ++k) x[k] += alpha * pv[k];
                 break;
             }
             apply_M_f(c, f, s, dt, t, &m);
             double tt = dot(n, t, t);
             omega = tt > 0.0 ? dot(n, t, s) / tt : 0.0;
+#pragma omp parallel for
             for (size_t k = 0; k < n; ++k) {
                 x[k] += alpha * pv[k] + omega * s[k];
                 r[k] = s[k] - omega * t[k];
@@ -1096,6 +1145,7 @@ static int solve_f(const or_cfg *c, const nh2d_cells *f, const double *b, double
     }
     if (status != 0) {
         apply_M_f(c, f, x, dt, r, &m);
+#pragma omp parallel for
         for (size_t k = 0; k < n; ++k) r[k] = b[k] - r[k];
         *resid = sqrt(dot(n, r, r)) / bn;
         status = *resid <= c->tol ? 0 : -1;
@@ -1138,6 +1188,7 @@ static void wtransport2d(const or_cfg *c, const double *hb, const double *wb,
     double *eb = ext_cells(c), *ei = ext_cells(c), *es = ext_cells(c);
     load_cells(c, hb, eb); load_cells(c, h, ei); load_cells(c, hs, es);
     ghost2d(c, eb, 1.0, 1.0); ghost2d(c, ei, 1.0, 1.0); ghost2d(c, es, 1.0, 1.0);
+#pragma omp parallel for
     for (int J = 0; J <= ny; ++J)
         for (int I = 0; I <= nx; ++I) {
             const double ax = (I == 0 || I == nx) ? 0.5 : 1.0;
@@ -1175,7 +1226,9 @@ static void wtransport2d(const or_cfg *c, const double *hb, const double *wb,
 /* Dry cells carry no discharge (see dry_discharge_1d). */
 static void dry_discharge_2d(const or_cfg *c, const double *h, double *q1, double *q2)
 {
+    if (!c->dry_zero) return;
     size_t n = (size_t)c->nx * c->ny;
+#pragma omp parallel for
     for (size_t k = 0; k < n; ++k)
         if (h[k] <= c->hdry) { q1[k] = 0.0; q2[k] = 0.0; }
 }
@@ -1198,6 +1251,7 @@ static int stage2d(const or_cfg *c, const double *H, const double *hb, const dou
         FY = calloc((size_t)nx * (ny + 1), sizeof(double));
     }
     int clamped = hyp2d(c, H, h, q1, q2, dt, ho, q1o, q2o, FX, FY);
+#pragma omp parallel for
     for (size_t k = 0; k < n; ++k) {
         ho[k] = a * hb[k] + bw * ho[k];
         q1o[k] = a * q1b[k] + bw * q1o[k];
@@ -1207,6 +1261,7 @@ static int stage2d(const or_cfg *c, const double *H, const double *hb, const dou
         wtransport2d(c, hb, wb, h, w, FX, FY, ho, a, bw, dt, wo);
         free(FX); free(FY);
     } else {
+#pragma omp parallel for
         for (size_t k = 0; k < nn; ++k) wo[k] = a * wb[k] + bw * w[k];
     }
     const double de = bw * dt;
@@ -1225,16 +1280,19 @@ static int stage2d(const or_cfg *c, const double *H, const double *hb, const dou
     /* correction: q1 += de (T_N + T_S)/2, q2 += de (T_E + T_W)/2 (Eq. 36); w += de p / h_c */
     double *pe = ext_nodes(c), *TN = ext_cells(c), *TS = ext_cells(c);
     double *TE = ext_cells(c), *TW = ext_cells(c);
+#pragma omp parallel for
     for (int J = 0; J <= ny; ++J)
         for (int I = 0; I <= nx; ++I) pe[NE(I, J)] = p[NI(I, J)];
     ghostnodes2d(c, pe);
     half_T(c, &f, pe, de, TN, TS, TE, TW);
+#pragma omp parallel for
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             size_t e = CE(i, j);
             q1o[CI(i, j)] += 0.5 * (TN[e] + TS[e]);
             q2o[CI(i, j)] += 0.5 * (TE[e] + TW[e]);
         }
+#pragma omp parallel for
     for (int J = 0; J <= ny; ++J)
         for (int I = 0; I <= nx; ++I) {
             double hc = 0.25 * (f.h[CE(I - 1, J - 1)] + f.h[CE(I, J - 1)] + f.h[CE(I - 1, J)]
@@ -1316,6 +1374,7 @@ void or2d_relax(const or_cfg *c, const double *H, double *h, double *q1, double 
                 const double *q2_t, const double *w_t, const double *p_t)
 {
     const int nx = c->nx, ny = c->ny;
+#pragma omp parallel for
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             double m = relax_m1(i, nx, c->dx, c->relax[0], c->relax[1]) *
@@ -1328,6 +1387,7 @@ void or2d_relax(const or_cfg *c, const double *H, double *h, double *q1, double 
             q1[k] = m * q1[k] + (1.0 - m) * (q1_t ? q1_t[k] : 0.0);
             q2[k] = m * q2[k] + (1.0 - m) * (q2_t ? q2_t[k] : 0.0);
         }
+#pragma omp parallel for
     for (int J = 0; J <= ny; ++J)
         for (int I = 0; I <= nx; ++I) {
             double m = relax_node1(I, nx, c->dx, c->relax[0], c->relax[1]) *

@@ -28,6 +28,15 @@
  *   relaxation zones (Sec. 4.4) ............ pinned (interior untouched, fixed point at the
  *                                           target, boundary cell = target, absorption of
  *                                           an outgoing solitary wave against a wall)
+ *   Manning friction (1D, 2D) .............. pinned (uniform flow on a flat bottom converges
+ *                                           at first order to the ODE dq/dt = -k |q| q)
+ *   or1d_cfl_dt / or2d_cfl_dt (Eq. 23) ..... pinned (uniform states with u != v, dx != dy;
+ *                                           fastest cell; mesh scaling; 2D -> 1D limit)
+ *   wet/dry fronts of the second step ...... measured (Sec. 4.5 literal form by default:
+ *                                           dry-cell discharge, dry-node pressure, rounding
+ *                                           sensitivity against the dry_zero option)
+ * Threads: the 2D loops run under OpenMP (or_set_threads); results are bitwise the same for
+ * every thread count (only loops over disjoint entries are parallel, all sums are serial).
  */
 #ifndef NH_ORACLE_H
 #define NH_ORACLE_H
@@ -35,6 +44,11 @@
 #ifdef __cplusplus
 extern "C" {
 #endif
+
+/* Threads of the 2D loops (OpenMP; n <= 0 leaves the count unchanged); returns the count
+ * before the call.  Results do not depend on it: only loops over disjoint entries run in
+ * parallel and every sum is serial. */
+int or_set_threads(int n);
 
 enum { OR_WALL = 0, OR_OUTFLOW = 1, OR_PERIODIC = 2 };
 
@@ -57,6 +71,9 @@ typedef struct {
                             cells; 0: Yamazaki's h w_t = p                                */
     double relax[4];     /* L_Rel of the generating / absorbing zone (Sec. 4.4) on the west,
                             east, south, north side; 0: none (1D: west, east)             */
+    int dry_zero;        /* 0: the second step as Sec. 4.5 states it, no truncation at
+                            wet/dry fronts; 1: q = 0 in dry cells (h <= hdry) after each
+                            stage (App. B A.2's premise q = w = 0 where h vanishes)       */
 } or_cfg;
 
 typedef struct {

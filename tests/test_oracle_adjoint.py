@@ -46,15 +46,16 @@ def test_forward_step_equals_c_oracle(bc):
         assert np.abs(got.numpy() - ref).max() <= 1e-11 * max(np.abs(ref).max(), 1e-30)
 
 
-def test_forward_wet_dry_equals_c_oracle():
+@pytest.mark.parametrize("dry_zero", [False, True])
+def test_forward_wet_dry_equals_c_oracle(dry_zero):
     wl = inputs.island_2d(n=24, L=9.6, center=(4.8, None), x0=2.0)
     ny, nx = wl.H.shape
     h = np.maximum(wl.eta + wl.H, 0)
-    c = O.cfg(nx, ny, dx=wl.dx, bc=wl.bc, tol=1e-15, max_iter=20000)
+    c = O.cfg(nx, ny, dx=wl.dx, bc=wl.bc, tol=1e-15, max_iter=20000, dry_zero=dry_zero)
     dt = 0.5 * O.cfl_dt_2d(c, wl.H, h, wl.q1, wl.q2)
     z = np.zeros((ny + 1, nx + 1))
     ho, ao, bo, wo, po, _ = O.step_2d(c, wl.H, h, wl.q1, wl.q2, z, z, dt)
-    ct = A.Cfg2(nx, ny, wl.dx, wl.dx, wl.bc)
+    ct = A.Cfg2(nx, ny, wl.dx, wl.dx, wl.bc, dry_zero=dry_zero)
     T = lambda a: torch.as_tensor(a, dtype=torch.float64)
     hh, aa, bb, ww, pp = A.step(ct, T(wl.H), T(h), T(wl.q1), T(wl.q2), T(z), dt)
     for got, ref in ((hh, ho), (aa, ao), (bb, bo), (pp, po)):
