@@ -9,9 +9,9 @@ the C file lists the readings taken where the paper is silent or garbled.
 Parity status: every function is pinned by ``tests/test_oracle_*.py``; the breaking terms
 (Sec. 3, Eq. 12) by closed forms on linear fields and by invariants; Manning friction by the
 decay of a uniform flow (first-order convergence to its ODE) and the Eq. (23) rate by closed
-forms on uniform states (``tests/test_oracle_friction_rate.py``).  Wet/dry fronts follow
-Sec. 4.5 literally (no truncation); ``cfg(dry_zero=True)`` sets q = 0 in dry cells after
-each stage instead (``tests/test_oracle_wetdry.py``).  The 2D loops run under OpenMP
+forms on uniform states (``tests/test_oracle_friction_rate.py``).  ``cfg(dry_zero=False)``
+runs the wet/dry fronts as Sec. 4.5 states them (no truncation); ``dry_zero=True`` sets q = 0 in dry cells after
+each stage, and is the default of ``cfg`` (``tests/test_oracle_wetdry.py`` records why).  The 2D loops run under OpenMP
 (``set_threads``) with results bitwise independent of the thread count.  ``cfg(w_transport=True)`` selects the
 energy-consistent w equation of Sec. 2 (pinned by donor-cell upwind on uniform flow and
 by invariants); ``relax_1d`` / ``relax_2d`` and ``cfg(relax=...)`` the relaxation zones of
@@ -125,7 +125,7 @@ def cfg(nx: int, ny: int = 1, dx: float = 1.0, dy: float | None = None, bc=(WALL
         manning: float = 0.0, B1: float = 0.15, B2: float = 0.5, breaking: bool = False,
         nonhydro: bool = True, tol: float = 1e-13, max_iter: int = 4000,
         w_transport: bool = False, relax=(0.0, 0.0, 0.0, 0.0),
-        dry_zero: bool = False) -> Cfg:
+        dry_zero: bool = True) -> Cfg:
     c = Cfg()
     c.nx, c.ny = int(nx), int(ny)
     c.dx = float(dx)

@@ -48,7 +48,7 @@ class Cfg2:
     delta: float = 1e-5
     hdry: float = 1e-5
     frozen_limiter: bool = False   # derivative with the limiter ratio held fixed (see slope())
-    dry_zero: bool = False         # q = 0 in dry cells after each stage (the C oracle's option)
+    dry_zero: bool = True          # q = 0 in dry cells after each stage (as the C oracle's cfg)
 
 
 def desing(h, q, delta):
@@ -294,7 +294,7 @@ def stage(c: Cfg2, H, hb, q1b, q2b, wb, h, q1, q2, w, a, bw, dt):
     ao = ao + 0.5 * (TN + TS)[1:-1, 1:-1]
     bo = bo + 0.5 * (TE + TW)[1:-1, 1:-1]
     wo = wo + de * p * desing(hcn, torch.ones_like(hcn), c.delta)
-    if not c.dry_zero:   # Sec. 4.5: no truncation at wet/dry fronts
+    if not c.dry_zero:   # Sec. 4.5 as stated: no truncation at wet/dry fronts
         return ho, ao, bo, wo, p
     wet = ho > c.hdry
     z = torch.zeros_like(ao)

@@ -41,11 +41,13 @@
  *   - Runge-Kutta (Sec. 4.3, Sec. 6 "steps 1-4 are repeated twice"): the projection of the
  *     second stage acts on the Shu-Osher combination, so U^{n+1} itself satisfies the
  *     discrete constraint; p^{n+1} is that projection's pressure.
- *   - Wet/dry fronts in the second step (Sec. 4.5): no special treatment, as the paper
- *     states.  The correction T_NH has a term p (2 eta - h)_x that does not vanish with h,
- *     so a dry cell next to the shoreline takes up a small discharge; its velocity stays 0
- *     through the desingularisation.  The option dry_zero = 1 sets q = 0 in dry cells
- *     after each stage instead (App. B A.2 takes q = w = 0 where the depth vanishes).
+ *   - Wet/dry fronts in the second step (Sec. 4.5 states that they need no special
+ *     treatment): the correction T_NH has a term p (2 eta - h)_x that does not vanish
+ *     with h, so a dry cell next to the shoreline takes up a small discharge.  Whether a
+ *     later step clamps that cell's depth (and zeroes the discharge) then hangs on depths
+ *     of 1e-20 m and below that the flux arithmetic leaves in dry cells.  dry_zero = 1
+ *     sets q = 0 in dry cells after each stage (App. B A.2 takes q = w = 0 where the depth
+ *     vanishes), which removes that dependence; dry_zero = 0 is the literal form.
  *   - dt (Eq. 23) in 2D: CFL / max((|u|+c)/dx + (|v|+c)/dy), from the current state.
  *   - The 2D system is solved by unpreconditioned BiCGStab to a relative residual tol.
  *   - Energy-consistent w equation (w_transport = 1; Sec. 2 names the system of [7] and
@@ -571,10 +573,10 @@ static void wtransport1d(const or_cfg *c, const double *hb, const double *wb,
     free(eb); free(ei); free(es);
 }
 
-/* Option dry_zero = 1: dry cells carry no discharge, q = 0 where h <= hdry at the end of
- * each stage (the premise of App. B A.2, q = w = 0 where the depth vanishes, imposed).
- * The default (dry_zero = 0) is the second step as Sec. 4.5 states it, with no special
- * treatment and no truncation at wet/dry fronts. */
+/* dry_zero = 1: dry cells carry no discharge, q = 0 where h <= hdry at the end of each
+ * stage (the premise of App. B A.2, q = w = 0 where the depth vanishes, imposed).
+ * dry_zero = 0 is the second step as Sec. 4.5 states it, with no special treatment and no
+ * truncation at wet/dry fronts. */
 static void dry_discharge_1d(const or_cfg *c, const double *h, double *q)
 {
     if (!c->dry_zero) return;

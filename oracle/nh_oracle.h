@@ -32,9 +32,9 @@
  *                                           at first order to the ODE dq/dt = -k |q| q)
  *   or1d_cfl_dt / or2d_cfl_dt (Eq. 23) ..... pinned (uniform states with u != v, dx != dy;
  *                                           fastest cell; mesh scaling; 2D -> 1D limit)
- *   wet/dry fronts of the second step ...... measured (Sec. 4.5 literal form by default:
- *                                           dry-cell discharge, dry-node pressure, rounding
- *                                           sensitivity against the dry_zero option)
+ *   wet/dry fronts of the second step ...... measured (the Sec. 4.5 literal form against
+ *                                           the dry_zero option: dry-cell discharge, dry-node
+ *                                           pressure, rounding sensitivity)
  * Threads: the 2D loops run under OpenMP (or_set_threads); results are bitwise the same for
  * every thread count (only loops over disjoint entries are parallel, all sums are serial).
  */
@@ -73,7 +73,8 @@ typedef struct {
                             east, south, north side; 0: none (1D: west, east)             */
     int dry_zero;        /* 0: the second step as Sec. 4.5 states it, no truncation at
                             wet/dry fronts; 1: q = 0 in dry cells (h <= hdry) after each
-                            stage (App. B A.2's premise q = w = 0 where h vanishes)       */
+                            stage (App. B A.2's premise q = w = 0 where h vanishes; the
+                            default of the Python wrapper's cfg())                        */
 } or_cfg;
 
 typedef struct {

@@ -1,10 +1,11 @@
 """Wet/dry fronts in the second step (Sec. 4.5) and the oracle's thread-count invariance.
 
 Sec. 4.5 states that the non-hydrostatic step needs no special treatment at wet/dry fronts
-and no truncation.  The oracle follows that by default; ``dry_zero`` is the option that sets
-q = 0 in dry cells after each stage (App. B A.2 takes q = w = 0 where h vanishes).  These
-tests record what the literal form does in dry cells on the conical island, and that
-neither form is better conditioned than the other.
+and no truncation (``dry_zero=False``); ``dry_zero=True``, the default, sets q = 0 in dry
+cells after each stage (App. B A.2 takes q = w = 0 where h vanishes).  These tests record
+what the literal form does in dry cells: a small discharge, no worse conditioning under
+perturbations of the wet depths -- but results that hang on depths of 1e-20 m and below,
+which a state held as eta = h - H (as the FP32 form must hold it) cannot represent.
 """
 import numpy as np
 import pytest
@@ -74,6 +75,33 @@ def test_both_forms_equally_sensitive_to_rounding(steps):
         spread[dz] = np.abs(per[0] - ref[0]).max() / np.abs(ref[0]).max()
     assert spread[True] > 0.0
     assert spread[False] <= 2.0 * spread[True], spread
+
+
+def test_literal_form_depends_on_depths_below_1e20():
+    """After 4 literal steps on an uneven ensemble domain with dry patches, the flux
+    arithmetic has left depths down to ~1e-128 m in a few dry cells.  Setting just those
+    depths (below 1e-20 m) to 0 -- what a state held as eta = h - H gives, since
+    (h - H) + H rounds them away -- moves the next step's p by ~1e-5 and its discharges by
+    ~1e-6 (measured 8.9e-6 and 2.8e-6): whether the depth clamp zeroes a dry cell's
+    discharge turns on those depths.  With q = 0 in dry cells no such depths arise and the
+    step is unchanged."""
+    w = inputs.ensemble_member(1, sides=(40,))
+    rel = lambda x, y: np.abs(x - y).max() / np.abs(y).max()
+    out = {}
+    for dz in (False, True):
+        c = O.cfg(w.nx, w.ny, dx=w.dx, dy=w.dy, bc=w.bc, tol=1e-14, dry_zero=dz)
+        zn = np.zeros((w.ny + 1, w.nx + 1))
+        h, a, b, wv, p, t, s, it = O.run_2d(c, w.H, np.maximum(w.eta + w.H, 0), w.q1, w.q2,
+                                            zn, zn, max_steps=4)
+        tiny = (h > 0) & (h < 1e-20)
+        dt = O.cfl_dt_2d(c, w.H, h, a, b)
+        A = O.step_2d(c, w.H, h, a, b, wv, p, dt)
+        B = O.step_2d(c, w.H, np.where(tiny, 0.0, h), a, b, wv, p, dt)
+        out[dz] = (tiny.sum(), rel(B[4], A[4]), max(rel(B[1], A[1]), rel(B[2], A[2])))
+    n, dp, dq = out[False]
+    assert n > 0 and dp > 1e-7 and dq > 1e-8, out[False]
+    n, dp, dq = out[True]
+    assert n == 0 and dp == 0.0 and dq == 0.0, out[True]
 
 
 def test_threads_do_not_change_results_bitwise():
