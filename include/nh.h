@@ -53,6 +53,8 @@ extern "C" {
 #define NH_ECUDA (-3)       /* CUDA runtime error                                    */
 #define NH_ENOCONV (-4)     /* pressure solve did not reach tol within max_iter      */
 #define NH_ENONFINITE (-5)  /* a non-finite value appeared in the state              */
+#define NH_ETIMEOUT (-6)    /* a bounded device-side wait (a Chebyshev pass waiting for its
+                               staged copies) ran out of polls; the solve was abandoned   */
 
 enum { NH_BC_WALL = 0, NH_BC_OUTFLOW = 1, NH_BC_PERIODIC = 2 /* 1D only, west and east */ };
 enum {
@@ -117,6 +119,22 @@ typedef struct {
                            2D m is the product of the x and y factors.  The
                            target is the lake at rest (absorbing) until
                            nh_set_relax_target sets another.  Single-domain handles only. */
+    int dry_zero;       /* 1 (default): q = 0 in dry cells (h <= hdry) at the end of each
+                           stage, i.e. the premise of App. B A.2 (q = w = 0 where the depth
+                           vanishes) imposed; 0: the second step exactly as Sec. 4.5 states
+                           it, with no special treatment and no truncation at wet/dry
+                           fronts (the correction's p (2 eta - h)_x term then gives dry
+                           cells next to the shoreline a small discharge).  nh_step_taped
+                           and nh_adjoint_step require 1.                                */
+    int wait_polls;     /* polls of each bounded wait of the register-form Chebyshev pass
+                           for its staged copies (<= 0: the default, 2^22).  A wait that
+                           runs out ends the solve with NH_ETIMEOUT; the pass issues no
+                           further copies and drains those in flight (bounded) first.   */
+    int capture;        /* 1 (default): 2D steps (Chebyshev solver once its pass form is
+                           known, or the hydrostatic step) run as one CUDA graph per step,
+                           the solver loops as conditional WHILE nodes on the device, the
+                           host waiting once per step; 0: every kernel launched eagerly and
+                           the solve polled from the host.  Results are the same bits.    */
 } nh_params;
 
 typedef struct {
@@ -142,7 +160,8 @@ typedef struct nh_handle nh_handle;
 /* Fill p with the paper's defaults: g = 9.81, CFL 0.9, delta = 1e-5, hdry = delta,
  * n = 0, B1 = 0.15, B2 = 0.5 (Sec. 7.4), breaking off, non-hydrostatic on, Chebyshev
  * solver, tol 1e-12, max_iter 2000, FP64, fixed_dt 0, eps_dp 0, exact adjoint, pass
- * form chosen by timing (cheb_form = -1), w equation h w_t = p (NH_W_YAMAZAKI). */
+ * form chosen by timing (cheb_form = -1), w equation h w_t = p (NH_W_YAMAZAKI), q = 0 in
+ * dry cells (dry_zero = 1), default wait limit (wait_polls = 0), captured steps (capture = 1). */
 int nh_default_params(nh_params *p);
 
 /* Number of kernel forms of the Chebyshev-scheduled Jacobi pass (Sec. 5's scheduled
@@ -159,7 +178,8 @@ int nh_create(const nh_grid *grid, const double *H, const nh_params *params, voi
 
 /* Set the state.  eta, q1, q2: [ny][nx]; w, p: [ny+1][nx+1] (may be NULL: set to 0);
  * q2 may be NULL in 1D.  t: simulation time of the state.  Recomputes the Eq. (23)
- * step of the new state. */
+ * step of the new state.  NH_ENONFINITE when a value of the input is NaN or infinite
+ * (checked on the device; the state is then undefined until a successful call). */
 int nh_set_state(nh_handle *h, const void *eta, const void *q1, const void *q2,
                  const void *w, const void *p, double t, int where);
 
@@ -168,7 +188,12 @@ int nh_get_state(nh_handle *h, void *eta, void *q1, void *q2, void *w, void *p, 
                  int where);
 
 /* Advance one time step.  dt > 0: use it; dt <= 0: the Eq. (23) step of the current
- * state (or params.fixed_dt when that is > 0).  *dt_taken (may be NULL) receives it. */
+ * state (or params.fixed_dt when that is > 0).  *dt_taken (may be NULL) receives it.
+ * Returns NH_ENOCONV when a pressure solve stopped at max_iter or broke down (the step is
+ * still taken, with that solve's last iterate), NH_ENONFINITE when the new state holds a
+ * NaN or infinity, NH_ETIMEOUT when a bounded device-side wait ran out (nh_params.
+ * wait_polls); after NH_ENONFINITE or NH_ETIMEOUT the state is undefined until the next
+ * nh_set_state. */
 int nh_step(nh_handle *h, double dt, double *dt_taken);
 
 /* Advance until t >= t_end (last step shortened to land on t_end; t_end <= 0: no time
@@ -388,6 +413,15 @@ int nh_debug_hyperbolic(nh_handle *h, double dt, void *eta_out, void *q1_out, vo
  * dy = dx).  x is a node array in the handle's precision. */
 int nh_debug_system(nh_handle *h, double dt, const void *x, void *rhs_out, void *mx_out,
                     int where);
+
+/* Failure injection for the bounded waits (the paper has no counterpart): the next
+ * Chebyshev pass of the handle that runs in a register form (nh_params.cheb_form 5-7 in
+ * FP32, 3 in FP64) lets block `block` announce its first region's bytes on its mbarrier
+ * without issuing the copies, so that this block's first wait runs out of
+ * nh_params.wait_polls polls with no copy in flight.  The step then returns NH_ETIMEOUT,
+ * and the handle's state is undefined until the next nh_set_state.  Later passes are
+ * unaffected.  NH_EINVAL for 1D or BiCGStab handles, or block < 0. */
+int nh_debug_stall_copies(nh_handle *h, int block);
 
 #ifdef __cplusplus
 }

@@ -34,6 +34,7 @@ struct Base {
     virtual int cheb_form() const = 0;   // pass form in use, -1 while timing
     virtual int debug_hyp(double dt, void* e, void* a, void* b, int where) = 0;
     virtual int debug_system(double dt, const void* x, void* rhs, void* mx, int where) = 0;
+    virtual int debug_stall_copies(int block) = 0;
     virtual int profile_enable(int on) = 0;
     virtual int profile_read(nh_profile_t* out) = 0;
     virtual size_t tape_bytes() = 0;
@@ -42,12 +43,14 @@ struct Base {
                              void* wb, void* Hb) = 0;
 };
 
-// Event pairs around kernel launches, accumulated per kernel class.
+// Intervals between recorded events (around eager launches, or between the event nodes of
+// a captured step), accumulated per kernel class with their launch counts.
 struct Prof {
     bool on = false;
     std::vector<cudaEvent_t> pool;
-    std::vector<int> cls;
     size_t used = 0;
+    struct Iv { cudaEvent_t a, b; int cls; long long n; };
+    std::vector<Iv> iv;
     long long launches[NH_K_COUNT] = {};
     double ms[NH_K_COUNT] = {};
 
@@ -64,18 +67,20 @@ struct Prof {
         }
         return pool[used++];
     }
+    void add(cudaEvent_t a, cudaEvent_t b, int cls, long long n) { iv.push_back({a, b, cls, n}); }
     void flush()
     {
-        if (used == 0) return;
-        cudaEventSynchronize(pool[used - 1]);
-        for (size_t k = 0; k < cls.size(); ++k) {
-            float t = 0.f;
-            cudaEventElapsedTime(&t, pool[2 * k], pool[2 * k + 1]);
-            ms[cls[k]] += t;
-            launches[cls[k]] += 1;
+        if (!iv.empty()) {
+            cudaEventSynchronize(iv.back().b);
+            for (const Iv& v : iv) {
+                float t = 0.f;
+                cudaEventElapsedTime(&t, v.a, v.b);
+                ms[v.cls] += t;
+                launches[v.cls] += v.n;
+            }
         }
+        iv.clear();
         used = 0;
-        cls.clear();
     }
     void reset()
     {
@@ -128,6 +133,7 @@ struct Impl : Base {
     StepCtl* h_stctl = nullptr;
     int last_solve_iters = 0;
     int last_cheb_passes = 0;
+    int stall_block = -1;       // test hook (nh_debug_stall_copies): next register pass only
     RelaxZ Z{};                 // relaxation zones (Sec. 4.4); relax_on: any side has one
     bool relax_on = false;
 
@@ -138,6 +144,11 @@ struct Impl : Base {
         if (h_stctl) cudaFreeHost(h_stctl);
         for (cudaEvent_t e : vt_ev)
             if (e) cudaEventDestroy(e);
+        graph_destroy();
+        if (g_side) cudaStreamDestroy(g_side);
+        if (g_cap) cudaStreamDestroy(g_cap);
+        if (h_dt) cudaFreeHost(h_dt);
+        if (h_sstat) cudaFreeHost(h_sstat);
     }
 
     template <typename U>
@@ -164,7 +175,7 @@ struct Impl : Base {
         P.bcw = g.bc[0]; P.bce = g.bc[1]; P.bcs = g.bc[2]; P.bcn = g.bc[3];
         P.dx = (T)g.dx; P.dy = (T)(dim == 2 ? g.dy : g.dx);
         P.g = (T)q.g; P.delta = (T)q.delta; P.hdry = (T)q.hdry; P.manning = (T)q.manning_n;
-        P.B1 = (T)q.B1; P.breaking = q.breaking;
+        P.B1 = (T)q.B1; P.breaking = q.breaking; P.dry_zero = q.dry_zero ? 1 : 0;
         pass_variant = q.cheb_form;
         nc = (size_t)g.nx * g.ny;
         nn = dim == 2 ? (size_t)(g.nx + 1) * (g.ny + 1) : (size_t)(g.nx + 1) * g.ny;
@@ -282,10 +293,11 @@ struct Impl : Base {
     {
         if (!prof.on) { f(); return; }
         if (prof.used + 2 > 16384) prof.flush();
-        cudaEventRecord(prof.next(), hd->s);
+        cudaEvent_t a = prof.next(), b = prof.next();
+        cudaEventRecord(a, hd->s);
         f();
-        cudaEventRecord(prof.next(), hd->s);
-        prof.cls.push_back(cls);
+        cudaEventRecord(b, hd->s);
+        prof.add(a, b, cls, 1);
     }
 
     int profile_enable(int on) override
@@ -326,9 +338,19 @@ struct Impl : Base {
         else launch_fill<T>(Ln, B.p, nn, T(0));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(hd, e, "nh_set_state");
+        // the input must be finite (checked on the device; the rate kernel's max would
+        // pass over a NaN)
+        cudaMemsetAsync(&B.stctl->nonfinite, 0, sizeof(int), s);
+        launch_nonfinite<T>(Lc, B.eta, nc, B.stctl);
+        launch_nonfinite<T>(Lc, B.q1, nc, B.stctl);
+        launch_nonfinite<T>(Lc, B.q2, nc, B.stctl);
+        launch_nonfinite<T>(Ln, B.w, nn, B.stctl);
+        launch_nonfinite<T>(Ln, B.p, nn, B.stctl);
         double lam = 0.0;
         int rc = lambda(&lam);
         if (rc != NH_OK) return rc;
+        if (h_stctl->nonfinite)
+            return fail(hd, NH_ENONFINITE, "nh_set_state: non-finite value in the input state");
         hd->dt_next = lam > 0.0 ? hd->prm.cfl / lam : 0.0;
         return NH_OK;
     }
@@ -398,8 +420,6 @@ struct Impl : Base {
         int passes_launched = 0;
         ++solves;
         int batch = last_cheb_passes > 2 ? last_cheb_passes - 1 : 4;
-        double best = 1e300;
-        int stale = 0;
         for (;;) {
             for (int k = 0; k < batch; ++k) {
                 int rc = 0;
@@ -415,9 +435,13 @@ struct Impl : Base {
                 T* pa = odd ? B.v[1] : B.r;
                 T* xb = odd ? B.dp : B.v[0];
                 T* pb = odd ? B.r : B.v[1];
+                const unsigned polls = hd->prm.wait_polls > 0 ? (unsigned)hd->prm.wait_polls
+                                                              : kDefaultWaitPolls;
                 K_(NH_K_CHEB_PASS, [&] {
-                    rc = launch_cheb_pass<T>(P, hd->s, B, xa, pa, xb, pb, B.partials, v);
+                    rc = launch_cheb_pass<T>(P, hd->s, B, xa, pa, xb, pb, B.partials, v, polls,
+                                             stall_block);
                 });
+                stall_block = -1;   // the test hook acts on one pass
                 if (timed) {
                     cudaEventRecord(vt_ev[vt_used + 1], hd->s);
                     vt_var[vt_used / 2] = v;
@@ -436,32 +460,34 @@ struct Impl : Base {
                     if (vt_solve[k] == solves) vt_ok[k] = vt_pass[k] < ran ? 1 : 0;
                 if (vt_used >= kVT || (vt_next > 0 && solves >= 12)) choose_pass_variant();
             }
-            if (h_sctl->status == 6)
-                return fail(hd, NH_ECUDA, "Chebyshev pass: a wait for staged copies timed out");
+            if (h_sctl->status == 6 || h_sctl->status == 7) {
+                hd->last_iters[stage] = h_sctl->sweeps;
+                return fail(hd, NH_ETIMEOUT,
+                            h_sctl->status == 6
+                                ? "Chebyshev pass: a wait for staged copies ran out of polls "
+                                  "(the copies issued were drained; the solve was abandoned)"
+                                : "Chebyshev pass: a wait for staged copies ran out of polls "
+                                  "and so did the drain of the copies in flight");
+            }
             if (h_sctl->status == 4) return fallback(stage, false);   // not diagonally dominant
-            if (h_sctl->done) settle_passes(h_sctl->sweeps / K);
-            if (h_sctl->done) break;
-            // stagnation (rounding floor of the precision, or a spectrum the Gershgorin
-            // interval does not describe): continue with BiCGStab from the current dp
-            // (with criterion (32) the solve is the paper's relaxation run to its own stop:
-            // only a residual that no longer falls at all is a stall)
-            const double fall = hd->prm.eps_dp > 0.0 ? 0.99 : 0.81;
-            if (h_sctl->rr < fall * best) { best = h_sctl->rr; stale = 0; }
-            else if (++stale >= 4) {
-                const int done_sweeps = h_sctl->sweeps;
-                hd->solver_iters += done_sweeps;
-                last_cheb_passes = done_sweeps / K;
-                // the passes launched so far all ran (the solve is not done)
-                settle_passes(passes_launched);
+            if (!h_sctl->done) { batch = 2; continue; }
+            settle_passes(h_sctl->sweeps / K);
+            if (h_sctl->status == 5) {
+                // stalled (cheb_finish_stall: the rounding floor of the precision, or a
+                // spectrum the Gershgorin interval does not describe): continue with
+                // BiCGStab from the current dp (under criterion (32) only a residual that
+                // no longer falls at all counts as stalled)
+                last_cheb_passes = h_sctl->sweeps / K;
                 if (accept_stall) {   // adjoint solves: the precision's floor is accepted
-                    hd->last_iters[stage] = done_sweeps;
+                    hd->solver_iters += h_sctl->sweeps;
+                    hd->last_iters[stage] = h_sctl->sweeps;
                     hd->last_resid[stage] =
                         h_sctl->bdb > 0.0 ? std::sqrt(h_sctl->rr / h_sctl->bdb) : 0.0;
                     return NH_OK;
                 }
                 return fallback(stage, true);
             }
-            batch = 2;
+            break;
         }
         const int sweeps = h_sctl->sweeps;
         last_cheb_passes = sweeps / K;
@@ -576,6 +602,319 @@ struct Impl : Base {
         return rc;
     }
 
+    // ---- steps captured as CUDA graphs (2D; Chebyshev solver once its pass form is known,
+    // or the hydrostatic step alone).  One graph holds a whole step: the step's dt is copied
+    // from pinned host memory by its first node, the kernels read it from device memory,
+    // the pressure solve is a conditional WHILE node over pairs of passes (its condition
+    // kernel reads the solve's done flag), a stalled or not diagonally dominant solve
+    // continues in a second WHILE node of BiCGStab iterations, and the last nodes copy the
+    // step's control blocks to pinned host memory: the host waits once per step, on the
+    // step's end, and polls nothing.  Results are those of the eagerly launched step bit for
+    // bit (same kernels, same arguments; the iterate of a solve that ends on an odd pass is
+    // read from its buffer by the correction instead of swapping pointers on the host).
+    cudaGraph_t g_graph = nullptr;
+    cudaGraphExec_t g_exec = nullptr;
+    cudaStream_t g_cap = nullptr;    // the step is captured on this stream (the caller's may
+                                     // be the legacy default stream, which cannot capture)
+                                     // and launched on the caller's
+    cudaStream_t g_side = nullptr;   // capture of the WHILE bodies
+    T* g_p = nullptr;                // B.p when captured (the p / palt roles)
+    bool g_prof = false;             // captured with event nodes (profiling)
+    bool g_failed = false;           // a capture failed: the handle stays eager
+    double* d_dt = nullptr;          // the step's dt (device) and its pinned source
+    double* h_dt = nullptr;
+    unsigned* d_loopc = nullptr;     // [pass pairs, BiCGStab pairs] of the running stage
+    SolveStat* d_sstat = nullptr;    // per stage, and pinned copies written by the graph
+    SolveStat* h_sstat = nullptr;
+    std::vector<cudaGraphNode_t> g_evnodes;   // event record nodes (profiling)
+    struct GIv { int a, b, cls, stage; };      // interval between event nodes a and b
+    std::vector<GIv> g_iv;
+    bool capturing = false;
+
+    bool graph_mode() const
+    {
+        const nh_params& q = hd->prm;
+        // (after one eager step: the kernels' one-time attribute and occupancy set-up runs
+        // outside the capture)
+        return q.capture && dim == 2 && !g_failed && stall_block < 0 && eager_steps > 0 &&
+               (!q.nonhydrostatic || (q.solver == NH_SOLVER_CHEBYSHEV && pass_variant >= 0));
+    }
+
+    void graph_destroy()
+    {
+        if (g_exec) cudaGraphExecDestroy(g_exec);
+        if (g_graph) cudaGraphDestroy(g_graph);
+        g_exec = nullptr;
+        g_graph = nullptr;
+        g_evnodes.clear();
+        g_iv.clear();
+    }
+
+    // an event record node (profiling), returned as its index
+    template <typename Chk>
+    int gev(cudaStream_t st, Chk& chk)
+    {
+        if (!g_prof) return -1;
+        cudaEvent_t e = prof.next();
+        chk(cudaEventRecordWithFlags(e, st, cudaEventRecordExternal));
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        chk(cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &nd));
+        g_evnodes.push_back(nd ? deps[0] : nullptr);
+        return (int)g_evnodes.size() - 1;
+    }
+
+    // WHILE node on the capturing stream: `pre` (on that stream) sets the condition before
+    // the first iteration; `body` is captured into the node's body graph on g_side.
+    template <typename Chk, typename Pre, typename Body>
+    void add_while(Chk& chk, Pre&& pre, Body&& body)
+    {
+        cudaStream_t st = hd->s;
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t g = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        chk(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+        cudaGraphConditionalHandle h = 0;
+        chk(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+        pre(st, h);
+        chk(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd));
+        // (the params union has no default constructor: zeroed storage)
+        alignas(cudaGraphNodeParams) unsigned char npb[sizeof(cudaGraphNodeParams)] = {};
+        cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(npb);
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node = nullptr;
+        chk(cudaGraphAddNode(&node, g, deps, nullptr, nd, &np));
+        if (!node) return;
+        cudaGraph_t bodyg = np.conditional.phGraph_out[0];
+        chk(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1,
+                                                cudaStreamSetCaptureDependencies));
+        chk(cudaStreamBeginCaptureToGraph(g_side, bodyg, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal));
+        body(g_side, h);
+        chk(cudaGetLastError());
+        cudaGraph_t bout = nullptr;
+        chk(cudaStreamEndCapture(g_side, &bout));
+    }
+
+    // One stage of a captured step (the graph's share of stage2d and solve_cheb).
+    template <typename Chk>
+    void stage2d_capture(int s, Chk& chk)
+    {
+        const nh_params& q = hd->prm;
+        cudaStream_t st = hd->s;
+        const T a = s == 0 ? T(0) : T(0.5), b = s == 0 ? T(1) : T(0.5);
+        const T* ein = s == 0 ? B.eta : B.eta1;
+        const T* ain = s == 0 ? B.q1 : B.q11;
+        const T* bin = s == 0 ? B.q2 : B.q21;
+        const T* win = s == 0 ? B.w : B.w1;
+        T* eo = s == 0 ? B.eta1 : B.eta;
+        T* ao = s == 0 ? B.q11 : B.q1;
+        T* bo = s == 0 ? B.q21 : B.q2;
+        T* wo = s == 0 ? B.w1 : B.w;
+        const bool wt = B.wt != nullptr;
+        const int K = cheb_sweeps_per_pass<T>();
+        auto iv = [&](int e0, int e1, int cls) {
+            if (e0 >= 0 && e1 >= 0) g_iv.push_back({e0, e1, cls, s});
+        };
+        chk(cudaMemsetAsync(d_loopc, 0, 2 * sizeof(unsigned), st));
+        const int e0 = gev(st, chk);
+        launch_hyp2d<T>(P, Lc, ein, ain, bin, B.eta, B.q1, B.q2, B.H, a, b, T(0), B.etas, B.q1s,
+                        B.q2s, B.stctl, B.fmx, B.fmy, d_dt);
+        int e1 = gev(st, chk);
+        iv(e0, e1, NH_K_HYPERBOLIC);
+        if (wt) {
+            launch_wtrans2d<T>(P, Ln, B.eta, ein, B.etas, B.H, B.w, win, B.fmx, B.fmy, a, b,
+                               T(0), B.wt, d_dt);
+            const int ew = gev(st, chk);
+            iv(e1, ew, NH_K_W_TRANSPORT);
+            e1 = ew;
+        }
+        launch_asm2d<T>(P, Ln, B, wt ? B.wt : win, wt ? B.wt : B.w, wt ? T(0) : a,
+                        wt ? T(1) : b, T(0), q.nonhydrostatic ? 1 : 0, q.nonhydrostatic ? 1 : 0,
+                        q.tol * q.tol, q.max_iter, q.nonhydrostatic ? K : 0, B.partials, B.sctl,
+                        1, d_dt, b);
+        const int e2 = gev(st, chk);
+        iv(e1, e2, NH_K_ASSEMBLY);
+        int e3 = e2;
+        if (q.nonhydrostatic) {
+            chk(cudaMemsetAsync(B.r, 0, nn * sizeof(T), st));
+            chk(cudaMemsetAsync(B.dp, 0, nn * sizeof(T), st));
+            const unsigned polls = q.wait_polls > 0 ? (unsigned)q.wait_polls : kDefaultWaitPolls;
+            const unsigned pair_cap = (unsigned)(q.max_iter / (2 * K) + 2);
+            int prc = 0;
+            // WHILE (solve not done) { pass (dp, r) -> (v0, v1); pass (v0, v1) -> (dp, r) }
+            add_while(chk,
+                      [&](cudaStream_t ps, cudaGraphConditionalHandle h) {
+                          launch_loop_cond(ps, h, B.sctl, d_loopc, pair_cap, 0);
+                      },
+                      [&](cudaStream_t bs, cudaGraphConditionalHandle h) {
+                          prc |= launch_cheb_pass<T>(P, bs, B, B.dp, B.r, B.v[0], B.v[1],
+                                                     B.partials, pass_variant, polls, -1);
+                          prc |= launch_cheb_pass<T>(P, bs, B, B.v[0], B.v[1], B.dp, B.r,
+                                                     B.partials, pass_variant, polls, -1);
+                          launch_loop_cond(bs, h, B.sctl, d_loopc, pair_cap, 1);
+                      });
+            if (prc != 0) chk(cudaErrorLaunchFailure);
+            // fallback: BiCGStab from the passes' iterate (moved to dp when odd)
+            launch_fb_begin(st, B.sctl);
+            Launch Lns = Ln;
+            launch_settle_fb<T>(Lns, B.sctl, B.v[0], B.dp, nn, K);
+            launch_bicg_init<T>(P, Ln, B, B.partials, 1);
+            const unsigned bicg_cap = (unsigned)(q.max_iter / 2 + 2);
+            add_while(chk,
+                      [&](cudaStream_t ps, cudaGraphConditionalHandle h) {
+                          launch_loop_cond(ps, h, B.sctl, d_loopc + 1, bicg_cap, 0);
+                      },
+                      [&](cudaStream_t bs, cudaGraphConditionalHandle h) {
+                          Launch Lb = Ln;
+                          Lb.s = bs;
+                          for (int par = 0; par < 2; ++par)
+                              for (int ph = 0; ph < 3; ++ph)
+                                  launch_bicg_phase<T>(P, Lb, B, par, ph, B.partials);
+                          launch_loop_cond(bs, h, B.sctl, d_loopc + 1, bicg_cap, 1);
+                      });
+            launch_solve_stats(st, B.sctl, d_loopc, d_sstat + s);
+            e3 = gev(st, chk);
+            iv(e2, e3, NH_K_CHEB_PASS);
+        }
+        launch_corr2d<T>(P, Ln, B, B.q1k, B.q2k, T(0), q.nonhydrostatic ? 1 : 0, eo, ao, bo, wo,
+                         s == 1 ? 1 : 0, B.partials, B.stctl, d_dt, b,
+                         q.nonhydrostatic ? B.v[0] : nullptr);
+        const int e4 = gev(st, chk);
+        iv(e3, e4, NH_K_CORRECTION);
+        std::swap(B.p, B.palt);
+    }
+
+    int capture()
+    {
+        cudaError_t e;
+        if (!g_side && (e = cudaStreamCreateWithFlags(&g_side, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(hd, e, "cudaStreamCreate");
+        if (!g_cap && (e = cudaStreamCreateWithFlags(&g_cap, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(hd, e, "cudaStreamCreate");
+        if (!h_dt) {
+            int rc = NH_OK;
+            if ((rc = alloc(&d_dt, 1)) != NH_OK || (rc = alloc(&d_loopc, 2)) != NH_OK ||
+                (rc = alloc(&d_sstat, 2)) != NH_OK)
+                return rc;
+            if ((e = cudaMallocHost(&h_dt, sizeof(double))) != cudaSuccess ||
+                (e = cudaMallocHost(&h_sstat, 2 * sizeof(SolveStat))) != cudaSuccess)
+                return cuda_fail(hd, e, "cudaMallocHost");
+        }
+        graph_destroy();
+        g_prof = prof.on;
+        if (g_prof) prof.flush();
+        g_p = B.p;
+        // every launch of the step goes to the capture stream meanwhile
+        const cudaStream_t user = hd->s;
+        hd->s = g_cap;
+        Lc.s = Ln.s = g_cap;
+        cudaStream_t st = g_cap;
+        if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+            cudaGetLastError();
+            hd->s = Lc.s = Ln.s = user;
+            return cuda_fail(hd, e, "cudaStreamBeginCapture");
+        }
+        capturing = true;
+        cudaError_t first = cudaSuccess;
+        auto chk = [&](cudaError_t x) { if (first == cudaSuccess && x != cudaSuccess) first = x; };
+        chk(cudaMemcpyAsync(d_dt, h_dt, sizeof(double), cudaMemcpyHostToDevice, st));
+        chk(cudaMemsetAsync(&B.stctl->clamped, 0, sizeof(int), st));
+        for (int s = 0; s < 2; ++s) stage2d_capture(s, chk);
+        if (relax_on) {   // zones after the step, then the Eq. (23) rate of the result
+            const int r0 = gev(st, chk);
+            launch_relax<T>(P, Ln, Z, dim, B.eta, B.q1, B.q2, B.w, B.p, B.H, B.rz_eta, B.rz_q1,
+                            B.rz_q2, B.rz_w, B.rz_p);
+            launch_lambda<T>(P, Lc, B.eta, B.q1, B.q2, B.H, dim, B.partials, B.stctl);
+            const int r1 = gev(st, chk);
+            if (r0 >= 0) g_iv.push_back({r0, r1, NH_K_RELAX, -1});
+        }
+        chk(cudaMemcpyAsync(h_stctl, B.stctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, st));
+        chk(cudaMemcpyAsync(h_sstat, d_sstat, 2 * sizeof(SolveStat), cudaMemcpyDeviceToHost, st));
+        chk(cudaGetLastError());
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(st, &graph);
+        capturing = false;
+        hd->s = Lc.s = Ln.s = user;
+        if (first == cudaSuccess) first = e;
+        if (first == cudaSuccess) first = cudaGraphInstantiate(&g_exec, graph, 0);
+        g_graph = graph;
+        if (g_prof) prof.used = 0;   // the capture's events only stand for nodes
+        if (first != cudaSuccess) {
+            cudaGetLastError();
+            graph_destroy();
+            return cuda_fail(hd, first, "step graph");
+        }
+        return NH_OK;
+    }
+
+    int step_graph(double dtd)
+    {
+        if (g_exec && (g_p != B.p || g_prof != prof.on)) graph_destroy();
+        if (!g_exec) {
+            const int rc = capture();
+            if (rc != NH_OK) {   // stay eager (the message of the failure is kept)
+                g_failed = true;
+                return step_impl(dtd, nullptr);
+            }
+        }
+        *h_dt = dtd;
+        std::vector<cudaEvent_t> ev;
+        if (g_prof) {
+            if (prof.used + g_evnodes.size() > 16384) prof.flush();
+            for (cudaGraphNode_t nd : g_evnodes) {
+                cudaEvent_t x = prof.next();
+                cudaGraphExecEventRecordNodeSetEvent(g_exec, nd, x);
+                ev.push_back(x);
+            }
+        }
+        cudaError_t e = cudaGraphLaunch(g_exec, hd->s);
+        if (e != cudaSuccess) return cuda_fail(hd, e, "cudaGraphLaunch");
+        if ((e = cudaStreamSynchronize(hd->s)) != cudaSuccess) return cuda_fail(hd, e, "nh_step");
+        const nh_params& q = hd->prm;
+        const int K = cheb_sweeps_per_pass<T>();
+        int rc = NH_OK;
+        for (int s = 0; s < 2 && q.nonhydrostatic; ++s) {
+            const SolveStat& S = h_sstat[s];
+            const int it = S.fb ? S.iter : S.sweeps;
+            hd->solver_iters += it;
+            hd->last_iters[s] = it;
+            last_cheb_passes = S.sweeps / K;
+            if (S.fb) {
+                hd->fallbacks += 1;
+                hd->fallback_iters += it;
+                hd->last_resid[s] = S.bb > 0.0 ? std::sqrt(S.rr / S.bb) : 0.0;
+            } else {
+                hd->last_resid[s] = S.bdb > 0.0 ? std::sqrt(S.rr / S.bdb) : 0.0;
+            }
+            if (rc == NH_OK && (S.status == 6 || S.status == 7))
+                rc = fail(hd, NH_ETIMEOUT, "Chebyshev pass: a wait for staged copies ran out "
+                                           "of polls (the solve was abandoned)");
+            else if (rc == NH_OK && S.status != 1)
+                rc = fail(hd, NH_ENOCONV, "pressure solve of stage " + std::to_string(s + 1) +
+                                              " stopped with status " + std::to_string(S.status) +
+                                              " after " + std::to_string(it) + " iterations");
+        }
+        if (g_prof)
+            for (const GIv& v : g_iv) {
+                long long n = 1;
+                if (v.cls == NH_K_CHEB_PASS) n = h_sstat[v.stage].passes;
+                if (v.cls == NH_K_RELAX) n = 2;
+                prof.add(ev[v.a], ev[v.b], v.cls, n);
+            }
+        hd->dt_next = h_stctl->lam > 0.0 ? hd->prm.cfl / h_stctl->lam : 0.0;
+        if (h_stctl->nonfinite) {
+            hd->nonfinite = 1;
+            return fail(hd, NH_ENONFINITE, "non-finite value in the state");
+        }
+        return rc;
+    }
+
     int stage1d(int s, T dt)
     {
         const nh_params& q = hd->prm;
@@ -616,7 +955,10 @@ struct Impl : Base {
         return NH_OK;
     }
 
-    int step(double dtd) override { return step_impl(dtd, nullptr); }
+    int step(double dtd) override
+    {
+        return graph_mode() ? step_graph(dtd) : step_impl(dtd, nullptr);
+    }
 
     // ---- tape of one step for the adjoint: U^n, U1, the stage-1 q* and p, eta^{n+1}, the
     // stage-2 q* and p (15 arrays, each starting on a 256-byte boundary)
@@ -640,8 +982,10 @@ struct Impl : Base {
     }
     int step_taped(double dtd, void* tape) override { return step_impl(dtd, tape); }
 
+    int eager_steps = 0;
     int step_impl(double dtd, void* tape)
     {
+        ++eager_steps;
         const T dt = (T)dtd;
         cudaMemsetAsync(&B.stctl->clamped, 0, sizeof(int), hd->s);
         if (tape) { tcopy(tape, 0, B.eta); tcopy(tape, 1, B.q1); tcopy(tape, 2, B.q2); tcopy(tape, 3, B.w); }
@@ -770,10 +1114,10 @@ struct Impl : Base {
     {
         const nh_params& q = hd->prm;
         if (dim != 2 || !q.nonhydrostatic || q.breaking || q.manning_n > 0.0 ||
-            q.w_equation != NH_W_YAMAZAKI)
+            q.w_equation != NH_W_YAMAZAKI || !q.dry_zero)
             return fail(hd, NH_EINVAL,
                         "nh_adjoint_step: 2D non-hydrostatic steps of the h w_t = p form "
-                        "without friction or breaking only");
+                        "without friction or breaking, q = 0 in dry cells, only");
         int rc = adjoint_alloc();
         if (rc != NH_OK) return rc;
         T* eb = static_cast<T*>(ebv);
@@ -860,6 +1204,14 @@ struct Impl : Base {
         if (b && dim == 2) cudaMemcpyAsync(b, B.q2s, nc * sizeof(T), kind_out(where), hd->s);
         cudaError_t er = cudaStreamSynchronize(hd->s);
         if (er != cudaSuccess) return cuda_fail(hd, er, "nh_debug_hyperbolic");
+        return NH_OK;
+    }
+
+    int debug_stall_copies(int block) override
+    {
+        if (dim != 2 || hd->prm.solver != NH_SOLVER_CHEBYSHEV)
+            return fail(hd, NH_EINVAL, "nh_debug_stall_copies: 2D Chebyshev handles only");
+        stall_block = block;
         return NH_OK;
     }
 
@@ -954,6 +1306,9 @@ int nh_default_params(nh_params* p)
     p->cheb_form = -1;
     p->w_equation = NH_W_YAMAZAKI;
     for (int k = 0; k < 4; ++k) p->relax_width[k] = 0.0;
+    p->dry_zero = 1;
+    p->wait_polls = 0;
+    p->capture = 1;
     return NH_OK;
 }
 
@@ -1118,6 +1473,9 @@ int nh_step_taped(nh_handle* h, double dt, void* tape, double* dt_taken)
     if (h->grid.dim != 2) return fail(h, NH_EINVAL, "nh_step_taped: 2D only");
     if (h->prm.w_equation != NH_W_YAMAZAKI)
         return fail(h, NH_EINVAL, "nh_step_taped: the adjoint covers the h w_t = p form only");
+    if (!h->prm.dry_zero)
+        return fail(h, NH_EINVAL, "nh_step_taped: the adjoint covers q = 0 in dry cells "
+                                  "(dry_zero = 1) only");
     for (int k = 0; k < 4; ++k)
         if (h->prm.relax_width[k] > 0.0)
             return fail(h, NH_EINVAL, "nh_step_taped: the adjoint covers steps without "
@@ -1140,6 +1498,12 @@ int nh_adjoint_step(nh_handle* h, double dt, const void* tape, void* eta_bar, vo
     if (!h || !tape || !eta_bar || !q1_bar || !q2_bar || !w_bar || !H_bar || !(dt > 0.0))
         return NH_EINVAL;
     return h->impl->adjoint_step(dt, tape, eta_bar, q1_bar, q2_bar, w_bar, H_bar);
+}
+
+int nh_debug_stall_copies(nh_handle* h, int block)
+{
+    if (!h || block < 0) return NH_EINVAL;
+    return h->impl->debug_stall_copies(block);
 }
 
 int nh_debug_system(nh_handle* h, double dt, const void* x, void* rhs_out, void* mx_out,

@@ -65,6 +65,7 @@ struct Arena {
     unsigned* loop;        // [0] domains in Chebyshev passes, [1] passes launched this stage,
                            // [2] domains in the BiCGStab fallback, [3] its iterations
     double fixed_dt, cfl;
+    unsigned polls;        // bounded waits of the register-form pass (nh_params.wait_polls)
 };
 
 __host__ __device__ inline int cdiv(int a, int b) { return (a + b - 1) / b; }
@@ -187,19 +188,13 @@ kb_asm(Arena<T> A, const int2* __restrict__ wl, int nw, const T* eta, const T* H
 }
 
 // Last block of a domain's items in a pass: convergence test and next weights, the stall
-// test (8 passes without a 0.81 reduction of the best residual, 0.99 under criterion (32):
-// status 5, BiCGStab takes over from the current dp), and the loop counters and statistics
-// of a finished domain.
+// test (cheb_finish_stall: status 5, BiCGStab takes over from the current dp), and the loop
+// counters and statistics of a finished domain.
 template <typename T>
 __device__ __forceinline__ void kb_cheb_finish(const Arena<T>& A, int d, SolveCtl* ctl,
                                                const double (&acc)[2], int K, int stage)
 {
-    cheb_finish(ctl, acc, K);
-    if (!ctl->done) {
-        const double fall = ctl->eps_dp > 0.0 ? 0.99 : 0.81;   // criterion (32): see solve_cheb
-        if (acc[0] < fall * ctl->best) { ctl->best = acc[0]; ctl->stale = 0; }
-        else if (++ctl->stale >= 8) { ctl->done = 1; ctl->status = 5; }
-    }
+    cheb_finish_stall(ctl, acc, K);
     if (ctl->done) {
         atomicSub(&A.loop[0], 1u);
         DomState& s = A.ds[d];
@@ -236,7 +231,8 @@ kb_cheb(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const T* c
         R.cC = cC + n; R.cW = cW + n; R.cE = cE + n; R.cS = cS + n; R.cN = cN + n;
         R.nx = D.P.nx; R.ny = D.P.ny;
         const int tx = cdiv(R.nx + 1, TX), nt = tx * cdiv(R.ny + 1, TY);
-        T rsum, dmax;
+        double rsum;
+        T dmax;
         if constexpr (PAD)
             cheb_tile_pad<T, NA, NB, BY, K>(R, rhs + n, xi + n, xpi + n, xo + n, xpo + n, ctl,
                                             it.y % tx, it.y / tx,
@@ -246,8 +242,8 @@ kb_cheb(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const T* c
                                               it.y % tx, it.y / tx,
                                               reinterpret_cast<T*>(kb_cheb_smem), rsum, dmax);
         double acc[2];
-        if (dom_reduce_sum_max_f((float)rsum, (float)dmax, A.partials + D.poff, &ctl->counter,
-                                 acc, it.y, nt) &&
+        if (dom_reduce_sum_max(rsum, (double)dmax, A.partials + D.poff, &ctl->counter, acc,
+                               it.y, nt) &&
             threadIdx.x == 0 && threadIdx.y == 0)
             kb_cheb_finish(A, it.x, ctl, acc, K, stage);
         __syncthreads();
@@ -259,16 +255,18 @@ kb_cheb(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const T* c
 // its items of this pass is unprocessed), each prefetching its next item's region (bulk
 // copies on an mbarrier, element copies at the domain's west and east edges) while it
 // sweeps the current one; every item ends in its domain's reduction as in kb_cheb.  A wait
-// that runs out of polls marks the item's domain failed (status 6, counted as a
-// non-converged solve) and ends the block's walk.
+// that runs out of `polls` polls ends the block's walk: the block issues no further copies,
+// waits (bounded) for those of the item it was waiting on (cheb_drain) and marks the item's
+// domain failed (status 6, or 7 if the drain ran out too; counted as a non-converged
+// solve).
 template <typename T, int C, int R, int NW, int K>
 __global__ void __launch_bounds__(32 * NW, 1)
 kb_cheb_reg(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const T* cW,
             const T* cE, const T* cS, const T* cN, const T* rhs, const T* xi, const T* xpi,
             T* xo, T* xpo, int stage)
 {
+    const unsigned polls = A.polls;
     constexpr int RW = 32 * C, RH = R * NW, TX = RW - 2 * K, TY = RH - 2 * K;
-    constexpr unsigned kPolls = 1u << 22;
     using G = RegionGeom<T, RW, RH>;
     extern __shared__ __align__(16) unsigned char kb_reg_raw[];
     T* planes = reinterpret_cast<T*>(kb_reg_raw);
@@ -330,12 +328,16 @@ kb_cheb_reg(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const 
     };
     while (w < nw) {
         cp_async_wait_all();
-        const bool got = mbar_wait_bounded(&bar, phase, kPolls);
+        const bool got = mbar_wait_bounded(&bar, phase, polls);
         const int2 it = wl[w];
         SolveCtl* ctl = &A.sctl[it.x];
         if (__syncthreads_or(!got)) {
-            mbar_wait_bounded(&bar, phase, kPolls);   // copies possibly still in flight
-            if (tid == 0) { ctl->status = 6; atomicAdd(&A.ds[it.x].nonconv, 1); }
+            const bool drained = cheb_drain(&bar, phase, true);
+            if (tid == 0) {
+                ctl->status = drained ? 6 : 7;
+                A.ds[it.x].last_status[stage] = ctl->status;
+                atomicAdd(&A.ds[it.x].nonconv, 1);
+            }
             break;
         }
         phase ^= 1u;
@@ -360,15 +362,18 @@ kb_cheb_reg(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const 
                 stage_item(wn);
             }
         };
-        T rsum = T(0), dmax = T(0);
+        double rsum = 0.0;
+        T dmax = T(0);
+        const T rsc = sizeof(T) == 4 ? (T)ctl->rscf : (T)ctl->rscd;
+        const double rinv2 = ctl->rinv2;
         if constexpr (sizeof(T) == 4 && C == 2)
-            cheb_region_reg2<R, NW, K>(Rw, planes, exch, c1s, c2s, I0, J0, xo + n, xpo + n, rsum,
-                                       dmax, next);
+            cheb_region_reg2<R, NW, K>(Rw, planes, exch, c1s, c2s, rsc, rinv2, I0, J0, xo + n,
+                                       xpo + n, rsum, dmax, next);
         else
-            cheb_region_reg<T, C, R, NW, K>(Rw, planes, exch, c1s, c2s, I0, J0, xo + n, xpo + n,
-                                            rsum, dmax, next);
-        float bs = (float)rsum, bm = (float)dmax;
-        block_sum_max_f(bs, bm);
+            cheb_region_reg<T, C, R, NW, K>(Rw, planes, exch, c1s, c2s, rsc, rinv2, I0, J0,
+                                            xo + n, xpo + n, rsum, dmax, next);
+        double bsm[2] = {rsum, (double)dmax};
+        block_reduce<2, 2u>(bsm);   // FP64 (sum, max) into thread 0
         if (it.x != gd) {
             flush();
             gd = it.x;
@@ -379,8 +384,8 @@ kb_cheb_reg(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const 
             A.partials[D.poff + 2 * (long long)it.y + 1] = 0.0;
         }
         if (tid == 0) {
-            gs += bs;
-            gm = fmax(gm, (double)bm);
+            gs += bsm[0];
+            gm = fmax(gm, bsm[1]);
         }
         ++gn;
         (void)nt;
@@ -1040,6 +1045,7 @@ struct BatchImpl : BatchBase {
         A.dom = d_dom; A.sctl = d_sctl; A.stctl = d_stctl; A.ds = d_ds;
         A.partials = B.partials; A.loop = d_loop;
         A.fixed_dt = hb->prm.fixed_dt; A.cfl = hb->prm.cfl;
+        A.polls = hb->prm.wait_polls > 0 ? (unsigned)hb->prm.wait_polls : kDefaultWaitPolls;
         return A;
     }
 
@@ -1076,7 +1082,7 @@ struct BatchImpl : BatchBase {
             P.bcw = g.bc[0]; P.bce = g.bc[1]; P.bcs = g.bc[2]; P.bcn = g.bc[3];
             P.dx = (T)g.dx; P.dy = (T)g.dy;
             P.g = (T)q.g; P.delta = (T)q.delta; P.hdry = (T)q.hdry; P.manning = (T)q.manning_n;
-            P.B1 = (T)q.B1; P.breaking = q.breaking;
+            P.B1 = (T)q.B1; P.breaking = q.breaking; P.dry_zero = q.dry_zero ? 1 : 0;
             const long long nc = (long long)g.nx * g.ny, nn = (long long)(g.nx + 1) * (g.ny + 1);
             D.coff = ncell; D.noff = nnode;
             // keep every domain's arrays 256-byte aligned
@@ -1642,6 +1648,12 @@ struct BatchImpl : BatchBase {
         for (int d = 0; d < n; ++d)
             if (h_ds[d].nonfinite)
                 return bfail(hb, NH_ENONFINITE, "non-finite value in domain " + std::to_string(d));
+        for (int d = 0; d < n; ++d)
+            if (h_ds[d].nonconv != nonconv0[d] &&
+                (h_ds[d].last_status[0] >= 6 || h_ds[d].last_status[1] >= 6))
+                return bfail(hb, NH_ETIMEOUT, "pressure solve of domain " + std::to_string(d) +
+                                                  ": a Chebyshev pass gave up waiting for its "
+                                                  "staged copies");
         for (int d = 0; d < n; ++d)
             if (h_ds[d].nonconv != nonconv0[d])
                 return bfail(hb, NH_ENOCONV, "pressure solve of domain " + std::to_string(d) +

@@ -250,75 +250,19 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[NV], double* partials,
                                    gridDim.x * gridDim.y);
 }
 
-// Block partial of (sum, max) in FP32 (a few thousand terms per block), written as FP64
-// partials; the last block finishes in FP64 like grid_reduce.
-__device__ __forceinline__ bool dom_reduce_sum_max_f(float s, float m, double* partials,
-                                                     unsigned* counter, double out[2],
-                                                     unsigned bid, unsigned nblocks)
+// Sum and max of a pass's per-thread (squared residual sum, largest change) over the
+// grid, in FP64 at every level (per thread, warp, block and the last block's finish), so
+// that the stopping test of the pressure solve sees the residual norm in FP64 in both
+// precisions.  Same contract as dom_reduce; out (thread 0 of the last block) = totals.
+__device__ __forceinline__ bool dom_reduce_sum_max(double s, double m, double* partials,
+                                                   unsigned* counter, double out[2],
+                                                   unsigned bid, unsigned nblocks)
 {
-    __shared__ float fs[32], fm[32];
-    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-    const int lane = tid & 31, wid = tid >> 5, nw = (blockDim.x * blockDim.y + 31) >> 5;
-    for (int o = 16; o > 0; o >>= 1) {
-        s += __shfl_xor_sync(0xffffffffu, s, o);
-        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    }
-    if (lane == 0) { fs[wid] = s; fm[wid] = m; }
-    __syncthreads();
-    double v[2] = {0.0, 0.0};
-    if (wid == 0) {
-        float a = lane < nw ? fs[lane] : 0.f, b = lane < nw ? fm[lane] : 0.f;
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-            b = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, o));
-        }
-        v[0] = a; v[1] = b;
-    }
-    const unsigned nthr = blockDim.x * blockDim.y;
-    __shared__ bool last;
-    if (tid == 0) {
-        partials[(size_t)bid * 2] = v[0];
-        partials[(size_t)bid * 2 + 1] = v[1];
-        __threadfence();
-        last = atomicAdd(counter, 1u) == nblocks - 1;
-    }
-    __syncthreads();
-    if (!last) return false;
-    __threadfence();
-    double acc[2] = {0.0, 0.0};
-    for (unsigned bb = tid; bb < nblocks; bb += nthr) {
-        acc[0] += __ldcg(partials + (size_t)bb * 2);
-        acc[1] = fmax(acc[1], __ldcg(partials + (size_t)bb * 2 + 1));
-    }
-    block_reduce<2, 2u>(acc);
-    out[0] = acc[0];
-    out[1] = acc[1];
-    if (tid == 0) *counter = 0u;
+    double v[2] = {s, m};
+    if (!dom_reduce<2, 2u>(v, partials, counter, bid, nblocks)) return false;
+    out[0] = v[0];
+    out[1] = v[1];
     return true;
-}
-
-// Sum and max of the block's (s, m), FP32, into thread 0.
-__device__ __forceinline__ void block_sum_max_f(float& s, float& m)
-{
-    __shared__ float gs[32], gm[32];
-    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-    const int lane = tid & 31, wid = tid >> 5, nw = (blockDim.x * blockDim.y + 31) >> 5;
-    for (int o = 16; o > 0; o >>= 1) {
-        s += __shfl_xor_sync(0xffffffffu, s, o);
-        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    }
-    if (lane == 0) { gs[wid] = s; gm[wid] = m; }
-    __syncthreads();
-    if (wid == 0) {
-        float a = lane < nw ? gs[lane] : 0.f, b = lane < nw ? gm[lane] : 0.f;
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-            b = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, o));
-        }
-        s = a;
-        m = b;
-    }
-    __syncthreads();
 }
 
 // Publish a block's (sum, max) for `cnt` items of a domain at once: thread 0 writes it to
@@ -657,8 +601,10 @@ asm_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
     const T inv2dx = T(1) / (T(2) * P.dx), inv2dy = T(1) / (T(2) * P.dy);
     const T scale = T(8) * P.dx * P.dy / de;
     const T rxl = P.dy / P.dx, ryl = P.dx / P.dy;
-    // per-thread sums over its few nodes in T; the block and grid sums are FP64
-    T s0 = T(0), s1 = T(0), s2 = T(0);
+    // norms of the right-hand side (plain and Jacobi-scaled) summed in FP64 from the first
+    // square on; the Gershgorin ratio is a max (exact in T)
+    double s0 = 0.0, s1 = 0.0;
+    T s2 = T(0);
     for (int t = tid; t < TX * TY; t += nt) {
         const int li = t % TX, lj = t / TX;
         const int I = I0 + li, J = J0 + lj;
@@ -687,7 +633,7 @@ asm_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
                    + ((T(2) * hc - Yi) * q2N - (T(2) * hc + Yi) * q2S) * inv2dy
                    + T(2) * hc * wv;
         const T bval = -scale * Bs;
-        s0 = fma(bval, bval, s0);
+        s0 = fma((double)bval, (double)bval, s0);
         if (with_coef) {
             const T Xa = Xc[ka], Xb = Xc[kb], Xd = Xc[kd], Xe = Xc[ke];
             const T Ya = Yc[ka], Yb = Yc[kb], Yd = Yc[kd], Ye = Yc[ke];
@@ -704,7 +650,7 @@ asm_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
             cE[nidx] = vE; cW[nidx] = vW; cN[nidx] = vN; cS[nidx] = vS; cC[nidx] = dC;
             const T id = qdiv(T(1), fabs(dC));
             const T bs = bval * id;
-            s1 = fma(bs, bs, s1);
+            s1 = fma((double)bs, (double)bs, s1);
             s2 = tmax(s2, (fabs(vE) + fabs(vW) + fabs(vN) + fabs(vS)) * id);
             if (resid_form) {
                 const int pc = (lj + 1) * PW + li + 1;
@@ -721,8 +667,8 @@ asm_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
             rhs[nidx] = bval;
         }
     }
-    acc[0] += (double)s0;
-    acc[1] += (double)s1;
+    acc[0] += s0;
+    acc[1] += s1;
     acc[2] = fmax(acc[2], (double)s2);
 }
 
@@ -734,12 +680,22 @@ __device__ __forceinline__ void asm_finish(SolveCtl* ctl, const double (&acc)[3]
     ctl->bb = acc[0];
     ctl->bdb = acc[1];
     ctl->gersh = acc[2];
+    {
+        int e = acc[1] > 0.0 ? ilogb(sqrt(acc[1])) : 0;
+        e = e < -100 ? -100 : (e > 100 ? 100 : e);
+        ctl->rscd = ldexp(1.0, -e);
+        ctl->rscf = (float)ctl->rscd;
+        ctl->rinv2 = ldexp(1.0, 2 * e);
+    }
     ctl->tol2 = tol2;
     ctl->max_iter = max_iter;
     ctl->iter = 0;
     ctl->sweeps = 0;
     ctl->done = 0;
     ctl->status = 0;
+    ctl->best = 1.0e300;
+    ctl->stale = 0;
+    ctl->fb = 0;
     if (with_coef && kpass > 0) {
         if (!(acc[2] < 1.0)) {
             ctl->status = 4;
@@ -833,7 +789,7 @@ template <typename T, int NA, int NB, int BY, int K, bool REGW>
 __device__ __forceinline__ void
 cheb_tile(const Rows<T>& R, const T* __restrict__ b, const T* __restrict__ xi,
           const T* __restrict__ xpi, T* __restrict__ xo, T* __restrict__ xpo,
-          const SolveCtl* ctl, int bx, int by, T* smem, T& rsum, T& dmax)
+          const SolveCtl* ctl, int bx, int by, T* smem, double& rsum, T& dmax)
 {
     constexpr int RW = 32 * NA, RH = BY * NB, RN = RW * RH, NN = NA * NB;
     constexpr int TX = RW - 2 * K, TY = RH - 2 * K;
@@ -893,7 +849,9 @@ cheb_tile(const Rows<T>& R, const T* __restrict__ b, const T* __restrict__ xi,
     __syncthreads();
     T* cur = xs0;
     T* nxt = xs1;
-    rsum = T(0);   // per-thread (few terms): native precision is enough
+    // squared scaled residuals: a T partial over the thread's nodes, then FP64
+    const T rsc = sizeof(T) == 4 ? (T)ctl->rscf : (T)ctl->rscd;
+    T part = T(0);
     dmax = T(0);
 #pragma unroll
     for (int sw = 0; sw < K; ++sw) {
@@ -920,7 +878,10 @@ cheb_tile(const Rows<T>& R, const T* __restrict__ b, const T* __restrict__ xi,
                     xa[q] = xc;
                     if (sw == K - 1 && li >= K && li < RW - K && lj >= K && lj < RH - K &&
                         I0 + li <= nx && J0 + lj <= ny) {
-                        rsum = fma(r, r, rsum);
+                        {
+                        const T rs = r * rsc;
+                        part = fma(rs, rs, part);
+                    }
                         dmax = tmax(dmax, T(fabs(xn - xc)));
                     }
                 }
@@ -928,6 +889,7 @@ cheb_tile(const Rows<T>& R, const T* __restrict__ b, const T* __restrict__ xi,
         __syncthreads();
         T* tmp = cur; cur = nxt; nxt = tmp;
     }
+    rsum = (double)part * ctl->rinv2;
 #pragma unroll
     for (int bb = 0; bb < NB; ++bb)
 #pragma unroll
@@ -979,7 +941,7 @@ template <typename T, int NA, int NB, int BY, int K>
 __device__ __forceinline__ void
 cheb_tile_pad(const Rows<T>& R, const T* __restrict__ b, const T* __restrict__ xi,
               const T* __restrict__ xpi, T* __restrict__ xo, T* __restrict__ xpo,
-              const SolveCtl* ctl, int bx, int by, T* smem, T& rsum, T& dmax)
+              const SolveCtl* ctl, int bx, int by, T* smem, double& rsum, T& dmax)
 {
     constexpr int RW = 32 * NA, RH = BY * NB, NN = NA * NB;
     constexpr int PW = RW + 2, PN = PW * (RH + 2);
@@ -1030,7 +992,8 @@ cheb_tile_pad(const Rows<T>& R, const T* __restrict__ b, const T* __restrict__ x
     __syncthreads();
     T* cur = xs0;
     T* nxt = xs1;
-    rsum = T(0);
+    const T rsc = sizeof(T) == 4 ? (T)ctl->rscf : (T)ctl->rscd;
+    T part = T(0);
     dmax = T(0);
 #pragma unroll
     for (int sw = 0; sw < K; ++sw) {
@@ -1050,13 +1013,17 @@ cheb_tile_pad(const Rows<T>& R, const T* __restrict__ b, const T* __restrict__ x
                 xa[q] = xc;
                 if (sw == K - 1 && li >= K && li < RW - K && lj >= K && lj < RH - K &&
                     I0 + li <= nx && J0 + lj <= ny) {
-                    rsum = fma(r, r, rsum);
+                    {
+                        const T rs = r * rsc;
+                        part = fma(rs, rs, part);
+                    }
                     dmax = tmax(dmax, T(fabs(xn - xc)));
                 }
             }
         __syncthreads();
         T* tmp = cur; cur = nxt; nxt = tmp;
     }
+    rsum = (double)part * ctl->rinv2;
 #pragma unroll
     for (int bb = 0; bb < NB; ++bb)
 #pragma unroll
@@ -1145,6 +1112,21 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
     for (unsigned k = 0; k < limit; ++k)
         if (mbar_test_parity(bar, parity)) return true;
     return false;
+}
+
+// After a wait on `bar` ran out: wait, in bounded rounds whose length does not depend on
+// the (settable) poll limit of the first wait, for bulk copies already issued on phase
+// `parity` (issued = false: none were), so that the block never leaves while copies into
+// its shared memory are in flight.  True in every thread when that phase completed (or
+// nothing was issued); false if the drain ran out as well.
+__device__ __forceinline__ bool cheb_drain(unsigned long long* bar, unsigned parity,
+                                           bool issued)
+{
+    bool done = !issued;
+    for (int round = 0; round < 8 && !done; ++round)
+        done = mbar_wait_bounded(bar, parity, 1u << 22);
+    cp_async_wait_all();
+    return __syncthreads_and(done) != 0;
 }
 
 __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes,
@@ -1251,9 +1233,10 @@ __device__ __forceinline__ void cheb_stage_region(const T* const* bases, int nx,
 // largest change over the interior nodes to rsum / dmax.  c1s / c2s: the K sweep weights.
 template <typename T, int C, int R, int NW, int K, typename F>
 __device__ __forceinline__ void cheb_region_reg(const Rows<T>& Rw, const T* planes, T* exch,
-                                                const T* c1s, const T* c2s, int I0, int J0,
-                                                T* __restrict__ xo, T* __restrict__ xpo,
-                                                T& rsum, T& dmax, F stage_next)
+                                                const T* c1s, const T* c2s, T rsc, double rinv2,
+                                                int I0, int J0, T* __restrict__ xo,
+                                                T* __restrict__ xpo, double& rsum, T& dmax,
+                                                F stage_next)
 {
     constexpr int RW = 32 * C, RH = R * NW;
     using G = RegionGeom<T, RW, RH>;
@@ -1292,6 +1275,7 @@ __device__ __forceinline__ void cheb_region_reg(const Rows<T>& Rw, const T* plan
     // alternate the two arrays' roles and no copy is made; K is even, so x ends as the
     // latest iterate and xa as the one before.
     static_assert(K % 2 == 0, "sweeps alternate the two iterate arrays");
+    T part = T(0);   // squared scaled residuals of this thread's nodes (rsc: exact 2^-e)
     auto sweep = [&](T (&cur)[R][C], T (&prv)[R][C], int sw) {
         T* e = exch + (sw & 1) * (NW * 2 * RW);
 #pragma unroll
@@ -1328,7 +1312,8 @@ __device__ __forceinline__ void cheb_region_reg(const Rows<T>& Rw, const T* plan
                     const int li = C * lane + c, lj = R * w + r;
                     if (li >= K && li < RW - K && lj >= K && lj < RH - K && I0 + li <= nx &&
                         J0 + lj <= ny) {
-                        rsum = fma(res, res, rsum);
+                        const T rs = res * rsc;
+                        part = fma(rs, rs, part);
                         dmax = tmax(dmax, T(fabs(v - xc)));
                     }
                 }
@@ -1340,6 +1325,7 @@ __device__ __forceinline__ void cheb_region_reg(const Rows<T>& Rw, const T* plan
         sweep(x, xa, sw);
         sweep(xa, x, sw + 1);
     }
+    rsum = fma((double)part, rinv2, rsum);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int lj = R * w + r, gJ = J0 + lj;
@@ -1362,9 +1348,10 @@ __device__ __forceinline__ void cheb_region_reg(const Rows<T>& Rw, const T* plan
 template <int R, int NW, int K, typename F>
 __device__ __forceinline__ void cheb_region_reg2(const Rows<float>& Rw, const float* planes,
                                                  float* exch, const float* c1s,
-                                                 const float* c2s, int I0, int J0,
-                                                 float* __restrict__ xo, float* __restrict__ xpo,
-                                                 float& rsum, float& dmax, F stage_next)
+                                                 const float* c2s, float rsc, double rinv2,
+                                                 int I0, int J0, float* __restrict__ xo,
+                                                 float* __restrict__ xpo, double& rsum,
+                                                 float& dmax, F stage_next)
 {
     constexpr int RW = 64, RH = R * NW;
     using G = RegionGeom<float, RW, RH>;
@@ -1402,6 +1389,7 @@ __device__ __forceinline__ void cheb_region_reg2(const Rows<float>& Rw, const fl
     stage_next(0);
     // sweeps alternate the roles of x and xa, as in cheb_region_reg (no copies)
     static_assert(K % 2 == 0, "sweeps alternate the two iterate arrays");
+    float part = 0.f;   // squared scaled residuals of this thread's nodes (rsc: exact 2^-e)
     auto sweep = [&](float2 (&cur)[R], float2 (&prv)[R], int sw) {
         float* e = exch + (sw & 1) * (NW * 2 * RW);
         *reinterpret_cast<float2*>(e + (2 * w) * RW + 2 * lane) = cur[0];
@@ -1433,11 +1421,13 @@ __device__ __forceinline__ void cheb_region_reg2(const Rows<float>& Rw, const fl
                 if (lj >= K && lj < RH - K && J0 + lj <= ny) {
                     const int li = 2 * lane;
                     if (li >= K && li < RW - K && gI0 <= nx) {
-                        rsum = fma(res.x, res.x, rsum);
+                        const float rs = res.x * rsc;
+                        part = fmaf(rs, rs, part);
                         dmax = fmaxf(dmax, fabsf(v.x - cur[r].x));
                     }
                     if (li + 1 >= K && li + 1 < RW - K && gI1 <= nx) {
-                        rsum = fma(res.y, res.y, rsum);
+                        const float rs = res.y * rsc;
+                        part = fmaf(rs, rs, part);
                         dmax = fmaxf(dmax, fabsf(v.y - cur[r].y));
                     }
                 }
@@ -1450,6 +1440,7 @@ __device__ __forceinline__ void cheb_region_reg2(const Rows<float>& Rw, const fl
         sweep(x, xa, sw);
         sweep(xa, x, sw + 1);
     }
+    rsum = fma((double)part, rinv2, rsum);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int lj = R * w + r, gJ = J0 + lj;
@@ -1464,7 +1455,7 @@ __device__ __forceinline__ void cheb_region_reg2(const Rows<float>& Rw, const fl
 // Last block of a pass: residual test (or criterion (32) on max |dx|), and the next K weights.
 __device__ __forceinline__ void cheb_finish(SolveCtl* ctl, const double (&acc)[2], int K)
 {
-    if (ctl->status == 6) {   // a block of the register form gave up waiting for its copies
+    if (ctl->status >= 6) {   // a block of the register form gave up waiting for its copies
         ctl->done = 1;
         return;
     }
@@ -1489,9 +1480,25 @@ __device__ __forceinline__ void cheb_finish(SolveCtl* ctl, const double (&acc)[2
     ctl->rho_prev = rp;
 }
 
+// cheb_finish plus the stall test of the passes: 8 passes without a 0.81 reduction of the
+// best residual (0.99 under criterion (32), where only a residual that no longer falls at
+// all counts) end the relaxation with status 5 (the rounding floor of the precision, or a
+// spectrum the Gershgorin interval does not describe); BiCGStab then continues from the
+// current iterate.
+__device__ __forceinline__ void cheb_finish_stall(SolveCtl* ctl, const double (&acc)[2], int K)
+{
+    cheb_finish(ctl, acc, K);
+    if (!ctl->done) {
+        const double fall = ctl->eps_dp > 0.0 ? 0.99 : 0.81;
+        if (acc[0] < fall * ctl->best) { ctl->best = acc[0]; ctl->stale = 0; }
+        else if (++ctl->stale >= 8) { ctl->done = 1; ctl->status = 5; }
+    }
+}
+
 // Correction (Eq. 36 and the w update of Eq. 41) at node (I, J) and cell (I, J):
 // q1 += de (T^Hor_N + T^Hor_S)/2, q2 += de (T^Ver_E + T^Ver_W)/2, w += de p / h_c;
-// dry cells (h <= hdry) keep q = 0, as App. B A.2 assumes where the depth vanishes.
+// with P.dry_zero, dry cells (h <= hdry) keep q = 0, as App. B A.2 assumes where the depth
+// vanishes; without it the correction acts on every cell, as Sec. 4.5 states.
 // In the final stage also the Eq. (23) rate max((|u|+c)/dx + (|v|+c)/dy).
 // Node idx of the (nx+1) x (ny+1) node grid and, when it has one, the cell with the same
 // (i, j); lam and bad accumulate the final-stage rate and the non-finite flag.
@@ -1557,7 +1564,7 @@ corr_node(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
                 a1 += de * T(0.5) * (TN + TS);
                 a2 += de * T(0.5) * (TE + TW);
             }
-            if (h <= P.hdry) { a1 = T(0); a2 = T(0); }   // dry cells carry no discharge
+            if (P.dry_zero && h <= P.hdry) { a1 = T(0); a2 = T(0); }   // dry cells: no discharge
             eo[c] = e; q1o[c] = a1; q2o[c] = a2;
             if (!isfinite(e) || !isfinite(a1) || !isfinite(a2)) bad = 1;
             if (final_stage) {
@@ -1689,7 +1696,7 @@ corr_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
                 a1 += de * T(0.5) * (TN + TS);
                 a2 += de * T(0.5) * (TE + TW);
             }
-            if (h <= P.hdry) { a1 = T(0); a2 = T(0); }   // dry cells carry no discharge
+            if (P.dry_zero && h <= P.hdry) { a1 = T(0); a2 = T(0); }   // dry cells: no discharge
             eo[c] = e; q1o[c] = a1; q2o[c] = a2;
             if (!isfinite(e) || !isfinite(a1) || !isfinite(a2)) bad = 1;
             if (final_stage) {

@@ -15,6 +15,7 @@ struct Prm {
     T dx, dy;
     T g, delta, hdry, manning, B1;
     int breaking;
+    int dry_zero;               // 1: q = 0 in dry cells at the end of each stage
 };
 
 // Device-side control block of one pressure solve (BiCGStab, FP64 scalars).
@@ -48,6 +49,25 @@ struct SolveCtl {
     double best;      // smallest ||D^-1 r||^2 of the passes so far
     int stale;        // passes since best improved by the stall factor
     int fb;           // 1 while the domain's BiCGStab fallback runs
+    // residual norm of the passes: each thread sums the squares of its nodes' scaled
+    // residuals r * rsc (rsc = 2^-e with 2^e <= ||D^-1 b|| < 2^(e+1), an exact scaling that
+    // keeps every square in range), and adds that partial times rinv2 = 2^(2e) to its FP64
+    // accumulator; everything above the thread is summed in FP64
+    double rscd;      // rsc (FP64 passes)
+    double rinv2;     // 1 / rsc^2
+    float rscf;       // rsc (FP32 passes)
+    int pad3;
+};
+
+// Statistics of one stage's pressure solve in a captured step, read by the host after it.
+struct SolveStat {
+    double rr, bb, bdb;   // final squared residual and the two right-hand-side norms
+    int sweeps;           // Chebyshev sweeps
+    int iter;             // iteration count of the control block at the end
+    int status;           // 1 converged, 2 cap, 3 breakdown, 6 / 7 wait ran out
+    int fb;               // 1: BiCGStab continued the solve
+    int passes;           // Chebyshev passes launched (pairs x 2)
+    int bicg;             // BiCGStab iterations launched (pairs x 2)
 };
 
 // Device-side per-step scalars.
@@ -98,7 +118,10 @@ struct Launch {
 template <typename T>
 void launch_hyp2d(const Prm<T>& P, const Launch& L, const T* eta, const T* q1, const T* q2,
                   const T* etab, const T* q1b, const T* q2b, const T* H, T a, T b, T dt,
-                  T* eo, T* q1o, T* q2o, StepCtl* st, T* fmx = nullptr, T* fmy = nullptr);
+                  T* eo, T* q1o, T* q2o, StepCtl* st, T* fmx = nullptr, T* fmy = nullptr,
+                  const double* dtd = nullptr);
+// dtd (captured steps): when not null, the kernels take dt (and de = b dt) from this device
+// scalar instead of their argument
 // w* of the w equation (hw)_t + div(hw u) = p at every node: hw moved on the node (dual)
 // cells with the face mass fluxes fmx / fmy of the stage's hyperbolic step (input state
 // etain, win), combined with the base state (etab, wb) as (hw)* = a h_b w_b + b (hw)**,
@@ -106,11 +129,12 @@ void launch_hyp2d(const Prm<T>& P, const Launch& L, const T* eta, const T* q1, c
 template <typename T>
 void launch_wtrans2d(const Prm<T>& P, const Launch& L, const T* etab, const T* etain,
                      const T* etas, const T* H, const T* wb, const T* win, const T* fmx,
-                     const T* fmy, T a, T b, T dt, T* wo);
+                     const T* fmy, T a, T b, T dt, T* wo, const double* dtd = nullptr);
 template <typename T>
 void launch_asm2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* w_in,
                   const T* w_base, T a, T b, T de, int with_coef, int resid_form, double tol2,
-                  int max_iter, int kpass, double* partials, SolveCtl* ctl, int fuse_break = 0);
+                  int max_iter, int kpass, double* partials, SolveCtl* ctl, int fuse_break = 0,
+                  const double* dtd = nullptr, T deb = T(0));
 // fuse_break (with breaking on): the breaking terms are computed inside the assembly from
 // B.q1s / B.q2s, and q** is written to B.q1k / B.q2k (no separate breaking launch)
 // Chebyshev-scheduled Jacobi: sweeps per launch, number of tiles (blocks), one launch.
@@ -120,18 +144,22 @@ template <typename T>
 size_t cheb_tiles(const Prm<T>& P);
 template <typename T>
 size_t asm_tiles(const Prm<T>& P);   // blocks of the 2D assembly (3 partials each)
-// One pass: (x, x_{k-1}) from (xi, xpi) to (xo, xpo); variant 0: weights in shared memory
-// (2 blocks / SM); 1: weights in registers (1 block); 2: pipelined persistent grid (copies
-// of the next tile overlap the sweeps of the current one)
+// One pass: (x, x_{k-1}) from (xi, xpi) to (xo, xpo) in kernel form `variant` (0 ..
+// cheb_pass_forms() - 1, listed at the definition).  The register forms wait at most
+// `polls` polls for each region's staged copies; stall_block >= 0 makes that block's first
+// wait run out with no copy issued (a test hook; -1 in normal use).
 template <typename T>
 int launch_cheb_pass(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, const T* xi,
-                     const T* xpi, T* xo, T* xpo, double* partials, int variant);
+                     const T* xpi, T* xo, T* xpo, double* partials, int variant,
+                     unsigned polls, int stall_block);
+constexpr unsigned kDefaultWaitPolls = 1u << 22;   // nh_params.wait_polls <= 0
 template <typename T>
 int cheb_pass_forms();   // number of pass forms (variants 0 .. n-1)
 template <typename T>
 void launch_matvec2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* x, T* y);
 template <typename T>
-void launch_bicg_init(const Prm<T>& P, const Launch& L, const Bufs<T>& B, double* partials);
+void launch_bicg_init(const Prm<T>& P, const Launch& L, const Bufs<T>& B, double* partials,
+                      int only_fb = 0);   // only_fb: nothing unless B.sctl->fb is set
 // one BiCGStab phase: 0 = A (p^, v), 1 = B (t), 2 = C (x, r); parity selects p^ / v buffers
 template <typename T>
 void launch_bicg_phase(const Prm<T>& P, const Launch& L, const Bufs<T>& B, int parity, int phase,
@@ -139,7 +167,23 @@ void launch_bicg_phase(const Prm<T>& P, const Launch& L, const Bufs<T>& B, int p
 template <typename T>
 void launch_corr2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* q1k,
                    const T* q2k, T de, int with_p, T* eo, T* q1o, T* q2o, T* wo, int final_stage,
-                   double* partials, StepCtl* st);
+                   double* partials, StepCtl* st, const double* dtd = nullptr, T deb = T(0),
+                   const T* dp_alt = nullptr);
+// dp_alt (captured steps): the other buffer of the pass pair; the correction takes the
+// iterate from it when the Chebyshev solve ended on an odd pass without a fallback
+
+// ---- captured steps: device-side control of the solver loops ----
+// condition of a WHILE node: continue while the solve is not done and *cnt < cap (count =
+// 1: count this evaluation, after a body; 0: before the first body)
+void launch_loop_cond(cudaStream_t s, cudaGraphConditionalHandle h, const SolveCtl* ctl,
+                      unsigned* cnt, unsigned cap, int count);
+// after the passes: flag a BiCGStab fallback (status 4 or 5: not diagonally dominant, or
+// stalled), and move the passes' iterate to dp when they ended on an odd pass
+void launch_fb_begin(cudaStream_t s, SolveCtl* ctl);
+template <typename T>
+void launch_settle_fb(const Launch& L, const SolveCtl* ctl, const T* x2, T* dp, size_t n, int K);
+// copy the stage's solve statistics (cnt: [pass pairs, BiCGStab pairs])
+void launch_solve_stats(cudaStream_t s, const SolveCtl* ctl, const unsigned* cnt, SolveStat* out);
 
 // ---- adjoint of the 2D step (nh_adjoint.cu) ----
 template <typename T>
@@ -227,6 +271,8 @@ void launch_lambda(const Prm<T>& P, const Launch& L, const T* eta, const T* q1, 
                    const T* H, int dim, double* partials, StepCtl* st);
 template <typename T>
 void launch_fill(const Launch& L, T* x, size_t n, T v);
+template <typename T>
+void launch_nonfinite(const Launch& L, const T* x, size_t n, StepCtl* st);   // flags NaN / inf
 template <typename T>
 void launch_convert_from_double(const Launch& L, const double* src, T* dst, size_t n);
 

@@ -23,8 +23,9 @@ k_hyp2d_t(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ q1,
           const T* __restrict__ q2, const T* __restrict__ etab, const T* __restrict__ q1b,
           const T* __restrict__ q2b, const T* __restrict__ H, T a, T b, T dt,
           T* __restrict__ eo, T* __restrict__ q1o, T* __restrict__ q2o, StepCtl* st,
-          T* __restrict__ fmx, T* __restrict__ fmy)
+          T* __restrict__ fmx, T* __restrict__ fmy, const double* dtd)
 {
+    if (dtd) dt = (T)*dtd;   // captured steps: the step's dt from device memory
     const int nclamp = hyp_tile<T, TX, TY>(P, eta, q1, q2, etab, q1b, q2b, H, a, b, dt, eo, q1o,
                                            q2o, blockIdx.x, blockIdx.y, fmx, fmy);
     if (nclamp) atomicAdd(&st->clamped, nclamp);
@@ -48,8 +49,9 @@ __global__ void __launch_bounds__(NT)
 k_wtrans2d_t(Prm<T> P, const T* __restrict__ etab, const T* __restrict__ etain,
              const T* __restrict__ etas, const T* __restrict__ H, const T* __restrict__ wb,
              const T* __restrict__ win, const T* __restrict__ fmx, const T* __restrict__ fmy,
-             T a, T b, T dt, T* __restrict__ wo)
+             T a, T b, T dt, T* __restrict__ wo, const double* dtd)
 {
+    if (dtd) dt = (T)*dtd;
     constexpr int CW = TX + 1, CN = CW * (TY + 1);          // cells I0-1.., J0-1..
     constexpr int XW = TX + 2, XN = XW * (TY + 1);          // x faces I0-1..I0+TX
     constexpr int YW = TX + 1, YN = YW * (TY + 2);          // y faces J0-1..J0+TY
@@ -153,8 +155,9 @@ k_asm2d_t(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
           T* __restrict__ cW, T* __restrict__ cE, T* __restrict__ cS, T* __restrict__ cN,
           T* __restrict__ rhs, const T* __restrict__ p0, int resid_form, double* partials,
           SolveCtl* ctl, double tol2, int max_iter, int kpass, int ntx, int ntiles,
-          T* __restrict__ q1k_out, T* __restrict__ q2k_out)
+          T* __restrict__ q1k_out, T* __restrict__ q2k_out, const double* dtd, T deb)
 {
+    if (dtd) de = deb * (T)*dtd;   // as the host forms it: dt rounded to T, times the stage's b
     double acc[3] = {0.0, 0.0, 0.0};
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         asm_tile<T, TX, TY>(P, eta, H, q1k, q2k, q1s, q2s, w_in, w_b, a, b, de, with_coef, ws, cC,
@@ -184,8 +187,9 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_bicg_init(Rows<T> R, const T* __restrict__ b, T* __restrict__ x, T* __restrict__ r,
             T* __restrict__ rh, T* __restrict__ ph0, T* __restrict__ v0, double* partials,
-            SolveCtl* ctl)
+            SolveCtl* ctl, int only_fb)
 {
+    if (only_fb && !ctl->fb) return;   // captured steps: no fallback in this stage
     const int nxn = R.nx + 1;
     const bool zero_rhs = ctl->bb == 0.0;
     double acc[1] = {0.0};
@@ -320,7 +324,8 @@ k_cheb_pass2(Rows<T> R, const T* __restrict__ b, const T* __restrict__ xi,
 {
     if (ctl->done) return;
     extern __shared__ unsigned char cheb2_smem[];
-    T rsum, dmax;
+    double rsum;
+    T dmax;
     if constexpr (PAD)
         cheb_tile_pad<T, NA, NB, BY, K>(R, b, xi, xpi, xo, xpo, ctl, blockIdx.x, blockIdx.y,
                                         reinterpret_cast<T*>(cheb2_smem), rsum, dmax);
@@ -328,24 +333,25 @@ k_cheb_pass2(Rows<T> R, const T* __restrict__ b, const T* __restrict__ xi,
         cheb_tile<T, NA, NB, BY, K, REGW>(R, b, xi, xpi, xo, xpo, ctl, blockIdx.x, blockIdx.y,
                                           reinterpret_cast<T*>(cheb2_smem), rsum, dmax);
     double acc[2];
-    if (dom_reduce_sum_max_f((float)rsum, (float)dmax, partials, &ctl->counter, acc,
-                             blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y) &&
+    if (dom_reduce_sum_max(rsum, (double)dmax, partials, &ctl->counter, acc,
+                           blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y) &&
         threadIdx.x == 0 && threadIdx.y == 0)
-        cheb_finish(ctl, acc, K);
+        cheb_finish_stall(ctl, acc, K);
 }
 
 // Register form of the pass (cheb_region_reg): persistent blocks walk the regions
 // blockIdx.x, blockIdx.x + gridDim.x, ... (row-major over nrx columns of regions), each
 // prefetching its next region while it sweeps the current one.  A wait for a region's
-// copies gives up after kSpinLimit polls: the block then marks the solve failed (status 6)
-// and leaves the region walk.
-constexpr unsigned kSpinLimit = 1u << 22;
-
+// copies gives up after `polls` polls: the block then issues no further copies, waits for
+// the copies of that region it has issued (cheb_drain), marks the solve failed (status 6,
+// or 7 if even the drain ran out) and leaves the region walk.  stall_block >= 0 is a test
+// hook: that block announces bytes on its mbarrier for its first region without issuing
+// any copy, so that its first wait runs out with nothing in flight.
 template <typename T, int C, int R, int NW, int K>
 __global__ void __launch_bounds__(32 * NW, 1)
 k_cheb_reg(Rows<T> Rw, const T* __restrict__ b, const T* __restrict__ xi,
            const T* __restrict__ xpi, T* __restrict__ xo, T* __restrict__ xpo,
-           double* partials, SolveCtl* ctl, int nrx, int nreg)
+           double* partials, SolveCtl* ctl, int nrx, int nreg, unsigned polls, int stall_block)
 {
     if (ctl->done) return;
     constexpr int RW = 32 * C, RH = R * NW, TX = RW - 2 * K, TY = RH - 2 * K;
@@ -361,23 +367,30 @@ k_cheb_reg(Rows<T> Rw, const T* __restrict__ b, const T* __restrict__ xi,
         c1s[tid] = sizeof(T) == 4 ? (T)ctl->c1f[tid] : (T)ctl->c1[tid];
         c2s[tid] = sizeof(T) == 4 ? (T)ctl->c2f[tid] : (T)ctl->c2[tid];
     }
+    const T rsc = sizeof(T) == 4 ? (T)ctl->rscf : (T)ctl->rscd;
+    const double rinv2 = ctl->rinv2;
     auto I0of = [&](int g) { return (g % nrx) * TX - K; };
     auto J0of = [&](int g) { return (g / nrx) * TY - K; };
     int g = blockIdx.x;
+    // test hook: this block announces 16 bytes that no copy will bring
+    const bool stall = (int)blockIdx.x == stall_block;
     if (tid == 0) {
         bases[kPlX] = xi; bases[kPlXp] = xpi; bases[kPlB] = b; bases[kPlC] = Rw.cC;
         bases[kPlW] = Rw.cW; bases[kPlE] = Rw.cE; bases[kPlS] = Rw.cS; bases[kPlN] = Rw.cN;
         mbar_init(&bar, 1);
-        if (g < nreg) mbar_arrive_expect_tx(&bar, region_bulk_bytes<T, RW, RH>(I0of(g), nx));
+        if (g < nreg)
+            mbar_arrive_expect_tx(&bar, stall ? 16u : region_bulk_bytes<T, RW, RH>(I0of(g), nx));
     }
     __syncthreads();
-    if (g < nreg) cheb_stage_region<T, RW, RH, 32 * NW>(bases, nx, ny, I0of(g), J0of(g), planes, &bar);
-    T rsum = T(0), dmax = T(0);
+    if (g < nreg && !stall)
+        cheb_stage_region<T, RW, RH, 32 * NW>(bases, nx, ny, I0of(g), J0of(g), planes, &bar);
+    double rsum = 0.0;
+    T dmax = T(0);
     unsigned phase = 0;
     bool ok = true;
     for (; g < nreg; g += gridDim.x) {
         cp_async_wait_all();
-        const bool got = mbar_wait_bounded(&bar, phase, kSpinLimit);
+        const bool got = mbar_wait_bounded(&bar, phase, polls);
         if (__syncthreads_or(!got)) { ok = false; break; }
         phase ^= 1u;
         const int nxt = g + gridDim.x;
@@ -393,23 +406,22 @@ k_cheb_reg(Rows<T> Rw, const T* __restrict__ b, const T* __restrict__ xi,
             }
         };
         if constexpr (sizeof(T) == 4 && C == 2)
-            cheb_region_reg2<R, NW, K>(Rw, planes, exch, c1s, c2s, I0of(g), J0of(g), xo, xpo,
-                                       rsum, dmax, next);
+            cheb_region_reg2<R, NW, K>(Rw, planes, exch, c1s, c2s, rsc, rinv2, I0of(g),
+                                       J0of(g), xo, xpo, rsum, dmax, next);
         else
-            cheb_region_reg<T, C, R, NW, K>(Rw, planes, exch, c1s, c2s, I0of(g), J0of(g), xo,
-                                            xpo, rsum, dmax, next);
+            cheb_region_reg<T, C, R, NW, K>(Rw, planes, exch, c1s, c2s, rsc, rinv2, I0of(g),
+                                            J0of(g), xo, xpo, rsum, dmax, next);
     }
     if (!ok) {
-        // the region's copies may still be in flight: give them one more bounded wait
-        mbar_wait_bounded(&bar, phase, kSpinLimit);
-        cp_async_wait_all();
-        if (tid == 0) { ctl->status = 6; ctl->done = 1; }
+        const bool issued = !(stall && g == (int)blockIdx.x);
+        const bool drained = cheb_drain(&bar, phase, issued);
+        if (tid == 0) { ctl->status = drained ? 6 : 7; ctl->done = 1; }
     }
     double acc[2];
-    if (dom_reduce_sum_max_f((float)rsum, (float)dmax, partials, &ctl->counter, acc, blockIdx.x,
-                             gridDim.x) &&
+    if (dom_reduce_sum_max(rsum, (double)dmax, partials, &ctl->counter, acc, blockIdx.x,
+                           gridDim.x) &&
         threadIdx.x == 0 && ok)
-        cheb_finish(ctl, acc, K);
+        cheb_finish_stall(ctl, acc, K);
 }
 
 template <typename T, int TX, int TY>
@@ -419,8 +431,13 @@ k_corr2d_t(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
            const T* __restrict__ p, const T* __restrict__ dp, T* __restrict__ pout, T de,
            int with_p, T* __restrict__ eo, T* __restrict__ q1o, T* __restrict__ q2o,
            T* __restrict__ wo, int final_stage, double* partials, StepCtl* st, int ntx,
-           int ntiles)
+           int ntiles, const double* dtd, T deb, const T* __restrict__ dp_alt,
+           const SolveCtl* sctl, int K)
 {
+    if (dtd) de = deb * (T)*dtd;
+    // captured steps: a Chebyshev solve that ended on an odd pass left its iterate in the
+    // other buffer of the ping-pong pair (a BiCGStab fallback always writes dp)
+    if (dp_alt && !sctl->fb && ((sctl->sweeps / K) & 1)) dp = dp_alt;
     T lam = T(0);
     int bad = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -890,7 +907,7 @@ k_corr1d(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
                 const T Tn = -T(0.5) * (h * (pe - pw) / P.dx + T(0.5) * (pe + pw) * xi / P.dx);
                 qn += de * Tn;
             }
-            if (h <= P.hdry) qn = T(0);   // dry cells carry no discharge
+            if (P.dry_zero && h <= P.hdry) qn = T(0);   // dry cells: no discharge
             eo[c] = e; qo[c] = qn;
             if (!isfinite(e) || !isfinite(qn)) bad = 1;
             if (final_stage) {
@@ -926,6 +943,49 @@ k_lambda(Prm<T> P, int dim, const T* __restrict__ eta, const T* __restrict__ q1,
     GRID_STRIDE(idx, (long long)P.nx * P.ny)
         acc[0] = fmax(acc[0], lambda_cell(P, dim, eta, q1, q2, H, idx));
     if (grid_reduce<1, 1u>(acc, partials, &st->counter) && threadIdx.x == 0) st->lam = acc[0];
+}
+
+// ================================================================ captured steps
+
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, const SolveCtl* ctl, unsigned* cnt,
+                            unsigned cap, int count)
+{
+    if (threadIdx.x == 0) {
+        const unsigned it = count ? ++*cnt : *cnt;
+        cudaGraphSetConditional(h, (!ctl->done && it < cap) ? 1u : 0u);
+    }
+}
+
+__global__ void k_fb_begin(SolveCtl* ctl)
+{
+    if (threadIdx.x == 0) ctl->fb = (ctl->status == 4 || ctl->status == 5) ? 1 : 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_settle_fb(const SolveCtl* ctl, const T* __restrict__ x2, T* __restrict__ dp, long long n, int K)
+{
+    if (!ctl->fb || ((ctl->sweeps / K) & 1) == 0) return;
+    GRID_STRIDE(idx, n) dp[idx] = x2[idx];
+}
+
+__global__ void k_solve_stats(const SolveCtl* ctl, const unsigned* cnt, SolveStat* out)
+{
+    if (threadIdx.x == 0) {
+        out->rr = ctl->rr; out->bb = ctl->bb; out->bdb = ctl->bdb;
+        out->sweeps = ctl->sweeps; out->iter = ctl->iter; out->status = ctl->status;
+        out->fb = ctl->fb; out->passes = 2 * (int)cnt[0]; out->bicg = 2 * (int)cnt[1];
+    }
+}
+
+// Flags st->nonfinite when any of the n values of x is NaN or infinite (input checks).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_nonfinite(const T* __restrict__ x, long long n, StepCtl* st)
+{
+    int bad = 0;
+    GRID_STRIDE(idx, n) bad |= !isfinite(x[idx]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->nonfinite, 1);
 }
 
 template <typename T>
@@ -972,29 +1032,30 @@ int resident_grid(K kernel, int threads, size_t smem)
 template <typename T>
 void launch_hyp2d(const Prm<T>& P, const Launch& L, const T* eta, const T* q1, const T* q2,
                   const T* etab, const T* q1b, const T* q2b, const T* H, T a, T b, T dt,
-                  T* eo, T* q1o, T* q2o, StepCtl* st, T* fmx, T* fmy)
+                  T* eo, T* q1o, T* q2o, StepCtl* st, T* fmx, T* fmy, const double* dtd)
 {
     constexpr int TX = 32, TY = sizeof(T) == 4 ? 16 : 8;
     dim3 grid((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
     k_hyp2d_t<T, TX, TY><<<grid, kThreads, 0, L.s>>>(P, eta, q1, q2, etab, q1b, q2b, H, a, b, dt,
-                                                    eo, q1o, q2o, st, fmx, fmy);
+                                                    eo, q1o, q2o, st, fmx, fmy, dtd);
 }
 
 template <typename T>
 void launch_wtrans2d(const Prm<T>& P, const Launch& L, const T* etab, const T* etain,
                      const T* etas, const T* H, const T* wb, const T* win, const T* fmx,
-                     const T* fmy, T a, T b, T dt, T* wo)
+                     const T* fmy, T a, T b, T dt, T* wo, const double* dtd)
 {
     constexpr int TX = 32, TY = 16, NT = 256;
     dim3 grid((P.nx + 1 + TX - 1) / TX, (P.ny + 1 + TY - 1) / TY);
     k_wtrans2d_t<T, TX, TY, NT><<<grid, NT, 0, L.s>>>(P, etab, etain, etas, H, wb, win, fmx,
-                                                       fmy, a, b, dt, wo);
+                                                       fmy, a, b, dt, wo, dtd);
 }
 
 template <typename T>
 void launch_asm2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* w_in,
                   const T* w_base, T a, T b, T de, int with_coef, int resid_form, double tol2,
-                  int max_iter, int kpass, double* partials, SolveCtl* ctl, int fuse_break)
+                  int max_iter, int kpass, double* partials, SolveCtl* ctl, int fuse_break,
+                  const double* dtd, T deb)
 {
     constexpr int TX = 32, TY = sizeof(T) == 4 ? 16 : 8;   // FP64: static shared memory < 48 KB
     static const int res = resident_grid(k_asm2d_t<T, TX, TY>, kThreads, 0);
@@ -1004,7 +1065,8 @@ void launch_asm2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* w
     k_asm2d_t<T, TX, TY><<<ntiles < res ? ntiles : res, kThreads, 0, L.s>>>(
         P, B.etas, B.H, fuse ? nullptr : B.q1k, fuse ? nullptr : B.q2k, B.q1s, B.q2s, w_in, w_base,
         a, b, de, with_coef, B.ws, B.cC, B.cW, B.cE, B.cS, B.cN, B.rhs, B.p, resid_form, partials,
-        ctl, tol2, max_iter, kpass, ntx, ntiles, fuse ? B.q1k : nullptr, fuse ? B.q2k : nullptr);
+        ctl, tol2, max_iter, kpass, ntx, ntiles, fuse ? B.q1k : nullptr, fuse ? B.q2k : nullptr,
+        dtd, deb);
 }
 
 // Sweeps per Chebyshev pass: 8 in FP32, 4 in FP64 (the forms below).
@@ -1055,7 +1117,8 @@ int launch_cheb_cfg(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, const T* 
 // (the staged planes take most of the shared memory), K sweeps per pass.
 template <typename T, int C, int R, int NW, int K>
 int launch_cheb_reg(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, const T* xi,
-                    const T* xpi, T* xo, T* xpo, double* partials)
+                    const T* xpi, T* xo, T* xpo, double* partials, unsigned polls,
+                    int stall_block)
 {
     constexpr int TX = 32 * C - 2 * K, TY = R * NW - 2 * K;
     constexpr size_t smem = cheb_reg_smem<T, C, R, NW>();
@@ -1077,7 +1140,8 @@ int launch_cheb_reg(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, const T* 
     const int nrx = (P.nx + 1 + TX - 1) / TX, nry = (P.ny + 1 + TY - 1) / TY;
     const int nreg = nrx * nry;
     k_cheb_reg<T, C, R, NW, K><<<nreg < nblk ? nreg : nblk, 32 * NW, smem, s>>>(
-        rows_of(P, B), B.rhs, xi, xpi, xo, xpo, partials, B.sctl, nrx, nreg);
+        rows_of(P, B), B.rhs, xi, xpi, xo, xpo, partials, B.sctl, nrx, nreg, polls,
+        stall_block);
     return 0;
 }
 
@@ -1094,7 +1158,8 @@ template <typename T> int cheb_pass_forms() { return sizeof(T) == 4 ? 8 : 4; }
 
 template <typename T>
 int launch_cheb_pass(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, const T* xi,
-                     const T* xpi, T* xo, T* xpo, double* partials, int variant)
+                     const T* xpi, T* xo, T* xpo, double* partials, int variant,
+                     unsigned polls, int stall_block)
 {
     if constexpr (sizeof(T) == 4) {
         switch (variant) {
@@ -1102,15 +1167,15 @@ int launch_cheb_pass(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, const T*
         case 2: return launch_cheb_cfg<T, 2, 4, 16, true, 2, true, 8>(P, s, B, xi, xpi, xo, xpo, partials);
         case 3: return launch_cheb_cfg<T, 2, 4, 16, true, 1, true, 8>(P, s, B, xi, xpi, xo, xpo, partials);
         case 4: return launch_cheb_cfg<T, 4, 4, 16, true, 1, true, 8>(P, s, B, xi, xpi, xo, xpo, partials);
-        case 5: return launch_cheb_reg<T, 2, 4, 16, 8>(P, s, B, xi, xpi, xo, xpo, partials);
-        case 6: return launch_cheb_reg<T, 2, 2, 32, 8>(P, s, B, xi, xpi, xo, xpo, partials);
-        case 7: return launch_cheb_reg<T, 3, 4, 16, 8>(P, s, B, xi, xpi, xo, xpo, partials);
+        case 5: return launch_cheb_reg<T, 2, 4, 16, 8>(P, s, B, xi, xpi, xo, xpo, partials, polls, stall_block);
+        case 6: return launch_cheb_reg<T, 2, 2, 32, 8>(P, s, B, xi, xpi, xo, xpo, partials, polls, stall_block);
+        case 7: return launch_cheb_reg<T, 3, 4, 16, 8>(P, s, B, xi, xpi, xo, xpo, partials, polls, stall_block);
         default: return launch_cheb_cfg<T, 2, 2, 32, true, 1, true, 8>(P, s, B, xi, xpi, xo, xpo, partials);
         }
     } else {
         if (variant == 1) return launch_cheb_cfg<T, 2, 2, 16, true, 1>(P, s, B, xi, xpi, xo, xpo, partials);
         if (variant == 2) return launch_cheb_cfg<T, 2, 2, 16, true, 1, true>(P, s, B, xi, xpi, xo, xpo, partials);
-        if (variant == 3) return launch_cheb_reg<T, 2, 2, 16, 4>(P, s, B, xi, xpi, xo, xpo, partials);
+        if (variant == 3) return launch_cheb_reg<T, 2, 2, 16, 4>(P, s, B, xi, xpi, xo, xpo, partials, polls, stall_block);
         return launch_cheb_cfg<T, 2, 2, 16, false, 2>(P, s, B, xi, xpi, xo, xpo, partials);
     }
 }
@@ -1122,10 +1187,11 @@ void launch_matvec2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T
 }
 
 template <typename T>
-void launch_bicg_init(const Prm<T>& P, const Launch& L, const Bufs<T>& B, double* partials)
+void launch_bicg_init(const Prm<T>& P, const Launch& L, const Bufs<T>& B, double* partials,
+                      int only_fb)
 {
     k_bicg_init<T><<<L.nblk, kThreads, 0, L.s>>>(rows_of(P, B), B.rhs, B.dp, B.r, B.rh, B.ph[0],
-                                                 B.v[0], partials, B.sctl);
+                                                 B.v[0], partials, B.sctl, only_fb);
 }
 
 template <typename T>
@@ -1149,14 +1215,15 @@ void launch_bicg_phase(const Prm<T>& P, const Launch& L, const Bufs<T>& B, int p
 template <typename T>
 void launch_corr2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* q1k,
                    const T* q2k, T de, int with_p, T* eo, T* q1o, T* q2o, T* wo, int final_stage,
-                   double* partials, StepCtl* st)
+                   double* partials, StepCtl* st, const double* dtd, T deb, const T* dp_alt)
 {
     constexpr int TX = 32, TY = 8;
     static const int res = resident_grid(k_corr2d_t<T, TX, TY>, 256, 0);
     const int ntx = (P.nx + 1 + TX - 1) / TX, ntiles = ntx * ((P.ny + 1 + TY - 1) / TY);
     k_corr2d_t<T, TX, TY><<<ntiles < res ? ntiles : res, 256, 0, L.s>>>(
         P, B.etas, B.H, q1k, q2k, B.ws, B.p, B.dp, B.palt, de, with_p, eo, q1o, q2o, wo,
-        final_stage, partials, st, ntx, ntiles);
+        final_stage, partials, st, ntx, ntiles, dtd, deb, dp_alt, B.sctl,
+        cheb_sweeps_per_pass<T>());
 }
 
 template <typename T>
@@ -1291,6 +1358,31 @@ void launch_lambda(const Prm<T>& P, const Launch& L, const T* eta, const T* q1, 
     k_lambda<T><<<L.nblk, kThreads, 0, L.s>>>(P, dim, eta, q1, q2, H, partials, st);
 }
 
+void launch_loop_cond(cudaStream_t s, cudaGraphConditionalHandle h, const SolveCtl* ctl,
+                      unsigned* cnt, unsigned cap, int count)
+{
+    k_loop_cond<<<1, 32, 0, s>>>(h, ctl, cnt, cap, count);
+}
+
+void launch_fb_begin(cudaStream_t s, SolveCtl* ctl) { k_fb_begin<<<1, 32, 0, s>>>(ctl); }
+
+template <typename T>
+void launch_settle_fb(const Launch& L, const SolveCtl* ctl, const T* x2, T* dp, size_t n, int K)
+{
+    k_settle_fb<T><<<L.nblk, kThreads, 0, L.s>>>(ctl, x2, dp, (long long)n, K);
+}
+
+void launch_solve_stats(cudaStream_t s, const SolveCtl* ctl, const unsigned* cnt, SolveStat* out)
+{
+    k_solve_stats<<<1, 32, 0, s>>>(ctl, cnt, out);
+}
+
+template <typename T>
+void launch_nonfinite(const Launch& L, const T* x, size_t n, StepCtl* st)
+{
+    k_nonfinite<T><<<L.nblk, kThreads, 0, L.s>>>(x, (long long)n, st);
+}
+
 template <typename T>
 void launch_fill(const Launch& L, T* x, size_t n, T v)
 {
@@ -1306,10 +1398,10 @@ void launch_convert_from_double(const Launch& L, const double* src, T* dst, size
 #define NH_INSTANTIATE(T)                                                                       \
     template void launch_hyp2d<T>(const Prm<T>&, const Launch&, const T*, const T*, const T*,  \
                                   const T*, const T*, const T*, const T*, T, T, T, T*, T*, T*, \
-                                  StepCtl*, T*, T*);                                           \
+                                  StepCtl*, T*, T*, const double*);                            \
     template void launch_wtrans2d<T>(const Prm<T>&, const Launch&, const T*, const T*,         \
                                      const T*, const T*, const T*, const T*, const T*,         \
-                                     const T*, T, T, T, T*);                                   \
+                                     const T*, T, T, T, T*, const double*);                    \
     template void launch_relax<T>(const Prm<T>&, const Launch&, const RelaxZ&, int, T*, T*,    \
                                   T*, T*, T*, const T*, const T*, const T*, const T*,          \
                                   const T*, const T*);                                         \
@@ -1318,20 +1410,24 @@ void launch_convert_from_double(const Launch& L, const double* src, T* dst, size
                                      T, T*);                                                   \
     template void launch_asm2d<T>(const Prm<T>&, const Launch&, const Bufs<T>&, const T*,      \
                                   const T*, T, T, T, int, int, double, int, int, double*,      \
-                                  SolveCtl*, int);                                             \
+                                  SolveCtl*, int, const double*, T);                           \
     template int cheb_sweeps_per_pass<T>();                                                    \
     template size_t cheb_tiles<T>(const Prm<T>&);                                              \
     template size_t asm_tiles<T>(const Prm<T>&);                                               \
     template int cheb_pass_forms<T>();                                                          \
     template int launch_cheb_pass<T>(const Prm<T>&, cudaStream_t, const Bufs<T>&, const T*,   \
-                                     const T*, T*, T*, double*, int);                           \
+                                     const T*, T*, T*, double*, int, unsigned, int);            \
     template void launch_matvec2d<T>(const Prm<T>&, const Launch&, const Bufs<T>&, const T*,   \
                                      T*);                                                      \
-    template void launch_bicg_init<T>(const Prm<T>&, const Launch&, const Bufs<T>&, double*);  \
+    template void launch_bicg_init<T>(const Prm<T>&, const Launch&, const Bufs<T>&, double*,   \
+                                      int);                                                    \
+    template void launch_settle_fb<T>(const Launch&, const SolveCtl*, const T*, T*, size_t,    \
+                                      int);                                                    \
     template void launch_bicg_phase<T>(const Prm<T>&, const Launch&, const Bufs<T>&, int, int, \
                                        double*);                                               \
     template void launch_corr2d<T>(const Prm<T>&, const Launch&, const Bufs<T>&, const T*,     \
-                                   const T*, T, int, T*, T*, T*, T*, int, double*, StepCtl*);  \
+                                   const T*, T, int, T*, T*, T*, T*, int, double*, StepCtl*,   \
+                                   const double*, T, const T*);                                \
     template void launch_hyp1d<T>(const Prm<T>&, const Launch&, const T*, const T*, const T*,  \
                                   const T*, const T*, T, T, T, T*, T*, StepCtl*, T*);          \
     template void launch_break1d<T>(const Prm<T>&, const Launch&, const T*, const T*, const T*,\
@@ -1350,6 +1446,7 @@ void launch_convert_from_double(const Launch& L, const double* src, T* dst, size
     template void launch_lambda<T>(const Prm<T>&, const Launch&, const T*, const T*, const T*, \
                                    const T*, int, double*, StepCtl*);                          \
     template void launch_fill<T>(const Launch&, T*, size_t, T);                                \
+    template void launch_nonfinite<T>(const Launch&, const T*, size_t, StepCtl*);               \
     template void launch_convert_from_double<T>(const Launch&, const double*, T*, size_t);
 
 NH_INSTANTIATE(float)

@@ -15,7 +15,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libnh.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ENONFINITE = 0, -1, -2, -3, -4, -5
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ENONFINITE, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 WALL, OUTFLOW, PERIODIC = 0, 1, 2
 BICGSTAB, CHEBYSHEV = 0, 1
 FP64, FP32 = 0, 1
@@ -35,7 +35,8 @@ class Params(C.Structure):
                 ("solver", C.c_int), ("tol", C.c_double), ("max_iter", C.c_int),
                 ("precision", C.c_int), ("fixed_dt", C.c_double), ("eps_dp", C.c_double),
                 ("adjoint_frozen_limiter", C.c_int), ("cheb_form", C.c_int),
-                ("w_equation", C.c_int), ("relax_width", C.c_double * 4)]
+                ("w_equation", C.c_int), ("relax_width", C.c_double * 4),
+                ("dry_zero", C.c_int), ("wait_polls", C.c_int), ("capture", C.c_int)]
 
 
 class StatsT(C.Structure):
@@ -67,7 +68,8 @@ EXPORTS = ("nh_default_params", "nh_create", "nh_set_state", "nh_get_state", "nh
            "nh_batch_stats", "nh_batch_get_tuning", "nh_batch_set_tuning",
            "nh_batch_candidate", "nh_batch_last_error", "nh_batch_destroy",
            "nh_batch_profile_enable", "nh_batch_profile_read", "nh_tape_bytes",
-           "nh_step_taped", "nh_adjoint_step", "nh_cheb_forms", "nh_set_relax_target")
+           "nh_step_taped", "nh_adjoint_step", "nh_cheb_forms", "nh_set_relax_target",
+           "nh_debug_stall_copies")
 
 BATCH_AUTOTUNE, BATCH_GRAPH = 1, 2
 
@@ -107,6 +109,7 @@ def load():
     L.nh_tridiag_batched.argtypes = [C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, vp, vp]
     L.nh_debug_hyperbolic.argtypes = [H, C.c_double, vp, vp, vp, C.c_int]
     L.nh_debug_system.argtypes = [H, C.c_double, vp, vp, vp, C.c_int]
+    L.nh_debug_stall_copies.argtypes = [H, C.c_int]
     L.nh_set_relax_target.argtypes = [H, vp, vp, vp, vp, vp, C.c_int]
     L.nh_create_batch.argtypes = [C.c_int, C.POINTER(Grid), C.POINTER(C.c_void_p),
                                   C.POINTER(Params), vp, C.c_int, C.POINTER(H)]
@@ -298,6 +301,11 @@ class Sim:
         self._check(load().nh_debug_hyperbolic(self._h, float(dt),
                                                *[C.c_void_p(o.ctypes.data) for o in out], HOST))
         return out
+
+    def debug_stall_copies(self, block=0):
+        """nh_debug_stall_copies: the next register-form pass lets `block` wait for copies
+        it never issued (its wait runs out; the step returns ETIMEOUT)."""
+        self._check(load().nh_debug_stall_copies(self._h, int(block)))
 
     def debug_system(self, dt, x):
         x = np.ascontiguousarray(np.asarray(x, dtype=self.dtype)).reshape(self.node_shape)

@@ -42,7 +42,7 @@ def make(wl, precision="fp64", **kw):
                  g=prm.get("g", 9.81), cfl=prm.get("cfl", 0.9),
                  manning=prm.get("manning_n", 0.0), breaking=bool(prm.get("breaking", 0)),
                  B1=prm.get("B1", 0.15), nonhydro=bool(prm.get("nonhydrostatic", 1)),
-                 tol=1e-14)
+                 tol=1e-14, dry_zero=bool(prm.get("dry_zero", 1)))
     return sim, ocfg
 
 
@@ -121,16 +121,29 @@ def test_full_step_shoals_fp64(solver):
     assert abs(g["t"] - t) < 1e-12 * t
 
 
-def test_full_step_island_wetdry_breaking_fp64():
+@pytest.mark.parametrize("dry_zero,steps", [(1, 15), (0, 2)])
+def test_full_step_island_wetdry_breaking_fp64(dry_zero, steps):
+    """Both readings of the wet/dry fronts of the second step: q = 0 in dry cells after
+    each stage (dry_zero = 1, App. B A.2's premise imposed) and the step exactly as Sec. 4.5
+    states it (dry_zero = 0), each against the oracle in the same mode.  In the literal form
+    the nearly dry cells at the shoreline carry a discharge, and their desingularised
+    velocity (~ sqrt(2) h q / delta^2 for h << delta) is proportional to depths of 1e-12 m
+    and less, which this path holds as eta = h - H to +-ulp(H)/2 (~3e-17 m absolute) while
+    the oracle holds h itself: from the second step on, p and q there part at the 1e-10 level
+    (3.2e-10 on p after 4 steps).  Rounding the oracle's own state through eta once per
+    step moves its q by 4.5e-9 after 8 steps in that form and by nothing above 1e-16 with
+    q = 0 in dry cells.  So the literal form is compared over 2 steps."""
     wl = island(64)
-    sim, g, (h, q1, q2, w, p, t, s, it) = _run_both(wl, 15)
+    sim, g, (h, q1, q2, w, p, t, s, it) = _run_both(wl, steps, dry_zero=dry_zero)
     assert rel(g["eta"] + wl.H, h) < 1e-10
     assert rel_q(g["q1"], g["q2"], q1, q2) < 1e-10
     assert rel(g["p"], p) < 1e-10
     hg = g["eta"] + wl.H
     assert (hg >= 0).all()
     dry = hg <= 1e-5
-    assert dry.any() and not g["q1"][dry].any() and not g["q2"][dry].any()
+    assert dry.any()
+    if dry_zero:
+        assert not g["q1"][dry].any() and not g["q2"][dry].any()
 
 
 def test_island_long_run_within_oracle_rounding_sensitivity():
@@ -208,12 +221,53 @@ def test_full_size_island_mass_with_walls_fp32():
     assert 0 <= st["cheb_form"] < nh.cheb_forms("fp32")
 
 
-def test_fp32_full_size_shoals_within_1e4_of_fp64_oracle():
-    """The 1024^2 shoals workload in FP32 (dx = 0.1 m) against the FP64 oracle: eta within
-    1e-4 relative L-infinity after 4 steps."""
-    wl = inputs.shoals_2d()
-    sim, g, (h, q1, q2, w, p, t, s, it) = _run_both(wl, 4, "fp32", tol=1e-5)
+def test_full_size_island_fp32_within_1e4_of_fp64_oracle():
+    """The bench configuration itself: the 4096^2 island in FP32 (wet/dry, breaking, Manning,
+    outflow, solver tol 1e-5, the pass form the timing chooser picks) for 2 steps against
+    the FP64 oracle (OpenMP, BiCGStab to 1e-9), element by element: eta within 1e-4
+    relative L-infinity, the same time reached."""
+    wl, sim = _island_full_size()
+    sim.set_state(wl.eta.astype(np.float32), wl.q1.astype(np.float32), wl.q2.astype(np.float32))
+    for _ in range(2):
+        sim.step()
+    g = sim.get_state()
+    sim.close()
+    c = O.cfg(wl.nx, wl.ny, dx=wl.dx, bc=wl.bc, manning=0.015, breaking=True, tol=1e-9)
+    zn = np.zeros((wl.ny + 1, wl.nx + 1))
+    h, q1, q2, w, p, t, s, it = O.run_2d(c, wl.H, wl.h, wl.q1, wl.q2, zn, zn, max_steps=2)
+    assert s == 2
     assert rel(g["eta"], h - wl.H) < 1e-4
+    assert abs(g["t"] - t) <= 1e-6 * t
+
+
+@pytest.mark.parametrize("steps,cfl", [(4, 0.9), (50, 0.9), (50, 0.7)])
+def test_fp32_full_size_shoals_against_fp64_oracle(steps, cfl):
+    """The 1024^2 shoals workload in FP32 (dx = 0.1 m) against the FP64 oracle (OpenMP,
+    BiCGStab to 1e-9), element by element on eta: within 1e-4 relative L-infinity, or, where
+    the scheme itself amplifies rounding beyond that, within the oracle's own distance to a
+    run from FP32-size perturbed depths (6e-8 relative).  At the paper's CFL 0.9 the
+    MUSCL-minmod / SSP-RK2 step amplifies rounding-size perturbations by orders of magnitude
+    within tens of steps (measured on the oracle: 6e-9 and 6e-8 input perturbations both
+    move eta by 5e-4 after 50 steps); at CFL 0.7 it does not (1.4e-5), and FP32 holds 1e-4."""
+    wl = inputs.shoals_2d()
+    sim, _ = make(wl, "fp32", tol=1e-5, cfl=cfl)
+    c = O.cfg(wl.nx, wl.ny, dx=wl.dx, bc=wl.bc, tol=1e-9, cfl=cfl)
+    sim.set_state(wl.eta.astype(np.float32), wl.q1.astype(np.float32), wl.q2.astype(np.float32))
+    for _ in range(steps):
+        sim.step()
+    g = sim.get_state()
+    sim.close()
+    zn = np.zeros((wl.ny + 1, wl.nx + 1))
+    h, q1, q2, w, p, t, s, it = O.run_2d(c, wl.H, wl.h, wl.q1, wl.q2, zn, zn, max_steps=steps)
+    err = rel(g["eta"], h - wl.H)
+    if steps <= 4 or cfl < 0.9:
+        assert err < 1e-4, err
+    else:
+        rng = np.random.default_rng(0)
+        hp = wl.h * (1 + 6e-8 * rng.standard_normal(wl.h.shape))
+        per = O.run_2d(c, wl.H, hp, wl.q1, wl.q2, zn, zn, max_steps=steps)
+        spread = rel(per[0] - wl.H, h - wl.H)
+        assert err <= max(1e-4, spread), (err, spread)
 
 
 def _oracle_spread(wl, c, steps, eps=6e-8):
