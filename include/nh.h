@@ -280,8 +280,11 @@ int nh_tridiag_batched(int n, int rows, int precision, const void *a, const void
  * current); make that first call before any stream capture.  All calls share the one
  * array: calls whose executions overlap on the GPU (for example on two streams at once)
  * race and give wrong results; serialise them.  No part of the scratch needs to start at
- * zero.  The paper has no counterpart of this entry point.  Same arguments and return
- * codes as nh_tridiag_batched. */
+ * zero.  The looked-up address is kept for the life of the process: do not call this
+ * entry point on a device after cudaDeviceReset (or any re-creation of its primary
+ * context) in the same process, since the kept address would then be stale.  The paper
+ * has no counterpart of this entry point.  Same arguments and return codes as
+ * nh_tridiag_batched. */
 int nh_tridiag_batched_noalloc(int n, int rows, int precision, const void *a, const void *b,
                                const void *c, const void *d, void *x, void *stream);
 
