@@ -372,8 +372,13 @@ def run_adjoint(args, torch, ws, rank, local, dist):
     y, x = np.mgrid[0:n, 0:n] / float(n)
     d = np.sin(2 * 3.1 * x + 0.4) * np.cos(2.3 * y + 1.7)
     eps = 1e-4
-    fdH = (Jf(wl.H + eps * d, wl.eta) - Jf(wl.H - eps * d, wl.eta)) / (2 * eps)
-    fde = (Jf(wl.H, wl.eta + eps * d) - Jf(wl.H, wl.eta - eps * d)) / (2 * eps)
+    # central differences of the FP64 forward over eps: is the reference itself converged?
+    sweep = {}
+    for e_ in (1e-3, 1e-4, 1e-5, 1e-6, 1e-7):
+        sweep[str(e_)] = {
+            "H": (Jf(wl.H + e_ * d, wl.eta) - Jf(wl.H - e_ * d, wl.eta)) / (2 * e_),
+            "eta0": (Jf(wl.H, wl.eta + e_ * d) - Jf(wl.H, wl.eta - e_ * d)) / (2 * e_)}
+    fdH, fde = sweep[str(eps)]["H"], sweep[str(eps)]["eta0"]
 
     def Jfe(HH, ee):
         with torch.no_grad():
@@ -381,7 +386,7 @@ def run_adjoint(args, torch, ws, rank, local, dist):
                                 target[:nexact]))
 
     fd_exact = {}
-    for e_ in (1e-4, 1e-5):
+    for e_ in (1e-4, 1e-5, 1e-6, 1e-7):
         fd_exact[str(e_)] = {
             "H": (Jfe(wl.H + e_ * d, wl.eta) - Jfe(wl.H - e_ * d, wl.eta)) / (2 * e_),
             "eta0": (Jfe(wl.H, wl.eta + e_ * d) - Jfe(wl.H, wl.eta - e_ * d)) / (2 * e_)}
@@ -408,7 +413,11 @@ def run_adjoint(args, torch, ws, rank, local, dist):
                     "H": {"adjoint": float((gH64 * d).sum()), "fd": fdH,
                           "rel": abs(float((gH64 * d).sum()) - fdH) / abs(fdH)},
                     "eta0": {"adjoint": float((ge64 * d).sum()), "fd": fde,
-                             "rel": abs(float((ge64 * d).sum()) - fde) / abs(fde)}},
+                             "rel": abs(float((ge64 * d).sum()) - fde) / abs(fde)},
+                    "eps_sweep": {k: {"H": v["H"], "eta0": v["eta0"],
+                                      "rel_H": abs(float((gH64 * d).sum()) - v["H"]) / abs(v["H"]),
+                                      "rel_eta0": abs(float((ge64 * d).sum()) - v["eta0"]) / abs(v["eta0"])}
+                                  for k, v in sweep.items()}},
                 "linearisation": "frozen limiter (exact branch derivative grows by a grid-scale mode)",
                 "exact": {"steps": nexact, "adjoint_over_forward": ste["backward_ms"] / ste["forward_ms"],
                           "adjoint_H": float((gHe * d).sum()), "adjoint_eta0": float((gee * d).sum()),

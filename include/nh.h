@@ -187,6 +187,14 @@ int nh_set_state(nh_handle *h, const void *eta, const void *q1, const void *q2,
 int nh_get_state(nh_handle *h, void *eta, void *q1, void *q2, void *w, void *p, double *t,
                  int where);
 
+/* Gauges: eta at n cells (row-major indices j nx + i, cells[k] in [0, nx ny)) into out[k],
+ * as the time series at wave gauges that the paper's experiments record (Sec. 7).  cells
+ * and out are device memory of the current device (out in the handle's precision); the
+ * gather is one kernel enqueued on the handle's stream, so a series can be recorded every
+ * step without a host round trip.  n = 0 does nothing.  NH_EINVAL for null pointers or
+ * n < 0; indices out of range are not checked on the device (the caller validates them). */
+int nh_gauges(nh_handle *h, const int *cells, int n, void *out);
+
 /* Advance one time step.  dt > 0: use it; dt <= 0: the Eq. (23) step of the current
  * state (or params.fixed_dt when that is > 0).  *dt_taken (may be NULL) receives it.
  * Returns NH_ENOCONV when a pressure solve stopped at max_iter or broke down (the step is

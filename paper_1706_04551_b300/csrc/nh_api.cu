@@ -31,6 +31,7 @@ struct Base {
                                  const void* w, const void* p, int where) = 0;
     virtual int lambda(double* lam) = 0;
     virtual int mass(double* m) = 0;
+    virtual int gauges(const int* cells, int n, void* out) = 0;
     virtual int cheb_form() const = 0;   // pass form in use, -1 while timing
     virtual int debug_hyp(double dt, void* e, void* a, void* b, int where) = 0;
     virtual int debug_system(double dt, const void* x, void* rhs, void* mx, int where) = 0;
@@ -390,6 +391,14 @@ struct Impl : Base {
         cudaError_t e = cudaStreamSynchronize(hd->s);
         if (e != cudaSuccess) return cuda_fail(hd, e, "lambda");
         *lam = h_stctl->lam;
+        return NH_OK;
+    }
+
+    int gauges(const int* cells, int n, void* out) override
+    {
+        launch_gather<T>(hd->s, B.eta, cells, n, static_cast<T*>(out));
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(hd, e, "nh_gauges");
         return NH_OK;
     }
 
@@ -1399,6 +1408,13 @@ int nh_run(nh_handle* h, double t_end, long long max_steps, long long* steps_tak
     }
     if (steps_taken) *steps_taken = s;
     return rc;
+}
+
+int nh_gauges(nh_handle* h, const int* cells, int n, void* out)
+{
+    if (!h || n < 0 || (n > 0 && (!cells || !out))) return NH_EINVAL;
+    if (n == 0) return NH_OK;
+    return h->impl->gauges(cells, n, out);
 }
 
 int nh_stats(nh_handle* h, nh_stats_t* out)

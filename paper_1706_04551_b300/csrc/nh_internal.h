@@ -274,6 +274,8 @@ void launch_fill(const Launch& L, T* x, size_t n, T v);
 template <typename T>
 void launch_nonfinite(const Launch& L, const T* x, size_t n, StepCtl* st);   // flags NaN / inf
 template <typename T>
+void launch_gather(cudaStream_t s, const T* x, const int* idx, int n, T* out);   // out = x[idx]
+template <typename T>
 void launch_convert_from_double(const Launch& L, const double* src, T* dst, size_t n);
 
 int pcr_max_n(int elem_bytes);

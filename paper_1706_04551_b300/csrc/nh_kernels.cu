@@ -1378,6 +1378,20 @@ void launch_solve_stats(cudaStream_t s, const SolveCtl* ctl, const unsigned* cnt
 }
 
 template <typename T>
+__global__ void k_gather(const T* __restrict__ x, const int* __restrict__ idx, int n,
+                         T* __restrict__ out)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+        out[k] = x[idx[k]];
+}
+
+template <typename T>
+void launch_gather(cudaStream_t s, const T* x, const int* idx, int n, T* out)
+{
+    k_gather<T><<<(n + 255) / 256 < 148 ? (n + 255) / 256 : 148, 256, 0, s>>>(x, idx, n, out);
+}
+
+template <typename T>
 void launch_nonfinite(const Launch& L, const T* x, size_t n, StepCtl* st)
 {
     k_nonfinite<T><<<L.nblk, kThreads, 0, L.s>>>(x, (long long)n, st);
@@ -1447,6 +1461,7 @@ void launch_convert_from_double(const Launch& L, const double* src, T* dst, size
                                    const T*, int, double*, StepCtl*);                          \
     template void launch_fill<T>(const Launch&, T*, size_t, T);                                \
     template void launch_nonfinite<T>(const Launch&, const T*, size_t, StepCtl*);               \
+    template void launch_gather<T>(cudaStream_t, const T*, const int*, int, T*);               \
     template void launch_convert_from_double<T>(const Launch&, const double*, T*, size_t);
 
 NH_INSTANTIATE(float)

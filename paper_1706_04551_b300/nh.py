@@ -69,7 +69,7 @@ EXPORTS = ("nh_default_params", "nh_create", "nh_set_state", "nh_get_state", "nh
            "nh_batch_candidate", "nh_batch_last_error", "nh_batch_destroy",
            "nh_batch_profile_enable", "nh_batch_profile_read", "nh_tape_bytes",
            "nh_step_taped", "nh_adjoint_step", "nh_cheb_forms", "nh_set_relax_target",
-           "nh_debug_stall_copies")
+           "nh_debug_stall_copies", "nh_gauges")
 
 BATCH_AUTOTUNE, BATCH_GRAPH = 1, 2
 
@@ -110,6 +110,7 @@ def load():
     L.nh_debug_hyperbolic.argtypes = [H, C.c_double, vp, vp, vp, C.c_int]
     L.nh_debug_system.argtypes = [H, C.c_double, vp, vp, vp, C.c_int]
     L.nh_debug_stall_copies.argtypes = [H, C.c_int]
+    L.nh_gauges.argtypes = [H, vp, C.c_int, vp]
     L.nh_set_relax_target.argtypes = [H, vp, vp, vp, vp, vp, C.c_int]
     L.nh_create_batch.argtypes = [C.c_int, C.POINTER(Grid), C.POINTER(C.c_void_p),
                                   C.POINTER(Params), vp, C.c_int, C.POINTER(H)]
@@ -267,6 +268,15 @@ class Sim:
         where = wheres.pop() if wheres else HOST
         self._check(load().nh_get_state(self._h, *[a[0] for a in args], None, where))
         self._keep.clear()
+
+    def gauges(self, cells, out):
+        """nh_gauges: eta at `cells` (torch CUDA int32 tensor of row-major cell indices)
+        into `out` (torch CUDA tensor of the handle's precision), on the handle's stream."""
+        assert cells.is_cuda and out.is_cuda and cells.dtype.itemsize == 4
+        assert out.element_size() == np.dtype(self.dtype).itemsize
+        assert cells.is_contiguous() and out.is_contiguous() and out.numel() >= cells.numel()
+        self._check(load().nh_gauges(self._h, C.c_void_p(cells.data_ptr()), int(cells.numel()),
+                                     C.c_void_p(out.data_ptr())))
 
     def step(self, dt=0.0):
         d = C.c_double()

@@ -107,13 +107,15 @@ def J_fp64(wl, HH, ee, dt, nsteps, gauges, target):
         return float(misfit(s, torch.tensor(target)))
 
 
-def test_bathymetry_gradient_against_central_differences():
+@pytest.mark.parametrize("nsteps,bar", [(20, 1e-5), (40, 5e-5)])
+def test_bathymetry_gradient_against_central_differences(nsteps, bar):
     """The adjoint workload's recipe at 96^2 (walls, Gaussian-sum depth 0.3 .. 0.8 m, hump,
-    fixed dt), 40 steps, 16 gauges: <dJ/dH, d> of the exact FP64 adjoint against central
-    differences of the GPU FP64 forward along two smooth directions.  The differences
-    themselves scatter by ~2e-5 between eps = 1e-5 and 1e-6 here (minmod branch switches
-    and the iterative solves' tolerance), which sets the bar."""
-    nsteps = 40
+    fixed dt), 16 gauges: <dJ/dH, d> of the exact FP64 adjoint against central differences
+    of the GPU FP64 forward along two smooth directions.  The differences must take
+    eps <= 1e-6: with larger eps the minmod branches switch inside +-eps and the
+    differences scatter (measured at 10 steps: 1e-4 at eps 1e-4, 5e-5 at 1e-5, 6e-9 at
+    1e-6).  At eps 1e-6 the adjoint meets 1e-5 over 20 steps (2e-9 and below); over 40
+    steps the two directions agree to 1.5e-6 and 2.0e-5."""
     wl, gauges, dt, target = adjoint_workload(96, nsteps, 1.0)
     z = np.zeros_like(wl.H)
     J, gH, ge, _, _ = gpu_grad(wl.H, wl.eta, z, z, wl.dx, dt, nsteps, gauges, target,
@@ -125,7 +127,7 @@ def test_bathymetry_gradient_against_central_differences():
         d = np.sin((k + 2) * 3.1 * x + rng.uniform(0, 6)) * np.cos((k + 1) * 2.3 * y + rng.uniform(0, 6))
         fd = (J_fp64(wl, wl.H + eps * d, wl.eta, dt, nsteps, gauges, target) -
               J_fp64(wl, wl.H - eps * d, wl.eta, dt, nsteps, gauges, target)) / (2 * eps)
-        assert abs(float((gH * d).sum()) - fd) <= 5e-5 * abs(fd)
+        assert abs(float((gH * d).sum()) - fd) <= bar * abs(fd), (k, float((gH * d).sum()), fd)
 
 
 def test_exact_adjoint_grows_and_frozen_limiter_adjoint_stays_bounded():
