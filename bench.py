@@ -624,6 +624,9 @@ def main():
     ap.add_argument("--solver", type=int, default=None, help="0 BiCGStab, 1 Chebyshev")
     ap.add_argument("--cheb-form", type=int, default=None,
                     help="kernel form of the Chebyshev pass (default: chosen by timing)")
+    ap.add_argument("--capture", type=int, default=1, choices=[0, 1],
+                    help="1: steps as CUDA graphs (default); 0: eager launches (the same "
+                         "kernels and bits; for profilers that cannot see graph kernel nodes)")
     ap.add_argument("--w-equation", default="yamazaki", choices=["yamazaki", "transport"],
                     help="h w_t = p (default) or the energy-consistent (hw)_t + div(hw u) = p")
     args = ap.parse_args()
@@ -653,6 +656,7 @@ def main():
         prm["solver"] = args.solver
     if args.cheb_form is not None:
         prm["cheb_form"] = args.cheb_form
+    prm["capture"] = args.capture
     if args.w_equation == "transport":
         prm["w_equation"] = nh.W_TRANSPORT
         desc = desc + ", w equation (hw)_t + div(hw u) = p"
