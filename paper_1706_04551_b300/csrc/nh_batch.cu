@@ -231,7 +231,7 @@ kb_cheb(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const T* c
         R.cC = cC + n; R.cW = cW + n; R.cE = cE + n; R.cS = cS + n; R.cN = cN + n;
         R.nx = D.P.nx; R.ny = D.P.ny;
         const int tx = cdiv(R.nx + 1, TX), nt = tx * cdiv(R.ny + 1, TY);
-        double rsum;
+        NormAcc<T> rsum;
         T dmax;
         if constexpr (PAD)
             cheb_tile_pad<T, NA, NB, BY, K>(R, rhs + n, xi + n, xpi + n, xo + n, xpo + n, ctl,
@@ -242,8 +242,8 @@ kb_cheb(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const T* c
                                               it.y % tx, it.y / tx,
                                               reinterpret_cast<T*>(kb_cheb_smem), rsum, dmax);
         double acc[2];
-        if (dom_reduce_sum_max(rsum, (double)dmax, A.partials + D.poff, &ctl->counter, acc,
-                               it.y, nt) &&
+        if (dom_reduce_sum_max<T>(rsum, (double)dmax, ctl->rinv2, A.partials + D.poff,
+                                  &ctl->counter, acc, it.y, nt) &&
             threadIdx.x == 0 && threadIdx.y == 0)
             kb_cheb_finish(A, it.x, ctl, acc, K, stage);
         __syncthreads();
@@ -362,18 +362,20 @@ kb_cheb_reg(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const 
                 stage_item(wn);
             }
         };
-        double rsum = 0.0;
+        NormAcc<T> rsum;
+        norm_zero(rsum);
         T dmax = T(0);
         const T rsc = sizeof(T) == 4 ? (T)ctl->rscf : (T)ctl->rscd;
         const double rinv2 = ctl->rinv2;
         if constexpr (sizeof(T) == 4 && C == 2)
-            cheb_region_reg2<R, NW, K>(Rw, planes, exch, c1s, c2s, rsc, rinv2, I0, J0, xo + n,
+            cheb_region_reg2<R, NW, K>(Rw, planes, exch, c1s, c2s, rsc, I0, J0, xo + n,
                                        xpo + n, rsum, dmax, next);
         else
-            cheb_region_reg<T, C, R, NW, K>(Rw, planes, exch, c1s, c2s, rsc, rinv2, I0, J0,
+            cheb_region_reg<T, C, R, NW, K>(Rw, planes, exch, c1s, c2s, rsc, I0, J0,
                                             xo + n, xpo + n, rsum, dmax, next);
-        double bsm[2] = {rsum, (double)dmax};
-        block_reduce<2, 2u>(bsm);   // FP64 (sum, max) into thread 0
+        double bsm[2];
+        block_sum_max_scaled<T>(rsum, (double)dmax, bsm[0], bsm[1]);   // into thread 0
+        bsm[0] *= rinv2;
         if (it.x != gd) {
             flush();
             gd = it.x;

@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace nh {
 namespace dev {
 
@@ -250,18 +252,110 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[NV], double* partials,
                                    gridDim.x * gridDim.y);
 }
 
-// Sum and max of a pass's per-thread (squared residual sum, largest change) over the
-// grid, in FP64 at every level (per thread, warp, block and the last block's finish), so
-// that the stopping test of the pressure solve sees the residual norm in FP64 in both
-// precisions.  Same contract as dom_reduce; out (thread 0 of the last block) = totals.
-__device__ __forceinline__ bool dom_reduce_sum_max(double s, double m, double* partials,
-                                                   unsigned* counter, double out[2],
-                                                   unsigned bid, unsigned nblocks)
+// Sum (and max) of a pass's per-thread scaled squared-residual sums over the block, thread
+// 0 receiving the totals.  FP32 passes: every sum -- a thread's over its regions, a warp's,
+// the block's over its warps -- is a double-single pair (float hi + lo kept exact by Knuth's
+// TwoSum, about 44 significant bits), converted to FP64 once per block: FP64-class sums
+// without FP64 additions, which B300 runs at 1/64 of its FP32 rate.  The thread values are scaled by rsc^2 (an exact power
+// of two, see SolveCtl), so they lie far inside the FP32 range.  FP64 passes add in FP64.
+// The max is exact in either precision.
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x)
 {
-    double v[2] = {s, m};
-    if (!dom_reduce<2, 2u>(v, partials, counter, bid, nblocks)) return false;
-    out[0] = v[0];
-    out[1] = v[1];
+    const float s = hi + x;
+    const float bp = s - hi;
+    const float e = (hi - (s - bp)) + (x - bp);
+    hi = s;
+    lo += e;
+}
+
+// Per-thread accumulator of the scaled squares: a double-single pair in FP32 passes, a
+// double in FP64 passes.
+struct SumDS {
+    float hi, lo;
+};
+template <typename T>
+using NormAcc = typename std::conditional<sizeof(T) == 4, SumDS, double>::type;
+__device__ __forceinline__ void norm_zero(SumDS& a) { a.hi = 0.f; a.lo = 0.f; }
+__device__ __forceinline__ void norm_zero(double& a) { a = 0.0; }
+__device__ __forceinline__ void norm_add(SumDS& a, float x) { two_sum_add(a.hi, a.lo, x); }
+__device__ __forceinline__ void norm_add(double& a, double x) { a += x; }
+
+// one level of a double-single shuffle tree
+__device__ __forceinline__ void ds_shfl_add(float& hi, float& lo, int o)
+{
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    two_sum_add(hi, lo, h2);
+    lo += l2;
+}
+
+template <typename T>
+__device__ __forceinline__ void block_sum_max_scaled(NormAcc<T> s, double m, double& out_s,
+                                                     double& out_m)
+{
+    if constexpr (sizeof(T) == 8) {
+        double v[2] = {s, m};
+        block_reduce<2, 2u>(v);
+        out_s = v[0];
+        out_m = v[1];
+    } else {
+        __shared__ float wh[32], wl[32], wm[32];
+        const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+        const int lane = tid & 31, wid = tid >> 5, nw = (blockDim.x * blockDim.y + 31) >> 5;
+        float hi = s.hi, lo = s.lo, mx = (float)m;
+        for (int o = 16; o > 0; o >>= 1) {
+            ds_shfl_add(hi, lo, o);
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        }
+        if (lane == 0) { wh[wid] = hi; wl[wid] = lo; wm[wid] = mx; }
+        __syncthreads();
+        if (wid == 0) {
+            hi = lane < nw ? wh[lane] : 0.f;
+            lo = lane < nw ? wl[lane] : 0.f;
+            mx = lane < nw ? wm[lane] : 0.f;
+            for (int o = 16; o > 0; o >>= 1) {
+                ds_shfl_add(hi, lo, o);
+                mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            }
+            out_s = (double)hi + (double)lo;
+            out_m = (double)mx;
+        }
+        __syncthreads();
+    }
+}
+
+// The pass's grid reduction: block totals of (scaled sum, max) by block_sum_max_scaled, the
+// sum times `scale` (1 / rsc^2) written as this block's FP64 partial, and the last block
+// (fixed order over the partials) receives the totals in out (thread 0).
+template <typename T>
+__device__ __forceinline__ bool dom_reduce_sum_max(NormAcc<T> s, double m, double scale,
+                                                   double* partials, unsigned* counter,
+                                                   double out[2], unsigned bid,
+                                                   unsigned nblocks)
+{
+    double bs = 0.0, bm = 0.0;
+    block_sum_max_scaled<T>(s, m, bs, bm);
+    const unsigned tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const unsigned nthr = blockDim.x * blockDim.y;
+    __shared__ bool last;
+    if (tid == 0) {
+        partials[(size_t)bid * 2] = bs * scale;
+        partials[(size_t)bid * 2 + 1] = bm;
+        __threadfence();
+        last = atomicAdd(counter, 1u) == nblocks - 1;
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double acc[2] = {0.0, 0.0};
+    for (unsigned bb = tid; bb < nblocks; bb += nthr) {
+        acc[0] += __ldcg(partials + (size_t)bb * 2);
+        acc[1] = fmax(acc[1], __ldcg(partials + (size_t)bb * 2 + 1));
+    }
+    block_reduce<2, 2u>(acc);
+    out[0] = acc[0];
+    out[1] = acc[1];
+    if (tid == 0) *counter = 0u;
     return true;
 }
 
@@ -789,7 +883,7 @@ template <typename T, int NA, int NB, int BY, int K, bool REGW>
 __device__ __forceinline__ void
 cheb_tile(const Rows<T>& R, const T* __restrict__ b, const T* __restrict__ xi,
           const T* __restrict__ xpi, T* __restrict__ xo, T* __restrict__ xpo,
-          const SolveCtl* ctl, int bx, int by, T* smem, double& rsum, T& dmax)
+          const SolveCtl* ctl, int bx, int by, T* smem, NormAcc<T>& rsum, T& dmax)
 {
     constexpr int RW = 32 * NA, RH = BY * NB, RN = RW * RH, NN = NA * NB;
     constexpr int TX = RW - 2 * K, TY = RH - 2 * K;
@@ -889,7 +983,8 @@ cheb_tile(const Rows<T>& R, const T* __restrict__ b, const T* __restrict__ xi,
         __syncthreads();
         T* tmp = cur; cur = nxt; nxt = tmp;
     }
-    rsum = (double)part * ctl->rinv2;
+    norm_zero(rsum);
+    norm_add(rsum, part);   // scaled; the block applies 1 / rsc^2
 #pragma unroll
     for (int bb = 0; bb < NB; ++bb)
 #pragma unroll
@@ -941,7 +1036,7 @@ template <typename T, int NA, int NB, int BY, int K>
 __device__ __forceinline__ void
 cheb_tile_pad(const Rows<T>& R, const T* __restrict__ b, const T* __restrict__ xi,
               const T* __restrict__ xpi, T* __restrict__ xo, T* __restrict__ xpo,
-              const SolveCtl* ctl, int bx, int by, T* smem, double& rsum, T& dmax)
+              const SolveCtl* ctl, int bx, int by, T* smem, NormAcc<T>& rsum, T& dmax)
 {
     constexpr int RW = 32 * NA, RH = BY * NB, NN = NA * NB;
     constexpr int PW = RW + 2, PN = PW * (RH + 2);
@@ -1023,7 +1118,8 @@ cheb_tile_pad(const Rows<T>& R, const T* __restrict__ b, const T* __restrict__ x
         __syncthreads();
         T* tmp = cur; cur = nxt; nxt = tmp;
     }
-    rsum = (double)part * ctl->rinv2;
+    norm_zero(rsum);
+    norm_add(rsum, part);   // scaled; the block applies 1 / rsc^2
 #pragma unroll
     for (int bb = 0; bb < NB; ++bb)
 #pragma unroll
@@ -1233,9 +1329,9 @@ __device__ __forceinline__ void cheb_stage_region(const T* const* bases, int nx,
 // largest change over the interior nodes to rsum / dmax.  c1s / c2s: the K sweep weights.
 template <typename T, int C, int R, int NW, int K, typename F>
 __device__ __forceinline__ void cheb_region_reg(const Rows<T>& Rw, const T* planes, T* exch,
-                                                const T* c1s, const T* c2s, T rsc, double rinv2,
+                                                const T* c1s, const T* c2s, T rsc,
                                                 int I0, int J0, T* __restrict__ xo,
-                                                T* __restrict__ xpo, double& rsum, T& dmax,
+                                                T* __restrict__ xpo, NormAcc<T>& rsum, T& dmax,
                                                 F stage_next)
 {
     constexpr int RW = 32 * C, RH = R * NW;
@@ -1325,7 +1421,7 @@ __device__ __forceinline__ void cheb_region_reg(const Rows<T>& Rw, const T* plan
         sweep(x, xa, sw);
         sweep(xa, x, sw + 1);
     }
-    rsum = fma((double)part, rinv2, rsum);
+    norm_add(rsum, part);   // scaled; the block applies 1 / rsc^2
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int lj = R * w + r, gJ = J0 + lj;
@@ -1348,9 +1444,9 @@ __device__ __forceinline__ void cheb_region_reg(const Rows<T>& Rw, const T* plan
 template <int R, int NW, int K, typename F>
 __device__ __forceinline__ void cheb_region_reg2(const Rows<float>& Rw, const float* planes,
                                                  float* exch, const float* c1s,
-                                                 const float* c2s, float rsc, double rinv2,
+                                                 const float* c2s, float rsc,
                                                  int I0, int J0, float* __restrict__ xo,
-                                                 float* __restrict__ xpo, double& rsum,
+                                                 float* __restrict__ xpo, SumDS& rsum,
                                                  float& dmax, F stage_next)
 {
     constexpr int RW = 64, RH = R * NW;
@@ -1440,7 +1536,7 @@ __device__ __forceinline__ void cheb_region_reg2(const Rows<float>& Rw, const fl
         sweep(x, xa, sw);
         sweep(xa, x, sw + 1);
     }
-    rsum = fma((double)part, rinv2, rsum);
+    norm_add(rsum, part);   // scaled; the block applies 1 / rsc^2
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int lj = R * w + r, gJ = J0 + lj;

@@ -51,8 +51,9 @@ struct SolveCtl {
     int fb;           // 1 while the domain's BiCGStab fallback runs
     // residual norm of the passes: each thread sums the squares of its nodes' scaled
     // residuals r * rsc (rsc = 2^-e with 2^e <= ||D^-1 b|| < 2^(e+1), an exact scaling that
-    // keeps every square in range), and adds that partial times rinv2 = 2^(2e) to its FP64
-    // accumulator; everything above the thread is summed in FP64
+    // keeps every square in range) into an FP64 accumulator; a block adds its threads'
+    // sums in double-single (warps) and FP64 (across warps) arithmetic and multiplies by
+    // rinv2 = 2^(2e) before its FP64 partial joins the grid sum
     double rscd;      // rsc (FP64 passes)
     double rinv2;     // 1 / rsc^2
     float rscf;       // rsc (FP32 passes)

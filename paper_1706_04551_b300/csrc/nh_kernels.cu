@@ -324,7 +324,7 @@ k_cheb_pass2(Rows<T> R, const T* __restrict__ b, const T* __restrict__ xi,
 {
     if (ctl->done) return;
     extern __shared__ unsigned char cheb2_smem[];
-    double rsum;
+    NormAcc<T> rsum;
     T dmax;
     if constexpr (PAD)
         cheb_tile_pad<T, NA, NB, BY, K>(R, b, xi, xpi, xo, xpo, ctl, blockIdx.x, blockIdx.y,
@@ -333,8 +333,8 @@ k_cheb_pass2(Rows<T> R, const T* __restrict__ b, const T* __restrict__ xi,
         cheb_tile<T, NA, NB, BY, K, REGW>(R, b, xi, xpi, xo, xpo, ctl, blockIdx.x, blockIdx.y,
                                           reinterpret_cast<T*>(cheb2_smem), rsum, dmax);
     double acc[2];
-    if (dom_reduce_sum_max(rsum, (double)dmax, partials, &ctl->counter, acc,
-                           blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y) &&
+    if (dom_reduce_sum_max<T>(rsum, (double)dmax, ctl->rinv2, partials, &ctl->counter, acc,
+                              blockIdx.y * gridDim.x + blockIdx.x, gridDim.x * gridDim.y) &&
         threadIdx.x == 0 && threadIdx.y == 0)
         cheb_finish_stall(ctl, acc, K);
 }
@@ -384,7 +384,8 @@ k_cheb_reg(Rows<T> Rw, const T* __restrict__ b, const T* __restrict__ xi,
     __syncthreads();
     if (g < nreg && !stall)
         cheb_stage_region<T, RW, RH, 32 * NW>(bases, nx, ny, I0of(g), J0of(g), planes, &bar);
-    double rsum = 0.0;
+    NormAcc<T> rsum;
+    norm_zero(rsum);
     T dmax = T(0);
     unsigned phase = 0;
     bool ok = true;
@@ -406,10 +407,10 @@ k_cheb_reg(Rows<T> Rw, const T* __restrict__ b, const T* __restrict__ xi,
             }
         };
         if constexpr (sizeof(T) == 4 && C == 2)
-            cheb_region_reg2<R, NW, K>(Rw, planes, exch, c1s, c2s, rsc, rinv2, I0of(g),
+            cheb_region_reg2<R, NW, K>(Rw, planes, exch, c1s, c2s, rsc, I0of(g),
                                        J0of(g), xo, xpo, rsum, dmax, next);
         else
-            cheb_region_reg<T, C, R, NW, K>(Rw, planes, exch, c1s, c2s, rsc, rinv2, I0of(g),
+            cheb_region_reg<T, C, R, NW, K>(Rw, planes, exch, c1s, c2s, rsc, I0of(g),
                                             J0of(g), xo, xpo, rsum, dmax, next);
     }
     if (!ok) {
@@ -418,8 +419,8 @@ k_cheb_reg(Rows<T> Rw, const T* __restrict__ b, const T* __restrict__ xi,
         if (tid == 0) { ctl->status = drained ? 6 : 7; ctl->done = 1; }
     }
     double acc[2];
-    if (dom_reduce_sum_max(rsum, (double)dmax, partials, &ctl->counter, acc, blockIdx.x,
-                           gridDim.x) &&
+    if (dom_reduce_sum_max<T>(rsum, (double)dmax, rinv2, partials, &ctl->counter, acc,
+                              blockIdx.x, gridDim.x) &&
         threadIdx.x == 0 && ok)
         cheb_finish_stall(ctl, acc, K);
 }
