@@ -135,6 +135,13 @@ typedef struct {
                            the solver loops as conditional WHILE nodes on the device, the
                            host waiting once per step; 0: every kernel launched eagerly and
                            the solve polled from the host.  Results are the same bits.    */
+    int refine_fp32;    /* FP64 2D Chebyshev handles (residual test, eps_dp = 0): 1 = solve
+                           each pressure system by defect correction, FP32 inner solves of
+                           M d = r (r = b - M x in FP64, scaled by an exact power of two) to
+                           a relative 1e-4 by the same scheduled relaxation, x += d in
+                           FP64, until the FP64 scaled residual meets tol; the sweeps run
+                           at the FP32 rate.  0 (default): FP64 sweeps.  Such handles step
+                           eagerly (capture does not apply).                              */
 } nh_params;
 
 typedef struct {

@@ -142,6 +142,7 @@ struct Impl : Base {
     {
         for (void* p : allocs) cudaFree(p);
         if (h_sctl) cudaFreeHost(h_sctl);
+        if (h_sctl32) cudaFreeHost(h_sctl32);
         if (h_stctl) cudaFreeHost(h_stctl);
         for (cudaEvent_t e : vt_ev)
             if (e) cudaEventDestroy(e);
@@ -237,6 +238,18 @@ struct Impl : Base {
             A(B.rz_eta, nc); A(B.rz_q1, nc); A(B.rz_w, nn); A(B.rz_p, nn);
             if (dim == 2) A(B.rz_q2, nc);
         }
+        if (sizeof(T) == 8 && dim == 2 && q.nonhydrostatic &&
+            q.solver == NH_SOLVER_CHEBYSHEV && q.refine_fp32 && !(q.eps_dp > 0.0)) {
+            // FP32 copies of the rows and the inner solve's vectors
+            float** f32[] = {&B32.cC, &B32.cW, &B32.cE, &B32.cS, &B32.cN, &B32.rhs, &B32.dp,
+                             &B32.r, &B32.v[0], &B32.v[1]};
+            for (float** f : f32) A(*f, nn);
+            A(B32.sctl, 1);
+            P32.nx = P.nx; P32.ny = P.ny;
+            P32.bcw = P.bcw; P32.bce = P.bce; P32.bcs = P.bcs; P32.bcn = P.bcn;
+            P32.dx = (float)P.dx; P32.dy = (float)P.dy;
+            refine = true;
+        }
         if (q.w_equation == NH_W_TRANSPORT) {
             // face mass fluxes: x faces [ny][nx+1] (1D: [rows][nx+1]), y faces [ny+1][nx]
             A(B.fmx, (size_t)(g.nx + 1) * g.ny);
@@ -249,6 +262,11 @@ struct Impl : Base {
         for (cudaEvent_t& ev : vt_ev)
             if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(hd, e, "cudaEventCreate");
         if ((e = cudaMallocHost(&h_stctl, sizeof(StepCtl))) != cudaSuccess) return cuda_fail(hd, e, "cudaMallocHost");
+        if (refine) {
+            if ((e = cudaMallocHost(&h_sctl32, sizeof(SolveCtl))) != cudaSuccess)
+                return cuda_fail(hd, e, "cudaMallocHost");
+            cudaMemsetAsync(B32.sctl, 0, sizeof(SolveCtl), h->s);
+        }
         cudaMemsetAsync(B.sctl, 0, sizeof(SolveCtl), h->s);
         cudaMemsetAsync(B.stctl, 0, sizeof(StepCtl), h->s);
         h_sctl->eps_dp = q.eps_dp;
@@ -602,7 +620,9 @@ struct Impl : Base {
                             B.partials, B.sctl, 1);
         });
         int rc = NH_OK;
-        if (q.nonhydrostatic) rc = q.solver == NH_SOLVER_CHEBYSHEV ? solve_cheb(s) : solve2d(s, false);
+        if (q.nonhydrostatic)
+            rc = q.solver == NH_SOLVER_CHEBYSHEV ? (refine ? solve_refine(s) : solve_cheb(s))
+                                                 : solve2d(s, false);
         K_(NH_K_CORRECTION, [&] {
             launch_corr2d<T>(P, Ln, B, B.q1k, B.q2k, de, q.nonhydrostatic ? 1 : 0, eo, ao, bo,
                              wo, s == 1 ? 1 : 0, B.partials, B.stctl);
@@ -646,6 +666,7 @@ struct Impl : Base {
         // (after one eager step: the kernels' one-time attribute and occupancy set-up runs
         // outside the capture)
         return q.capture && dim == 2 && !g_failed && stall_block < 0 && eager_steps > 0 &&
+               !refine &&
                (!q.nonhydrostatic || (q.solver == NH_SOLVER_CHEBYSHEV && pass_variant >= 0));
     }
 
@@ -878,7 +899,8 @@ struct Impl : Base {
             if (prof.used + g_evnodes.size() > 16384) prof.flush();
             for (cudaGraphNode_t nd : g_evnodes) {
                 cudaEvent_t x = prof.next();
-                cudaGraphExecEventRecordNodeSetEvent(g_exec, nd, x);
+                const cudaError_t es = cudaGraphExecEventRecordNodeSetEvent(g_exec, nd, x);
+                if (es != cudaSuccess) return cuda_fail(hd, es, "profiling event of a step graph");
                 ev.push_back(x);
             }
         }
@@ -1200,6 +1222,107 @@ struct Impl : Base {
     }
     bool accept_stall = false;   // set during the adjoint's transposed solves
 
+    // ---- FP64 solves by defect correction with FP32 inner solves (nh_params.refine_fp32):
+    // round k takes r = b - M x in FP64 (x = 0 at first), scales it by an exact power of two
+    // into FP32, solves M d = r with FP32 rows to a relative 1e-4 by the same
+    // Chebyshev-scheduled passes (the 96x64 register form), and adds d to x in FP64, until
+    // ||D^-1 r|| <= tol ||D^-1 b|| in FP64.  The FP64 rows decide convergence, so the
+    // result meets the FP64 tolerance while the sweeps run at the FP32 rate.
+    Bufs<float> B32{};
+    Prm<float> P32{};
+    SolveCtl* h_sctl32 = nullptr;
+    bool refine = false;
+    int last32 = 0;
+
+    // FP32 passes on (B32.dp, B32.r) <-> (B32.v[0], B32.v[1]) until ctl32 is done; the
+    // iterate ends in B32.v[0] when an odd number of passes did work.
+    int run_inner32(int& sweeps, const float*& d)
+    {
+        const int K = cheb_sweeps_per_pass<float>();
+        const unsigned polls = hd->prm.wait_polls > 0 ? (unsigned)hd->prm.wait_polls
+                                                      : kDefaultWaitPolls;
+        cudaMemsetAsync(B32.r, 0, nn * sizeof(float), hd->s);
+        cudaMemsetAsync(B32.dp, 0, nn * sizeof(float), hd->s);
+        int launched = 0;
+        int batch = last32 > 2 ? last32 - 1 : 4;
+        for (;;) {
+            for (int k = 0; k < batch; ++k) {
+                const bool odd = (launched++ & 1) != 0;
+                float* xa = odd ? B32.v[0] : B32.dp;
+                float* pa = odd ? B32.v[1] : B32.r;
+                float* xb = odd ? B32.dp : B32.v[0];
+                float* pb = odd ? B32.r : B32.v[1];
+                int rc = 0;
+                K_(NH_K_CHEB_PASS, [&] {
+                    rc = launch_cheb_pass<float>(P32, hd->s, B32, xa, pa, xb, pb, B.partials,
+                                                 7, polls, -1);
+                });
+                if (rc != 0) return fail(hd, NH_ECUDA, "Chebyshev pass launch failed");
+            }
+            cudaMemcpyAsync(h_sctl32, B32.sctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, hd->s);
+            cudaError_t e = cudaStreamSynchronize(hd->s);
+            if (e != cudaSuccess) return cuda_fail(hd, e, "inner pressure solve");
+            if (h_sctl32->done) break;
+            batch = 2;
+        }
+        if (h_sctl32->status == 6 || h_sctl32->status == 7)
+            return fail(hd, NH_ETIMEOUT, "Chebyshev pass: a wait for staged copies ran out "
+                                         "of polls (the solve was abandoned)");
+        sweeps = h_sctl32->sweeps;
+        last32 = sweeps / K;
+        d = ((sweeps / K) & 1) ? B32.v[0] : B32.dp;
+        return NH_OK;
+    }
+
+    int solve_refine(int stage)
+    {
+        if constexpr (sizeof(T) != 8) {
+            return fail(hd, NH_EINVAL, "defect correction applies to FP64 handles");
+        } else {
+            const nh_params& q = hd->prm;
+            const int K32 = cheb_sweeps_per_pass<float>();
+            for (int k = 0; k < 5; ++k) {
+                const T* src[5] = {B.cC, B.cW, B.cE, B.cS, B.cN};
+                float* dst[5] = {B32.cC, B32.cW, B32.cE, B32.cS, B32.cN};
+                launch_convert_from_double<float>(Ln, src[k], dst[k], nn);
+            }
+            cudaMemcpyAsync(h_sctl, B.sctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, hd->s);
+            cudaError_t e = cudaStreamSynchronize(hd->s);
+            if (e != cudaSuccess) return cuda_fail(hd, e, "pressure solve");
+            if (h_sctl->status == 4) return fallback(stage, false);   // not diagonally dominant
+            const double bdb = h_sctl->bdb, tol2 = q.tol * q.tol, tol_in = 1e-4;
+            cudaMemsetAsync(B.dp, 0, nn * sizeof(T), hd->s);
+            int total = 0;
+            bool conv = false;
+            double rr = 0.0;
+            for (int round = 0; round < 16; ++round) {
+                K_(NH_K_SOLVE_INIT, [&] {
+                    launch_refine_resid(P, Ln, B, B.dp, B.r, B.partials, B.sctl, B32.sctl,
+                                        tol_in * tol_in, q.max_iter, K32);
+                });
+                cudaMemcpyAsync(h_sctl, B.sctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, hd->s);
+                if ((e = cudaStreamSynchronize(hd->s)) != cudaSuccess)
+                    return cuda_fail(hd, e, "pressure solve");
+                rr = h_sctl->rr;
+                if (rr <= tol2 * bdb) { conv = true; break; }
+                if (total >= q.max_iter) break;
+                K_(NH_K_SOLVE_INIT, [&] { launch_refine_scale(Ln, B.r, B32.rhs, nn, B.sctl); });
+                int sw = 0;
+                const float* d = nullptr;
+                const int rc = run_inner32(sw, d);
+                if (rc != NH_OK) return rc;
+                total += sw;
+                K_(NH_K_SOLVE_INIT, [&] { launch_refine_add(Ln, B.dp, d, nn, B.sctl); });
+            }
+            hd->solver_iters += total;
+            hd->last_iters[stage] = total;
+            hd->last_resid[stage] = bdb > 0.0 ? std::sqrt(rr / bdb) : 0.0;
+            if (conv) return NH_OK;
+            // not there within the rounds or the cap: BiCGStab goes on from x in FP64
+            return fallback(stage, true);
+        }
+    }
+
     int debug_hyp(double dtd, void* e, void* a, void* b, int where) override
     {
         if (dim == 2)
@@ -1318,6 +1441,7 @@ int nh_default_params(nh_params* p)
     p->dry_zero = 1;
     p->wait_polls = 0;
     p->capture = 1;
+    p->refine_fp32 = 0;
     return NH_OK;
 }
 

@@ -58,6 +58,8 @@ struct SolveCtl {
     double rinv2;     // 1 / rsc^2
     float rscf;       // rsc (FP32 passes)
     int pad3;
+    double rfs;       // defect correction with FP32 inner solves: the power of two that
+                      // scales the FP64 residual into the inner right-hand side
 };
 
 // Statistics of one stage's pressure solve in a captured step, read by the host after it.
@@ -172,6 +174,21 @@ void launch_corr2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* 
                    const T* dp_alt = nullptr);
 // dp_alt (captured steps): the other buffer of the pass pair; the correction takes the
 // iterate from it when the Chebyshev solve ended on an odd pass without a fallback
+
+// ---- FP64 solves by defect correction with FP32 inner solves (FP64 handles) ----
+// r = b - M x in FP64 into r64, its Jacobi-scaled square norm into ctl64->rr, the scale
+// rfs = 2^-e (2^e ~ the rms of D^-1 r) into ctl64, and the inner solve's control block
+// ctl32 prepared as an assembly would (norms of the scaled residual, the interval of
+// ctl64->gersh, tolerance tol2_in, kpass sweeps per pass)
+void launch_refine_resid(const Prm<double>& P, const Launch& L, const Bufs<double>& B,
+                         const double* x, double* r64, double* partials, SolveCtl* ctl64,
+                         SolveCtl* ctl32, double tol2_in, int max_iter_in, int kpass);
+// r32 = (float)(r64 rfs)
+void launch_refine_scale(const Launch& L, const double* r64, float* r32, size_t n,
+                         const SolveCtl* ctl64);
+// x += (double)d32 / rfs
+void launch_refine_add(const Launch& L, double* x, const float* d32, size_t n,
+                       const SolveCtl* ctl64);
 
 // ---- captured steps: device-side control of the solver loops ----
 // condition of a WHILE node: continue while the solve is not done and *cnt < cap (count =

@@ -946,6 +946,53 @@ k_lambda(Prm<T> P, int dim, const T* __restrict__ eta, const T* __restrict__ q1,
     if (grid_reduce<1, 1u>(acc, partials, &st->counter) && threadIdx.x == 0) st->lam = acc[0];
 }
 
+// ================================================================ FP64 defect correction
+
+__global__ void __launch_bounds__(kThreads)
+k_refine_resid(Rows<double> R, const double* __restrict__ b, const double* __restrict__ x,
+               double* __restrict__ r64, double* partials, SolveCtl* ctl64, SolveCtl* ctl32,
+               double tol2_in, int max_iter_in, int kpass)
+{
+    const int nxn = R.nx + 1;
+    const long long n = (long long)(R.nx + 1) * (R.ny + 1);
+    double acc[1] = {0.0};
+    GRID_STRIDE(idx, n)
+    {
+        const int I = (int)(idx % nxn), J = (int)(idx / nxn);
+        const double r = b[idx] - row_apply(R, I, J, x[idx], [&](size_t m) { return x[m]; });
+        r64[idx] = r;
+        const double rd = r / R.cC[idx];
+        acc[0] = fma(rd, rd, acc[0]);
+    }
+    if (grid_reduce<1, 0u>(acc, partials, &ctl64->counter) && threadIdx.x == 0) {
+        ctl64->rr = acc[0];
+        const double rms = sqrt(acc[0] / (double)n);
+        int e = rms > 0.0 ? ilogb(rms) : 0;
+        e = e < -120 ? -120 : (e > 120 ? 120 : e);
+        const double s = ldexp(1.0, -e);
+        ctl64->rfs = s;
+        const double a3[3] = {0.0, acc[0] * s * s, ctl64->gersh};
+        asm_finish(ctl32, a3, tol2_in, max_iter_in, kpass, 1);
+        ctl32->eps_dp = 0.0;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_refine_scale(const double* __restrict__ r64, float* __restrict__ r32, long long n,
+               const SolveCtl* ctl64)
+{
+    const double s = ctl64->rfs;
+    GRID_STRIDE(idx, n) r32[idx] = (float)(r64[idx] * s);
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_refine_add(double* __restrict__ x, const float* __restrict__ d32, long long n,
+             const SolveCtl* ctl64)
+{
+    const double is = 1.0 / ctl64->rfs;   // a power of two: exact
+    GRID_STRIDE(idx, n) x[idx] += (double)d32[idx] * is;
+}
+
 // ================================================================ captured steps
 
 __global__ void k_loop_cond(cudaGraphConditionalHandle h, const SolveCtl* ctl, unsigned* cnt,
@@ -1357,6 +1404,26 @@ void launch_lambda(const Prm<T>& P, const Launch& L, const T* eta, const T* q1, 
                    const T* H, int dim, double* partials, StepCtl* st)
 {
     k_lambda<T><<<L.nblk, kThreads, 0, L.s>>>(P, dim, eta, q1, q2, H, partials, st);
+}
+
+void launch_refine_resid(const Prm<double>& P, const Launch& L, const Bufs<double>& B,
+                         const double* x, double* r64, double* partials, SolveCtl* ctl64,
+                         SolveCtl* ctl32, double tol2_in, int max_iter_in, int kpass)
+{
+    k_refine_resid<<<L.nblk, kThreads, 0, L.s>>>(rows_of(P, B), B.rhs, x, r64, partials, ctl64,
+                                                 ctl32, tol2_in, max_iter_in, kpass);
+}
+
+void launch_refine_scale(const Launch& L, const double* r64, float* r32, size_t n,
+                         const SolveCtl* ctl64)
+{
+    k_refine_scale<<<L.nblk, kThreads, 0, L.s>>>(r64, r32, (long long)n, ctl64);
+}
+
+void launch_refine_add(const Launch& L, double* x, const float* d32, size_t n,
+                       const SolveCtl* ctl64)
+{
+    k_refine_add<<<L.nblk, kThreads, 0, L.s>>>(x, d32, (long long)n, ctl64);
 }
 
 void launch_loop_cond(cudaStream_t s, cudaGraphConditionalHandle h, const SolveCtl* ctl,

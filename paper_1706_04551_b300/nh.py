@@ -36,7 +36,8 @@ class Params(C.Structure):
                 ("precision", C.c_int), ("fixed_dt", C.c_double), ("eps_dp", C.c_double),
                 ("adjoint_frozen_limiter", C.c_int), ("cheb_form", C.c_int),
                 ("w_equation", C.c_int), ("relax_width", C.c_double * 4),
-                ("dry_zero", C.c_int), ("wait_polls", C.c_int), ("capture", C.c_int)]
+                ("dry_zero", C.c_int), ("wait_polls", C.c_int), ("capture", C.c_int),
+                ("refine_fp32", C.c_int)]
 
 
 class StatsT(C.Structure):
