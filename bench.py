@@ -150,6 +150,11 @@ def workload(name):
         wl = inputs.shoals_2d(n=1024)
         prm = dict(cfl=0.9, tol=1e-12)
         return wl, prm, "fp64", "shoals_2d 1024x1024 dx=0.1 m FP64, walls"
+    if name == "shoals_1024_fp64r":
+        wl = inputs.shoals_2d(n=1024)
+        prm = dict(cfl=0.9, tol=1e-12, refine_fp32=1)
+        return wl, prm, "fp64", ("shoals_2d 1024x1024 dx=0.1 m FP64, walls, pressure solves by "
+                                 "defect correction with FP32 inner sweeps")
     raise SystemExit(f"unknown workload {name}")
 
 
