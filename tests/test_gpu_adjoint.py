@@ -156,3 +156,25 @@ def test_adjoint_rejects_friction():
     wz = torch.zeros((H.shape[0] + 1) * (H.shape[1] + 1), dtype=torch.float64, device="cuda")
     with pytest.raises(nh.NHError):
         sim.adjoint_step(tape, 1e-3, z[0], z[1], z[2], wz, torch.zeros_like(z[0]))
+
+
+def test_adjoint_rejects_the_literal_wet_dry_form():
+    H, eta, q1, q2, dx = small_case()
+    sim = nh.Sim(H, dx, precision="fp64", dry_zero=0)
+    tape = torch.empty(sim.tape_bytes(), dtype=torch.uint8, device="cuda")
+    sim.set_state(eta, q1, q2)
+    with pytest.raises(nh.NHError) as ei:
+        sim.step_taped(tape, 1e-3)
+    assert ei.value.code == nh.EINVAL
+    sim.close()
+
+
+def test_adjoint_of_refined_fp64_steps_equals_plain():
+    """Taped steps whose pressure solves are refined in FP32 (refine_fp32) give the
+    gradient of the plain FP64 steps to the solver tolerance's order."""
+    H, eta, q1, q2, dx, dt, nsteps, gauges, target = setup()
+    a = gpu_grad(H, eta, q1, q2, dx, dt, nsteps, gauges, target)
+    b = gpu_grad(H, eta, q1, q2, dx, dt, nsteps, gauges, target, refine_fp32=1)
+    assert b[0] == pytest.approx(a[0], rel=1e-10)
+    for x, y in zip(a[1:], b[1:]):
+        assert rel(y, x) < 1e-8

@@ -194,3 +194,31 @@ def test_full_ensemble_sampled_against_oracle():
     for d in range(0, 256, 17):
         st = b.stats(d)
         assert st["steps"] == 2 and not st["nonfinite"]
+
+
+def test_batch_literal_wet_dry_form_matches_oracle():
+    """dry_zero = 0 (the second step as Sec. 4.5 states it, no truncation in dry cells) on
+    the batched form, against the oracle in the same mode, over 2 steps.  The device holds
+    eta, so a depth h is known there only to ulp(H) / h relative, and the literal form keeps
+    q in such cells and divides fluxes by h: the two sides agree to 1e-10 only while every
+    wet depth stays above 1e6 ulps of H (1.1e-10 m here).  These members form thinner
+    films within 2 steps (one reaches 2.5e-44 m, below any eta); a step is compared on the
+    domains whose oracle depths all stay above that bound, at least three per step."""
+    wls = small_members()
+    b = make_batch(wls, dry_zero=0)
+    for steps in (1, 2):
+        b.run(1)
+        compared = 0
+        for d, w in enumerate(wls):
+            c = O.cfg(w.nx, w.ny, dx=w.dx, dy=w.dy, bc=w.bc, tol=1e-14, dry_zero=False)
+            zn = np.zeros((w.ny + 1, w.nx + 1))
+            h, q1, q2, _, p, t, _, _ = O.run_2d(c, w.H, np.maximum(w.eta + w.H, 0), w.q1,
+                                                w.q2, zn, zn, max_steps=steps)
+            if h[h > 0].min() < 1e6 * np.spacing(np.abs(w.H).max()):
+                continue
+            g = b.get_state(d)
+            assert rel(g["eta"] + w.H, h) < 1e-10, (steps, d)
+            assert rel_q(g["q1"], g["q2"], q1, q2) < 1e-10, (steps, d)
+            assert rel(g["p"], p) < 1e-10, (steps, d)
+            compared += 1
+        assert compared >= 3, steps
