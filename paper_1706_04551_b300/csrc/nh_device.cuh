@@ -399,10 +399,21 @@ __device__ __forceinline__ bool dom_publish_sum_max(double s, double m, double* 
 
 // ================================================================ 2D bodies
 
+// Faces per run of the hyperbolic tile: the shortest run for which the x-face runs (padded
+// to whole warps) and the y-face runs of a TX x TY tile take one round of NTHR threads.
+__host__ __device__ constexpr int hyp_run_len(int TX, int TY, int NTHR)
+{
+    int r = 1;
+    while (r < TX + 1 &&
+           ((TX + r) / r * TY + 31) / 32 * 32 + (TY + r) / r * TX > NTHR)
+        ++r;
+    return r;
+}
+
 // Face-based form of the hyperbolic update for a TX x TY cell tile: the block stages the
 // tile plus a 2-cell halo (h, eta, u, v) in shared memory, then every face is evaluated
-// once: it reconstructs the two cells next to it (minmod slopes of its side only) and
-// stores, for the left cell, D^- + F_c(U^-) + (0, g h_L eta^-, 0) and, for the right cell,
+// once from the edge states of the two cells next to it (each cell's minmod slopes along
+// the face normal are computed once per run of faces) and stores, for the left cell, D^- + F_c(U^-) + (0, g h_L eta^-, 0) and, for the right cell,
 // D^+ - F_c(U^+) - (0, g h_R eta^+, 0) (normal frame), i.e. the fluctuation plus that
 // cell's half of the inner-cell term of Eq. (22) / (30).  A cell sums its four faces.
 // fmx / fmy (or null): every face's mass flux F_h(U^-) + D^-_h (its left cell's output)
@@ -436,45 +447,68 @@ hyp_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ q1,
     __syncthreads();
     auto L = [&](int i, int j) { return (j + 2) * LW + (i + 2); };   // local cell index
     const T sg = qsqrt(g);
-    // one face: cells cm, cl | cr, cp along the normal (stride s0 in the staged tile);
-    // un, ut: the staged normal and tangential velocities; writes the left cell's and the
-    // right cell's outputs (stride `stride` between the three components)
-    auto face = [&](int cl, int s0, const T* un, const T* ut, T* oL0, T* oR0, int stride) {
-        const int cr = cl + s0, cm = cl - s0, cp = cr + s0;
-        const T uL = un[cl], uR = un[cr], tL = ut[cl], tR = ut[cr];
-        const T sLh = minmod(sh[cl] - sh[cm], sh[cr] - sh[cl]);
-        const T sLu = minmod(uL - un[cm], uR - uL);
-        const T sLt = minmod(tL - ut[cm], tR - tL);
-        const bool dL = (sh[cm] <= hdry) | (sh[cl] <= hdry) | (sh[cr] <= hdry);
-        const T sLe = dL ? T(0) : minmod(se[cl] - se[cm], se[cr] - se[cl]);
-        const T sRh = minmod(sh[cr] - sh[cl], sh[cp] - sh[cr]);
-        const T sRu = minmod(uR - uL, un[cp] - uR);
-        const T sRt = minmod(tR - tL, ut[cp] - tR);
-        const bool dR = (sh[cl] <= hdry) | (sh[cr] <= hdry) | (sh[cp] <= hdry);
-        const T sRe = dR ? T(0) : minmod(se[cr] - se[cl], se[cp] - se[cr]);
-        const T hL = sh[cl] + T(0.5) * sLh, eL = se[cl] + T(0.5) * sLe;
-        const T nL = uL + T(0.5) * sLu, tLv = tL + T(0.5) * sLt;
-        const T hR = sh[cr] - T(0.5) * sRh, eR = se[cr] - T(0.5) * sRe;
-        const T nR = uR - T(0.5) * sRu, tRv = tR - T(0.5) * sRt;
-        T Dm[3], Dp[3];
-        pvm(g, sg, hdry, hL, eL, nL, tLv, hR, eR, nR, tRv, Dm, Dp);
-        const T qL = hL * nL, qR = hR * nR;
-        oL0[0] = Dm[0] + qL;
-        oL0[stride] = Dm[1] + qL * nL + g * sh[cl] * eL;
-        oL0[2 * stride] = Dm[2] + qL * tLv;
-        oR0[0] = Dp[0] - qR;
-        oR0[stride] = Dp[1] - (qR * nR + g * sh[cr] * eR);
-        oR0[2 * stride] = Dp[2] - qR * tRv;
+    // A thread walks a run of up to RUN consecutive faces along their normal (stride s0 in
+    // the staged tile; un, ut: the staged normal and tangential velocities).  Each cell's
+    // minmod slopes and edge states are computed once and carried from one face to the
+    // next.  Face m of the run lies between cells k0 + m s0 and k0 + (m + 1) s0; it writes
+    // its left cell's output to oL + m fs and its right cell's to oR + m fs (stride `stride`
+    // between the three components).
+    struct Cv { T h, e, n, t; };
+    auto ld = [&](int k, const T* un, const T* ut) { return Cv{sh[k], se[k], un[k], ut[k]}; };
+    // minmod slopes of cell b from its neighbours a, c and its low / high edge states
+    auto recon = [&](const Cv& a, const Cv& b, const Cv& c, Cv& lo, Cv& hi) {
+        const T s_h = minmod(b.h - a.h, c.h - b.h);
+        const T s_n = minmod(b.n - a.n, c.n - b.n);
+        const T s_t = minmod(b.t - a.t, c.t - b.t);
+        const bool dry = (a.h <= hdry) | (b.h <= hdry) | (c.h <= hdry);
+        const T s_e = dry ? T(0) : minmod(b.e - a.e, c.e - b.e);
+        lo.h = b.h - T(0.5) * s_h; lo.e = b.e - T(0.5) * s_e;
+        lo.n = b.n - T(0.5) * s_n; lo.t = b.t - T(0.5) * s_t;
+        hi.h = b.h + T(0.5) * s_h; hi.e = b.e + T(0.5) * s_e;
+        hi.n = b.n + T(0.5) * s_n; hi.t = b.t + T(0.5) * s_t;
     };
-    // x faces f = 0..TX between local cells f-1 and f, rows 0..TY-1
-    for (int t = tid; t < NFX; t += nt) {
-        const int f = t % (TX + 1), r = t / (TX + 1);
-        face(L(f - 1, r), 1, su, sv, &CLx[0][t], &CRx[0][t], NFX);
-    }
-    // y faces f = 0..TY between local rows f-1 and f, columns 0..TX-1
-    for (int t = tid; t < NFY; t += nt) {
-        const int f = t % TX, r = t / TX;
-        face(L(f, r - 1), LW, sv, su, &CLy[0][t], &CRy[0][t], NFY);
+    constexpr int RUN = hyp_run_len(TX, TY, kThreads);
+    auto run = [&](int k0, int s0, const T* un, const T* ut, int nf, T* oL, T* oR, int fs,
+                   int stride) {
+        Cv b = ld(k0, un, ut), c = ld(k0 + s0, un, ut), blo, bhi;
+        recon(ld(k0 - s0, un, ut), b, c, blo, bhi);
+#pragma unroll
+        for (int m = 0; m < RUN; ++m) {
+            if (m >= nf) break;
+            const Cv d = ld(k0 + (m + 2) * s0, un, ut);
+            Cv clo, chi;
+            recon(b, c, d, clo, chi);
+            T Dm[3], Dp[3];
+            pvm(g, sg, hdry, bhi.h, bhi.e, bhi.n, bhi.t, clo.h, clo.e, clo.n, clo.t, Dm, Dp);
+            const T qL = bhi.h * bhi.n, qR = clo.h * clo.n;
+            T* o = oL + m * fs;
+            o[0] = Dm[0] + qL;
+            o[stride] = Dm[1] + qL * bhi.n + g * b.h * bhi.e;
+            o[2 * stride] = Dm[2] + qL * bhi.t;
+            o = oR + m * fs;
+            o[0] = Dp[0] - qR;
+            o[stride] = Dp[1] - (qR * clo.n + g * c.h * clo.e);
+            o[2 * stride] = Dp[2] - qR * clo.t;
+            b = c; c = d; bhi = chi;
+        }
+    };
+    // x faces f = 0..TX between local cells f-1 and f of rows 0..TY-1, in runs of RUN faces
+    // (lanes over rows); then y faces f = 0..TY between local rows f-1 and f of columns
+    // 0..TX-1 (lanes over columns); the y runs start on a warp boundary
+    constexpr int NRX = (TX + 1 + RUN - 1) / RUN, NRY = (TY + 1 + RUN - 1) / RUN;
+    constexpr int NTX = NRX * TY, NTX32 = (NTX + 31) / 32 * 32, NT = NTX32 + NRY * TX;
+    for (int t = tid; t < NT; t += nt) {
+        if (t < NTX) {
+            const int r = t % TY, f0 = (t / TY) * RUN;
+            const int nf = TX + 1 - f0 < RUN ? TX + 1 - f0 : RUN;
+            const int e = r * (TX + 1) + f0;
+            run(L(f0 - 1, r), 1, su, sv, nf, &CLx[0][e], &CRx[0][e], 1, NFX);
+        } else if (t >= NTX32) {
+            const int u = t - NTX32, col = u % TX, f0 = (u / TX) * RUN;
+            const int nf = TY + 1 - f0 < RUN ? TY + 1 - f0 : RUN;
+            const int e = f0 * TX + col;
+            run(L(col, f0 - 1), LW, sv, su, nf, &CLy[0][e], &CRy[0][e], TX, NFY);
+        }
     }
     __syncthreads();
     if (fmx != nullptr) {

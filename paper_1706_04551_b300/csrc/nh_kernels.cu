@@ -18,7 +18,7 @@ using namespace dev;
 // ================================================================ 2D kernels
 
 template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 2)
 k_hyp2d_t(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ q1,
           const T* __restrict__ q2, const T* __restrict__ etab, const T* __restrict__ q1b,
           const T* __restrict__ q2b, const T* __restrict__ H, T a, T b, T dt,
