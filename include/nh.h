@@ -142,6 +142,12 @@ typedef struct {
                            FP64, until the FP64 scaled residual meets tol; the sweeps run
                            at the FP32 rate.  0 (default): FP64 sweeps.  Such handles step
                            eagerly (capture does not apply).                              */
+    int fallback_block_nodes; /* batches: a domain of at most this many nodes whose rows
+                           fail the Gershgorin test at assembly runs its whole BiCGStab
+                           solve in one thread block, beside the Chebyshev passes of the
+                           other domains (default 70000); 0: every fallback solve uses the
+                           grid-wide BiCGStab after the passes.  Single-domain handles
+                           ignore it.                                                     */
 } nh_params;
 
 typedef struct {
@@ -250,6 +256,7 @@ enum {
     NH_K_ADJ_CORRECTION,  /* adjoint: correction terms                                   */
     NH_K_W_TRANSPORT,     /* w* of the (hw)_t + div(hw u) = p form (NH_W_TRANSPORT)      */
     NH_K_RELAX,           /* relaxation zones (Sec. 4.4) and the Eq. (23) rate after them */
+    NH_K_BICG_BLOCK,      /* batches: whole BiCGStab solves of small domains, a block each */
     NH_K_COUNT
 };
 

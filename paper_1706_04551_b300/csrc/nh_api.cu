@@ -1442,6 +1442,7 @@ int nh_default_params(nh_params* p)
     p->wait_polls = 0;
     p->capture = 1;
     p->refine_fp32 = 0;
+    p->fallback_block_nodes = 70000;
     return NH_OK;
 }
 

@@ -217,8 +217,12 @@ template <typename T, int NA, int NB, int BY, int K, bool REGW, int MINB, bool P
 __global__ void __launch_bounds__(32 * BY, MINB)
 kb_cheb(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const T* cW,
         const T* cE, const T* cS, const T* cN, const T* rhs, const T* xi, const T* xpi, T* xo,
-        T* xpo, int stage)
+        T* xpo, int stage, const int* plan, int want)
 {
+    if (plan) {   // a planned pass: run only the branch the plan chose (kb_cheb_plan)
+        if (plan[0] != want) return;
+        if (want == 1) nw = plan[1];
+    }
     extern __shared__ unsigned char kb_cheb_smem[];
     constexpr int TX = 32 * NA - 2 * K, TY = BY * NB - 2 * K;
     for (int w = blockIdx.x; w < nw; w += gridDim.x) {
@@ -250,21 +254,29 @@ kb_cheb(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const T* c
     }
 }
 
-// Register form of the batched pass: persistent blocks walk the work list (items of
-// domains that have converged are skipped: a domain's done flag cannot change while one of
-// its items of this pass is unprocessed), each prefetching its next item's region (bulk
-// copies on an mbarrier, element copies at the domain's west and east edges) while it
-// sweeps the current one; every item ends in its domain's reduction as in kb_cheb.  A wait
-// that runs out of `polls` polls ends the block's walk: the block issues no further copies,
-// waits (bounded) for those of the item it was waiting on (cheb_drain) and marks the item's
-// domain failed (status 6, or 7 if the drain ran out too; counted as a non-converged
-// solve).
+// Register form of the batched pass: each persistent block takes a contiguous, balanced
+// share [lo, hi) of the work list, in which a domain's items are contiguous, so a share
+// covers parts of a few domains.  The block walks its share, skipping whole domains that
+// have converged, and prefetches its next item's region (bulk copies on an mbarrier,
+// element copies at the domain's west and east edges) while it sweeps the current one.  A
+// domain's geometry and solver weights are read when the walk enters it (the next region
+// of the same domain follows by arithmetic), and the residual sums of the block's
+// consecutive items of one domain accumulate in registers and are published once for the
+// group (dom_publish_sum_max: the group's first slot holds the sum, its other slots zero).
+// A wait that runs out of `polls` polls ends the block's walk: the block issues no further
+// copies, waits (bounded) for those of the item it was waiting on (cheb_drain) and marks
+// the item's domain failed (status 6, or 7 if the drain ran out too; counted as a
+// non-converged solve).
 template <typename T, int C, int R, int NW, int K>
 __global__ void __launch_bounds__(32 * NW, 1)
 kb_cheb_reg(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const T* cW,
             const T* cE, const T* cS, const T* cN, const T* rhs, const T* xi, const T* xpi,
-            T* xo, T* xpo, int stage)
+            T* xo, T* xpo, int stage, const int* plan, int want)
 {
+    if (plan) {   // a planned pass: run only the branch the plan chose (kb_cheb_plan)
+        if (plan[0] != want) return;
+        if (want == 1) nw = plan[1];
+    }
     const unsigned polls = A.polls;
     constexpr int RW = 32 * C, RH = R * NW, TX = RW - 2 * K, TY = RH - 2 * K;
     using G = RegionGeom<T, RW, RH>;
@@ -275,123 +287,134 @@ kb_cheb_reg(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const 
     __shared__ const T* bases[kPlanes];
     __shared__ __align__(8) unsigned long long bar;
     const int tid = threadIdx.x;
-    auto next_active = [&](int w) {
-        for (; w < nw; w += gridDim.x)
-            if (!A.sctl[wl[w].x].done) return w;
-        return nw;
+    const int lo = (int)((long long)nw * blockIdx.x / gridDim.x);
+    const int hi = (int)((long long)nw * (blockIdx.x + 1) / gridDim.x);
+    // an item of the walk (uniform across the block): work-list index, domain, region and
+    // the domain's node offset and size
+    struct Item { int w, d, y, nx, ny; long long n; };
+    auto ntx_of = [&](const Item& it) { return cdiv(it.nx + 1, TX); };
+    auto nt_of = [&](const Item& it) { return ntx_of(it) * cdiv(it.ny + 1, TY); };
+    // the first item at or after `from` of this share whose domain still solves; `cur` is
+    // the item being processed (a domain still solving), so its successor inside the same
+    // domain needs no load.  False when the share is exhausted.
+    auto advance = [&](const Item& cur, int from, Item& it) -> bool {
+        if (from >= hi) return false;
+        if (cur.w == from - 1 && cur.y + 1 < nt_of(cur)) {
+            it = cur;
+            it.w = from;
+            it.y = cur.y + 1;
+            return true;
+        }
+        for (int w = from; w < hi;) {
+            const int2 e = wl[w];
+            const Dom<T>& D = A.dom[e.x];
+            it.w = w; it.d = e.x; it.y = e.y; it.nx = D.P.nx; it.ny = D.P.ny; it.n = D.noff;
+            if (!A.sctl[e.x].done) return true;
+            w += nt_of(it) - it.y;   // past this domain's items
+        }
+        return false;
     };
-    // region origin of item w (nx, ny of its domain)
-    auto origin = [&](int w, int& I0, int& J0, int& nx, int& ny) {
-        const int2 it = wl[w];
-        const Prm<T>& P = A.dom[it.x].P;
-        nx = P.nx; ny = P.ny;
-        const int ntx = cdiv(nx + 1, TX);
+    auto origin = [&](const Item& it, int& I0, int& J0) {
+        const int ntx = ntx_of(it);
         I0 = (it.y % ntx) * TX - K;
         J0 = (it.y / ntx) * TY - K;
     };
-    auto announce = [&](int w) {   // thread 0: the item's sources and expected bytes
-        const long long n = A.dom[wl[w].x].noff;
+    auto announce = [&](const Item& it) {   // thread 0: the item's sources and expected bytes
+        const long long n = it.n;
         bases[kPlX] = xi + n; bases[kPlXp] = xpi + n; bases[kPlB] = rhs + n; bases[kPlC] = cC + n;
         bases[kPlW] = cW + n; bases[kPlE] = cE + n; bases[kPlS] = cS + n; bases[kPlN] = cN + n;
-        int I0, J0, nx, ny;
-        origin(w, I0, J0, nx, ny);
-        mbar_arrive_expect_tx(&bar, region_bulk_bytes<T, RW, RH>(I0, nx));
+        int I0, J0;
+        origin(it, I0, J0);
+        mbar_arrive_expect_tx(&bar, region_bulk_bytes<T, RW, RH>(I0, it.nx));
     };
-    auto stage_item = [&](int w) {
-        int I0, J0, nx, ny;
-        origin(w, I0, J0, nx, ny);
-        cheb_stage_region<T, RW, RH, 32 * NW>(bases, nx, ny, I0, J0, planes, &bar);
+    auto stage_item = [&](const Item& it) {
+        int I0, J0;
+        origin(it, I0, J0);
+        cheb_stage_region<T, RW, RH, 32 * NW>(bases, it.nx, it.ny, I0, J0, planes, &bar);
     };
-    int w = next_active(blockIdx.x);
+    Item cur{-2, 0, 0, 0, 0, 0}, nxt{-2, 0, 0, 0, 0, 0};
+    bool have = advance(cur, lo, nxt);
     if (tid == 0) {
         mbar_init(&bar, 1);
-        if (w < nw) announce(w);
+        if (have) announce(nxt);
     }
     __syncthreads();
-    if (w < nw) stage_item(w);
+    if (have) stage_item(nxt);
     unsigned phase = 0;
-    // consecutive items of one domain pool their residual sums: one publication (fence and
-    // ticket) per group instead of one per item
-    int gd = -1, gy = 0;
-    unsigned gn = 0;
-    double gs = 0.0, gm = 0.0;   // (thread 0)
+    // the group: this block's consecutive items of domain gd (first item gy, gn items)
+    int gd = -1, gy = 0, gn = 0, gnt = 0;
+    long long gpoff = 0;
+    NormAcc<T> rsum;
+    norm_zero(rsum);
+    T dmax = T(0), rsc = T(0);
+    double rinv2 = 0.0;
     auto flush = [&]() {
         if (gn == 0) return;
-        const Dom<T>& Dg = A.dom[gd];
-        const int ntg = cdiv(Dg.P.nx + 1, TX) * cdiv(Dg.P.ny + 1, TY);
+        double bs = 0.0, bm = 0.0;
+        block_sum_max_scaled<T>(rsum, (double)dmax, bs, bm);   // into thread 0
         double acc[2];
-        if (dom_publish_sum_max(gs, gm, A.partials + Dg.poff, &A.sctl[gd].counter, gy, gn, ntg,
-                                acc) &&
+        if (dom_publish_sum_max(bs * rinv2, bm, A.partials + gpoff, &A.sctl[gd].counter, gy, gn,
+                                gnt, acc) &&
             tid == 0)
             kb_cheb_finish(A, gd, &A.sctl[gd], acc, K, stage);
         gn = 0;
+        norm_zero(rsum);
+        dmax = T(0);
     };
-    while (w < nw) {
+    while (have) {
+        cur = nxt;
         cp_async_wait_all();
         const bool got = mbar_wait_bounded(&bar, phase, polls);
-        const int2 it = wl[w];
-        SolveCtl* ctl = &A.sctl[it.x];
         if (__syncthreads_or(!got)) {
             const bool drained = cheb_drain(&bar, phase, true);
             if (tid == 0) {
-                ctl->status = drained ? 6 : 7;
-                A.ds[it.x].last_status[stage] = ctl->status;
-                atomicAdd(&A.ds[it.x].nonconv, 1);
+                A.sctl[cur.d].status = drained ? 6 : 7;
+                A.ds[cur.d].last_status[stage] = drained ? 6 : 7;
+                atomicAdd(&A.ds[cur.d].nonconv, 1);
             }
             break;
         }
         phase ^= 1u;
-        const Dom<T>& D = A.dom[it.x];
-        const long long n = D.noff;
-        Rows<T> Rw;
-        Rw.cC = cC + n; Rw.cW = cW + n; Rw.cE = cE + n; Rw.cS = cS + n; Rw.cN = cN + n;
-        Rw.nx = D.P.nx; Rw.ny = D.P.ny;
-        if (tid < K) {
-            c1s[tid] = sizeof(T) == 4 ? (T)ctl->c1f[tid] : (T)ctl->c1[tid];
-            c2s[tid] = sizeof(T) == 4 ? (T)ctl->c2f[tid] : (T)ctl->c2[tid];
+        if (cur.d != gd) {   // the walk enters a domain: publish the last one's group
+            flush();
+            gd = cur.d;
+            gy = cur.y;
+            gnt = nt_of(cur);
+            gpoff = A.dom[gd].poff;
+            const SolveCtl* ctl = &A.sctl[gd];
+            if (tid < K) {   // read by the sweeps after the region's first barrier
+                c1s[tid] = sizeof(T) == 4 ? (T)ctl->c1f[tid] : (T)ctl->c1[tid];
+                c2s[tid] = sizeof(T) == 4 ? (T)ctl->c2f[tid] : (T)ctl->c2[tid];
+            }
+            rsc = sizeof(T) == 4 ? (T)ctl->rscf : (T)ctl->rscd;
+            rinv2 = ctl->rinv2;
+        } else if (tid == 0) {   // pooled into the group's slot: this item's slot is zero
+            A.partials[gpoff + 2 * (long long)cur.y] = 0.0;
+            A.partials[gpoff + 2 * (long long)cur.y + 1] = 0.0;
         }
-        const int ntx = cdiv(Rw.nx + 1, TX), nt = ntx * cdiv(Rw.ny + 1, TY);
-        const int I0 = (it.y % ntx) * TX - K, J0 = (it.y / ntx) * TY - K;
-        const int wn = next_active(w + gridDim.x);
+        have = advance(cur, cur.w + 1, nxt);
         auto next = [&](int part) {
-            if (wn >= nw) return;
+            if (!have) return;
             if (part < 0) {   // before the barrier that frees the planes
                 fence_proxy_async_smem();
-                if (tid == 0) announce(wn);
+                if (tid == 0) announce(nxt);
             } else {
-                stage_item(wn);
+                stage_item(nxt);
             }
         };
-        NormAcc<T> rsum;
-        norm_zero(rsum);
-        T dmax = T(0);
-        const T rsc = sizeof(T) == 4 ? (T)ctl->rscf : (T)ctl->rscd;
-        const double rinv2 = ctl->rinv2;
+        Rows<T> Rw;
+        const long long n = cur.n;
+        Rw.cC = cC + n; Rw.cW = cW + n; Rw.cE = cE + n; Rw.cS = cS + n; Rw.cN = cN + n;
+        Rw.nx = cur.nx; Rw.ny = cur.ny;
+        int I0, J0;
+        origin(cur, I0, J0);
         if constexpr (sizeof(T) == 4 && C == 2)
-            cheb_region_reg2<R, NW, K>(Rw, planes, exch, c1s, c2s, rsc, I0, J0, xo + n,
-                                       xpo + n, rsum, dmax, next);
+            cheb_region_reg2<R, NW, K>(Rw, planes, exch, c1s, c2s, rsc, I0, J0, xo + n, xpo + n,
+                                       rsum, dmax, next);
         else
-            cheb_region_reg<T, C, R, NW, K>(Rw, planes, exch, c1s, c2s, rsc, I0, J0,
-                                            xo + n, xpo + n, rsum, dmax, next);
-        double bsm[2];
-        block_sum_max_scaled<T>(rsum, (double)dmax, bsm[0], bsm[1]);   // into thread 0
-        bsm[0] *= rinv2;
-        if (it.x != gd) {
-            flush();
-            gd = it.x;
-            gy = it.y;
-            gs = gm = 0.0;
-        } else if (tid == 0) {   // pooled into the group's slot: this item's slot is zero
-            A.partials[D.poff + 2 * (long long)it.y] = 0.0;
-            A.partials[D.poff + 2 * (long long)it.y + 1] = 0.0;
-        }
-        if (tid == 0) {
-            gs += bsm[0];
-            gm = fmax(gm, bsm[1]);
-        }
+            cheb_region_reg<T, C, R, NW, K>(Rw, planes, exch, c1s, c2s, rsc, I0, J0, xo + n,
+                                            xpo + n, rsum, dmax, next);
         ++gn;
-        (void)nt;
-        w = wn;
     }
     flush();
 }
@@ -423,6 +446,79 @@ __global__ void kb_loop_cond(cudaGraphConditionalHandle h, unsigned* loop, int k
     if (threadIdx.x == 0) {
         const unsigned it = count ? ++loop[k + 1] : loop[k + 1];
         cudaGraphSetConditional(h, (loop[k] > 0u && it < cap) ? 1u : 0u);
+    }
+}
+
+// Plan of one Chebyshev pass of a stage: the regions (TX x TY interior nodes each) of the
+// domains still solving, counted in work-list order by one block.  More than `cap` of them:
+// the pass walks the full work list (mode 0: converged domains' items are skipped there);
+// 1 .. cap: their (domain, region) pairs are compacted into wl_act and a grid of resident
+// blocks walks them (mode 1), so that the passes that only a few slowly converging domains
+// still need do not launch a block per item of every domain; none: mode 2.  plan[0] =
+// mode, plan[1] = length of wl_act.  In a captured step the plan also sets the conditions
+// of the two branches' IF nodes (graph != 0).
+template <typename T>
+__global__ void __launch_bounds__(1024)
+kb_cheb_plan(Arena<T> A, int n, const int* __restrict__ order, int TX, int TY, int cap,
+             int2* __restrict__ wl_act, int* __restrict__ plan, int graph,
+             cudaGraphConditionalHandle hbulk, cudaGraphConditionalHandle htail)
+{
+    __shared__ int wsum[32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nwarp = blockDim.x >> 5;
+    auto items_of = [&](int i) {
+        if (i >= n) return 0;
+        const int d = order[i];
+        if (A.sctl[d].done) return 0;
+        const Prm<T>& P = A.dom[d].P;
+        return cdiv(P.nx + 1, TX) * cdiv(P.ny + 1, TY);
+    };
+    // block-wide exclusive prefix of v (returned) and the block's total (tot)
+    auto scan = [&](int v, int& tot) {
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int t = lane < nwarp ? wsum[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            if (lane < nwarp) wsum[lane] = t;
+        }
+        __syncthreads();
+        const int pre = (wid > 0 ? wsum[wid - 1] : 0) + x - v;
+        tot = wsum[nwarp - 1];
+        __syncthreads();   // wsum is rewritten by the next call
+        return pre;
+    };
+    int total = 0;
+    for (int c0 = 0; c0 < n; c0 += blockDim.x) {
+        int t;
+        scan(items_of(c0 + tid), t);
+        total += t;
+    }
+    const int mode = total > cap ? 0 : (total > 0 ? 1 : 2);
+    if (mode == 1) {
+        int base = 0;
+        for (int c0 = 0; c0 < n; c0 += blockDim.x) {
+            const int v = items_of(c0 + tid);
+            int t;
+            const int pre = scan(v, t);
+            for (int y = 0; y < v; ++y) wl_act[base + pre + y] = make_int2(order[c0 + tid], y);
+            base += t;
+        }
+    }
+    if (tid == 0) {
+        plan[0] = mode;
+        plan[1] = mode == 1 ? total : 0;
+        if (graph) {
+            cudaGraphSetConditional(hbulk, mode == 0 ? 1u : 0u);
+            cudaGraphSetConditional(htail, mode == 1 ? 1u : 0u);
+        }
     }
 }
 
@@ -647,6 +743,234 @@ kb_bicg_C(Arena<T> A, const int2* __restrict__ wl, const int* __restrict__ nwp, 
     }
 }
 
+// The whole fallback solve of a small domain (at most max_nodes nodes) in one block: the
+// initial residual of kb_bicg_init and the iterations of kb_bicg_A / B / C with the same
+// node arithmetic, each phase separated by a block barrier instead of a launch and its dot
+// products summed by the block (FP64).  One block per domain (blockIdx.x = domain); a
+// domain it ends leaves the fallback (bicg_end clears fb), so the chunked kernels and their
+// loop see the other domains only.  In a step it runs on a side stream, concurrently with
+// the Chebyshev passes of the other domains, on one SM per domain.
+template <typename T>
+__global__ void __launch_bounds__(1024, 1)
+kb_bicg_small(Arena<T> A, BiVec<T> V, int stage, long long max_nodes)
+{
+    const int d = blockIdx.x;
+    SolveCtl* ctl = &A.sctl[d];
+    // only the domains the assembly sent to the fallback (status 4: the Chebyshev interval
+    // does not hold); no Chebyshev pass touches them, so this kernel may run beside the
+    // passes of the other domains
+    if (!ctl->fb || ctl->status != 4) return;
+    const Dom<T>& D = A.dom[d];
+    const long long n = D.noff, nn = (long long)(D.P.nx + 1) * (D.P.ny + 1);
+    if (nn > max_nodes) return;
+    const Rows<T> R = rows_at(V, D.P, n);
+    const int nxn = D.P.nx + 1;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    // each thread takes its nodes U at a time: the U nodes' values are computed (their loads
+    // in flight together) before any of them is stored (FP64: 2, within 64 registers)
+    constexpr int U = sizeof(T) == 4 ? 4 : 2;
+    const long long step = (long long)U * nt;
+    __shared__ double res[3];
+    __shared__ int stop;
+    // the block's totals into res (the third a max; every thread after the next barrier)
+    auto total1 = [&](double a0) {
+        double v[1] = {a0};
+        block_reduce<1, 0u>(v);
+        if (tid == 0) res[0] = v[0];
+    };
+    auto total2 = [&](double a0, double a1) {
+        double v[2] = {a0, a1};
+        block_reduce<2, 0u>(v);
+        if (tid == 0) { res[0] = v[0]; res[1] = v[1]; }
+    };
+    auto total3 = [&](double a0, double a1, double a2) {
+        double v[3] = {a0, a1, a2};
+        block_reduce<3, 4u>(v);
+        if (tid == 0) { res[0] = v[0]; res[1] = v[1]; res[2] = v[2]; }
+    };
+    T* x = V.x + n;
+    const T* b = V.b + n;
+    T* r = V.r + n;
+    T* rh = V.rh + n;
+    T* t = V.t + n;
+    {
+        const bool zero_rhs = ctl->bb == 0.0;
+        double a0 = 0.0;
+        for (long long k0 = tid; k0 < nn; k0 += step) {
+            T rv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const long long k = k0 + (long long)u * nt;
+                rv[u] = T(0);
+                if (k < nn && !zero_rhs) {
+                    const int I = (int)(k % nxn), J = (int)(k / nxn);
+                    rv[u] = b[k] - row_apply(R, I, J, x[k], [&](size_t m) { return x[m]; });
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const long long k = k0 + (long long)u * nt;
+                if (k >= nn) continue;
+                if (zero_rhs) x[k] = T(0);
+                r[k] = rv[u]; rh[k] = rv[u]; V.ph[0][n + k] = T(0); V.v[0][n + k] = T(0);
+                a0 += (double)rv[u] * (double)rv[u];
+            }
+        }
+        total1(a0);
+        __syncthreads();
+        if (tid == 0) {
+            ctl->rho1 = res[0];
+            ctl->rr = res[0];
+            ctl->rho = 1.0; ctl->alpha = 1.0; ctl->omega = 1.0;
+            ctl->iter = 0;
+            // (done stays 1: the Chebyshev passes running beside this solve skip the domain)
+            ctl->status = 0;
+            stop = 0;
+            if (zero_rhs || res[0] <= ctl->tol2 * ctl->bb) {
+                bicg_end(ctl, A.ds[d], A.loop, stage, 1);
+                stop = 1;
+            }
+        }
+        __syncthreads();
+    }
+    for (int parity = 0; !stop; parity ^= 1) {
+        const T* ph_old = (parity ? V.ph[1] : V.ph[0]) + n;
+        const T* v_old = (parity ? V.v[1] : V.v[0]) + n;
+        T* ph = (parity ? V.ph[0] : V.ph[1]) + n;
+        T* v = (parity ? V.v[0] : V.v[1]) + n;
+        // phase A: p^ = r + beta (p^ - omega v); v = M D^-1 p^; alpha = rho1 / (rhat . v)
+        {
+            const T beta = (T)((ctl->rho1 / ctl->rho) * (ctl->alpha / ctl->omega));
+            const T om = (T)ctl->omega;
+            auto pnew = [&](size_t m) { return r[m] + beta * (ph_old[m] - om * v_old[m]); };
+            double a0 = 0.0;
+            for (long long k0 = tid; k0 < nn; k0 += step) {
+                T pc[U], vc[U], rr[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const long long k = k0 + (long long)u * nt;
+                    pc[u] = vc[u] = rr[u] = T(0);
+                    if (k < nn) {
+                        const int I = (int)(k % nxn), J = (int)(k / nxn);
+                        pc[u] = pnew((size_t)k);
+                        vc[u] = row_apply(R, I, J, pc[u] / R.cC[k],
+                                          [&](size_t m) { return pnew(m) / R.cC[m]; });
+                        rr[u] = rh[k];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const long long k = k0 + (long long)u * nt;
+                    if (k >= nn) continue;
+                    ph[k] = pc[u];
+                    v[k] = vc[u];
+                    a0 += (double)rr[u] * (double)vc[u];
+                }
+            }
+            total1(a0);
+            __syncthreads();
+            if (tid == 0) {
+                ctl->rv = res[0];
+                ctl->rho = ctl->rho1;
+                if (res[0] == 0.0 || !isfinite(res[0])) {
+                    bicg_end(ctl, A.ds[d], A.loop, stage, 3);
+                    stop = 1;
+                } else {
+                    ctl->alpha = ctl->rho1 / res[0];
+                }
+            }
+            __syncthreads();
+            if (stop) break;
+        }
+        // phase B: s = r - alpha v; t = M D^-1 s; omega = (t . s) / (t . t)
+        {
+            const T al = (T)ctl->alpha;
+            auto sat = [&](size_t m) { return r[m] - al * v[m]; };
+            double a0 = 0.0, a1 = 0.0;
+            for (long long k0 = tid; k0 < nn; k0 += step) {
+                T sc[U], tc[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const long long k = k0 + (long long)u * nt;
+                    sc[u] = tc[u] = T(0);
+                    if (k < nn) {
+                        const int I = (int)(k % nxn), J = (int)(k / nxn);
+                        sc[u] = sat((size_t)k);
+                        tc[u] = row_apply(R, I, J, sc[u] / R.cC[k],
+                                          [&](size_t m) { return sat(m) / R.cC[m]; });
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const long long k = k0 + (long long)u * nt;
+                    if (k >= nn) continue;
+                    t[k] = tc[u];
+                    a0 += (double)tc[u] * (double)sc[u];
+                    a1 += (double)tc[u] * (double)tc[u];
+                }
+            }
+            total2(a0, a1);
+            __syncthreads();
+            if (tid == 0) {
+                ctl->ts = res[0];
+                ctl->tt = res[1];
+                ctl->omega = res[1] > 0.0 ? res[0] / res[1] : 0.0;
+            }
+            __syncthreads();
+        }
+        // phase C: x += alpha D^-1 p^ + omega D^-1 s; r = s - omega t; rho1 = rhat . r; test
+        {
+            const T al = (T)ctl->alpha, om = (T)ctl->omega;
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+            for (long long k0 = tid; k0 < nn; k0 += step) {
+                T xn[U], rn[U], dx[U], rr[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const long long k = k0 + (long long)u * nt;
+                    xn[u] = rn[u] = dx[u] = rr[u] = T(0);
+                    if (k < nn) {
+                        const T s = r[k] - al * v[k];
+                        const T dinv = T(1) / R.cC[k];
+                        dx[u] = (al * ph[k] + om * s) * dinv;
+                        xn[u] = x[k] + dx[u];
+                        rn[u] = s - om * t[k];
+                        rr[u] = rh[k];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const long long k = k0 + (long long)u * nt;
+                    if (k >= nn) continue;
+                    x[k] = xn[u];
+                    r[k] = rn[u];
+                    a0 += (double)rr[u] * (double)rn[u];
+                    a1 += (double)rn[u] * (double)rn[u];
+                    a2 = fmax(a2, (double)fabs(dx[u]));
+                }
+            }
+            total3(a0, a1, a2);
+            __syncthreads();
+            if (tid == 0) {
+                ctl->rho1 = res[0];
+                ctl->rr = res[1];
+                ctl->dpmax = res[2];
+                ctl->iter += 1;
+                if (res[1] <= ctl->tol2 * ctl->bb || (ctl->eps_dp > 0.0 && res[2] < ctl->eps_dp)) {
+                    bicg_end(ctl, A.ds[d], A.loop, stage, 1);
+                    stop = 1;
+                } else if (ctl->iter >= ctl->max_iter) {
+                    bicg_end(ctl, A.ds[d], A.loop, stage, 2);
+                    stop = 1;
+                } else if (ctl->omega == 0.0 || res[0] == 0.0 || !isfinite(res[1])) {
+                    bicg_end(ctl, A.ds[d], A.loop, stage, 3);
+                    stop = 1;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 2)
 kb_corr(Arena<T> A, const int2* __restrict__ wl, int nw, const T* eta, const T* H,
@@ -705,7 +1029,7 @@ using AsmFn = void (*)(int grid, cudaStream_t, const Arena<T>&, const int2*, int
 template <typename T>
 using ChebFn = void (*)(int grid, cudaStream_t, const Arena<T>&, const int2*, int, const T*,
                         const T*, const T*, const T*, const T*, const T*, const T*, const T*,
-                        T*, T*, int);
+                        T*, T*, int, const int*, int);
 
 template <typename T, int TX, int TY>
 void run_hyp(int grid, cudaStream_t s, const Arena<T>& A, const int2* wl, int nw, const T* e,
@@ -738,11 +1062,11 @@ constexpr size_t cheb_smem()
 template <typename T, int NA, int NB, int BY, bool REGW, int MINB, bool PAD>
 void run_cheb(int grid, cudaStream_t s, const Arena<T>& A, const int2* wl, int nw, const T* cC,
               const T* cW, const T* cE, const T* cS, const T* cN, const T* rhs, const T* xi,
-              const T* xpi, T* xo, T* xpo, int stage)
+              const T* xpi, T* xo, T* xpo, int stage, const int* plan, int want)
 {
     kb_cheb<T, NA, NB, BY, ChebK<T>::value, REGW, MINB, PAD>
         <<<grid, dim3(32, BY), cheb_smem<T, NA, NB, BY, REGW, PAD>(), s>>>(
-            A, wl, nw, cC, cW, cE, cS, cN, rhs, xi, xpi, xo, xpo, stage);
+            A, wl, nw, cC, cW, cE, cS, cN, rhs, xi, xpi, xo, xpo, stage, plan, want);
 }
 
 #define KB_CHEB(T, NA, NB, BY, REGW, MINB, PAD) kb_cheb<T, NA, NB, BY, ChebK<T>::value, REGW, MINB, PAD>
@@ -751,11 +1075,12 @@ void run_cheb(int grid, cudaStream_t s, const Arena<T>& A, const int2* wl, int n
 template <typename T, int C, int R, int NW>
 void run_cheb_reg(int grid, cudaStream_t s, const Arena<T>& A, const int2* wl, int nw,
                   const T* cC, const T* cW, const T* cE, const T* cS, const T* cN, const T* rhs,
-                  const T* xi, const T* xpi, T* xo, T* xpo, int stage)
+                  const T* xi, const T* xpi, T* xo, T* xpo, int stage, const int* plan,
+                  int want)
 {
     kb_cheb_reg<T, C, R, NW, ChebK<T>::value>
         <<<grid, 32 * NW, cheb_reg_smem<T, C, R, NW>(), s>>>(A, wl, nw, cC, cW, cE, cS, cN, rhs,
-                                                             xi, xpi, xo, xpo, stage);
+                                                             xi, xpi, xo, xpo, stage, plan, want);
 }
 
 #define KB_CHEB_REG(T, C, R, NW) kb_cheb_reg<T, C, R, NW, ChebK<T>::value>
@@ -919,6 +1244,9 @@ struct nh_batch {
     cudaStream_t s = nullptr;
     cudaStream_t own = nullptr;     // created when the caller passes the legacy stream
     cudaStream_t side = nullptr;    // capture of the solver-loop bodies
+    cudaStream_t side2 = nullptr;   // capture of the branches inside a loop body
+    cudaStream_t side3 = nullptr;   // fallback solves beside the Chebyshev passes
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::unique_ptr<BatchBase> impl;
     std::string err;
 };
@@ -993,6 +1321,12 @@ struct BatchImpl : BatchBase {
     StepCtl* d_stctl = nullptr;
     unsigned* d_loop = nullptr;
     unsigned* h_loop = nullptr;        // pinned
+    // planned Chebyshev passes (kb_cheb_plan): domains in work-list order, the compacted
+    // items of the few domains still solving, and the plan (mode, length)
+    int* d_order = nullptr;
+    int2* wl_act = nullptr;
+    int* d_plan = nullptr;
+    int cap_tail = 0;
     DomState* h_ds = nullptr;          // pinned
     std::vector<void*> allocs;
     // work lists: element items (cell chunks, node chunks) and one per tile candidate
@@ -1134,6 +1468,10 @@ struct BatchImpl : BatchBase {
         A_(d_sctl, n);
         A_(d_stctl, n);
         A_(d_loop, 8);   // [0..3] solver loops, [4] length of the fallback list
+        cap_tail = 16 * nsm;
+        A_(d_order, n);
+        A_(wl_act, (size_t)cap_tail + 1);
+        A_(d_plan, 4);
 #undef A_
         cudaError_t e;
         if ((e = cudaMallocHost(&h_loop, 4 * sizeof(unsigned))) != cudaSuccess) return bcuda(hb, e, "cudaMallocHost");
@@ -1143,6 +1481,8 @@ struct BatchImpl : BatchBase {
         cudaMemsetAsync(d_ds, 0, n * sizeof(DomState), s);
         cudaMemsetAsync(d_stctl, 0, n * sizeof(StepCtl), s);
         cudaMemsetAsync(d_loop, 0, 8 * sizeof(unsigned), s);
+        cudaMemsetAsync(d_plan, 0, 4 * sizeof(int), s);
+        cudaMemcpyAsync(d_order, order.data(), n * sizeof(int), cudaMemcpyHostToDevice, s);
         {
             std::vector<SolveCtl> sc(n);
             std::memset(sc.data(), 0, n * sizeof(SolveCtl));
@@ -1271,23 +1611,82 @@ struct BatchImpl : BatchBase {
                           B.p, G);
     }
 
-    // pass `odd`: reads (dp, r) and writes (v[0], v[1]) when 0, the other way when 1
-    void cheb_pass(int s, int cand, bool persistent, cudaStream_t st, int odd)
+    // pass `odd`: reads (dp, r) and writes (v[0], v[1]) when 0, the other way when 1;
+    // over the items wl[0 .. nw) on `grid` blocks, or the branch `want` of a plan
+    void cheb_launch(int s, int cand, int grid, cudaStream_t st, int odd, const int2* wl, int nw,
+                     const int* plan, int want)
     {
-        const Shape sh = C::cheb_shape(cand);
         T* xa = odd ? B.v[0] : B.dp;
         T* pa = odd ? B.v[1] : B.r;
         T* xb = odd ? B.dp : B.v[0];
         T* pb = odd ? B.r : B.v[1];
-        C::cheb(cand)(grid_of(C::cheb_kernel(cand), sh.threads, C::cheb_smem_of(cand), nw_cheb[cand], persistent),
-                      st, arena(), wl_cheb[cand], nw_cheb[cand], B.cC, B.cW, B.cE, B.cS, B.cN,
-                      B.rhs, xa, pa, xb, pb, s);
+        C::cheb(cand)(grid, st, arena(), wl, nw, B.cC, B.cW, B.cE, B.cS, B.cN, B.rhs, xa, pa, xb,
+                      pb, s, plan, want);
     }
-    // two passes (the buffer pairs alternate, so a pair of passes restores them)
+    // an unplanned pass over the full work list (the autotuner's timings)
+    void cheb_pass(int s, int cand, bool persistent, cudaStream_t st, int odd)
+    {
+        const Shape sh = C::cheb_shape(cand);
+        cheb_launch(s, cand, grid_of(C::cheb_kernel(cand), sh.threads, C::cheb_smem_of(cand),
+                                     nw_cheb[cand], persistent),
+                    st, odd, wl_cheb[cand], nw_cheb[cand], nullptr, 0);
+    }
+    // the plan of a pass of the tuned candidate (graph: set the branch conditions too)
+    void cheb_plan(cudaStream_t st, int graph, cudaGraphConditionalHandle hbulk,
+                   cudaGraphConditionalHandle htail)
+    {
+        const Shape sh = C::cheb_shape(tun.cheb);
+        constexpr int K = ChebK<T>::value;
+        kb_cheb_plan<T><<<1, 1024, 0, st>>>(arena(), n, d_order, sh.tx - 2 * K, sh.ty - 2 * K,
+                                            cap_tail, wl_act, d_plan, graph, hbulk, htail);
+    }
+    // the two branches of a planned pass: the tuned launch over the full list, or a grid of
+    // resident blocks over the compacted items
+    void cheb_bulk(int s, cudaStream_t st, int odd)
+    {
+        const int cand = tun.cheb;
+        const Shape sh = C::cheb_shape(cand);
+        cheb_launch(s, cand, grid_of(C::cheb_kernel(cand), sh.threads, C::cheb_smem_of(cand),
+                                     nw_cheb[cand], pers(2)),
+                    st, odd, wl_cheb[cand], nw_cheb[cand], d_plan, 0);
+    }
+    void cheb_tail(int s, cudaStream_t st, int odd)
+    {
+        const int cand = tun.cheb;
+        const Shape sh = C::cheb_shape(cand);
+        cheb_launch(s, cand, grid_of(C::cheb_kernel(cand), sh.threads, C::cheb_smem_of(cand),
+                                     cap_tail, true),
+                    st, odd, wl_act, cap_tail, d_plan, 1);
+    }
+    // two eager passes (the buffer pairs alternate, so a pair of passes restores them); each
+    // launches its plan and both branches, of which the one the plan did not choose returns
     void cheb_pair(int s, cudaStream_t st)
     {
         for (int odd = 0; odd < 2; ++odd)
-            K_(NH_K_CHEB_PASS, st, [&] { cheb_pass(s, tun.cheb, pers(2), st, odd); });
+            K_(NH_K_CHEB_PASS, st, [&] {
+                cheb_plan(st, 0, 0, 0);
+                cheb_bulk(s, st, odd);
+                cheb_tail(s, st, odd);
+            });
+    }
+    // the same two passes inside a captured loop body (stream bs): plan, then one IF node
+    // per branch, whose bodies are captured on side2
+    template <typename Chk>
+    void cheb_pair_graph(int s, cudaStream_t bs, Chk& chk)
+    {
+        for (int odd = 0; odd < 2; ++odd) {
+            cudaStreamCaptureStatus cs;
+            cudaGraph_t g = nullptr;
+            chk(cudaStreamGetCaptureInfo(bs, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+            cudaGraphConditionalHandle hbulk = 0, htail = 0;
+            chk(cudaGraphConditionalHandleCreate(&hbulk, g, 0, cudaGraphCondAssignDefault));
+            chk(cudaGraphConditionalHandleCreate(&htail, g, 0, cudaGraphCondAssignDefault));
+            cheb_plan(bs, 1, hbulk, htail);
+            add_cond(bs, hb->side2, chk, hbulk, cudaGraphCondTypeIf,
+                     [&](cudaStream_t ts) { cheb_bulk(s, ts, odd); });
+            add_cond(bs, hb->side2, chk, htail, cudaGraphCondTypeIf,
+                     [&](cudaStream_t ts) { cheb_tail(s, ts, odd); });
+        }
     }
     void settle(cudaStream_t st)
     {
@@ -1308,6 +1707,17 @@ struct BatchImpl : BatchBase {
     }
 
     const int* nfb() const { return reinterpret_cast<const int*>(d_loop + 4); }
+
+    // the fallback solves that the assembly decided (status 4) of the domains of at most
+    // nh_params.fallback_block_nodes nodes, one block each
+    void bicg_small(int s, cudaStream_t st)
+    {
+        const long long lim = hb->prm.fallback_block_nodes;
+        if (lim <= 0) return;
+        K_(NH_K_BICG_BLOCK, st, [&] {
+            kb_bicg_small<T><<<n, 1024, 0, st>>>(arena(), bivec(), s, lim);
+        });
+    }
 
     // compacted list of the fallback domains' chunks, then the BiCGStab initial residual
     void bicg_init(int s, cudaStream_t st)
@@ -1374,6 +1784,7 @@ struct BatchImpl : BatchBase {
         unsigned passes = 0;   // pairs of passes
         int batch = 2;
         cudaError_t e;
+        bicg_small(s, hb->s);   // (beside the passes in a captured step)
         for (;;) {
             for (int k = 0; k < batch; ++k) cheb_pair(s, hb->s);
             passes += batch;
@@ -1408,6 +1819,37 @@ struct BatchImpl : BatchBase {
         return e == cudaSuccess ? NH_OK : bcuda(hb, e, "batched step");
     }
 
+    // Append to the capture on stream s a conditional node of `type` on handle h, whose body
+    // is captured from body(bs) on stream bs.
+    template <typename Chk, typename Body>
+    void add_cond(cudaStream_t s, cudaStream_t bs, Chk& chk, cudaGraphConditionalHandle h,
+                  cudaGraphConditionalNodeType type, Body&& body)
+    {
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t g = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        chk(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+        // (the params union has no default constructor: zeroed storage)
+        alignas(cudaGraphNodeParams) unsigned char npb[sizeof(cudaGraphNodeParams)] = {};
+        cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(npb);
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = type;
+        np.conditional.size = 1;
+        cudaGraphNode_t node = nullptr;
+        chk(cudaGraphAddNode(&node, g, deps, nullptr, nd, &np));
+        if (!node) return;
+        cudaGraph_t bodyg = np.conditional.phGraph_out[0];
+        chk(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+        chk(cudaStreamBeginCaptureToGraph(bs, bodyg, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal));
+        body(bs);
+        chk(cudaGetLastError());
+        cudaGraph_t bout = nullptr;
+        chk(cudaStreamEndCapture(bs, &bout));
+    }
+
     // Append to the capture on stream s a conditional WHILE node whose body is captured from
     // body(side stream, handle); pre(handle), when given, is captured before the node and
     // sets the first condition (the handle's default value is dflt).
@@ -1416,31 +1858,12 @@ struct BatchImpl : BatchBase {
     {
         cudaStreamCaptureStatus cs;
         cudaGraph_t g = nullptr;
-        const cudaGraphNode_t* deps = nullptr;
-        size_t nd = 0;
         chk(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
         cudaGraphConditionalHandle h = 0;
         chk(cudaGraphConditionalHandleCreate(&h, g, dflt, cudaGraphCondAssignDefault));
         call_pre(pre, h);
-        chk(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
-        // (the params union has no default constructor: zeroed storage)
-        alignas(cudaGraphNodeParams) unsigned char npb[sizeof(cudaGraphNodeParams)] = {};
-        cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(npb);
-        np.type = cudaGraphNodeTypeConditional;
-        np.conditional.handle = h;
-        np.conditional.type = cudaGraphCondTypeWhile;
-        np.conditional.size = 1;
-        cudaGraphNode_t node = nullptr;
-        chk(cudaGraphAddNode(&node, g, deps, nullptr, nd, &np));
-        if (!node) return;
-        cudaGraph_t bodyg = np.conditional.phGraph_out[0];
-        chk(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
-        chk(cudaStreamBeginCaptureToGraph(hb->side, bodyg, nullptr, nullptr, 0,
-                                          cudaStreamCaptureModeThreadLocal));
-        body(hb->side, h);
-        chk(cudaGetLastError());
-        cudaGraph_t bout = nullptr;
-        chk(cudaStreamEndCapture(hb->side, &bout));
+        add_cond(s, hb->side, chk, h, cudaGraphCondTypeWhile,
+                 [&](cudaStream_t bs) { body(bs, h); });
     }
     template <typename Pre>
     static void call_pre(Pre& pre, cudaGraphConditionalHandle h) { pre(h); }
@@ -1457,13 +1880,21 @@ struct BatchImpl : BatchBase {
         for (int st = 0; st < 2; ++st) {
             pre_solve(st);
             if (hb->prm.nonhydrostatic) {
+                // the small domains whose rows fail the Gershgorin test: their BiCGStab solves
+                // on side3, beside the Chebyshev passes of the others
+                chk(cudaEventRecord(hb->ev_fork, s));
+                chk(cudaStreamWaitEvent(hb->side3, hb->ev_fork, 0));
+                bicg_small(st, hb->side3);
+                chk(cudaEventRecord(hb->ev_join, hb->side3));
                 // Chebyshev passes: WHILE (domains solving) { pass; test }
                 add_while(s, chk, 1, [&](cudaStream_t bs, cudaGraphConditionalHandle h) {
-                    cheb_pair(st, bs);
+                    cheb_pair_graph(st, bs, chk);
                     kb_loop_cond<<<1, 32, 0, bs>>>(h, d_loop, 0, pass_cap(), 1);
                 }, nullptr);
+                chk(cudaStreamWaitEvent(s, hb->ev_join, 0));
                 settle(s);
-                // fallback: init; WHILE (domains in BiCGStab) { two iterations; test }
+                // fallback for the others (stalled Chebyshev solves, larger domains): init;
+                // WHILE (domains in BiCGStab) { two iterations; test }
                 bicg_init(st, s);
                 add_while(s, chk, 0, [&](cudaStream_t bs, cudaGraphConditionalHandle h) {
                     bicg_pair(st, bs);
@@ -1794,6 +2225,10 @@ int nh_create_batch(int n, const nh_grid* grids, const double* const* H, const n
         b->s = b->own;
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side3, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete b;
@@ -1902,6 +2337,10 @@ void nh_batch_destroy(nh_batch* b)
     if (b->s) cudaStreamSynchronize(b->s);
     b->impl.reset();
     if (b->side) cudaStreamDestroy(b->side);
+    if (b->side2) cudaStreamDestroy(b->side2);
+    if (b->side3) cudaStreamDestroy(b->side3);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
     if (b->own) cudaStreamDestroy(b->own);
     delete b;
 }

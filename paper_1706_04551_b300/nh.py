@@ -37,7 +37,7 @@ class Params(C.Structure):
                 ("adjoint_frozen_limiter", C.c_int), ("cheb_form", C.c_int),
                 ("w_equation", C.c_int), ("relax_width", C.c_double * 4),
                 ("dry_zero", C.c_int), ("wait_polls", C.c_int), ("capture", C.c_int),
-                ("refine_fp32", C.c_int)]
+                ("refine_fp32", C.c_int), ("fallback_block_nodes", C.c_int)]
 
 
 class StatsT(C.Structure):
@@ -77,7 +77,7 @@ BATCH_AUTOTUNE, BATCH_GRAPH = 1, 2
 # kernel classes of nh_profile_t, in enum order
 KERNELS = ("hyperbolic", "breaking", "assembly", "solve_init", "bicg_A", "bicg_B", "bicg_C",
            "cheb_pass", "tridiag", "correction", "adj_hyperbolic", "adj_assembly",
-           "adj_correction", "w_transport", "relax")
+           "adj_correction", "w_transport", "relax", "bicg_block")
 
 
 class ProfileT(C.Structure):

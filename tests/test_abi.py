@@ -31,8 +31,8 @@ def test_binding_loads_and_default_params():
     assert p.g == 9.81 and p.cfl == 0.9 and p.delta == 1e-5 and p.B1 == 0.15
     # q = 0 in dry cells by default (Sec. 4.5 literal form: dry_zero = 0); default wait limit
     assert p.dry_zero == 1 and p.wait_polls == 0
-    # steps captured as graphs
-    assert p.capture == 1
+    # steps captured as graphs; small batched fallback solves in one block each
+    assert p.capture == 1 and p.fallback_block_nodes == 70000
 
 
 def test_create_rejects_bad_grid_without_touching_the_gpu():

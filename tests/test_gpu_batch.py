@@ -70,6 +70,25 @@ def test_batch_fp64_matches_oracle_per_domain():
     assert sum(b.stats(d)["fallbacks"] for d in range(len(wls))) > 0
 
 
+@pytest.mark.parametrize("block_nodes", [70000, 0])
+def test_batch_fallback_forms_match_oracle(block_nodes):
+    """The BiCGStab solves of the domains whose rows fail the Gershgorin test: in one thread
+    block each, beside the Chebyshev passes of the others (the default), or by the
+    grid-wide BiCGStab after the passes (fallback_block_nodes = 0); captured steps, FP64,
+    each domain against the oracle at 1e-10."""
+    wls = small_members()
+    b = make_batch(wls, graph=True, fallback_block_nodes=block_nodes)
+    b.run(4)
+    assert b.tuning()["graph"] == 1
+    for d, w in enumerate(wls):
+        g = b.get_state(d)
+        h, q1, q2, _, p, t, steps, _ = oracle_run(w, 4)
+        assert rel(g["eta"] + w.H, h) < 1e-10, d
+        assert rel_q(g["q1"], g["q2"], q1, q2) < 1e-10, d
+        assert rel(g["p"], p) < 1e-10, d
+    assert sum(b.stats(d)["fallbacks"] for d in range(len(wls))) > 0
+
+
 def test_batch_profile_counts_launches():
     wls = small_members()
     b = make_batch(wls, "fp32", graph=True)
@@ -79,6 +98,8 @@ def test_batch_profile_counts_launches():
     b.profile(False)
     assert pr["hyperbolic"][0] == 2 and pr["assembly"][0] == 2 and pr["correction"][0] == 2
     assert pr["cheb_pass"][0] >= 2 and all(v[1] >= 0 for v in pr.values())
+    # the fallback solves of the small steep members: one block launch per stage
+    assert pr["bicg_block"][0] == 2
 
 
 def test_batch_fp32_matches_oracle_and_single_domain():
