@@ -971,43 +971,74 @@ kb_bicg_small(Arena<T> A, BiVec<T> V, int stage, long long max_nodes)
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 2)
-kb_corr(Arena<T> A, const int2* __restrict__ wl, int nw, const T* eta, const T* H,
-        const T* q1k, const T* q2k, const T* ws, const T* p, const T* dp, T* pout, T bfac,
-        int with_p, T* eo, T* q1o, T* q2o, T* wo, int final_stage)
+// Correction of q and w (and the Eq. (23) rate in the final stage) over a work list of
+// (domain, tile) items of TX x TY nodes: corr_tile, the single-domain tile body.  Blocks
+// walk contiguous shares [lo, hi) of the list (one item
+// each when the grid has one block per item); the rates of a block's consecutive items of
+// one domain are pooled and published once (the group's first slot holds them, its other
+// slots zero), and the domain's last publication advances its clock and sets its next
+// step (every item of the domain has read the step by then).
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
+kb_corr_t(Arena<T> A, const int2* __restrict__ wl, int nw, const T* eta, const T* H,
+          const T* q1k, const T* q2k, const T* ws, const T* p, const T* dp, T* pout, T bfac,
+          int with_p, T* eo, T* q1o, T* q2o, T* wo, int final_stage)
 {
-    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
+    const int lo = (int)((long long)nw * blockIdx.x / gridDim.x);
+    const int hi = (int)((long long)nw * (blockIdx.x + 1) / gridDim.x);
+    int gd = -1, gy = 0, gn = 0, gnt = 0;
+    long long gpoff = 0;
+    T lam = T(0);   // the group's rate (this thread's part)
+    auto flush = [&]() {
+        if (gn == 0) return;
+        double v[1] = {(double)lam};
+        block_reduce<1, 1u>(v);   // into thread 0
+        double acc[2];
+        if (dom_publish_sum_max(0.0, v[0], A.partials + gpoff, &A.stctl[gd].counter, gy, gn,
+                                gnt, acc) &&
+            threadIdx.x == 0) {
+            DomState& s = A.ds[gd];
+            s.t += s.dt;
+            s.steps += 1;
+            s.lam = acc[1];
+            s.dt = A.fixed_dt > 0.0 ? A.fixed_dt : (acc[1] > 0.0 ? A.cfl / acc[1] : 0.0);
+        }
+        gn = 0;
+        lam = T(0);
+    };
+    for (int w = lo; w < hi; ++w) {
         const int2 it = wl[w];
         const Dom<T>& D = A.dom[it.x];
         const Prm<T> P = D.P;
         const long long c = D.coff, n = D.noff;
-        const long long nn = (long long)(P.nx + 1) * (P.ny + 1);
-        DomState& s = A.ds[it.x];
-        const T de = bfac * (T)s.dt;
-        T lam = T(0);
-        int bad = 0;
-        for (long long k = (long long)it.y * kChunk + threadIdx.x;
-             k < nn && k < (long long)(it.y + 1) * kChunk; k += blockDim.x)
-            corr_node(P, eta + c, H + c, q1k + c, q2k + c, ws + n, p + n, dp + n, pout + n, de,
-                      with_p, eo + c, q1o + c, q2o + c, wo + n, final_stage, k, lam, bad);
-        double acc[1] = {(double)lam};
-        if (bad) atomicOr(&s.nonfinite, 1);
+        const int ntx = cdiv(P.nx + 1, TX);
         if (final_stage) {
-            if (dom_reduce<1, 1u>(acc, A.partials + D.poff, &A.stctl[it.x].counter, it.y,
-                                  D.nnc) &&
-                threadIdx.x == 0) {
-                // every item of this domain has read s.dt: advance its clock and set the
-                // next step from the new state
-                s.t += s.dt;
-                s.steps += 1;
-                s.lam = acc[0];
-                s.dt = A.fixed_dt > 0.0 ? A.fixed_dt : (acc[0] > 0.0 ? A.cfl / acc[0] : 0.0);
+            if (it.x != gd) {
+                flush();
+                gd = it.x;
+                gy = it.y;
+                gnt = ntx * cdiv(P.ny + 1, TY);
+                gpoff = D.poff;
+            } else if (threadIdx.x == 0) {
+                A.partials[gpoff + 2 * (long long)it.y] = 0.0;
+                A.partials[gpoff + 2 * (long long)it.y + 1] = 0.0;
             }
         }
-        __syncthreads();
+        DomState& s = A.ds[it.x];
+        const T de = bfac * (T)s.dt;
+        int bad = 0;
+        corr_tile<T, TX, TY>(P, eta + c, H + c, q1k + c, q2k + c, ws + n, p + n, dp + n,
+                             pout + n, de, with_p, eo + c, q1o + c, q2o + c, wo + n,
+                             final_stage, it.y % ntx, it.y / ntx, lam, bad);
+        if (bad) atomicOr(&s.nonfinite, 1);
+        if (final_stage) ++gn;
+        __syncthreads();   // the tile's shared arrays are restaged by the next item
     }
+    if (final_stage) flush();
 }
+
+// correction tiles of the batched form (nodes)
+constexpr int kCorrTX = 32, kCorrTY = 8;
 
 // ---------------------------------------------------------------- candidates
 
@@ -1330,8 +1361,8 @@ struct BatchImpl : BatchBase {
     DomState* h_ds = nullptr;          // pinned
     std::vector<void*> allocs;
     // work lists: element items (cell chunks, node chunks) and one per tile candidate
-    int2 *wl_cell = nullptr, *wl_node = nullptr, *wl_fb = nullptr;
-    int nw_cell = 0, nw_node = 0;
+    int2 *wl_cell = nullptr, *wl_node = nullptr, *wl_fb = nullptr, *wl_corr = nullptr;
+    int nw_cell = 0, nw_node = 0, nw_corr = 0;
     std::vector<int2*> wl_hyp, wl_asm, wl_cheb;
     std::vector<int> nw_hyp, nw_asm, nw_cheb;
     nh_batch_tuning tun{};
@@ -1437,6 +1468,7 @@ struct BatchImpl : BatchBase {
                 np = std::max<long long>(np, 2LL * cdiv(g.nx + 1, s.tx - 2 * ChebK<T>::value) *
                                                   cdiv(g.ny + 1, s.ty - 2 * ChebK<T>::value));
             }
+            np = std::max<long long>(np, 2LL * cdiv(g.nx + 1, kCorrTX) * cdiv(g.ny + 1, kCorrTY));
             D.poff = poff;
             poff += (np + 31) / 32 * 32;
         }
@@ -1515,6 +1547,10 @@ struct BatchImpl : BatchBase {
         }
         if ((rc = make_list([&](int d) { return doms[d].ncc; }, &wl_cell, &nw_cell)) != NH_OK) return rc;
         if ((rc = make_list([&](int d) { return doms[d].nnc; }, &wl_node, &nw_node)) != NH_OK) return rc;
+        if ((rc = make_list([&](int d) {
+                 return cdiv(doms[d].P.nx + 1, kCorrTX) * cdiv(doms[d].P.ny + 1, kCorrTY);
+             }, &wl_corr, &nw_corr)) != NH_OK)
+            return rc;
         if ((rc = alloc(&wl_fb, (size_t)nw_node + 1)) != NH_OK) return rc;
         wl_hyp.resize(C::nh); nw_hyp.resize(C::nh);
         for (int k = 0; k < C::nh; ++k) {
@@ -1770,8 +1806,8 @@ struct BatchImpl : BatchBase {
         T* wo = s == 0 ? B.w1 : B.w;
         const T b = s == 0 ? T(1) : T(0.5);
         K_(NH_K_CORRECTION, hb->s, [&] {
-            kb_corr<T><<<grid_of((const void*)kb_corr<T>, kThreads, 0, nw_node, pers(3)), kThreads, 0, hb->s>>>(
-                arena(), wl_node, nw_node, B.etas, B.H, B.q1k, B.q2k, B.ws, B.p, B.dp, B.palt, b,
+            kb_corr_t<T, kCorrTX, kCorrTY><<<grid_of((const void*)kb_corr_t<T, kCorrTX, kCorrTY>, kThreads, 0, nw_corr, pers(3)), kThreads, 0, hb->s>>>(
+                arena(), wl_corr, nw_corr, B.etas, B.H, B.q1k, B.q2k, B.ws, B.p, B.dp, B.palt, b,
                 q.nonhydrostatic ? 1 : 0, eo, ao, bo, wo, s == 1 ? 1 : 0);
         });
         std::swap(B.p, B.palt);
@@ -1973,15 +2009,15 @@ struct BatchImpl : BatchBase {
             tun.ms[2] = best;
         }
         {
-            // element kernels (correction, breaking): compare the two grid forms on the correction
-            // of a stage-1 pass writing into the stage-1 outputs (overwritten by the real step)
+            // the correction: compare its two grid forms on a stage-1 correction writing into
+            // the stage-1 outputs (overwritten by the real step)
             float tb[2];
             for (int p = 0; p < 2; ++p) {
-                const int gsz = grid_of((const void*)kb_corr<T>, kThreads, 0, nw_node, p == 1);
+                const int gsz = grid_of((const void*)kb_corr_t<T, kCorrTX, kCorrTY>, kThreads, 0, nw_corr, p == 1);
                 tb[p] = time_ms([&] {
-                    kb_corr<T><<<gsz, kThreads, 0, s>>>(arena(), wl_node, nw_node, B.etas, B.H, B.q1k,
-                                                       B.q2k, B.ws, B.p, B.dp, B.palt, T(1), 0, B.eta1,
-                                                       B.q11, B.q21, B.w1, 0);
+                    kb_corr_t<T, kCorrTX, kCorrTY><<<gsz, kThreads, 0, s>>>(
+                        arena(), wl_corr, nw_corr, B.etas, B.H, B.q1k, B.q2k, B.ws, B.p, B.dp,
+                        B.palt, T(1), 0, B.eta1, B.q11, B.q21, B.w1, 0);
                 }, reps);
             }
             tun.persistent = (tun.persistent & ~8) | ((tb[1] < tb[0] ? 1 : 0) << 3);

@@ -1629,86 +1629,11 @@ __device__ __forceinline__ void cheb_finish_stall(SolveCtl* ctl, const double (&
 // q1 += de (T^Hor_N + T^Hor_S)/2, q2 += de (T^Ver_E + T^Ver_W)/2, w += de p / h_c;
 // with P.dry_zero, dry cells (h <= hdry) keep q = 0, as App. B A.2 assumes where the depth
 // vanishes; without it the correction acts on every cell, as Sec. 4.5 states.
-// In the final stage also the Eq. (23) rate max((|u|+c)/dx + (|v|+c)/dy).
-// Node idx of the (nx+1) x (ny+1) node grid and, when it has one, the cell with the same
-// (i, j); lam and bad accumulate the final-stage rate and the non-finite flag.
-template <typename T>
-__device__ __forceinline__ void
-corr_node(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
-          const T* __restrict__ q1k, const T* __restrict__ q2k, const T* __restrict__ ws,
-          const T* __restrict__ p, const T* __restrict__ dp, T* __restrict__ pout, T de,
-          int with_p, T* __restrict__ eo, T* __restrict__ q1o, T* __restrict__ q2o,
-          T* __restrict__ wo, int final_stage, long long idx, T& lam, int& bad)
-{
-    const T d2 = P.delta * P.delta, d4 = d2 * d2;
-    const int nxn = P.nx + 1;
-    {
-        const int I = (int)(idx % nxn), J = (int)(idx / nxn);
-        // node
-        T pc = T(0);
-        if (with_p) {
-            pc = p[idx] + dp[idx];
-            T hs = T(0);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                bool rx, ry;
-                int ii = map_cell(I - 1 + (k & 1), P.nx, P.bcw, P.bce, rx);
-                int jj = map_cell(J - 1 + (k >> 1), P.ny, P.bcs, P.bcn, ry);
-                size_t m = (size_t)jj * P.nx + ii;
-                hs += tmax(eta[m] + H[m], T(0));
-            }
-            const T hc = T(0.25) * hs;
-            const T wn = ws[idx] + de * pc * desing(hc, T(1), d4);
-            wo[idx] = wn;
-            pout[idx] = pc;
-            if (!isfinite(wn) || !isfinite(pc)) bad = 1;
-        } else {
-            wo[idx] = ws[idx];
-            pout[idx] = T(0);
-        }
-        // cell
-        if (I < P.nx && J < P.ny) {
-            const int i = I, j = J;
-            const size_t c = (size_t)j * P.nx + i;
-            const T e = eta[c], Hc = H[c];
-            const T h = tmax(e + Hc, T(0));
-            T a1 = q1k[c], a2 = q2k[c];
-            if (with_p) {
-                bool rx, ry;
-                int iw = map_cell(i - 1, P.nx, P.bcw, P.bce, rx);
-                int ie = map_cell(i + 1, P.nx, P.bcw, P.bce, rx);
-                int js = map_cell(j - 1, P.ny, P.bcs, P.bcn, ry);
-                int jn = map_cell(j + 1, P.ny, P.bcs, P.bcn, ry);
-                const size_t mw = (size_t)j * P.nx + iw, me = (size_t)j * P.nx + ie;
-                const size_t ms = (size_t)js * P.nx + i, mn = (size_t)jn * P.nx + i;
-                const T X = T(0.5) * ((eta[me] - H[me]) - (eta[mw] - H[mw]));
-                const T Y = T(0.5) * ((eta[mn] - H[mn]) - (eta[ms] - H[ms]));
-                auto pat = [&](size_t m) { return p[m] + dp[m]; };
-                const T pSW = pat((size_t)J * nxn + I), pSE = pat((size_t)J * nxn + I + 1);
-                const T pNW = pat((size_t)(J + 1) * nxn + I), pNE = pat((size_t)(J + 1) * nxn + I + 1);
-                const T idx_ = T(1) / P.dx, idy_ = T(1) / P.dy;
-                const T TN = (-T(0.5) * h * (pNE - pNW) - T(0.25) * (pNE + pNW) * X) * idx_;
-                const T TS = (-T(0.5) * h * (pSE - pSW) - T(0.25) * (pSE + pSW) * X) * idx_;
-                const T TE = (-T(0.5) * h * (pNE - pSE) - T(0.25) * (pNE + pSE) * Y) * idy_;
-                const T TW = (-T(0.5) * h * (pNW - pSW) - T(0.25) * (pNW + pSW) * Y) * idy_;
-                a1 += de * T(0.5) * (TN + TS);
-                a2 += de * T(0.5) * (TE + TW);
-            }
-            if (P.dry_zero && h <= P.hdry) { a1 = T(0); a2 = T(0); }   // dry cells: no discharge
-            eo[c] = e; q1o[c] = a1; q2o[c] = a2;
-            if (!isfinite(e) || !isfinite(a1) || !isfinite(a2)) bad = 1;
-            if (final_stage) {
-                const T u = desing(h, a1, d4), v = desing(h, a2, d4), cw = qsqrt(P.g * h);
-                lam = tmax(lam, (fabs(u) + cw) * (T(1) / P.dx) + (fabs(v) + cw) * (T(1) / P.dy));
-            }
-        }
-    }
-}
-
-// Tiled form of corr_node for a TX x TY tile of nodes (and the cells with the same (i, j)):
-// the block stages eta and H of the cells around the tile (a 1-cell ring) and p + dp of the
-// tile's nodes plus one row and column, so each value is loaded once per tile.  Same
-// arithmetic as corr_node.
+// In the final stage also the Eq. (23) rate max((|u|+c)/dx + (|v|+c)/dy); lam and bad
+// accumulate the final-stage rate and the non-finite flag.
+// Tiled for a TX x TY tile of nodes (and the cells with the same (i, j)): the block stages
+// eta and H of the cells around the tile (a 1-cell ring) and p + dp of the tile's nodes
+// plus one row and column, so each value is loaded once per tile.
 template <typename T, int TX, int TY>
 __device__ __forceinline__ void
 corr_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
