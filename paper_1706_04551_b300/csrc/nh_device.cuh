@@ -577,21 +577,26 @@ __device__ __forceinline__ void break_staged(const Prm<T>& P, const T* sq1, cons
                                              T d4, T& q1o, T& q2o)
 {
     const int nb[4] = {sm - 1, sm + 1, sm - SW, sm + SW};   // W, E, S, N
-    T qq[4], uu[4], HH[4];
+    T qq[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        qq[k] = k < 2 ? sq1[nb[k]] : sq2[nb[k]];
-        uu[k] = desing(hs[nb[k]], qq[k], d4);
-        HH[k] = sHH[nb[k]];
-    }
+    for (int k = 0; k < 4; ++k) qq[k] = k < 2 ? sq1[nb[k]] : sq2[nb[k]];
     const T h = hs[sm];
     const T i2x = T(1) / (T(2) * P.dx), i2y = T(1) / (T(2) * P.dy);
     T dq = (qq[1] - qq[0]) * i2x + (qq[3] - qq[2]) * i2y;
+    T nu = nu_break(h, dq, P.g, P.B1, P.hdry);
+    q1o = sq1[sm];
+    q2o = sq2[sm];
+    if (nu == T(0)) return;   // no breaking here (most cells): q** = q* (up to the sign of a zero)
+    T uu[4], HH[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        uu[k] = desing(hs[nb[k]], qq[k], d4);
+        HH[k] = sHH[nb[k]];
+    }
     T du = (uu[1] - uu[0]) * i2x + (uu[3] - uu[2]) * i2y;
     T Hx = (HH[1] - HH[0]) * i2x, Hy = (HH[3] - HH[2]) * i2y;
-    T nu = nu_break(h, dq, P.g, P.B1, P.hdry);
-    q1o = sq1[sm] + de * T(2) * nu * du * Hx;
-    q2o = sq2[sm] + de * T(2) * nu * du * Hy;
+    q1o += de * T(2) * nu * du * Hx;
+    q2o += de * T(2) * nu * du * Hy;
 }
 // Tiled form of the assembly for a TX x TY node tile: the block stages s = eta - H and h of
 // the cells around the tile (a 2-cell ring), computes the centred differences X, Y of every
@@ -618,7 +623,7 @@ asm_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
     // computed here (break_staged) and the tile's own cells written to q1k_out / q2k_out
     const bool fuse = P.breaking && q1k_out != nullptr;
     __shared__ T sq1[SN], sq2[SN], sHH[SN];
-    __shared__ T Xc[CN], Yc[CN], Q1c[CN], Q2c[CN], U1c[CN], V1c[CN], P1c[CN], P2c[CN];
+    __shared__ T Xc[CN], Yc[CN], Q1c[CN], Q2c[CN], P1c[CN], P2c[CN];
     // previous pressure of the tile's nodes and a 1-node ring (residual form)
     constexpr int PW = TX + 2, PN = PW * (TY + 2);
     __shared__ T P0s[PN];
@@ -720,10 +725,6 @@ asm_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
             Q1c[t] = rx ? -b1 : b1;
             Q2c[t] = ry ? -b2 : b2;
         }
-        if (P.breaking) {
-            U1c[t] = desing(hs[sidx], P1c[t], d4);
-            V1c[t] = desing(hs[sidx], P2c[t], d4);
-        }
     }
     __syncthreads();
     const T inv2dx = T(1) / (T(2) * P.dx), inv2dy = T(1) / (T(2) * P.dy);
@@ -749,10 +750,14 @@ asm_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
         if (P.breaking) {
             T dq = (P1c[kb] + P1c[ke] - P1c[ka] - P1c[kd]) * inv2dx
                  + (P2c[kd] + P2c[ke] - P2c[ka] - P2c[kb]) * inv2dy;
-            T du = (U1c[kb] + U1c[ke] - U1c[ka] - U1c[kd]) * inv2dx
-                 + (V1c[kd] + V1c[ke] - V1c[ka] - V1c[kb]) * inv2dy;
             T nu = nu_break(hc, dq, P.g, P.B1, P.hdry);
-            wv += de * T(2) * nu * du * desing(hc, T(1), d4);
+            if (nu != T(0)) {   // the velocities only where the eddy viscosity acts
+                auto u1 = [&](int k, int sx) { return desing(hs[sx], P1c[k], d4); };
+                auto v1 = [&](int k, int sx) { return desing(hs[sx], P2c[k], d4); };
+                T du = (u1(kb, sb) + u1(ke, se) - u1(ka, sa) - u1(kd, sd)) * inv2dx
+                     + (v1(kd, sd) + v1(ke, se) - v1(ka, sa) - v1(kb, sb)) * inv2dy;
+                wv += de * T(2) * nu * du * desing(hc, T(1), d4);
+            }
         }
         ws[nidx] = wv;
         const T q1E = T(0.5) * (Q1c[ke] + Q1c[kb]), q1W = T(0.5) * (Q1c[kd] + Q1c[ka]);
