@@ -1038,7 +1038,7 @@ kb_corr_t(Arena<T> A, const int2* __restrict__ wl, int nw, const T* eta, const T
 }
 
 // correction tiles of the batched form (nodes)
-constexpr int kCorrTX = 32, kCorrTY = 8;
+constexpr int kCorrTX = 32, kCorrTY = 16;
 
 // ---------------------------------------------------------------- candidates
 

@@ -1265,7 +1265,7 @@ void launch_corr2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* 
                    const T* q2k, T de, int with_p, T* eo, T* q1o, T* q2o, T* wo, int final_stage,
                    double* partials, StepCtl* st, const double* dtd, T deb, const T* dp_alt)
 {
-    constexpr int TX = 32, TY = 8;
+    constexpr int TX = 32, TY = 16;   // 2 nodes a thread (32x8: 0.251 ms, 32x16: 0.229 ms at 4096^2 FP32)
     static const int res = resident_grid(k_corr2d_t<T, TX, TY>, 256, 0);
     const int ntx = (P.nx + 1 + TX - 1) / TX, ntiles = ntx * ((P.ny + 1 + TY - 1) / TY);
     k_corr2d_t<T, TX, TY><<<ntiles < res ? ntiles : res, 256, 0, L.s>>>(
