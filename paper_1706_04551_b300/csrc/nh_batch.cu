@@ -149,29 +149,24 @@ kb_asm(Arena<T> A, const int2* __restrict__ wl, int nw, const T* eta, const T* H
        T* q1k, T* q2k, const T* q1s, const T* q2s, const T* w_in, const T* w_b,
        T a, T b, T* ws, T* cC, T* cW, T* cE, T* cS, T* cN, T* rhs, const T* p0, AsmArgs G)
 {
-    for (int w = blockIdx.x; w < nw; w += gridDim.x) {
-        const int2 it = wl[w];
-        const Dom<T>& D = A.dom[it.x];
-        const Prm<T> P = D.P;
-        const long long c = D.coff, n = D.noff;
-        const T de = b * (T)A.ds[it.x].dt;
-        const int tx = cdiv(P.nx + 1, TX), nt = tx * cdiv(P.ny + 1, TY);
-        double acc[3] = {0.0, 0.0, 0.0};
-        // fused breaking: q** is computed in the tile and written to q1k / q2k (not read)
-        const bool fuse = G.fuse && P.breaking;
-        asm_tile<T, TX, TY>(P, eta + c, H + c, fuse ? nullptr : q1k + c, fuse ? nullptr : q2k + c,
-                            q1s + c, q2s + c, w_in + n, w_b + n, a, b, de, G.with_coef, ws + n,
-                            cC + n, cW + n, cE + n, cS + n, cN + n, rhs + n, p0 + n,
-                            /*resid_form=*/G.with_coef, it.y % tx, it.y / tx, acc,
-                            fuse ? q1k + c : nullptr, fuse ? q2k + c : nullptr);
-        SolveCtl* ctl = &A.sctl[it.x];
-        if (dom_reduce<3, 4u>(acc, A.partials + D.poff, &ctl->counter, it.y, nt) &&
+    // a contiguous share of the list (one item when the grid has a block per item); the
+    // norms and Gershgorin ratio of the block's consecutive items of one domain accumulate
+    // per thread and are published once for the group (dom_publish)
+    const int lo = (int)((long long)nw * blockIdx.x / gridDim.x);
+    const int hi = (int)((long long)nw * (blockIdx.x + 1) / gridDim.x);
+    int gd = -1, gy = 0, gn = 0, gnt = 0;
+    long long gpoff = 0;
+    double acc[3] = {0.0, 0.0, 0.0};
+    auto flush = [&]() {
+        if (gn == 0) return;
+        SolveCtl* ctl = &A.sctl[gd];
+        if (dom_publish<3, 4u>(acc, A.partials + gpoff, &ctl->counter, gy, gn, gnt) &&
             threadIdx.x == 0) {
             asm_finish(ctl, acc, G.tol2, G.max_iter, G.kpass, G.with_coef);
             ctl->best = 1.0e300;
             ctl->stale = 0;
             ctl->fb = 0;
-            A.ds[it.x].last_sweeps[G.stage] = 0;
+            A.ds[gd].last_sweeps[G.stage] = 0;
             if (!G.with_coef) {
                 ctl->done = 1;
             } else if (!ctl->done) {
@@ -183,8 +178,37 @@ kb_asm(Arena<T> A, const int2* __restrict__ wl, int nw, const T* eta, const T* H
                 atomicAdd(&A.loop[2], 1u);
             }
         }
-        __syncthreads();
+        gn = 0;
+        acc[0] = acc[1] = acc[2] = 0.0;
+    };
+    for (int w = lo; w < hi; ++w) {
+        const int2 it = wl[w];
+        const Dom<T>& D = A.dom[it.x];
+        const Prm<T> P = D.P;
+        const long long c = D.coff, n = D.noff;
+        const T de = b * (T)A.ds[it.x].dt;
+        const int tx = cdiv(P.nx + 1, TX);
+        if (it.x != gd) {
+            flush();
+            gd = it.x;
+            gy = it.y;
+            gnt = tx * cdiv(P.ny + 1, TY);
+            gpoff = D.poff;
+        } else if (threadIdx.x == 0) {   // pooled into the group's slot: this item's is zero
+            double* sl = A.partials + gpoff + 3 * (long long)it.y;
+            sl[0] = sl[1] = sl[2] = 0.0;
+        }
+        // fused breaking: q** is computed in the tile and written to q1k / q2k (not read)
+        const bool fuse = G.fuse && P.breaking;
+        asm_tile<T, TX, TY>(P, eta + c, H + c, fuse ? nullptr : q1k + c, fuse ? nullptr : q2k + c,
+                            q1s + c, q2s + c, w_in + n, w_b + n, a, b, de, G.with_coef, ws + n,
+                            cC + n, cW + n, cE + n, cS + n, cN + n, rhs + n, p0 + n,
+                            /*resid_form=*/G.with_coef, it.y % tx, it.y / tx, acc,
+                            fuse ? q1k + c : nullptr, fuse ? q2k + c : nullptr);
+        ++gn;
+        __syncthreads();   // the tile's shared arrays are restaged by the next item
     }
+    flush();
 }
 
 // Last block of a domain's items in a pass: convergence test and next weights, the stall

@@ -244,6 +244,46 @@ __device__ __forceinline__ bool dom_reduce(double (&v)[NV], double* partials, un
     return true;
 }
 
+// Publish a block's totals for `cnt` items of a domain at once (the pooled form of
+// dom_reduce): the block reduces v, thread 0 writes the totals to slot `slot` (the block
+// has written zeros to the slots of its other cnt - 1 items) and counts cnt arrivals.
+// Returns true, in every thread, in the block whose arrivals complete the domain's nitems;
+// that block receives the totals (fixed order over the slots) in v.  Maxima must be
+// non-negative (a zero slot is neutral).
+template <int NV, unsigned MAXMASK>
+__device__ __forceinline__ bool dom_publish(double (&v)[NV], double* partials,
+                                            unsigned* counter, unsigned slot, unsigned cnt,
+                                            unsigned nitems)
+{
+    block_reduce<NV, MAXMASK>(v);
+    const unsigned tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const unsigned nthr = blockDim.x * blockDim.y;
+    __shared__ bool last;
+    if (tid == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) partials[(size_t)slot * NV + k] = v[k];
+        __threadfence();
+        last = atomicAdd(counter, cnt) + cnt == nitems;
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = ((MAXMASK >> k) & 1u) ? -1.0e300 : 0.0;
+    for (unsigned bb = tid; bb < nitems; bb += nthr)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double x = __ldcg(partials + (size_t)bb * NV + k);
+            acc[k] = ((MAXMASK >> k) & 1u) ? fmax(acc[k], x) : acc[k] + x;
+        }
+    block_reduce<NV, MAXMASK>(acc);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = acc[k];
+    if (tid == 0) *counter = 0u;
+    return true;
+}
+
 template <int NV, unsigned MAXMASK>
 __device__ __forceinline__ bool grid_reduce(double (&v)[NV], double* partials,
                                             unsigned* counter)
