@@ -374,8 +374,9 @@ typedef struct {
     int cheb;         /* Chebyshev-pass node region                                      */
     int persistent;   /* bit k set: kernel class k (0 hyperbolic, 1 assembly, 2 Chebyshev,
                          3 correction and breaking) runs as a persistent grid of the
-                         blocks resident at once looping over the work list; clear: one
-                         block per work item                                              */
+                         blocks resident at once looping over the work list (a register-
+                         form Chebyshev candidate: blocks of 8 consecutive work items
+                         each); clear: one block per work item                            */
     int graph;        /* 1: steps run as a CUDA graph (NH_BATCH_GRAPH)                   */
     int tuned;        /* 1: chosen by the autotuner                                      */
     double ms[3];     /* autotuner's time of the chosen hyperbolic launch, assembly launch

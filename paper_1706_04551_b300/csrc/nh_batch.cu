@@ -278,9 +278,9 @@ kb_cheb(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const T* c
     }
 }
 
-// Register form of the batched pass: each persistent block takes a contiguous, balanced
-// share [lo, hi) of the work list, in which a domain's items are contiguous, so a share
-// covers parts of a few domains.  The block walks its share, skipping whole domains that
+// Register form of the batched pass: each block takes a contiguous, balanced share
+// [lo, hi) of the work list (a chunk of a few items, or a whole resident block's share), in
+// which a domain's items are contiguous, so a share covers parts of a few domains.  The block walks its share, skipping whole domains that
 // have converged, and prefetches its next item's region (bulk copies on an mbarrier,
 // element copies at the domain's west and east edges) while it sweeps the current one.  A
 // domain's geometry and solver weights are read when the walk enters it (the next region
@@ -1205,6 +1205,7 @@ struct Cands<float> {
                              (const void*)KB_CHEB_REG(float, 2, 4, 16)};
         return f[k];
     }
+    static bool cheb_is_reg(int k) { return k >= 4; }
     static size_t cheb_smem_of(int k)
     {
         const size_t s[nc] = {cheb_smem<float, 2, 2, 32, true, true>(),
@@ -1260,6 +1261,7 @@ struct Cands<double> {
                              (const void*)KB_CHEB_REG(double, 2, 2, 16)};
         return f[k];
     }
+    static bool cheb_is_reg(int k) { return k == 2; }
     static size_t cheb_smem_of(int k)
     {
         const size_t s[nc] = {cheb_smem<double, 2, 2, 16, false, false>(),
@@ -1683,13 +1685,26 @@ struct BatchImpl : BatchBase {
         C::cheb(cand)(grid, st, arena(), wl, nw, B.cC, B.cW, B.cE, B.cS, B.cN, B.rhs, xa, pa, xb,
                       pb, s, plan, want);
     }
+    // grid of a pass of candidate cand over the full list: one block per item; or (the
+    // tuning's persistent form) for the register forms chunks of kRegChunk consecutive items
+    // a block, for the others the resident blocks.  Chunks keep the hardware's in-order
+    // block scheduling, under which the regions being swept at a time are neighbours whose
+    // shared rows stay in L2, and let each block prefetch its next region and publish one
+    // residual sum per chunk (a resident grid of register-form blocks walking whole shares
+    // loses that locality).
+    static constexpr int kRegChunk = 8;
+    int cheb_grid(int cand, bool persistent)
+    {
+        const int nw = nw_cheb[cand];
+        if (persistent && C::cheb_is_reg(cand)) return nw > 0 ? (nw + kRegChunk - 1) / kRegChunk : 1;
+        const Shape sh = C::cheb_shape(cand);
+        return grid_of(C::cheb_kernel(cand), sh.threads, C::cheb_smem_of(cand), nw, persistent);
+    }
     // an unplanned pass over the full work list (the autotuner's timings)
     void cheb_pass(int s, int cand, bool persistent, cudaStream_t st, int odd)
     {
-        const Shape sh = C::cheb_shape(cand);
-        cheb_launch(s, cand, grid_of(C::cheb_kernel(cand), sh.threads, C::cheb_smem_of(cand),
-                                     nw_cheb[cand], persistent),
-                    st, odd, wl_cheb[cand], nw_cheb[cand], nullptr, 0);
+        cheb_launch(s, cand, cheb_grid(cand, persistent), st, odd, wl_cheb[cand], nw_cheb[cand],
+                    nullptr, 0);
     }
     // the plan of a pass of the tuned candidate (graph: set the branch conditions too)
     void cheb_plan(cudaStream_t st, int graph, cudaGraphConditionalHandle hbulk,
@@ -1705,10 +1720,8 @@ struct BatchImpl : BatchBase {
     void cheb_bulk(int s, cudaStream_t st, int odd)
     {
         const int cand = tun.cheb;
-        const Shape sh = C::cheb_shape(cand);
-        cheb_launch(s, cand, grid_of(C::cheb_kernel(cand), sh.threads, C::cheb_smem_of(cand),
-                                     nw_cheb[cand], pers(2)),
-                    st, odd, wl_cheb[cand], nw_cheb[cand], d_plan, 0);
+        cheb_launch(s, cand, cheb_grid(cand, pers(2)), st, odd, wl_cheb[cand], nw_cheb[cand],
+                    d_plan, 0);
     }
     void cheb_tail(int s, cudaStream_t st, int odd)
     {
