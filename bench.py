@@ -525,11 +525,14 @@ def run_ensemble(args, torch, ws, rank, local, dist):
     nodes = [(w.nx + 1) * (w.ny + 1) for w in wls]
     b.run(args.warmup)   # the first call tunes the kernel shapes and captures the graph
     if args.cheb_form is not None:
-        # a fixed Chebyshev candidate, one block per item (profilers distort the tuner's
-        # own timings); the other tuned choices are kept
+        # a fixed Chebyshev candidate (profilers distort the tuner's own timings) in the grid
+        # form the tuner gives its kind: the register forms (candidates 4, 5) in blocks of
+        # consecutive regions, the shared-memory forms one block per item; the other tuned
+        # choices are kept
         t = b.tuning()
+        reg = 4 if args.cheb_form >= 4 else 0
         b.set_tuning(hyp=t["hyp"], assembly=t["assembly"], cheb=args.cheb_form,
-                     persistent=t["persistent"] & ~4, graph=t["graph"])
+                     persistent=(t["persistent"] & ~4) | reg, graph=t["graph"])
         b.run(1)   # (re)captures the step graph outside the timed region
     torch.cuda.synchronize()
     if dist:
