@@ -1442,6 +1442,18 @@ __device__ __forceinline__ void cheb_region_reg(const Rows<T>& Rw, const T* plan
             wN[r][c] = fy ? cs : cn;
         }
     }
+    // the tile interior inside the grid (the nodes this region writes and measures)
+    bool okc[C], okr[R];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const int li = C * lane + c;
+        okc[c] = li >= K && li < RW - K && I0 + li <= nx;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int lj = R * w + r;
+        okr[r] = lj >= K && lj < RH - K && J0 + lj <= ny;
+    }
     stage_next(-1);
     __syncthreads();   // every warp has its registers: the planes may be refilled
     stage_next(0);
@@ -1484,9 +1496,7 @@ __device__ __forceinline__ void cheb_region_reg(const Rows<T>& Rw, const T* plan
                 const T v = cheb_next(xc, prv[r][c], c1, c2, res);
                 prv[r][c] = v;
                 if (sw == K - 1) {
-                    const int li = C * lane + c, lj = R * w + r;
-                    if (li >= K && li < RW - K && lj >= K && lj < RH - K && I0 + li <= nx &&
-                        J0 + lj <= ny) {
+                    if (okr[r] && okc[c]) {
                         const T rs = res * rsc;
                         part = fma(rs, rs, part);
                         dmax = tmax(dmax, T(fabs(v - xc)));
@@ -1503,11 +1513,11 @@ __device__ __forceinline__ void cheb_region_reg(const Rows<T>& Rw, const T* plan
     norm_add(rsum, part);   // scaled; the block applies 1 / rsc^2
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int lj = R * w + r, gJ = J0 + lj;
+        const int gJ = J0 + R * w + r;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            const int li = C * lane + c, gI = I0 + li;
-            if (li >= K && li < RW - K && lj >= K && lj < RH - K && gI <= nx && gJ <= ny) {
+            const int gI = I0 + C * lane + c;
+            if (okr[r] && okc[c]) {
                 const size_t g = (size_t)gJ * NX + gI;
                 xo[g] = x[r][c];
                 xpo[g] = xa[r][c];
