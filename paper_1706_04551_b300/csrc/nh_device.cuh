@@ -1454,6 +1454,9 @@ __device__ __forceinline__ void cheb_region_reg(const Rows<T>& Rw, const T* plan
         const int lj = R * w + r;
         okr[r] = lj >= K && lj < RH - K && J0 + lj <= ny;
     }
+    // exchange rows of the warps above and below (the first and last warps read their own
+    // edge rows back: the region's edge rows are halo)
+    const int lo_row = (w > 0 ? 2 * w - 1 : 2 * w) * RW, hi_row = (w < NW - 1 ? 2 * w + 2 : 2 * w + 1) * RW;
     stage_next(-1);
     __syncthreads();   // every warp has its registers: the planes may be refilled
     stage_next(0);
@@ -1474,16 +1477,16 @@ __device__ __forceinline__ void cheb_region_reg(const Rows<T>& Rw, const T* plan
         T lo[C], hi[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            lo[c] = w > 0 ? e[(2 * w - 1) * RW + C * lane + c] : cur[0][c];
-            hi[c] = w < NW - 1 ? e[(2 * w + 2) * RW + C * lane + c] : cur[R - 1][c];
+            lo[c] = e[lo_row + C * lane + c];
+            hi[c] = e[hi_row + C * lane + c];
         }
         const T c1 = c1s[sw], c2 = c2s[sw];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            T left = __shfl_up_sync(0xffffffffu, cur[r][C - 1], 1);
-            T right = __shfl_down_sync(0xffffffffu, cur[r][0], 1);
-            if (lane == 0) left = cur[r][0];
-            if (lane == 31) right = cur[r][C - 1];
+            // (lanes 0 and 31 read their own values: halo columns of the region, whose
+            // errors do not reach the interior within the K sweeps)
+            const T left = __shfl_up_sync(0xffffffffu, cur[r][C - 1], 1);
+            const T right = __shfl_down_sync(0xffffffffu, cur[r][0], 1);
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 const T xc = cur[r][c];
