@@ -1418,30 +1418,39 @@ __device__ __forceinline__ void cheb_region_reg(const Rows<T>& Rw, const T* plan
     const int nx = Rw.nx, ny = Rw.ny, NX = nx + 1;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     T x[R][C], xa[R][C], rb[R][C], wW[R][C], wE[R][C], wS[R][C], wN[R][C];
+    // registers from the planes; nodes outside the grid hold mirror images, whose W / E and
+    // S / N weights swap (tested only in regions that reach past the grid)
+    auto load = [&](auto edge) {
+        constexpr bool E = decltype(edge)::value;
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int lj = R * w + r, gJ = J0 + lj;
-        const bool fy = gJ < 0 || gJ > ny;
-        const int row = lj * G::SP + region_row_off<T, RW, RH>(I0, J0, lj, nx, ny);
+        for (int r = 0; r < R; ++r) {
+            const int lj = R * w + r, gJ = J0 + lj;
+            const bool fy = E && (gJ < 0 || gJ > ny);
+            const int row = lj * G::SP + region_row_off<T, RW, RH>(I0, J0, lj, nx, ny);
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-            const int li = C * lane + c, gI = I0 + li;
-            const bool fx = gI < 0 || gI > nx;
-            const int t = row + li;
-            const T ic = qdiv(T(1), planes[kPlC * G::PLN + t]);
-            x[r][c] = planes[kPlX * G::PLN + t];
-            xa[r][c] = planes[kPlXp * G::PLN + t];
-            rb[r][c] = mul_rn(planes[kPlB * G::PLN + t], ic);
-            const T cw = mul_rn(planes[kPlW * G::PLN + t], ic);
-            const T ce = mul_rn(planes[kPlE * G::PLN + t], ic);
-            const T cs = mul_rn(planes[kPlS * G::PLN + t], ic);
-            const T cn = mul_rn(planes[kPlN * G::PLN + t], ic);
-            wW[r][c] = fx ? ce : cw;
-            wE[r][c] = fx ? cw : ce;
-            wS[r][c] = fy ? cn : cs;
-            wN[r][c] = fy ? cs : cn;
+            for (int c = 0; c < C; ++c) {
+                const int li = C * lane + c, gI = I0 + li;
+                const bool fx = E && (gI < 0 || gI > nx);
+                const int t = row + li;
+                const T ic = qdiv(T(1), planes[kPlC * G::PLN + t]);
+                x[r][c] = planes[kPlX * G::PLN + t];
+                xa[r][c] = planes[kPlXp * G::PLN + t];
+                rb[r][c] = mul_rn(planes[kPlB * G::PLN + t], ic);
+                const T cw = mul_rn(planes[kPlW * G::PLN + t], ic);
+                const T ce = mul_rn(planes[kPlE * G::PLN + t], ic);
+                const T cs = mul_rn(planes[kPlS * G::PLN + t], ic);
+                const T cn = mul_rn(planes[kPlN * G::PLN + t], ic);
+                wW[r][c] = fx ? ce : cw;
+                wE[r][c] = fx ? cw : ce;
+                wS[r][c] = fy ? cn : cs;
+                wN[r][c] = fy ? cs : cn;
+            }
         }
-    }
+    };
+    if (I0 >= 0 && I0 + RW - 1 <= nx && J0 >= 0 && J0 + RH - 1 <= ny)
+        load(std::false_type{});
+    else
+        load(std::true_type{});
     // the tile interior inside the grid (the nodes this region writes and measures)
     bool okc[C], okr[R];
 #pragma unroll
