@@ -1477,17 +1477,36 @@ __device__ __forceinline__ void cheb_region_reg(const Rows<T>& Rw, const T* plan
     T part = T(0);   // squared scaled residuals of this thread's nodes (rsc: exact 2^-e)
     auto sweep = [&](T (&cur)[R][C], T (&prv)[R][C], int sw) {
         T* e = exch + (sw & 1) * (NW * 2 * RW);
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            e[(2 * w) * RW + C * lane + c] = cur[0][c];
-            e[(2 * w + 1) * RW + C * lane + c] = cur[R - 1][c];
-        }
-        __syncthreads();
         T lo[C], hi[C];
+        if constexpr (sizeof(T) == 4 && C == 3) {
+            // an exchange row holds the lanes' (c0, c1) pairs, then their c2 values
+            auto put = [&](int row, const T (&v)[C]) {
+                reinterpret_cast<float2*>(e + row)[lane] = make_float2(v[0], v[1]);
+                e[row + 64 + lane] = v[2];
+            };
+            auto get = [&](int row, T (&v)[C]) {
+                const float2 q = reinterpret_cast<const float2*>(e + row)[lane];
+                v[0] = q.x;
+                v[1] = q.y;
+                v[2] = e[row + 64 + lane];
+            };
+            put((2 * w) * RW, cur[0]);
+            put((2 * w + 1) * RW, cur[R - 1]);
+            __syncthreads();
+            get(lo_row, lo);
+            get(hi_row, hi);
+        } else {
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-            lo[c] = e[lo_row + C * lane + c];
-            hi[c] = e[hi_row + C * lane + c];
+            for (int c = 0; c < C; ++c) {
+                e[(2 * w) * RW + C * lane + c] = cur[0][c];
+                e[(2 * w + 1) * RW + C * lane + c] = cur[R - 1][c];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                lo[c] = e[lo_row + C * lane + c];
+                hi[c] = e[hi_row + C * lane + c];
+            }
         }
         const T c1 = c1s[sw], c2 = c2s[sw];
 #pragma unroll
