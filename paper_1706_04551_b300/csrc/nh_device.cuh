@@ -475,14 +475,25 @@ hyp_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ q1,
     const T g = P.g, hdry = P.hdry;
     const int i0 = bx * TX, j0 = by * TY;
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int t = tid; t < LN; t += nt) {
-        const int li = t % LW, lj = t / LW;
-        // cells more than 2 outside the domain only feed discarded faces: clamp them
-        int ci = i0 + li - 2, cj = j0 + lj - 2;
-        ci = ci > P.nx + 1 ? P.nx + 1 : ci;
-        cj = cj > P.ny + 1 ? P.ny + 1 : cj;
-        const St<T> c = load_st(P, eta, q1, q2, H, ci, cj, d4);
-        sh[t] = c.h; se[t] = c.e; su[t] = c.u; sv[t] = c.v;
+    if (i0 >= 2 && j0 >= 2 && i0 + TX + 2 <= P.nx && j0 + TY + 2 <= P.ny) {
+        // the tile and its 2-cell halo inside the grid: no boundary mapping
+        for (int t = tid; t < LN; t += nt) {
+            const int li = t % LW, lj = t / LW;
+            const size_t k = (size_t)(j0 + lj - 2) * P.nx + (i0 + li - 2);
+            const T e = eta[k];
+            const T h = tmax(e + H[k], T(0));
+            sh[t] = h; se[t] = e; su[t] = desing(h, q1[k], d4); sv[t] = desing(h, q2[k], d4);
+        }
+    } else {
+        for (int t = tid; t < LN; t += nt) {
+            const int li = t % LW, lj = t / LW;
+            // cells more than 2 outside the domain only feed discarded faces: clamp them
+            int ci = i0 + li - 2, cj = j0 + lj - 2;
+            ci = ci > P.nx + 1 ? P.nx + 1 : ci;
+            cj = cj > P.ny + 1 ? P.ny + 1 : cj;
+            const St<T> c = load_st(P, eta, q1, q2, H, ci, cj, d4);
+            sh[t] = c.h; se[t] = c.e; su[t] = c.u; sv[t] = c.v;
+        }
     }
     __syncthreads();
     auto L = [&](int i, int j) { return (j + 2) * LW + (i + 2); };   // local cell index
@@ -675,6 +686,8 @@ asm_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
     // thread: every load of a round is issued before its first shared store, so a 256-thread
     // block waits on one round of memory latency instead of one per loop
     constexpr int NS = 3;
+    // the staged cells (and the pressure ring) all inside the grid: no boundary mapping
+    const bool inner = I0 >= 2 && J0 >= 2 && I0 + TX + 1 <= P.nx && J0 + TY + 1 <= P.ny;
     for (int base = tid; base < SN; base += NS * nt) {
         T ve[NS], vH[NS], v1[NS], v2[NS], vp[NS];
         bool fx[NS], fy[NS];
@@ -686,11 +699,13 @@ asm_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
             if (t < SN) {
                 const int li = t % SW, lj = t / SW;
                 int ci = I0 - 2 + li, cj = J0 - 2 + lj;
-                ci = ci > P.nx + 1 ? P.nx + 1 : ci;
-                cj = cj > P.ny + 1 ? P.ny + 1 : cj;
-                const int ii = map_cell(ci, P.nx, P.bcw, P.bce, fx[k]);
-                const int jj = map_cell(cj, P.ny, P.bcs, P.bcn, fy[k]);
-                const size_t m = (size_t)jj * P.nx + ii;
+                if (!inner) {
+                    ci = ci > P.nx + 1 ? P.nx + 1 : ci;
+                    cj = cj > P.ny + 1 ? P.ny + 1 : cj;
+                    ci = map_cell(ci, P.nx, P.bcw, P.bce, fx[k]);
+                    cj = map_cell(cj, P.ny, P.bcs, P.bcn, fy[k]);
+                }
+                const size_t m = (size_t)cj * P.nx + ci;
                 ve[k] = eta[m];
                 vH[k] = H[m];
                 if (fuse) {
@@ -700,9 +715,13 @@ asm_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
             }
             if (resid_form && t < PN) {
                 int I = I0 - 1 + t % PW, J = J0 - 1 + t / PW;
-                I = I > P.nx + 1 ? P.nx + 1 : I;   // beyond the mirror: feeds no node of the tile
-                J = J > P.ny + 1 ? P.ny + 1 : J;
-                vp[k] = p0[(size_t)map_node(J, P.ny) * nxn + map_node(I, P.nx)];
+                if (!inner) {
+                    I = I > P.nx + 1 ? P.nx + 1 : I;   // beyond the mirror: feeds no node of the tile
+                    J = J > P.ny + 1 ? P.ny + 1 : J;
+                    I = map_node(I, P.nx);
+                    J = map_node(J, P.ny);
+                }
+                vp[k] = p0[(size_t)J * nxn + I];
             }
         }
 #pragma unroll
@@ -752,8 +771,8 @@ asm_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
             bool rx = false, ry = false;
             if (ci <= P.nx && cj <= P.ny) {   // cells beyond the first ghost feed no node
                 // a ghost cell holds its real cell's q** under the side's mirror / copy
-                const int mi = map_cell(ci, P.nx, P.bcw, P.bce, rx);
-                const int mj = map_cell(cj, P.ny, P.bcs, P.bcn, ry);
+                const int mi = inner ? ci : map_cell(ci, P.nx, P.bcw, P.bce, rx);
+                const int mj = inner ? cj : map_cell(cj, P.ny, P.bcs, P.bcn, ry);
                 const int sm = (mj - (J0 - 2)) * SW + (mi - (I0 - 2));
                 break_staged(P, sq1, sq2, hs, sHH, sm, SW, de, d4, b1, b2);
                 if (li >= 1 && lj >= 1 && ci < P.nx && cj < P.ny) {   // this tile's own cells
@@ -1756,6 +1775,8 @@ corr_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
     // round issued before its first shared store (one round of memory latency per tile)
     static_assert(NNd < CN, "the nodes are staged with the cells");
     constexpr int NS = 2;
+    // the staged cells and nodes all inside the grid: no boundary mapping
+    const bool inner = I0 >= 1 && J0 >= 1 && I0 + TX + 1 <= nx && J0 + TY + 1 <= ny;
     for (int base = tid; base < CN; base += NS * nt) {
         T ve[NS], vH[NS], vp[NS], vd[NS];
 #pragma unroll
@@ -1765,18 +1786,21 @@ corr_tile(const Prm<T>& P, const T* __restrict__ eta, const T* __restrict__ H,
             if (t < CN) {
                 const int li = t % CW, lj = t / CW;
                 int ci = I0 - 1 + li, cj = J0 - 1 + lj;
-                ci = ci > nx + 1 ? nx + 1 : ci;
-                cj = cj > ny + 1 ? ny + 1 : cj;
-                bool rx, ry;
-                const int ii = map_cell(ci, nx, P.bcw, P.bce, rx);
-                const int jj = map_cell(cj, ny, P.bcs, P.bcn, ry);
-                const size_t m = (size_t)jj * nx + ii;
+                if (!inner) {
+                    ci = ci > nx + 1 ? nx + 1 : ci;
+                    cj = cj > ny + 1 ? ny + 1 : cj;
+                    bool rx, ry;
+                    ci = map_cell(ci, nx, P.bcw, P.bce, rx);
+                    cj = map_cell(cj, ny, P.bcs, P.bcn, ry);
+                }
+                const size_t m = (size_t)cj * nx + ci;
                 ve[k] = eta[m];
                 vH[k] = H[m];
             }
             if (with_p && t < NNd) {
                 const int I = I0 + t % NW, J = J0 + t / NW;
-                const size_t m = (size_t)(J > ny ? ny : J) * nxn + (I > nx ? nx : I);
+                const size_t m = inner ? (size_t)J * nxn + I
+                                       : (size_t)(J > ny ? ny : J) * nxn + (I > nx ? nx : I);
                 vp[k] = p[m];
                 vd[k] = dp[m];
             }
