@@ -1379,6 +1379,16 @@ __device__ __forceinline__ int region_row_off(int I0, int J0, int lj, int nx, in
     return (int)(((size_t)mirror_node(J0 + lj, ny) * NX + I0) & (size_t)(G::A - 1));
 }
 
+// The same for a region inside the grid (node row J0 + lj itself, no mirror).
+template <typename T, int RW, int RH>
+__device__ __forceinline__ int region_row_off_in(int I0, int J, int nx)
+{
+    using G = RegionGeom<T, RW, RH>;
+    const int NX = nx + 1;
+    if (!G::bulk(I0, NX)) return 0;
+    return (int)(((size_t)J * NX + I0) & (size_t)(G::A - 1));
+}
+
 // Bytes the bulk copies of region (I0, J0) will complete on the mbarrier (0: element copies).
 template <typename T, int RW, int RH>
 __device__ __forceinline__ unsigned region_bulk_bytes(int I0, int nx)
@@ -1445,7 +1455,8 @@ __device__ __forceinline__ void cheb_region_reg(const Rows<T>& Rw, const T* plan
         for (int r = 0; r < R; ++r) {
             const int lj = R * w + r, gJ = J0 + lj;
             const bool fy = E && (gJ < 0 || gJ > ny);
-            const int row = lj * G::SP + region_row_off<T, RW, RH>(I0, J0, lj, nx, ny);
+            const int row = lj * G::SP + (E ? region_row_off<T, RW, RH>(I0, J0, lj, nx, ny)
+                                            : region_row_off_in<T, RW, RH>(I0, gJ, nx));
 #pragma unroll
             for (int c = 0; c < C; ++c) {
                 const int li = C * lane + c, gI = I0 + li;

@@ -369,9 +369,17 @@ k_cheb_reg(Rows<T> Rw, const T* __restrict__ b, const T* __restrict__ xi,
     }
     const T rsc = sizeof(T) == 4 ? (T)ctl->rscf : (T)ctl->rscd;
     const double rinv2 = ctl->rinv2;
-    auto I0of = [&](int g) { return (g % nrx) * TX - K; };
-    auto J0of = [&](int g) { return (g / nrx) * TY - K; };
-    int g = blockIdx.x;
+    // region g = gy nrx + gx, advanced by the grid stride (dgy rows and dgx columns, with a
+    // carry) instead of dividing by nrx for every region
+    int g = blockIdx.x, gx = g % nrx, gy = g / nrx;
+    const int dgx = (int)gridDim.x % nrx, dgy = (int)gridDim.x / nrx;
+    auto step = [&](int& x, int& y) {
+        x += dgx;
+        y += dgy;
+        if (x >= nrx) { x -= nrx; ++y; }
+    };
+    auto I0of = [&](int x) { return x * TX - K; };
+    auto J0of = [&](int y) { return y * TY - K; };
     // test hook: this block announces 16 bytes that no copy will bring
     const bool stall = (int)blockIdx.x == stall_block;
     if (tid == 0) {
@@ -379,11 +387,11 @@ k_cheb_reg(Rows<T> Rw, const T* __restrict__ b, const T* __restrict__ xi,
         bases[kPlW] = Rw.cW; bases[kPlE] = Rw.cE; bases[kPlS] = Rw.cS; bases[kPlN] = Rw.cN;
         mbar_init(&bar, 1);
         if (g < nreg)
-            mbar_arrive_expect_tx(&bar, stall ? 16u : region_bulk_bytes<T, RW, RH>(I0of(g), nx));
+            mbar_arrive_expect_tx(&bar, stall ? 16u : region_bulk_bytes<T, RW, RH>(I0of(gx), nx));
     }
     __syncthreads();
     if (g < nreg && !stall)
-        cheb_stage_region<T, RW, RH, 32 * NW>(bases, nx, ny, I0of(g), J0of(g), planes, &bar);
+        cheb_stage_region<T, RW, RH, 32 * NW>(bases, nx, ny, I0of(gx), J0of(gy), planes, &bar);
     NormAcc<T> rsum;
     norm_zero(rsum);
     T dmax = T(0);
@@ -395,23 +403,27 @@ k_cheb_reg(Rows<T> Rw, const T* __restrict__ b, const T* __restrict__ xi,
         if (__syncthreads_or(!got)) { ok = false; break; }
         phase ^= 1u;
         const int nxt = g + gridDim.x;
+        int nx_ = gx, ny_ = gy;
+        step(nx_, ny_);
         auto next = [&](int part) {
             if (nxt >= nreg) return;
             if (part < 0) {   // before the barrier that frees the planes
                 fence_proxy_async_smem();
                 if (tid == 0)
-                    mbar_arrive_expect_tx(&bar, region_bulk_bytes<T, RW, RH>(I0of(nxt), nx));
+                    mbar_arrive_expect_tx(&bar, region_bulk_bytes<T, RW, RH>(I0of(nx_), nx));
             } else {
-                cheb_stage_region<T, RW, RH, 32 * NW>(bases, nx, ny, I0of(nxt), J0of(nxt),
+                cheb_stage_region<T, RW, RH, 32 * NW>(bases, nx, ny, I0of(nx_), J0of(ny_),
                                                       planes, &bar);
             }
         };
         if constexpr (sizeof(T) == 4 && C == 2)
-            cheb_region_reg2<R, NW, K>(Rw, planes, exch, c1s, c2s, rsc, I0of(g),
-                                       J0of(g), xo, xpo, rsum, dmax, next);
+            cheb_region_reg2<R, NW, K>(Rw, planes, exch, c1s, c2s, rsc, I0of(gx),
+                                       J0of(gy), xo, xpo, rsum, dmax, next);
         else
-            cheb_region_reg<T, C, R, NW, K>(Rw, planes, exch, c1s, c2s, rsc, I0of(g),
-                                            J0of(g), xo, xpo, rsum, dmax, next);
+            cheb_region_reg<T, C, R, NW, K>(Rw, planes, exch, c1s, c2s, rsc, I0of(gx),
+                                            J0of(gy), xo, xpo, rsum, dmax, next);
+        gx = nx_;
+        gy = ny_;
     }
     if (!ok) {
         const bool issued = !(stall && g == (int)blockIdx.x);
