@@ -117,7 +117,7 @@ kb_mass(Arena<T> A, const int2* __restrict__ wl, int nw, const T* __restrict__ e
 }
 
 template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
 kb_hyp(Arena<T> A, const int2* __restrict__ wl, int nw, const T* eta, const T* q1,
        const T* q2, const T* etab, const T* q1b, const T* q2b, const T* H, T a, T b, T* eo,
        T* q1o, T* q2o)
@@ -315,7 +315,7 @@ kb_cheb_reg(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const 
     const int hi = (int)((long long)nw * (blockIdx.x + 1) / gridDim.x);
     // an item of the walk (uniform across the block): work-list index, domain, region and
     // the domain's node offset and size
-    struct Item { int w, d, y, nx, ny; long long n; };
+    struct Item { int w, d, y, cx, cy, nx, ny; long long n; };   // (cx, cy): region column, row
     auto ntx_of = [&](const Item& it) { return cdiv(it.nx + 1, TX); };
     auto nt_of = [&](const Item& it) { return ntx_of(it) * cdiv(it.ny + 1, TY); };
     // the first item at or after `from` of this share whose domain still solves; `cur` is
@@ -327,21 +327,26 @@ kb_cheb_reg(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const 
             it = cur;
             it.w = from;
             it.y = cur.y + 1;
+            if (++it.cx == ntx_of(it)) { it.cx = 0; ++it.cy; }
             return true;
         }
         for (int w = from; w < hi;) {
             const int2 e = wl[w];
             const Dom<T>& D = A.dom[e.x];
             it.w = w; it.d = e.x; it.y = e.y; it.nx = D.P.nx; it.ny = D.P.ny; it.n = D.noff;
-            if (!A.sctl[e.x].done) return true;
+            if (!A.sctl[e.x].done) {
+                const int ntx = ntx_of(it);
+                it.cx = e.y % ntx;
+                it.cy = e.y / ntx;
+                return true;
+            }
             w += nt_of(it) - it.y;   // past this domain's items
         }
         return false;
     };
     auto origin = [&](const Item& it, int& I0, int& J0) {
-        const int ntx = ntx_of(it);
-        I0 = (it.y % ntx) * TX - K;
-        J0 = (it.y / ntx) * TY - K;
+        I0 = it.cx * TX - K;
+        J0 = it.cy * TY - K;
     };
     auto announce = [&](const Item& it) {   // thread 0: the item's sources and expected bytes
         const long long n = it.n;
@@ -356,7 +361,7 @@ kb_cheb_reg(Arena<T> A, const int2* __restrict__ wl, int nw, const T* cC, const 
         origin(it, I0, J0);
         cheb_stage_region<T, RW, RH, 32 * NW>(bases, it.nx, it.ny, I0, J0, planes, &bar);
     };
-    Item cur{-2, 0, 0, 0, 0, 0}, nxt{-2, 0, 0, 0, 0, 0};
+    Item cur{-2, 0, 0, 0, 0, 0, 0, 0}, nxt{-2, 0, 0, 0, 0, 0, 0, 0};
     bool have = advance(cur, lo, nxt);
     if (tid == 0) {
         mbar_init(&bar, 1);
