@@ -39,7 +39,8 @@ WORDS = {
     "bicg_A": 11.0,       # r rhat p^ v 5 coefs -> p^ v
     "bicg_B": 8.0,        # r v 5 coefs -> t
     "bicg_C": 9.0,        # r rhat p^ v t x diag -> x r
-    "cheb_pass": 10.0,    # x x_prev b 5 coefs -> x x_prev (K sweeps in shared memory)
+    "cheb_pass": 10.0,    # x x_prev b 5 coefs -> x x_prev (K sweeps in shared memory);
+                          # the cyclic form: x b 5 coefs -> x, 8 words
     "tridiag": 5.0,
     "correction": 10.0,   # eta* H q1** q2** w* p -> eta q1 q2 w
     "w_transport": 11.0,  # (hw)_t + div(hw u) = p form, per node: face mass fluxes (2),
@@ -747,6 +748,10 @@ def main():
     esize = 4 if prec == "fp32" else 8
     units = cells if top in ("hyperbolic", "breaking") else nn
     words = dict(WORDS)
+    nf = nh.cheb_forms(prec)
+    cyclic = nf <= st["cheb_form"] < nf + nh.cheb_cyclic_forms(prec)
+    if cyclic:
+        words["cheb_pass"] = 8.0
     if not prm.get("breaking"):
         words["assembly"] = 13.5
     if prm.get("w_equation"):
@@ -775,8 +780,9 @@ def main():
                      "algo_bytes_per_launch": algo_bytes})
     elif prec == "fp64" and top == "cheb_pass":
         # FP64 runs on B300's FP64 units (about 1/60 of the FP32 rate): the pass is bound by
-        # FP64 arithmetic, 14 flops per node and sweep (residual 9, update 5; an FMA is 2)
-        flops = 14.0 * nn * 4 * nl
+        # FP64 arithmetic, 14 flops per node and sweep (residual 9, update 5; an FMA is 2);
+        # the cyclic form updates half the nodes per step, 11 flops each (update 2)
+        flops = (5.5 if cyclic else 14.0) * nn * 4 * nl
         roof = {"bound": "alu", "kernel": top, "achieved": flops / (tms / 1e3) / 1e12,
                 "peak": FP64_TFLOPS, "unit": "TFLOP/s",
                 "frac": flops / (tms / 1e3) / 1e12 / FP64_TFLOPS, "traffic": None,
@@ -804,7 +810,7 @@ def main():
                              "frac": value * 1e6 * model_words * esize / 1e9 / peak,
                              "note": "bytes a step without temporal blocking would move (the "
                                      "stencil passes plus 5 words per Jacobi sweep); the "
-                                     "Chebyshev passes move 10 words per "
+                                     f"Chebyshev passes move {words['cheb_pass']:g} words per "
                                      f"{8 if prec == 'fp32' else 4} sweeps instead"}}
 
     if rank == 0:
@@ -817,8 +823,10 @@ def main():
                        "parallelism": "replicas only (one independent domain per GPU)",
                        "l2": "inputs larger than L2 (state 268 MB FP32 at 4096^2)",
                        "solver": ("Jacobi with Chebyshev-scheduled relaxation, "
-                                  f"{8 if prec == 'fp32' else 4} sweeps per launch, "
-                                  f"scaled-residual tol {prm['tol']}"
+                                  + ("cyclic form (one colour per step), " if cyclic else "")
+                                  + f"{8 if prec == 'fp32' else 4} "
+                                  + ("steps" if cyclic else "sweeps")
+                                  + f" per launch, scaled-residual tol {prm['tol']}"
                                   if prm.get("solver", 1) == 1 else
                                   f"BiCGStab+Jacobi tol {prm['tol']}"),
                        "solver_iters_per_stage": iters / (2.0 * args.steps),

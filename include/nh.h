@@ -100,9 +100,12 @@ typedef struct {
     int adjoint_frozen_limiter; /* nh_adjoint_step: 0 = exact derivative of the step; 1 =
                            reconstruction linearised with the limiter ratio held fixed   */
     int cheb_form;      /* single-domain handles, Chebyshev solver: -1 (default) = the
-                           kernel form of the pass is chosen by timing the first passes;
-                           0 .. nh_cheb_forms(precision) - 1 = that form.  All forms give
-                           the same iterates.                                            */
+                           kernel form of the pass is chosen by timing the first passes
+                           (among the cyclic forms when cheb_cyclic applies, else among the
+                           Jacobi forms); 0 .. nh_cheb_forms(precision) - 1 = that Jacobi
+                           form; nh_cheb_forms(precision) + k = cyclic form k (k <
+                           nh_cheb_cyclic_forms(precision)).  The Jacobi forms give the
+                           same iterates, and so do the cyclic forms.                    */
     int w_equation;     /* NH_W_YAMAZAKI (default) or NH_W_TRANSPORT.  With NH_W_TRANSPORT
                            hw lives on the node (dual) cells: each stage moves it with the
                            mean of the surrounding cells' face mass fluxes, upwind in w,
@@ -148,6 +151,19 @@ typedef struct {
                            other domains (default 70000); 0: every fallback solve uses the
                            grid-wide BiCGStab after the passes.  Single-domain handles
                            ignore it.                                                     */
+    int cheb_cyclic;    /* single-domain 2D handles, Chebyshev solver, cheb_form = -1 and
+                           eps_dp = 0: 1 (default) = the cyclic form of the pass.  The
+                           five-point rows couple each node with nodes of the other colour
+                           (I + J) mod 2 only, and the Chebyshev interval is centred at 1, so
+                           the nodes of one colour at the odd steps and of the other at the
+                           even steps form a closed recurrence (Golub and Varga's cyclic
+                           Chebyshev method): each step updates one colour in place, half
+                           the work of a Jacobi sweep, and every node takes the values of
+                           the full iteration at the steps of its colour.  Its kernel forms
+                           (nh_cheb_cyclic_forms) are chosen by timing.  last_iters and
+                           solver_iters count these steps.  The inner solves of refine_fp32
+                           use it too.  0 = the Jacobi forms (cheb_form).  Batches ignore
+                           it.                                                            */
 } nh_params;
 
 typedef struct {
@@ -164,8 +180,10 @@ typedef struct {
                               that is not diagonally dominant)                           */
     long long fallback_iters; /* BiCGStab iterations of those (part of solver_iters)     */
     int cheb_form;         /* kernel form of the Chebyshev pass in use (nh_params.cheb_form,
-                              or the one chosen by timing); -1 while the forms are timed, or
-                              for a batch / a handle that does not run the Chebyshev solver */
+                              or the one chosen by timing; nh_cheb_forms(precision) + k for
+                              cyclic form k, nh_params.cheb_cyclic); -1 while the forms are
+                              timed, or for a batch / a handle that does not run the
+                              Chebyshev solver                                            */
 } nh_stats_t;
 
 typedef struct nh_handle nh_handle;
@@ -174,13 +192,20 @@ typedef struct nh_handle nh_handle;
  * n = 0, B1 = 0.15, B2 = 0.5 (Sec. 7.4), breaking off, non-hydrostatic on, Chebyshev
  * solver, tol 1e-12, max_iter 2000, FP64, fixed_dt 0, eps_dp 0, exact adjoint, pass
  * form chosen by timing (cheb_form = -1), w equation h w_t = p (NH_W_YAMAZAKI), q = 0 in
- * dry cells (dry_zero = 1), default wait limit (wait_polls = 0), captured steps (capture = 1). */
+ * dry cells (dry_zero = 1), default wait limit (wait_polls = 0), captured steps (capture = 1),
+ * defect correction off (refine_fp32 = 0), batched block fallback up to 70000 nodes, cyclic
+ * form of the pass (cheb_cyclic = 1). */
 int nh_default_params(nh_params *p);
 
 /* Number of kernel forms of the Chebyshev-scheduled Jacobi pass (Sec. 5's scheduled
  * relaxation; nh_params.cheb_form) for precision NH_FP32 or NH_FP64; NH_EINVAL otherwise.
  * No GPU work. */
 int nh_cheb_forms(int precision);
+
+/* Number of kernel forms of the cyclic pass (nh_params.cheb_cyclic; the handle times them
+ * against each other and reports the one in use as nh_stats_t.cheb_form =
+ * nh_cheb_forms(precision) + k) for NH_FP32 or NH_FP64; NH_EINVAL otherwise.  No GPU work. */
+int nh_cheb_cyclic_forms(int precision);
 
 /* Create a simulation on the current CUDA device.  H: host array [ny][nx] (double) of
  * still-water depths.  stream: a cudaStream_t (or 0).  The state is lake at rest
@@ -442,7 +467,7 @@ int nh_debug_system(nh_handle *h, double dt, const void *x, void *rhs_out, void 
 
 /* Failure injection for the bounded waits (the paper has no counterpart): the next
  * Chebyshev pass of the handle that runs in a register form (nh_params.cheb_form 5-7 in
- * FP32, 3 in FP64) lets block `block` announce its first region's bytes on its mbarrier
+ * FP32, 3 in FP64, or the cyclic form) lets block `block` announce its first region's bytes on its mbarrier
  * without issuing the copies, so that this block's first wait runs out of
  * nh_params.wait_polls polls with no copy in flight.  The step then returns NH_ETIMEOUT,
  * and the handle's state is undefined until the next nh_set_state.  Later passes are

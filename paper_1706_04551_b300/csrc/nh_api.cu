@@ -179,6 +179,10 @@ struct Impl : Base {
         P.g = (T)q.g; P.delta = (T)q.delta; P.hdry = (T)q.hdry; P.manning = (T)q.manning_n;
         P.B1 = (T)q.B1; P.breaking = q.breaking; P.dry_zero = q.dry_zero ? 1 : 0;
         pass_variant = q.cheb_form;
+        // the cyclic forms are timed against each other (the same iterates), not against
+        // the Jacobi forms
+        cyclic = q.cheb_form < 0 && q.cheb_cyclic && !(q.eps_dp > 0.0) && dim == 2;
+        if (cyclic && cheb_cyclic_forms<T>() == 1) pass_variant = cheb_pass_forms<T>();
         nc = (size_t)g.nx * g.ny;
         nn = dim == 2 ? (size_t)(g.nx + 1) * (g.ny + 1) : (size_t)(g.nx + 1) * g.ny;
         int dev = 0, nsm = 0;
@@ -452,7 +456,7 @@ struct Impl : Base {
                 int rc = 0;
                 // until the faster pass form is known, alternate the two (their sweeps are
                 // identical, so the solve does not depend on the choice) and time them
-                const int v = pass_variant >= 0 ? pass_variant : (vt_next++ % cheb_pass_forms<T>());
+                const int v = pass_variant >= 0 ? pass_variant : timed_variant();
                 const bool timed = pass_variant < 0 && vt_used + 2 <= kVT;
                 if (timed) cudaEventRecord(vt_ev[vt_used], hd->s);
                 if (timed) { vt_pass[vt_used / 2] = passes_launched; vt_solve[vt_used / 2] = solves; }
@@ -1201,9 +1205,14 @@ struct Impl : Base {
     int vt_next = 0, vt_used = 0, solves = 0;
     int vt_var[kVT / 2] = {}, vt_pass[kVT / 2] = {}, vt_solve[kVT / 2] = {}, vt_ok[kVT / 2] = {};
     cudaEvent_t vt_ev[kVT] = {};
+    bool cyclic = false;   // the cyclic forms (nh_params.cheb_cyclic) are the candidates
+    // candidates: the Jacobi forms 0 .. cheb_pass_forms() - 1, or the cyclic forms after them
+    int cand0() const { return cyclic ? cheb_pass_forms<T>() : 0; }
+    int ncand() const { return cyclic ? cheb_cyclic_forms<T>() : cheb_pass_forms<T>(); }
+    int timed_variant() { return cand0() + vt_next++ % ncand(); }
     void choose_pass_variant()
     {
-        const int nv = cheb_pass_forms<T>();
+        const int v0 = cand0(), nv = ncand();
         double sum[16] = {};
         int cnt[16] = {};
         // the first pass of each form warms it up and is not counted
@@ -1215,8 +1224,8 @@ struct Impl : Base {
             }
         }
         cudaGetLastError();
-        int best = 0;
-        for (int v = 1; v < nv; ++v)
+        int best = v0;
+        for (int v = v0 + 1; v < v0 + nv; ++v)
             if (cnt[v] && (!cnt[best] || sum[v] / cnt[v] < sum[best] / cnt[best])) best = v;
         pass_variant = best;
     }
@@ -1255,7 +1264,8 @@ struct Impl : Base {
                 int rc = 0;
                 K_(NH_K_CHEB_PASS, [&] {
                     rc = launch_cheb_pass<float>(P32, hd->s, B32, xa, pa, xb, pb, B.partials,
-                                                 7, polls, -1);
+                                                 hd->prm.cheb_cyclic ? cheb_pass_forms<float>() : 7,
+                                                 polls, -1);
                 });
                 if (rc != 0) return fail(hd, NH_ECUDA, "Chebyshev pass launch failed");
             }
@@ -1402,8 +1412,11 @@ int check_grid(const nh_grid* g, const nh_params* p, std::string& why)
         why = "adjoint_frozen_limiter must be 0 or 1";
         return 0;
     }
-    const int nforms = p->precision == NH_FP32 ? cheb_pass_forms<float>() : cheb_pass_forms<double>();
+    const int nforms = p->precision == NH_FP32
+                           ? cheb_pass_forms<float>() + cheb_cyclic_forms<float>()
+                           : cheb_pass_forms<double>() + cheb_cyclic_forms<double>();
     if (p->cheb_form < -1 || p->cheb_form >= nforms) { why = "cheb_form out of range"; return 0; }
+    if (p->cheb_cyclic != 0 && p->cheb_cyclic != 1) { why = "cheb_cyclic must be 0 or 1"; return 0; }
     if (p->w_equation != NH_W_YAMAZAKI && p->w_equation != NH_W_TRANSPORT) {
         why = "w_equation must be NH_W_YAMAZAKI or NH_W_TRANSPORT";
         return 0;
@@ -1443,6 +1456,7 @@ int nh_default_params(nh_params* p)
     p->capture = 1;
     p->refine_fp32 = 0;
     p->fallback_block_nodes = 70000;
+    p->cheb_cyclic = 1;
     return NH_OK;
 }
 
@@ -1450,6 +1464,13 @@ int nh_cheb_forms(int precision)
 {
     if (precision == NH_FP32) return cheb_pass_forms<float>();
     if (precision == NH_FP64) return cheb_pass_forms<double>();
+    return NH_EINVAL;
+}
+
+int nh_cheb_cyclic_forms(int precision)
+{
+    if (precision == NH_FP32) return cheb_cyclic_forms<float>();
+    if (precision == NH_FP64) return cheb_cyclic_forms<double>();
     return NH_EINVAL;
 }
 

@@ -1389,19 +1389,20 @@ __device__ __forceinline__ int region_row_off_in(int I0, int J, int nx)
     return (int)(((size_t)J * NX + I0) & (size_t)(G::A - 1));
 }
 
-// Bytes the bulk copies of region (I0, J0) will complete on the mbarrier (0: element copies).
-template <typename T, int RW, int RH>
+// Bytes the bulk copies of region (I0, J0)'s NP planes will complete on the mbarrier (0:
+// element copies).
+template <typename T, int RW, int RH, int NP = kPlanes>
 __device__ __forceinline__ unsigned region_bulk_bytes(int I0, int nx)
 {
     using G = RegionGeom<T, RW, RH>;
-    return G::bulk(I0, nx + 1) ? (unsigned)kPlanes * RH * G::ROWB : 0u;
+    return G::bulk(I0, nx + 1) ? (unsigned)NP * RH * G::ROWB : 0u;
 }
 
-// Issue the copies of region (I0, J0)'s eight planes (nodes outside the grid read their
-// mirror image, as the wall and outflow rows of M prescribe).  bases: the eight source
+// Issue the copies of region (I0, J0)'s NP planes (nodes outside the grid read their
+// mirror image, as the wall and outflow rows of M prescribe).  bases: the NP source
 // arrays in plane order.  Bulk copies complete on `bar` (whose expected bytes the caller
 // announced); element copies are committed as one cp.async group.
-template <typename T, int RW, int RH, int NTHR>
+template <typename T, int RW, int RH, int NTHR, int NP = kPlanes>
 __device__ __forceinline__ void cheb_stage_region(const T* const* bases, int nx, int ny,
                                                   int I0, int J0, T* planes,
                                                   unsigned long long* bar)
@@ -1410,7 +1411,7 @@ __device__ __forceinline__ void cheb_stage_region(const T* const* bases, int nx,
     const int NX = nx + 1;
     const int tid = threadIdx.x;
     if (G::bulk(I0, NX)) {
-        for (int c = tid; c < kPlanes * RH; c += NTHR) {
+        for (int c = tid; c < NP * RH; c += NTHR) {
             const int p = c / RH, lj = c - p * RH;
             const size_t e0 = (size_t)mirror_node(J0 + lj, ny) * NX + I0;
             const size_t a0 = e0 & ~(size_t)(G::A - 1);
@@ -1425,7 +1426,7 @@ __device__ __forceinline__ void cheb_stage_region(const T* const* bases, int nx,
         const size_t g = (size_t)mirror_node(J0 + lj, ny) * NX + mirror_node(I0 + li, nx);
         const unsigned s = s0 + (unsigned)((lj * G::SP + li) * sizeof(T));
 #pragma unroll
-        for (int p = 0; p < kPlanes; ++p) cp_async_elem<sizeof(T)>(s + p * PB, bases[p] + g);
+        for (int p = 0; p < NP; ++p) cp_async_elem<sizeof(T)>(s + p * PB, bases[p] + g);
     }
     cp_async_commit();
 }
@@ -1695,6 +1696,162 @@ __device__ __forceinline__ void cheb_region_reg2(const Rows<float>& Rw, const fl
         const size_t g = (size_t)gJ * NX + gI0;
         if (li >= K && li < RW - K && gI0 <= nx) { xo[g] = x[r].x; xpo[g] = xa[r].x; }
         if (li + 1 >= K && li + 1 < RW - K && gI1 <= nx) { xo[g + 1] = x[r].y; xpo[g + 1] = xa[r].y; }
+    }
+}
+
+// Planes of a region staged for the cyclic form of the pass (one iterate, no x_prev).
+enum { kRbX = 0, kRbB, kRbC, kRbW, kRbE, kRbS, kRbN, kRbPlanes };
+
+template <typename T, int R, int NW>
+constexpr size_t cheb_rb_smem()
+{
+    using G = RegionGeom<T, 64, R * NW>;
+    static_assert((kRbPlanes * G::PLN * sizeof(T)) % 16 == 0, "exchange rows 16-byte aligned");
+    return ((size_t)kRbPlanes * G::PLN + (size_t)2 * NW * 2 * 64) * sizeof(T);
+}
+
+template <typename T> struct Pair2;
+template <> struct Pair2<float> { using V = float2; };
+template <> struct Pair2<double> { using V = double2; };
+
+// Cyclic form of the Chebyshev-scheduled Jacobi pass: regions of 64 x (R NW) nodes, two
+// columns per lane, R rows per warp (R even), K steps per pass (K even).
+//   A row of M couples a node with its four neighbours only, and they have the other colour
+// (I + J) mod 2 (so do mirror images: a node and its image lie an even number of nodes
+// apart), so D^-1 (M - D) maps each colour to the other.  The Chebyshev interval
+// [1 - g, 1 + g] is centred at 1, so the weights satisfy c1 = c2 - 1 and the step
+// x_{k+1} = x_k + c1 (x_k - x_{k-1}) + c2 r_k equals c2 (D^-1 b - D^-1 (M - D) x_k) +
+// (1 - c2) x_{k-1}: a node at step k + 1 needs its neighbours at step k and itself at step
+// k - 1 only.  One colour at the odd steps and the other at the even steps therefore form a
+// closed recurrence (the cyclic Chebyshev semi-iterative method of Golub and Varga, 1961),
+// computed here in place: step s of a solve updates the nodes of colour s mod 2 by
+// x <- x + c2 r, r = D^-1 b - x - D^-1 (M - D) x their scaled residual.  A step touches
+// half the nodes of a Jacobi sweep and the pass carries one iterate; every node takes the
+// values of the full iteration at the steps of its colour (up to rounding).
+//   K is even, so each pass starts with colour 1.  The pass writes x of the tile interior
+// (colour 0 at step K, colour 1 at step K - 1) and measures the vector of colour 0 at step
+// K - 2 and colour 1 at step K - 1, whose scaled residual is (1 - c2) r at the colour-1
+// nodes of step K - 1 and r at the colour-0 nodes of step K.  stage_next as in
+// cheb_region_reg.
+template <typename T, int R, int NW, int K, typename F>
+__device__ __forceinline__ void cheb_region_rb(const Rows<T>& Rw, const T* planes, T* exch,
+                                               const T* c2s, T rsc, int I0, int J0,
+                                               T* __restrict__ xo, NormAcc<T>& rsum, T& dmax,
+                                               F stage_next)
+{
+    constexpr int RW = 64, RH = R * NW;
+    static_assert(R % 2 == 0 && K % 2 == 0, "colours uniform over the block; passes of even length");
+    using G = RegionGeom<T, RW, RH>;
+    using V2 = typename Pair2<T>::V;
+    const int nx = Rw.nx, ny = Rw.ny, NX = nx + 1;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T x[R][2], rb[R][2], wW[R][2], wE[R][2], wS[R][2], wN[R][2];
+    // registers from the planes; nodes outside the grid hold mirror images, whose W / E and
+    // S / N weights swap (tested only in regions that reach past the grid)
+    auto load = [&](auto edge) {
+        constexpr bool E = decltype(edge)::value;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int lj = R * w + r, gJ = J0 + lj;
+            const bool fy = E && (gJ < 0 || gJ > ny);
+            const int row = lj * G::SP + (E ? region_row_off<T, RW, RH>(I0, J0, lj, nx, ny)
+                                            : region_row_off_in<T, RW, RH>(I0, gJ, nx));
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int li = 2 * lane + c, gI = I0 + li;
+                const bool fx = E && (gI < 0 || gI > nx);
+                const int t = row + li;
+                const T ic = qdiv(T(1), planes[kRbC * G::PLN + t]);
+                x[r][c] = planes[kRbX * G::PLN + t];
+                rb[r][c] = mul_rn(planes[kRbB * G::PLN + t], ic);
+                const T cw = mul_rn(planes[kRbW * G::PLN + t], ic);
+                const T ce = mul_rn(planes[kRbE * G::PLN + t], ic);
+                const T cs = mul_rn(planes[kRbS * G::PLN + t], ic);
+                const T cn = mul_rn(planes[kRbN * G::PLN + t], ic);
+                wW[r][c] = fx ? ce : cw;
+                wE[r][c] = fx ? cw : ce;
+                wS[r][c] = fy ? cn : cs;
+                wN[r][c] = fy ? cs : cn;
+            }
+        }
+    };
+    if (I0 >= 0 && I0 + RW - 1 <= nx && J0 >= 0 && J0 + RH - 1 <= ny)
+        load(std::false_type{});
+    else
+        load(std::true_type{});
+    bool okc[2], okr[R];   // the tile interior inside the grid
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const int li = 2 * lane + c;
+        okc[c] = li >= K && li < RW - K && I0 + li <= nx;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int lj = R * w + r;
+        okr[r] = lj >= K && lj < RH - K && J0 + lj <= ny;
+    }
+    const int lo_row = (w > 0 ? 2 * w - 1 : 2 * w) * RW, hi_row = (w < NW - 1 ? 2 * w + 2 : 2 * w + 1) * RW;
+    stage_next(-1);
+    __syncthreads();   // every warp has its registers: the planes may be refilled
+    stage_next(0);
+    T part = T(0);   // squared scaled residuals of this thread's nodes (rsc: exact 2^-e)
+    // node (r, c) of this thread has colour (I0 + J0 + R w + r + c) mod 2; R is even, so
+    // the block's colours are fixed by Q = (I0 + J0) mod 2
+    auto steps = [&](auto qc) {
+        constexpr int Q = decltype(qc)::value;
+#pragma unroll
+        for (int sw = 0; sw < K; ++sw) {
+            T* e = exch + (sw & 1) * (NW * 2 * RW);
+            reinterpret_cast<V2*>(e + (2 * w) * RW)[lane] = V2{x[0][0], x[0][1]};
+            reinterpret_cast<V2*>(e + (2 * w + 1) * RW)[lane] = V2{x[R - 1][0], x[R - 1][1]};
+            __syncthreads();
+            const V2 lo2 = reinterpret_cast<const V2*>(e + lo_row)[lane];
+            const V2 hi2 = reinterpret_cast<const V2*>(e + hi_row)[lane];
+            const T lo[2] = {lo2.x, lo2.y}, hi[2] = {hi2.x, hi2.y};
+            const T c2 = c2s[sw];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int cu = (Q + r + sw + 1) & 1;   // the column of colour (sw + 1) mod 2
+                // (lanes 0 and 31 read their own values: halo columns of the region, whose
+                // errors do not reach the interior within the K steps)
+                T xw, xe;
+                if (cu == 0) {
+                    xw = __shfl_up_sync(0xffffffffu, x[r][1], 1);
+                    xe = x[r][1];
+                } else {
+                    xw = x[r][0];
+                    xe = __shfl_down_sync(0xffffffffu, x[r][0], 1);
+                }
+                const T xs = r == 0 ? lo[cu] : x[r - 1][cu];
+                const T xn = r == R - 1 ? hi[cu] : x[r + 1][cu];
+                const T xc = x[r][cu];
+                const T res = cheb_resid(rb[r][cu], xc, wW[r][cu], xw, wE[r][cu], xe,
+                                         wS[r][cu], xs, wN[r][cu], xn);
+                const T v = fma(c2, res, xc);
+                x[r][cu] = v;
+                if (sw >= K - 2) {
+                    if (okr[r] && okc[cu]) {
+                        const T rz = (sw == K - 2 ? (T(1) - c2) * res : res) * rsc;
+                        part = fma(rz, rz, part);
+                        dmax = tmax(dmax, T(fabs(v - xc)));
+                    }
+                }
+            }
+        }
+    };
+    if (((I0 + J0) & 1) == 0)
+        steps(std::integral_constant<int, 0>{});
+    else
+        steps(std::integral_constant<int, 1>{});
+    norm_add(rsum, part);   // scaled; the block applies 1 / rsc^2
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int gJ = J0 + R * w + r;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int gI = I0 + 2 * lane + c;
+            if (okr[r] && okc[c]) xo[(size_t)gJ * NX + gI] = x[r][c];
+        }
     }
 }
 

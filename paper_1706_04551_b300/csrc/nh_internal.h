@@ -148,7 +148,8 @@ size_t cheb_tiles(const Prm<T>& P);
 template <typename T>
 size_t asm_tiles(const Prm<T>& P);   // blocks of the 2D assembly (3 partials each)
 // One pass: (x, x_{k-1}) from (xi, xpi) to (xo, xpo) in kernel form `variant` (0 ..
-// cheb_pass_forms() - 1, listed at the definition).  The register forms wait at most
+// cheb_pass_forms() - 1, listed at the definition; the cyclic forms after them read xi and
+// write xo only).  The register forms wait at most
 // `polls` polls for each region's staged copies; stall_block >= 0 makes that block's first
 // wait run out with no copy issued (a test hook; -1 in normal use).
 template <typename T>
@@ -157,7 +158,9 @@ int launch_cheb_pass(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, const T*
                      unsigned polls, int stall_block);
 constexpr unsigned kDefaultWaitPolls = 1u << 22;   // nh_params.wait_polls <= 0
 template <typename T>
-int cheb_pass_forms();   // number of pass forms (variants 0 .. n-1)
+int cheb_pass_forms();   // number of Jacobi pass forms (variants 0 .. n-1)
+template <typename T>
+int cheb_cyclic_forms();   // number of cyclic forms (variants n .. n + this - 1)
 template <typename T>
 void launch_matvec2d(const Prm<T>& P, const Launch& L, const Bufs<T>& B, const T* x, T* y);
 template <typename T>

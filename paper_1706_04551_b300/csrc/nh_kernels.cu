@@ -437,6 +437,91 @@ k_cheb_reg(Rows<T> Rw, const T* __restrict__ b, const T* __restrict__ xi,
         cheb_finish_stall(ctl, acc, K);
 }
 
+// Cyclic form of the pass (cheb_region_rb): regions of 64 x (R NW) nodes, one persistent
+// block per SM walking them, the next region's seven planes fetched by bulk copies during
+// the steps; waits, time-out and test hook as in k_cheb_reg.  x only: the pass reads xi
+// and writes xo (no previous iterate).
+template <typename T, int R, int NW, int K>
+__global__ void __launch_bounds__(32 * NW, 1)
+k_cheb_rb(Rows<T> Rw, const T* __restrict__ b, const T* __restrict__ xi, T* __restrict__ xo,
+          double* partials, SolveCtl* ctl, int nrx, int nreg, unsigned polls, int stall_block)
+{
+    if (ctl->done) return;
+    constexpr int RW = 64, RH = R * NW, TX = RW - 2 * K, TY = RH - 2 * K;
+    using G = RegionGeom<T, RW, RH>;
+    extern __shared__ __align__(16) unsigned char cheb_rb_raw[];
+    T* planes = reinterpret_cast<T*>(cheb_rb_raw);
+    T* exch = planes + kRbPlanes * G::PLN;
+    __shared__ T c2s[K];
+    __shared__ const T* bases[kRbPlanes];
+    __shared__ __align__(8) unsigned long long bar;
+    const int tid = threadIdx.x, nx = Rw.nx, ny = Rw.ny;
+    if (tid < K) c2s[tid] = sizeof(T) == 4 ? (T)ctl->c2f[tid] : (T)ctl->c2[tid];
+    const T rsc = sizeof(T) == 4 ? (T)ctl->rscf : (T)ctl->rscd;
+    const double rinv2 = ctl->rinv2;
+    int g = blockIdx.x, gx = g % nrx, gy = g / nrx;
+    const int dgx = (int)gridDim.x % nrx, dgy = (int)gridDim.x / nrx;
+    auto step = [&](int& x, int& y) {
+        x += dgx;
+        y += dgy;
+        if (x >= nrx) { x -= nrx; ++y; }
+    };
+    auto I0of = [&](int x) { return x * TX - K; };
+    auto J0of = [&](int y) { return y * TY - K; };
+    const bool stall = (int)blockIdx.x == stall_block;
+    if (tid == 0) {
+        bases[kRbX] = xi; bases[kRbB] = b; bases[kRbC] = Rw.cC; bases[kRbW] = Rw.cW;
+        bases[kRbE] = Rw.cE; bases[kRbS] = Rw.cS; bases[kRbN] = Rw.cN;
+        mbar_init(&bar, 1);
+        if (g < nreg)
+            mbar_arrive_expect_tx(&bar, stall ? 16u
+                                              : region_bulk_bytes<T, RW, RH, kRbPlanes>(I0of(gx), nx));
+    }
+    __syncthreads();
+    if (g < nreg && !stall)
+        cheb_stage_region<T, RW, RH, 32 * NW, kRbPlanes>(bases, nx, ny, I0of(gx), J0of(gy),
+                                                         planes, &bar);
+    NormAcc<T> rsum;
+    norm_zero(rsum);
+    T dmax = T(0);
+    unsigned phase = 0;
+    bool ok = true;
+    for (; g < nreg; g += gridDim.x) {
+        cp_async_wait_all();
+        const bool got = mbar_wait_bounded(&bar, phase, polls);
+        if (__syncthreads_or(!got)) { ok = false; break; }
+        phase ^= 1u;
+        const int nxt = g + gridDim.x;
+        int nx_ = gx, ny_ = gy;
+        step(nx_, ny_);
+        auto next = [&](int part) {
+            if (nxt >= nreg) return;
+            if (part < 0) {   // before the barrier that frees the planes
+                fence_proxy_async_smem();
+                if (tid == 0)
+                    mbar_arrive_expect_tx(&bar, region_bulk_bytes<T, RW, RH, kRbPlanes>(I0of(nx_), nx));
+            } else {
+                cheb_stage_region<T, RW, RH, 32 * NW, kRbPlanes>(bases, nx, ny, I0of(nx_),
+                                                                 J0of(ny_), planes, &bar);
+            }
+        };
+        cheb_region_rb<T, R, NW, K>(Rw, planes, exch, c2s, rsc, I0of(gx), J0of(gy), xo, rsum,
+                                    dmax, next);
+        gx = nx_;
+        gy = ny_;
+    }
+    if (!ok) {
+        const bool issued = !(stall && g == (int)blockIdx.x);
+        const bool drained = cheb_drain(&bar, phase, issued);
+        if (tid == 0) { ctl->status = drained ? 6 : 7; ctl->done = 1; }
+    }
+    double acc[2];
+    if (dom_reduce_sum_max<T>(rsum, (double)dmax, rinv2, partials, &ctl->counter, acc,
+                              blockIdx.x, gridDim.x) &&
+        threadIdx.x == 0 && ok)
+        cheb_finish_stall(ctl, acc, K);
+}
+
 template <typename T, int TX, int TY>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
 k_corr2d_t(Prm<T> P, const T* __restrict__ eta, const T* __restrict__ H,
@@ -1205,6 +1290,35 @@ int launch_cheb_reg(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, const T* 
     return 0;
 }
 
+// Cyclic form: region 64 x (R NW) nodes, 32 NW threads, one resident block per SM.
+template <typename T, int R, int NW, int K>
+int launch_cheb_rb(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, const T* xi, T* xo,
+                   double* partials, unsigned polls, int stall_block)
+{
+    constexpr int TX = 64 - 2 * K, TY = R * NW - 2 * K;
+    constexpr size_t smem = cheb_rb_smem<T, R, NW>();
+    static int nblk = 0;
+    if (nblk == 0) {
+        if (cudaFuncSetAttribute(k_cheb_rb<T, R, NW, K>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return -1;
+        int dev = 0, nsm = 0, occ = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cheb_rb<T, R, NW, K>,
+                                                          32 * NW, smem) != cudaSuccess ||
+            occ < 1)
+            return -1;
+        nblk = nsm * occ;
+    }
+    const int nrx = (P.nx + 1 + TX - 1) / TX, nry = (P.ny + 1 + TY - 1) / TY;
+    const int nreg = nrx * nry;
+    k_cheb_rb<T, R, NW, K><<<nreg < nblk ? nreg : nblk, 32 * NW, smem, s>>>(
+        rows_of(P, B), B.rhs, xi, xo, partials, B.sctl, nrx, nreg, polls, stall_block);
+    return 0;
+}
+
 // The pass forms the handle chooses from by timing its first passes; all forms of a
 // precision sweep the same number of times per pass (K) and give the same iterates.
 // FP32 (K = 8, weights in registers, padded buffers): 0: 64x64 region, 1024 threads;
@@ -1214,7 +1328,12 @@ int launch_cheb_reg(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, const T* 
 // threads; 7: 96x64, 512 threads.
 // FP64 (K = 4): 0: 64x32, shared-memory weights; 1: 64x32, registers; 2: 64x32, registers,
 // padded; 3: register form, 64x32, 512 threads.
+// The cyclic forms (k_cheb_rb, one colour per step) follow: FP32 8: 64x96 region, 512
+// threads; 9: 64x64, 512 threads; 10: 64x64, 1024 threads; FP64 4: 64x32, 512 threads.  They
+// give the same iterates as each other (not those of the Jacobi forms), so they are timed
+// against each other only.
 template <typename T> int cheb_pass_forms() { return sizeof(T) == 4 ? 8 : 4; }
+template <typename T> int cheb_cyclic_forms() { return sizeof(T) == 4 ? 3 : 1; }
 
 template <typename T>
 int launch_cheb_pass(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, const T* xi,
@@ -1230,9 +1349,13 @@ int launch_cheb_pass(const Prm<T>& P, cudaStream_t s, const Bufs<T>& B, const T*
         case 5: return launch_cheb_reg<T, 2, 4, 16, 8>(P, s, B, xi, xpi, xo, xpo, partials, polls, stall_block);
         case 6: return launch_cheb_reg<T, 2, 2, 32, 8>(P, s, B, xi, xpi, xo, xpo, partials, polls, stall_block);
         case 7: return launch_cheb_reg<T, 3, 4, 16, 8>(P, s, B, xi, xpi, xo, xpo, partials, polls, stall_block);
+        case 8: return launch_cheb_rb<T, 6, 16, 8>(P, s, B, xi, xo, partials, polls, stall_block);
+        case 9: return launch_cheb_rb<T, 4, 16, 8>(P, s, B, xi, xo, partials, polls, stall_block);
+        case 10: return launch_cheb_rb<T, 2, 32, 8>(P, s, B, xi, xo, partials, polls, stall_block);
         default: return launch_cheb_cfg<T, 2, 2, 32, true, 1, true, 8>(P, s, B, xi, xpi, xo, xpo, partials);
         }
     } else {
+        if (variant == 4) return launch_cheb_rb<T, 2, 16, 4>(P, s, B, xi, xo, partials, polls, stall_block);
         if (variant == 1) return launch_cheb_cfg<T, 2, 2, 16, true, 1>(P, s, B, xi, xpi, xo, xpo, partials);
         if (variant == 2) return launch_cheb_cfg<T, 2, 2, 16, true, 1, true>(P, s, B, xi, xpi, xo, xpo, partials);
         if (variant == 3) return launch_cheb_reg<T, 2, 2, 16, 4>(P, s, B, xi, xpi, xo, xpo, partials, polls, stall_block);
@@ -1509,6 +1632,7 @@ void launch_convert_from_double(const Launch& L, const double* src, T* dst, size
     template size_t cheb_tiles<T>(const Prm<T>&);                                              \
     template size_t asm_tiles<T>(const Prm<T>&);                                               \
     template int cheb_pass_forms<T>();                                                          \
+    template int cheb_cyclic_forms<T>();                                                        \
     template int launch_cheb_pass<T>(const Prm<T>&, cudaStream_t, const Bufs<T>&, const T*,   \
                                      const T*, T*, T*, double*, int, unsigned, int);            \
     template void launch_matvec2d<T>(const Prm<T>&, const Launch&, const Bufs<T>&, const T*,   \

@@ -37,7 +37,8 @@ class Params(C.Structure):
                 ("adjoint_frozen_limiter", C.c_int), ("cheb_form", C.c_int),
                 ("w_equation", C.c_int), ("relax_width", C.c_double * 4),
                 ("dry_zero", C.c_int), ("wait_polls", C.c_int), ("capture", C.c_int),
-                ("refine_fp32", C.c_int), ("fallback_block_nodes", C.c_int)]
+                ("refine_fp32", C.c_int), ("fallback_block_nodes", C.c_int),
+                ("cheb_cyclic", C.c_int)]
 
 
 class StatsT(C.Structure):
@@ -69,7 +70,8 @@ EXPORTS = ("nh_default_params", "nh_create", "nh_set_state", "nh_get_state", "nh
            "nh_batch_stats", "nh_batch_get_tuning", "nh_batch_set_tuning",
            "nh_batch_candidate", "nh_batch_last_error", "nh_batch_destroy",
            "nh_batch_profile_enable", "nh_batch_profile_read", "nh_tape_bytes",
-           "nh_step_taped", "nh_adjoint_step", "nh_cheb_forms", "nh_set_relax_target",
+           "nh_step_taped", "nh_adjoint_step", "nh_cheb_forms", "nh_cheb_cyclic_forms",
+           "nh_set_relax_target",
            "nh_debug_stall_copies", "nh_gauges")
 
 BATCH_AUTOTUNE, BATCH_GRAPH = 1, 2
@@ -135,6 +137,7 @@ def load():
     L.nh_batch_profile_enable.argtypes = [H, C.c_int]
     L.nh_batch_profile_read.argtypes = [H, C.POINTER(ProfileT)]
     L.nh_cheb_forms.argtypes = [C.c_int]
+    L.nh_cheb_cyclic_forms.argtypes = [C.c_int]
     _lib = L
     return L
 
@@ -148,6 +151,14 @@ def default_params() -> Params:
 def cheb_forms(precision: str = "fp32") -> int:
     """Number of kernel forms of the Chebyshev pass (values of the cheb_form parameter)."""
     n = load().nh_cheb_forms(FP32 if precision == "fp32" else FP64)
+    if n < 0:
+        raise ValueError(precision)
+    return n
+
+
+def cheb_cyclic_forms(precision: str = "fp32") -> int:
+    """Number of kernel forms of the cyclic pass (reported as cheb_form = cheb_forms() + k)."""
+    n = load().nh_cheb_cyclic_forms(FP32 if precision == "fp32" else FP64)
     if n < 0:
         raise ValueError(precision)
     return n

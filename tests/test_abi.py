@@ -33,6 +33,8 @@ def test_binding_loads_and_default_params():
     assert p.dry_zero == 1 and p.wait_polls == 0
     # steps captured as graphs; small batched fallback solves in one block each
     assert p.capture == 1 and p.fallback_block_nodes == 70000
+    # the cyclic form of the Chebyshev pass
+    assert p.cheb_cyclic == 1
 
 
 def test_create_rejects_bad_grid_without_touching_the_gpu():
@@ -54,18 +56,27 @@ def test_cheb_forms_and_bad_form_rejected_without_touching_the_gpu():
     B.build()
     L = nh.load()
     assert nh.cheb_forms("fp32") == 8 and nh.cheb_forms("fp64") == 4
-    assert L.nh_cheb_forms(7) == nh.EINVAL
+    assert nh.cheb_cyclic_forms("fp32") == 3 and nh.cheb_cyclic_forms("fp64") == 1
+    assert L.nh_cheb_forms(7) == nh.EINVAL and L.nh_cheb_cyclic_forms(7) == nh.EINVAL
     p = nh.default_params()
     assert p.cheb_form == -1
     g = nh.Grid()
     g.dim, g.nx, g.ny, g.dx, g.dy = 2, 8, 8, 0.1, 0.1
     H = np.ones(64)
-    for prec, bad in ((nh.FP32, 8), (nh.FP64, 4), (nh.FP32, -2)):
+    # past the Jacobi forms come the cyclic ones (FP32 8-10, FP64 4)
+    for prec, bad in ((nh.FP32, 11), (nh.FP64, 5), (nh.FP32, -2)):
         p.precision, p.cheb_form = prec, bad
         h = ctypes.c_void_p()
         rc = L.nh_create(ctypes.byref(g), H.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                          ctypes.byref(p), None, ctypes.byref(h))
         assert rc == nh.EINVAL and not h.value
+    # the cyclic form is a switch (the form number nh_cheb_forms reports it under is not a
+    # value of cheb_form)
+    p.cheb_form, p.cheb_cyclic = -1, 2
+    h = ctypes.c_void_p()
+    rc = L.nh_create(ctypes.byref(g), H.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                     ctypes.byref(p), None, ctypes.byref(h))
+    assert rc == nh.EINVAL and not h.value
 
 
 def test_periodic_only_on_both_ends_of_1d_channels():

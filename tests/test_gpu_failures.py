@@ -64,9 +64,11 @@ def test_iteration_cap_returns_enoconv_and_the_step_is_taken(solver):
     s.close()
 
 
-@pytest.mark.parametrize("precision,form", [("fp32", 7), ("fp32", 5), ("fp64", 3)])
+@pytest.mark.parametrize("precision,form", [("fp32", 7), ("fp32", 5), ("fp64", 3), ("fp32", -1),
+                                            ("fp64", -1)])
 def test_bounded_wait_that_runs_out_returns_etimeout(precision, form):
-    """Block 0 of a register-form pass waits for a region whose copies were never issued:
+    """Block 0 of a register-form pass (form -1: the cyclic form, the default) waits for a
+    region whose copies were never issued:
     its wait runs out after wait_polls polls, the solve is abandoned with NH_ETIMEOUT, and a
     fresh handle on the same device then steps normally (the context is intact)."""
     wl = shoals(128)
