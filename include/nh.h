@@ -152,18 +152,22 @@ typedef struct {
                            grid-wide BiCGStab after the passes.  Single-domain handles
                            ignore it.                                                     */
     int cheb_cyclic;    /* single-domain 2D handles, Chebyshev solver, cheb_form = -1 and
-                           eps_dp = 0: 1 (default) = the cyclic form of the pass.  The
-                           five-point rows couple each node with nodes of the other colour
-                           (I + J) mod 2 only, and the Chebyshev interval is centred at 1, so
-                           the nodes of one colour at the odd steps and of the other at the
-                           even steps form a closed recurrence (Golub and Varga's cyclic
-                           Chebyshev method): each step updates one colour in place, half
-                           the work of a Jacobi sweep, and every node takes the values of
-                           the full iteration at the steps of its colour.  Its kernel forms
+                           eps_dp = 0: the cyclic form of the pass.  The five-point rows
+                           couple each node with nodes of the other colour (I + J) mod 2
+                           only, and the Chebyshev interval is centred at 1, so the nodes of
+                           one colour at the odd steps and of the other at the even steps
+                           form a closed recurrence (Golub and Varga's cyclic Chebyshev
+                           method): each step updates one colour in place, half the work of
+                           a Jacobi sweep, and every node takes the values of the full
+                           iteration at the steps of its colour.  Its stopping test measures
+                           a vector whose colours lie one step apart, which takes more steps
+                           than the Jacobi forms' sweeps (58 against 53 per stage on the
+                           4096^2 island, 36 against 32 on the 1024^2 shoals), and is still
+                           faster on every grid measured.  1 (default) = the cyclic form;
+                           0 = the Jacobi forms (cheb_form).  Its kernel forms
                            (nh_cheb_cyclic_forms) are chosen by timing.  last_iters and
-                           solver_iters count these steps.  The inner solves of refine_fp32
-                           use it too.  0 = the Jacobi forms (cheb_form).  Batches ignore
-                           it.                                                            */
+                           solver_iters count its steps.  The FP32 inner solves of
+                           refine_fp32 use it too.  Batches ignore it.                   */
 } nh_params;
 
 typedef struct {

@@ -179,16 +179,16 @@ struct Impl : Base {
         P.g = (T)q.g; P.delta = (T)q.delta; P.hdry = (T)q.hdry; P.manning = (T)q.manning_n;
         P.B1 = (T)q.B1; P.breaking = q.breaking; P.dry_zero = q.dry_zero ? 1 : 0;
         pass_variant = q.cheb_form;
-        // the cyclic forms are timed against each other (the same iterates), not against
-        // the Jacobi forms
-        cyclic = q.cheb_form < 0 && q.cheb_cyclic && !(q.eps_dp > 0.0) && dim == 2;
-        if (cyclic && cheb_cyclic_forms<T>() == 1) pass_variant = cheb_pass_forms<T>();
         nc = (size_t)g.nx * g.ny;
         nn = dim == 2 ? (size_t)(g.nx + 1) * (g.ny + 1) : (size_t)(g.nx + 1) * g.ny;
         int dev = 0, nsm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         if (nsm <= 0) nsm = 148;
+        // the cyclic forms are timed against each other (the same iterates), not against
+        // the Jacobi forms
+        cyclic = q.cheb_form < 0 && q.cheb_cyclic && !(q.eps_dp > 0.0) && dim == 2;
+        if (cyclic && cheb_cyclic_forms<T>() == 1) pass_variant = cheb_pass_forms<T>();
         auto grid_for = [&](size_t n) {
             long long want = (long long)((n + 255) / 256);
             long long cap = (long long)nsm * 8;

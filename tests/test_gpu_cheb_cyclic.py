@@ -1,8 +1,8 @@
 """The cyclic form of the Chebyshev-scheduled Jacobi pass (nh_params.cheb_cyclic, the
-default for single-domain 2D handles): each step updates the nodes of one colour
-(I + J) mod 2 in place, half the node updates of a Jacobi sweep, and every node takes the
-values of the full iteration at the steps of its colour.  Checked against the FP64 oracle,
-against the Jacobi forms of the pass, graph against eager, and at rest."""
+default for single-domain 2D handles): each step updates the nodes of one colour (I + J) mod 2 in place,
+half the node updates of a Jacobi sweep, and every node takes the values of the full
+iteration at the steps of its colour.  Checked against the FP64 oracle, against the Jacobi
+forms of the pass, graph against eager, and at rest."""
 import numpy as np
 import pytest
 
@@ -19,6 +19,7 @@ def island(n):
 
 
 def _steps(wl, precision, steps, state, **kw):
+    kw.setdefault("cheb_cyclic", 1)
     sim, _ = make(wl, precision, **kw)
     eta, q1, q2 = state
     sim.set_state(eta.astype(sim.dtype), q1.astype(sim.dtype), q2.astype(sim.dtype))
@@ -42,7 +43,7 @@ def test_cyclic_form_is_the_default_where_it_applies(precision):
     wl = inputs.shoals_2d(n=96)
     nf = nh.cheb_forms(precision)
     st = developed(wl, seed=1)
-    _, s, _ = _steps(wl, precision, 8, st)
+    _, s, _ = _steps(wl, precision, 8, st, cheb_cyclic=nh.default_params().cheb_cyclic)
     assert cyclic_form(s, precision), s["cheb_form"]
     # switched off, or under criterion (32), or with a form named: the Jacobi forms
     _, s, _ = _steps(wl, precision, 1, st, cheb_cyclic=0)
@@ -78,7 +79,7 @@ def test_cyclic_fp64_shoals_against_oracle():
 def test_cyclic_fp32_against_oracle(which):
     """FP32 (tol 1e-5): eta within 1e-4 of the FP64 oracle after 6 steps."""
     wl = inputs.shoals_2d(n=203) if which == "shoals" else island(150)
-    sim, g, (h, q1, q2, w, p, t, s, it) = _run_both(wl, 6, "fp32", tol=1e-5)
+    sim, g, (h, q1, q2, w, p, t, s, it) = _run_both(wl, 6, "fp32", tol=1e-5, cheb_cyclic=1)
     assert cyclic_form(sim.stats(), "fp32")
     assert rel(g["eta"], h - wl.H) < 1e-4
 
@@ -138,7 +139,7 @@ def test_cyclic_graph_equals_eager():
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_cyclic_lake_at_rest_exact(precision):
     wl = island(150)
-    sim, _ = make(wl, precision)
+    sim, _ = make(wl, precision, cheb_cyclic=1)
     eta0 = np.where(wl.H > 0, 0.0, -wl.H).astype(sim.dtype)
     z = np.zeros_like(eta0)
     sim.set_state(eta0, z, z)

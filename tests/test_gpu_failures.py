@@ -72,7 +72,8 @@ def test_bounded_wait_that_runs_out_returns_etimeout(precision, form):
     its wait runs out after wait_polls polls, the solve is abandoned with NH_ETIMEOUT, and a
     fresh handle on the same device then steps normally (the context is intact)."""
     wl = shoals(128)
-    s = sim(wl, precision, cheb_form=form, wait_polls=64)
+    cyc = dict(cheb_cyclic=1) if form < 0 else {}
+    s = sim(wl, precision, cheb_form=form, wait_polls=64, **cyc)
     s.set_state(*state(wl, s.dtype))
     s.debug_stall_copies(0)
     with pytest.raises(nh.NHError) as ei:
@@ -80,7 +81,7 @@ def test_bounded_wait_that_runs_out_returns_etimeout(precision, form):
     assert ei.value.code == nh.ETIMEOUT, ei.value
     assert "ran out of polls" in str(ei.value)
     s.close()
-    ok = sim(wl, precision, cheb_form=form)
+    ok = sim(wl, precision, cheb_form=form, **cyc)
     ok.set_state(*state(wl, ok.dtype))
     for _ in range(2):
         ok.step()
