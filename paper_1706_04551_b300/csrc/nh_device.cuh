@@ -1400,18 +1400,19 @@ __device__ __forceinline__ unsigned region_bulk_bytes(int I0, int nx)
 
 // Issue the copies of region (I0, J0)'s NP planes (nodes outside the grid read their
 // mirror image, as the wall and outflow rows of M prescribe).  bases: the NP source
-// arrays in plane order.  Bulk copies complete on `bar` (whose expected bytes the caller
+// arrays in plane order; planes p0 .. p1 - 1 only.  Bulk copies complete on `bar` (whose expected bytes the caller
 // announced); element copies are committed as one cp.async group.
 template <typename T, int RW, int RH, int NTHR, int NP = kPlanes>
 __device__ __forceinline__ void cheb_stage_region(const T* const* bases, int nx, int ny,
                                                   int I0, int J0, T* planes,
-                                                  unsigned long long* bar)
+                                                  unsigned long long* bar, int p0 = 0,
+                                                  int p1 = NP)
 {
     using G = RegionGeom<T, RW, RH>;
     const int NX = nx + 1;
     const int tid = threadIdx.x;
     if (G::bulk(I0, NX)) {
-        for (int c = tid; c < NP * RH; c += NTHR) {
+        for (int c = p0 * RH + tid; c < p1 * RH; c += NTHR) {
             const int p = c / RH, lj = c - p * RH;
             const size_t e0 = (size_t)mirror_node(J0 + lj, ny) * NX + I0;
             const size_t a0 = e0 & ~(size_t)(G::A - 1);
@@ -1426,7 +1427,7 @@ __device__ __forceinline__ void cheb_stage_region(const T* const* bases, int nx,
         const size_t g = (size_t)mirror_node(J0 + lj, ny) * NX + mirror_node(I0 + li, nx);
         const unsigned s = s0 + (unsigned)((lj * G::SP + li) * sizeof(T));
 #pragma unroll
-        for (int p = 0; p < NP; ++p) cp_async_elem<sizeof(T)>(s + p * PB, bases[p] + g);
+        for (int p = p0; p < p1; ++p) cp_async_elem<sizeof(T)>(s + p * PB, bases[p] + g);
     }
     cp_async_commit();
 }
@@ -1700,7 +1701,9 @@ __device__ __forceinline__ void cheb_region_reg2(const Rows<float>& Rw, const fl
 }
 
 // Planes of a region staged for the cyclic form of the pass (one iterate, no x_prev).
-enum { kRbX = 0, kRbB, kRbC, kRbW, kRbE, kRbS, kRbN, kRbPlanes };
+// The coefficient planes come first: a region reads them into registers and releases them
+// (planes 0 .. kRbRows - 1) before it reads x and b.
+enum { kRbC = 0, kRbW, kRbE, kRbS, kRbN, kRbRows, kRbX = kRbRows, kRbB, kRbPlanes };
 
 template <typename T, int R, int NW>
 constexpr size_t cheb_rb_smem()
@@ -1731,8 +1734,11 @@ template <> struct Pair2<double> { using V = double2; };
 //   K is even, so each pass starts with colour 1.  The pass writes x of the tile interior
 // (colour 0 at step K, colour 1 at step K - 1) and measures the vector of colour 0 at step
 // K - 2 and colour 1 at step K - 1, whose scaled residual is (1 - c2) r at the colour-1
-// nodes of step K - 1 and r at the colour-0 nodes of step K.  stage_next as in
-// cheb_region_reg.
+// nodes of step K - 1 and r at the colour-0 nodes of step K.
+//   stage_next(-1): fence this thread's plane reads and announce the next region's bytes
+// (before the barrier that releases the coefficient planes); stage_next(1): issue the copies
+// of those planes; stage_next(-2): fence the reads of x and b; stage_next(2), after the
+// first step's barrier: issue the copies of the x and b planes.
 template <typename T, int R, int NW, int K, typename F>
 __device__ __forceinline__ void cheb_region_rb(const Rows<T>& Rw, const T* planes, T* exch,
                                                const T* c2s, T rsc, int I0, int J0,
@@ -1746,10 +1752,13 @@ __device__ __forceinline__ void cheb_region_rb(const Rows<T>& Rw, const T* plane
     const int nx = Rw.nx, ny = Rw.ny, NX = nx + 1;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     T x[R][2], rb[R][2], wW[R][2], wE[R][2], wS[R][2], wN[R][2];
-    // registers from the planes; nodes outside the grid hold mirror images, whose W / E and
-    // S / N weights swap (tested only in regions that reach past the grid)
-    auto load = [&](auto edge) {
-        constexpr bool E = decltype(edge)::value;
+    // registers from the planes in two groups, the coefficients first (their planes are
+    // released, and the next region's copies into them issued, while x and b are read);
+    // nodes outside the grid hold mirror images, whose W / E and S / N weights swap (tested
+    // only in regions that reach past the grid).  rb holds 1 / cC until b is read.
+    const bool edge = !(I0 >= 0 && I0 + RW - 1 <= nx && J0 >= 0 && J0 + RH - 1 <= ny);
+    auto rows = [&](auto e, auto body) {
+        constexpr bool E = decltype(e)::value;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int lj = R * w + r, gJ = J0 + lj;
@@ -1758,27 +1767,32 @@ __device__ __forceinline__ void cheb_region_rb(const Rows<T>& Rw, const T* plane
                                             : region_row_off_in<T, RW, RH>(I0, gJ, nx));
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
-                const int li = 2 * lane + c, gI = I0 + li;
-                const bool fx = E && (gI < 0 || gI > nx);
-                const int t = row + li;
-                const T ic = qdiv(T(1), planes[kRbC * G::PLN + t]);
-                x[r][c] = planes[kRbX * G::PLN + t];
-                rb[r][c] = mul_rn(planes[kRbB * G::PLN + t], ic);
-                const T cw = mul_rn(planes[kRbW * G::PLN + t], ic);
-                const T ce = mul_rn(planes[kRbE * G::PLN + t], ic);
-                const T cs = mul_rn(planes[kRbS * G::PLN + t], ic);
-                const T cn = mul_rn(planes[kRbN * G::PLN + t], ic);
-                wW[r][c] = fx ? ce : cw;
-                wE[r][c] = fx ? cw : ce;
-                wS[r][c] = fy ? cn : cs;
-                wN[r][c] = fy ? cs : cn;
+                const int gI = I0 + 2 * lane + c;
+                body(r, c, row + 2 * lane + c, E && (gI < 0 || gI > nx), fy);
             }
         }
     };
-    if (I0 >= 0 && I0 + RW - 1 <= nx && J0 >= 0 && J0 + RH - 1 <= ny)
-        load(std::false_type{});
-    else
-        load(std::true_type{});
+    auto coef = [&](int r, int c, int t, bool fx, bool fy) {
+        const T ic = qdiv(T(1), planes[kRbC * G::PLN + t]);
+        rb[r][c] = ic;
+        const T cw = mul_rn(planes[kRbW * G::PLN + t], ic);
+        const T ce = mul_rn(planes[kRbE * G::PLN + t], ic);
+        const T cs = mul_rn(planes[kRbS * G::PLN + t], ic);
+        const T cn = mul_rn(planes[kRbN * G::PLN + t], ic);
+        wW[r][c] = fx ? ce : cw;
+        wE[r][c] = fx ? cw : ce;
+        wS[r][c] = fy ? cn : cs;
+        wN[r][c] = fy ? cs : cn;
+    };
+    auto state = [&](int r, int c, int t, bool, bool) {
+        x[r][c] = planes[kRbX * G::PLN + t];
+        rb[r][c] = mul_rn(planes[kRbB * G::PLN + t], rb[r][c]);
+    };
+    if (edge) rows(std::true_type{}, coef); else rows(std::false_type{}, coef);
+    stage_next(-1);
+    __syncthreads();   // the coefficient planes may be refilled
+    stage_next(1);
+    if (edge) rows(std::true_type{}, state); else rows(std::false_type{}, state);
     bool okc[2], okr[R];   // the tile interior inside the grid
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
@@ -1791,9 +1805,8 @@ __device__ __forceinline__ void cheb_region_rb(const Rows<T>& Rw, const T* plane
         okr[r] = lj >= K && lj < RH - K && J0 + lj <= ny;
     }
     const int lo_row = (w > 0 ? 2 * w - 1 : 2 * w) * RW, hi_row = (w < NW - 1 ? 2 * w + 2 : 2 * w + 1) * RW;
-    stage_next(-1);
-    __syncthreads();   // every warp has its registers: the planes may be refilled
-    stage_next(0);
+    stage_next(-2);   // this thread's reads of x and b are done: the first step's barrier
+                      // releases those planes
     T part = T(0);   // squared scaled residuals of this thread's nodes (rsc: exact 2^-e)
     // node (r, c) of this thread has colour (I0 + J0 + R w + r + c) mod 2; R is even, so
     // the block's colours are fixed by Q = (I0 + J0) mod 2
@@ -1805,6 +1818,7 @@ __device__ __forceinline__ void cheb_region_rb(const Rows<T>& Rw, const T* plane
             reinterpret_cast<V2*>(e + (2 * w) * RW)[lane] = V2{x[0][0], x[0][1]};
             reinterpret_cast<V2*>(e + (2 * w + 1) * RW)[lane] = V2{x[R - 1][0], x[R - 1][1]};
             __syncthreads();
+            if (sw == 0) stage_next(2);   // the x and b planes of the next region
             const V2 lo2 = reinterpret_cast<const V2*>(e + lo_row)[lane];
             const V2 hi2 = reinterpret_cast<const V2*>(e + hi_row)[lane];
             const T lo[2] = {lo2.x, lo2.y}, hi[2] = {hi2.x, hi2.y};

@@ -496,13 +496,14 @@ k_cheb_rb(Rows<T> Rw, const T* __restrict__ b, const T* __restrict__ xi, T* __re
         step(nx_, ny_);
         auto next = [&](int part) {
             if (nxt >= nreg) return;
-            if (part < 0) {   // before the barrier that frees the planes
+            if (part < 0) {   // before a barrier that frees planes
                 fence_proxy_async_smem();
-                if (tid == 0)
+                if (part == -1 && tid == 0)
                     mbar_arrive_expect_tx(&bar, region_bulk_bytes<T, RW, RH, kRbPlanes>(I0of(nx_), nx));
             } else {
-                cheb_stage_region<T, RW, RH, 32 * NW, kRbPlanes>(bases, nx, ny, I0of(nx_),
-                                                                 J0of(ny_), planes, &bar);
+                cheb_stage_region<T, RW, RH, 32 * NW, kRbPlanes>(
+                    bases, nx, ny, I0of(nx_), J0of(ny_), planes, &bar, part == 1 ? 0 : kRbRows,
+                    part == 1 ? kRbRows : kRbPlanes);
             }
         };
         cheb_region_rb<T, R, NW, K>(Rw, planes, exch, c2s, rsc, I0of(gx), J0of(gy), xo, rsum,
